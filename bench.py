@@ -1,0 +1,337 @@
+#!/usr/bin/env python3
+"""Throughput of the Vlasov-Hybrid time step on GB300 (marker-steps/s).
+
+Default workload: the two-stream instability 1d1v in the FP32 production
+form (nx = 512, nv = 1024, 4 x 4 markers per cell, electrons + mobile ions,
+16.8 M markers, dt = 0.05), timed over K full steps (K = 2000 is the whole
+run, linear growth and nonlinear saturation) starting from t = 0.  One step
+is the whole hot path: gather + push, VHS reconstruction, moment, FP64
+Poisson, diagnostics and the re-sort check.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line.  --impl reference times the FP64 CPU oracle on the
+host cores instead (a bounded sample of the same workload per step).
+Under torchrun each rank runs an independent replica (weak scaling, no
+collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+KERNEL_NAMES = ["k_pd1", "k_fin1", "k_field", "k_sort"]
+LAUNCHES_PER_STEP = 6   # k_pd1, k_fin1, k_field, k_sort_count1, k_sort_scan, k_scatter1
+BYTES_PER_MARKER_ALGO = {"fp32": 20.0, "fp64": 40.0}      # read x, v, f; write x, v
+BYTES_PER_MARKER_LAYOUT = {"fp32": 28.0, "fp64": 40.0}    # int32 cell + f32 offset for x
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=2000)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--workload", choices=["two_stream", "landau"], default="two_stream")
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-cpu", action="store_true")
+    return p.parse_args()
+
+
+def workload(name):
+    from paper_1804_03901_gb300 import inputs
+    return inputs.two_stream() if name == "two_stream" else inputs.landau()
+
+
+def markers_of(w):
+    n = 0
+    for sp, lat in zip(w["species"], w["lattice"]):
+        n += w["nx"] * int(np.prod(sp["nv"])) * int(np.prod(lat))
+    return n
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    local = int(os.environ.get("LOCAL_RANK", 0))
+    return rank, world, local
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("k_vhs1.cu", "avl_internal.cuh", "ptx.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_1804_03901_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(workload_name, prec):
+    """DRAM bytes per marker of k_pd1 from the committed ncu summary, if it
+    was taken on the current kernel source."""
+    path = os.path.join(ROOT, "profiles", "k_pd1_traffic.json")
+    if not os.path.exists(path):
+        return None
+    d = json.load(open(path))
+    rec = d.get(f"{workload_name}:{prec}")
+    if not rec or rec.get("source_hash") != kernel_source_hash():
+        return None
+    return float(rec["dram_bytes_per_marker"])
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, dev):
+        self.dev = dev
+        self.proc = None
+        self.path = tempfile.mktemp(suffix=".csv")
+
+    def start(self):
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                          "-i", str(self.dev), "-lms", "200"], stdout=self.fh,
+                                         stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        self.proc.wait()
+        self.fh.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def build_sim(A, w, stream, seed_offset=0):
+    prec = A.AVL_FP32 if w["precision"] == "fp32" else A.AVL_FP64
+    dom = A.make_domain(w["nvdim"], w["nx"], w["L"], w["dt"], 1.0, True, prec)
+    sim = A.Simulation(dom, [A.make_species(**sp) for sp in w["species"]], stream=stream)
+    init_markers(A, sim, w, seed_offset)
+    return sim
+
+
+def init_markers(A, sim, w, seed_offset=0):
+    for s, (f0, lat) in enumerate(zip(w["f0"], w["lattice"])):
+        sim.init_markers(s, lat, A.make_f0(f0["beams"], f0["modes"]), w["seed"] + seed_offset, w["jitter"])
+
+
+def cpu_oracle_rate(w, budget_s=12.0, sample_fraction=1.0, steps=None, seed=0):
+    """Marker-steps/s of the FP64 oracle (single thread) on the workload, or on
+    a random marker subsample of it."""
+    from oracle import oracle as O
+    species = [O.Species(**sp) for sp in w["species"]]
+    sim = O.OracleSim(w["nvdim"], w["nx"], w["L"], w["dt"], species)
+    rng = np.random.default_rng(seed)
+    for s, (f0, lat) in enumerate(zip(w["f0"], w["lattice"])):
+        sim.init_markers(s, lat, O.F0(f0["beams"], f0["modes"]), w["seed"], w["jitter"])
+        if sample_fraction < 1.0:
+            n = sim.x[s].size
+            keep = rng.choice(n, max(1, int(n * sample_fraction)), replace=False)
+            sim.set_markers(s, sim.x[s][keep], sim.v[s][:, keep], sim.fl[s][keep])
+    sim.refresh()
+    nmark = sum(x.size for x in sim.x)
+    done, t0 = 0, time.perf_counter()
+    while True:
+        sim.step(1)
+        done += 1
+        el = time.perf_counter() - t0
+        if steps is not None and done >= steps:
+            break
+        if steps is None and (el > budget_s and done >= 2):
+            break
+    return nmark * done / el, nmark, done, el
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    w = workload(args.workload)
+    frac = 1.0 / 64 if args.workload == "two_stream" else 1.0
+    cpu_oracle_rate(w, sample_fraction=frac, steps=max(1, args.warmup))   # warm-up (page-in)
+    rate, nmark, done, el = cpu_oracle_rate(w, sample_fraction=frac, steps=args.steps)
+    sample = (f"FP64 oracle, 1 thread, {done} steps of the {w['name']} workload with a random "
+              f"{frac:.4g} marker subsample ({nmark} markers) on the full grids")
+    line = {"impl": "reference", "metric": "marker_steps_per_s", "value": rate, "unit": "marker-steps/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * el / done, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": w["name"], "sample": sample},
+            "cpu_baseline": {"value": rate, "unit": "marker-steps/s", "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": rate, "unit": "marker-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import torch
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_1804_03901_gb300 import avl as A
+
+    w = workload(args.workload)
+    stream = torch.cuda.current_stream()
+    sim = build_sim(A, w, stream.cuda_stream, seed_offset=rank)
+    nmark = markers_of(w)
+    for s in range(len(w["species"])):
+        assert sim.marker_count(s) > 0
+
+    # warm-up, then restart the run from t = 0
+    sim.step(max(3, args.warmup))
+    sim.synchronize()
+    init_markers(A, sim, w, rank)
+    sim.synchronize()
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    try:
+        dev_id = "GPU-" + str(torch.cuda.get_device_properties(local).uuid)
+    except Exception:
+        dev_id = str(local)
+    clocks = Clocks(dev_id)
+    barrier()
+    clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    sim.step(args.steps)
+    e1.record(stream)
+    barrier()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    sim.synchronize()
+    stats = sim.get_stats()
+    if world > 1:
+        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    value = nmark * world * args.steps / (ms / 1e3)
+
+    # per-kernel CUDA-event timing over the same K steps from t = 0
+    init_markers(A, sim, w, rank)
+    sim.synchronize()
+    kms = sim.profile_steps(args.steps)
+    hbm, peak_kind = peaks()
+    pd_ms = kms[0] / args.steps
+    prec = w["precision"]
+    achieved = nmark * BYTES_PER_MARKER_ALGO[prec] / (pd_ms / 1e3) / 1e9
+    traffic_pm = recorded_traffic(w["name"], prec)
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                "traffic": traffic_pm * nmark if traffic_pm else None,
+                "kernel": "k_pd1 (gather + push + VHS deposit)",
+                "algorithmic_bytes_per_marker": BYTES_PER_MARKER_ALGO[prec],
+                "layout_bytes_per_marker": BYTES_PER_MARKER_LAYOUT[prec],
+                "frac_layout_bytes": nmark * BYTES_PER_MARKER_LAYOUT[prec] / (pd_ms / 1e3) / 1e9 / hbm,
+                "peak_kind": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else peak_kind,
+                "kernel_ms_per_step": {k: float(v / args.steps) for k, v in zip(KERNEL_NAMES, kms)},
+                "kernel_share": {k: float(v / kms.sum()) for k, v in zip(KERNEL_NAMES, kms)}}
+
+    # end to end through the C ABI with host buffers
+    e2e = None
+    if not args.no_e2e:
+        hx, hv, hf = [], [], []
+        for s in range(len(w["species"])):
+            x, v, f = sim.get_markers(s)
+            hx.append(torch.from_numpy(x).pin_memory())
+            hv.append(torch.from_numpy(np.ascontiguousarray(v[0])).pin_memory())
+            hf.append(torch.from_numpy(f).pin_memory())
+        diag = torch.zeros(3 + 3 * len(w["species"]), dtype=torch.float64).pin_memory()
+        h2d = sum(t.numel() * 8 for t in hx + hv + hf)
+        barrier()
+        t0 = time.perf_counter()
+        for s in range(len(w["species"])):
+            sim.set_markers(s, hx[s], hv[s], hf[s])
+        for _ in range(args.steps):
+            sim.step(1)
+            A.check(A.avl_get_diag(sim.ctx, A.C.cast(diag.data_ptr(), A.C.POINTER(A.C.c_double))), sim.ctx)
+        barrier()
+        el = time.perf_counter() - t0
+        e2e = {"value": nmark * world * args.steps / el, "unit": "marker-steps/s",
+               "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": diag.numel() * 8,
+               "note": "timed: avl_set_markers of the initial state from pinned host memory, then K x "
+                       "(avl_step + avl_get_diag to pinned host)"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        rate, nm, done, el = cpu_oracle_rate(w, budget_s=12.0)
+        cpu = {"value": rate, "unit": "marker-steps/s", "cores": 1, "kind": "oracle",
+               "sample": f"{done} full steps of the {w['name']} workload ({nm} markers), FP64, 1 thread, "
+                         f"{el:.1f} s"}
+
+    if rank == 0:
+        line = {"metric": "marker_steps_per_s", "value": value, "unit": "marker-steps/s", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f32" if prec == "fp32" else "f64", "data": "synthetic",
+                "config": {"workload": w["name"], "markers": nmark, "species": len(w["species"]),
+                           "steps_in_run": w["steps"], "timed_from": "t = 0",
+                           "l2": "inputs larger than L2 (markers 16 B each, 268 MB per step read)"
+                           if args.workload == "two_stream" else "small workload (fits in L2)",
+                           "parallelism": "single GPU" if world == 1 else f"{world} independent replicas"},
+                "roofline": roofline, "clocks": clk, "gpu_launches": LAUNCHES_PER_STEP * args.steps,
+                "resorts": [int(x) for x in stats[:, 1]], "e2e": e2e, "cpu_baseline": cpu}
+        print(json.dumps(line), flush=True)
+    sim.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

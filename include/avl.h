@@ -1,0 +1,185 @@
+/*
+ * avl.h -- C ABI of the GB300 library for the Vlasov-Hybrid (VHS) time step.
+ *
+ * One time step follows Fig. 2 of the paper: reconstruct the phase-space
+ * density f of every species on its (x, v) grid from the markers (Sec. 2,
+ * Eq. 4), take the velocity moment rho (Eq. 14), solve Poisson's equation
+ * spectrally for E (Sec. 3.1, Eq. 5 / Eq. 6a-c), gather E at every marker
+ * with the same cloud-in-cell weights and push the markers (Sec. 2).  All of
+ * it runs in hand-written sm_103a CUDA kernels; there is no CPU fallback.
+ *
+ * Units and conventions
+ *   - Normalised units by default: Poisson reads dE/dx = poisson_const * rho
+ *     (poisson_const = 1 normalised, 4 pi for the paper's CGS form, Eq. 2).
+ *   - x spans [0, L) in nx cells of width dx = L/nx, periodic.  Velocity
+ *     dimension d of species s spans [vmin[d], vmax[d]) in nv[d] cells
+ *     (Sec. 3.1, Fig. 3).  Grid values sit at cell centres.
+ *   - Phase-space arrays returned to the caller are row-major
+ *     [x][vx] (1d1v) or [x][vx][vy][vz] (1d3v), FP64.
+ *   - Marker arrays are structure-of-arrays, FP64: x[n], v[nvdim][n]
+ *     (component-major), f[n].  The library keeps markers binned in its own
+ *     order; avl_get_markers returns them in that (unspecified) order.
+ *
+ * Ownership and errors
+ *   - A context owns all its device memory; the caller owns every buffer it
+ *     passes.  No call frees or retains caller memory.
+ *   - Every call returns an avl_status and never aborts; avl_last_error gives
+ *     a message for the last failing call on that context.
+ *   - Work is enqueued on the context's CUDA stream in call order.  Calls with
+ *     on_device = 0 (host buffers) return after the copy has completed; calls
+ *     with on_device = 1 only enqueue the copy on the context stream.
+ *   - A context is not thread-safe.  One context uses one GPU (the device
+ *     current at avl_create).
+ */
+#ifndef AVL_H
+#define AVL_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    AVL_OK = 0,
+    AVL_EINVAL = 1,    /* bad argument: the message names it */
+    AVL_ENOMEM = 2,    /* device allocation failed */
+    AVL_ECUDA = 3,     /* CUDA runtime error: the message carries the CUDA text */
+    AVL_ETIMEOUT = 4,  /* a bounded device-side wait gave up */
+    AVL_ESTATE = 5,    /* call not valid in the context's current state */
+    AVL_ENUMERIC = 6   /* NaN or Inf found in the fields or diagnostics */
+} avl_status;
+
+enum { AVL_FP64 = 0, AVL_FP32 = 1 };
+enum { AVL_MAX_SPECIES = 8 };
+
+typedef struct avl_ctx avl_ctx;
+
+/* Simulation domain (Sec. 3.1, Sec. 3.3 numerical parameters).
+ * precision AVL_FP64: markers, deposit and grid in FP64.
+ * precision AVL_FP32: marker position = int32 cell + FP32 offset, velocity
+ *   and value in FP32, deposit sums compensated in FP32; the Poisson solve,
+ *   the charge-neutral k = 0 handling and the diagnostics stay FP64. */
+typedef struct {
+    int32_t nvdim;          /* 1 (1d1v) or 3 (1d3v, no magnetic field) */
+    int32_t nx;             /* cells in x, >= 4 */
+    double L;               /* domain length */
+    double dt;              /* time step */
+    double poisson_const;   /* 1 normalised, 4 pi CGS */
+    int32_t softening;      /* 1: Eq. 6 (sinc-softened), 0: Eq. 5 */
+    int32_t precision;      /* AVL_FP64 or AVL_FP32 */
+} avl_domain;
+
+/* One species (Sec. 3.3): charge and mass of a physical particle, velocity
+ * grid.  mobile = 0 makes a fixed background: never pushed, its density is
+ * reconstructed once and keeps contributing to rho. */
+typedef struct {
+    double q;
+    double m;
+    int32_t mobile;
+    int32_t nv[3];          /* nv[1] = nv[2] = 1 for 1d1v */
+    double vmin[3];
+    double vmax[3];
+} avl_species;
+
+/* Initial distribution (Sec. 3.3, Eq. 11; Eq. 17):
+ *   f0(x, v) = sum_b beam_n[b] prod_d M(v_d; beam_u[b][d], beam_vth[b][d])
+ *              * (1 + sum_m amp[m] cos(2 pi mode[m] x / L + phase[m])),
+ *   M(v; u, s) = exp(-(v-u)^2 / (2 s^2)) / (sqrt(2 pi) s). */
+typedef struct {
+    int32_t nbeam;          /* 1..4 */
+    double beam_n[4];
+    double beam_u[4][3];
+    double beam_vth[4][3];
+    int32_t nmode;          /* 0..64 */
+    int32_t mode[64];
+    double amp[64];
+    double phase[64];
+} avl_f0;
+
+/* Create a context for nspecies species (1..AVL_MAX_SPECIES) on the current
+ * device.  cuda_stream: a cudaStream_t to enqueue all work on, or NULL to let
+ * the context create its own non-blocking stream.  Errors: AVL_EINVAL for an
+ * unsupported shape (message says which), AVL_ENOMEM. */
+avl_status avl_create(const avl_domain* dom, const avl_species* sp, int32_t nspecies,
+                      void* cuda_stream, avl_ctx** out);
+
+/* Release all device memory of the context (after draining its stream). */
+void avl_destroy(avl_ctx* ctx);
+
+/* Message for the last failing call on ctx ("" if none).  ctx may be NULL,
+ * in which case the message of the last failing avl_create is returned. */
+const char* avl_last_error(const avl_ctx* ctx);
+
+/* Marker creation (Sec. 2; Sec. 3.1): lattice[0..3] = markers per cell
+ * along x, vx, vy, vz (ppc = product; lattice[2] = lattice[3] = 1 for 1d1v).
+ * Marker (cell, sub-point) sits at the centre of its sub-cell plus a jitter
+ * uniform in [-jitter/2, jitter/2) sub-cells per dimension, drawn from
+ * SplitMix64 with stream index (species << 48) | (4 * marker + dim), marker =
+ * cell * ppc + sub-point (row-major indices).  Marker value f_l = f0 at the
+ * marker.  Then f, rho and E are recomputed for the new markers.
+ * Errors: AVL_EINVAL (bad species, lattice, or f0 counts; jitter outside
+ * [0, 1]), AVL_ENOMEM. */
+avl_status avl_init_markers(avl_ctx* ctx, int32_t s, const int32_t lattice[4],
+                            const avl_f0* f0, uint64_t seed, double jitter);
+
+/* Replace the markers of species s by n caller markers (FP64, layout above,
+ * x in [0, L)); on_device selects device or host pointers.  Then f, rho and E
+ * are recomputed.  Errors: AVL_EINVAL (n <= 0 or too large, x outside [0, L),
+ * non-finite values), AVL_ENOMEM. */
+avl_status avl_set_markers(avl_ctx* ctx, int32_t s, int64_t n, const double* x,
+                           const double* v, const double* f, int32_t on_device);
+
+/* Number of markers of species s. */
+avl_status avl_marker_count(avl_ctx* ctx, int32_t s, int64_t* n);
+
+/* Copy the markers of species s out as FP64 (layout above, library order). */
+avl_status avl_get_markers(avl_ctx* ctx, int32_t s, double* x, double* v, double* f,
+                           int32_t on_device);
+
+/* Advance nsteps full time steps (Fig. 2): gather + push of every mobile
+ * species, reconstruction (Eq. 4), moment (Eq. 14), Poisson (Eq. 6), and the
+ * diagnostics of the new state.  Enqueued asynchronously (a CUDA graph per
+ * step).  Errors: AVL_ESTATE if a mobile species has no markers. */
+avl_status avl_step(avl_ctx* ctx, int32_t nsteps);
+
+/* Reconstructed f of species s and, if n_opt is not NULL, the denominator of
+ * Eq. 4 (sum of weights, the paper's "n" output, Sec. 3.4.3); FP64,
+ * [x][v...] row-major. */
+avl_status avl_get_f(avl_ctx* ctx, int32_t s, double* f, double* n_opt, int32_t on_device);
+
+/* Net charge density rho (nx, FP64) of the current state (Eq. 14). */
+avl_status avl_get_rho(avl_ctx* ctx, double* rho, int32_t on_device);
+
+/* Electric field E (nx, FP64) of the current state (Eq. 6). */
+avl_status avl_get_E(avl_ctx* ctx, double* E, int32_t on_device);
+
+/* Diagnostics of the current state (Sec. 3.4.1, FP64, host buffer of
+ * 3 + 3 * nspecies values): W_E, W_kin, W_total, then W_kin of each species,
+ * N (integral of f) of each species, entropy S of each species.
+ * W_E = 1/(2 poisson_const) sum E^2 dx (Eq. 12); W_kin = m/2 sum v^2 f dx dv.
+ * Returns AVL_ENUMERIC if any value is NaN or Inf. */
+avl_status avl_get_diag(avl_ctx* ctx, double* out);
+
+/* Counters (host buffer of 4 int64 per species): markers that deposited
+ * through the out-of-window path in the last step, re-sorts so far,
+ * markers whose velocity cloud leaves the velocity grid (last step, 0 if not
+ * tracked), steps so far. */
+avl_status avl_get_stats(avl_ctx* ctx, int64_t* out);
+
+/* Per-kernel timing (the paper's time breakdown, Sec. 3.2): advance nsteps
+ * steps exactly as avl_step does, but launched kernel by kernel with CUDA
+ * events recorded on the context stream around each kernel; writes the summed
+ * milliseconds of each kernel class into ms[0..3] = {push+deposit, finalize
+ * (f, moment, diagnostics), field (Poisson), re-sort}.  Blocks until done.
+ * Errors: AVL_EINVAL (nkernels < 4 or ms NULL), AVL_ESTATE as avl_step. */
+avl_status avl_profile_steps(avl_ctx* ctx, int32_t nsteps, double* ms, int32_t nkernels);
+
+/* Block the host until the context's stream has drained; reports device-side
+ * error flags (AVL_ETIMEOUT, AVL_ENUMERIC). */
+avl_status avl_synchronize(avl_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

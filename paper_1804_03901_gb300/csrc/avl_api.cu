@@ -1,0 +1,675 @@
+// avl_api.cu -- host layer of the C ABI declared in include/avl.h.
+//
+// Owns the device state of a context, picks the binning parameters, records
+// one time step (push+deposit -> finalize -> Poisson -> re-sort) as a CUDA
+// graph and replays it.  All work goes to the context stream.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "avl_internal.cuh"
+
+using namespace avl;
+
+struct avl_ctx {
+    int device = 0;
+    cudaStream_t st = nullptr;
+    bool own_stream = false;
+    avl_domain dom{};
+    int ns = 0;
+    avl_species sp[MAXS]{};
+    StepArgs h{};
+    StepArgs* d_args = nullptr;
+    Ctl* d_ctl = nullptr;
+    avl_f0* d_f0 = nullptr;
+    unsigned long long* d_bad = nullptr;
+    std::vector<void*> allocs;          // context-lifetime allocations
+    void* mk_alloc[MAXS] = {};          // marker storage per species
+    bool has_markers[MAXS] = {};
+    void* scratch = nullptr;            // staging for caller-layout copies
+    size_t scratch_bytes = 0;
+    cudaGraphExec_t gexec = nullptr;
+    std::string err;
+};
+
+static thread_local std::string g_create_err;
+
+namespace {
+
+avl_status fail(avl_ctx* c, avl_status st, const std::string& msg)
+{
+    if (c)
+        c->err = msg;
+    else
+        g_create_err = msg;
+    return st;
+}
+
+avl_status cuda_fail(avl_ctx* c, cudaError_t e, const char* where)
+{
+    std::string m = std::string(where) + ": " + cudaGetErrorString(e);
+    return fail(c, e == cudaErrorMemoryAllocation ? AVL_ENOMEM : AVL_ECUDA, m);
+}
+
+#define AVL_CUDA(c, expr)                                    \
+    do {                                                     \
+        cudaError_t e_ = (expr);                             \
+        if (e_ != cudaSuccess) return cuda_fail(c, e_, #expr); \
+    } while (0)
+
+cudaError_t dalloc(avl_ctx* c, void** p, size_t bytes, bool zero)
+{
+    *p = nullptr;
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) return e;
+    c->allocs.push_back(*p);
+    if (zero) e = cudaMemsetAsync(*p, 0, bytes, c->st);
+    return e;
+}
+
+avl_status upload_args(avl_ctx* c)
+{
+    AVL_CUDA(c, cudaMemcpyAsync(c->d_args, &c->h, sizeof(StepArgs), cudaMemcpyHostToDevice, c->st));
+    // the host copy must stay unchanged until the copy has run
+    AVL_CUDA(c, cudaStreamSynchronize(c->st));
+    return AVL_OK;
+}
+
+avl_status ensure_scratch(avl_ctx* c, size_t bytes)
+{
+    if (c->scratch_bytes >= bytes) return AVL_OK;
+    if (c->scratch) {
+        AVL_CUDA(c, cudaStreamSynchronize(c->st));
+        cudaFree(c->scratch);
+        c->scratch = nullptr;
+        c->scratch_bytes = 0;
+    }
+    AVL_CUDA(c, cudaMalloc(&c->scratch, bytes));
+    c->scratch_bytes = bytes;
+    return AVL_OK;
+}
+
+int env_int(const char* name, int dflt)
+{
+    const char* v = getenv(name);
+    return v ? atoi(v) : dflt;
+}
+
+size_t prec_bytes(int prec) { return prec == AVL_FP32 ? 4 : 8; }
+
+// allocate (or re-allocate) the double-buffered marker storage of species s
+avl_status alloc_markers(avl_ctx* c, int s, long long n)
+{
+    SpDev& sp = c->h.sp[s];
+    if (c->mk_alloc[s] && sp.n == n) return AVL_OK;
+    if (c->mk_alloc[s]) {
+        AVL_CUDA(c, cudaStreamSynchronize(c->st));
+        cudaFree(c->mk_alloc[s]);
+        c->mk_alloc[s] = nullptr;
+    }
+    const size_t pb = prec_bytes(c->h.prec);
+    const size_t nn = ((size_t)n + 63) / 64 * 64;
+    // per buffer: position (int cell or double xi), [offset], velocity components, value
+    const int nvc = c->h.nvdim;
+    const size_t per = (c->h.prec == AVL_FP32) ? (4 + 4 + 4 * nvc + 4) : (8 + 8 * nvc + 8);
+    void* base = nullptr;
+    AVL_CUDA(c, cudaMalloc(&base, 2 * per * nn));
+    c->mk_alloc[s] = base;
+    unsigned char* p = static_cast<unsigned char*>(base);
+    for (int b = 0; b < 2; ++b) {
+        sp.mx[b] = p;
+        p += (c->h.prec == AVL_FP32 ? 4 : 8) * nn;
+        if (c->h.prec == AVL_FP32) {
+            sp.moff[b] = reinterpret_cast<float*>(p);
+            p += 4 * nn;
+        } else {
+            sp.moff[b] = nullptr;
+        }
+        for (int d = 0; d < 3; ++d) {
+            if (d < nvc) {
+                sp.mv[b][d] = p;
+                p += pb * nn;
+            } else {
+                sp.mv[b][d] = nullptr;
+            }
+        }
+        sp.mf[b] = p;
+        p += pb * nn;
+    }
+    sp.n = n;
+    return AVL_OK;
+}
+
+avl_status set_cur_zero(avl_ctx* c, int s)
+{
+    const int zero = 0;
+    AVL_CUDA(c, cudaMemcpyAsync(&c->d_ctl->cur[s], &zero, sizeof(int), cudaMemcpyHostToDevice, c->st));
+    AVL_CUDA(c, cudaStreamSynchronize(c->st));
+    return AVL_OK;
+}
+
+// reconstruct every species with markers, then rho and E (no push)
+avl_status refresh(avl_ctx* c)
+{
+    AVL_CUDA(c, launch_pd1(c->h, c->d_args, 0, c->st));
+    AVL_CUDA(c, launch_fin1(c->h, c->d_args, 1, c->st));
+    AVL_CUDA(c, launch_field(c->h, c->d_args, 0, c->st));
+    AVL_CUDA(c, launch_sort1(c->h, c->d_args, c->st));
+    return AVL_OK;
+}
+
+avl_status enqueue_step(avl_ctx* c)
+{
+    AVL_CUDA(c, launch_pd1(c->h, c->d_args, 1, c->st));
+    AVL_CUDA(c, launch_fin1(c->h, c->d_args, 0, c->st));
+    AVL_CUDA(c, launch_field(c->h, c->d_args, 1, c->st));
+    AVL_CUDA(c, launch_sort1(c->h, c->d_args, c->st));
+    return AVL_OK;
+}
+
+avl_status build_graph(avl_ctx* c)
+{
+    if (c->gexec) return AVL_OK;
+    cudaGraph_t g = nullptr;
+    AVL_CUDA(c, cudaStreamBeginCapture(c->st, cudaStreamCaptureModeThreadLocal));
+    avl_status st = enqueue_step(c);
+    cudaError_t e = cudaStreamEndCapture(c->st, &g);
+    if (st != AVL_OK) {
+        if (g) cudaGraphDestroy(g);
+        return st;
+    }
+    if (e != cudaSuccess) return cuda_fail(c, e, "cudaStreamEndCapture");
+    e = cudaGraphInstantiate(&c->gexec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        c->gexec = nullptr;
+        return cuda_fail(c, e, "cudaGraphInstantiate");
+    }
+    return AVL_OK;
+}
+
+avl_status check_species(avl_ctx* c, int s)
+{
+    if (!c) return AVL_EINVAL;
+    if (s < 0 || s >= c->ns) return fail(c, AVL_EINVAL, "species index out of range");
+    return AVL_OK;
+}
+
+avl_status read_errors(avl_ctx* c)
+{
+    int err = 0;
+    AVL_CUDA(c, cudaMemcpyAsync(&err, &c->d_ctl->err, sizeof(int), cudaMemcpyDeviceToHost, c->st));
+    AVL_CUDA(c, cudaStreamSynchronize(c->st));
+    if (err & ERR_TIMEOUT) return fail(c, AVL_ETIMEOUT, "a bounded device-side wait gave up");
+    if (err & ERR_NUMERIC) return fail(c, AVL_ENUMERIC, "NaN or Inf in the field or diagnostics");
+    return AVL_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* avl_last_error(const avl_ctx* ctx)
+{
+    return ctx ? ctx->err.c_str() : g_create_err.c_str();
+}
+
+avl_status avl_create(const avl_domain* dom, const avl_species* spec, int32_t nspecies, void* cuda_stream,
+                      avl_ctx** out)
+{
+    if (!out) return fail(nullptr, AVL_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!dom || !spec) return fail(nullptr, AVL_EINVAL, "dom or species is NULL");
+    if (dom->nvdim != 1) return fail(nullptr, AVL_EINVAL, "nvdim must be 1 (1d3v is not built yet)");
+    if (dom->nx < 4 || dom->nx > (1 << 20)) return fail(nullptr, AVL_EINVAL, "nx must be in [4, 2^20]");
+    if (!(dom->L > 0) || !(dom->dt > 0) || !(dom->poisson_const > 0) || !isfinite(dom->L) ||
+        !isfinite(dom->dt) || !isfinite(dom->poisson_const))
+        return fail(nullptr, AVL_EINVAL, "L, dt and poisson_const must be positive and finite");
+    if (dom->softening != 0 && dom->softening != 1) return fail(nullptr, AVL_EINVAL, "softening must be 0 or 1");
+    if (dom->precision != AVL_FP64 && dom->precision != AVL_FP32)
+        return fail(nullptr, AVL_EINVAL, "precision must be AVL_FP64 or AVL_FP32");
+    if (nspecies < 1 || nspecies > MAXS) return fail(nullptr, AVL_EINVAL, "nspecies must be in [1, 8]");
+    for (int s = 0; s < nspecies; ++s) {
+        const avl_species& p = spec[s];
+        if (!(p.m > 0) || !isfinite(p.q) || !isfinite(p.m))
+            return fail(nullptr, AVL_EINVAL, "species mass must be positive, charge finite");
+        if (p.nv[0] < 2 || p.nv[0] > (1 << 20) || p.nv[1] != 1 || p.nv[2] != 1)
+            return fail(nullptr, AVL_EINVAL, "1d1v species need nv[0] in [2, 2^20] and nv[1] = nv[2] = 1");
+        if (!(p.vmax[0] > p.vmin[0]) || !isfinite(p.vmin[0]) || !isfinite(p.vmax[0]))
+            return fail(nullptr, AVL_EINVAL, "species velocity range must satisfy vmin < vmax");
+    }
+
+    avl_ctx* c = new avl_ctx();
+    c->dom = *dom;
+    c->ns = nspecies;
+    for (int s = 0; s < nspecies; ++s) c->sp[s] = spec[s];
+    cudaError_t e = cudaGetDevice(&c->device);
+    if (e != cudaSuccess) {
+        delete c;
+        return cuda_fail(nullptr, e, "cudaGetDevice");
+    }
+    if (cuda_stream) {
+        c->st = static_cast<cudaStream_t>(cuda_stream);
+    } else {
+        e = cudaStreamCreateWithFlags(&c->st, cudaStreamNonBlocking);
+        if (e != cudaSuccess) {
+            delete c;
+            return cuda_fail(nullptr, e, "cudaStreamCreate");
+        }
+        c->own_stream = true;
+    }
+
+    auto bail = [&](avl_status st) {
+        std::string m = c->err;
+        avl_destroy(c);
+        return fail(nullptr, st, m);
+    };
+
+    StepArgs& h = c->h;
+    memset(&h, 0, sizeof(h));
+    h.ns = nspecies;
+    h.prec = dom->precision;
+    h.nvdim = dom->nvdim;
+    const int nx = dom->nx;
+    const double dx = dom->L / nx;
+    const size_t pb = prec_bytes(h.prec);
+
+    // --- field arrays and spectral multipliers ---------------------------
+    FieldDev& fd = h.fd;
+    fd.nx = nx;
+    fd.pow2 = (nx >= 4 && (nx & (nx - 1)) == 0) ? 1 : 0;
+    fd.softening = dom->softening;
+    fd.ndiag = 3 + 3 * nspecies;
+    fd.L = dom->L;
+    fd.dx = dx;
+    fd.cP = dom->poisson_const;
+    std::vector<double2> tw(nx);
+    for (int k = 0; k < nx; ++k) {
+        const double a = 2.0 * M_PI * (double)k / (double)nx;
+        tw[k] = make_double2(cos(a), -sin(a));
+    }
+    std::vector<double> gm(nx / 2 + 1, 0.0);
+    for (int m = 1; m <= nx / 2; ++m) {
+        if (2 * m == nx) continue;   // Nyquist mode carries no field
+        const double k = 2.0 * M_PI * (double)m / dom->L;
+        double kappa, K2;
+        if (dom->softening) {
+            const double y1 = k * dx, y2 = 0.5 * k * dx;
+            kappa = k * (sin(y1) / y1);
+            K2 = k * k * (sin(y2) / y2) * (sin(y2) / y2);
+        } else {
+            kappa = k;
+            K2 = k * k;
+        }
+        gm[m] = dom->poisson_const * kappa / K2;
+    }
+    void *p_rho, *p_E64, *p_E32, *p_tw, *p_gm, *p_diag;
+    if ((e = dalloc(c, &p_rho, nx * 8, true)) || (e = dalloc(c, &p_E64, nx * 8, true)) ||
+        (e = dalloc(c, &p_E32, nx * 4, true)) || (e = dalloc(c, &p_tw, nx * 16, false)) ||
+        (e = dalloc(c, &p_gm, (nx / 2 + 1) * 8, false)) || (e = dalloc(c, &p_diag, fd.ndiag * 8, true))) {
+        cuda_fail(c, e, "cudaMalloc(field)");
+        return bail(AVL_ENOMEM);
+    }
+    fd.rho = (double*)p_rho;
+    fd.E64 = (double*)p_E64;
+    fd.E32 = (float*)p_E32;
+    fd.tw = (const double2*)p_tw;
+    fd.gmul = (const double*)p_gm;
+    fd.diag = (double*)p_diag;
+    if ((e = cudaMemcpyAsync(p_tw, tw.data(), nx * 16, cudaMemcpyHostToDevice, c->st)) ||
+        (e = cudaMemcpyAsync(p_gm, gm.data(), (nx / 2 + 1) * 8, cudaMemcpyHostToDevice, c->st)) ||
+        (e = cudaStreamSynchronize(c->st))) {
+        cuda_fail(c, e, "upload spectral tables");
+        return bail(AVL_ECUDA);
+    }
+
+    // --- per species binning and grids ------------------------------------
+    const int hw = 3, hd = 1;
+    int bin_base = 0, rb_base = 0;
+    int nv_total = 0;
+    for (int s = 0; s < nspecies; ++s) nv_total += spec[s].nv[0];
+    for (int s = 0; s < nspecies; ++s) {
+        const avl_species& p = spec[s];
+        SpDev& sp = h.sp[s];
+        sp.nvdim = 1;
+        sp.nx = nx;
+        sp.nv[0] = p.nv[0];
+        sp.nv[1] = sp.nv[2] = 1;
+        sp.nvflat = p.nv[0];
+        sp.mobile = p.mobile ? 1 : 0;
+        sp.q = p.q;
+        sp.m = p.m;
+        sp.qm = p.q / p.m;
+        sp.dx = dx;
+        for (int d = 0; d < 3; ++d) {
+            sp.vmin[d] = d == 0 ? p.vmin[0] : -0.5;
+            sp.dv[d] = d == 0 ? (p.vmax[0] - p.vmin[0]) / p.nv[0] : 1.0;
+            sp.inv_dv[d] = 1.0 / sp.dv[d];
+        }
+        sp.qm_dt = sp.qm * dom->dt;
+        sp.dt_dx = dom->dt / dx;
+        // window: W rows of nx cells, 16 bytes per cell, within a shared-memory budget
+        const int budget_kb = env_int("AVL_WINDOW_KB", 72);
+        size_t budget = (size_t)budget_kb * 1024;
+        budget = std::max(budget, (size_t)16 * nx * (2 * hw + 1));
+        if (budget > 200 * 1024) {
+            c->err = "nx too large for the 1d1v shared-memory window (nx <= 1828)";
+            return bail(AVL_EINVAL);
+        }
+        const int wmax = (int)(budget / (16 * (size_t)nx));
+        int tv = std::max(1, wmax - 2 * hw);
+        const int tv_env = env_int("AVL_TV", 0);
+        if (tv_env > 0) tv = tv_env;
+        tv = std::min(tv, p.nv[0]);
+        sp.tv = tv;
+        sp.hw = hw;
+        sp.hd = hd;
+        sp.W = tv + 2 * hw;
+        sp.nbins = (p.nv[0] + tv - 1) / tv;
+        sp.bin_base = bin_base;
+        bin_base += sp.nbins;
+        int rb = std::max(1, (nv_total + 303) / 304);
+        const int rb_env = env_int("AVL_RB", 0);
+        if (rb_env > 0) rb = rb_env;
+        rb = std::min(rb, p.nv[0]);
+        sp.rb = rb;
+        sp.nrb = (p.nv[0] + rb - 1) / rb;
+        sp.rb_base = rb_base;
+        rb_base += sp.nrb;
+        const size_t cells = (size_t)nx * sp.nvflat;
+        void *pf, *pn, *pp, *po, *pr, *pd, *pb0, *pb1, *pc, *ph;
+        if ((e = dalloc(c, &pf, cells * pb, true)) || (e = dalloc(c, &pn, cells * pb, true)) ||
+            (e = dalloc(c, &pp, (size_t)sp.nbins * 16 * sp.W * nx, true)) ||
+            (e = dalloc(c, &po, 2 * cells * 8, true)) || (e = dalloc(c, &pr, (size_t)sp.nrb * nx * 8, true)) ||
+            (e = dalloc(c, &pd, (size_t)sp.nrb * 4 * 8, true)) ||
+            (e = dalloc(c, &pb0, (size_t)(sp.nbins + 1) * 4, true)) ||
+            (e = dalloc(c, &pb1, (size_t)(sp.nbins + 1) * 4, true)) ||
+            (e = dalloc(c, &pc, (size_t)sp.nbins * 4, true)) || (e = dalloc(c, &ph, (size_t)sp.nbins * 4, true))) {
+            cuda_fail(c, e, "cudaMalloc(species)");
+            return bail(AVL_ENOMEM);
+        }
+        sp.fgrid = pf;
+        sp.ngrid = pn;
+        sp.partial = pp;
+        sp.ovf = (double*)po;
+        sp.rho_part = (double*)pr;
+        sp.dpart = (double*)pd;
+        sp.bin_start[0] = (int*)pb0;
+        sp.bin_start[1] = (int*)pb1;
+        sp.cursor = (int*)pc;
+        sp.hist = (int*)ph;
+        sp.n = 0;
+    }
+    h.nbins_total = bin_base;
+    h.nrb_total = rb_base;
+
+    void *pa, *pc, *pf0, *pbad;
+    if ((e = dalloc(c, &pa, sizeof(StepArgs), false)) || (e = dalloc(c, &pc, sizeof(Ctl), true)) ||
+        (e = dalloc(c, &pf0, sizeof(avl_f0), false)) || (e = dalloc(c, &pbad, 8, true))) {
+        cuda_fail(c, e, "cudaMalloc(control)");
+        return bail(AVL_ENOMEM);
+    }
+    c->d_args = (StepArgs*)pa;
+    c->d_ctl = (Ctl*)pc;
+    c->d_f0 = (avl_f0*)pf0;
+    c->d_bad = (unsigned long long*)pbad;
+    h.ctl = c->d_ctl;
+    if (upload_args(c) != AVL_OK) return bail(AVL_ECUDA);
+    *out = c;
+    return AVL_OK;
+}
+
+void avl_destroy(avl_ctx* c)
+{
+    if (!c) return;
+    if (c->st) cudaStreamSynchronize(c->st);
+    if (c->gexec) cudaGraphExecDestroy(c->gexec);
+    for (void* p : c->allocs) cudaFree(p);
+    for (int s = 0; s < MAXS; ++s)
+        if (c->mk_alloc[s]) cudaFree(c->mk_alloc[s]);
+    if (c->scratch) cudaFree(c->scratch);
+    if (c->own_stream && c->st) cudaStreamDestroy(c->st);
+    delete c;
+}
+
+avl_status avl_init_markers(avl_ctx* c, int32_t s, const int32_t lattice[4], const avl_f0* f0, uint64_t seed,
+                            double jitter)
+{
+    avl_status st = check_species(c, s);
+    if (st) return st;
+    if (!lattice || !f0) return fail(c, AVL_EINVAL, "lattice or f0 is NULL");
+    if (lattice[0] < 1 || lattice[1] < 1 || lattice[2] != 1 || lattice[3] != 1)
+        return fail(c, AVL_EINVAL, "1d1v lattice must be {px >= 1, pv >= 1, 1, 1}");
+    if (f0->nbeam < 1 || f0->nbeam > 4 || f0->nmode < 0 || f0->nmode > 64)
+        return fail(c, AVL_EINVAL, "f0 needs 1..4 beams and 0..64 modes");
+    for (int b = 0; b < f0->nbeam; ++b)
+        if (!(f0->beam_vth[b][0] > 0)) return fail(c, AVL_EINVAL, "beam thermal speeds must be positive");
+    if (!(jitter >= 0.0 && jitter <= 1.0)) return fail(c, AVL_EINVAL, "jitter must be in [0, 1]");
+    SpDev& sp = c->h.sp[s];
+    const long long ppc = (long long)lattice[0] * lattice[1];
+    const long long n = (long long)sp.nx * sp.nvflat * ppc;
+    if (n >= (1ll << 31) - 1024) return fail(c, AVL_EINVAL, "too many markers for one species (2^31)");
+    if ((st = alloc_markers(c, s, n))) return st;
+    // bin ranges of the lattice: bin b holds rows [b tv, min(nv, (b+1) tv))
+    std::vector<int> bs(sp.nbins + 1);
+    for (int b = 0; b <= sp.nbins; ++b)
+        bs[b] = (int)((long long)std::min(sp.nvflat, b * sp.tv) * sp.nx * ppc);
+    if ((st = set_cur_zero(c, s))) return st;
+    AVL_CUDA(c, cudaMemcpyAsync(sp.bin_start[0], bs.data(), bs.size() * 4, cudaMemcpyHostToDevice, c->st));
+    AVL_CUDA(c, cudaMemcpyAsync(c->d_f0, f0, sizeof(avl_f0), cudaMemcpyHostToDevice, c->st));
+    if ((st = upload_args(c))) return st;
+    AVL_CUDA(c, launch_init1(c->h, c->d_args, s, lattice, c->d_f0, seed, jitter, c->st));
+    c->has_markers[s] = true;
+    if ((st = refresh(c))) return st;
+    AVL_CUDA(c, cudaStreamSynchronize(c->st));
+    return AVL_OK;
+}
+
+avl_status avl_set_markers(avl_ctx* c, int32_t s, int64_t n, const double* x, const double* v, const double* f,
+                           int32_t on_device)
+{
+    avl_status st = check_species(c, s);
+    if (st) return st;
+    if (n <= 0 || n >= (1ll << 31) - 1024) return fail(c, AVL_EINVAL, "n must be in [1, 2^31)");
+    if (!x || !v || !f) return fail(c, AVL_EINVAL, "x, v or f is NULL");
+    const double *dx_ = x, *dv_ = v, *df_ = f;
+    const int nvd = c->h.nvdim;
+    if (!on_device) {
+        if ((st = ensure_scratch(c, (size_t)n * 8 * (2 + nvd)))) return st;
+        double* base = static_cast<double*>(c->scratch);
+        AVL_CUDA(c, cudaMemcpyAsync(base, x, n * 8, cudaMemcpyHostToDevice, c->st));
+        AVL_CUDA(c, cudaMemcpyAsync(base + n, v, n * 8 * nvd, cudaMemcpyHostToDevice, c->st));
+        AVL_CUDA(c, cudaMemcpyAsync(base + n * (1 + nvd), f, n * 8, cudaMemcpyHostToDevice, c->st));
+        dx_ = base;
+        dv_ = base + n;
+        df_ = base + n * (1 + nvd);
+    }
+    if ((st = alloc_markers(c, s, n))) return st;
+    if ((st = set_cur_zero(c, s))) return st;
+    if ((st = upload_args(c))) return st;
+    AVL_CUDA(c, cudaMemsetAsync(c->d_bad, 0, 8, c->st));
+    AVL_CUDA(c, launch_set1(c->h, c->d_args, s, n, dx_, dv_, df_, c->d_bad, c->st));
+    unsigned long long bad = 0;
+    AVL_CUDA(c, cudaMemcpyAsync(&bad, c->d_bad, 8, cudaMemcpyDeviceToHost, c->st));
+    AVL_CUDA(c, cudaStreamSynchronize(c->st));
+    if (bad) {
+        c->has_markers[s] = false;
+        return fail(c, AVL_EINVAL, "markers with x outside [0, L) or non-finite values: " + std::to_string(bad));
+    }
+    c->has_markers[s] = true;
+    if ((st = refresh(c))) return st;
+    AVL_CUDA(c, cudaStreamSynchronize(c->st));
+    return AVL_OK;
+}
+
+avl_status avl_marker_count(avl_ctx* c, int32_t s, int64_t* n)
+{
+    avl_status st = check_species(c, s);
+    if (st) return st;
+    if (!n) return fail(c, AVL_EINVAL, "n is NULL");
+    *n = c->has_markers[s] ? c->h.sp[s].n : 0;
+    return AVL_OK;
+}
+
+avl_status avl_get_markers(avl_ctx* c, int32_t s, double* x, double* v, double* f, int32_t on_device)
+{
+    avl_status st = check_species(c, s);
+    if (st) return st;
+    if (!c->has_markers[s]) return fail(c, AVL_ESTATE, "species has no markers");
+    const long long n = c->h.sp[s].n;
+    const int nvd = c->h.nvdim;
+    if (on_device) {
+        AVL_CUDA(c, launch_get1(c->h, c->d_args, s, x, v, f, c->st));
+        return AVL_OK;
+    }
+    if ((st = ensure_scratch(c, (size_t)n * 8 * (2 + nvd)))) return st;
+    double* base = static_cast<double*>(c->scratch);
+    AVL_CUDA(c, launch_get1(c->h, c->d_args, s, base, base + n, base + n * (1 + nvd), c->st));
+    if (x) AVL_CUDA(c, cudaMemcpyAsync(x, base, n * 8, cudaMemcpyDeviceToHost, c->st));
+    if (v) AVL_CUDA(c, cudaMemcpyAsync(v, base + n, n * 8 * nvd, cudaMemcpyDeviceToHost, c->st));
+    if (f) AVL_CUDA(c, cudaMemcpyAsync(f, base + n * (1 + nvd), n * 8, cudaMemcpyDeviceToHost, c->st));
+    AVL_CUDA(c, cudaStreamSynchronize(c->st));
+    return AVL_OK;
+}
+
+avl_status avl_step(avl_ctx* c, int32_t nsteps)
+{
+    if (!c) return AVL_EINVAL;
+    if (nsteps < 0) return fail(c, AVL_EINVAL, "nsteps must be >= 0");
+    for (int s = 0; s < c->ns; ++s)
+        if (c->h.sp[s].mobile && !c->has_markers[s])
+            return fail(c, AVL_ESTATE, "mobile species " + std::to_string(s) + " has no markers");
+    if (nsteps == 0) return AVL_OK;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    AVL_CUDA(c, cudaStreamIsCapturing(c->st, &cap));
+    if (cap != cudaStreamCaptureStatusNone || env_int("AVL_NO_GRAPH", 0)) {
+        for (int i = 0; i < nsteps; ++i) {
+            avl_status st = enqueue_step(c);
+            if (st) return st;
+        }
+        return AVL_OK;
+    }
+    avl_status st = build_graph(c);
+    if (st) return st;
+    for (int i = 0; i < nsteps; ++i) AVL_CUDA(c, cudaGraphLaunch(c->gexec, c->st));
+    return AVL_OK;
+}
+
+avl_status avl_get_f(avl_ctx* c, int32_t s, double* f, double* n_opt, int32_t on_device)
+{
+    avl_status st = check_species(c, s);
+    if (st) return st;
+    if (!f) return fail(c, AVL_EINVAL, "f is NULL");
+    const SpDev& sp = c->h.sp[s];
+    const size_t cells = (size_t)sp.nx * sp.nvflat;
+    if (on_device) {
+        AVL_CUDA(c, launch_getf(c->h, s, f, n_opt, c->st));
+        return AVL_OK;
+    }
+    if ((st = ensure_scratch(c, cells * 16))) return st;
+    double* base = static_cast<double*>(c->scratch);
+    AVL_CUDA(c, launch_getf(c->h, s, base, n_opt ? base + cells : nullptr, c->st));
+    AVL_CUDA(c, cudaMemcpyAsync(f, base, cells * 8, cudaMemcpyDeviceToHost, c->st));
+    if (n_opt) AVL_CUDA(c, cudaMemcpyAsync(n_opt, base + cells, cells * 8, cudaMemcpyDeviceToHost, c->st));
+    AVL_CUDA(c, cudaStreamSynchronize(c->st));
+    return AVL_OK;
+}
+
+static avl_status get_field(avl_ctx* c, const double* src, double* dst, int on_device)
+{
+    if (!c) return AVL_EINVAL;
+    if (!dst) return fail(c, AVL_EINVAL, "output is NULL");
+    const size_t bytes = (size_t)c->h.fd.nx * 8;
+    AVL_CUDA(c, cudaMemcpyAsync(dst, src, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                                c->st));
+    if (!on_device) AVL_CUDA(c, cudaStreamSynchronize(c->st));
+    return AVL_OK;
+}
+
+avl_status avl_get_rho(avl_ctx* c, double* rho, int32_t on_device)
+{
+    return get_field(c, c ? c->h.fd.rho : nullptr, rho, on_device);
+}
+
+avl_status avl_get_E(avl_ctx* c, double* E, int32_t on_device)
+{
+    return get_field(c, c ? c->h.fd.E64 : nullptr, E, on_device);
+}
+
+avl_status avl_get_diag(avl_ctx* c, double* out)
+{
+    if (!c) return AVL_EINVAL;
+    if (!out) return fail(c, AVL_EINVAL, "out is NULL");
+    const int nd = c->h.fd.ndiag;
+    AVL_CUDA(c, cudaMemcpyAsync(out, c->h.fd.diag, nd * 8, cudaMemcpyDeviceToHost, c->st));
+    AVL_CUDA(c, cudaStreamSynchronize(c->st));
+    for (int i = 0; i < nd; ++i)
+        if (!isfinite(out[i])) return fail(c, AVL_ENUMERIC, "non-finite diagnostic value");
+    return AVL_OK;
+}
+
+avl_status avl_get_stats(avl_ctx* c, int64_t* out)
+{
+    if (!c) return AVL_EINVAL;
+    if (!out) return fail(c, AVL_EINVAL, "out is NULL");
+    Ctl h;
+    AVL_CUDA(c, cudaMemcpyAsync(&h, c->d_ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, c->st));
+    AVL_CUDA(c, cudaStreamSynchronize(c->st));
+    for (int s = 0; s < c->ns; ++s) {
+        out[4 * s + 0] = (int64_t)h.ovf_last[s];
+        out[4 * s + 1] = (int64_t)h.nsort[s];
+        out[4 * s + 2] = 0;
+        out[4 * s + 3] = (int64_t)h.step;
+    }
+    return AVL_OK;
+}
+
+avl_status avl_profile_steps(avl_ctx* c, int32_t nsteps, double* ms, int32_t nkernels)
+{
+    if (!c) return AVL_EINVAL;
+    if (!ms || nkernels < 4 || nsteps < 0) return fail(c, AVL_EINVAL, "ms must hold 4 values, nsteps >= 0");
+    for (int s = 0; s < c->ns; ++s)
+        if (c->h.sp[s].mobile && !c->has_markers[s])
+            return fail(c, AVL_ESTATE, "mobile species " + std::to_string(s) + " has no markers");
+    cudaEvent_t ev[5];
+    for (int i = 0; i < 5; ++i) AVL_CUDA(c, cudaEventCreate(&ev[i]));
+    double acc[4] = {0, 0, 0, 0};
+    avl_status st = AVL_OK;
+    for (int i = 0; i < nsteps && st == AVL_OK; ++i) {
+        cudaError_t e = cudaEventRecord(ev[0], c->st);
+        if (!e) e = launch_pd1(c->h, c->d_args, 1, c->st);
+        if (!e) e = cudaEventRecord(ev[1], c->st);
+        if (!e) e = launch_fin1(c->h, c->d_args, 0, c->st);
+        if (!e) e = cudaEventRecord(ev[2], c->st);
+        if (!e) e = launch_field(c->h, c->d_args, 1, c->st);
+        if (!e) e = cudaEventRecord(ev[3], c->st);
+        if (!e) e = launch_sort1(c->h, c->d_args, c->st);
+        if (!e) e = cudaEventRecord(ev[4], c->st);
+        if (!e) e = cudaEventSynchronize(ev[4]);
+        for (int k = 0; k < 4 && !e; ++k) {
+            float t = 0.f;
+            e = cudaEventElapsedTime(&t, ev[k], ev[k + 1]);
+            acc[k] += t;
+        }
+        if (e) st = cuda_fail(c, e, "avl_profile_steps");
+    }
+    for (int i = 0; i < 5; ++i) cudaEventDestroy(ev[i]);
+    for (int k = 0; k < 4; ++k) ms[k] = acc[k];
+    return st;
+}
+
+avl_status avl_synchronize(avl_ctx* c)
+{
+    if (!c) return AVL_EINVAL;
+    AVL_CUDA(c, cudaStreamSynchronize(c->st));
+    return read_errors(c);
+}
+
+}  // extern "C"

@@ -1,0 +1,214 @@
+// k_field.cu -- net charge density and spectral Poisson solve (Sec. 3.1,
+// Eq. 5 / Eq. 6a-c), diagnostics row (Sec. 3.4.1) and the re-sort decision.
+//
+// One thread-block cluster of FIELD_CLUSTER CTAs.  Every CTA sums the charge
+// partials of a slice of x over all species and velocity row blocks and
+// writes its slice into CTA 0's shared memory (distributed shared memory);
+// CTA 0 then runs an FP64 real FFT of length nx (a complex radix-2 FFT of
+// length nx/2 with the even/odd split), multiplies by -i cP kappa / K^2,
+// transforms back, and writes E in FP64 and FP32.  A direct DFT serves grid
+// sizes that are not a power of two.
+#include <cooperative_groups.h>
+#include <math.h>
+
+#include "avl_internal.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace avl {
+
+__device__ __forceinline__ double2 cmul(double2 a, double2 b)
+{
+    return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ double2 csub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ double2 conj2(double2 a) { return make_double2(a.x, -a.y); }
+
+// in-place radix-2 decimation-in-time FFT of length M (power of two) on
+// shared memory, input already in bit-reversed order; tw[k] = exp(-2 pi i k/N)
+// with N = 2 M; inverse uses the conjugate twiddles (no scaling).
+__device__ void fft_pow2(double2* a, int M, int N, const double2* __restrict__ tw, bool inverse)
+{
+    for (int len = 2; len <= M; len <<= 1) {
+        const int half = len >> 1;
+        const int step = N / len;
+        for (int t = threadIdx.x; t < M / 2; t += blockDim.x) {
+            const int grp = t / half, k = t - grp * half;
+            const int i1 = grp * len + k, i2 = i1 + half;
+            double2 w = tw[k * step];
+            if (inverse) w.y = -w.y;
+            const double2 u = a[i1];
+            const double2 v = cmul(a[i2], w);
+            a[i1] = cadd(u, v);
+            a[i2] = csub(u, v);
+        }
+        __syncthreads();
+    }
+}
+
+__device__ __forceinline__ int bitrev(int x, int bits) { return (int)(__brev((unsigned)x) >> (32 - bits)); }
+
+__global__ void __cluster_dims__(FIELD_CLUSTER, 1, 1) __launch_bounds__(FIELD_THREADS)
+    k_field(const StepArgs* __restrict__ A, int count_step)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    cg::cluster_group cluster = cg::this_cluster();
+    const int rank = (int)cluster.block_rank();
+    const FieldDev& fd = A->fd;
+    const int nx = fd.nx;
+    double* rho_s = reinterpret_cast<double*>(smem);                 // nx
+    double2* work = reinterpret_cast<double2*>(smem + ((size_t)nx * 8 + 15) / 16 * 16);   // nx/2 + 1
+    __shared__ double red[FIELD_THREADS / 32];
+
+    // --- rho slice: sum over species and row blocks (fixed order) --------
+    double* rho0 = cluster.map_shared_rank(rho_s, 0);
+    const int per = (nx + FIELD_CLUSTER - 1) / FIELD_CLUSTER;
+    const int xlo = rank * per, xhi = min(nx, xlo + per);
+    for (int x = xlo + threadIdx.x; x < xhi; x += FIELD_THREADS) {
+        double r = 0.0;
+        for (int s = 0; s < A->ns; ++s) {
+            const SpDev& sp = A->sp[s];
+            for (int k = 0; k < sp.nrb; ++k) r += sp.rho_part[(size_t)k * nx + x];
+        }
+        rho0[x] = r;
+    }
+    cluster.sync();
+    if (rank != 0) return;
+
+    // --- CTA 0: Poisson --------------------------------------------------
+    for (int x = threadIdx.x; x < nx; x += FIELD_THREADS) fd.rho[x] = rho_s[x];
+    double* Eout = fd.E64;
+    if (fd.pow2) {
+        const int M = nx / 2;
+        int bits = 0;
+        while ((1 << bits) < M) ++bits;
+        for (int n = threadIdx.x; n < M; n += FIELD_THREADS)
+            work[bitrev(n, bits)] = make_double2(rho_s[2 * n], rho_s[2 * n + 1]);
+        __syncthreads();
+        fft_pow2(work, M, nx, fd.tw, false);
+        // unpack X_m = Ev_m + W^m Od_m and form Ehat_m = -i g_m X_m  (m = 0..M)
+        // then pack Y_m = Ev'_m + i Od'_m of the field for the inverse.
+        double2* Y = reinterpret_cast<double2*>(rho_s);   // reuse: needs M * 16 = nx * 8 bytes
+        // compute Ehat into registers per m, then pair (m, M - m)
+        for (int m = threadIdx.x; m < M; m += FIELD_THREADS) {
+            // X_m and X_{M-m}
+            const double2 Zm = work[m];
+            const double2 Zc = conj2(work[(M - m) % M]);
+            const double2 ev = make_double2(0.5 * (Zm.x + Zc.x), 0.5 * (Zm.y + Zc.y));
+            const double2 dd = make_double2(0.5 * (Zm.x - Zc.x), 0.5 * (Zm.y - Zc.y));   // = i Od
+            const double2 od = make_double2(dd.y, -dd.x);                                 // Od = -i dd
+            const double2 Xm = cadd(ev, cmul(fd.tw[m], od));
+            // partner index p = M - m (for m = 0 the partner is the Nyquist mode M)
+            const int mp = M - m;
+            const double2 Zp = work[mp % M];
+            const double2 Zpc = conj2(work[m]);   // Z_{M - mp} = Z_m
+            const double2 evp = make_double2(0.5 * (Zp.x + Zpc.x), 0.5 * (Zp.y + Zpc.y));
+            const double2 ddp = make_double2(0.5 * (Zp.x - Zpc.x), 0.5 * (Zp.y - Zpc.y));
+            const double2 odp = make_double2(ddp.y, -ddp.x);
+            double2 twp = (mp < nx) ? fd.tw[mp] : make_double2(1.0, 0.0);
+            const double2 Xp = cadd(evp, cmul(twp, odp));
+            // Ehat = -i g X  ->  (g X.y, -g X.x)
+            const double gm = fd.gmul[m], gp = fd.gmul[mp];
+            const double2 Em = make_double2(gm * Xm.y, -gm * Xm.x);
+            const double2 Ep = make_double2(gp * Xp.y, -gp * Xp.x);
+            // inverse pack: Ev'_m = (E_m + conj(E_{M-m}))/2, Od'_m = (E_m - conj(E_{M-m}))/2 * exp(+2 pi i m/N)
+            const double2 Epc = conj2(Ep);
+            const double2 ev2 = make_double2(0.5 * (Em.x + Epc.x), 0.5 * (Em.y + Epc.y));
+            const double2 od2 = cmul(make_double2(0.5 * (Em.x - Epc.x), 0.5 * (Em.y - Epc.y)), conj2(fd.tw[m]));
+            Y[bitrev(m, bits)] = make_double2(ev2.x - od2.y, ev2.y + od2.x);   // ev2 + i od2
+        }
+        __syncthreads();
+        fft_pow2(Y, M, nx, fd.tw, true);
+        const double inv = 1.0 / (double)M;
+        for (int n = threadIdx.x; n < M; n += FIELD_THREADS) {
+            const double2 y = Y[n];
+            Eout[2 * n] = y.x * inv;
+            Eout[2 * n + 1] = y.y * inv;
+        }
+    } else {
+        // direct DFT: Ehat_m for m = 1 .. (nx-1)/2, then E_i = (2/N) sum Re(Ehat_m e^{+i})
+        const int mmax = (nx - 1) / 2;
+        for (int m = 1 + threadIdx.x; m <= mmax; m += FIELD_THREADS) {
+            double rr = 0.0, ri = 0.0;
+            for (int i = 0; i < nx; ++i) {
+                const double2 w = fd.tw[(int)(((long long)m * i) % nx)];
+                rr += rho_s[i] * w.x;
+                ri += rho_s[i] * w.y;
+            }
+            const double g = fd.gmul[m];
+            work[m] = make_double2(g * ri, -g * rr);   // -i g (rr + i ri)
+        }
+        __syncthreads();
+        for (int i = threadIdx.x; i < nx; i += FIELD_THREADS) {
+            double acc = 0.0;
+            for (int m = 1; m <= mmax; ++m) {
+                const double2 w = fd.tw[(int)(((long long)m * i) % nx)];
+                // Re(E_m * conj(w))
+                acc += work[m].x * w.x + work[m].y * w.y;
+            }
+            Eout[i] = 2.0 * acc / (double)nx;
+        }
+    }
+    __syncthreads();
+    // --- E in FP32, field energy, diagnostics row --------------------------
+    double we = 0.0;
+    for (int x = threadIdx.x; x < nx; x += FIELD_THREADS) {
+        const double e = Eout[x];
+        fd.E32[x] = (float)e;
+        we += e * e;
+    }
+    for (int o = 16; o > 0; o >>= 1) we += __shfl_down_sync(0xffffffffu, we, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = we;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s2 = 0.0;
+        for (int w = 0; w < FIELD_THREADS / 32; ++w) s2 += red[w];
+        const double WE = s2 * fd.dx / (2.0 * fd.cP);
+        const int ns = A->ns;
+        double wk_tot = 0.0;
+        bool bad = !isfinite(WE);
+        for (int s = 0; s < ns; ++s) {
+            const SpDev& sp = A->sp[s];
+            double N = 0.0, Wk = 0.0, S = 0.0;
+            for (int k = 0; k < sp.nrb; ++k) {
+                N += sp.dpart[(size_t)k * 4 + 0];
+                Wk += sp.dpart[(size_t)k * 4 + 1];
+                S += sp.dpart[(size_t)k * 4 + 2];
+            }
+            fd.diag[3 + s] = Wk;
+            fd.diag[3 + ns + s] = N;
+            fd.diag[3 + 2 * ns + s] = S;
+            wk_tot += Wk;
+            bad = bad || !isfinite(N) || !isfinite(Wk) || !isfinite(S);
+        }
+        fd.diag[0] = WE;
+        fd.diag[1] = wk_tot;
+        fd.diag[2] = WE + wk_tot;
+        Ctl* ctl = A->ctl;
+        if (bad) ctl->err |= ERR_NUMERIC;
+        // re-sort decision for the next step
+        int any = 0;
+        for (int s = 0; s < ns; ++s) {
+            const int flag = (A->sp[s].mobile && ctl->dirty[s] > 0) ? 1 : 0;
+            ctl->sort_flag[s] = flag;
+            any |= flag;
+            ctl->dirty[s] = 0;
+            ctl->ovf_last[s] = ctl->ovf_count[s];
+            ctl->ovf_count[s] = 0;
+        }
+        ctl->any_sort = any;
+        if (count_step) ctl->step += 1;
+    }
+}
+
+cudaError_t launch_field(const StepArgs& h, const StepArgs* d, int count_step, cudaStream_t st)
+{
+    const int nx = h.fd.nx;
+    const size_t smem = ((size_t)nx * 8 + 15) / 16 * 16 + ((size_t)nx / 2 + 2) * 16;
+    cudaFuncSetAttribute(k_field, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_field<<<FIELD_CLUSTER, FIELD_THREADS, smem, st>>>(d, count_step);
+    return cudaGetLastError();
+}
+
+}  // namespace avl

@@ -1,0 +1,78 @@
+"""Seeded synthetic workloads and marker states.
+
+This module only holds parameters and random draws (numpy's PCG64 seeded per
+workload); it contains none of the method's arithmetic.  Both the GPU tests
+and the CPU oracle tests take their inputs from here.
+
+Workloads (normalised units: omega_p = 1, lambda_D = 1, v_th,e = 1, electron
+charge -1 and mass 1, Poisson constant 1):
+
+landau      Landau damping 1d1v, FP64: electrons only (immobile neutralising
+            ions are the removed k = 0 mode); nx = 64, L = 4 pi (k = 0.5),
+            nv = 128 on [-6, 6]; 2 x 2 markers per cell (32768); f0 =
+            Maxwellian (1 + 0.01 cos 0.5 x); dt = 0.1; 200 steps.
+two_stream  Two-stream instability 1d1v, FP32: electrons 0.5 M(v-3) + 0.5
+            M(v+3) with 1e-4 density perturbations in modes 1-16 (seeded
+            random phases); mobile ions (m = 1836, T_i = T_e, v range
+            +-10 v_th,i, unperturbed); nx = 512, L = 0.4 nx = 204.8,
+            nv = 1024 on [-10, 10] v_th; 4 x 4 markers per cell (8388608 per
+            species); dt = 0.05; 2000 steps.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+BASE_SEED = 1804_03901
+
+
+def _maxwell(n, u, vth):
+    return (n, (u, 0.0, 0.0), (vth, 1.0, 1.0))
+
+
+def landau(nx=64, nv=128, steps=200):
+    return {
+        "name": f"landau_1d1v_fp64_nx{nx}_nv{nv}",
+        "nvdim": 1, "nx": nx, "L": 4 * math.pi, "dt": 0.1, "precision": "fp64",
+        "species": [dict(q=-1.0, m=1.0, nv=(nv,), vmin=(-6.0,), vmax=(6.0,), mobile=True)],
+        "f0": [dict(beams=[_maxwell(1.0, 0.0, 1.0)], modes=[(1, 0.01, 0.0)])],
+        "lattice": [(2, 2, 1, 1)],
+        "seed": BASE_SEED + 0, "jitter": 1.0, "steps": steps,
+    }
+
+
+def two_stream(nx=512, nv=1024, lattice=(4, 4, 1, 1), steps=2000, nmodes=16, amp=1e-4):
+    rng = np.random.default_rng(BASE_SEED + 1)
+    phases = rng.uniform(0.0, 2 * math.pi, nmodes)
+    vthi = 1836.0 ** -0.5
+    return {
+        "name": f"two_stream_1d1v_fp32_nx{nx}_nv{nv}",
+        "nvdim": 1, "nx": nx, "L": 0.4 * nx, "dt": 0.05, "precision": "fp32",
+        "species": [dict(q=-1.0, m=1.0, nv=(nv,), vmin=(-10.0,), vmax=(10.0,), mobile=True),
+                    dict(q=1.0, m=1836.0, nv=(nv,), vmin=(-10.0 * vthi,), vmax=(10.0 * vthi,),
+                         mobile=True)],
+        "f0": [dict(beams=[_maxwell(0.5, 3.0, 1.0), _maxwell(0.5, -3.0, 1.0)],
+                    modes=[(m + 1, amp, float(phases[m])) for m in range(nmodes)]),
+               dict(beams=[_maxwell(1.0, 0.0, vthi)], modes=[])],
+        "lattice": [tuple(lattice), tuple(lattice)],
+        "seed": BASE_SEED + 1, "jitter": 1.0, "steps": steps,
+    }
+
+
+def random_markers(seed, n, L, vmin, vmax, v_overhang=0.05, fmin=1e-12, fmax=1.0):
+    """Markers scattered uniformly in x and v (a few percent of them beyond
+    the velocity grid), values log-uniform over [fmin, fmax]; values are made
+    distinct so that two marker sets can be matched by value."""
+    rng = np.random.default_rng(seed)
+    x = rng.uniform(0.0, L, n)
+    span = vmax - vmin
+    v = rng.uniform(vmin - v_overhang * span, vmax + v_overhang * span, n)
+    f = np.exp(rng.uniform(math.log(fmin), math.log(fmax), n))
+    # distinct values even after rounding to FP32
+    f = np.unique(f.astype(np.float32)).astype(np.float64)
+    while f.size < n:
+        extra = np.exp(rng.uniform(math.log(fmin), math.log(fmax), n - f.size)).astype(np.float32)
+        f = np.unique(np.concatenate([f.astype(np.float32), extra])).astype(np.float64)
+    f = rng.permutation(f[:n])
+    return x, v, f
