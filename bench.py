@@ -34,7 +34,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 KERNEL_NAMES = ["k_pd1", "k_fin1", "k_field", "k_sort"]
-LAUNCHES_PER_STEP = 6   # k_pd1, k_fin1, k_field, k_sort_count1, k_sort_scan, k_scatter1
+LAUNCHES_PER_STEP = 3   # k_pd1, k_fin1, k_field (+3 re-sort kernels on steps that re-sort)
 BYTES_PER_MARKER_ALGO = {"fp32": 20.0, "fp64": 40.0}      # read x, v, f; write x, v
 BYTES_PER_MARKER_LAYOUT = {"fp32": 28.0, "fp64": 40.0}    # int32 cell + f32 offset for x
 
@@ -48,12 +48,15 @@ def parse():
     p.add_argument("--workload", choices=["two_stream", "landau"], default="two_stream")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--nv", type=int, default=0, help="velocity cells (profiling of a smaller case)")
     return p.parse_args()
 
 
-def workload(name):
+def workload(name, nv=0):
     from paper_1804_03901_gb300 import inputs
-    return inputs.two_stream() if name == "two_stream" else inputs.landau()
+    if name == "two_stream":
+        return inputs.two_stream(nv=nv) if nv else inputs.two_stream()
+    return inputs.landau(nv=nv) if nv else inputs.landau()
 
 
 def markers_of(w):
@@ -189,7 +192,7 @@ def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return
-    w = workload(args.workload)
+    w = workload(args.workload, args.nv)
     frac = 1.0 / 64 if args.workload == "two_stream" else 1.0
     cpu_oracle_rate(w, sample_fraction=frac, steps=max(1, args.warmup))   # warm-up (page-in)
     rate, nmark, done, el = cpu_oracle_rate(w, sample_fraction=frac, steps=args.steps)
@@ -215,8 +218,10 @@ def run_ours(args):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     from paper_1804_03901_gb300 import avl as A
 
-    w = workload(args.workload)
-    stream = torch.cuda.current_stream()
+    w = workload(args.workload, args.nv)
+    # a dedicated stream: the library enqueues on it, the timing events too
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
     sim = build_sim(A, w, stream.cuda_stream, seed_offset=rank)
     nmark = markers_of(w)
     for s in range(len(w["species"])):
@@ -317,7 +322,7 @@ def run_ours(args):
                            "l2": "inputs larger than L2 (markers 16 B each, 268 MB per step read)"
                            if args.workload == "two_stream" else "small workload (fits in L2)",
                            "parallelism": "single GPU" if world == 1 else f"{world} independent replicas"},
-                "roofline": roofline, "clocks": clk, "gpu_launches": LAUNCHES_PER_STEP * args.steps,
+                "roofline": roofline, "clocks": clk, "gpu_launches": LAUNCHES_PER_STEP * args.steps + 3 * int(stats[:, 1].max()),
                 "resorts": [int(x) for x in stats[:, 1]], "e2e": e2e, "cpu_baseline": cpu}
         print(json.dumps(line), flush=True)
     sim.close()

@@ -160,32 +160,74 @@ avl_status refresh(avl_ctx* c)
 {
     AVL_CUDA(c, launch_pd1(c->h, c->d_args, 0, c->st));
     AVL_CUDA(c, launch_fin1(c->h, c->d_args, 1, c->st));
-    AVL_CUDA(c, launch_field(c->h, c->d_args, 0, c->st));
+    AVL_CUDA(c, launch_field(c->h, c->d_args, 0, 0, c->st));
     AVL_CUDA(c, launch_sort1(c->h, c->d_args, c->st));
     return AVL_OK;
 }
 
+// one step without a graph: the re-sort kernels always run and return at
+// once unless the field kernel flagged a species
 avl_status enqueue_step(avl_ctx* c)
 {
     AVL_CUDA(c, launch_pd1(c->h, c->d_args, 1, c->st));
     AVL_CUDA(c, launch_fin1(c->h, c->d_args, 0, c->st));
-    AVL_CUDA(c, launch_field(c->h, c->d_args, 1, c->st));
+    AVL_CUDA(c, launch_field(c->h, c->d_args, 1, 0, c->st));
     AVL_CUDA(c, launch_sort1(c->h, c->d_args, c->st));
     return AVL_OK;
 }
 
+// one step as a graph: push+deposit -> finalize -> field, then an IF node
+// whose body (the re-sort) runs only when the field kernel sets the
+// condition from the device
 avl_status build_graph(avl_ctx* c)
 {
     if (c->gexec) return AVL_OK;
     cudaGraph_t g = nullptr;
-    AVL_CUDA(c, cudaStreamBeginCapture(c->st, cudaStreamCaptureModeThreadLocal));
-    avl_status st = enqueue_step(c);
-    cudaError_t e = cudaStreamEndCapture(c->st, &g);
-    if (st != AVL_OK) {
-        if (g) cudaGraphDestroy(g);
-        return st;
+    AVL_CUDA(c, cudaGraphCreate(&g, 0));
+    cudaGraphConditionalHandle cond = 0;
+    cudaError_t e = cudaGraphConditionalHandleCreate(&cond, g, 0, cudaGraphCondAssignDefault);
+    if (!e) e = cudaStreamBeginCaptureToGraph(c->st, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+    if (e) {
+        cudaGraphDestroy(g);
+        return cuda_fail(c, e, "graph capture setup");
     }
-    if (e != cudaSuccess) return cuda_fail(c, e, "cudaStreamEndCapture");
+    cudaError_t el = launch_pd1(c->h, c->d_args, 1, c->st);
+    if (!el) el = launch_fin1(c->h, c->d_args, 0, c->st);
+    if (!el) el = launch_field(c->h, c->d_args, 1, (unsigned long long)cond, c->st);
+    cudaGraphNode_t cnode = nullptr;
+    cudaGraph_t body = nullptr;
+    if (!el) {
+        cudaStreamCaptureStatus cs;
+        cudaGraph_t capg = nullptr;
+        const cudaGraphNode_t* deps = nullptr;
+        size_t ndeps = 0;
+        el = cudaStreamGetCaptureInfo(c->st, &cs, nullptr, &capg, &deps, nullptr, &ndeps);
+        if (!el) {
+            cudaGraphNodeParams cp = {};
+            cp.type = cudaGraphNodeTypeConditional;
+            cp.conditional.handle = cond;
+            cp.conditional.type = cudaGraphCondTypeIf;
+            cp.conditional.size = 1;
+            el = cudaGraphAddNode(&cnode, capg, deps, nullptr, ndeps, &cp);
+            if (!el) body = cp.conditional.phGraph_out[0];
+        }
+        if (!el) el = cudaStreamUpdateCaptureDependencies(c->st, &cnode, nullptr, 1, cudaStreamSetCaptureDependencies);
+    }
+    cudaGraph_t got = nullptr;
+    e = cudaStreamEndCapture(c->st, &got);
+    if (el || e) {
+        cudaGraphDestroy(g);
+        return cuda_fail(c, el ? el : e, "graph capture of the step");
+    }
+    e = cudaStreamBeginCaptureToGraph(c->st, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+    if (!e) {
+        el = launch_sort1(c->h, c->d_args, c->st);
+        e = cudaStreamEndCapture(c->st, &got);
+    }
+    if (el || e) {
+        cudaGraphDestroy(g);
+        return cuda_fail(c, el ? el : e, "graph capture of the re-sort body");
+    }
     e = cudaGraphInstantiate(&c->gexec, g, 0);
     cudaGraphDestroy(g);
     if (e != cudaSuccess) {
@@ -332,9 +374,7 @@ avl_status avl_create(const avl_domain* dom, const avl_species* spec, int32_t ns
 
     // --- per species binning and grids ------------------------------------
     const int hw = 3, hd = 1;
-    int bin_base = 0, rb_base = 0;
-    int nv_total = 0;
-    for (int s = 0; s < nspecies; ++s) nv_total += spec[s].nv[0];
+    int bin_base = 0, fin_base = 0;
     for (int s = 0; s < nspecies; ++s) {
         const avl_species& p = spec[s];
         SpDev& sp = h.sp[s];
@@ -375,20 +415,24 @@ avl_status avl_create(const avl_domain* dom, const avl_species* spec, int32_t ns
         sp.nbins = (p.nv[0] + tv - 1) / tv;
         sp.bin_base = bin_base;
         bin_base += sp.nbins;
-        int rb = std::max(1, (nv_total + 303) / 304);
-        const int rb_env = env_int("AVL_RB", 0);
-        if (rb_env > 0) rb = rb_env;
-        rb = std::min(rb, p.nv[0]);
-        sp.rb = rb;
-        sp.nrb = (p.nv[0] + rb - 1) / rb;
-        sp.rb_base = rb_base;
-        rb_base += sp.nrb;
+        // finalize blocks: FIN_XB columns x rq rows, about 4 blocks per SM in total
+        sp.nxb = (nx + FIN_XB - 1) / FIN_XB;
+        int nrq = std::max(1, (608 + nspecies * sp.nxb - 1) / (nspecies * sp.nxb));
+        const int rq_env = env_int("AVL_RQ", 0);
+        int rq = std::max(8, (p.nv[0] + nrq - 1) / nrq);
+        if (rq_env > 0) rq = rq_env;
+        rq = std::min(rq, p.nv[0]);
+        sp.rq = rq;
+        sp.nrq = (p.nv[0] + rq - 1) / rq;
+        sp.nfin = sp.nxb * sp.nrq;
+        sp.fin_base = fin_base;
+        fin_base += sp.nfin;
         const size_t cells = (size_t)nx * sp.nvflat;
         void *pf, *pn, *pp, *po, *pr, *pd, *pb0, *pb1, *pc, *ph;
         if ((e = dalloc(c, &pf, cells * pb, true)) || (e = dalloc(c, &pn, cells * pb, true)) ||
             (e = dalloc(c, &pp, (size_t)sp.nbins * 16 * sp.W * nx, true)) ||
-            (e = dalloc(c, &po, 2 * cells * 8, true)) || (e = dalloc(c, &pr, (size_t)sp.nrb * nx * 8, true)) ||
-            (e = dalloc(c, &pd, (size_t)sp.nrb * 4 * 8, true)) ||
+            (e = dalloc(c, &po, 2 * cells * 8, true)) || (e = dalloc(c, &pr, (size_t)sp.nrq * nx * 8, true)) ||
+            (e = dalloc(c, &pd, (size_t)sp.nfin * 4 * 8, true)) ||
             (e = dalloc(c, &pb0, (size_t)(sp.nbins + 1) * 4, true)) ||
             (e = dalloc(c, &pb1, (size_t)(sp.nbins + 1) * 4, true)) ||
             (e = dalloc(c, &pc, (size_t)sp.nbins * 4, true)) || (e = dalloc(c, &ph, (size_t)sp.nbins * 4, true))) {
@@ -408,7 +452,7 @@ avl_status avl_create(const avl_domain* dom, const avl_species* spec, int32_t ns
         sp.n = 0;
     }
     h.nbins_total = bin_base;
-    h.nrb_total = rb_base;
+    h.nfin_total = fin_base;
 
     void *pa, *pc, *pf0, *pbad;
     if ((e = dalloc(c, &pa, sizeof(StepArgs), false)) || (e = dalloc(c, &pc, sizeof(Ctl), true)) ||
@@ -421,6 +465,10 @@ avl_status avl_create(const avl_domain* dom, const avl_species* spec, int32_t ns
     c->d_f0 = (avl_f0*)pf0;
     c->d_bad = (unsigned long long*)pbad;
     h.ctl = c->d_ctl;
+    if ((e = configure_vhs1(h)) || (e = configure_field(h))) {
+        cuda_fail(c, e, "cudaFuncSetAttribute (shared memory)");
+        return bail(AVL_ECUDA);
+    }
     if (upload_args(c) != AVL_OK) return bail(AVL_ECUDA);
     *out = c;
     return AVL_OK;
@@ -648,7 +696,7 @@ avl_status avl_profile_steps(avl_ctx* c, int32_t nsteps, double* ms, int32_t nke
         if (!e) e = cudaEventRecord(ev[1], c->st);
         if (!e) e = launch_fin1(c->h, c->d_args, 0, c->st);
         if (!e) e = cudaEventRecord(ev[2], c->st);
-        if (!e) e = launch_field(c->h, c->d_args, 1, c->st);
+        if (!e) e = launch_field(c->h, c->d_args, 1, 0, c->st);
         if (!e) e = cudaEventRecord(ev[3], c->st);
         if (!e) e = launch_sort1(c->h, c->d_args, c->st);
         if (!e) e = cudaEventRecord(ev[4], c->st);

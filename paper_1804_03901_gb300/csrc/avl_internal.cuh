@@ -23,6 +23,7 @@ constexpr int MAXS = AVL_MAX_SPECIES;
 constexpr int PD_THREADS = 256;     // push + deposit block
 constexpr int PD_UNROLL = 4;        // markers in flight per thread
 constexpr int FIN_THREADS = 256;    // finalize block
+constexpr int FIN_XB = 16;          // x columns per finalize block
 constexpr int FIELD_THREADS = 512;  // Poisson cluster block
 constexpr int FIELD_CLUSTER = 8;    // CTAs in the Poisson cluster
 constexpr int SORT_THREADS = 256;
@@ -46,7 +47,8 @@ struct SpDev {
     int W;                     // window rows = tv + 2 hw
     int nbins;
     int bin_base;              // first global bin index of this species
-    int rb, nrb, rb_base;      // finalize row blocks
+    // finalize blocks: FIN_XB x-columns times a group of rq velocity rows
+    int nxb, rq, nrq, nfin, fin_base;
     // markers
     void* mx[2];               // FP32: int cell; FP64: double xi
     float* moff[2];            // FP32 only
@@ -60,8 +62,8 @@ struct SpDev {
     void* ngrid;
     void* partial;             // [nbins][planes][W][nx]
     double* ovf;               // [2][nvflat][nx] FP64 overflow num/den
-    double* rho_part;          // [nrb][nx]
-    double* dpart;             // [nrb][4] : N, Wkin, S, -
+    double* rho_part;          // [nrq][nx] charge of this species per row group
+    double* dpart;             // [nfin][4] : N, Wkin, S, -
 };
 
 struct FieldDev {
@@ -90,7 +92,7 @@ struct Ctl {
 
 struct StepArgs {
     int ns, prec, nvdim;
-    int nbins_total, nrb_total;
+    int nbins_total, nfin_total;
     SpDev sp[MAXS];
     FieldDev fd;
     Ctl* ctl;
@@ -99,7 +101,8 @@ struct StepArgs {
 // kernel launchers (defined in the .cu files; all enqueue on `st`)
 cudaError_t launch_pd1(const StepArgs& h, const StepArgs* d, int push, cudaStream_t st);
 cudaError_t launch_fin1(const StepArgs& h, const StepArgs* d, int all_species, cudaStream_t st);
-cudaError_t launch_field(const StepArgs& h, const StepArgs* d, int count_step, cudaStream_t st);
+cudaError_t launch_field(const StepArgs& h, const StepArgs* d, int count_step,
+                         unsigned long long sort_cond, cudaStream_t st);
 cudaError_t launch_sort1(const StepArgs& h, const StepArgs* d, cudaStream_t st);
 cudaError_t launch_init1(const StepArgs& h, const StepArgs* d, int s, const int lattice[4],
                          const avl_f0* f0_dev, unsigned long long seed, double jitter,
@@ -112,5 +115,7 @@ cudaError_t launch_get1(const StepArgs& h, const StepArgs* d, int s, double* x, 
 cudaError_t launch_getf(const StepArgs& h, int s, double* f, double* n, cudaStream_t st);
 
 size_t pd1_smem_bytes(const SpDev& sp, int prec);
+cudaError_t configure_vhs1(const StepArgs& h);
+cudaError_t configure_field(const StepArgs& h);
 
 }  // namespace avl

@@ -50,7 +50,7 @@ __device__ void fft_pow2(double2* a, int M, int N, const double2* __restrict__ t
 __device__ __forceinline__ int bitrev(int x, int bits) { return (int)(__brev((unsigned)x) >> (32 - bits)); }
 
 __global__ void __cluster_dims__(FIELD_CLUSTER, 1, 1) __launch_bounds__(FIELD_THREADS)
-    k_field(const StepArgs* __restrict__ A, int count_step)
+    k_field(const StepArgs* __restrict__ A, int count_step, unsigned long long sort_cond)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     cg::cluster_group cluster = cg::this_cluster();
@@ -69,7 +69,7 @@ __global__ void __cluster_dims__(FIELD_CLUSTER, 1, 1) __launch_bounds__(FIELD_TH
         double r = 0.0;
         for (int s = 0; s < A->ns; ++s) {
             const SpDev& sp = A->sp[s];
-            for (int k = 0; k < sp.nrb; ++k) r += sp.rho_part[(size_t)k * nx + x];
+            for (int k = 0; k < sp.nrq; ++k) r += sp.rho_part[(size_t)k * nx + x];
         }
         rho0[x] = r;
     }
@@ -161,20 +161,41 @@ __global__ void __cluster_dims__(FIELD_CLUSTER, 1, 1) __launch_bounds__(FIELD_TH
     for (int o = 16; o > 0; o >>= 1) we += __shfl_down_sync(0xffffffffu, we, o);
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = we;
     __syncthreads();
+    // per-species sums of the finalize blocks' diagnostics (fixed order per thread)
+    __shared__ double dsum[3 * MAXS][FIELD_THREADS / 32];
+    const int ns = A->ns;
+    for (int s = 0; s < ns; ++s) {
+        const SpDev& sp = A->sp[s];
+        double N = 0.0, Wk = 0.0, S = 0.0;
+        for (int k = threadIdx.x; k < sp.nfin; k += FIELD_THREADS) {
+            N += sp.dpart[(size_t)k * 4 + 0];
+            Wk += sp.dpart[(size_t)k * 4 + 1];
+            S += sp.dpart[(size_t)k * 4 + 2];
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            N += __shfl_down_sync(0xffffffffu, N, o);
+            Wk += __shfl_down_sync(0xffffffffu, Wk, o);
+            S += __shfl_down_sync(0xffffffffu, S, o);
+        }
+        if ((threadIdx.x & 31) == 0) {
+            dsum[3 * s + 0][threadIdx.x >> 5] = N;
+            dsum[3 * s + 1][threadIdx.x >> 5] = Wk;
+            dsum[3 * s + 2][threadIdx.x >> 5] = S;
+        }
+    }
+    __syncthreads();
     if (threadIdx.x == 0) {
         double s2 = 0.0;
         for (int w = 0; w < FIELD_THREADS / 32; ++w) s2 += red[w];
         const double WE = s2 * fd.dx / (2.0 * fd.cP);
-        const int ns = A->ns;
         double wk_tot = 0.0;
         bool bad = !isfinite(WE);
         for (int s = 0; s < ns; ++s) {
-            const SpDev& sp = A->sp[s];
             double N = 0.0, Wk = 0.0, S = 0.0;
-            for (int k = 0; k < sp.nrb; ++k) {
-                N += sp.dpart[(size_t)k * 4 + 0];
-                Wk += sp.dpart[(size_t)k * 4 + 1];
-                S += sp.dpart[(size_t)k * 4 + 2];
+            for (int w = 0; w < FIELD_THREADS / 32; ++w) {
+                N += dsum[3 * s + 0][w];
+                Wk += dsum[3 * s + 1][w];
+                S += dsum[3 * s + 2][w];
             }
             fd.diag[3 + s] = Wk;
             fd.diag[3 + ns + s] = N;
@@ -199,15 +220,25 @@ __global__ void __cluster_dims__(FIELD_CLUSTER, 1, 1) __launch_bounds__(FIELD_TH
         }
         ctl->any_sort = any;
         if (count_step) ctl->step += 1;
+        if (sort_cond) cudaGraphSetConditional((cudaGraphConditionalHandle)sort_cond, any ? 1u : 0u);
     }
 }
 
-cudaError_t launch_field(const StepArgs& h, const StepArgs* d, int count_step, cudaStream_t st)
+static size_t field_smem(const StepArgs& h)
 {
     const int nx = h.fd.nx;
-    const size_t smem = ((size_t)nx * 8 + 15) / 16 * 16 + ((size_t)nx / 2 + 2) * 16;
-    cudaFuncSetAttribute(k_field, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_field<<<FIELD_CLUSTER, FIELD_THREADS, smem, st>>>(d, count_step);
+    return ((size_t)nx * 8 + 15) / 16 * 16 + ((size_t)nx / 2 + 2) * 16;
+}
+
+cudaError_t configure_field(const StepArgs& h)
+{
+    return cudaFuncSetAttribute(k_field, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)field_smem(h));
+}
+
+cudaError_t launch_field(const StepArgs& h, const StepArgs* d, int count_step, unsigned long long sort_cond,
+                         cudaStream_t st)
+{
+    k_field<<<FIELD_CLUSTER, FIELD_THREADS, field_smem(h), st>>>(d, count_step, sort_cond);
     return cudaGetLastError();
 }
 

@@ -134,17 +134,23 @@ struct Window<double> {
     }
 };
 
+// periodic neighbours of a lower CIC cell i0 in [-1, nx-1]; clamped so that a
+// non-finite position can never index outside the grid
+__device__ __forceinline__ void wrap_pair(int i0, int nx, int& ia, int& ib)
+{
+    ia = i0 < 0 ? i0 + nx : i0;
+    ib = (i0 + 1 >= nx) ? i0 + 1 - nx : i0 + 1;
+    ia = min(max(ia, 0), nx - 1);
+    ib = min(max(ib, 0), nx - 1);
+}
+
 __device__ __forceinline__ int floor_div(int a, int b) { return a >= 0 ? a / b : -((-a + b - 1) / b); }
 __device__ __forceinline__ int ceil_div(int a, int b) { return a >= 0 ? (a + b - 1) / b : -((-a) / b); }
 
-__device__ __forceinline__ int species_of(const StepArgs* A, int g, bool by_rb)
+__device__ __forceinline__ int species_of(const StepArgs* A, int g, bool)
 {
     int s = 0;
-    if (by_rb) {
-        while (s + 1 < A->ns && g >= A->sp[s + 1].rb_base) ++s;
-    } else {
-        while (s + 1 < A->ns && g >= A->sp[s + 1].bin_base) ++s;
-    }
+    while (s + 1 < A->ns && g >= A->sp[s + 1].bin_base) ++s;
     return s;
 }
 
@@ -251,11 +257,10 @@ __global__ void __launch_bounds__(PD_THREADS) k_pd1(const StepArgs* __restrict__
             bool dirty = false, over = false;
             if (valid) {
                 if (push) {
-                    int i0;
+                    int i0, ia, ib;
                     T w;
                     pos[u].cic(i0, w);
-                    const int ia = i0 < 0 ? i0 + nx : i0;
-                    const int ib = (i0 + 1 >= nx) ? i0 + 1 - nx : i0 + 1;
+                    wrap_pair(i0, nx, ia, ib);
                     const T El = ((T)1 - w) * Es[ia] + w * Es[ib];
                     dv[u] += qm_dt * El;
                     pos[u].drift(vref_dtdx + dv[u] * dt_dx, nx);
@@ -263,11 +268,10 @@ __global__ void __launch_bounds__(PD_THREADS) k_pd1(const StepArgs* __restrict__
                     dvp[k] = dv[u];
                 }
                 // deposit at the new position (Eq. 4 numerator and denominator)
-                int i0;
+                int i0, ia, ib;
                 T wx;
                 pos[u].cic(i0, wx);
-                const int ia = i0 < 0 ? i0 + nx : i0;
-                const int ib = (i0 + 1 >= nx) ? i0 + 1 - nx : i0 + 1;
+                wrap_pair(i0, nx, ia, ib);
                 const T t = dv[u] * inv_dv - (T)0.5;
                 const T ft = floor(t);
                 const int r0 = (int)ft;
@@ -325,74 +329,182 @@ __global__ void __launch_bounds__(PD_THREADS) k_pd1(const StepArgs* __restrict__
 }
 
 // ---------------------------------------------------------------------------
-// finalize: f = num / den, rho partial sums, diagnostics partial sums
+// finalize: f = num / den (Eq. 4), charge per row group (Eq. 14), diagnostics
 // ---------------------------------------------------------------------------
+// FP32 path: float-float arithmetic (an unevaluated sum hi + lo) so that the
+// cell values and the column sums keep the accuracy of the compensated
+// deposit without per-cell FP64 work.
+struct ff {
+    float hi, lo;
+};
+
+__device__ __forceinline__ void ff_add(ff& a, float x)
+{
+    const float s = __fadd_rn(a.hi, x);
+    const float bp = __fsub_rn(s, a.hi);
+    const float e = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bp)), __fsub_rn(x, bp));
+    a.hi = s;
+    a.lo = __fadd_rn(a.lo, e);
+}
+
+template <typename T>
+struct CellSum;
+
+template <>
+struct CellSum<float> {
+    ff num{0.f, 0.f}, den{0.f, 0.f};
+    __device__ __forceinline__ void add_partial(const float* p, int plane)
+    {
+        ff_add(num, p[0]);
+        num.lo = __fadd_rn(num.lo, p[plane]);
+        ff_add(den, p[2 * plane]);
+        den.lo = __fadd_rn(den.lo, p[3 * plane]);
+    }
+    __device__ __forceinline__ void add_ovf(double n, double d)
+    {
+        ff_add(num, (float)n);
+        num.lo = __fadd_rn(num.lo, (float)(n - (double)(float)n));
+        ff_add(den, (float)d);
+        den.lo = __fadd_rn(den.lo, (float)(d - (double)(float)d));
+    }
+    // f = num / den as float-float (q, r / den); den = 0 gives f = 0
+    __device__ __forceinline__ void value(float& fh, float& fl, float& dsum) const
+    {
+        dsum = __fadd_rn(den.hi, den.lo);
+        if (den.hi > 0.f) {
+            const float q = __fdiv_rn(num.hi, den.hi);
+            float r = fmaf(-q, den.hi, num.hi);
+            r = __fadd_rn(r, __fsub_rn(num.lo, __fmul_rn(q, den.lo)));
+            fh = q;
+            fl = __fdiv_rn(r, den.hi);
+        } else {
+            fh = 0.f;
+            fl = 0.f;
+        }
+    }
+};
+
+template <>
+struct CellSum<double> {
+    double num = 0.0, den = 0.0;
+    __device__ __forceinline__ void add_partial(const double* p, int plane)
+    {
+        num += p[0];
+        den += p[plane];
+    }
+    __device__ __forceinline__ void add_ovf(double n, double d)
+    {
+        num += n;
+        den += d;
+    }
+    __device__ __forceinline__ void value(double& fh, double& fl, double& dsum) const
+    {
+        dsum = den;
+        fh = den > 0.0 ? num / den : 0.0;
+        fl = 0.0;
+    }
+};
+
+template <typename T>
+struct ColAcc;
+
+template <>
+struct ColAcc<float> {
+    ff rho{0.f, 0.f}, w{0.f, 0.f}, ent{0.f, 0.f};
+    __device__ __forceinline__ void add(float fh, float fl, float v2)
+    {
+        ff_add(rho, fh);
+        rho.lo = __fadd_rn(rho.lo, fl);
+        ff_add(w, __fmul_rn(v2, fh));
+        if (fh > 0.f) ff_add(ent, __fmul_rn(fh, logf(fh)));
+    }
+    __device__ __forceinline__ double r() const { return (double)rho.hi + (double)rho.lo; }
+    __device__ __forceinline__ double wk() const { return (double)w.hi + (double)w.lo; }
+    __device__ __forceinline__ double s() const { return (double)ent.hi + (double)ent.lo; }
+};
+
+template <>
+struct ColAcc<double> {
+    double rho = 0.0, w = 0.0, ent = 0.0;
+    __device__ __forceinline__ void add(double fh, double, double v2)
+    {
+        rho += fh;
+        w += v2 * fh;
+        if (fh > 0.0) ent += fh * log(fh);
+    }
+    __device__ __forceinline__ double r() const { return rho; }
+    __device__ __forceinline__ double wk() const { return w; }
+    __device__ __forceinline__ double s() const { return ent; }
+};
+
+__device__ __forceinline__ int species_of_fin(const StepArgs* A, int g)
+{
+    int s = 0;
+    while (s + 1 < A->ns && g >= A->sp[s + 1].fin_base) ++s;
+    return s;
+}
+
 template <typename T>
 __global__ void __launch_bounds__(FIN_THREADS) k_fin1(const StepArgs* __restrict__ A, int all_species)
 {
-    extern __shared__ __align__(16) double rho_acc[];
+    constexpr int RL = FIN_THREADS / FIN_XB;   // row lanes
+    __shared__ double col_red[RL][FIN_XB];
     __shared__ double red[3][FIN_THREADS / 32];
     const int g = blockIdx.x;
-    const int s = species_of(A, g, true);
+    const int s = species_of_fin(A, g);
     const SpDev& sp = A->sp[s];
     if (!all_species && !sp.mobile) return;
     Ctl* ctl = A->ctl;
-    const int rbk = g - sp.rb_base;
+    const int blk = g - sp.fin_base;
+    const int xb = blk % sp.nxb, rqi = blk / sp.nxb;
     const int nx = sp.nx, nv = sp.nvflat, tv = sp.tv, hw = sp.hw, W = sp.W;
-    const int j0 = rbk * sp.rb;
-    const int j1 = min(nv, j0 + sp.rb);
+    const int col = threadIdx.x % FIN_XB, lr = threadIdx.x / FIN_XB;
+    const int x = xb * FIN_XB + col;
+    const bool xok = x < nx;
+    const int j0 = rqi * sp.rq, j1 = min(nv, j0 + sp.rq);
     const int plane = W * nx;
     const bool any_ovf = ctl->ovf_count[s] != 0;
     double* ovf_num = sp.ovf;
     double* ovf_den = sp.ovf + (size_t)nv * nx;
     T* fg = reinterpret_cast<T*>(sp.fgrid);
     T* ng = reinterpret_cast<T*>(sp.ngrid);
+    const T* part = reinterpret_cast<const T*>(sp.partial);
+    const int planes = sizeof(T) == 4 ? 4 : 2;
 
-    for (int x = threadIdx.x; x < nx; x += FIN_THREADS) rho_acc[x] = 0.0;
-    double dN = 0.0, dW = 0.0, dS = 0.0;
-
-    for (int j = j0; j < j1; ++j) {
-        // bins whose windows [b tv - hw, b tv + tv + hw) contain row j
-        const int blo = max(ceil_div(j - tv - hw + 1, tv), 0);
-        const int bhi = min(floor_div(j + hw, tv), sp.nbins - 1);
-        const double vj = sp.vmin[0] + (j + 0.5) * sp.dv[0];
-        for (int x = threadIdx.x; x < nx; x += FIN_THREADS) {
-            double num = 0.0, den = 0.0;
+    ColAcc<T> acc;
+    if (xok) {
+        for (int j = j0 + lr; j < j1; j += RL) {
+            const int blo = max(ceil_div(j - tv - hw + 1, tv), 0);
+            const int bhi = min(floor_div(j + hw, tv), sp.nbins - 1);
+            CellSum<T> cs;
             for (int b = blo; b <= bhi; ++b) {
                 const int wr = j - (b * tv - hw);
-                if (sizeof(T) == 4) {
-                    const float* p = reinterpret_cast<const float*>(sp.partial) + (size_t)b * 4 * plane +
-                                     (size_t)wr * nx + x;
-                    num += (double)p[0] + (double)p[plane];
-                    den += (double)p[2 * plane] + (double)p[3 * plane];
-                } else {
-                    const double* p = reinterpret_cast<const double*>(sp.partial) +
-                                      (size_t)b * 2 * plane + (size_t)wr * nx + x;
-                    num += p[0];
-                    den += p[plane];
-                }
+                cs.add_partial(part + (size_t)b * planes * plane + (size_t)wr * nx + x, plane);
             }
             if (any_ovf) {
                 const size_t o = (size_t)j * nx + x;
-                num += ovf_num[o];
-                den += ovf_den[o];
+                cs.add_ovf(ovf_num[o], ovf_den[o]);
                 ovf_num[o] = 0.0;
                 ovf_den[o] = 0.0;
             }
-            const double f = den > 0.0 ? num / den : 0.0;
-            fg[(size_t)j * nx + x] = (T)f;
-            ng[(size_t)j * nx + x] = (T)den;
-            rho_acc[x] += f;
-            dN += f;
-            dW += vj * vj * f;
-            if (f > 0.0) dS += f * log(f);
+            T fh, fl, dsum;
+            cs.value(fh, fl, dsum);
+            fg[(size_t)j * nx + x] = fh + fl;
+            ng[(size_t)j * nx + x] = dsum;
+            const T vj = (T)(sp.vmin[0] + (j + 0.5) * sp.dv[0]);
+            acc.add(fh, fl, vj * vj);
         }
     }
+    // charge of this species per column, summed over the row lanes in order
+    col_red[lr][col] = acc.r();
     __syncthreads();
-    const double dvol = sp.dv[0];
-    for (int x = threadIdx.x; x < nx; x += FIN_THREADS)
-        sp.rho_part[(size_t)rbk * nx + x] = sp.q * dvol * rho_acc[x];
-    // block reduction of the diagnostics
+    if (lr == 0 && xok) {
+        double r = 0.0;
+        for (int k = 0; k < RL; ++k) r += col_red[k][col];
+        sp.rho_part[(size_t)rqi * nx + x] = sp.q * sp.dv[0] * r;
+    }
+    // diagnostics of the block
+    double dN = acc.r(), dW = acc.wk(), dS = acc.s();
     for (int o = 16; o > 0; o >>= 1) {
         dN += __shfl_down_sync(0xffffffffu, dN, o);
         dW += __shfl_down_sync(0xffffffffu, dW, o);
@@ -412,11 +524,11 @@ __global__ void __launch_bounds__(FIN_THREADS) k_fin1(const StepArgs* __restrict
             bb += red[1][w];
             c += red[2][w];
         }
-        const double cell = sp.dx * dvol;
-        sp.dpart[(size_t)rbk * 4 + 0] = a * cell;
-        sp.dpart[(size_t)rbk * 4 + 1] = 0.5 * sp.m * bb * cell;
-        sp.dpart[(size_t)rbk * 4 + 2] = c * cell;
-        sp.dpart[(size_t)rbk * 4 + 3] = 0.0;
+        const double cell = sp.dx * sp.dv[0];
+        sp.dpart[(size_t)blk * 4 + 0] = a * cell;
+        sp.dpart[(size_t)blk * 4 + 1] = 0.5 * sp.m * bb * cell;
+        sp.dpart[(size_t)blk * 4 + 2] = c * cell;
+        sp.dpart[(size_t)blk * 4 + 3] = 0.0;
     }
 }
 
@@ -678,6 +790,7 @@ __global__ void k_set_scatter1(const StepArgs* __restrict__ A, int s, long long 
 {
     const SpDev& sp = A->sp[s];
     const int cb = A->ctl->cur[s];
+    const double L = sp.nx * sp.dx;
     for (long long base = blockIdx.x * (long long)blockDim.x; base < n; base += (long long)gridDim.x * blockDim.x) {
         const long long k = base + threadIdx.x;
         int key = -1;
@@ -686,9 +799,11 @@ __global__ void k_set_scatter1(const StepArgs* __restrict__ A, int s, long long 
             xv = x[k];
             vv = v[k];
             fv = f[k];
-            int row = (int)floor((vv - sp.vmin[0]) * sp.inv_dv[0]);
-            row = row < 0 ? 0 : (row >= sp.nv[0] ? sp.nv[0] - 1 : row);
-            key = row / sp.tv;
+            if ((xv >= 0.0 && xv < L) && isfinite(vv) && isfinite(fv)) {   // same filter as the count
+                int row = (int)floor((vv - sp.vmin[0]) * sp.inv_dv[0]);
+                row = row < 0 ? 0 : (row >= sp.nv[0] ? sp.nv[0] - 1 : row);
+                key = row / sp.tv;
+            }
         }
         const int d = warp_aggregate_add(sp.cursor, key);
         if (key >= 0) {
@@ -775,31 +890,31 @@ static int max_pd_smem(const StepArgs& h)
     return (int)m;
 }
 
+// dynamic shared-memory limits, set once per context (outside any capture)
+cudaError_t configure_vhs1(const StepArgs& h)
+{
+    const int smem = max_pd_smem(h);
+    if (h.prec == AVL_FP32)
+        return cudaFuncSetAttribute(k_pd1<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    return cudaFuncSetAttribute(k_pd1<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+}
+
 cudaError_t launch_pd1(const StepArgs& h, const StepArgs* d, int push, cudaStream_t st)
 {
     const int smem = max_pd_smem(h);
-    if (h.prec == AVL_FP32) {
-        cudaFuncSetAttribute(k_pd1<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (h.prec == AVL_FP32)
         k_pd1<float><<<h.nbins_total, PD_THREADS, smem, st>>>(d, push);
-    } else {
-        cudaFuncSetAttribute(k_pd1<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    else
         k_pd1<double><<<h.nbins_total, PD_THREADS, smem, st>>>(d, push);
-    }
     return cudaGetLastError();
 }
 
 cudaError_t launch_fin1(const StepArgs& h, const StepArgs* d, int all_species, cudaStream_t st)
 {
-    int nxmax = 0;
-    for (int s = 0; s < h.ns; ++s) nxmax = std::max(nxmax, h.sp[s].nx);
-    const int smem = nxmax * 8;
-    if (h.prec == AVL_FP32) {
-        cudaFuncSetAttribute(k_fin1<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        k_fin1<float><<<h.nrb_total, FIN_THREADS, smem, st>>>(d, all_species);
-    } else {
-        cudaFuncSetAttribute(k_fin1<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        k_fin1<double><<<h.nrb_total, FIN_THREADS, smem, st>>>(d, all_species);
-    }
+    if (h.prec == AVL_FP32)
+        k_fin1<float><<<h.nfin_total, FIN_THREADS, 0, st>>>(d, all_species);
+    else
+        k_fin1<double><<<h.nfin_total, FIN_THREADS, 0, st>>>(d, all_species);
     return cudaGetLastError();
 }
 
