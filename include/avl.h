@@ -167,6 +167,18 @@ avl_status avl_get_diag(avl_ctx* ctx, double* out);
  * tracked), steps so far. */
 avl_status avl_get_stats(avl_ctx* ctx, int64_t* out);
 
+/* Stand-alone spectral Poisson solve (Sec. 3.1, Eq. 5 / Eq. 6a-c): E from
+ * rho on a periodic grid of nx cells over length L, k = 0 and Nyquist modes
+ * removed.  rho and E are device pointers to nx FP64 values (E may not alias
+ * rho); the work runs on cuda_stream (NULL: the legacy default stream).  The
+ * transform tables live in scratch memory that the call allocates with
+ * cudaMalloc and frees before returning; the call returns after the solve
+ * has completed.  Errors (message via avl_last_error(NULL)): AVL_EINVAL for
+ * nx outside [4, 65536] (or more shared memory than one block holds),
+ * non-positive L or poisson_const, NULL pointers; AVL_ENOMEM; AVL_ECUDA. */
+avl_status avl_field_solve(int32_t nx, double L, double poisson_const, int32_t softening,
+                           const double* rho, double* E, void* cuda_stream);
+
 /* Per-kernel timing (the paper's time breakdown, Sec. 3.2): advance nsteps
  * steps exactly as avl_step does, but launched kernel by kernel with CUDA
  * events recorded on the context stream around each kernel; writes the summed

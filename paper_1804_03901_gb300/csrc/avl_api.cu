@@ -333,25 +333,8 @@ avl_status avl_create(const avl_domain* dom, const avl_species* spec, int32_t ns
     fd.dx = dx;
     fd.cP = dom->poisson_const;
     std::vector<double2> tw(nx);
-    for (int k = 0; k < nx; ++k) {
-        const double a = 2.0 * M_PI * (double)k / (double)nx;
-        tw[k] = make_double2(cos(a), -sin(a));
-    }
     std::vector<double> gm(nx / 2 + 1, 0.0);
-    for (int m = 1; m <= nx / 2; ++m) {
-        if (2 * m == nx) continue;   // Nyquist mode carries no field
-        const double k = 2.0 * M_PI * (double)m / dom->L;
-        double kappa, K2;
-        if (dom->softening) {
-            const double y1 = k * dx, y2 = 0.5 * k * dx;
-            kappa = k * (sin(y1) / y1);
-            K2 = k * k * (sin(y2) / y2) * (sin(y2) / y2);
-        } else {
-            kappa = k;
-            K2 = k * k;
-        }
-        gm[m] = dom->poisson_const * kappa / K2;
-    }
+    spectral_tables(nx, dom->L, dom->poisson_const, dom->softening, tw.data(), gm.data());
     void *p_rho, *p_E64, *p_E32, *p_tw, *p_gm, *p_diag;
     if ((e = dalloc(c, &p_rho, nx * 8, true)) || (e = dalloc(c, &p_E64, nx * 8, true)) ||
         (e = dalloc(c, &p_E32, nx * 4, true)) || (e = dalloc(c, &p_tw, nx * 16, false)) ||
@@ -711,6 +694,34 @@ avl_status avl_profile_steps(avl_ctx* c, int32_t nsteps, double* ms, int32_t nke
     for (int i = 0; i < 5; ++i) cudaEventDestroy(ev[i]);
     for (int k = 0; k < 4; ++k) ms[k] = acc[k];
     return st;
+}
+
+avl_status avl_field_solve(int32_t nx, double L, double poisson_const, int32_t softening, const double* rho,
+                           double* E, void* cuda_stream)
+{
+    if (nx < 4 || nx > (1 << 16)) return fail(nullptr, AVL_EINVAL, "nx must be in [4, 65536]");
+    if (!(L > 0) || !(poisson_const > 0) || !isfinite(L) || !isfinite(poisson_const))
+        return fail(nullptr, AVL_EINVAL, "L and poisson_const must be positive and finite");
+    if (softening != 0 && softening != 1) return fail(nullptr, AVL_EINVAL, "softening must be 0 or 1");
+    if (!rho || !E) return fail(nullptr, AVL_EINVAL, "rho or E is NULL");
+    if (poisson_smem_bytes(nx) > 200 * 1024) return fail(nullptr, AVL_EINVAL, "nx too large for one block");
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    std::vector<double2> tw(nx);
+    std::vector<double> gm(nx / 2 + 1);
+    spectral_tables(nx, L, poisson_const, softening, tw.data(), gm.data());
+    void* tab = nullptr;
+    const size_t twb = (size_t)nx * 16, gmb = (size_t)(nx / 2 + 1) * 8;
+    cudaError_t e = cudaMalloc(&tab, twb + gmb);
+    if (e) return cuda_fail(nullptr, e, "cudaMalloc(spectral tables)");
+    double2* dtw = static_cast<double2*>(tab);
+    double* dgm = reinterpret_cast<double*>(static_cast<unsigned char*>(tab) + twb);
+    e = cudaMemcpyAsync(dtw, tw.data(), twb, cudaMemcpyHostToDevice, st);
+    if (!e) e = cudaMemcpyAsync(dgm, gm.data(), gmb, cudaMemcpyHostToDevice, st);
+    if (!e) e = launch_poisson(rho, E, nx, dtw, dgm, st);
+    cudaError_t e2 = cudaStreamSynchronize(st);
+    cudaFree(tab);
+    if (e || e2) return cuda_fail(nullptr, e ? e : e2, "avl_field_solve");
+    return AVL_OK;
 }
 
 avl_status avl_synchronize(avl_ctx* c)

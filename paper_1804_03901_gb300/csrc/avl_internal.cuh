@@ -117,5 +117,10 @@ cudaError_t launch_getf(const StepArgs& h, int s, double* f, double* n, cudaStre
 size_t pd1_smem_bytes(const SpDev& sp, int prec);
 cudaError_t configure_vhs1(const StepArgs& h);
 cudaError_t configure_field(const StepArgs& h);
+// spectral tables of the Poisson solve (host) and the stand-alone solve
+void spectral_tables(int nx, double L, double cP, int softening, double2* tw, double* gm);
+size_t poisson_smem_bytes(int nx);
+cudaError_t launch_poisson(const double* rho, double* E, int nx, const double2* tw, const double* gmul,
+                           cudaStream_t st);
 
 }  // namespace avl

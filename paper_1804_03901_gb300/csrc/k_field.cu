@@ -11,6 +11,8 @@
 #include <cooperative_groups.h>
 #include <math.h>
 
+#include <vector>
+
 #include "avl_internal.cuh"
 
 namespace cg = cooperative_groups;
@@ -49,6 +51,86 @@ __device__ void fft_pow2(double2* a, int M, int N, const double2* __restrict__ t
 
 __device__ __forceinline__ int bitrev(int x, int bits) { return (int)(__brev((unsigned)x) >> (32 - bits)); }
 
+// Spectral Poisson solve (Eq. 5 / Eq. 6a-c) by the whole block: rho_s holds
+// rho in shared memory (nx doubles, overwritten), work is shared scratch of
+// nx/2 + 2 complex values; tw[k] = exp(-2 pi i k / nx), gmul[m] = cP kappa_m /
+// K2_m (zero at m = 0 and at the Nyquist mode).  Writes E (nx) to Eout.
+__device__ void poisson_spectral(double* rho_s, double2* work, double* Eout, int nx, int pow2,
+                                 const double2* __restrict__ tw, const double* __restrict__ gmul)
+{
+    if (pow2) {
+        const int M = nx / 2;
+        int bits = 0;
+        while ((1 << bits) < M) ++bits;
+        for (int n = threadIdx.x; n < M; n += FIELD_THREADS)
+            work[bitrev(n, bits)] = make_double2(rho_s[2 * n], rho_s[2 * n + 1]);
+        __syncthreads();
+        fft_pow2(work, M, nx, tw, false);
+        // unpack X_m = Ev_m + W^m Od_m and form Ehat_m = -i g_m X_m  (m = 0..M)
+        // then pack Y_m = Ev'_m + i Od'_m of the field for the inverse.
+        double2* Y = reinterpret_cast<double2*>(rho_s);   // reuse: needs M * 16 = nx * 8 bytes
+        // compute Ehat into registers per m, then pair (m, M - m)
+        for (int m = threadIdx.x; m < M; m += FIELD_THREADS) {
+            // X_m and X_{M-m}
+            const double2 Zm = work[m];
+            const double2 Zc = conj2(work[(M - m) % M]);
+            const double2 ev = make_double2(0.5 * (Zm.x + Zc.x), 0.5 * (Zm.y + Zc.y));
+            const double2 dd = make_double2(0.5 * (Zm.x - Zc.x), 0.5 * (Zm.y - Zc.y));   // = i Od
+            const double2 od = make_double2(dd.y, -dd.x);                                 // Od = -i dd
+            const double2 Xm = cadd(ev, cmul(tw[m], od));
+            // partner index p = M - m (for m = 0 the partner is the Nyquist mode M)
+            const int mp = M - m;
+            const double2 Zp = work[mp % M];
+            const double2 Zpc = conj2(work[m]);   // Z_{M - mp} = Z_m
+            const double2 evp = make_double2(0.5 * (Zp.x + Zpc.x), 0.5 * (Zp.y + Zpc.y));
+            const double2 ddp = make_double2(0.5 * (Zp.x - Zpc.x), 0.5 * (Zp.y - Zpc.y));
+            const double2 odp = make_double2(ddp.y, -ddp.x);
+            double2 twp = (mp < nx) ? tw[mp] : make_double2(1.0, 0.0);
+            const double2 Xp = cadd(evp, cmul(twp, odp));
+            // Ehat = -i g X  ->  (g X.y, -g X.x)
+            const double gm = gmul[m], gp = gmul[mp];
+            const double2 Em = make_double2(gm * Xm.y, -gm * Xm.x);
+            const double2 Ep = make_double2(gp * Xp.y, -gp * Xp.x);
+            // inverse pack: Ev'_m = (E_m + conj(E_{M-m}))/2, Od'_m = (E_m - conj(E_{M-m}))/2 * exp(+2 pi i m/N)
+            const double2 Epc = conj2(Ep);
+            const double2 ev2 = make_double2(0.5 * (Em.x + Epc.x), 0.5 * (Em.y + Epc.y));
+            const double2 od2 = cmul(make_double2(0.5 * (Em.x - Epc.x), 0.5 * (Em.y - Epc.y)), conj2(tw[m]));
+            Y[bitrev(m, bits)] = make_double2(ev2.x - od2.y, ev2.y + od2.x);   // ev2 + i od2
+        }
+        __syncthreads();
+        fft_pow2(Y, M, nx, tw, true);
+        const double inv = 1.0 / (double)M;
+        for (int n = threadIdx.x; n < M; n += FIELD_THREADS) {
+            const double2 y = Y[n];
+            Eout[2 * n] = y.x * inv;
+            Eout[2 * n + 1] = y.y * inv;
+        }
+    } else {
+        // direct DFT: Ehat_m for m = 1 .. (nx-1)/2, then E_i = (2/N) sum Re(Ehat_m e^{+i})
+        const int mmax = (nx - 1) / 2;
+        for (int m = 1 + threadIdx.x; m <= mmax; m += FIELD_THREADS) {
+            double rr = 0.0, ri = 0.0;
+            for (int i = 0; i < nx; ++i) {
+                const double2 w = tw[(int)(((long long)m * i) % nx)];
+                rr += rho_s[i] * w.x;
+                ri += rho_s[i] * w.y;
+            }
+            const double g = gmul[m];
+            work[m] = make_double2(g * ri, -g * rr);   // -i g (rr + i ri)
+        }
+        __syncthreads();
+        for (int i = threadIdx.x; i < nx; i += FIELD_THREADS) {
+            double acc = 0.0;
+            for (int m = 1; m <= mmax; ++m) {
+                const double2 w = tw[(int)(((long long)m * i) % nx)];
+                // Re(E_m * conj(w))
+                acc += work[m].x * w.x + work[m].y * w.y;
+            }
+            Eout[i] = 2.0 * acc / (double)nx;
+        }
+    }
+}
+
 __global__ void __cluster_dims__(FIELD_CLUSTER, 1, 1) __launch_bounds__(FIELD_THREADS)
     k_field(const StepArgs* __restrict__ A, int count_step, unsigned long long sort_cond)
 {
@@ -79,77 +161,7 @@ __global__ void __cluster_dims__(FIELD_CLUSTER, 1, 1) __launch_bounds__(FIELD_TH
     // --- CTA 0: Poisson --------------------------------------------------
     for (int x = threadIdx.x; x < nx; x += FIELD_THREADS) fd.rho[x] = rho_s[x];
     double* Eout = fd.E64;
-    if (fd.pow2) {
-        const int M = nx / 2;
-        int bits = 0;
-        while ((1 << bits) < M) ++bits;
-        for (int n = threadIdx.x; n < M; n += FIELD_THREADS)
-            work[bitrev(n, bits)] = make_double2(rho_s[2 * n], rho_s[2 * n + 1]);
-        __syncthreads();
-        fft_pow2(work, M, nx, fd.tw, false);
-        // unpack X_m = Ev_m + W^m Od_m and form Ehat_m = -i g_m X_m  (m = 0..M)
-        // then pack Y_m = Ev'_m + i Od'_m of the field for the inverse.
-        double2* Y = reinterpret_cast<double2*>(rho_s);   // reuse: needs M * 16 = nx * 8 bytes
-        // compute Ehat into registers per m, then pair (m, M - m)
-        for (int m = threadIdx.x; m < M; m += FIELD_THREADS) {
-            // X_m and X_{M-m}
-            const double2 Zm = work[m];
-            const double2 Zc = conj2(work[(M - m) % M]);
-            const double2 ev = make_double2(0.5 * (Zm.x + Zc.x), 0.5 * (Zm.y + Zc.y));
-            const double2 dd = make_double2(0.5 * (Zm.x - Zc.x), 0.5 * (Zm.y - Zc.y));   // = i Od
-            const double2 od = make_double2(dd.y, -dd.x);                                 // Od = -i dd
-            const double2 Xm = cadd(ev, cmul(fd.tw[m], od));
-            // partner index p = M - m (for m = 0 the partner is the Nyquist mode M)
-            const int mp = M - m;
-            const double2 Zp = work[mp % M];
-            const double2 Zpc = conj2(work[m]);   // Z_{M - mp} = Z_m
-            const double2 evp = make_double2(0.5 * (Zp.x + Zpc.x), 0.5 * (Zp.y + Zpc.y));
-            const double2 ddp = make_double2(0.5 * (Zp.x - Zpc.x), 0.5 * (Zp.y - Zpc.y));
-            const double2 odp = make_double2(ddp.y, -ddp.x);
-            double2 twp = (mp < nx) ? fd.tw[mp] : make_double2(1.0, 0.0);
-            const double2 Xp = cadd(evp, cmul(twp, odp));
-            // Ehat = -i g X  ->  (g X.y, -g X.x)
-            const double gm = fd.gmul[m], gp = fd.gmul[mp];
-            const double2 Em = make_double2(gm * Xm.y, -gm * Xm.x);
-            const double2 Ep = make_double2(gp * Xp.y, -gp * Xp.x);
-            // inverse pack: Ev'_m = (E_m + conj(E_{M-m}))/2, Od'_m = (E_m - conj(E_{M-m}))/2 * exp(+2 pi i m/N)
-            const double2 Epc = conj2(Ep);
-            const double2 ev2 = make_double2(0.5 * (Em.x + Epc.x), 0.5 * (Em.y + Epc.y));
-            const double2 od2 = cmul(make_double2(0.5 * (Em.x - Epc.x), 0.5 * (Em.y - Epc.y)), conj2(fd.tw[m]));
-            Y[bitrev(m, bits)] = make_double2(ev2.x - od2.y, ev2.y + od2.x);   // ev2 + i od2
-        }
-        __syncthreads();
-        fft_pow2(Y, M, nx, fd.tw, true);
-        const double inv = 1.0 / (double)M;
-        for (int n = threadIdx.x; n < M; n += FIELD_THREADS) {
-            const double2 y = Y[n];
-            Eout[2 * n] = y.x * inv;
-            Eout[2 * n + 1] = y.y * inv;
-        }
-    } else {
-        // direct DFT: Ehat_m for m = 1 .. (nx-1)/2, then E_i = (2/N) sum Re(Ehat_m e^{+i})
-        const int mmax = (nx - 1) / 2;
-        for (int m = 1 + threadIdx.x; m <= mmax; m += FIELD_THREADS) {
-            double rr = 0.0, ri = 0.0;
-            for (int i = 0; i < nx; ++i) {
-                const double2 w = fd.tw[(int)(((long long)m * i) % nx)];
-                rr += rho_s[i] * w.x;
-                ri += rho_s[i] * w.y;
-            }
-            const double g = fd.gmul[m];
-            work[m] = make_double2(g * ri, -g * rr);   // -i g (rr + i ri)
-        }
-        __syncthreads();
-        for (int i = threadIdx.x; i < nx; i += FIELD_THREADS) {
-            double acc = 0.0;
-            for (int m = 1; m <= mmax; ++m) {
-                const double2 w = fd.tw[(int)(((long long)m * i) % nx)];
-                // Re(E_m * conj(w))
-                acc += work[m].x * w.x + work[m].y * w.y;
-            }
-            Eout[i] = 2.0 * acc / (double)nx;
-        }
-    }
+    poisson_spectral(rho_s, work, Eout, nx, fd.pow2, fd.tw, fd.gmul);
     __syncthreads();
     // --- E in FP32, field energy, diagnostics row --------------------------
     double we = 0.0;
@@ -222,6 +234,56 @@ __global__ void __cluster_dims__(FIELD_CLUSTER, 1, 1) __launch_bounds__(FIELD_TH
         if (count_step) ctl->step += 1;
         if (sort_cond) cudaGraphSetConditional((cudaGraphConditionalHandle)sort_cond, any ? 1u : 0u);
     }
+}
+
+// stand-alone field solve: one block, rho and E in global memory
+__global__ void __launch_bounds__(FIELD_THREADS)
+    k_poisson(const double* __restrict__ rho, double* __restrict__ E, int nx, int pow2,
+              const double2* __restrict__ tw, const double* __restrict__ gmul)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    double* rho_s = reinterpret_cast<double*>(smem);
+    double2* work = reinterpret_cast<double2*>(smem + ((size_t)nx * 8 + 15) / 16 * 16);
+    for (int x = threadIdx.x; x < nx; x += FIELD_THREADS) rho_s[x] = rho[x];
+    __syncthreads();
+    poisson_spectral(rho_s, work, E, nx, pow2, tw, gmul);
+}
+
+size_t poisson_smem_bytes(int nx) { return ((size_t)nx * 8 + 15) / 16 * 16 + ((size_t)nx / 2 + 2) * 16; }
+
+void spectral_tables(int nx, double L, double cP, int softening, double2* tw, double* gm)
+{
+    const double dx = L / nx;
+    for (int k = 0; k < nx; ++k) {
+        const double a = 2.0 * M_PI * (double)k / (double)nx;
+        tw[k] = make_double2(cos(a), -sin(a));
+    }
+    for (int m = 0; m <= nx / 2; ++m) gm[m] = 0.0;
+    for (int m = 1; m <= nx / 2; ++m) {
+        if (2 * m == nx) continue;   // Nyquist mode carries no field
+        const double k = 2.0 * M_PI * (double)m / L;
+        double kappa, K2;
+        if (softening) {
+            const double y1 = k * dx, y2 = 0.5 * k * dx;
+            kappa = k * (sin(y1) / y1);
+            K2 = k * k * (sin(y2) / y2) * (sin(y2) / y2);
+        } else {
+            kappa = k;
+            K2 = k * k;
+        }
+        gm[m] = cP * kappa / K2;
+    }
+}
+
+cudaError_t launch_poisson(const double* rho, double* E, int nx, const double2* tw, const double* gmul,
+                           cudaStream_t st)
+{
+    const size_t smem = poisson_smem_bytes(nx);
+    cudaError_t e = cudaFuncSetAttribute(k_poisson, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e) return e;
+    const int pow2 = (nx >= 4 && (nx & (nx - 1)) == 0) ? 1 : 0;
+    k_poisson<<<1, FIELD_THREADS, smem, st>>>(rho, E, nx, pow2, tw, gmul);
+    return cudaGetLastError();
 }
 
 static size_t field_smem(const StepArgs& h)
