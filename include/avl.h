@@ -179,6 +179,26 @@ avl_status avl_get_stats(avl_ctx* ctx, int64_t* out);
 avl_status avl_field_solve(int32_t nx, double L, double poisson_const, int32_t softening,
                            const double* rho, double* E, void* cuda_stream);
 
+/* Allocation-free variant of avl_field_solve; the paper has no counterpart.
+ * For callers that cannot allocate device memory when they need a field
+ * solve: their GPU memory is fully reserved by another allocator (a caching
+ * allocator, a fixed budget), or they run a time-critical loop that must not
+ * pay for cudaMalloc/cudaFree, which synchronise the device.  The transform
+ * tables live in one file-scope device array of 328 KiB, sized for
+ * nx <= 16384, that every GPU loading the library holds until the process
+ * exits; the call allocates nothing (no cudaMalloc, cudaFree or allocating
+ * library routine).  Same arguments and result as avl_field_solve, but the
+ * work is only enqueued on cuda_stream (the call does not wait for it).
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress, with that device current); make that first call
+ * before any stream capture.  Every call on a device shares the array and
+ * rewrites all of it before reading it, so no state carries over between
+ * calls; calls that overlap on the GPU (other streams, other host threads)
+ * race on it.  Errors (message via avl_last_error(NULL)): AVL_EINVAL for nx
+ * outside [4, 16384] and the argument errors of avl_field_solve; AVL_ECUDA. */
+avl_status avl_field_solve_noalloc(int32_t nx, double L, double poisson_const, int32_t softening,
+                                   const double* rho, double* E, void* cuda_stream);
+
 /* Per-kernel timing (the paper's time breakdown, Sec. 3.2): advance nsteps
  * steps exactly as avl_step does, but launched kernel by kernel with CUDA
  * events recorded on the context stream around each kernel; writes the summed

@@ -25,7 +25,8 @@ STATUS_NAMES = {0: "AVL_OK", 1: "AVL_EINVAL", 2: "AVL_ENOMEM", 3: "AVL_ECUDA",
 
 EXPORTED = ["avl_create", "avl_destroy", "avl_last_error", "avl_init_markers", "avl_set_markers",
             "avl_marker_count", "avl_get_markers", "avl_step", "avl_get_f", "avl_get_rho",
-            "avl_get_E", "avl_get_diag", "avl_get_stats", "avl_field_solve", "avl_profile_steps",
+            "avl_get_E", "avl_get_diag", "avl_get_stats", "avl_field_solve", "avl_field_solve_noalloc",
+            "avl_profile_steps",
             "avl_synchronize"]
 
 
@@ -74,6 +75,7 @@ def _load():
         "avl_get_diag": (C.c_int, [vp, dp]),
         "avl_get_stats": (C.c_int, [vp, i64p]),
         "avl_field_solve": (C.c_int, [C.c_int32, C.c_double, C.c_double, C.c_int32, vp, vp, vp]),
+        "avl_field_solve_noalloc": (C.c_int, [C.c_int32, C.c_double, C.c_double, C.c_int32, vp, vp, vp]),
         "avl_profile_steps": (C.c_int, [vp, C.c_int32, dp, C.c_int32]),
         "avl_synchronize": (C.c_int, [vp]),
     }
@@ -101,6 +103,7 @@ avl_get_E = lib.avl_get_E
 avl_get_diag = lib.avl_get_diag
 avl_get_stats = lib.avl_get_stats
 avl_field_solve = lib.avl_field_solve
+avl_field_solve_noalloc = lib.avl_field_solve_noalloc
 avl_profile_steps = lib.avl_profile_steps
 avl_synchronize = lib.avl_synchronize
 

@@ -256,6 +256,9 @@ avl_status read_errors(avl_ctx* c)
 
 }  // namespace
 
+// error reporting for the context-free entry points of other translation units
+avl_status avl_noalloc_fail(avl_status st, const char* msg) { return fail(nullptr, st, msg); }
+
 extern "C" {
 
 const char* avl_last_error(const avl_ctx* ctx)
