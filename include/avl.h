@@ -161,10 +161,10 @@ avl_status avl_get_E(avl_ctx* ctx, double* E, int32_t on_device);
  * Returns AVL_ENUMERIC if any value is NaN or Inf. */
 avl_status avl_get_diag(avl_ctx* ctx, double* out);
 
-/* Counters (host buffer of 4 int64 per species): markers that deposited
- * through the out-of-window path in the last step, re-sorts so far,
- * markers whose velocity cloud leaves the velocity grid (last step, 0 if not
- * tracked), steps so far. */
+/* Counters (host buffer of 4 int64 per species): runs of markers that
+ * deposited through the out-of-window path in the last step, steps that
+ * re-sorted this species so far (every pushed step does), 0 (reserved),
+ * steps so far. */
 avl_status avl_get_stats(avl_ctx* ctx, int64_t* out);
 
 /* Stand-alone spectral Poisson solve (Sec. 3.1, Eq. 5 / Eq. 6a-c): E from
@@ -202,8 +202,9 @@ avl_status avl_field_solve_noalloc(int32_t nx, double L, double poisson_const, i
 /* Per-kernel timing (the paper's time breakdown, Sec. 3.2): advance nsteps
  * steps exactly as avl_step does, but launched kernel by kernel with CUDA
  * events recorded on the context stream around each kernel; writes the summed
- * milliseconds of each kernel class into ms[0..3] = {push+deposit, finalize
- * (f, moment, diagnostics), field (Poisson), re-sort}.  Blocks until done.
+ * milliseconds of each kernel class into ms[0..3] = {key count + slot scan,
+ * push + deposit + re-sorted write, finalize (f, moment, diagnostics), field
+ * (Poisson)}.  Blocks until done.
  * Errors: AVL_EINVAL (nkernels < 4 or ms NULL), AVL_ESTATE as avl_step. */
 avl_status avl_profile_steps(avl_ctx* ctx, int32_t nsteps, double* ms, int32_t nkernels);
 

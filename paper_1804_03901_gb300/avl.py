@@ -212,7 +212,7 @@ class Simulation:
 
     def profile_steps(self, n):
         """Milliseconds summed over n steps per kernel class:
-        [push+deposit, finalize, field, re-sort]."""
+        [key count + scan, push + deposit + re-sorted write, finalize, field]."""
         ms = np.zeros(4)
         self._chk(avl_profile_steps(self.ctx, n, ms.ctypes.data_as(C.POINTER(C.c_double)), 4))
         return ms

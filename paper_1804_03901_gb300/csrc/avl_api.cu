@@ -30,7 +30,8 @@ struct avl_ctx {
     avl_f0* d_f0 = nullptr;
     unsigned long long* d_bad = nullptr;
     std::vector<void*> allocs;          // context-lifetime allocations
-    void* mk_alloc[MAXS] = {};          // marker storage per species
+    std::vector<void*> layout[MAXS];    // marker storage, chunk tables and partial sums per species
+    int num_sms = 152;
     bool has_markers[MAXS] = {};
     void* scratch = nullptr;            // staging for caller-layout copies
     size_t scratch_bytes = 0;
@@ -104,46 +105,105 @@ int env_int(const char* name, int dflt)
 
 size_t prec_bytes(int prec) { return prec == AVL_FP32 ? 4 : 8; }
 
-// allocate (or re-allocate) the double-buffered marker storage of species s
-avl_status alloc_markers(avl_ctx* c, int s, long long n)
+void free_layout(avl_ctx* c, int s)
+{
+    for (void* p : c->layout[s]) cudaFree(p);
+    c->layout[s].clear();
+}
+
+// Chunk layout of species s for n markers: chunk size M (a multiple of 64,
+// about AVL_CHUNKS_PER_SM chunks per SM over all species), window rows Wmax
+// (the rows one chunk's keys span, plus the cloud-in-cell reach and one step
+// of drift on each side), marker storage (two buffers), chunk tables and
+// window partial sums.  Invalidates the step graph (grid sizes change).
+avl_status plan_layout(avl_ctx* c, int s, long long n)
 {
     SpDev& sp = c->h.sp[s];
-    if (c->mk_alloc[s] && sp.n == n) return AVL_OK;
-    if (c->mk_alloc[s]) {
-        AVL_CUDA(c, cudaStreamSynchronize(c->st));
-        cudaFree(c->mk_alloc[s]);
-        c->mk_alloc[s] = nullptr;
-    }
+    AVL_CUDA(c, cudaStreamSynchronize(c->st));
+    free_layout(c, s);
+    sp.nchunk = 0;
+    sp.n = 0;
+    const int per_sm = std::max(1, env_int("AVL_CHUNKS_PER_SM", 2));
+    const long long target = std::max(1, per_sm * c->num_sms / c->ns);
+    long long chunks = std::min<long long>(std::max<long long>(1, (n + 8191) / 8192), target);
+    long long M = (n + chunks - 1) / chunks;
+    M = (M + 63) / 64 * 64;
+    const int m_env = env_int("AVL_CHUNK_M", 0);
+    if (m_env > 0) M = (m_env + 63) / 64 * 64;
+    const int nch = (int)((n + M - 1) / M);
+    const double mpk = std::max(1.0, (double)n / sp.nvflat);
+    int span = (int)std::ceil((double)M / mpk) + 1;
+    int Wmax = span + 2 * HALO + 1;
+    Wmax = std::min(Wmax, sp.nvflat + 2 * HALO + 2);
+    const int w_env = env_int("AVL_WMAX", 0);
+    if (w_env > 0) Wmax = w_env;
+    sp.M = (int)M;
+    sp.Wmax = Wmax;
+    if (pd1_smem_bytes(sp, c->h.prec) > 220 * 1024)
+        return fail(c, AVL_EINVAL, "window of " + std::to_string(Wmax) + " velocity rows x " + std::to_string(sp.nx) +
+                                       " cells does not fit in shared memory (use fewer markers per chunk)");
+    int l = 0;
+    while ((1ll << l) < M) ++l;
+    sp.div_l = std::max(l, 1);
+    sp.div_m = (unsigned)(((1ull << (31 + sp.div_l)) + (unsigned long long)M - 1) / (unsigned long long)M);
+
     const size_t pb = prec_bytes(c->h.prec);
     const size_t nn = ((size_t)n + 63) / 64 * 64;
-    // per buffer: position (int cell or double xi), [offset], velocity components, value
     const int nvc = c->h.nvdim;
-    const size_t per = (c->h.prec == AVL_FP32) ? (4 + 4 + 4 * nvc + 4) : (8 + 8 * nvc + 8);
-    void* base = nullptr;
-    AVL_CUDA(c, cudaMalloc(&base, 2 * per * nn));
-    c->mk_alloc[s] = base;
-    unsigned char* p = static_cast<unsigned char*>(base);
-    for (int b = 0; b < 2; ++b) {
-        sp.mx[b] = p;
-        p += (c->h.prec == AVL_FP32 ? 4 : 8) * nn;
+    auto grab = [&](void** p, size_t bytes, bool zero) -> cudaError_t {
+        *p = nullptr;
+        cudaError_t e = cudaMalloc(p, std::max<size_t>(bytes, 16));
+        if (e) return e;
+        c->layout[s].push_back(*p);
+        return zero ? cudaMemsetAsync(*p, 0, std::max<size_t>(bytes, 16), c->st) : cudaSuccess;
+    };
+    cudaError_t e = cudaSuccess;
+    for (int b = 0; b < 2 && !e; ++b) {
+        if (!e) e = grab(&sp.mx[b], pb * nn, true);
         if (c->h.prec == AVL_FP32) {
-            sp.moff[b] = reinterpret_cast<float*>(p);
-            p += 4 * nn;
+            void* p = nullptr;
+            if (!e) e = grab(&p, 4 * nn, true);
+            sp.moff[b] = (float*)p;
         } else {
             sp.moff[b] = nullptr;
         }
         for (int d = 0; d < 3; ++d) {
-            if (d < nvc) {
-                sp.mv[b][d] = p;
-                p += pb * nn;
-            } else {
-                sp.mv[b][d] = nullptr;
-            }
+            sp.mv[b][d] = nullptr;
+            if (d < nvc && !e) e = grab(&sp.mv[b][d], pb * nn, true);
         }
-        sp.mf[b] = p;
-        p += pb * nn;
+        if (!e) e = grab(&sp.mf[b], pb * nn, true);
+        void* kb = nullptr;
+        if (!e) e = grab(&kb, (size_t)nch * 4, true);
+        sp.KB[b] = (int*)kb;
     }
+    void *pc = nullptr, *po = nullptr, *pk = nullptr, *pw = nullptr;
+    if (!e) e = grab(&pc, (size_t)nch * HIST_S * 4, true);
+    if (!e) e = grab(&po, (size_t)nch * HIST_S * 4, true);
+    if (!e) e = grab(&pk, (size_t)nch * 2 * 4, true);
+    if (!e) e = grab(&pw, (size_t)nch * 4, true);
+    if (!e) e = grab(&sp.partial, (size_t)nch * 16 * Wmax * sp.nx, true);
+    if (e) {
+        free_layout(c, s);
+        return cuda_fail(c, e, "cudaMalloc(markers)");
+    }
+    sp.cnt = (int*)pc;
+    sp.offs = (int*)po;
+    sp.kmm = (int*)pk;
+    sp.wrow0 = (int*)pw;
+    sp.nchunk = nch;
     sp.n = n;
+    // global chunk numbering over the species
+    int base = 0;
+    for (int q = 0; q < c->ns; ++q) {
+        c->h.sp[q].chunk_base = base;
+        base += c->h.sp[q].nchunk;
+    }
+    c->h.nchunk_total = base;
+    AVL_CUDA(c, configure_vhs1(c->h));
+    if (c->gexec) {
+        cudaGraphExecDestroy(c->gexec);
+        c->gexec = nullptr;
+    }
     return AVL_OK;
 }
 
@@ -158,76 +218,36 @@ avl_status set_cur_zero(avl_ctx* c, int s)
 // reconstruct every species with markers, then rho and E (no push)
 avl_status refresh(avl_ctx* c)
 {
+    AVL_CUDA(c, launch_count1(c->h, c->d_args, 0, c->st));
     AVL_CUDA(c, launch_pd1(c->h, c->d_args, 0, c->st));
     AVL_CUDA(c, launch_fin1(c->h, c->d_args, 1, c->st));
-    AVL_CUDA(c, launch_field(c->h, c->d_args, 0, 0, c->st));
-    AVL_CUDA(c, launch_sort1(c->h, c->d_args, c->st));
+    AVL_CUDA(c, launch_field(c->h, c->d_args, 0, c->st));
     return AVL_OK;
 }
 
-// one step without a graph: the re-sort kernels always run and return at
-// once unless the field kernel flagged a species
+// one step: keys of the current markers and their slots in the re-sorted
+// layout -> push + deposit + re-sorted write -> f, rho, diagnostics -> E
 avl_status enqueue_step(avl_ctx* c)
 {
+    AVL_CUDA(c, launch_count1(c->h, c->d_args, 1, c->st));
     AVL_CUDA(c, launch_pd1(c->h, c->d_args, 1, c->st));
     AVL_CUDA(c, launch_fin1(c->h, c->d_args, 0, c->st));
-    AVL_CUDA(c, launch_field(c->h, c->d_args, 1, 0, c->st));
-    AVL_CUDA(c, launch_sort1(c->h, c->d_args, c->st));
+    AVL_CUDA(c, launch_field(c->h, c->d_args, 1, c->st));
     return AVL_OK;
 }
 
-// one step as a graph: push+deposit -> finalize -> field, then an IF node
-// whose body (the re-sort) runs only when the field kernel sets the
-// condition from the device
 avl_status build_graph(avl_ctx* c)
 {
     if (c->gexec) return AVL_OK;
     cudaGraph_t g = nullptr;
-    AVL_CUDA(c, cudaGraphCreate(&g, 0));
-    cudaGraphConditionalHandle cond = 0;
-    cudaError_t e = cudaGraphConditionalHandleCreate(&cond, g, 0, cudaGraphCondAssignDefault);
-    if (!e) e = cudaStreamBeginCaptureToGraph(c->st, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
-    if (e) {
-        cudaGraphDestroy(g);
-        return cuda_fail(c, e, "graph capture setup");
+    AVL_CUDA(c, cudaStreamBeginCapture(c->st, cudaStreamCaptureModeThreadLocal));
+    avl_status st = enqueue_step(c);
+    cudaError_t e = cudaStreamEndCapture(c->st, &g);
+    if (st != AVL_OK) {
+        if (g) cudaGraphDestroy(g);
+        return st;
     }
-    cudaError_t el = launch_pd1(c->h, c->d_args, 1, c->st);
-    if (!el) el = launch_fin1(c->h, c->d_args, 0, c->st);
-    if (!el) el = launch_field(c->h, c->d_args, 1, (unsigned long long)cond, c->st);
-    cudaGraphNode_t cnode = nullptr;
-    cudaGraph_t body = nullptr;
-    if (!el) {
-        cudaStreamCaptureStatus cs;
-        cudaGraph_t capg = nullptr;
-        const cudaGraphNode_t* deps = nullptr;
-        size_t ndeps = 0;
-        el = cudaStreamGetCaptureInfo(c->st, &cs, nullptr, &capg, &deps, nullptr, &ndeps);
-        if (!el) {
-            cudaGraphNodeParams cp = {};
-            cp.type = cudaGraphNodeTypeConditional;
-            cp.conditional.handle = cond;
-            cp.conditional.type = cudaGraphCondTypeIf;
-            cp.conditional.size = 1;
-            el = cudaGraphAddNode(&cnode, capg, deps, nullptr, ndeps, &cp);
-            if (!el) body = cp.conditional.phGraph_out[0];
-        }
-        if (!el) el = cudaStreamUpdateCaptureDependencies(c->st, &cnode, nullptr, 1, cudaStreamSetCaptureDependencies);
-    }
-    cudaGraph_t got = nullptr;
-    e = cudaStreamEndCapture(c->st, &got);
-    if (el || e) {
-        cudaGraphDestroy(g);
-        return cuda_fail(c, el ? el : e, "graph capture of the step");
-    }
-    e = cudaStreamBeginCaptureToGraph(c->st, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
-    if (!e) {
-        el = launch_sort1(c->h, c->d_args, c->st);
-        e = cudaStreamEndCapture(c->st, &got);
-    }
-    if (el || e) {
-        cudaGraphDestroy(g);
-        return cuda_fail(c, el ? el : e, "graph capture of the re-sort body");
-    }
+    if (e != cudaSuccess) return cuda_fail(c, e, "cudaStreamEndCapture");
     e = cudaGraphInstantiate(&c->gexec, g, 0);
     cudaGraphDestroy(g);
     if (e != cudaSuccess) {
@@ -358,9 +378,11 @@ avl_status avl_create(const avl_domain* dom, const avl_species* spec, int32_t ns
         return bail(AVL_ECUDA);
     }
 
-    // --- per species binning and grids ------------------------------------
-    const int hw = 3, hd = 1;
-    int bin_base = 0, fin_base = 0;
+    // --- per species grids and tables ------------------------------------
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device) == cudaSuccess && sms > 0)
+        c->num_sms = sms;
+    int fin_base = 0;
     for (int s = 0; s < nspecies; ++s) {
         const avl_species& p = spec[s];
         SpDev& sp = h.sp[s];
@@ -381,31 +403,13 @@ avl_status avl_create(const avl_domain* dom, const avl_species* spec, int32_t ns
         }
         sp.qm_dt = sp.qm * dom->dt;
         sp.dt_dx = dom->dt / dx;
-        // window: W rows of nx cells, 16 bytes per cell, within a shared-memory budget
-        const int budget_kb = env_int("AVL_WINDOW_KB", 72);
-        size_t budget = (size_t)budget_kb * 1024;
-        budget = std::max(budget, (size_t)16 * nx * (2 * hw + 1));
-        if (budget > 200 * 1024) {
-            c->err = "nx too large for the 1d1v shared-memory window (nx <= 1828)";
-            return bail(AVL_EINVAL);
-        }
-        const int wmax = (int)(budget / (16 * (size_t)nx));
-        int tv = std::max(1, wmax - 2 * hw);
-        const int tv_env = env_int("AVL_TV", 0);
-        if (tv_env > 0) tv = tv_env;
-        tv = std::min(tv, p.nv[0]);
-        sp.tv = tv;
-        sp.hw = hw;
-        sp.hd = hd;
-        sp.W = tv + 2 * hw;
-        sp.nbins = (p.nv[0] + tv - 1) / tv;
-        sp.bin_base = bin_base;
-        bin_base += sp.nbins;
+        sp.nchunk = 0;
+        sp.n = 0;
         // finalize blocks: FIN_XB columns x rq rows, about 4 blocks per SM in total
         sp.nxb = (nx + FIN_XB - 1) / FIN_XB;
-        int nrq = std::max(1, (608 + nspecies * sp.nxb - 1) / (nspecies * sp.nxb));
-        const int rq_env = env_int("AVL_RQ", 0);
+        const int nrq = std::max(1, (4 * c->num_sms + nspecies * sp.nxb - 1) / (nspecies * sp.nxb));
         int rq = std::max(8, (p.nv[0] + nrq - 1) / nrq);
+        const int rq_env = env_int("AVL_RQ", 0);
         if (rq_env > 0) rq = rq_env;
         rq = std::min(rq, p.nv[0]);
         sp.rq = rq;
@@ -414,30 +418,28 @@ avl_status avl_create(const avl_domain* dom, const avl_species* spec, int32_t ns
         sp.fin_base = fin_base;
         fin_base += sp.nfin;
         const size_t cells = (size_t)nx * sp.nvflat;
-        void *pf, *pn, *pp, *po, *pr, *pd, *pb0, *pb1, *pc, *ph;
+        const size_t nvk = (size_t)sp.nvflat;
+        void *pf, *pn, *po, *pr, *pd, *p1, *p2, *p3, *p4, *p5;
         if ((e = dalloc(c, &pf, cells * pb, true)) || (e = dalloc(c, &pn, cells * pb, true)) ||
-            (e = dalloc(c, &pp, (size_t)sp.nbins * 16 * sp.W * nx, true)) ||
             (e = dalloc(c, &po, 2 * cells * 8, true)) || (e = dalloc(c, &pr, (size_t)sp.nrq * nx * 8, true)) ||
-            (e = dalloc(c, &pd, (size_t)sp.nfin * 4 * 8, true)) ||
-            (e = dalloc(c, &pb0, (size_t)(sp.nbins + 1) * 4, true)) ||
-            (e = dalloc(c, &pb1, (size_t)(sp.nbins + 1) * 4, true)) ||
-            (e = dalloc(c, &pc, (size_t)sp.nbins * 4, true)) || (e = dalloc(c, &ph, (size_t)sp.nbins * 4, true))) {
+            (e = dalloc(c, &pd, (size_t)sp.nfin * 4 * 8, true)) || (e = dalloc(c, &p1, nvk * 4, true)) ||
+            (e = dalloc(c, &p2, nvk * 4, true)) || (e = dalloc(c, &p3, (nvk + 1) * 4, true)) ||
+            (e = dalloc(c, &p4, nvk * 4, true)) || (e = dalloc(c, &p5, nvk * 4, true))) {
             cuda_fail(c, e, "cudaMalloc(species)");
             return bail(AVL_ENOMEM);
         }
         sp.fgrid = pf;
         sp.ngrid = pn;
-        sp.partial = pp;
         sp.ovf = (double*)po;
         sp.rho_part = (double*)pr;
         sp.dpart = (double*)pd;
-        sp.bin_start[0] = (int*)pb0;
-        sp.bin_start[1] = (int*)pb1;
-        sp.cursor = (int*)pc;
-        sp.hist = (int*)ph;
-        sp.n = 0;
+        sp.far_cnt = (int*)p1;
+        sp.far_cur = (int*)p2;
+        sp.base_new = (int*)p3;
+        sp.rc_lo = (int*)p4;
+        sp.rc_hi = (int*)p5;
     }
-    h.nbins_total = bin_base;
+    h.nchunk_total = 0;
     h.nfin_total = fin_base;
 
     void *pa, *pc, *pf0, *pbad;
@@ -466,8 +468,7 @@ void avl_destroy(avl_ctx* c)
     if (c->st) cudaStreamSynchronize(c->st);
     if (c->gexec) cudaGraphExecDestroy(c->gexec);
     for (void* p : c->allocs) cudaFree(p);
-    for (int s = 0; s < MAXS; ++s)
-        if (c->mk_alloc[s]) cudaFree(c->mk_alloc[s]);
+    for (int s = 0; s < MAXS; ++s) free_layout(c, s);
     if (c->scratch) cudaFree(c->scratch);
     if (c->own_stream && c->st) cudaStreamDestroy(c->st);
     delete c;
@@ -490,20 +491,14 @@ avl_status avl_init_markers(avl_ctx* c, int32_t s, const int32_t lattice[4], con
     const long long ppc = (long long)lattice[0] * lattice[1];
     const long long n = (long long)sp.nx * sp.nvflat * ppc;
     if (n >= (1ll << 31) - 1024) return fail(c, AVL_EINVAL, "too many markers for one species (2^31)");
-    if ((st = alloc_markers(c, s, n))) return st;
-    // bin ranges of the lattice: bin b holds rows [b tv, min(nv, (b+1) tv))
-    std::vector<int> bs(sp.nbins + 1);
-    for (int b = 0; b <= sp.nbins; ++b)
-        bs[b] = (int)((long long)std::min(sp.nvflat, b * sp.tv) * sp.nx * ppc);
+    if ((st = plan_layout(c, s, n))) return st;
     if ((st = set_cur_zero(c, s))) return st;
-    AVL_CUDA(c, cudaMemcpyAsync(sp.bin_start[0], bs.data(), bs.size() * 4, cudaMemcpyHostToDevice, c->st));
     AVL_CUDA(c, cudaMemcpyAsync(c->d_f0, f0, sizeof(avl_f0), cudaMemcpyHostToDevice, c->st));
     if ((st = upload_args(c))) return st;
     AVL_CUDA(c, launch_init1(c->h, c->d_args, s, lattice, c->d_f0, seed, jitter, c->st));
     c->has_markers[s] = true;
     if ((st = refresh(c))) return st;
-    AVL_CUDA(c, cudaStreamSynchronize(c->st));
-    return AVL_OK;
+    return read_errors(c);
 }
 
 avl_status avl_set_markers(avl_ctx* c, int32_t s, int64_t n, const double* x, const double* v, const double* f,
@@ -525,7 +520,7 @@ avl_status avl_set_markers(avl_ctx* c, int32_t s, int64_t n, const double* x, co
         dv_ = base + n;
         df_ = base + n * (1 + nvd);
     }
-    if ((st = alloc_markers(c, s, n))) return st;
+    if ((st = plan_layout(c, s, n))) return st;
     if ((st = set_cur_zero(c, s))) return st;
     if ((st = upload_args(c))) return st;
     AVL_CUDA(c, cudaMemsetAsync(c->d_bad, 0, 8, c->st));
@@ -539,8 +534,7 @@ avl_status avl_set_markers(avl_ctx* c, int32_t s, int64_t n, const double* x, co
     }
     c->has_markers[s] = true;
     if ((st = refresh(c))) return st;
-    AVL_CUDA(c, cudaStreamSynchronize(c->st));
-    return AVL_OK;
+    return read_errors(c);
 }
 
 avl_status avl_marker_count(avl_ctx* c, int32_t s, int64_t* n)
@@ -658,7 +652,7 @@ avl_status avl_get_stats(avl_ctx* c, int64_t* out)
     AVL_CUDA(c, cudaStreamSynchronize(c->st));
     for (int s = 0; s < c->ns; ++s) {
         out[4 * s + 0] = (int64_t)h.ovf_last[s];
-        out[4 * s + 1] = (int64_t)h.nsort[s];
+        out[4 * s + 1] = c->h.sp[s].mobile ? (int64_t)h.step : 0;
         out[4 * s + 2] = 0;
         out[4 * s + 3] = (int64_t)h.step;
     }
@@ -678,13 +672,13 @@ avl_status avl_profile_steps(avl_ctx* c, int32_t nsteps, double* ms, int32_t nke
     avl_status st = AVL_OK;
     for (int i = 0; i < nsteps && st == AVL_OK; ++i) {
         cudaError_t e = cudaEventRecord(ev[0], c->st);
-        if (!e) e = launch_pd1(c->h, c->d_args, 1, c->st);
+        if (!e) e = launch_count1(c->h, c->d_args, 1, c->st);
         if (!e) e = cudaEventRecord(ev[1], c->st);
-        if (!e) e = launch_fin1(c->h, c->d_args, 0, c->st);
+        if (!e) e = launch_pd1(c->h, c->d_args, 1, c->st);
         if (!e) e = cudaEventRecord(ev[2], c->st);
-        if (!e) e = launch_field(c->h, c->d_args, 1, 0, c->st);
+        if (!e) e = launch_fin1(c->h, c->d_args, 0, c->st);
         if (!e) e = cudaEventRecord(ev[3], c->st);
-        if (!e) e = launch_sort1(c->h, c->d_args, c->st);
+        if (!e) e = launch_field(c->h, c->d_args, 1, c->st);
         if (!e) e = cudaEventRecord(ev[4], c->st);
         if (!e) e = cudaEventSynchronize(ev[4]);
         for (int k = 0; k < 4 && !e; ++k) {

@@ -2,15 +2,20 @@
 // host layer of the GB300 Vlasov-Hybrid library.
 //
 // HBM layout of one species (1d1v):
-//   markers, double-buffered for re-sorting, structure of arrays:
-//     FP32: cell int32[n], off f32[n] (position in cells = cell + off,
-//           off in [0,1)), dv f32[n] (velocity relative to the reference
-//           velocity of the marker's bin), f f32[n]
-//     FP64: xi f64[n] (position in cells), dv f64[n], f f64[n]
-//   bins: markers are grouped by velocity row block ("bin" = TV rows of the
-//     velocity grid); bin_start[nbins+1] gives each bin's marker range.
-//   grids are stored [v][x] (x fastest): f, n (= denominator of Eq. 4).
-//   partial sums of each bin's window: [nbins][planes][W][nx].
+//   markers, double-buffered (every step writes the re-sorted markers into
+//   the other buffer), structure of arrays:
+//     FP32: cell int32[n], off f32[n] (position in cells = cell + off, off in
+//           [0,1)), dv f32[n], f f32[n]                      16 B per marker
+//     FP64: xi f64[n] (position in cells), dv f64[n], f f64[n]   24 B
+//   Markers are sorted by their key, the lower velocity row of their
+//   cloud-in-cell footprint (the "dual row", clamped to [0, nv)).  The marker
+//   array is cut into chunks of M markers (chunk c = [c M, (c+1) M)); one CTA
+//   owns one chunk.  dv is the velocity relative to the chunk's reference
+//   row KB[c] (reference velocity vmin + KB[c] dv), so that FP32 keeps
+//   velocity resolution at every |v|.
+//   Grids are stored [v][x] (x fastest): f and n (denominator of Eq. 4).
+//   Window partial sums of chunk c: [nchunk][planes][Wmax][nx] covering the
+//   velocity rows [wrow0[c], wrow0[c] + Wmax).
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -20,13 +25,16 @@
 namespace avl {
 
 constexpr int MAXS = AVL_MAX_SPECIES;
-constexpr int PD_THREADS = 256;     // push + deposit block
-constexpr int PD_UNROLL = 4;        // markers in flight per thread
+constexpr int PD_THREADS = 512;     // push + deposit block
+constexpr int MPT = 4;              // consecutive markers per thread and iteration
+constexpr int CNT_THREADS = 512;    // key-count block
+constexpr int HIST_S = 64;          // keys per chunk histogram
+constexpr int HIST_R = 16;          // of which below the chunk's reference key
+constexpr int HALO = 2;             // window rows beyond the chunk's keys (one step of drift)
 constexpr int FIN_THREADS = 256;    // finalize block
 constexpr int FIN_XB = 16;          // x columns per finalize block
 constexpr int FIELD_THREADS = 512;  // Poisson cluster block
 constexpr int FIELD_CLUSTER = 8;    // CTAs in the Poisson cluster
-constexpr int SORT_THREADS = 256;
 constexpr long long WAIT_LIMIT = 1ll << 22;   // bounded mbarrier polls
 
 // device-side error bits (Ctl::err)
@@ -40,30 +48,38 @@ struct SpDev {
     double vmin[3], dv[3], inv_dv[3];
     double dx;
     double qm_dt, dt_dx;       // (q/m) dt, dt/dx
-    // binning by velocity row blocks (1d1v)
-    int tv;                    // rows per bin
-    int hw;                    // window rows beyond the bin on each side (CIC + drift halo)
-    int hd;                    // rows a marker may wander out of its bin before a re-sort
-    int W;                     // window rows = tv + 2 hw
-    int nbins;
-    int bin_base;              // first global bin index of this species
-    // finalize blocks: FIN_XB x-columns times a group of rq velocity rows
-    int nxb, rq, nrq, nfin, fin_base;
+    // chunks
+    int M;                     // markers per chunk (multiple of 64)
+    int nchunk;                // chunks (0: no markers)
+    int chunk_base;            // first global chunk index of this species
+    int Wmax;                  // window rows
+    unsigned div_m;            // magic multiplier and shift for slot / M
+    int div_l;
     // markers
     void* mx[2];               // FP32: int cell; FP64: double xi
     float* moff[2];            // FP32 only
-    void* mv[2][3];            // velocity components (vx bin-relative)
+    void* mv[2][3];            // velocity components (vx chunk-relative)
     void* mf[2];
-    int* bin_start[2];
-    int* cursor;
-    int* hist;
+    int* KB[2];                // [nchunk] reference key of each chunk, per buffer
+    // re-sort tables
+    int* cnt;                  // [nchunk][HIST_S] keys of the current state, by chunk
+    int* offs;                 // [nchunk][HIST_S] first slot in the new layout
+    int* kmm;                  // [nchunk][2] min / max key of the current state
+    int* far_cnt;              // [nv] markers whose key is outside their chunk's histogram
+    int* far_cur;              // [nv] slot cursors for those
+    int* base_new;             // [nv + 1] first slot of each key in the new layout
+    int* wrow0;                // [nchunk] first window row of each chunk
+    int* rc_lo;                // [nv] first chunk whose window covers the row
+    int* rc_hi;                // [nv] last such chunk
     // grids and scratch
     void* fgrid;               // [nvflat][nx] (storage precision)
     void* ngrid;
-    void* partial;             // [nbins][planes][W][nx]
+    void* partial;             // [nchunk][planes][Wmax][nx]
     double* ovf;               // [2][nvflat][nx] FP64 overflow num/den
     double* rho_part;          // [nrq][nx] charge of this species per row group
     double* dpart;             // [nfin][4] : N, Wkin, S, -
+    // finalize blocks: FIN_XB x-columns times a group of rq velocity rows
+    int nxb, rq, nrq, nfin, fin_base;
 };
 
 struct FieldDev {
@@ -78,32 +94,33 @@ struct FieldDev {
 };
 
 struct Ctl {
-    int cur[MAXS];
-    int sort_flag[MAXS];
-    unsigned long long dirty[MAXS];
+    int cur[MAXS];             // buffer holding the current markers
     unsigned long long ovf_count[MAXS];
     unsigned long long ovf_last[MAXS];
-    unsigned long long nsort[MAXS];
-    unsigned int scatter_done;
-    int any_sort;
+    unsigned long long far_last[MAXS];
+    unsigned int count_done;   // CTAs of the count kernel finished (the last one scans)
+    int pad;
     long long step;
     int err;
 };
 
 struct StepArgs {
     int ns, prec, nvdim;
-    int nbins_total, nfin_total;
+    int nchunk_total, nfin_total;
     SpDev sp[MAXS];
     FieldDev fd;
     Ctl* ctl;
 };
 
-// kernel launchers (defined in the .cu files; all enqueue on `st`)
-cudaError_t launch_pd1(const StepArgs& h, const StepArgs* d, int push, cudaStream_t st);
+// kernel launchers (defined in the .cu files; all enqueue on `st`).
+// mode: 0 = refresh (every species with markers, no push, no re-sort)
+//       1 = step (mobile species: push + deposit + re-sort)
+cudaError_t launch_count1(const StepArgs& h, const StepArgs* d, int mode, cudaStream_t st);
+cudaError_t launch_pd1(const StepArgs& h, const StepArgs* d, int mode, cudaStream_t st);
 cudaError_t launch_fin1(const StepArgs& h, const StepArgs* d, int all_species, cudaStream_t st);
-cudaError_t launch_field(const StepArgs& h, const StepArgs* d, int count_step,
-                         unsigned long long sort_cond, cudaStream_t st);
-cudaError_t launch_sort1(const StepArgs& h, const StepArgs* d, cudaStream_t st);
+cudaError_t launch_field(const StepArgs& h, const StepArgs* d, int count_step, cudaStream_t st);
+// markers from the lattice generator or from caller arrays into the sorted
+// layout of buffer 0 of species s
 cudaError_t launch_init1(const StepArgs& h, const StepArgs* d, int s, const int lattice[4],
                          const avl_f0* f0_dev, unsigned long long seed, double jitter,
                          cudaStream_t st);

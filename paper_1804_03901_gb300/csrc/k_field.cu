@@ -132,7 +132,7 @@ __device__ void poisson_spectral(double* rho_s, double2* work, double* Eout, int
 }
 
 __global__ void __cluster_dims__(FIELD_CLUSTER, 1, 1) __launch_bounds__(FIELD_THREADS)
-    k_field(const StepArgs* __restrict__ A, int count_step, unsigned long long sort_cond)
+    k_field(const StepArgs* __restrict__ A, int count_step)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     cg::cluster_group cluster = cg::this_cluster();
@@ -220,19 +220,13 @@ __global__ void __cluster_dims__(FIELD_CLUSTER, 1, 1) __launch_bounds__(FIELD_TH
         fd.diag[2] = WE + wk_tot;
         Ctl* ctl = A->ctl;
         if (bad) ctl->err |= ERR_NUMERIC;
-        // re-sort decision for the next step
-        int any = 0;
+        // the re-sorted markers written by this step become current
         for (int s = 0; s < ns; ++s) {
-            const int flag = (A->sp[s].mobile && ctl->dirty[s] > 0) ? 1 : 0;
-            ctl->sort_flag[s] = flag;
-            any |= flag;
-            ctl->dirty[s] = 0;
+            if (count_step && A->sp[s].mobile && A->sp[s].nchunk > 0) ctl->cur[s] = 1 - ctl->cur[s];
             ctl->ovf_last[s] = ctl->ovf_count[s];
             ctl->ovf_count[s] = 0;
         }
-        ctl->any_sort = any;
         if (count_step) ctl->step += 1;
-        if (sort_cond) cudaGraphSetConditional((cudaGraphConditionalHandle)sort_cond, any ? 1u : 0u);
     }
 }
 
@@ -297,10 +291,9 @@ cudaError_t configure_field(const StepArgs& h)
     return cudaFuncSetAttribute(k_field, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)field_smem(h));
 }
 
-cudaError_t launch_field(const StepArgs& h, const StepArgs* d, int count_step, unsigned long long sort_cond,
-                         cudaStream_t st)
+cudaError_t launch_field(const StepArgs& h, const StepArgs* d, int count_step, cudaStream_t st)
 {
-    k_field<<<FIELD_CLUSTER, FIELD_THREADS, field_smem(h), st>>>(d, count_step, sort_cond);
+    k_field<<<FIELD_CLUSTER, FIELD_THREADS, field_smem(h), st>>>(d, count_step);
     return cudaGetLastError();
 }
 

@@ -1,11 +1,18 @@
-// k_vhs1.cu -- 1d1v kernels of the Vlasov-Hybrid time step (Fig. 2):
-//   k_pd1      gather E + push (Sec. 2) fused with the VHS deposit of the
+// k_vhs1.cu -- 1d1v kernels of the Vlasov-Hybrid time step (Fig. 2).
+//
+// One step of one species runs as
+//   k_count1   keys of the current markers per chunk; the last CTA scans the
+//              counts into the slots of the re-sorted layout and places the
+//              deposit window of every chunk
+//   k_pd1      per chunk: gather E + push (Sec. 2), VHS deposit of the
 //              numerator and denominator of Eq. 4 into a shared-memory window
+//              (runs of markers with the same cloud-in-cell footprint are
+//              summed in registers first), and the write of every pushed
+//              marker into its slot of the re-sorted layout
 //   k_fin1     f = num / den (Eq. 4), velocity moment (Eq. 14), per-block
 //              diagnostics (Sec. 3.4.1)
-//   k_sort*    re-binning of the markers by velocity row block
-//   k_init1    lattice markers weighted to f0 (Sec. 2, Sec. 3.1)
-//   k_set1 / k_get1 / k_getf  conversion to and from the caller's FP64 layout
+// Marker creation (lattice weighted to f0, Sec. 2 / Sec. 3.1) and caller
+// markers go through the same count / scan / scatter with another source.
 #include <math.h>
 
 #include <algorithm>
@@ -14,6 +21,41 @@
 #include "ptx.cuh"
 
 namespace avl {
+
+// ---------------------------------------------------------------------------
+// small helpers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
+
+// n / M for 0 <= n < 2^31 by a multiply-high (magic m, shift l from the host)
+__device__ __forceinline__ int chunk_of(int n, unsigned m, int l)
+{
+    return (int)(__umulhi((unsigned)n, m) >> (l - 1));
+}
+
+// periodic neighbours of a lower CIC cell i0 in [-1, nx-1]; clamped so that a
+// non-finite position can never index outside the grid
+__device__ __forceinline__ void wrap_pair(int i0, int nx, int& ia, int& ib)
+{
+    ia = i0 < 0 ? i0 + nx : i0;
+    ib = (i0 + 1 >= nx) ? i0 + 1 - nx : i0 + 1;
+    ia = min(max(ia, 0), nx - 1);
+    ib = min(max(ib, 0), nx - 1);
+}
+
+__device__ __forceinline__ int species_of_chunk(const StepArgs* A, int g)
+{
+    int s = 0;
+    while (s + 1 < A->ns && g >= A->sp[s + 1].chunk_base) ++s;
+    return s;
+}
+
+__device__ __forceinline__ int species_of_fin(const StepArgs* A, int g)
+{
+    int s = 0;
+    while (s + 1 < A->ns && g >= A->sp[s + 1].fin_base) ++s;
+    return s;
+}
 
 // ---------------------------------------------------------------------------
 // marker storage access
@@ -50,7 +92,7 @@ struct Pos<float> {
     __device__ __forceinline__ void drift(float disp, int nx)
     {
         o += disp;
-        float fo = floorf(o);
+        const float fo = floorf(o);
         c += static_cast<int>(fo);
         o -= fo;
         if (o >= 1.0f) {
@@ -62,6 +104,7 @@ struct Pos<float> {
             if (c < 0) c += nx;
         }
     }
+    __device__ __forceinline__ double cells() const { return (double)c + (double)o; }
 };
 
 // FP64: position in cells, xi in [0, nx)
@@ -78,15 +121,15 @@ struct Pos<double> {
     }
     __device__ __forceinline__ void cic(int& i0, double& w) const
     {
-        double u = xi - 0.5;
-        double fl = floor(u);
+        const double u = xi - 0.5;
+        const double fl = floor(u);
         i0 = static_cast<int>(fl);
         w = u - fl;
     }
     __device__ __forceinline__ void drift(double disp, int nx)
     {
         double x = xi + disp;
-        double n = static_cast<double>(nx);
+        const double n = static_cast<double>(nx);
         if (x < 0.0 || x >= n) {
             x = fmod(x, n);
             if (x < 0.0) x += n;
@@ -94,102 +137,584 @@ struct Pos<double> {
         }
         xi = x;
     }
+    __device__ __forceinline__ double cells() const { return xi; }
 };
 
-// shared-memory window accumulation of (alpha f, alpha)
-__device__ __forceinline__ void acc_comp(float* hi, float* lo, float x)
-{
-    // compensated add: the atomic returns the old value, TwoSum recovers the
-    // rounding error of old + x exactly; errors accumulate in the lo plane
-    float old = atomicAdd(hi, x);
-    float s = __fadd_rn(old, x);
-    float bp = __fsub_rn(s, old);
-    float err = __fadd_rn(__fsub_rn(old, __fsub_rn(s, bp)), __fsub_rn(x, bp));
-    if (err != 0.0f) atomicAdd(lo, err);
-}
-
+// position from a value in cells (FP64) given by a caller or the generator
 template <typename T>
-struct Window;
-
-template <>
-struct Window<float> {
-    // planes: num_hi, num_lo, den_hi, den_lo
-    float* p;
-    int plane;
-    __device__ __forceinline__ void add(int cell, float a, float af)
-    {
-        acc_comp(p + cell, p + plane + cell, af);
-        acc_comp(p + 2 * plane + cell, p + 3 * plane + cell, a);
-    }
-};
-
-template <>
-struct Window<double> {
-    double* p;
-    int plane;
-    __device__ __forceinline__ void add(int cell, double a, double af)
-    {
-        atomicAdd(p + cell, af);
-        atomicAdd(p + plane + cell, a);
-    }
-};
-
-// periodic neighbours of a lower CIC cell i0 in [-1, nx-1]; clamped so that a
-// non-finite position can never index outside the grid
-__device__ __forceinline__ void wrap_pair(int i0, int nx, int& ia, int& ib)
+__device__ __forceinline__ Pos<T> pos_from_cells(double xi, int nx)
 {
-    ia = i0 < 0 ? i0 + nx : i0;
-    ib = (i0 + 1 >= nx) ? i0 + 1 - nx : i0 + 1;
-    ia = min(max(ia, 0), nx - 1);
-    ib = min(max(ib, 0), nx - 1);
+    Pos<T> p;
+    if constexpr (sizeof(T) == 4) {
+        const double c = floor(xi);
+        int ci = (int)c;
+        const double o = xi - c;
+        if (ci >= nx) ci -= nx;
+        if (ci < 0) ci += nx;
+        p.c = min(max(ci, 0), nx - 1);
+        p.o = (float)o;
+        if (p.o >= 1.0f) {
+            p.o = 0.0f;
+            p.c = (p.c + 1) % nx;
+        }
+    } else {
+        p.xi = xi < nx ? xi : xi - nx;
+    }
+    return p;
 }
 
-__device__ __forceinline__ int floor_div(int a, int b) { return a >= 0 ? a / b : -((-a + b - 1) / b); }
-__device__ __forceinline__ int ceil_div(int a, int b) { return a >= 0 ? (a + b - 1) / b : -((-a) / b); }
-
-__device__ __forceinline__ int species_of(const StepArgs* A, int g, bool)
+// key = lower velocity row of the cloud-in-cell footprint ("dual row"),
+// clamped to [0, nv).  Explicit fused multiply-add so that every kernel
+// computes bit-identical keys.
+__device__ __forceinline__ int key_rel(float dv, int kb, float inv_dv, int nv)
 {
-    int s = 0;
-    while (s + 1 < A->ns && g >= A->sp[s + 1].bin_base) ++s;
-    return s;
+    return clampi(kb + (int)floorf(__fmaf_rn(dv, inv_dv, -0.5f)), 0, nv - 1);
+}
+__device__ __forceinline__ int key_rel(double dv, int kb, double inv_dv, int nv)
+{
+    return clampi(kb + (int)floor(__fma_rn(dv, inv_dv, -0.5)), 0, nv - 1);
+}
+__device__ __forceinline__ int key_abs(double v, double vmin, double inv_dv, int nv)
+{
+    const double t = __fma_rn(__dsub_rn(v, vmin), inv_dv, -0.5);
+    if (!(t > -4.0e9 && t < 4.0e9)) return t > 0 ? nv - 1 : 0;
+    return clampi((int)floor(t), 0, nv - 1);
+}
+
+// relative key code used by the histograms and slot assignment:
+// [0, HIST_S) inside the chunk's histogram, HIST_S + key for far keys
+__device__ __forceinline__ int rel_code(int key, int kbase)
+{
+    const int r = key - kbase;
+    return (r >= 0 && r < HIST_S) ? r : HIST_S + key;
+}
+
+// MPT consecutive values from an aligned address (marker arrays are padded to
+// a multiple of 64 entries, so a group starting below n is in bounds)
+__device__ __forceinline__ void loadg(const float* p, float (&o)[4])
+{
+    const float4 a = *reinterpret_cast<const float4*>(p);
+    o[0] = a.x; o[1] = a.y; o[2] = a.z; o[3] = a.w;
+}
+__device__ __forceinline__ void loadg(const int* p, int (&o)[4])
+{
+    const int4 a = *reinterpret_cast<const int4*>(p);
+    o[0] = a.x; o[1] = a.y; o[2] = a.z; o[3] = a.w;
+}
+__device__ __forceinline__ void loadg(const double* p, double (&o)[4])
+{
+    const double2 a = reinterpret_cast<const double2*>(p)[0], b = reinterpret_cast<const double2*>(p)[1];
+    o[0] = a.x; o[1] = a.y; o[2] = b.x; o[3] = b.y;
+}
+__device__ __forceinline__ void storeg(float* p, const float (&o)[4])
+{
+    *reinterpret_cast<float4*>(p) = make_float4(o[0], o[1], o[2], o[3]);
+}
+__device__ __forceinline__ void storeg(int* p, const int (&o)[4])
+{
+    *reinterpret_cast<int4*>(p) = make_int4(o[0], o[1], o[2], o[3]);
+}
+__device__ __forceinline__ void storeg(double* p, const double (&o)[4])
+{
+    reinterpret_cast<double2*>(p)[0] = make_double2(o[0], o[1]);
+    reinterpret_cast<double2*>(p)[1] = make_double2(o[2], o[3]);
+}
+// eight consecutive values (count kernel)
+__device__ __forceinline__ void load8(const float* p, float (&o)[8])
+{
+    const float4 a = *reinterpret_cast<const float4*>(p), b = *reinterpret_cast<const float4*>(p + 4);
+    o[0] = a.x; o[1] = a.y; o[2] = a.z; o[3] = a.w; o[4] = b.x; o[5] = b.y; o[6] = b.z; o[7] = b.w;
+}
+__device__ __forceinline__ void load8(const int* p, int (&o)[8])
+{
+    const int4 a = *reinterpret_cast<const int4*>(p), b = *reinterpret_cast<const int4*>(p + 4);
+    o[0] = a.x; o[1] = a.y; o[2] = a.z; o[3] = a.w; o[4] = b.x; o[5] = b.y; o[6] = b.z; o[7] = b.w;
+}
+__device__ __forceinline__ void load8(const double* p, double (&o)[8])
+{
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const double2 a = reinterpret_cast<const double2*>(p)[q];
+        o[2 * q] = a.x;
+        o[2 * q + 1] = a.y;
+    }
+}
+__device__ __forceinline__ void store8(float* p, const float (&o)[8])
+{
+    reinterpret_cast<float4*>(p)[0] = make_float4(o[0], o[1], o[2], o[3]);
+    reinterpret_cast<float4*>(p)[1] = make_float4(o[4], o[5], o[6], o[7]);
+}
+__device__ __forceinline__ void store8(int* p, const int (&o)[8])
+{
+    reinterpret_cast<int4*>(p)[0] = make_int4(o[0], o[1], o[2], o[3]);
+    reinterpret_cast<int4*>(p)[1] = make_int4(o[4], o[5], o[6], o[7]);
+}
+__device__ __forceinline__ void store8(double* p, const double (&o)[8])
+{
+#pragma unroll
+    for (int q = 0; q < 4; ++q) reinterpret_cast<double2*>(p)[q] = make_double2(o[2 * q], o[2 * q + 1]);
+}
+
+// ---------------------------------------------------------------------------
+// compensated accumulation
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void two_sum_add(float& hi, float& lo, float x)
+{
+    const float s = __fadd_rn(hi, x);
+    const float bp = __fsub_rn(s, hi);
+    const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bp)), __fsub_rn(x, bp));
+    hi = s;
+    lo = __fadd_rn(lo, e);
+}
+
+// shared memory: the atomic returns the old value, TwoSum recovers the
+// rounding error of old + x exactly; that error and the caller's own low part
+// accumulate in the lo plane
+__device__ __forceinline__ void smem_comp_add(float* hi, float* lo, float x, float xlo)
+{
+    const float old = atomicAdd(hi, x);
+    const float s = __fadd_rn(old, x);
+    const float bp = __fsub_rn(s, old);
+    const float err = __fadd_rn(__fsub_rn(old, __fsub_rn(s, bp)), __fsub_rn(x, bp));
+    const float l = __fadd_rn(err, xlo);
+    if (l != 0.0f) atomicAdd(lo, l);
+}
+
+// numerator and denominator contributions of a run of markers that share the
+// same four cells (lower corner i0, j0)
+template <typename T>
+struct Run;
+
+// FP32: a run holds at most MPT markers, summed plainly in registers (its
+// rounding error is relative to the small run sum); the run sums are then
+// accumulated in shared memory with compensation
+template <>
+struct Run<float> {
+    int i0, j0;
+    float nh[4], dh[4];
+    __device__ __forceinline__ void reset(int i, int j)
+    {
+        i0 = i;
+        j0 = j;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) nh[k] = dh[k] = 0.f;
+    }
+    __device__ __forceinline__ void add(const float (&a)[4], float f)
+    {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            nh[k] = __fadd_rn(nh[k], __fmul_rn(a[k], f));
+            dh[k] = __fadd_rn(dh[k], a[k]);
+        }
+    }
+    // window planes: num_hi, num_lo, den_hi, den_lo
+    __device__ __forceinline__ void to_window(float* win, int plane, const int (&cell)[4]) const
+    {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            smem_comp_add(win + cell[k], win + plane + cell[k], nh[k], 0.f);
+            smem_comp_add(win + 2 * plane + cell[k], win + 3 * plane + cell[k], dh[k], 0.f);
+        }
+    }
+    __device__ __forceinline__ double num(int k) const { return (double)nh[k]; }
+    __device__ __forceinline__ double den(int k) const { return (double)dh[k]; }
+};
+
+template <>
+struct Run<double> {
+    int i0, j0;
+    double nh[4], dh[4];
+    __device__ __forceinline__ void reset(int i, int j)
+    {
+        i0 = i;
+        j0 = j;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) nh[k] = dh[k] = 0.0;
+    }
+    __device__ __forceinline__ void add(const double (&a)[4], double f)
+    {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            nh[k] += a[k] * f;
+            dh[k] += a[k];
+        }
+    }
+    // window planes: num, den
+    __device__ __forceinline__ void to_window(double* win, int plane, const int (&cell)[4]) const
+    {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            atomicAdd(win + cell[k], nh[k]);
+            atomicAdd(win + plane + cell[k], dh[k]);
+        }
+    }
+    __device__ __forceinline__ double num(int k) const { return nh[k]; }
+    __device__ __forceinline__ double den(int k) const { return dh[k]; }
+};
+
+// the rare out-of-window path: FP64 global atomics into the overflow grids
+__device__ __noinline__ void flush_overflow(int ia, int ib, int j0, int nx, int nv, double n0, double n1, double n2,
+                                            double n3, double d0, double d1, double d2, double d3,
+                                            double* ovf_num, double* ovf_den)
+{
+    if (j0 >= 0 && j0 < nv) {
+        const size_t o = (size_t)j0 * nx;
+        atomicAdd(ovf_num + o + ia, n0);
+        atomicAdd(ovf_den + o + ia, d0);
+        atomicAdd(ovf_num + o + ib, n1);
+        atomicAdd(ovf_den + o + ib, d1);
+    }
+    if (j0 + 1 >= 0 && j0 + 1 < nv) {
+        const size_t o = (size_t)(j0 + 1) * nx;
+        atomicAdd(ovf_num + o + ia, n2);
+        atomicAdd(ovf_den + o + ia, d2);
+        atomicAdd(ovf_num + o + ib, n3);
+        atomicAdd(ovf_den + o + ib, d3);
+    }
+}
+
+// flush a run into the window (rows [row0, row0 + W)) or, if its rows fall
+// outside, into the FP64 overflow grids; returns true for the overflow path
+template <typename T>
+__device__ __forceinline__ bool flush_run(const Run<T>& r, T* win, int plane, int row0, int W, int nx, int nv,
+                                          double* ovf_num, double* ovf_den)
+{
+    int ia, ib;
+    wrap_pair(r.i0, nx, ia, ib);
+    const int wr = r.j0 - row0;
+    if (wr >= 0 && wr + 1 < W) {
+        const int c0 = wr * nx;
+        const int cell[4] = {c0 + ia, c0 + ib, c0 + nx + ia, c0 + nx + ib};
+        r.to_window(win, plane, cell);
+        return false;
+    }
+    flush_overflow(ia, ib, r.j0, nx, nv, r.num(0), r.num(1), r.num(2), r.num(3), r.den(0), r.den(1), r.den(2),
+                   r.den(3), ovf_num, ovf_den);
+    return true;
 }
 
 size_t pd1_smem_bytes(const SpDev& sp, int prec)
 {
     size_t eb = (size_t)sp.nx * (prec == AVL_FP32 ? 4 : 8);
     eb = (eb + 15) & ~size_t(15);
-    return eb + 32 + (size_t)16 * sp.W * sp.nx;
+    return eb + 32 + (size_t)HIST_S * 4 + (size_t)16 * sp.Wmax * sp.nx;
 }
 
 // ---------------------------------------------------------------------------
-// push + deposit: one CTA per velocity bin of one species
+// slot assignment within a warp
+// ---------------------------------------------------------------------------
+// Every lane holds up to MPT consecutive markers with key codes code[m]
+// (-1: no marker), lanes in storage order.  For every key the warp's markers
+// get consecutive slots in storage order, starting at the chunk's first slot
+// for that key offs[code] (global) plus the chunk's running count scnt[code]
+// (shared); so a thread's run of same-key markers stays together.  Far keys
+// (code >= HIST_S) take slots from the global per-key cursor far_cur.
+__device__ __forceinline__ void assign_slots(const int (&code)[MPT], int* scnt, const int* __restrict__ offs,
+                                             int* far_cur, int (&dst)[MPT])
+{
+    const int lane = threadIdx.x & 31;
+    // common case: every lane holds MPT markers of one in-histogram key
+    {
+        const int k0 = code[0];
+        bool same = k0 >= 0 && k0 < HIST_S;
+#pragma unroll
+        for (int m = 1; m < MPT; ++m) same = same && code[m] == k0;
+        const int kw = __shfl_sync(0xffffffffu, k0, 0);
+        if (__all_sync(0xffffffffu, same && k0 == kw)) {
+            int base = 0;
+            if (lane == 0) base = offs[kw] + atomicAdd(scnt + kw, 32 * MPT);
+            base = __shfl_sync(0xffffffffu, base, 0) + lane * MPT;
+#pragma unroll
+            for (int m = 0; m < MPT; ++m) dst[m] = base + m;
+            return;
+        }
+    }
+    unsigned done = 0;
+#pragma unroll
+    for (int m = 0; m < MPT; ++m) {
+        dst[m] = -1;
+        if (code[m] < 0) done |= 1u << m;
+    }
+    for (int guard = 0; guard < 32 * MPT + 1; ++guard) {
+        int mine = 0x7fffffff;
+#pragma unroll
+        for (int m = 0; m < MPT; ++m)
+            if (!(done >> m & 1)) mine = min(mine, code[m]);
+        const int k = __reduce_min_sync(0xffffffffu, mine);
+        if (k == 0x7fffffff) break;
+        int n = 0;
+#pragma unroll
+        for (int m = 0; m < MPT; ++m) n += (!(done >> m & 1) && code[m] == k) ? 1 : 0;
+        int incl = n;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        const int total = __shfl_sync(0xffffffffu, incl, 31);
+        int base = 0;
+        if (lane == 0) base = (k >= HIST_S) ? atomicAdd(far_cur + (k - HIST_S), total) : offs[k] + atomicAdd(scnt + k, total);
+        base = __shfl_sync(0xffffffffu, base, 0);
+        int d = base + incl - n;
+#pragma unroll
+        for (int m = 0; m < MPT; ++m) {
+            if (!(done >> m & 1) && code[m] == k) {
+                dst[m] = d++;
+                done |= 1u << m;
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// scan of the per-chunk key counts
+// ---------------------------------------------------------------------------
+// kref[c]: reference key of source chunk c (its histogram covers keys
+// [kref - HIST_R, kref - HIST_R + HIST_S)).  sorted: kref is non-decreasing
+// over chunks (the current layout), so the chunks that count key k are found
+// by binary search; otherwise every chunk is visited.  Writes base_new,
+// offs, far_cur (and clears far_cnt); kb_new (if given) receives the
+// reference key of every chunk of the new layout; windows: the rows covered
+// by the current chunks' deposit windows (placed by the count kernel).
+__device__ void chunk_range(const int* kref, int nch, int k, bool sorted, int& c0, int& c1)
+{
+    c0 = 0;
+    c1 = nch;
+    if (!sorted) return;
+    // chunks with kbase = kref - HIST_R in (k - HIST_S, k]
+    int lo = 0, hi = nch;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (kref[mid] - HIST_R > k - HIST_S) hi = mid; else lo = mid + 1;
+    }
+    c0 = lo;
+    hi = nch;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (kref[mid] - HIST_R > k) hi = mid; else lo = mid + 1;
+    }
+    c1 = lo;
+}
+
+__device__ void scan_species(const SpDev& sp, const int* __restrict__ kref, bool sorted, int* kb_new, bool windows)
+{
+    const int nv = sp.nvflat, nch = sp.nchunk;
+    __shared__ int warp_sums[32];
+    __shared__ int carry;
+    // (a) totals per key
+    for (int k = threadIdx.x; k < nv; k += blockDim.x) {
+        int tot = sp.far_cnt[k];
+        int c0, c1;
+        chunk_range(kref, nch, k, sorted, c0, c1);
+        for (int c = c0; c < c1; ++c) {
+            const int r = k - (kref[c] - HIST_R);
+            if (r >= 0 && r < HIST_S) tot += sp.cnt[(size_t)c * HIST_S + r];
+        }
+        sp.base_new[k] = tot;
+    }
+    __syncthreads();
+    // (b) exclusive scan over keys
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int b0 = 0; b0 < nv; b0 += blockDim.x) {
+        const int i = b0 + threadIdx.x;
+        const int v = i < nv ? sp.base_new[i] : 0;
+        int x = v;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) warp_sums[warp] = x;
+        __syncthreads();
+        if (warp == 0) {
+            int w = lane < nw ? warp_sums[lane] : 0;
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, w, o);
+                if (lane >= o) w += y;
+            }
+            warp_sums[lane] = w;
+        }
+        __syncthreads();
+        const int incl = x + (warp > 0 ? warp_sums[warp - 1] : 0) + carry;
+        if (i < nv) sp.base_new[i] = incl - v;
+        __syncthreads();
+        if (threadIdx.x == blockDim.x - 1) carry = incl;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) sp.base_new[nv] = carry;
+    __syncthreads();
+    // (c) first slot of every (chunk, key), then of the far markers of each key
+    for (int k = threadIdx.x; k < nv; k += blockDim.x) {
+        int run = sp.base_new[k];
+        int c0, c1;
+        chunk_range(kref, nch, k, sorted, c0, c1);
+        for (int c = c0; c < c1; ++c) {
+            const int r = k - (kref[c] - HIST_R);
+            if (r >= 0 && r < HIST_S) {
+                sp.offs[(size_t)c * HIST_S + r] = run;
+                run += sp.cnt[(size_t)c * HIST_S + r];
+            }
+        }
+        sp.far_cur[k] = run;
+        sp.far_cnt[k] = 0;
+    }
+    // (d) reference key of every chunk of the new layout: the key of its first slot
+    if (kb_new) {
+        for (int c = threadIdx.x; c < nch; c += blockDim.x) {
+            const int p = c * sp.M;
+            int lo = 0, hi = nv;   // largest k with base_new[k] <= p
+            while (hi - lo > 1) {
+                const int mid = (lo + hi) >> 1;
+                if (sp.base_new[mid] <= p) lo = mid; else hi = mid;
+            }
+            kb_new[c] = lo;
+        }
+    }
+    // (e) deposit windows of the current chunks and the rows they cover
+    if (windows) {
+        for (int j = threadIdx.x; j < nv; j += blockDim.x) {
+            sp.rc_lo[j] = nch;
+            sp.rc_hi[j] = -1;
+        }
+        __syncthreads();
+        for (int c = threadIdx.x; c < nch; c += blockDim.x) {
+            const int r0 = sp.wrow0[c];
+            const int jlo = max(r0, 0), jhi = min(r0 + sp.Wmax, nv);
+            for (int j = jlo; j < jhi; ++j) {
+                atomicMin(sp.rc_lo + j, c);
+                atomicMax(sp.rc_hi + j, c);
+            }
+        }
+    }
+    __syncthreads();
+}
+
+// last CTA of a grid (counted on ctl->count_done): true in every thread of it
+__device__ __forceinline__ bool last_block(Ctl* ctl)
+{
+    __shared__ bool is_last;
+    __threadfence();   // every thread's writes become visible device-wide
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const unsigned done = atomicAdd(&ctl->count_done, 1u);
+        is_last = (done == gridDim.x - 1);
+        if (is_last) __threadfence();
+    }
+    __syncthreads();
+    return is_last;
+}
+
+// warp-aggregated histogram of key codes
+__device__ __forceinline__ void hist_add(int* hist, int* far_cnt, int code, bool valid)
+{
+    const int key = valid ? code : -1;
+    const unsigned mask = __match_any_sync(0xffffffffu, key);
+    const int lane = threadIdx.x & 31;
+    if (valid && lane == __ffs(mask) - 1) {
+        if (code < HIST_S)
+            atomicAdd(hist + code, __popc(mask));
+        else
+            atomicAdd(far_cnt + (code - HIST_S), __popc(mask));
+    }
+}
+
+// ---------------------------------------------------------------------------
+// count kernel over the current layout (one CTA per chunk)
 // ---------------------------------------------------------------------------
 template <typename T>
-__global__ void __launch_bounds__(PD_THREADS) k_pd1(const StepArgs* __restrict__ A, int push)
+__global__ void __launch_bounds__(CNT_THREADS) k_count1(const StepArgs* __restrict__ A, int mode)
+{
+    __shared__ int hist[HIST_S];
+    const int g = blockIdx.x;
+    const int s = species_of_chunk(A, g);
+    const SpDev& sp = A->sp[s];
+    Ctl* ctl = A->ctl;
+    const bool active = mode == 0 || sp.mobile;
+    const int c = g - sp.chunk_base;
+    if (active) {
+        const int cb = ctl->cur[s];
+        const int kb = sp.KB[cb][c];
+        const int kbase = kb - HIST_R;
+        const int beg = c * sp.M, end = (int)min((long long)(c + 1) * sp.M, sp.n);
+        for (int i = threadIdx.x; i < HIST_S; i += CNT_THREADS) hist[i] = 0;
+        __syncthreads();
+        const T* dvp = reinterpret_cast<const T*>(sp.mv[cb][0]);
+        const T inv_dv = (T)sp.inv_dv[0];
+        const int nv = sp.nvflat;
+        for (int b0 = beg; b0 < end; b0 += CNT_THREADS * 8) {
+            const int g0 = b0 + threadIdx.x * 8;
+            T d8[8];
+            if (g0 < end) load8(dvp + g0, d8);
+#pragma unroll
+            for (int m = 0; m < 8; ++m) {
+                const bool ok = g0 + m < end;
+                const int key = ok ? key_rel(d8[m], kb, inv_dv, nv) : 0;
+                hist_add(hist, sp.far_cnt, rel_code(key, kbase), ok);
+            }
+        }
+        __syncthreads();
+        for (int i = threadIdx.x; i < HIST_S; i += CNT_THREADS) sp.cnt[(size_t)c * HIST_S + i] = hist[i];
+        // deposit window: the Wmax rows that serve the most markers, allowing
+        // HALO rows of drift and the cloud's second row
+        if (threadIdx.x == 0) {
+            const int wk = max(1, min(HIST_S, sp.Wmax - 2 * HALO - 1));
+            int sum = 0;
+            for (int r = 0; r < wk; ++r) sum += hist[r];
+            int best = sum, bestr = 0;
+            for (int r = 1; r + wk <= HIST_S; ++r) {
+                sum += hist[r + wk - 1] - hist[r - 1];
+                if (sum > best) {
+                    best = sum;
+                    bestr = r;
+                }
+            }
+            sp.wrow0[c] = kbase + bestr - HALO;
+        }
+    }
+    if (!last_block(ctl)) return;
+    // the last CTA scans every species counted by this grid
+    for (int q = 0; q < A->ns; ++q) {
+        const SpDev& spq = A->sp[q];
+        if (spq.nchunk == 0 || !(mode == 0 || spq.mobile)) continue;
+        const int cbq = ctl->cur[q];
+        scan_species(spq, spq.KB[cbq], true, mode == 1 ? spq.KB[1 - cbq] : nullptr, true);
+    }
+    if (threadIdx.x == 0) ctl->count_done = 0;
+}
+
+// ---------------------------------------------------------------------------
+// push + deposit + re-sorted write (one CTA per chunk)
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(PD_THREADS, 2) k_pd1(const StepArgs* __restrict__ A, int mode)
 {
     extern __shared__ __align__(128) unsigned char smem[];
     const int g = blockIdx.x;
-    const int s = species_of(A, g, false);
+    const int s = species_of_chunk(A, g);
     const SpDev& sp = A->sp[s];
-    if (push && !sp.mobile) return;
+    if (mode == 1 && !sp.mobile) return;
     Ctl* ctl = A->ctl;
-
-    const int b = g - sp.bin_base;
-    const int nx = sp.nx, tv = sp.tv, hw = sp.hw, W = sp.W, nv = sp.nv[0];
+    const bool push = mode == 1;
+    const int c = g - sp.chunk_base;
+    const int nx = sp.nx, nv = sp.nvflat, W = sp.Wmax;
     const int cb = ctl->cur[s];
-    const int beg = sp.bin_start[cb][b];
-    const int end = sp.bin_start[cb][b + 1];
+    const int n_all = (int)sp.n;
+    const int beg = c * sp.M, end = min((c + 1) * sp.M, n_all);
+    const int kb = sp.KB[cb][c];
+    const int kbase = kb - HIST_R;
+    const int row0 = sp.wrow0[c];
 
-    size_t eb = ((size_t)nx * sizeof(T) + 15) & ~size_t(15);
+    const size_t eb = ((size_t)nx * sizeof(T) + 15) & ~size_t(15);
     T* Es = reinterpret_cast<T*>(smem);
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem + eb);
-    unsigned* cnt = reinterpret_cast<unsigned*>(smem + eb + 16);   // [0] dirty, [1] overflow
-    unsigned char* win = smem + eb + 32;
+    unsigned* cnt = reinterpret_cast<unsigned*>(smem + eb + 16);   // [0] overflow runs, [1] bad slots
+    int* scnt = reinterpret_cast<int*>(smem + eb + 32);
+    unsigned char* winb = smem + eb + 32 + HIST_S * 4;
     const int plane = W * nx;
     const size_t win_bytes = (size_t)16 * plane;
 
-    const T* Eg = (sizeof(T) == 4) ? reinterpret_cast<const T*>(A->fd.E32)
-                                   : reinterpret_cast<const T*>(A->fd.E64);
+    const T* Eg = (sizeof(T) == 4) ? reinterpret_cast<const T*>(A->fd.E32) : reinterpret_cast<const T*>(A->fd.E64);
     const bool use_bulk = push && ((nx * sizeof(T)) % 16 == 0);
     if (threadIdx.x == 0) {
         cnt[0] = 0;
@@ -199,131 +724,176 @@ __global__ void __launch_bounds__(PD_THREADS) k_pd1(const StepArgs* __restrict__
             fence_mbar_init();
         }
     }
+    for (int i = threadIdx.x; i < HIST_S; i += PD_THREADS) scnt[i] = 0;
     __syncthreads();
     if (use_bulk && threadIdx.x == 0) {
         mbar_arrive_expect_tx(bar, (unsigned)(nx * sizeof(T)));
         bulk_g2s(Es, Eg, (unsigned)(nx * sizeof(T)), bar);
     }
-    // zero the window while the field is in flight
-    {
-        float4* w4 = reinterpret_cast<float4*>(win);
+    {   // zero the window while the field is in flight
+        float4* w4 = reinterpret_cast<float4*>(winb);
         const int n4 = (int)(win_bytes / 16);
         for (int i = threadIdx.x; i < n4; i += PD_THREADS) w4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
     }
-    if (push && !use_bulk) {
+    if (push && !use_bulk)
         for (int i = threadIdx.x; i < nx; i += PD_THREADS) Es[i] = Eg[i];
-    }
-    if (use_bulk) {
-        if (!mbar_wait_bounded(bar, 0, WAIT_LIMIT)) {
-            if (threadIdx.x == 0) atomicOr(&ctl->err, ERR_TIMEOUT);
-            mbar_wait_bounded(bar, 0, WAIT_LIMIT);
-            return;
-        }
+    if (use_bulk && !mbar_wait_bounded(bar, 0, WAIT_LIMIT)) {
+        if (threadIdx.x == 0) atomicOr(&ctl->err, ERR_TIMEOUT);
+        mbar_wait_bounded(bar, 0, WAIT_LIMIT);
+        return;
     }
     __syncthreads();
 
-    Window<T> wacc;
-    wacc.p = reinterpret_cast<T*>(win);
-    wacc.plane = plane;
-
+    T* win = reinterpret_cast<T*>(winb);
     const T inv_dv = (T)sp.inv_dv[0];
     const T qm_dt = (T)sp.qm_dt;
     const T dt_dx = (T)sp.dt_dx;
-    const double vref = sp.vmin[0] + (double)b * tv * sp.dv[0];
-    const T vref_dtdx = (T)(vref * sp.dt_dx);
-    const int row_base = b * tv;
-    T* dvp = reinterpret_cast<T*>(sp.mv[cb][0]);
-    const T* fp = reinterpret_cast<const T*>(sp.mf[cb]);
+    const T vref_dtdx = (T)((sp.vmin[0] + (double)kb * sp.dv[0]) * sp.dt_dx);
+    const T dvk = (T)sp.dv[0];
     double* ovf_num = sp.ovf;
-    double* ovf_den = sp.ovf + (size_t)sp.nvflat * nx;
-    const int lane = threadIdx.x & 31;
+    double* ovf_den = sp.ovf + (size_t)nv * nx;
+    const T* dvp = reinterpret_cast<const T*>(sp.mv[cb][0]);
+    const T* fp = reinterpret_cast<const T*>(sp.mf[cb]);
+    const int nb = 1 - cb;
+    T* dvp_out = reinterpret_cast<T*>(sp.mv[nb][0]);
+    T* fp_out = reinterpret_cast<T*>(sp.mf[nb]);
+    const int* offs = sp.offs + (size_t)c * HIST_S;
+    const int* kb_new = sp.KB[nb];
+    unsigned n_over = 0, n_bad = 0;
 
-    for (int base = beg; base < end; base += PD_THREADS * PD_UNROLL) {
-        Pos<T> pos[PD_UNROLL];
-        T dv[PD_UNROLL], fl[PD_UNROLL];
+    for (int base = beg; base < end; base += PD_THREADS * MPT) {
+        const int g0 = base + threadIdx.x * MPT;
+        const bool any = g0 < end;
+        // all eight markers of the group at once (vector loads, padded arrays)
+        T dv8[MPT], f8[MPT];
+        Pos<T> pos8[MPT];
+        if (any) {
+            loadg(dvp + g0, dv8);
+            loadg(fp + g0, f8);
+            if constexpr (sizeof(T) == 4) {
+                int c8[MPT];
+                float o8[MPT];
+                loadg(reinterpret_cast<const int*>(sp.mx[cb]) + g0, c8);
+                loadg(sp.moff[cb] + g0, o8);
 #pragma unroll
-        for (int u = 0; u < PD_UNROLL; ++u) {
-            const int k = base + u * PD_THREADS + threadIdx.x;
-            if (k < end) {
-                pos[u].load(sp, cb, k);
-                dv[u] = dvp[k];
-                fl[u] = fp[k];
+                for (int m = 0; m < MPT; ++m) {
+                    pos8[m].c = c8[m];
+                    pos8[m].o = o8[m];
+                }
+            } else {
+                double x8[MPT];
+                loadg(reinterpret_cast<const double*>(sp.mx[cb]) + g0, x8);
+#pragma unroll
+                for (int m = 0; m < MPT; ++m) pos8[m].xi = x8[m];
             }
         }
+        // slots in the re-sorted layout, keyed by the current state
+        int dst[MPT];
+        if (push) {
+            int code[MPT];
 #pragma unroll
-        for (int u = 0; u < PD_UNROLL; ++u) {
-            const int k = base + u * PD_THREADS + threadIdx.x;
-            const bool valid = k < end;
-            bool dirty = false, over = false;
-            if (valid) {
+            for (int m = 0; m < MPT; ++m)
+                code[m] = (g0 + m < end) ? rel_code(key_rel(dv8[m], kb, inv_dv, nv), kbase) : -1;
+            assign_slots(code, scnt, offs, sp.far_cur, dst);
+        }
+        Run<T> run;
+        run.reset(0x7fffffff, 0);
+        bool have = false;
+#pragma unroll
+        for (int m = 0; m < MPT; ++m) {
+            if (g0 + m < end) {
+                Pos<T>& pos = pos8[m];
+                T dv = dv8[m];
+                const T fl = f8[m];
                 if (push) {
                     int i0, ia, ib;
                     T w;
-                    pos[u].cic(i0, w);
+                    pos.cic(i0, w);
                     wrap_pair(i0, nx, ia, ib);
                     const T El = ((T)1 - w) * Es[ia] + w * Es[ib];
-                    dv[u] += qm_dt * El;
-                    pos[u].drift(vref_dtdx + dv[u] * dt_dx, nx);
-                    pos[u].store(sp, cb, k);
-                    dvp[k] = dv[u];
+                    dv += qm_dt * El;
+                    pos.drift(vref_dtdx + dv * dt_dx, nx);
+                    dv8[m] = dv;
                 }
-                // deposit at the new position (Eq. 4 numerator and denominator)
-                int i0, ia, ib;
+                // cloud-in-cell footprint of the new state (Eq. 4 weights)
+                int i0;
                 T wx;
-                pos[u].cic(i0, wx);
-                wrap_pair(i0, nx, ia, ib);
-                const T t = dv[u] * inv_dv - (T)0.5;
+                pos.cic(i0, wx);
+                const T t = dv * inv_dv - (T)0.5;
                 const T ft = floor(t);
-                const int r0 = (int)ft;
+                const int j0 = kb + (int)ft;
                 const T wv = t - ft;
-                const T a00 = ((T)1 - wx) * ((T)1 - wv), a10 = wx * ((T)1 - wv);
-                const T a01 = ((T)1 - wx) * wv, a11 = wx * wv;
-                const int wr = r0 + hw;
-                if (wr >= 0 && wr + 1 < W) {
-                    const int c0 = wr * nx;
-                    wacc.add(c0 + ia, a00, a00 * fl[u]);
-                    wacc.add(c0 + ib, a10, a10 * fl[u]);
-                    wacc.add(c0 + nx + ia, a01, a01 * fl[u]);
-                    wacc.add(c0 + nx + ib, a11, a11 * fl[u]);
-                } else {
-                    const int j0 = row_base + r0;
-                    if (j0 >= 0 && j0 < nv) {
-                        over = true;
-                        atomicAdd(ovf_num + (size_t)j0 * nx + ia, (double)(a00 * fl[u]));
-                        atomicAdd(ovf_den + (size_t)j0 * nx + ia, (double)a00);
-                        atomicAdd(ovf_num + (size_t)j0 * nx + ib, (double)(a10 * fl[u]));
-                        atomicAdd(ovf_den + (size_t)j0 * nx + ib, (double)a10);
+                if (!have || i0 != run.i0 || j0 != run.j0) {
+                    if (have) n_over += flush_run<T>(run, win, plane, row0, W, nx, nv, ovf_num, ovf_den) ? 1u : 0u;
+                    run.reset(i0, j0);
+                    have = true;
+                }
+                const T a[4] = {((T)1 - wx) * ((T)1 - wv), wx * ((T)1 - wv), ((T)1 - wx) * wv, wx * wv};
+                run.add(a, fl);
+            }
+        }
+        if (have) n_over += flush_run<T>(run, win, plane, row0, W, nx, nv, ovf_num, ovf_den) ? 1u : 0u;
+        if (push && any) {
+            // write the pushed markers into their slots, velocity re-referenced
+            // to the target chunk; one vector store per array when the eight
+            // slots are contiguous and aligned
+            bool vec = (g0 + MPT <= end) && (dst[0] % MPT == 0) && ((unsigned)dst[0] + MPT <= (unsigned)n_all);
+#pragma unroll
+            for (int m = 1; m < MPT; ++m) vec = vec && (dst[m] == dst[0] + m);
+            T dvo[MPT];
+#pragma unroll
+            for (int m = 0; m < MPT; ++m) {
+                const int d = dst[m];
+                const int c2 = ((unsigned)d < (unsigned)n_all) ? chunk_of(d, sp.div_m, sp.div_l) : c;
+                dvo[m] = dv8[m] + (T)(kb - kb_new[c2]) * dvk;
+            }
+            if (vec) {
+                const int d0 = dst[0];
+                storeg(dvp_out + d0, dvo);
+                storeg(fp_out + d0, f8);
+                if constexpr (sizeof(T) == 4) {
+                    int c8[MPT];
+                    float o8[MPT];
+#pragma unroll
+                    for (int m = 0; m < MPT; ++m) {
+                        c8[m] = pos8[m].c;
+                        o8[m] = pos8[m].o;
                     }
-                    if (j0 + 1 >= 0 && j0 + 1 < nv) {
-                        over = true;
-                        atomicAdd(ovf_num + (size_t)(j0 + 1) * nx + ia, (double)(a01 * fl[u]));
-                        atomicAdd(ovf_den + (size_t)(j0 + 1) * nx + ia, (double)a01);
-                        atomicAdd(ovf_num + (size_t)(j0 + 1) * nx + ib, (double)(a11 * fl[u]));
-                        atomicAdd(ovf_den + (size_t)(j0 + 1) * nx + ib, (double)a11);
+                    storeg(reinterpret_cast<int*>(sp.mx[nb]) + d0, c8);
+                    storeg(sp.moff[nb] + d0, o8);
+                } else {
+                    double x8[MPT];
+#pragma unroll
+                    for (int m = 0; m < MPT; ++m) x8[m] = pos8[m].xi;
+                    storeg(reinterpret_cast<double*>(sp.mx[nb]) + d0, x8);
+                }
+            } else {
+#pragma unroll
+                for (int m = 0; m < MPT; ++m) {
+                    if (g0 + m >= end) continue;
+                    const int d = dst[m];
+                    if ((unsigned)d < (unsigned)n_all) {
+                        pos8[m].store(sp, nb, d);
+                        dvp_out[d] = dvo[m];
+                        fp_out[d] = f8[m];
+                    } else {
+                        ++n_bad;
                     }
                 }
-                // has the marker wandered out of its bin (re-sort trigger)?
-                int row = row_base + (int)floor(dv[u] * inv_dv);
-                row = row < 0 ? 0 : (row >= nv ? nv - 1 : row);
-                dirty = (row < row_base - sp.hd) || (row >= row_base + tv + sp.hd);
-            }
-            const unsigned bd = __ballot_sync(0xffffffffu, dirty);
-            const unsigned bo = __ballot_sync(0xffffffffu, over);
-            if (lane == 0 && (bd | bo)) {
-                if (bd) atomicAdd(&cnt[0], (unsigned)__popc(bd));
-                if (bo) atomicAdd(&cnt[1], (unsigned)__popc(bo));
             }
         }
     }
+    if (n_over) atomicAdd(&cnt[0], n_over);
+    if (n_bad) atomicAdd(&cnt[1], n_bad);
     __syncthreads();
-    // flush the window to this bin's partial sums with one bulk copy
+    // flush the window to this chunk's partial sums with one bulk copy
     if (threadIdx.x == 0) {
         fence_proxy_async_smem();
-        unsigned char* dst = reinterpret_cast<unsigned char*>(sp.partial) + (size_t)b * win_bytes;
-        bulk_s2g(dst, win, (unsigned)win_bytes);
+        unsigned char* dstp = reinterpret_cast<unsigned char*>(sp.partial) + (size_t)c * win_bytes;
+        bulk_s2g(dstp, winb, (unsigned)win_bytes);
         bulk_commit();
-        if (cnt[0]) atomicAdd(&ctl->dirty[s], (unsigned long long)cnt[0]);
-        if (cnt[1]) atomicAdd(&ctl->ovf_count[s], (unsigned long long)cnt[1]);
+        if (cnt[0]) atomicAdd(&ctl->ovf_count[s], (unsigned long long)cnt[0]);
+        if (cnt[1]) atomicOr(&ctl->err, ERR_CAPACITY);
         bulk_wait_all();
     }
 }
@@ -338,14 +908,7 @@ struct ff {
     float hi, lo;
 };
 
-__device__ __forceinline__ void ff_add(ff& a, float x)
-{
-    const float s = __fadd_rn(a.hi, x);
-    const float bp = __fsub_rn(s, a.hi);
-    const float e = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bp)), __fsub_rn(x, bp));
-    a.hi = s;
-    a.lo = __fadd_rn(a.lo, e);
-}
+__device__ __forceinline__ void ff_add(ff& a, float x) { two_sum_add(a.hi, a.lo, x); }
 
 template <typename T>
 struct CellSum;
@@ -437,13 +1000,6 @@ struct ColAcc<double> {
     __device__ __forceinline__ double s() const { return ent; }
 };
 
-__device__ __forceinline__ int species_of_fin(const StepArgs* A, int g)
-{
-    int s = 0;
-    while (s + 1 < A->ns && g >= A->sp[s + 1].fin_base) ++s;
-    return s;
-}
-
 template <typename T>
 __global__ void __launch_bounds__(FIN_THREADS) k_fin1(const StepArgs* __restrict__ A, int all_species)
 {
@@ -457,29 +1013,32 @@ __global__ void __launch_bounds__(FIN_THREADS) k_fin1(const StepArgs* __restrict
     Ctl* ctl = A->ctl;
     const int blk = g - sp.fin_base;
     const int xb = blk % sp.nxb, rqi = blk / sp.nxb;
-    const int nx = sp.nx, nv = sp.nvflat, tv = sp.tv, hw = sp.hw, W = sp.W;
+    const int nx = sp.nx, nv = sp.nvflat, W = sp.Wmax;
     const int col = threadIdx.x % FIN_XB, lr = threadIdx.x / FIN_XB;
     const int x = xb * FIN_XB + col;
     const bool xok = x < nx;
     const int j0 = rqi * sp.rq, j1 = min(nv, j0 + sp.rq);
     const int plane = W * nx;
     const bool any_ovf = ctl->ovf_count[s] != 0;
+    const bool any_chunk = sp.nchunk > 0;
     double* ovf_num = sp.ovf;
     double* ovf_den = sp.ovf + (size_t)nv * nx;
     T* fg = reinterpret_cast<T*>(sp.fgrid);
     T* ng = reinterpret_cast<T*>(sp.ngrid);
     const T* part = reinterpret_cast<const T*>(sp.partial);
-    const int planes = sizeof(T) == 4 ? 4 : 2;
+    constexpr int planes = sizeof(T) == 4 ? 4 : 2;
 
     ColAcc<T> acc;
     if (xok) {
         for (int j = j0 + lr; j < j1; j += RL) {
-            const int blo = max(ceil_div(j - tv - hw + 1, tv), 0);
-            const int bhi = min(floor_div(j + hw, tv), sp.nbins - 1);
             CellSum<T> cs;
-            for (int b = blo; b <= bhi; ++b) {
-                const int wr = j - (b * tv - hw);
-                cs.add_partial(part + (size_t)b * planes * plane + (size_t)wr * nx + x, plane);
+            if (any_chunk) {
+                const int clo = sp.rc_lo[j], chi = sp.rc_hi[j];
+                for (int cc = clo; cc <= chi; ++cc) {
+                    const int wr = j - sp.wrow0[cc];
+                    if (wr >= 0 && wr < W)
+                        cs.add_partial(part + (size_t)cc * planes * plane + (size_t)wr * nx + x, plane);
+                }
             }
             if (any_ovf) {
                 const size_t o = (size_t)j * nx + x;
@@ -518,169 +1077,22 @@ __global__ void __launch_bounds__(FIN_THREADS) k_fin1(const StepArgs* __restrict
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        double a = 0, bb = 0, c = 0;
+        double a = 0, bb = 0, cc = 0;
         for (int w = 0; w < FIN_THREADS / 32; ++w) {
             a += red[0][w];
             bb += red[1][w];
-            c += red[2][w];
+            cc += red[2][w];
         }
         const double cell = sp.dx * sp.dv[0];
         sp.dpart[(size_t)blk * 4 + 0] = a * cell;
         sp.dpart[(size_t)blk * 4 + 1] = 0.5 * sp.m * bb * cell;
-        sp.dpart[(size_t)blk * 4 + 2] = c * cell;
+        sp.dpart[(size_t)blk * 4 + 2] = cc * cell;
         sp.dpart[(size_t)blk * 4 + 3] = 0.0;
     }
 }
 
 // ---------------------------------------------------------------------------
-// re-binning: count -> scan -> scatter, only for flagged species
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ int warp_aggregate_add(int* counters, int key)
-{
-    // all 32 lanes call this; key < 0 means "no slot"
-    const unsigned mask = __match_any_sync(0xffffffffu, key);
-    const int lane = threadIdx.x & 31;
-    const int leader = __ffs(mask) - 1;
-    const int rank = __popc(mask & ((1u << lane) - 1u));
-    int base = 0;
-    if (lane == leader && key >= 0) base = atomicAdd(counters + key, __popc(mask));
-    base = __shfl_sync(0xffffffffu, base, leader);
-    return base + rank;
-}
-
-template <typename T>
-__device__ __forceinline__ int bin_key(const SpDev& sp, int b, T dv)
-{
-    int row = b * sp.tv + (int)floor(dv * (T)sp.inv_dv[0]);
-    row = row < 0 ? 0 : (row >= sp.nv[0] ? sp.nv[0] - 1 : row);
-    return row / sp.tv;
-}
-
-template <typename T>
-__global__ void __launch_bounds__(SORT_THREADS) k_sort_count1(const StepArgs* __restrict__ A)
-{
-    Ctl* ctl = A->ctl;
-    if (!ctl->any_sort) return;
-    const int g = blockIdx.x;
-    const int s = species_of(A, g, false);
-    if (!ctl->sort_flag[s]) return;
-    const SpDev& sp = A->sp[s];
-    const int b = g - sp.bin_base;
-    const int cb = ctl->cur[s];
-    const int beg = sp.bin_start[cb][b], end = sp.bin_start[cb][b + 1];
-    const T* dvp = reinterpret_cast<const T*>(sp.mv[cb][0]);
-    for (int base = beg; base < end; base += SORT_THREADS) {
-        const int k = base + threadIdx.x;
-        const int key = k < end ? bin_key<T>(sp, b, dvp[k]) : -1;
-        warp_aggregate_add(sp.hist, key);
-    }
-}
-
-__global__ void __launch_bounds__(1024) k_sort_scan(const StepArgs* __restrict__ A, int only_species)
-{
-    Ctl* ctl = A->ctl;
-    if (only_species < 0 && !ctl->any_sort) return;
-    __shared__ int warp_sums[32];
-    __shared__ int carry;
-    for (int s = 0; s < A->ns; ++s) {
-        if (only_species >= 0 ? s != only_species : !ctl->sort_flag[s]) continue;
-        const SpDev& sp = A->sp[s];
-        const int nb = sp.nbins;
-        // only_species >= 0: set_markers scans into the current buffer
-        int* out = sp.bin_start[only_species >= 0 ? ctl->cur[s] : 1 - ctl->cur[s]];
-        if (threadIdx.x == 0) carry = 0;
-        __syncthreads();
-        for (int base = 0; base < nb; base += 1024) {
-            const int i = base + threadIdx.x;
-            const int v = i < nb ? sp.hist[i] : 0;
-            int x = v;
-            const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-            for (int o = 1; o < 32; o <<= 1) {
-                const int y = __shfl_up_sync(0xffffffffu, x, o);
-                if (lane >= o) x += y;
-            }
-            if (lane == 31) warp_sums[warp] = x;
-            __syncthreads();
-            if (warp == 0) {
-                int w = warp_sums[lane];
-                for (int o = 1; o < 32; o <<= 1) {
-                    const int y = __shfl_up_sync(0xffffffffu, w, o);
-                    if (lane >= o) w += y;
-                }
-                warp_sums[lane] = w;
-            }
-            __syncthreads();
-            const int incl = x + (warp > 0 ? warp_sums[warp - 1] : 0) + carry;
-            if (i < nb) {
-                out[i] = incl - v;
-                sp.cursor[i] = incl - v;
-                sp.hist[i] = 0;
-            }
-            __syncthreads();
-            if (threadIdx.x == 1023) carry = incl;
-            __syncthreads();
-        }
-        if (threadIdx.x == 0) out[nb] = carry;
-        __syncthreads();
-    }
-}
-
-template <typename T>
-__device__ __forceinline__ void move_marker(const SpDev& sp, int src_buf, int k, int dst_buf, int d,
-                                            T dv_shift)
-{
-    Pos<T> p;
-    p.load(sp, src_buf, k);
-    p.store(sp, dst_buf, d);
-    reinterpret_cast<T*>(sp.mv[dst_buf][0])[d] = reinterpret_cast<const T*>(sp.mv[src_buf][0])[k] + dv_shift;
-    reinterpret_cast<T*>(sp.mf[dst_buf])[d] = reinterpret_cast<const T*>(sp.mf[src_buf])[k];
-}
-
-template <typename T>
-__global__ void __launch_bounds__(SORT_THREADS) k_scatter1(const StepArgs* __restrict__ A)
-{
-    Ctl* ctl = A->ctl;
-    if (!ctl->any_sort) return;
-    const int g = blockIdx.x;
-    const int s = species_of(A, g, false);
-    const SpDev& sp = A->sp[s];
-    if (ctl->sort_flag[s]) {
-        const int b = g - sp.bin_base;
-        const int cb = ctl->cur[s];
-        const int beg = sp.bin_start[cb][b], end = sp.bin_start[cb][b + 1];
-        const T* dvp = reinterpret_cast<const T*>(sp.mv[cb][0]);
-        for (int base = beg; base < end; base += SORT_THREADS) {
-            const int k = base + threadIdx.x;
-            const int key = k < end ? bin_key<T>(sp, b, dvp[k]) : -1;
-            const int d = warp_aggregate_add(sp.cursor, key);
-            if (key >= 0) {
-                const T shift = (T)((double)(b - key) * sp.tv * sp.dv[0]);
-                move_marker<T>(sp, cb, k, 1 - cb, d, shift);
-            }
-        }
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        __threadfence();
-        const unsigned done = atomicAdd(&ctl->scatter_done, 1u);
-        if (done == gridDim.x - 1) {
-            __threadfence();
-            for (int q = 0; q < A->ns; ++q) {
-                if (ctl->sort_flag[q]) {
-                    ctl->cur[q] = 1 - ctl->cur[q];
-                    ctl->sort_flag[q] = 0;
-                    ctl->nsort[q] += 1;
-                }
-            }
-            ctl->any_sort = 0;
-            ctl->scatter_done = 0;
-            __threadfence();
-        }
-    }
-}
-
-// ---------------------------------------------------------------------------
-// marker initialisation on a jittered lattice (Sec. 2, Sec. 3.1)
+// marker sources for creation: the jittered lattice and caller arrays
 // ---------------------------------------------------------------------------
 // SplitMix64 (Steele, Lea & Flood 2014): output n of the generator seeded
 // with `seed`.
@@ -707,130 +1119,160 @@ __device__ double f0_value(const avl_f0* p, int nvdim, double L, double x, const
     for (int b = 0; b < p->nbeam; ++b) {
         double gb = p->beam_n[b];
         for (int d = 0; d < nvdim; ++d) {
-            const double s = p->beam_vth[b][d];
-            const double t = (v[d] - p->beam_u[b][d]) / s;
-            gb *= exp(-0.5 * t * t) / (sqrt(2.0 * M_PI) * s);
+            const double sd = p->beam_vth[b][d];
+            const double t = (v[d] - p->beam_u[b][d]) / sd;
+            gb *= exp(-0.5 * t * t) / (sqrt(2.0 * M_PI) * sd);
         }
         sum += gb;
     }
     return sum * pert;
 }
 
-template <typename T>
-__global__ void k_init1(const StepArgs* __restrict__ A, int s, int px, int pv, const avl_f0* __restrict__ f0,
-                        unsigned long long seed, double jitter)
-{
-    const SpDev& sp = A->sp[s];
-    const int cb = A->ctl->cur[s];
-    const int nx = sp.nx, nv = sp.nv[0], tv = sp.tv;
-    const int ppc = px * pv;
-    const long long per_bin = (long long)tv * nx * ppc;
-    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < sp.n;
-         k += (long long)gridDim.x * blockDim.x) {
-        const int b = (int)(k / per_bin);
-        const int rows = min(tv, nv - b * tv);
-        const long long kl = k - (long long)b * per_bin;
-        const int p = (int)(kl / ((long long)rows * nx));
-        const int rem = (int)(kl - (long long)p * rows * nx);
-        const int r = rem / nx;
-        const int i = rem - r * nx;
-        const int j = b * tv + r;
+struct MarkerIn {
+    double xi;   // position in cells
+    double v;
+    double f;
+    bool ok;
+};
+
+// lattice marker number k in generation order (velocity row j slowest, then
+// cell i, then sub-point p), which is nearly sorted by key; the jitter stream
+// uses the row-major marker number (cell * ppc + p)
+struct LatticeSrc {
+    const avl_f0* f0;
+    unsigned long long seed;
+    double jitter;
+    int s, px, pv;
+    __device__ MarkerIn get(const SpDev& sp, long long k) const
+    {
+        const int ppc = px * pv;
+        const long long per_row = (long long)sp.nx * ppc;
+        const int j = (int)(k / per_row);
+        const long long rem = k - (long long)j * per_row;
+        const int i = (int)(rem / ppc);
+        const int p = (int)(rem - (long long)i * ppc);
         const int a = p / pv, bv = p - a * pv;
-        const long long m = ((long long)i * nv + j) * ppc + p;
+        const long long m = ((long long)i * sp.nvflat + j) * ppc + p;
         const double J0 = (jitter_u01(seed, s, m, 0) - 0.5) * jitter;
         const double J1 = (jitter_u01(seed, s, m, 1) - 0.5) * jitter;
-        const double off = ((double)a + 0.5 + J0) / px;
-        const double x = ((double)i + off) * sp.dx;
-        const double frac_v = (double)r + ((double)bv + 0.5 + J1) / pv;   // rows above the bin base
-        double v[3] = {sp.vmin[0] + ((double)j + ((double)bv + 0.5 + J1) / pv) * sp.dv[0], 0.0, 0.0};
-        const double fl = f0_value(f0, 1, sp.nx * sp.dx, x, v);
-        Pos<T> pos;
-        if constexpr (sizeof(T) == 4) {
-            pos.c = i;
-            pos.o = (float)off;
-            if (pos.o >= 1.0f) pos.o = 0.99999994f;
-        } else {
-            pos.xi = (double)i + off;
-        }
-        pos.store(sp, cb, (int)k);
-        reinterpret_cast<T*>(sp.mv[cb][0])[k] = (T)(frac_v * sp.dv[0]);
-        reinterpret_cast<T*>(sp.mf[cb])[k] = (T)fl;
+        MarkerIn r;
+        r.xi = (double)i + ((double)a + 0.5 + J0) / px;
+        const double v[3] = {sp.vmin[0] + ((double)j + ((double)bv + 0.5 + J1) / pv) * sp.dv[0], 0.0, 0.0};
+        r.v = v[0];
+        r.f = f0_value(f0, 1, sp.nx * sp.dx, r.xi * sp.dx, v);
+        r.ok = true;
+        return r;
     }
+};
+
+struct ArraySrc {
+    const double* x;
+    const double* v;
+    const double* f;
+    __device__ MarkerIn get(const SpDev& sp, long long k) const
+    {
+        MarkerIn r;
+        const double L = sp.nx * sp.dx;
+        const double xv = x[k];
+        r.v = v[k];
+        r.f = f[k];
+        r.ok = (xv >= 0.0 && xv < L) && isfinite(r.v) && isfinite(r.f);
+        r.xi = r.ok ? xv / sp.dx : 0.0;
+        if (!r.ok) {
+            r.v = sp.vmin[0];
+            r.f = 0.0;
+        }
+        return r;
+    }
+};
+
+// count keys of a source chunk; reference key = key of the chunk's first marker
+template <typename Src>
+__global__ void __launch_bounds__(CNT_THREADS) k_src_count(const StepArgs* __restrict__ A, int s, Src src,
+                                                          int* kref_out, unsigned long long* bad)
+{
+    __shared__ int hist[HIST_S];
+    __shared__ int kref_s;
+    const SpDev& sp = A->sp[s];
+    const int c = blockIdx.x;
+    const long long beg = (long long)c * sp.M, end = min((long long)(c + 1) * sp.M, sp.n);
+    const int nv = sp.nvflat;
+    for (int i = threadIdx.x; i < HIST_S; i += CNT_THREADS) hist[i] = 0;
+    if (threadIdx.x == 0) {
+        kref_s = key_abs(src.get(sp, beg).v, sp.vmin[0], sp.inv_dv[0], nv);
+        kref_out[c] = kref_s;
+    }
+    __syncthreads();
+    const int kbase = kref_s - HIST_R;
+    unsigned nbad = 0;
+    for (long long b0 = beg; b0 < end; b0 += CNT_THREADS) {
+        const long long k = b0 + threadIdx.x;
+        const bool ok = k < end;
+        int code = 0;
+        if (ok) {
+            const MarkerIn mk = src.get(sp, k);
+            if (!mk.ok) nbad++;
+            code = rel_code(key_abs(mk.v, sp.vmin[0], sp.inv_dv[0], nv), kbase);
+        }
+        hist_add(hist, sp.far_cnt, code, ok);
+    }
+    if (nbad && bad) atomicAdd(bad, (unsigned long long)nbad);
+    __syncthreads();
+    for (int i = threadIdx.x; i < HIST_S; i += CNT_THREADS) sp.cnt[(size_t)c * HIST_S + i] = hist[i];
 }
 
-// ---------------------------------------------------------------------------
-// caller markers (FP64, arbitrary order) -> binned storage
-// ---------------------------------------------------------------------------
-__global__ void k_set_count1(const StepArgs* __restrict__ A, int s, long long n, const double* __restrict__ x,
-                             const double* __restrict__ v, const double* __restrict__ f,
-                             unsigned long long* bad)
+__global__ void __launch_bounds__(512) k_src_scan(const StepArgs* __restrict__ A, int s, const int* kref)
 {
     const SpDev& sp = A->sp[s];
-    const double L = sp.nx * sp.dx;
-    for (long long base = blockIdx.x * (long long)blockDim.x; base < n; base += (long long)gridDim.x * blockDim.x) {
-        const long long k = base + threadIdx.x;
-        int key = -1;
-        if (k < n) {
-            const double xv = x[k], vv = v[k], fv = f[k];
-            if (!(xv >= 0.0 && xv < L) || !isfinite(vv) || !isfinite(fv)) {
-                atomicAdd(bad, 1ull);
-            } else {
-                int row = (int)floor((vv - sp.vmin[0]) * sp.inv_dv[0]);
-                row = row < 0 ? 0 : (row >= sp.nv[0] ? sp.nv[0] - 1 : row);
-                key = row / sp.tv;
-            }
-        }
-        warp_aggregate_add(sp.hist, key);
-    }
+    scan_species(sp, kref, false, sp.KB[0], false);   // the new layout goes to buffer 0
 }
 
-template <typename T>
-__global__ void k_set_scatter1(const StepArgs* __restrict__ A, int s, long long n, const double* __restrict__ x,
-                               const double* __restrict__ v, const double* __restrict__ f)
+template <typename T, typename Src>
+__global__ void __launch_bounds__(PD_THREADS) k_src_scatter(const StepArgs* __restrict__ A, int s, Src src,
+                                                           const int* kref)
 {
+    __shared__ int scnt[HIST_S];
+    __shared__ unsigned nbad_s;
     const SpDev& sp = A->sp[s];
-    const int cb = A->ctl->cur[s];
-    const double L = sp.nx * sp.dx;
-    for (long long base = blockIdx.x * (long long)blockDim.x; base < n; base += (long long)gridDim.x * blockDim.x) {
-        const long long k = base + threadIdx.x;
-        int key = -1;
-        double xv = 0, vv = 0, fv = 0;
-        if (k < n) {
-            xv = x[k];
-            vv = v[k];
-            fv = f[k];
-            if ((xv >= 0.0 && xv < L) && isfinite(vv) && isfinite(fv)) {   // same filter as the count
-                int row = (int)floor((vv - sp.vmin[0]) * sp.inv_dv[0]);
-                row = row < 0 ? 0 : (row >= sp.nv[0] ? sp.nv[0] - 1 : row);
-                key = row / sp.tv;
-            }
+    const int c = blockIdx.x;
+    const int n_all = (int)sp.n;
+    const int beg = c * sp.M, end = min((c + 1) * sp.M, n_all);
+    const int nv = sp.nvflat;
+    const int kbase = kref[c] - HIST_R;
+    for (int i = threadIdx.x; i < HIST_S; i += PD_THREADS) scnt[i] = 0;
+    if (threadIdx.x == 0) nbad_s = 0;
+    __syncthreads();
+    const int* offs = sp.offs + (size_t)c * HIST_S;
+    for (int base = beg; base < end; base += PD_THREADS * MPT) {
+        const int g0 = base + threadIdx.x * MPT;
+        int code[MPT], dst[MPT];
+#pragma unroll
+        for (int m = 0; m < MPT; ++m) {
+            const int k = g0 + m;
+            code[m] = k < end ? rel_code(key_abs(src.get(sp, k).v, sp.vmin[0], sp.inv_dv[0], nv), kbase) : -1;
         }
-        const int d = warp_aggregate_add(sp.cursor, key);
-        if (key >= 0) {
-            const double xi = xv / sp.dx;
-            Pos<T> pos;
-            if constexpr (sizeof(T) == 4) {
-                double c = floor(xi);
-                double o = xi - c;
-                int ci = (int)c;
-                if (ci >= sp.nx) {
-                    ci -= sp.nx;
+        assign_slots(code, scnt, offs, sp.far_cur, dst);
+#pragma unroll
+        for (int m = 0; m < MPT; ++m) {
+            const int k = g0 + m;
+            if (k < end) {
+                const MarkerIn mk = src.get(sp, k);
+                const int d = dst[m];
+                if ((unsigned)d < (unsigned)n_all) {
+                    const int c2 = chunk_of(d, sp.div_m, sp.div_l);
+                    const Pos<T> p = pos_from_cells<T>(mk.xi, sp.nx);
+                    p.store(sp, 0, d);
+                    const double vref = sp.vmin[0] + (double)sp.KB[0][c2] * sp.dv[0];
+                    reinterpret_cast<T*>(sp.mv[0][0])[d] = (T)(mk.v - vref);
+                    reinterpret_cast<T*>(sp.mf[0])[d] = (T)mk.f;
+                } else {
+                    atomicAdd(&nbad_s, 1u);
                 }
-                pos.c = ci;
-                pos.o = (float)o;
-                if (pos.o >= 1.0f) {
-                    pos.o = 0.0f;
-                    pos.c = (ci + 1) % sp.nx;
-                }
-            } else {
-                pos.xi = xi < sp.nx ? xi : xi - sp.nx;
             }
-            pos.store(sp, cb, d);
-            const double vref = sp.vmin[0] + (double)key * sp.tv * sp.dv[0];
-            reinterpret_cast<T*>(sp.mv[cb][0])[d] = (T)(vv - vref);
-            reinterpret_cast<T*>(sp.mf[cb])[d] = (T)fv;
         }
     }
+    __syncthreads();
+    if (threadIdx.x == 0 && nbad_s) atomicOr(&A->ctl->err, ERR_CAPACITY);
 }
 
 template <typename T>
@@ -838,19 +1280,14 @@ __global__ void k_get1(const StepArgs* __restrict__ A, int s, double* __restrict
                        double* __restrict__ f)
 {
     const SpDev& sp = A->sp[s];
-    const int b = blockIdx.x;
+    const int c = blockIdx.x;
     const int cb = A->ctl->cur[s];
-    const int beg = sp.bin_start[cb][b], end = sp.bin_start[cb][b + 1];
-    const double vref = sp.vmin[0] + (double)b * sp.tv * sp.dv[0];
+    const int beg = c * sp.M, end = (int)min((long long)(c + 1) * sp.M, sp.n);
+    const double vref = sp.vmin[0] + (double)sp.KB[cb][c] * sp.dv[0];
     for (int k = beg + threadIdx.x; k < end; k += blockDim.x) {
         Pos<T> pos;
         pos.load(sp, cb, k);
-        double xi;
-        if constexpr (sizeof(T) == 4)
-            xi = (double)pos.c + (double)pos.o;
-        else
-            xi = pos.xi;
-        if (x) x[k] = xi * sp.dx;
+        if (x) x[k] = pos.cells() * sp.dx;
         if (v) v[k] = vref + (double)reinterpret_cast<const T*>(sp.mv[cb][0])[k];
         if (f) f[k] = (double)reinterpret_cast<const T*>(sp.mf[cb])[k];
     }
@@ -886,26 +1323,38 @@ __global__ void k_getf(const T* __restrict__ fg, const T* __restrict__ ng, int n
 static int max_pd_smem(const StepArgs& h)
 {
     size_t m = 0;
-    for (int s = 0; s < h.ns; ++s) m = std::max(m, pd1_smem_bytes(h.sp[s], h.prec));
-    return (int)m;
+    for (int s = 0; s < h.ns; ++s)
+        if (h.sp[s].nchunk) m = std::max(m, pd1_smem_bytes(h.sp[s], h.prec));
+    return (int)std::max<size_t>(m, 1024);
 }
 
-// dynamic shared-memory limits, set once per context (outside any capture)
+// dynamic shared-memory limit of the deposit kernel, set whenever the chunk
+// layout changes (outside any stream capture)
 cudaError_t configure_vhs1(const StepArgs& h)
 {
     const int smem = max_pd_smem(h);
-    if (h.prec == AVL_FP32)
-        return cudaFuncSetAttribute(k_pd1<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (h.prec == AVL_FP32) return cudaFuncSetAttribute(k_pd1<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     return cudaFuncSetAttribute(k_pd1<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
 }
 
-cudaError_t launch_pd1(const StepArgs& h, const StepArgs* d, int push, cudaStream_t st)
+cudaError_t launch_count1(const StepArgs& h, const StepArgs* d, int mode, cudaStream_t st)
 {
+    if (h.nchunk_total == 0) return cudaSuccess;
+    if (h.prec == AVL_FP32)
+        k_count1<float><<<h.nchunk_total, CNT_THREADS, 0, st>>>(d, mode);
+    else
+        k_count1<double><<<h.nchunk_total, CNT_THREADS, 0, st>>>(d, mode);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pd1(const StepArgs& h, const StepArgs* d, int mode, cudaStream_t st)
+{
+    if (h.nchunk_total == 0) return cudaSuccess;
     const int smem = max_pd_smem(h);
     if (h.prec == AVL_FP32)
-        k_pd1<float><<<h.nbins_total, PD_THREADS, smem, st>>>(d, push);
+        k_pd1<float><<<h.nchunk_total, PD_THREADS, smem, st>>>(d, mode);
     else
-        k_pd1<double><<<h.nbins_total, PD_THREADS, smem, st>>>(d, push);
+        k_pd1<double><<<h.nchunk_total, PD_THREADS, smem, st>>>(d, mode);
     return cudaGetLastError();
 }
 
@@ -918,52 +1367,44 @@ cudaError_t launch_fin1(const StepArgs& h, const StepArgs* d, int all_species, c
     return cudaGetLastError();
 }
 
-cudaError_t launch_sort1(const StepArgs& h, const StepArgs* d, cudaStream_t st)
+// source -> sorted layout in buffer 0 of species s; kref_tmp holds nchunk ints
+template <typename Src>
+static cudaError_t source_to_layout(const StepArgs& h, const StepArgs* d, int s, Src src, int* kref_tmp,
+                                    unsigned long long* bad, cudaStream_t st)
 {
-    if (h.prec == AVL_FP32) {
-        k_sort_count1<float><<<h.nbins_total, SORT_THREADS, 0, st>>>(d);
-        k_sort_scan<<<1, 1024, 0, st>>>(d, -1);
-        k_scatter1<float><<<h.nbins_total, SORT_THREADS, 0, st>>>(d);
-    } else {
-        k_sort_count1<double><<<h.nbins_total, SORT_THREADS, 0, st>>>(d);
-        k_sort_scan<<<1, 1024, 0, st>>>(d, -1);
-        k_scatter1<double><<<h.nbins_total, SORT_THREADS, 0, st>>>(d);
-    }
+    const SpDev& sp = h.sp[s];
+    k_src_count<Src><<<sp.nchunk, CNT_THREADS, 0, st>>>(d, s, src, kref_tmp, bad);
+    k_src_scan<<<1, 512, 0, st>>>(d, s, kref_tmp);
+    if (h.prec == AVL_FP32)
+        k_src_scatter<float, Src><<<sp.nchunk, PD_THREADS, 0, st>>>(d, s, src, kref_tmp);
+    else
+        k_src_scatter<double, Src><<<sp.nchunk, PD_THREADS, 0, st>>>(d, s, src, kref_tmp);
     return cudaGetLastError();
 }
 
 cudaError_t launch_init1(const StepArgs& h, const StepArgs* d, int s, const int lattice[4], const avl_f0* f0_dev,
                          unsigned long long seed, double jitter, cudaStream_t st)
 {
-    const long long n = h.sp[s].n;
-    const int blocks = (int)std::min<long long>((n + 255) / 256, 152LL * 16);
-    if (h.prec == AVL_FP32)
-        k_init1<float><<<blocks, 256, 0, st>>>(d, s, lattice[0], lattice[1], f0_dev, seed, jitter);
-    else
-        k_init1<double><<<blocks, 256, 0, st>>>(d, s, lattice[0], lattice[1], f0_dev, seed, jitter);
-    return cudaGetLastError();
+    const LatticeSrc src{f0_dev, seed, jitter, s, lattice[0], lattice[1]};
+    // the kmm table (2 ints per chunk) holds the source references meanwhile
+    return source_to_layout(h, d, s, src, h.sp[s].kmm, nullptr, st);
 }
 
-cudaError_t launch_set1(const StepArgs& h, const StepArgs* d, int s, long long n, const double* x, const double* v,
+cudaError_t launch_set1(const StepArgs& h, const StepArgs* d, int s, long long, const double* x, const double* v,
                         const double* f, unsigned long long* bad, cudaStream_t st)
 {
-    const int blocks = (int)std::min<long long>((n + 255) / 256, 152LL * 16);
-    k_set_count1<<<blocks, 256, 0, st>>>(d, s, n, x, v, f, bad);
-    k_sort_scan<<<1, 1024, 0, st>>>(d, s);
-    if (h.prec == AVL_FP32)
-        k_set_scatter1<float><<<blocks, 256, 0, st>>>(d, s, n, x, v, f);
-    else
-        k_set_scatter1<double><<<blocks, 256, 0, st>>>(d, s, n, x, v, f);
-    return cudaGetLastError();
+    const ArraySrc src{x, v, f};
+    return source_to_layout(h, d, s, src, h.sp[s].kmm, bad, st);
 }
 
 cudaError_t launch_get1(const StepArgs& h, const StepArgs* d, int s, double* x, double* v, double* f,
                         cudaStream_t st)
 {
+    if (h.sp[s].nchunk == 0) return cudaSuccess;
     if (h.prec == AVL_FP32)
-        k_get1<float><<<h.sp[s].nbins, 256, 0, st>>>(d, s, x, v, f);
+        k_get1<float><<<h.sp[s].nchunk, 256, 0, st>>>(d, s, x, v, f);
     else
-        k_get1<double><<<h.sp[s].nbins, 256, 0, st>>>(d, s, x, v, f);
+        k_get1<double><<<h.sp[s].nchunk, 256, 0, st>>>(d, s, x, v, f);
     return cudaGetLastError();
 }
 

@@ -76,15 +76,15 @@ SPECIES2 = lambda nv: [dict(q=-1.0, m=1.0, nv=(nv,), vmin=(-3.0,), vmax=(3.0,)),
 
 
 @pytest.mark.parametrize("prec", [0, 1], ids=["fp64", "fp32"])
-@pytest.mark.parametrize("nx,nv,n,tv", [(64, 96, 20011, 4), (48, 40, 5003, 3), (64, 96, 20011, 0),
-                                         (4, 2, 7, 1)])
-def test_step_parity_random_markers(A, monkeypatch, prec, nx, nv, n, tv):
+@pytest.mark.parametrize("nx,nv,n,chunk", [(64, 96, 20011, 1024), (48, 40, 5003, 640), (64, 96, 20011, 0),
+                                            (4, 2, 7, 0), (32, 64, 30000, 64)])
+def test_step_parity_random_markers(A, monkeypatch, prec, nx, nv, n, chunk):
     """Random marker states (some beyond the velocity grid, values over 12
-    decades), several bins and a ragged last block, power-of-two (FFT) and
-    other (DFT) grids; one set + refresh and three steps, each compared from
-    identical states."""
-    if tv:
-        monkeypatch.setenv("AVL_TV", str(tv))
+    decades), many chunks and a ragged last chunk, power-of-two (FFT) and
+    other (DFT) grids; one set + refresh and three steps (each re-sorting the
+    markers), each compared from identical states."""
+    if chunk:
+        monkeypatch.setenv("AVL_CHUNK_M", str(chunk))
     L, dt = 7.3, 0.07
     species = SPECIES2(nv)
     sim, orc = make_pair(A, nx, L, dt, species, prec)
@@ -173,9 +173,9 @@ def test_landau_free_running_fp64(A):
 
 def test_strong_field_resort_and_overflow(A, monkeypatch):
     """A light, strongly perturbed species: markers cross many velocity rows
-    per step, exercising the re-sort and the out-of-window deposit; parity
-    holds at every step."""
-    monkeypatch.setenv("AVL_TV", "2")
+    per step, exercising far keys in the re-sort and the out-of-window
+    deposit; parity holds at every step."""
+    monkeypatch.setenv("AVL_CHUNK_M", "256")
     nx, nv, L, dt = 32, 64, 4.0, 0.2
     species = [dict(q=-1.0, m=0.05, nv=(nv,), vmin=(-4.0,), vmax=(4.0,))]
     for prec in (0, 1):
@@ -188,7 +188,7 @@ def test_strong_field_resort_and_overflow(A, monkeypatch):
             orc.step(1)
             compare_grids(sim, orc, TOL[prec], f"prec {prec} step {k}")
         st = sim.get_stats()
-        assert st[0, 1] > 0          # re-sorted at least once
+        assert st[0, 1] == 6         # every pushed step re-sorts
         sim.synchronize()
 
 
