@@ -33,10 +33,19 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-KERNEL_NAMES = ["k_count1", "k_pd1", "k_fin1", "k_field"]
-LAUNCHES_PER_STEP = 4   # k_count1 (+ scan in its last CTA), k_pd1, k_fin1, k_field
-BYTES_PER_MARKER_ALGO = {"fp32": 20.0, "fp64": 40.0}      # read x, v, f; write x, v
-BYTES_PER_MARKER_LAYOUT = {"fp32": 32.0, "fp64": 48.0}    # stored layout: read and re-sorted write of all fields
+# per velocity dimension: kernel classes of avl_profile_steps, launches per
+# step, algorithmic bytes per marker of the push + deposit kernel (read x,
+# v, f and write x, v_x) and the bytes of the stored layout it moves
+KERNEL_NAMES = {1: ["k_count1", "k_pd1", "k_fin1", "k_field"],
+                3: ["k_sort3", "k_pd3", "k_fin3", "k_field"]}
+LAUNCHES_PER_STEP = {1: 4,   # k_pd1 (in place and re-sorting instances), k_fin1, k_field
+                     3: 4}   # k_pd3, k_fin3, k_field, k_sort3
+BYTES_PER_MARKER_ALGO = {(1, "fp32"): 20.0, (1, "fp64"): 40.0,    # 1d1v: read x, v, f; write x, v
+                         (3, "fp32"): 28.0, (3, "fp64"): 56.0}    # 1d3v: read x, vx, vy, vz, f; write x, vx
+BYTES_PER_MARKER_LAYOUT = {(1, "fp32"): 32.0, (1, "fp64"): 48.0,  # read and re-sorted write of all fields
+                           (3, "fp32"): 36.0, (3, "fp64"): 64.0}  # read all fields, write cell, off, vx in place
+KERNEL_DESC = {1: "k_pd1 (gather + push + VHS deposit + re-sorted write)",
+               3: "k_pd3 (gather + push + x-sorted VHS deposit per pencil, in place)"}
 
 
 def parse():
@@ -45,7 +54,7 @@ def parse():
     p.add_argument("--steps", type=int, default=2000)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    p.add_argument("--workload", choices=["two_stream", "landau"], default="two_stream")
+    p.add_argument("--workload", choices=["two_stream", "landau", "bump_on_tail"], default="two_stream")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--nv", type=int, default=0, help="velocity cells (profiling of a smaller case)")
@@ -56,7 +65,12 @@ def workload(name, nv=0):
     from paper_1804_03901_gb300 import inputs
     if name == "two_stream":
         return inputs.two_stream(nv=nv) if nv else inputs.two_stream()
+    if name == "bump_on_tail":
+        return inputs.bump_on_tail(nv=nv) if nv else inputs.bump_on_tail()
     return inputs.landau(nv=nv) if nv else inputs.landau()
+
+
+SAMPLE_FRACTION = {"two_stream": 1.0 / 64, "bump_on_tail": 1.0 / 256, "landau": 1.0}
 
 
 def markers_of(w):
@@ -81,22 +95,27 @@ def peaks():
     return 6800.0, "fallback"
 
 
-def kernel_source_hash():
+KERNEL_SOURCES = {1: ("k_vhs1.cu", "common.cuh", "resort.cuh", "ptx.cuh", "avl_internal.cuh"),
+                  3: ("k_vhs3.cu", "common.cuh", "avl_internal.cuh")}
+
+
+def kernel_source_hash(nvdim):
+    """Hash of the sources the push + deposit kernel of nvdim is built from."""
     h = hashlib.sha256()
-    for f in ("k_vhs1.cu", "avl_internal.cuh", "ptx.cuh"):  # the dominant kernel's sources
+    for f in KERNEL_SOURCES[nvdim]:
         h.update(open(os.path.join(ROOT, "paper_1804_03901_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(workload_name, prec):
-    """DRAM bytes per marker of k_pd1 from the committed ncu summary, if it
-    was taken on the current kernel source."""
-    path = os.path.join(ROOT, "profiles", "k_pd1_traffic.json")
+def recorded_traffic(workload_name, prec, nvdim):
+    """DRAM bytes per marker of the push + deposit kernel from the committed
+    ncu summary, if it was taken on the current kernel source."""
+    path = os.path.join(ROOT, "profiles", "pd_traffic.json")
     if not os.path.exists(path):
         return None
     d = json.load(open(path))
     rec = d.get(f"{workload_name}:{prec}")
-    if not rec or rec.get("source_hash") != kernel_source_hash():
+    if not rec or rec.get("source_hash") != kernel_source_hash(nvdim):
         return None
     return float(rec["dram_bytes_per_marker"])
 
@@ -193,7 +212,7 @@ def run_reference(args):
     if rank != 0:
         return
     w = workload(args.workload, args.nv)
-    frac = 1.0 / 64 if args.workload == "two_stream" else 1.0
+    frac = SAMPLE_FRACTION[args.workload]
     cpu_oracle_rate(w, sample_fraction=frac, steps=max(1, args.warmup))   # warm-up (page-in)
     rate, nmark, done, el = cpu_oracle_rate(w, sample_fraction=frac, steps=args.steps)
     sample = (f"FP64 oracle, 1 thread, {done} steps of the {w['name']} workload with a random "
@@ -268,17 +287,20 @@ def run_ours(args):
     hbm, peak_kind = peaks()
     pd_ms = kms[1] / args.steps
     prec = w["precision"]
-    achieved = nmark * BYTES_PER_MARKER_ALGO[prec] / (pd_ms / 1e3) / 1e9
-    traffic_pm = recorded_traffic(w["name"], prec)
+    nvd = w["nvdim"]
+    algo, lay = BYTES_PER_MARKER_ALGO[(nvd, prec)], BYTES_PER_MARKER_LAYOUT[(nvd, prec)]
+    achieved = nmark * algo / (pd_ms / 1e3) / 1e9
+    traffic_pm = recorded_traffic(w["name"], prec, nvd)
+    names = KERNEL_NAMES[nvd]
     roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
                 "traffic": traffic_pm * nmark if traffic_pm else None,
-                "kernel": "k_pd1 (gather + push + VHS deposit + re-sorted write)",
-                "algorithmic_bytes_per_marker": BYTES_PER_MARKER_ALGO[prec],
-                "layout_bytes_per_marker": BYTES_PER_MARKER_LAYOUT[prec],
-                "frac_layout_bytes": nmark * BYTES_PER_MARKER_LAYOUT[prec] / (pd_ms / 1e3) / 1e9 / hbm,
+                "kernel": KERNEL_DESC[nvd],
+                "algorithmic_bytes_per_marker": algo,
+                "layout_bytes_per_marker": lay,
+                "frac_layout_bytes": nmark * lay / (pd_ms / 1e3) / 1e9 / hbm,
                 "peak_kind": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else peak_kind,
-                "kernel_ms_per_step": {k: float(v / args.steps) for k, v in zip(KERNEL_NAMES, kms)},
-                "kernel_share": {k: float(v / kms.sum()) for k, v in zip(KERNEL_NAMES, kms)}}
+                "kernel_ms_per_step": {k: float(v / args.steps) for k, v in zip(names, kms)},
+                "kernel_share": {k: float(v / kms.sum()) for k, v in zip(names, kms)}}
 
     # end to end through the C ABI with host buffers
     e2e = None
@@ -287,7 +309,7 @@ def run_ours(args):
         for s in range(len(w["species"])):
             x, v, f = sim.get_markers(s)
             hx.append(torch.from_numpy(x).pin_memory())
-            hv.append(torch.from_numpy(np.ascontiguousarray(v[0])).pin_memory())
+            hv.append(torch.from_numpy(np.ascontiguousarray(v[:nvd])).pin_memory())
             hf.append(torch.from_numpy(f).pin_memory())
         diag = torch.zeros(3 + 3 * len(w["species"]), dtype=torch.float64).pin_memory()
         h2d = sum(t.numel() * 8 for t in hx + hv + hf)
@@ -307,9 +329,11 @@ def run_ours(args):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        rate, nm, done, el = cpu_oracle_rate(w, budget_s=12.0)
+        frac = 1.0 if args.workload == "two_stream" else SAMPLE_FRACTION[args.workload]
+        rate, nm, done, el = cpu_oracle_rate(w, budget_s=12.0, sample_fraction=frac)
+        what = "full steps" if frac == 1.0 else f"steps of a random {frac:.4g} marker subsample (full grids)"
         cpu = {"value": rate, "unit": "marker-steps/s", "cores": 1, "kind": "oracle",
-               "sample": f"{done} full steps of the {w['name']} workload ({nm} markers), FP64, 1 thread, "
+               "sample": f"{done} {what} of the {w['name']} workload ({nm} markers), FP64, 1 thread, "
                          f"{el:.1f} s"}
 
     if rank == 0:
@@ -319,11 +343,13 @@ def run_ours(args):
                 "dtype": "f32" if prec == "fp32" else "f64", "data": "synthetic",
                 "config": {"workload": w["name"], "markers": nmark, "species": len(w["species"]),
                            "steps_in_run": w["steps"], "timed_from": "t = 0",
-                           "l2": "inputs larger than L2 (markers 16 B each, 268 MB per step read)"
-                           if args.workload == "two_stream" else "small workload (fits in L2)",
+                           "l2": {"two_stream": "inputs larger than L2 (markers 16 B each, 268 MB per step read)",
+                                  "bump_on_tail": "inputs larger than L2 (markers 24 B each, 3.2 GB per step read)",
+                                  "landau": "small workload (fits in L2)"}[args.workload],
                            "parallelism": "single GPU" if world == 1 else f"{world} independent replicas"},
-                "roofline": roofline, "clocks": clk, "gpu_launches": LAUNCHES_PER_STEP * args.steps,
-                "out_of_window_runs_last_step": [int(x) for x in stats[:, 0]], "e2e": e2e,
+                "roofline": roofline, "clocks": clk, "gpu_launches": LAUNCHES_PER_STEP[nvd] * args.steps,
+                ("out_of_window_runs_last_step" if nvd == 1 else "movers_last_step"): [int(x) for x in stats[:, 0]],
+                "resort_steps": [int(x) for x in stats[:, 1]], "e2e": e2e,
                 "cpu_baseline": cpu}
         print(json.dumps(line), flush=True)
     sim.close()

@@ -58,8 +58,13 @@ typedef struct avl_ctx avl_ctx;
 /* Simulation domain (Sec. 3.1, Sec. 3.3 numerical parameters).
  * precision AVL_FP64: markers, deposit and grid in FP64.
  * precision AVL_FP32: marker position = int32 cell + FP32 offset, velocity
- *   and value in FP32, deposit sums compensated in FP32; the Poisson solve,
- *   the charge-neutral k = 0 handling and the diagnostics stay FP64. */
+ *   and value in FP32, deposit sums compensated in FP32 (1d1v; 1d3v sums
+ *   plain FP32); the Poisson solve, the charge-neutral k = 0 handling and
+ *   the diagnostics stay FP64.
+ * nvdim = 3 (Sec. 2 with three velocity dimensions, no magnetic field: the
+ *   field accelerates v_x only) needs nx <= 1024 (FP32) or nx <= 512 (FP64),
+ *   nv[0] in [2, 1024], nv[1], nv[2] in [2, 4096] and fewer than 2^31 grid
+ *   cells; all species of a context share nvdim. */
 typedef struct {
     int32_t nvdim;          /* 1 (1d1v) or 3 (1d3v, no magnetic field) */
     int32_t nx;             /* cells in x, >= 4 */
@@ -161,10 +166,12 @@ avl_status avl_get_E(avl_ctx* ctx, double* E, int32_t on_device);
  * Returns AVL_ENUMERIC if any value is NaN or Inf. */
 avl_status avl_get_diag(avl_ctx* ctx, double* out);
 
-/* Counters (host buffer of 4 int64 per species): runs of markers that
- * deposited through the out-of-window path in the last step, steps that
- * re-sorted this species so far (every pushed step does), 0 (reserved),
- * steps so far. */
+/* Counters (host buffer of 4 int64 per species): [0] 1d1v: runs of markers
+ * that deposited through the out-of-window path in the last step; 1d3v:
+ * markers whose v_x dual row had left their segment's in the last step;
+ * [1] steps that re-sorted this species so far; [2] 1d1v: markers outside
+ * their chunk's best window at the last decision, 1d3v: 0; [3] steps so
+ * far. */
 avl_status avl_get_stats(avl_ctx* ctx, int64_t* out);
 
 /* Stand-alone spectral Poisson solve (Sec. 3.1, Eq. 5 / Eq. 6a-c): E from
@@ -202,9 +209,9 @@ avl_status avl_field_solve_noalloc(int32_t nx, double L, double poisson_const, i
 /* Per-kernel timing (the paper's time breakdown, Sec. 3.2): advance nsteps
  * steps exactly as avl_step does, but launched kernel by kernel with CUDA
  * events recorded on the context stream around each kernel; writes the summed
- * milliseconds of each kernel class into ms[0..3] = {key count + slot scan,
- * push + deposit + re-sorted write, finalize (f, moment, diagnostics), field
- * (Poisson)}.  Blocks until done.
+ * milliseconds of each kernel class into ms[0..3] = {1d1v: key count + slot
+ * scan, 1d3v: pencil re-sort; push + deposit (+ re-sorted write in 1d1v);
+ * finalize (f, moment, diagnostics); field (Poisson)}.  Blocks until done.
  * Errors: AVL_EINVAL (nkernels < 4 or ms NULL), AVL_ESTATE as avl_step. */
 avl_status avl_profile_steps(avl_ctx* ctx, int32_t nsteps, double* ms, int32_t nkernels);
 

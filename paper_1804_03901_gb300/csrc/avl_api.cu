@@ -209,6 +209,66 @@ avl_status plan_layout(avl_ctx* c, int s, long long n)
     return AVL_OK;
 }
 
+// 1d3v layout of species s for n markers: marker storage (two buffers, the
+// re-sort writes the other), the segment tables of both buffers and the
+// bucket counts of the creation path.  Renumbers the pencil blocks of all
+// species and invalidates the step graph.
+avl_status plan_layout3(avl_ctx* c, int s, long long n)
+{
+    SpDev& sp = c->h.sp[s];
+    AVL_CUDA(c, cudaStreamSynchronize(c->st));
+    free_layout(c, s);
+    sp.n = 0;
+    sp.npen = 0;
+    const int npen = (sp.nv[1] + 1) * (sp.nv[2] + 1);
+    const int nkey = sp.nv[0] + 1;
+    const size_t pb = prec_bytes(c->h.prec);
+    const size_t nn = ((size_t)n + 63) / 64 * 64;
+    auto grab = [&](void** p, size_t bytes, bool zero) -> cudaError_t {
+        *p = nullptr;
+        cudaError_t e = cudaMalloc(p, std::max<size_t>(bytes, 16));
+        if (e) return e;
+        c->layout[s].push_back(*p);
+        return zero ? cudaMemsetAsync(*p, 0, std::max<size_t>(bytes, 16), c->st) : cudaSuccess;
+    };
+    cudaError_t e = cudaSuccess;
+    for (int b = 0; b < 2 && !e; ++b) {
+        e = grab(&sp.mx[b], pb * nn, true);
+        sp.moff[b] = nullptr;
+        if (!e && c->h.prec == AVL_FP32) {
+            void* q = nullptr;
+            e = grab(&q, 4 * nn, true);
+            sp.moff[b] = (float*)q;
+        }
+        for (int d = 0; d < 3 && !e; ++d) e = grab(&sp.mv[b][d], pb * nn, true);
+        if (!e) e = grab(&sp.mf[b], pb * nn, true);
+        void* sg = nullptr;
+        if (!e) e = grab(&sg, (size_t)npen * (nkey + 1) * 4, true);
+        sp.seg[b] = (int*)sg;
+    }
+    void* kc = nullptr;
+    if (!e) e = grab(&kc, ((size_t)npen * nkey + 1) * 4, true);
+    if (e) {
+        free_layout(c, s);
+        return cuda_fail(c, e, "cudaMalloc(markers)");
+    }
+    sp.kcount = (int*)kc;
+    sp.npen = npen;
+    sp.nkey = nkey;
+    sp.n = n;
+    int base = 0;
+    for (int q = 0; q < c->ns; ++q) {
+        c->h.sp[q].pen_base = base;
+        base += c->h.sp[q].npen;
+    }
+    c->h.npen_total = base;
+    if (c->gexec) {
+        cudaGraphExecDestroy(c->gexec);
+        c->gexec = nullptr;
+    }
+    return AVL_OK;
+}
+
 // a freshly created layout: buffer 0, key counts in buffer 0, no re-sort
 // pending; the scratch counts of the creation path start at zero
 avl_status set_cur_zero(avl_ctx* c, int s)
@@ -222,8 +282,14 @@ avl_status set_cur_zero(avl_ctx* c, int s)
     const int one = 1;
     AVL_CUDA(c, cudaMemcpyAsync(&c->d_ctl->prev_sorted[s], &one, sizeof(int), cudaMemcpyHostToDevice, c->st));
     const SpDev& sp = c->h.sp[s];
-    AVL_CUDA(c, cudaMemsetAsync(sp.far_cnt[0], 0, (size_t)sp.nvflat * 4, c->st));
-    AVL_CUDA(c, cudaMemsetAsync(sp.far_cnt[1], 0, (size_t)sp.nvflat * 4, c->st));
+    if (sp.nvdim == 1) {
+        AVL_CUDA(c, cudaMemsetAsync(sp.far_cnt[0], 0, (size_t)sp.nvflat * 4, c->st));
+        AVL_CUDA(c, cudaMemsetAsync(sp.far_cnt[1], 0, (size_t)sp.nvflat * 4, c->st));
+    } else {
+        const unsigned long long z = 0;
+        AVL_CUDA(c, cudaMemcpyAsync(&c->d_ctl->movers[s], &z, 8, cudaMemcpyHostToDevice, c->st));
+        AVL_CUDA(c, cudaMemcpyAsync(&c->d_ctl->far_movers[s], &z, 8, cudaMemcpyHostToDevice, c->st));
+    }
     AVL_CUDA(c, cudaStreamSynchronize(c->st));
     return AVL_OK;
 }
@@ -232,6 +298,7 @@ avl_status set_cur_zero(avl_ctx* c, int s)
 // count kernel recounts the current state of every species with markers)
 avl_status clear_far_counts(avl_ctx* c)
 {
+    if (c->h.nvdim == 3) return AVL_OK;
     for (int s = 0; s < c->ns; ++s) {
         const SpDev& sp = c->h.sp[s];
         AVL_CUDA(c, cudaMemsetAsync(sp.far_cnt[0], 0, (size_t)sp.nvflat * 4, c->st));
@@ -243,6 +310,12 @@ avl_status clear_far_counts(avl_ctx* c)
 // reconstruct every species with markers, then rho and E (no push)
 avl_status refresh(avl_ctx* c)
 {
+    if (c->h.nvdim == 3) {
+        AVL_CUDA(c, launch_pd3(c->h, c->d_args, 0, c->st));
+        AVL_CUDA(c, launch_fin3(c->h, c->d_args, 1, c->st));
+        AVL_CUDA(c, launch_field(c->h, c->d_args, 0, c->st));
+        return AVL_OK;
+    }
     avl_status st = clear_far_counts(c);
     if (st) return st;
     AVL_CUDA(c, launch_count1(c->h, c->d_args, c->st));
@@ -257,6 +330,13 @@ avl_status refresh(avl_ctx* c)
 // slots for the next step
 avl_status enqueue_step(avl_ctx* c)
 {
+    if (c->h.nvdim == 3) {
+        AVL_CUDA(c, launch_pd3(c->h, c->d_args, 1, c->st));
+        AVL_CUDA(c, launch_fin3(c->h, c->d_args, 0, c->st));
+        AVL_CUDA(c, launch_field(c->h, c->d_args, 1, c->st));
+        AVL_CUDA(c, launch_sort3(c->h, c->d_args, c->st));
+        return AVL_OK;
+    }
     AVL_CUDA(c, launch_pd1(c->h, c->d_args, 1, c->st));
     AVL_CUDA(c, launch_fin1(c->h, c->d_args, 0, c->st));
     AVL_CUDA(c, launch_field(c->h, c->d_args, 1, c->st));
@@ -298,6 +378,86 @@ avl_status read_errors(avl_ctx* c)
     AVL_CUDA(c, cudaStreamSynchronize(c->st));
     if (err & ERR_TIMEOUT) return fail(c, AVL_ETIMEOUT, "a bounded device-side wait gave up");
     if (err & ERR_NUMERIC) return fail(c, AVL_ENUMERIC, "NaN or Inf in the field or diagnostics");
+    if (err & ERR_CAPACITY) return fail(c, AVL_ECUDA, "internal check of the marker layout failed");
+    return AVL_OK;
+}
+
+// grids and tables of a 1d3v species (the markers come with plan_layout3):
+// f, the two deposit accumulators, |v|^2 per velocity cell, the finalize
+// partial sums (FIN3_X columns x rq velocity cells per block) and the shift
+// tables the field kernel writes for every species
+avl_status create_species3(avl_ctx* c, int s, const avl_species& p, int& fin_base)
+{
+    StepArgs& h = c->h;
+    SpDev& sp = h.sp[s];
+    const int nx = c->dom.nx;
+    const size_t pb = prec_bytes(h.prec);
+    sp.nvdim = 3;
+    sp.nx = nx;
+    sp.nvflat = 1;
+    for (int d = 0; d < 3; ++d) {
+        sp.nv[d] = p.nv[d];
+        sp.nvflat *= p.nv[d];
+        sp.vmin[d] = p.vmin[d];
+        sp.dv[d] = (p.vmax[d] - p.vmin[d]) / p.nv[d];
+        sp.inv_dv[d] = 1.0 / sp.dv[d];
+    }
+    sp.mobile = p.mobile ? 1 : 0;
+    sp.q = p.q;
+    sp.m = p.m;
+    sp.qm = p.q / p.m;
+    sp.dx = c->dom.L / nx;
+    sp.qm_dt = sp.qm * c->dom.dt;
+    sp.dt_dx = c->dom.dt / sp.dx;
+    sp.nchunk = 0;
+    sp.npen = 0;
+    sp.n = 0;
+    sp.nxb = (nx + FIN3_X - 1) / FIN3_X;
+    const int nrq0 = std::max(1, (4 * c->num_sms + c->ns * sp.nxb - 1) / (c->ns * sp.nxb));
+    int rq = std::max(1, (sp.nvflat + nrq0 - 1) / nrq0);
+    const int rq_env = env_int("AVL_RQ", 0);
+    if (rq_env > 0) rq = std::min(rq_env, sp.nvflat);
+    sp.rq = rq;
+    sp.nrq = (sp.nvflat + rq - 1) / rq;
+    sp.nfin = sp.nxb * sp.nrq;
+    sp.fin_base = fin_base;
+    fin_base += sp.nfin;
+    h.nfin_total = fin_base;
+    const size_t cells = (size_t)nx * sp.nvflat;
+    void *pf, *pa0, *pa1, *pv2, *pr, *pd, *p5, *p6;
+    cudaError_t e;
+    if ((e = dalloc(c, &pf, cells * pb, true)) || (e = dalloc(c, &pa0, 2 * cells * pb, true)) ||
+        (e = dalloc(c, &pa1, 2 * cells * pb, true)) || (e = dalloc(c, &pv2, (size_t)sp.nvflat * pb, false)) ||
+        (e = dalloc(c, &pr, (size_t)sp.nrq * nx * 8, true)) || (e = dalloc(c, &pd, (size_t)sp.nfin * 4 * 8, true)) ||
+        (e = dalloc(c, &p5, (size_t)nx * 4, true)) || (e = dalloc(c, &p6, (size_t)nx * 4, true)))
+        return cuda_fail(c, e, "cudaMalloc(species)");
+    sp.fgrid = pf;
+    sp.ngrid = nullptr;
+    sp.acc[0] = pa0;
+    sp.acc[1] = pa1;
+    sp.v2row = pv2;
+    sp.rho_part = (double*)pr;
+    sp.dpart = (double*)pd;
+    sp.shift[0] = (int*)p5;
+    sp.shift[1] = (int*)p6;
+    // |v|^2 at the cell centres, internal order [vz][vy][vx]
+    std::vector<double> v2(sp.nvflat);
+    for (int kz = 0; kz < sp.nv[2]; ++kz)
+        for (int ky = 0; ky < sp.nv[1]; ++ky)
+            for (int kx = 0; kx < sp.nv[0]; ++kx) {
+                const double vx = sp.vmin[0] + (kx + 0.5) * sp.dv[0];
+                const double vy = sp.vmin[1] + (ky + 0.5) * sp.dv[1];
+                const double vz = sp.vmin[2] + (kz + 0.5) * sp.dv[2];
+                v2[((size_t)kz * sp.nv[1] + ky) * sp.nv[0] + kx] = vx * vx + vy * vy + vz * vz;
+            }
+    if (h.prec == AVL_FP32) {
+        std::vector<float> v2f(v2.begin(), v2.end());
+        AVL_CUDA(c, cudaMemcpyAsync(pv2, v2f.data(), v2f.size() * 4, cudaMemcpyHostToDevice, c->st));
+        AVL_CUDA(c, cudaStreamSynchronize(c->st));
+    } else {
+        AVL_CUDA(c, cudaMemcpyAsync(pv2, v2.data(), v2.size() * 8, cudaMemcpyHostToDevice, c->st));
+        AVL_CUDA(c, cudaStreamSynchronize(c->st));
+    }
     return AVL_OK;
 }
 
@@ -319,8 +479,11 @@ avl_status avl_create(const avl_domain* dom, const avl_species* spec, int32_t ns
     if (!out) return fail(nullptr, AVL_EINVAL, "out is NULL");
     *out = nullptr;
     if (!dom || !spec) return fail(nullptr, AVL_EINVAL, "dom or species is NULL");
-    if (dom->nvdim != 1) return fail(nullptr, AVL_EINVAL, "nvdim must be 1 (1d3v is not built yet)");
+    if (dom->nvdim != 1 && dom->nvdim != 3) return fail(nullptr, AVL_EINVAL, "nvdim must be 1 or 3");
     if (dom->nx < 4 || dom->nx > (1 << 20)) return fail(nullptr, AVL_EINVAL, "nx must be in [4, 2^20]");
+    if (dom->nvdim == 3 && (dom->precision == AVL_FP32 || dom->precision == AVL_FP64) &&
+        pd3_smem_bytes(dom->nx, dom->precision) > 220 * 1024)
+        return fail(nullptr, AVL_EINVAL, "1d3v needs nx <= 1024 (FP32) or nx <= 512 (FP64)");
     if (!(dom->L > 0) || !(dom->dt > 0) || !(dom->poisson_const > 0) || !isfinite(dom->L) ||
         !isfinite(dom->dt) || !isfinite(dom->poisson_const))
         return fail(nullptr, AVL_EINVAL, "L, dt and poisson_const must be positive and finite");
@@ -332,10 +495,19 @@ avl_status avl_create(const avl_domain* dom, const avl_species* spec, int32_t ns
         const avl_species& p = spec[s];
         if (!(p.m > 0) || !isfinite(p.q) || !isfinite(p.m))
             return fail(nullptr, AVL_EINVAL, "species mass must be positive, charge finite");
-        if (p.nv[0] < 2 || p.nv[0] > (1 << 20) || p.nv[1] != 1 || p.nv[2] != 1)
-            return fail(nullptr, AVL_EINVAL, "1d1v species need nv[0] in [2, 2^20] and nv[1] = nv[2] = 1");
-        if (!(p.vmax[0] > p.vmin[0]) || !isfinite(p.vmin[0]) || !isfinite(p.vmax[0]))
-            return fail(nullptr, AVL_EINVAL, "species velocity range must satisfy vmin < vmax");
+        if (dom->nvdim == 1) {
+            if (p.nv[0] < 2 || p.nv[0] > (1 << 20) || p.nv[1] != 1 || p.nv[2] != 1)
+                return fail(nullptr, AVL_EINVAL, "1d1v species need nv[0] in [2, 2^20] and nv[1] = nv[2] = 1");
+        } else {
+            if (p.nv[0] < 2 || p.nv[0] > NV3_MAX || p.nv[1] < 2 || p.nv[1] > 4096 || p.nv[2] < 2 ||
+                p.nv[2] > 4096)
+                return fail(nullptr, AVL_EINVAL, "1d3v species need nv[0] in [2, 1024], nv[1], nv[2] in [2, 4096]");
+            const long long cells = (long long)dom->nx * p.nv[0] * p.nv[1] * p.nv[2];
+            if (cells >= (1ll << 31)) return fail(nullptr, AVL_EINVAL, "1d3v grid must have fewer than 2^31 cells");
+        }
+        for (int d = 0; d < dom->nvdim; ++d)
+            if (!(p.vmax[d] > p.vmin[d]) || !isfinite(p.vmin[d]) || !isfinite(p.vmax[d]))
+                return fail(nullptr, AVL_EINVAL, "species velocity range must satisfy vmin < vmax");
     }
 
     avl_ctx* c = new avl_ctx();
@@ -410,7 +582,11 @@ avl_status avl_create(const avl_domain* dom, const avl_species* spec, int32_t ns
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device) == cudaSuccess && sms > 0)
         c->num_sms = sms;
     int fin_base = 0;
-    for (int s = 0; s < nspecies; ++s) {
+    for (int s = 0; s < nspecies && dom->nvdim == 3; ++s) {
+        avl_status st3 = create_species3(c, s, spec[s], fin_base);
+        if (st3 != AVL_OK) return bail(st3);
+    }
+    for (int s = 0; s < nspecies && dom->nvdim == 1; ++s) {
         const avl_species& p = spec[s];
         SpDev& sp = h.sp[s];
         sp.nvdim = 1;
@@ -482,7 +658,7 @@ avl_status avl_create(const avl_domain* dom, const avl_species* spec, int32_t ns
     c->d_f0 = (avl_f0*)pf0;
     c->d_bad = (unsigned long long*)pbad;
     h.ctl = c->d_ctl;
-    if ((e = configure_vhs1(h)) || (e = configure_field(h))) {
+    if ((e = configure_vhs1(h)) || (e = configure_vhs3(h)) || (e = configure_field(h))) {
         cuda_fail(c, e, "cudaFuncSetAttribute (shared memory)");
         return bail(AVL_ECUDA);
     }
@@ -509,22 +685,30 @@ avl_status avl_init_markers(avl_ctx* c, int32_t s, const int32_t lattice[4], con
     avl_status st = check_species(c, s);
     if (st) return st;
     if (!lattice || !f0) return fail(c, AVL_EINVAL, "lattice or f0 is NULL");
-    if (lattice[0] < 1 || lattice[1] < 1 || lattice[2] != 1 || lattice[3] != 1)
+    const int nvd = c->h.nvdim;
+    if (nvd == 1 && (lattice[0] < 1 || lattice[1] < 1 || lattice[2] != 1 || lattice[3] != 1))
         return fail(c, AVL_EINVAL, "1d1v lattice must be {px >= 1, pv >= 1, 1, 1}");
+    if (nvd == 3 && (lattice[0] < 1 || lattice[1] < 1 || lattice[2] < 1 || lattice[3] < 1 ||
+                     (long long)lattice[0] * lattice[1] * lattice[2] * lattice[3] > 4096))
+        return fail(c, AVL_EINVAL, "1d3v lattice must be {px, pvx, pvy, pvz} >= 1 with at most 4096 points");
     if (f0->nbeam < 1 || f0->nbeam > 4 || f0->nmode < 0 || f0->nmode > 64)
         return fail(c, AVL_EINVAL, "f0 needs 1..4 beams and 0..64 modes");
     for (int b = 0; b < f0->nbeam; ++b)
-        if (!(f0->beam_vth[b][0] > 0)) return fail(c, AVL_EINVAL, "beam thermal speeds must be positive");
+        for (int d = 0; d < nvd; ++d)
+            if (!(f0->beam_vth[b][d] > 0)) return fail(c, AVL_EINVAL, "beam thermal speeds must be positive");
     if (!(jitter >= 0.0 && jitter <= 1.0)) return fail(c, AVL_EINVAL, "jitter must be in [0, 1]");
     SpDev& sp = c->h.sp[s];
-    const long long ppc = (long long)lattice[0] * lattice[1];
+    const long long ppc = (long long)lattice[0] * lattice[1] * lattice[2] * lattice[3];
     const long long n = (long long)sp.nx * sp.nvflat * ppc;
     if (n >= (1ll << 31) - 1024) return fail(c, AVL_EINVAL, "too many markers for one species (2^31)");
-    if ((st = plan_layout(c, s, n))) return st;
+    if ((st = nvd == 3 ? plan_layout3(c, s, n) : plan_layout(c, s, n))) return st;
     if ((st = set_cur_zero(c, s))) return st;
     AVL_CUDA(c, cudaMemcpyAsync(c->d_f0, f0, sizeof(avl_f0), cudaMemcpyHostToDevice, c->st));
     if ((st = upload_args(c))) return st;
-    AVL_CUDA(c, launch_init1(c->h, c->d_args, s, lattice, c->d_f0, seed, jitter, c->st));
+    if (nvd == 3)
+        AVL_CUDA(c, launch_init3(c->h, c->d_args, s, lattice, c->d_f0, seed, jitter, c->st));
+    else
+        AVL_CUDA(c, launch_init1(c->h, c->d_args, s, lattice, c->d_f0, seed, jitter, c->st));
     c->has_markers[s] = true;
     if ((st = refresh(c))) return st;
     return read_errors(c);
@@ -549,11 +733,14 @@ avl_status avl_set_markers(avl_ctx* c, int32_t s, int64_t n, const double* x, co
         dv_ = base + n;
         df_ = base + n * (1 + nvd);
     }
-    if ((st = plan_layout(c, s, n))) return st;
+    if ((st = nvd == 3 ? plan_layout3(c, s, n) : plan_layout(c, s, n))) return st;
     if ((st = set_cur_zero(c, s))) return st;
     if ((st = upload_args(c))) return st;
     AVL_CUDA(c, cudaMemsetAsync(c->d_bad, 0, 8, c->st));
-    AVL_CUDA(c, launch_set1(c->h, c->d_args, s, n, dx_, dv_, df_, c->d_bad, c->st));
+    if (nvd == 3)
+        AVL_CUDA(c, launch_set3(c->h, c->d_args, s, n, dx_, dv_, df_, c->d_bad, c->st));
+    else
+        AVL_CUDA(c, launch_set1(c->h, c->d_args, s, n, dx_, dv_, df_, c->d_bad, c->st));
     unsigned long long bad = 0;
     AVL_CUDA(c, cudaMemcpyAsync(&bad, c->d_bad, 8, cudaMemcpyDeviceToHost, c->st));
     AVL_CUDA(c, cudaStreamSynchronize(c->st));
@@ -582,13 +769,17 @@ avl_status avl_get_markers(avl_ctx* c, int32_t s, double* x, double* v, double* 
     if (!c->has_markers[s]) return fail(c, AVL_ESTATE, "species has no markers");
     const long long n = c->h.sp[s].n;
     const int nvd = c->h.nvdim;
+    auto get = [&](double* gx, double* gv, double* gf) {
+        return nvd == 3 ? launch_get3(c->h, c->d_args, s, gx, gv, gf, c->st)
+                        : launch_get1(c->h, c->d_args, s, gx, gv, gf, c->st);
+    };
     if (on_device) {
-        AVL_CUDA(c, launch_get1(c->h, c->d_args, s, x, v, f, c->st));
+        AVL_CUDA(c, get(x, v, f));
         return AVL_OK;
     }
     if ((st = ensure_scratch(c, (size_t)n * 8 * (2 + nvd)))) return st;
     double* base = static_cast<double*>(c->scratch);
-    AVL_CUDA(c, launch_get1(c->h, c->d_args, s, base, base + n, base + n * (1 + nvd), c->st));
+    AVL_CUDA(c, get(base, base + n, base + n * (1 + nvd)));
     if (x) AVL_CUDA(c, cudaMemcpyAsync(x, base, n * 8, cudaMemcpyDeviceToHost, c->st));
     if (v) AVL_CUDA(c, cudaMemcpyAsync(v, base + n, n * 8 * nvd, cudaMemcpyDeviceToHost, c->st));
     if (f) AVL_CUDA(c, cudaMemcpyAsync(f, base + n * (1 + nvd), n * 8, cudaMemcpyDeviceToHost, c->st));
@@ -626,13 +817,23 @@ avl_status avl_get_f(avl_ctx* c, int32_t s, double* f, double* n_opt, int32_t on
     if (!f) return fail(c, AVL_EINVAL, "f is NULL");
     const SpDev& sp = c->h.sp[s];
     const size_t cells = (size_t)sp.nx * sp.nvflat;
+    int which = 0;   // 1d3v: accumulator of the last deposit
+    if (sp.nvdim == 3) {
+        int asel = 0;
+        AVL_CUDA(c, cudaMemcpyAsync(&asel, &c->d_ctl->asel[s], sizeof(int), cudaMemcpyDeviceToHost, c->st));
+        AVL_CUDA(c, cudaStreamSynchronize(c->st));
+        which = 1 - asel;
+    }
+    auto getf = [&](double* gf, double* gn) {
+        return sp.nvdim == 3 ? launch_getf3(c->h, s, which, gf, gn, c->st) : launch_getf(c->h, s, gf, gn, c->st);
+    };
     if (on_device) {
-        AVL_CUDA(c, launch_getf(c->h, s, f, n_opt, c->st));
+        AVL_CUDA(c, getf(f, n_opt));
         return AVL_OK;
     }
     if ((st = ensure_scratch(c, cells * 16))) return st;
     double* base = static_cast<double*>(c->scratch);
-    AVL_CUDA(c, launch_getf(c->h, s, base, n_opt ? base + cells : nullptr, c->st));
+    AVL_CUDA(c, getf(base, n_opt ? base + cells : nullptr));
     AVL_CUDA(c, cudaMemcpyAsync(f, base, cells * 8, cudaMemcpyDeviceToHost, c->st));
     if (n_opt) AVL_CUDA(c, cudaMemcpyAsync(n_opt, base + cells, cells * 8, cudaMemcpyDeviceToHost, c->st));
     AVL_CUDA(c, cudaStreamSynchronize(c->st));
@@ -680,7 +881,7 @@ avl_status avl_get_stats(avl_ctx* c, int64_t* out)
     AVL_CUDA(c, cudaMemcpyAsync(&h, c->d_ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, c->st));
     AVL_CUDA(c, cudaStreamSynchronize(c->st));
     for (int s = 0; s < c->ns; ++s) {
-        out[4 * s + 0] = (int64_t)h.ovf_last[s];
+        out[4 * s + 0] = (int64_t)(c->h.nvdim == 3 ? h.movers_last[s] : h.ovf_last[s]);
         out[4 * s + 1] = (int64_t)h.nsort[s];
         out[4 * s + 2] = (int64_t)h.uncovered[s];
         out[4 * s + 3] = (int64_t)h.step;
@@ -700,11 +901,13 @@ avl_status avl_profile_steps(avl_ctx* c, int32_t nsteps, double* ms, int32_t nke
     double acc[4] = {0, 0, 0, 0};
     avl_status st = AVL_OK;
     for (int i = 0; i < nsteps && st == AVL_OK; ++i) {
+        const bool d3 = c->h.nvdim == 3;
         cudaError_t e = cudaEventRecord(ev[0], c->st);
+        if (!e && d3) e = launch_sort3(c->h, c->d_args, c->st);
         if (!e) e = cudaEventRecord(ev[1], c->st);
-        if (!e) e = launch_pd1(c->h, c->d_args, 1, c->st);
+        if (!e) e = d3 ? launch_pd3(c->h, c->d_args, 1, c->st) : launch_pd1(c->h, c->d_args, 1, c->st);
         if (!e) e = cudaEventRecord(ev[2], c->st);
-        if (!e) e = launch_fin1(c->h, c->d_args, 0, c->st);
+        if (!e) e = d3 ? launch_fin3(c->h, c->d_args, 0, c->st) : launch_fin1(c->h, c->d_args, 0, c->st);
         if (!e) e = cudaEventRecord(ev[3], c->st);
         if (!e) e = launch_field(c->h, c->d_args, 1, c->st);
         if (!e) e = cudaEventRecord(ev[4], c->st);

@@ -16,6 +16,16 @@
 //   Grids are stored [v][x] (x fastest): f and n (denominator of Eq. 4).
 //   Window partial sums of chunk c: [nchunk][planes][Wmax][nx] covering the
 //   velocity rows [wrow0[c], wrow0[c] + Wmax).
+//
+// HBM layout of one species (1d3v, no magnetic field: v_y, v_z never change):
+//   markers as above plus v_y, v_z (FP32: cell, off, vx, vy, vz, f = 24 B);
+//   velocities are absolute.  Sorted by pencil p = (jz + 1)(nvy + 1) + jy + 1
+//   (jy, jz: dual rows of v_y, v_z, clamped to [-1, nv - 1]) and inside a
+//   pencil by key k = jx + 1 (dual row of v_x, clamped likewise): seg[b][p][k]
+//   is the first marker of key k of pencil p in buffer b, seg[b][p][nkey] the
+//   end of the pencil.  A pencil's range is the same in both buffers.
+//   Grids are stored [vz][vy][vx][x] (x fastest); acc[a] holds the numerator
+//   and then the denominator of Eq. 4 for the deposit into accumulator a.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -36,6 +46,10 @@ constexpr int FIN_XB = 16;          // x columns per finalize block
 constexpr int FIELD_THREADS = 512;  // Poisson cluster block
 constexpr int FIELD_CLUSTER = 8;    // CTAs in the Poisson cluster
 constexpr long long WAIT_LIMIT = 1ll << 22;   // bounded mbarrier polls
+constexpr int P3_THREADS = 256;     // 1d3v pencil block (one thread per x column and CPT3 columns)
+constexpr int FIN3_X = 32;          // 1d3v finalize: x columns per block
+constexpr int FIN3_R = 8;           //                row lanes per block
+constexpr int NV3_MAX = 1024;       // 1d3v: largest nv[0] (key histogram of a pencil in shared memory)
 
 // device-side error bits (Ctl::err)
 enum : int { ERR_TIMEOUT = 1, ERR_NUMERIC = 2, ERR_CAPACITY = 4 };
@@ -83,6 +97,14 @@ struct SpDev {
     double* dpart;             // [nfin][4] : N, Wkin, S, -
     // finalize blocks: FIN_XB x-columns times a group of rq velocity rows
     int nxb, rq, nrq, nfin, fin_base;
+    // 1d3v
+    int npen;                  // (nv[1] + 1) (nv[2] + 1) pencils
+    int nkey;                  // nv[0] + 1 keys per pencil
+    int pen_base;              // first global pencil block of this species
+    int* seg[2];               // [npen][nkey + 1] first marker of every key, per buffer
+    void* acc[2];              // [2][nvflat][nx] numerator, denominator of the deposit
+    void* v2row;               // [nvflat] |v|^2 at the centre of every velocity cell
+    int* kcount;               // [npen * nkey + 1] creation scratch (counts, then cursors)
 };
 
 struct FieldDev {
@@ -111,11 +133,17 @@ struct Ctl {
                                // (sorted by the keys of the previous state)
     long long step;
     int err;
+    // 1d3v
+    int asel[MAXS];                        // accumulator the next deposit writes into
+    unsigned long long movers[MAXS];       // markers whose key left their segment (this pass)
+    unsigned long long far_movers[MAXS];   // of which two or more rows away
+    unsigned long long movers_last[MAXS];
 };
 
 struct StepArgs {
     int ns, prec, nvdim;
     int nchunk_total, nfin_total;
+    int npen_total;
     SpDev sp[MAXS];
     FieldDev fd;
     Ctl* ctl;
@@ -141,6 +169,25 @@ cudaError_t launch_set1(const StepArgs& h, const StepArgs* d, int s, long long n
 cudaError_t launch_get1(const StepArgs& h, const StepArgs* d, int s, double* x, double* v,
                         double* f, cudaStream_t st);
 cudaError_t launch_getf(const StepArgs& h, int s, double* f, double* n, cudaStream_t st);
+
+// 1d3v (k_vhs3.cu).  launch_pd3 mode as launch_pd1; launch_sort3 re-sorts the
+// pencils of the species the field kernel marked (a no-op otherwise)
+cudaError_t configure_vhs3(const StepArgs& h);
+cudaError_t launch_pd3(const StepArgs& h, const StepArgs* d, int mode, cudaStream_t st);
+cudaError_t launch_fin3(const StepArgs& h, const StepArgs* d, int all_species, cudaStream_t st);
+cudaError_t launch_sort3(const StepArgs& h, const StepArgs* d, cudaStream_t st);
+cudaError_t launch_init3(const StepArgs& h, const StepArgs* d, int s, const int lattice[4],
+                         const avl_f0* f0_dev, unsigned long long seed, double jitter,
+                         cudaStream_t st);
+cudaError_t launch_set3(const StepArgs& h, const StepArgs* d, int s, long long n,
+                        const double* x, const double* v, const double* f,
+                        unsigned long long* bad, cudaStream_t st);
+cudaError_t launch_get3(const StepArgs& h, const StepArgs* d, int s, double* x, double* v,
+                        double* f, cudaStream_t st);
+// f (and n) of the current deposit in the caller's [x][vx][vy][vz] order;
+// asel = accumulator selector after the last deposit
+cudaError_t launch_getf3(const StepArgs& h, int s, int asel, double* f, double* n, cudaStream_t st);
+size_t pd3_smem_bytes(int nx, int prec);
 
 size_t pd1_smem_bytes(const SpDev& sp, int prec);
 cudaError_t configure_vhs1(const StepArgs& h);

@@ -1,0 +1,216 @@
+// common.cuh -- device helpers shared by the 1d1v and 1d3v kernels: marker
+// position storage, periodic cloud-in-cell neighbours, compensated FP32
+// sums, and the marker generator (SplitMix64 jitter, analytic f0).
+#pragma once
+#include <math.h>
+
+#include "avl_internal.cuh"
+
+namespace avl {
+
+__device__ __forceinline__ int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
+
+// periodic neighbours of a lower CIC cell i0 in [-1, nx-1]; clamped so that a
+// non-finite position can never index outside the grid
+__device__ __forceinline__ void wrap_pair(int i0, int nx, int& ia, int& ib)
+{
+    ia = i0 < 0 ? i0 + nx : i0;
+    ib = (i0 + 1 >= nx) ? i0 + 1 - nx : i0 + 1;
+    ia = min(max(ia, 0), nx - 1);
+    ib = min(max(ib, 0), nx - 1);
+}
+
+// ---------------------------------------------------------------------------
+// marker storage access
+// ---------------------------------------------------------------------------
+template <typename T>
+struct Pos;
+
+// FP32: position = int cell + FP32 offset in [0, 1)
+template <>
+struct Pos<float> {
+    int c;
+    float o;
+    __device__ __forceinline__ void load(const SpDev& sp, int cb, int k)
+    {
+        c = reinterpret_cast<const int*>(sp.mx[cb])[k];
+        o = sp.moff[cb][k];
+    }
+    __device__ __forceinline__ void store(const SpDev& sp, int cb, int k) const
+    {
+        reinterpret_cast<int*>(sp.mx[cb])[k] = c;
+        sp.moff[cb][k] = o;
+    }
+    // cloud-in-cell: lower cell i0 (may be -1) and weight w of cell i0 + 1
+    __device__ __forceinline__ void cic(int& i0, float& w) const
+    {
+        if (o >= 0.5f) {
+            i0 = c;
+            w = o - 0.5f;
+        } else {
+            i0 = c - 1;
+            w = o + 0.5f;
+        }
+    }
+    __device__ __forceinline__ void drift(float disp, int nx)
+    {
+        o += disp;
+        const float fo = floorf(o);
+        c += static_cast<int>(fo);
+        o -= fo;
+        if (o >= 1.0f) {
+            o -= 1.0f;
+            c += 1;
+        }
+        if (c < 0 || c >= nx) {
+            c %= nx;
+            if (c < 0) c += nx;
+        }
+    }
+    __device__ __forceinline__ double cells() const { return (double)c + (double)o; }
+};
+
+// FP64: position in cells, xi in [0, nx)
+template <>
+struct Pos<double> {
+    double xi;
+    __device__ __forceinline__ void load(const SpDev& sp, int cb, int k)
+    {
+        xi = reinterpret_cast<const double*>(sp.mx[cb])[k];
+    }
+    __device__ __forceinline__ void store(const SpDev& sp, int cb, int k) const
+    {
+        reinterpret_cast<double*>(sp.mx[cb])[k] = xi;
+    }
+    __device__ __forceinline__ void cic(int& i0, double& w) const
+    {
+        const double u = xi - 0.5;
+        const double fl = floor(u);
+        i0 = static_cast<int>(fl);
+        w = u - fl;
+    }
+    __device__ __forceinline__ void drift(double disp, int nx)
+    {
+        double x = xi + disp;
+        const double n = static_cast<double>(nx);
+        if (x < 0.0 || x >= n) {
+            x = fmod(x, n);
+            if (x < 0.0) x += n;
+            if (x >= n) x -= n;
+        }
+        xi = x;
+    }
+    __device__ __forceinline__ double cells() const { return xi; }
+};
+
+// position from a value in cells (FP64) given by a caller or the generator
+template <typename T>
+__device__ __forceinline__ Pos<T> pos_from_cells(double xi, int nx)
+{
+    Pos<T> p;
+    if constexpr (sizeof(T) == 4) {
+        const double c = floor(xi);
+        int ci = (int)c;
+        const double o = xi - c;
+        if (ci >= nx) ci -= nx;
+        if (ci < 0) ci += nx;
+        p.c = min(max(ci, 0), nx - 1);
+        p.o = (float)o;
+        if (p.o >= 1.0f) {
+            p.o = 0.0f;
+            p.c = (p.c + 1) % nx;
+        }
+    } else {
+        p.xi = xi < nx ? xi : xi - nx;
+    }
+    return p;
+}
+
+// ---------------------------------------------------------------------------
+// compensated accumulation
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void two_sum_add(float& hi, float& lo, float x)
+{
+    const float s = __fadd_rn(hi, x);
+    const float bp = __fsub_rn(s, hi);
+    const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bp)), __fsub_rn(x, bp));
+    hi = s;
+    lo = __fadd_rn(lo, e);
+}
+
+
+// FP32 path: float-float arithmetic (an unevaluated sum hi + lo) so that the
+// cell values and the column sums keep the accuracy of the compensated
+// deposit without per-cell FP64 work.
+struct ff {
+    float hi, lo;
+};
+
+__device__ __forceinline__ void ff_add(ff& a, float x) { two_sum_add(a.hi, a.lo, x); }
+
+template <typename T>
+struct ColAcc;
+
+template <>
+struct ColAcc<float> {
+    ff rho{0.f, 0.f}, w{0.f, 0.f}, ent{0.f, 0.f};
+    __device__ __forceinline__ void add(float fh, float fl, float v2)
+    {
+        ff_add(rho, fh);
+        rho.lo = __fadd_rn(rho.lo, fl);
+        ff_add(w, __fmul_rn(v2, fh));
+        if (fh > 0.f) ff_add(ent, __fmul_rn(fh, logf(fh)));
+    }
+    __device__ __forceinline__ double r() const { return (double)rho.hi + (double)rho.lo; }
+    __device__ __forceinline__ double wk() const { return (double)w.hi + (double)w.lo; }
+    __device__ __forceinline__ double s() const { return (double)ent.hi + (double)ent.lo; }
+};
+
+template <>
+struct ColAcc<double> {
+    double rho = 0.0, w = 0.0, ent = 0.0;
+    __device__ __forceinline__ void add(double fh, double, double v2)
+    {
+        rho += fh;
+        w += v2 * fh;
+        if (fh > 0.0) ent += fh * log(fh);
+    }
+    __device__ __forceinline__ double r() const { return rho; }
+    __device__ __forceinline__ double wk() const { return w; }
+    __device__ __forceinline__ double s() const { return ent; }
+};
+
+// SplitMix64 (Steele, Lea & Flood 2014): output n of the generator seeded
+// with `seed`.
+__device__ __forceinline__ unsigned long long splitmix64(unsigned long long seed, unsigned long long n)
+{
+    unsigned long long z = seed + (n + 1ull) * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+__device__ __forceinline__ double jitter_u01(unsigned long long seed, int s, long long m, int d)
+{
+    const unsigned long long n = ((unsigned long long)(unsigned)s << 48) | ((unsigned long long)m * 4ull + d);
+    return (double)(splitmix64(seed, n) >> 11) * (1.0 / 9007199254740992.0);
+}
+
+__device__ __forceinline__ double f0_value(const avl_f0* p, int nvdim, double L, double x, const double* v)
+{
+    double pert = 1.0;
+    for (int m = 0; m < p->nmode; ++m)
+        pert += p->amp[m] * cos(2.0 * M_PI * (double)p->mode[m] / L * x + p->phase[m]);
+    double sum = 0.0;
+    for (int b = 0; b < p->nbeam; ++b) {
+        double gb = p->beam_n[b];
+        for (int d = 0; d < nvdim; ++d) {
+            const double sd = p->beam_vth[b][d];
+            const double t = (v[d] - p->beam_u[b][d]) / sd;
+            gb *= exp(-0.5 * t * t) / (sqrt(2.0 * M_PI) * sd);
+        }
+        sum += gb;
+    }
+    return sum * pert;
+}
+}  // namespace avl

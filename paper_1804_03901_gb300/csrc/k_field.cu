@@ -333,10 +333,33 @@ __global__ void __cluster_dims__(FIELD_CLUSTER, 1, 1) __launch_bounds__(FIELD_TH
     // wait for the re-sort decision of CTA 1 and the clearing by the others,
     // then make this step's markers and key counts current
     cluster.sync();
-    if (threadIdx.x == 0 && count_step) {
+    if (threadIdx.x == 0) {
         Ctl* ctl = A->ctl;
         for (int s = 0; s < ns; ++s) {
             const SpDev& sp = A->sp[s];
+            if (sp.nvdim == 3) {
+                // 1d3v: the deposit just finalized becomes current, the other
+                // accumulator (cleared by the finalize) takes the next one.
+                // Re-sort when more than 1/64 of the markers sit off their
+                // segment's row, or 1/4096 two or more rows off.
+                const bool deposited = count_step ? sp.mobile != 0 : true;
+                if (deposited) ctl->asel[s] ^= 1;
+                const unsigned long long mv = ctl->movers[s], fm = ctl->far_movers[s];
+                ctl->movers[s] = 0;
+                ctl->far_movers[s] = 0;
+                if (count_step && sp.mobile) {
+                    ctl->movers_last[s] = mv;
+                    const unsigned long long n = (unsigned long long)sp.n;
+                    const int so = (n > 0 && (mv * 64ull > n || fm * 4096ull > n)) ? 1 : 0;
+                    ctl->sort_now[s] = so;
+                    if (so) {
+                        ctl->cur[s] = 1 - ctl->cur[s];
+                        ctl->nsort[s] += 1;
+                    }
+                }
+                continue;
+            }
+            if (!count_step) continue;
             if (!sp.mobile || sp.nchunk == 0) continue;
             if (ctl->sort_now[s]) {
                 ctl->cur[s] = 1 - ctl->cur[s];
@@ -347,7 +370,7 @@ __global__ void __cluster_dims__(FIELD_CLUSTER, 1, 1) __launch_bounds__(FIELD_TH
             ctl->hsel[s] = 1 - ctl->hsel[s];
             ctl->shsel[s] = 1 - ctl->shsel[s];
         }
-        ctl->step += 1;
+        if (count_step) ctl->step += 1;
     }
 }
 

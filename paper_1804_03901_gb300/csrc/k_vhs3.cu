@@ -1,0 +1,964 @@
+// k_vhs3.cu -- 1d3v kernels of the Vlasov-Hybrid time step (Fig. 2; Sec. 2
+// with three velocity dimensions and no magnetic field, so that the field
+// changes v_x only and v_y, v_z ride along unchanged).
+//
+// Layout: markers sorted by pencil (the dual rows of v_y and v_z, fixed for
+// the life of a marker) and inside a pencil by key (dual row of v_x + 1).
+// One CTA owns one pencil and walks its keys in order; per segment (the
+// markers stored under one key):
+//   push    gather E (cloud-in-cell, Sec. 2), v_x += (q/m) E dt, x += v_x dt,
+//           written back in place
+//   sort    the markers whose new key is still the segment's key ("stays")
+//           are counting-sorted by their x dual cell in shared memory
+//   gather  one thread per x column adds the 16 cloud-in-cell weights (Eq. 4
+//           numerator alpha f and denominator alpha) of the markers of its
+//           two dual cells into registers: rows j, j+1 of v_x times the
+//           pencil's four (v_y, v_z) cells -- no atomics
+//   flush   a finished v_x row is added into the global accumulators; each
+//           cell receives the sums of the four pencils that reach it
+// Markers whose key moved one row since the last re-sort deposit through a
+// four-row shared-memory ring, farther ones through global atomics; their
+// counts decide the next re-sort (k_sort3, per pencil, into the other
+// buffer).  k_fin3 forms f = num / den, the moment (Eq. 14) and the
+// diagnostics (Sec. 3.4.1) and clears the other accumulator.
+#include <math.h>
+
+#include <algorithm>
+
+#include "avl_internal.cuh"
+#include "common.cuh"
+
+namespace avl {
+
+template <typename T>
+struct Cfg3;
+template <>
+struct Cfg3<float> {
+    static constexpr int MPT = 4;   // markers per thread and batch
+};
+template <>
+struct Cfg3<double> {
+    static constexpr int MPT = 2;
+};
+
+__device__ __forceinline__ int species_of_pen(const StepArgs* A, int g)
+{
+    int s = 0;
+    while (s + 1 < A->ns && g >= A->sp[s + 1].pen_base) ++s;
+    return s;
+}
+
+__device__ __forceinline__ int species_of_fin3(const StepArgs* A, int g)
+{
+    int s = 0;
+    while (s + 1 < A->ns && g >= A->sp[s + 1].fin_base) ++s;
+    return s;
+}
+
+// Dual row of a velocity component on a grid of n cells: t = v a + b with
+// a = 1/dv and b = -vmin/dv - 1/2 (the cloud-in-cell rule of Fig. 1 on a
+// cell-centred grid).  Returns floor(t) limited to [-2, n] (-2 and n: the
+// footprint misses the grid) and the weight w = t - floor(t) of row j + 1.
+// One explicit fused multiply-add, so that every kernel finds the same row.
+__device__ __forceinline__ int dual3(float v, float a, float b, int n, float& w)
+{
+    const float t = __fmaf_rn(v, a, b);
+    if (!(t > -2.0f && t < (float)n)) {
+        w = 0.0f;
+        return t > 0.0f ? n : -2;
+    }
+    const float fl = floorf(t);
+    w = t - fl;
+    return (int)fl;
+}
+__device__ __forceinline__ int dual3(double v, double a, double b, int n, double& w)
+{
+    const double t = __fma_rn(v, a, b);
+    if (!(t > -2.0 && t < (double)n)) {
+        w = 0.0;
+        return t > 0.0 ? n : -2;
+    }
+    const double fl = floor(t);
+    w = t - fl;
+    return (int)fl;
+}
+
+// coefficients of dual3 for dimension d of a species, in storage precision
+template <typename T>
+struct VCoef {
+    T a[3], b[3];
+    int n[3];
+    __device__ __forceinline__ void init(const SpDev& sp)
+    {
+        for (int d = 0; d < 3; ++d) {
+            a[d] = (T)sp.inv_dv[d];
+            b[d] = (T)(-sp.vmin[d] * sp.inv_dv[d] - 0.5);
+            n[d] = sp.nv[d];
+        }
+    }
+};
+
+__device__ __forceinline__ int key_of(int j, int n) { return clampi(j, -1, n - 1) + 1; }
+
+// warp-aggregated slot: lanes with equal keys take consecutive slots of
+// cur[key] (one atomic per distinct key in the warp); lanes with ok = false
+// take part but get no slot
+__device__ __forceinline__ int warp_slot(int* cur, int key, bool ok)
+{
+    const int kk = ok ? key : -1;
+    const unsigned grp = __match_any_sync(0xffffffffu, kk);
+    const int lane = threadIdx.x & 31;
+    const int leader = __ffs(grp) - 1;
+    int base = 0;
+    if (ok && lane == leader) base = atomicAdd(&cur[key], __popc(grp));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    return base + __popc(grp & ((1u << lane) - 1u));
+}
+
+// exclusive scan of in[0, n) into out[0, n], out[n] = total, by a block of
+// P3_THREADS threads; each thread takes `items` consecutive entries
+// (items * P3_THREADS >= n); in may alias out
+__device__ void block_exscan(const int* in, int* out, int n, int items, int* wsum)
+{
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const int i0 = t * items;
+    int loc = 0;
+    for (int i = 0; i < items; ++i)
+        if (i0 + i < n) loc += in[i0 + i];
+    int x = loc;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) wsum[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        int w = lane < P3_THREADS / 32 ? wsum[lane] : 0;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += y;
+        }
+        if (lane < P3_THREADS / 32) wsum[lane] = w;
+    }
+    __syncthreads();
+    int run = x - loc + (warp > 0 ? wsum[warp - 1] : 0);
+    for (int i = 0; i < items; ++i)
+        if (i0 + i < n) {
+            const int v = in[i0 + i];
+            out[i0 + i] = run;
+            run += v;
+        }
+    if (t == P3_THREADS - 1) out[n] = run;
+    __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// push + deposit
+// ---------------------------------------------------------------------------
+size_t pd3_smem_bytes(int nx, int prec)
+{
+    const size_t tb = prec == AVL_FP32 ? 4 : 8;
+    const size_t nb = (size_t)P3_THREADS * (prec == AVL_FP32 ? Cfg3<float>::MPT : Cfg3<double>::MPT);
+    size_t b = tb * (32 * (size_t)nx + 7 * nb + nx);   // ring, sorted payload, E
+    b += 4 * (2 * (size_t)nx + 1) + 64;                // histogram, bin starts, padding
+    return (b + 15) / 16 * 16;
+}
+
+template <typename T>
+struct Ring {
+    T* r;   // [4 rows][4 planes][2: num, den][nx]
+    int nx;
+    __device__ __forceinline__ T* at(int row, int q, int c, int x) const
+    {
+        return r + ((size_t)(((row & 3) * 4 + q) * 2 + c)) * nx + x;
+    }
+};
+
+// weights of the pencil's four (v_y, v_z) cells: (jy, jz), (jy+1, jz),
+// (jy, jz+1), (jy+1, jz+1)
+template <typename T>
+__device__ __forceinline__ void plane_weights(T wy, T wz, T (&q)[4])
+{
+    const T ya = (T)1 - wy, za = (T)1 - wz;
+    q[0] = ya * za;
+    q[1] = wy * za;
+    q[2] = ya * wz;
+    q[3] = wy * wz;
+}
+
+// the 16 cloud-in-cell contributions of one marker whose v_x dual row j is
+// not the segment's: into the ring (rows within one of the segment's) or
+// straight into the global accumulator
+template <typename T>
+__device__ __forceinline__ void deposit_single(const SpDev& sp, const Ring<T>& ring, bool to_ring, T* gacc,
+                                               size_t cells, int bin, T u, int j, T w, int pjy, int pjz,
+                                               const T (&wq)[4], T f)
+{
+    const int nx = sp.nx, nvx = sp.nv[0], nvy = sp.nv[1], nvz = sp.nv[2];
+#pragma unroll
+    for (int cx = 0; cx < 2; ++cx) {
+        const int x = cx ? (bin + 1 == nx ? 0 : bin + 1) : bin;
+        const T ax = cx ? u : (T)1 - u;
+#pragma unroll
+        for (int cv = 0; cv < 2; ++cv) {
+            const int row = j + cv;
+            if (row < 0 || row >= nvx) continue;
+            const T av = ax * (cv ? w : (T)1 - w);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int ky = pjy + (q & 1), kz = pjz + (q >> 1);
+                if (ky < 0 || ky >= nvy || kz < 0 || kz >= nvz) continue;
+                const T a = av * wq[q];
+                if (a == (T)0) continue;
+                if (to_ring) {
+                    atomicAdd(ring.at(row, q, 0, x), a * f);
+                    atomicAdd(ring.at(row, q, 1, x), a);
+                } else {
+                    const size_t o = ((size_t)((kz * nvy + ky) * nvx + row)) * nx + x;
+                    atomicAdd(gacc + o, a * f);
+                    atomicAdd(gacc + cells + o, a);
+                }
+            }
+        }
+    }
+}
+
+// add one finished v_x row of the ring into the global accumulator (columns
+// of this thread) and clear it
+template <typename T, int CPT>
+__device__ __forceinline__ void flush_row(const SpDev& sp, const Ring<T>& ring, T* gacc, size_t cells, int row,
+                                          int pjy, int pjz)
+{
+    const int nx = sp.nx, nvx = sp.nv[0], nvy = sp.nv[1], nvz = sp.nv[2];
+    if (row < 0 || row >= nvx) return;
+#pragma unroll
+    for (int c = 0; c < CPT; ++c) {
+        const int x = threadIdx.x + c * P3_THREADS;
+        if (x >= nx) continue;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int ky = pjy + (q & 1), kz = pjz + (q >> 1);
+            const bool ok = ky >= 0 && ky < nvy && kz >= 0 && kz < nvz;
+            T* pn = ring.at(row, q, 0, x);
+            T* pd = ring.at(row, q, 1, x);
+            const T vn = *pn, vd = *pd;
+            *pn = (T)0;
+            *pd = (T)0;
+            if (ok && vd != (T)0) {
+                const size_t o = ((size_t)((kz * nvy + ky) * nvx + row)) * nx + x;
+                atomicAdd(gacc + o, vn);
+                atomicAdd(gacc + cells + o, vd);
+            }
+        }
+    }
+}
+
+// mode 0: deposit of the current markers of every species (refresh);
+// mode 1: push of the mobile species, then deposit of the new state
+template <typename T, int CPT>
+__global__ void __launch_bounds__(P3_THREADS, (sizeof(T) == 4 && CPT == 1) ? 3 : 1)
+    k_pd3(const StepArgs* __restrict__ A, int mode)
+{
+    constexpr int MPT = Cfg3<T>::MPT;
+    constexpr int NB = P3_THREADS * MPT;
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ int wsum[P3_THREADS / 32];
+    __shared__ unsigned long long mov_s, far_s;
+    __shared__ int bad_s;
+
+    const int g = blockIdx.x;
+    const int s = species_of_pen(A, g);
+    const SpDev& sp = A->sp[s];
+    const bool push = mode == 1;
+    if (push && !sp.mobile) return;
+    Ctl* ctl = A->ctl;
+    const int p = g - sp.pen_base;
+    const int nx = sp.nx, nvx = sp.nv[0];
+    const int pjy = p % (sp.nv[1] + 1) - 1, pjz = p / (sp.nv[1] + 1) - 1;
+    const int cb = ctl->cur[s];
+    const size_t cells = (size_t)sp.nvflat * nx;
+    T* gacc = reinterpret_cast<T*>(sp.acc[ctl->asel[s]]);
+    const int* seg = sp.seg[cb] + (size_t)p * (sp.nkey + 1);
+
+    // shared memory: ring | payload (7 arrays of NB) | E | hist | start
+    Ring<T> ring{reinterpret_cast<T*>(smem), nx};
+    T* pay = ring.r + 32 * (size_t)nx;
+    T* Es = pay + 7 * (size_t)NB;
+    int* hist = reinterpret_cast<int*>(Es + nx);
+    int* start = hist + nx;
+
+    for (int i = threadIdx.x; i < 32 * nx; i += P3_THREADS) ring.r[i] = (T)0;
+    for (int i = threadIdx.x; i < nx; i += P3_THREADS) {
+        hist[i] = 0;
+        if (push) Es[i] = sizeof(T) == 4 ? (T)A->fd.E32[i] : (T)A->fd.E64[i];
+    }
+    if (threadIdx.x == 0) {
+        mov_s = 0;
+        far_s = 0;
+        bad_s = 0;
+    }
+    __syncthreads();
+
+    VCoef<T> vc;
+    vc.init(sp);
+    const T qm_dt = (T)sp.qm_dt, dt_dx = (T)sp.dt_dx;
+    T* mvx = reinterpret_cast<T*>(sp.mv[cb][0]);
+    const T* mvy = reinterpret_cast<const T*>(sp.mv[cb][1]);
+    const T* mvz = reinterpret_cast<const T*>(sp.mv[cb][2]);
+    const T* mf = reinterpret_cast<const T*>(sp.mf[cb]);
+
+    T R0[CPT][8], R1[CPT][8];
+#pragma unroll
+    for (int c = 0; c < CPT; ++c)
+#pragma unroll
+        for (int e = 0; e < 8; ++e) R0[c][e] = R1[c][e] = (T)0;
+    unsigned long long nmov = 0, nfar = 0;
+
+    for (int k = 0; k < sp.nkey; ++k) {
+        const int jseg = k - 1;
+        const int beg = seg[k], end = seg[k + 1];
+        for (int b0 = beg; b0 < end; b0 += NB) {
+            T pu[MPT], pw[MPT], pf[MPT], pq[MPT][4];
+            int pbin[MPT], prank[MPT];
+#pragma unroll
+            for (int m = 0; m < MPT; ++m) {
+                prank[m] = -1;
+                pbin[m] = 0;
+                const int idx = b0 + m * P3_THREADS + threadIdx.x;
+                if (idx >= end) continue;
+                Pos<T> pos;
+                pos.load(sp, cb, idx);
+                T vx = mvx[idx];
+                if (push) {
+                    int i0;
+                    T wx;
+                    pos.cic(i0, wx);
+                    int ia, ib;
+                    wrap_pair(i0, nx, ia, ib);
+                    const T El = ((T)1 - wx) * Es[ia] + wx * Es[ib];
+                    vx = vx + qm_dt * El;
+                    pos.drift(vx * dt_dx, nx);
+                    pos.store(sp, cb, idx);
+                    mvx[idx] = vx;
+                }
+                const T f = mf[idx];
+                T wy, wz, w;
+                const int jy = dual3(mvy[idx], vc.a[1], vc.b[1], vc.n[1], wy);
+                const int jz = dual3(mvz[idx], vc.a[2], vc.b[2], vc.n[2], wz);
+                if (jy != pjy || jz != pjz) {
+                    // outside the pencil only when the footprint misses the grid
+                    if (jy >= -1 && jy < vc.n[1] && jz >= -1 && jz < vc.n[2]) bad_s = 1;
+                    continue;
+                }
+                const int jx = dual3(vx, vc.a[0], vc.b[0], nvx, w);
+                if (jx < -1 || jx >= nvx) continue;
+                int i0;
+                T u;
+                pos.cic(i0, u);
+                int bin = i0 < 0 ? i0 + nx : i0;
+                bin = min(max(bin, 0), nx - 1);
+                T wq[4];
+                plane_weights(wy, wz, wq);
+                const int d = jx - jseg;
+                if (d == 0) {
+                    prank[m] = atomicAdd(&hist[bin], 1);
+                    pbin[m] = bin;
+                    pu[m] = u;
+                    pw[m] = w;
+                    pf[m] = f;
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) pq[m][q] = wq[q];
+                } else {
+                    ++nmov;
+                    const bool near = d == 1 || d == -1;
+                    if (!near) ++nfar;
+                    deposit_single<T>(sp, ring, near, gacc, cells, bin, u, jx, w, pjy, pjz, wq, f);
+                }
+            }
+            __syncthreads();
+            block_exscan(hist, start, nx, CPT, wsum);
+            for (int i = threadIdx.x; i < nx; i += P3_THREADS) hist[i] = 0;
+            // stays into x-sorted order
+#pragma unroll
+            for (int m = 0; m < MPT; ++m) {
+                if (prank[m] < 0) continue;
+                const int o = start[pbin[m]] + prank[m];
+                pay[0 * NB + o] = pu[m];
+                pay[1 * NB + o] = pw[m];
+                pay[2 * NB + o] = pf[m];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) pay[(3 + q) * NB + o] = pq[m][q];
+            }
+            __syncthreads();
+            // gather: column x takes weight 1 - u from dual cell x and u from x - 1
+#pragma unroll
+            for (int c = 0; c < CPT; ++c) {
+                const int x = threadIdx.x + c * P3_THREADS;
+                if (x >= nx) continue;
+                const int xm = x == 0 ? nx - 1 : x - 1;
+#pragma unroll
+                for (int side = 0; side < 2; ++side) {
+                    const int bb = side ? xm : x;
+                    const int i1 = start[bb + 1];
+                    for (int i = start[bb]; i < i1; ++i) {
+                        const T u = pay[i];
+                        const T ax = side ? u : (T)1 - u;
+                        const T a1 = ax * pay[NB + i];
+                        const T a0 = ax - a1;
+                        const T f = pay[2 * NB + i];
+                        const T f0 = a0 * f, f1 = a1 * f;
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) {
+                            const T wqv = pay[(3 + q) * NB + i];
+                            R0[c][2 * q] += f0 * wqv;
+                            R0[c][2 * q + 1] += a0 * wqv;
+                            R1[c][2 * q] += f1 * wqv;
+                            R1[c][2 * q + 1] += a1 * wqv;
+                        }
+                    }
+                }
+            }
+            __syncthreads();
+        }
+        // row jseg is complete in registers: into the ring; row jseg - 1 is
+        // complete (no later segment reaches it): into the global accumulator
+        if (jseg >= 0) {
+#pragma unroll
+            for (int c = 0; c < CPT; ++c) {
+                const int x = threadIdx.x + c * P3_THREADS;
+                if (x >= nx) continue;
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    *ring.at(jseg, q, 0, x) += R0[c][2 * q];
+                    *ring.at(jseg, q, 1, x) += R0[c][2 * q + 1];
+                }
+            }
+        }
+        flush_row<T, CPT>(sp, ring, gacc, cells, jseg - 1, pjy, pjz);
+#pragma unroll
+        for (int c = 0; c < CPT; ++c)
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+                R0[c][e] = R1[c][e];
+                R1[c][e] = (T)0;
+            }
+        __syncthreads();
+    }
+    flush_row<T, CPT>(sp, ring, gacc, cells, nvx - 1, pjy, pjz);
+
+    if (nmov) atomicAdd(&mov_s, nmov);
+    if (nfar) atomicAdd(&far_s, nfar);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        if (mov_s) atomicAdd(&ctl->movers[s], mov_s);
+        if (far_s) atomicAdd(&ctl->far_movers[s], far_s);
+        if (bad_s) atomicOr(&ctl->err, ERR_CAPACITY);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// finalize: f = num / den (Eq. 4), charge per row group (Eq. 14), diagnostics
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(FIN3_X * FIN3_R) k_fin3(const StepArgs* __restrict__ A, int all_species)
+{
+    constexpr int NT = FIN3_X * FIN3_R;
+    __shared__ double col_red[FIN3_R][FIN3_X];
+    __shared__ double red[3][NT / 32];
+    const int g = blockIdx.x;
+    const int s = species_of_fin3(A, g);
+    const SpDev& sp = A->sp[s];
+    if (!all_species && !sp.mobile) return;
+    const int blk = g - sp.fin_base;
+    const int xb = blk % sp.nxb, rqi = blk / sp.nxb;
+    const int nx = sp.nx, nvf = sp.nvflat;
+    const int col = threadIdx.x % FIN3_X, lr = threadIdx.x / FIN3_X;
+    const int x = xb * FIN3_X + col;
+    const bool xok = x < nx;
+    const int j0 = rqi * sp.rq, j1 = min(nvf, j0 + sp.rq);
+    const int a = A->ctl->asel[s];
+    const size_t cells = (size_t)nvf * nx;
+    const T* num = reinterpret_cast<const T*>(sp.acc[a]);
+    const T* den = num + cells;
+    T* clr = reinterpret_cast<T*>(sp.acc[1 - a]);
+    T* fg = reinterpret_cast<T*>(sp.fgrid);
+    const T* v2 = reinterpret_cast<const T*>(sp.v2row);
+    ColAcc<T> acc;
+    if (xok) {
+        for (int j = j0 + lr; j < j1; j += FIN3_R) {
+            const size_t o = (size_t)j * nx + x;
+            const T nn = num[o], dd = den[o];
+            const T f = dd > (T)0 ? nn / dd : (T)0;
+            fg[o] = f;
+            clr[o] = (T)0;
+            clr[cells + o] = (T)0;
+            acc.add(f, (T)0, v2[j]);
+        }
+    }
+    const double dvol = sp.dv[0] * sp.dv[1] * sp.dv[2];
+    col_red[lr][col] = acc.r();
+    __syncthreads();
+    if (lr == 0 && xok) {
+        double r = 0.0;
+        for (int k = 0; k < FIN3_R; ++k) r += col_red[k][col];
+        sp.rho_part[(size_t)rqi * nx + x] = sp.q * dvol * r;
+    }
+    double dN = acc.r(), dW = acc.wk(), dS = acc.s();
+    for (int o = 16; o > 0; o >>= 1) {
+        dN += __shfl_down_sync(0xffffffffu, dN, o);
+        dW += __shfl_down_sync(0xffffffffu, dW, o);
+        dS += __shfl_down_sync(0xffffffffu, dS, o);
+    }
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) {
+        red[0][warp] = dN;
+        red[1][warp] = dW;
+        red[2][warp] = dS;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double n0 = 0, w0 = 0, s0 = 0;
+        for (int w = 0; w < NT / 32; ++w) {
+            n0 += red[0][w];
+            w0 += red[1][w];
+            s0 += red[2][w];
+        }
+        const double cell = sp.dx * dvol;
+        sp.dpart[(size_t)blk * 4 + 0] = n0 * cell;
+        sp.dpart[(size_t)blk * 4 + 1] = 0.5 * sp.m * w0 * cell;
+        sp.dpart[(size_t)blk * 4 + 2] = s0 * cell;
+        sp.dpart[(size_t)blk * 4 + 3] = 0.0;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// re-sort: every pencil of a species the field kernel marked, from buffer
+// 1 - cur into buffer cur (the field kernel has already flipped cur)
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(P3_THREADS) k_sort3(const StepArgs* __restrict__ A)
+{
+    __shared__ int cnt[NV3_MAX + 2];
+    __shared__ int wsum[P3_THREADS / 32];
+    const int g = blockIdx.x;
+    const int s = species_of_pen(A, g);
+    const SpDev& sp = A->sp[s];
+    const Ctl* ctl = A->ctl;
+    if (!sp.mobile || !ctl->sort_now[s]) return;
+    const int p = g - sp.pen_base;
+    const int dst = ctl->cur[s], src = 1 - dst;
+    const int nk = sp.nkey, nvx = sp.nv[0];
+    const int* sg = sp.seg[src] + (size_t)p * (nk + 1);
+    int* dg = sp.seg[dst] + (size_t)p * (nk + 1);
+    const int beg = sg[0], end = sg[nk];
+    const T ax = (T)sp.inv_dv[0], bx = (T)(-sp.vmin[0] * sp.inv_dv[0] - 0.5);
+    const T* vxs = reinterpret_cast<const T*>(sp.mv[src][0]);
+    for (int i = threadIdx.x; i < nk + 1; i += P3_THREADS) cnt[i] = 0;
+    __syncthreads();
+    for (int b0 = beg; b0 < end; b0 += P3_THREADS) {
+        const int k = b0 + threadIdx.x;
+        const bool ok = k < end;
+        int key = 0;
+        if (ok) {
+            T w;
+            key = key_of(dual3(vxs[k], ax, bx, nvx, w), nvx);
+        }
+        const int kk = ok ? key : -1;
+        const unsigned grp = __match_any_sync(0xffffffffu, kk);
+        if (ok && (threadIdx.x & 31) == __ffs(grp) - 1) atomicAdd(&cnt[key], __popc(grp));
+    }
+    __syncthreads();
+    block_exscan(cnt, cnt, nk, (nk + P3_THREADS - 1) / P3_THREADS, wsum);
+    for (int i = threadIdx.x; i <= nk; i += P3_THREADS) dg[i] = beg + cnt[i];
+    __syncthreads();
+    for (int b0 = beg; b0 < end; b0 += P3_THREADS) {
+        const int k = b0 + threadIdx.x;
+        const bool ok = k < end;
+        int key = 0;
+        T vx = 0;
+        if (ok) {
+            T w;
+            vx = vxs[k];
+            key = key_of(dual3(vx, ax, bx, nvx, w), nvx);
+        }
+        const int slot = beg + warp_slot(cnt, key, ok);
+        if (ok && slot >= beg && slot < end) {
+            Pos<T> pos;
+            pos.load(sp, src, k);
+            pos.store(sp, dst, slot);
+            reinterpret_cast<T*>(sp.mv[dst][0])[slot] = vx;
+            reinterpret_cast<T*>(sp.mv[dst][1])[slot] = reinterpret_cast<const T*>(sp.mv[src][1])[k];
+            reinterpret_cast<T*>(sp.mv[dst][2])[slot] = reinterpret_cast<const T*>(sp.mv[src][2])[k];
+            reinterpret_cast<T*>(sp.mf[dst])[slot] = reinterpret_cast<const T*>(sp.mf[src])[k];
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// marker creation: jittered lattice (Sec. 2 / Sec. 3.1) or caller arrays,
+// counting-sorted by (pencil, key) into buffer 0
+// ---------------------------------------------------------------------------
+struct MarkerIn3 {
+    double xi;   // position in cells
+    double v[3];
+    double f;
+    bool ok;
+};
+
+// lattice marker number k in generation order (v_z, v_y, v_x cell slowest,
+// then x cell, then sub-point); the jitter streams use the row-major marker
+// number ((((i nvx + jx) nvy + jy) nvz + jz) ppc + sub)
+struct LatticeSrc3 {
+    const avl_f0* f0;
+    unsigned long long seed;
+    double jitter;
+    int s;
+    int l[4];
+    __device__ MarkerIn3 get(const SpDev& sp, long long k) const
+    {
+        const int ppc = l[0] * l[1] * l[2] * l[3];
+        const int sub = (int)(k % ppc);
+        long long r = k / ppc;
+        const int i = (int)(r % sp.nx);
+        r /= sp.nx;
+        const int jx = (int)(r % sp.nv[0]);
+        r /= sp.nv[0];
+        const int jy = (int)(r % sp.nv[1]);
+        const int jz = (int)(r / sp.nv[1]);
+        const long long cell = (((long long)i * sp.nv[0] + jx) * sp.nv[1] + jy) * sp.nv[2] + jz;
+        const long long m = cell * ppc + sub;
+        const int bz = sub % l[3], by = (sub / l[3]) % l[2], bx = (sub / (l[3] * l[2])) % l[1];
+        const int a = sub / (l[3] * l[2] * l[1]);
+        const int j[3] = {jx, jy, jz}, b[3] = {bx, by, bz};
+        MarkerIn3 o;
+        const double J0 = (jitter_u01(seed, s, m, 0) - 0.5) * jitter;
+        o.xi = (double)i + ((double)a + 0.5 + J0) / l[0];
+        for (int d = 0; d < 3; ++d) {
+            const double Jd = (jitter_u01(seed, s, m, d + 1) - 0.5) * jitter;
+            o.v[d] = sp.vmin[d] + ((double)j[d] + ((double)b[d] + 0.5 + Jd) / l[d + 1]) * sp.dv[d];
+        }
+        o.f = f0_value(f0, 3, sp.nx * sp.dx, o.xi * sp.dx, o.v);
+        o.ok = true;
+        return o;
+    }
+};
+
+struct ArraySrc3 {
+    const double* x;
+    const double* v;   // component-major: v[d * n + k]
+    const double* f;
+    long long n;
+    __device__ MarkerIn3 get(const SpDev& sp, long long k) const
+    {
+        MarkerIn3 o;
+        const double L = sp.nx * sp.dx;
+        const double xv = x[k];
+        o.f = f[k];
+        o.ok = (xv >= 0.0 && xv < L) && isfinite(o.f);
+        for (int d = 0; d < 3; ++d) {
+            o.v[d] = v[(long long)d * n + k];
+            o.ok = o.ok && isfinite(o.v[d]);
+        }
+        o.xi = o.ok ? xv / sp.dx : 0.0;
+        if (!o.ok) {
+            for (int d = 0; d < 3; ++d) o.v[d] = sp.vmin[d];
+            o.f = 0.0;
+        }
+        return o;
+    }
+};
+
+// bucket (pencil * nkey + key) of a marker from its stored velocities
+template <typename T>
+__device__ __forceinline__ int bucket3(const SpDev& sp, const VCoef<T>& vc, const T (&v)[3])
+{
+    T w;
+    const int kx = key_of(dual3(v[0], vc.a[0], vc.b[0], vc.n[0], w), vc.n[0]);
+    const int ky = key_of(dual3(v[1], vc.a[1], vc.b[1], vc.n[1], w), vc.n[1]);
+    const int kz = key_of(dual3(v[2], vc.a[2], vc.b[2], vc.n[2], w), vc.n[2]);
+    return (kz * (vc.n[1] + 1) + ky) * sp.nkey + kx;
+}
+
+template <typename T, typename Src>
+__global__ void __launch_bounds__(256) k_src3_count(const StepArgs* __restrict__ A, int s, Src src,
+                                                    unsigned long long* bad)
+{
+    const SpDev& sp = A->sp[s];
+    VCoef<T> vc;
+    vc.init(sp);
+    unsigned nbad = 0;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    // whole warps iterate together (warp-aggregated counting)
+    const long long n_pad = (sp.n + 31) / 32 * 32;
+    for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < n_pad; k += stride) {
+        const bool ok = k < sp.n;
+        int b = 0;
+        if (ok) {
+            const MarkerIn3 mk = src.get(sp, k);
+            if (!mk.ok) ++nbad;
+            const T v[3] = {(T)mk.v[0], (T)mk.v[1], (T)mk.v[2]};
+            b = bucket3<T>(sp, vc, v);
+        }
+        const int kk = ok ? b : -1;
+        const unsigned grp = __match_any_sync(0xffffffffu, kk);
+        if (ok && (threadIdx.x & 31) == __ffs(grp) - 1) atomicAdd(&sp.kcount[b], __popc(grp));
+    }
+    if (nbad && bad) atomicAdd(bad, (unsigned long long)nbad);
+}
+
+// exclusive scan of the bucket counts (one block) -> cursors and seg[0]
+__global__ void __launch_bounds__(1024) k_src3_scan(const StepArgs* __restrict__ A, int s)
+{
+    __shared__ int warp_sums[32];
+    __shared__ int carry;
+    const SpDev& sp = A->sp[s];
+    const int nb = sp.npen * sp.nkey;
+    int* c = sp.kcount;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int b0 = 0; b0 < nb; b0 += blockDim.x) {
+        const int i = b0 + threadIdx.x;
+        const int v = i < nb ? c[i] : 0;
+        int x = v;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) warp_sums[warp] = x;
+        __syncthreads();
+        if (warp == 0) {
+            int w = lane < nw ? warp_sums[lane] : 0;
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, w, o);
+                if (lane >= o) w += y;
+            }
+            warp_sums[lane] = w;
+        }
+        __syncthreads();
+        const int incl = x + (warp > 0 ? warp_sums[warp - 1] : 0) + carry;
+        if (i < nb) c[i] = incl - v;
+        __syncthreads();
+        if (threadIdx.x == blockDim.x - 1) carry = incl;
+        __syncthreads();
+    }
+    const int total = carry;
+    const int nk = sp.nkey;
+    for (int i = threadIdx.x; i < sp.npen * (nk + 1); i += blockDim.x) {
+        const int p = i / (nk + 1), k = i % (nk + 1);
+        const int b = p * nk + k;   // k == nk: first bucket of the next pencil
+        sp.seg[0][i] = b < nb ? c[b] : total;
+    }
+}
+
+template <typename T, typename Src>
+__global__ void __launch_bounds__(256) k_src3_scatter(const StepArgs* __restrict__ A, int s, Src src)
+{
+    const SpDev& sp = A->sp[s];
+    VCoef<T> vc;
+    vc.init(sp);
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    const long long n_pad = (sp.n + 31) / 32 * 32;
+    bool over = false;
+    for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < n_pad; k += stride) {
+        const bool ok = k < sp.n;
+        MarkerIn3 mk{};
+        T v[3] = {(T)0, (T)0, (T)0};
+        int b = 0;
+        if (ok) {
+            mk = src.get(sp, k);
+            for (int d = 0; d < 3; ++d) v[d] = (T)mk.v[d];
+            b = bucket3<T>(sp, vc, v);
+        }
+        const int slot = warp_slot(sp.kcount, b, ok);
+        if (!ok) continue;
+        if (slot < 0 || (long long)slot >= sp.n) {
+            over = true;
+            continue;
+        }
+        const Pos<T> pos = pos_from_cells<T>(mk.xi, sp.nx);
+        pos.store(sp, 0, slot);
+        for (int d = 0; d < 3; ++d) reinterpret_cast<T*>(sp.mv[0][d])[slot] = v[d];
+        reinterpret_cast<T*>(sp.mf[0])[slot] = (T)mk.f;
+    }
+    if (over) atomicOr(&A->ctl->err, ERR_CAPACITY);
+}
+
+template <typename T>
+__global__ void k_get3(const StepArgs* __restrict__ A, int s, double* __restrict__ x, double* __restrict__ v,
+                       double* __restrict__ f)
+{
+    const SpDev& sp = A->sp[s];
+    const int cb = A->ctl->cur[s];
+    const long long n = sp.n;
+    for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
+        Pos<T> pos;
+        pos.load(sp, cb, (int)k);
+        if (x) x[k] = pos.cells() * sp.dx;
+        if (v)
+            for (int d = 0; d < 3; ++d) v[(long long)d * n + k] = (double)reinterpret_cast<const T*>(sp.mv[cb][d])[k];
+        if (f) f[k] = (double)reinterpret_cast<const T*>(sp.mf[cb])[k];
+    }
+}
+
+// internal [vz][vy][vx][x] -> caller [x][vx][vy][vz], 32 x 32 tiles of (x, vz)
+template <typename T>
+__global__ void k_getf3(const T* __restrict__ fg, const T* __restrict__ dg, int nx, int X, int Y, int Z,
+                        double* __restrict__ f, double* __restrict__ n)
+{
+    __shared__ double tile[2][32][33];
+    const int tx = (nx + 31) / 32, tz = (Z + 31) / 32;
+    const long long ntile = (long long)tx * tz * X * Y;
+    const long long nvf = (long long)X * Y * Z;
+    for (long long t = blockIdx.x; t < ntile; t += gridDim.x) {
+        const int xt = (int)(t % tx);
+        long long r = t / tx;
+        const int zt = (int)(r % tz);
+        r /= tz;
+        const int Xi = (int)(r / Y), Yi = (int)(r % Y);
+        for (int rr = threadIdx.y; rr < 32; rr += blockDim.y) {
+            const int zi = zt * 32 + rr, xi = xt * 32 + threadIdx.x;
+            if (zi < Z && xi < nx) {
+                const size_t o = (((size_t)zi * Y + Yi) * X + Xi) * nx + xi;
+                tile[0][rr][threadIdx.x] = (double)fg[o];
+                if (n) tile[1][rr][threadIdx.x] = (double)dg[o];
+            }
+        }
+        __syncthreads();
+        for (int rr = threadIdx.y; rr < 32; rr += blockDim.y) {
+            const int xi = xt * 32 + rr, zi = zt * 32 + threadIdx.x;
+            if (zi < Z && xi < nx) {
+                const size_t o = (size_t)xi * nvf + ((size_t)Xi * Y + Yi) * Z + zi;
+                f[o] = tile[0][threadIdx.x][rr];
+                if (n) n[o] = tile[1][threadIdx.x][rr];
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------
+static int cpt_of(int nx) { return nx <= P3_THREADS ? 1 : (nx <= 2 * P3_THREADS ? 2 : 4); }
+
+template <typename T>
+static cudaError_t set_pd3_attr(int smem)
+{
+    cudaError_t e;
+    if ((e = cudaFuncSetAttribute(k_pd3<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem))) return e;
+    if ((e = cudaFuncSetAttribute(k_pd3<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem))) return e;
+    return cudaFuncSetAttribute(k_pd3<T, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+}
+
+cudaError_t configure_vhs3(const StepArgs& h)
+{
+    const int smem = (int)pd3_smem_bytes(h.fd.nx, h.prec);
+    return h.prec == AVL_FP32 ? set_pd3_attr<float>(smem) : set_pd3_attr<double>(smem);
+}
+
+template <typename T>
+static void pd3_go(const StepArgs& h, const StepArgs* d, int mode, cudaStream_t st)
+{
+    const int smem = (int)pd3_smem_bytes(h.fd.nx, h.prec);
+    switch (cpt_of(h.fd.nx)) {
+        case 1: k_pd3<T, 1><<<h.npen_total, P3_THREADS, smem, st>>>(d, mode); break;
+        case 2: k_pd3<T, 2><<<h.npen_total, P3_THREADS, smem, st>>>(d, mode); break;
+        default: k_pd3<T, 4><<<h.npen_total, P3_THREADS, smem, st>>>(d, mode); break;
+    }
+}
+
+cudaError_t launch_pd3(const StepArgs& h, const StepArgs* d, int mode, cudaStream_t st)
+{
+    if (h.npen_total == 0) return cudaSuccess;
+    if (h.prec == AVL_FP32)
+        pd3_go<float>(h, d, mode, st);
+    else
+        pd3_go<double>(h, d, mode, st);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fin3(const StepArgs& h, const StepArgs* d, int all_species, cudaStream_t st)
+{
+    if (h.prec == AVL_FP32)
+        k_fin3<float><<<h.nfin_total, FIN3_X * FIN3_R, 0, st>>>(d, all_species);
+    else
+        k_fin3<double><<<h.nfin_total, FIN3_X * FIN3_R, 0, st>>>(d, all_species);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sort3(const StepArgs& h, const StepArgs* d, cudaStream_t st)
+{
+    if (h.npen_total == 0) return cudaSuccess;
+    if (h.prec == AVL_FP32)
+        k_sort3<float><<<h.npen_total, P3_THREADS, 0, st>>>(d);
+    else
+        k_sort3<double><<<h.npen_total, P3_THREADS, 0, st>>>(d);
+    return cudaGetLastError();
+}
+
+// source -> layout in buffer 0 (kcount must be zero; the caller clears it)
+template <typename Src>
+static cudaError_t source_to_layout3(const StepArgs& h, const StepArgs* d, int s, Src src, unsigned long long* bad,
+                                     cudaStream_t st)
+{
+    const long long n = h.sp[s].n;
+    const int blocks = (int)std::max<long long>(1, std::min<long long>((n + 255) / 256, 152ll * 16));
+    if (h.prec == AVL_FP32) {
+        k_src3_count<float, Src><<<blocks, 256, 0, st>>>(d, s, src, bad);
+        k_src3_scan<<<1, 1024, 0, st>>>(d, s);
+        k_src3_scatter<float, Src><<<blocks, 256, 0, st>>>(d, s, src);
+    } else {
+        k_src3_count<double, Src><<<blocks, 256, 0, st>>>(d, s, src, bad);
+        k_src3_scan<<<1, 1024, 0, st>>>(d, s);
+        k_src3_scatter<double, Src><<<blocks, 256, 0, st>>>(d, s, src);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_init3(const StepArgs& h, const StepArgs* d, int s, const int lattice[4], const avl_f0* f0_dev,
+                         unsigned long long seed, double jitter, cudaStream_t st)
+{
+    const LatticeSrc3 src{f0_dev, seed, jitter, s, {lattice[0], lattice[1], lattice[2], lattice[3]}};
+    return source_to_layout3(h, d, s, src, nullptr, st);
+}
+
+cudaError_t launch_set3(const StepArgs& h, const StepArgs* d, int s, long long n, const double* x, const double* v,
+                        const double* f, unsigned long long* bad, cudaStream_t st)
+{
+    const ArraySrc3 src{x, v, f, n};
+    return source_to_layout3(h, d, s, src, bad, st);
+}
+
+cudaError_t launch_get3(const StepArgs& h, const StepArgs* d, int s, double* x, double* v, double* f, cudaStream_t st)
+{
+    const long long n = h.sp[s].n;
+    if (n == 0) return cudaSuccess;
+    const int blocks = (int)std::min<long long>((n + 255) / 256, 152ll * 16);
+    if (h.prec == AVL_FP32)
+        k_get3<float><<<blocks, 256, 0, st>>>(d, s, x, v, f);
+    else
+        k_get3<double><<<blocks, 256, 0, st>>>(d, s, x, v, f);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_getf3(const StepArgs& h, int s, int which, double* f, double* n, cudaStream_t st)
+{
+    const SpDev& sp = h.sp[s];
+    const size_t cells = (size_t)sp.nvflat * sp.nx;
+    const long long ntile = (long long)((sp.nx + 31) / 32) * ((sp.nv[2] + 31) / 32) * sp.nv[0] * sp.nv[1];
+    const int blocks = (int)std::max<long long>(1, std::min<long long>(ntile, 152ll * 32));
+    dim3 block(32, 8);
+    if (h.prec == AVL_FP32) {
+        const float* dg = reinterpret_cast<const float*>(sp.acc[which]) + cells;
+        k_getf3<float><<<blocks, block, 0, st>>>(reinterpret_cast<const float*>(sp.fgrid), dg, sp.nx, sp.nv[0],
+                                                 sp.nv[1], sp.nv[2], f, n);
+    } else {
+        const double* dg = reinterpret_cast<const double*>(sp.acc[which]) + cells;
+        k_getf3<double><<<blocks, block, 0, st>>>(reinterpret_cast<const double*>(sp.fgrid), dg, sp.nx, sp.nv[0],
+                                                  sp.nv[1], sp.nv[2], f, n);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace avl

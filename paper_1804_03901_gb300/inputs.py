@@ -17,6 +17,12 @@ two_stream  Two-stream instability 1d1v, FP32: electrons 0.5 M(v-3) + 0.5
             +-10 v_th,i, unperturbed); nx = 512, L = 0.4 nx = 204.8,
             nv = 1024 on [-10, 10] v_th; 4 x 4 markers per cell (8388608 per
             species); dt = 0.05; 2000 steps.
+bump_on_tail  Bump-on-tail 1d3v, FP32: electrons 0.95 M3(v; 1) + 0.05
+            M3(v - 4 e_x; 0.5) (isotropic Maxwellians), density perturbation
+            1e-3 cos(0.3 x); immobile ions (the removed k = 0 mode);
+            nx = 256, L = 2 pi / 0.3 (k = 0.3 is mode 1), nv = 64^3 on
+            [-8, 8]^3; 2 markers per cell along x (134217728); dt = 0.05;
+            500 steps.
 """
 from __future__ import annotations
 
@@ -60,6 +66,19 @@ def two_stream(nx=512, nv=1024, lattice=(4, 4, 1, 1), steps=2000, nmodes=16, amp
     }
 
 
+def bump_on_tail(nx=256, nv=64, lattice=(2, 1, 1, 1), steps=500):
+    return {
+        "name": f"bump_on_tail_1d3v_fp32_nx{nx}_nv{nv}^3",
+        "nvdim": 3, "nx": nx, "L": 2 * math.pi / 0.3, "dt": 0.05, "precision": "fp32",
+        "species": [dict(q=-1.0, m=1.0, nv=(nv,) * 3, vmin=(-8.0,) * 3, vmax=(8.0,) * 3, mobile=True)],
+        "f0": [dict(beams=[(0.95, (0.0, 0.0, 0.0), (1.0, 1.0, 1.0)),
+                           (0.05, (4.0, 0.0, 0.0), (0.5, 0.5, 0.5))],
+                    modes=[(1, 1e-3, 0.0)])],
+        "lattice": [tuple(lattice)],
+        "seed": BASE_SEED + 2, "jitter": 1.0, "steps": steps,
+    }
+
+
 def random_markers(seed, n, L, vmin, vmax, v_overhang=0.05, fmin=1e-12, fmax=1.0):
     """Markers scattered uniformly in x and v (a few percent of them beyond
     the velocity grid), values log-uniform over [fmin, fmax]; values are made
@@ -76,3 +95,16 @@ def random_markers(seed, n, L, vmin, vmax, v_overhang=0.05, fmin=1e-12, fmax=1.0
         f = np.unique(np.concatenate([f.astype(np.float32), extra])).astype(np.float64)
     f = rng.permutation(f[:n])
     return x, v, f
+
+
+def random_markers3(seed, n, L, vmin, vmax, v_overhang=0.05, fmin=1e-12, fmax=1.0):
+    """1d3v version of random_markers: v has shape (3, n), each component
+    uniform over its range widened by v_overhang on both sides."""
+    rng = np.random.default_rng(seed)
+    x, _, f = random_markers(seed + 7919, n, L, vmin[0], vmax[0], v_overhang, fmin, fmax)
+    v = np.empty((3, n))
+    for d in range(3):
+        span = vmax[d] - vmin[d]
+        v[d] = rng.uniform(vmin[d] - v_overhang * span, vmax[d] + v_overhang * span, n)
+    return x, v, f
+
