@@ -27,6 +27,7 @@
 
 #include "avl_internal.cuh"
 #include "common.cuh"
+#include "ptx.cuh"
 
 namespace avl {
 
@@ -34,7 +35,7 @@ template <typename T>
 struct Cfg3;
 template <>
 struct Cfg3<float> {
-    static constexpr int MPT = 4;   // markers per thread and batch
+    static constexpr int MPT = 3;   // markers per thread and chunk
 };
 template <>
 struct Cfg3<double> {
@@ -155,14 +156,28 @@ __device__ void block_exscan(const int* in, int* out, int n, int items, int* wsu
 // ---------------------------------------------------------------------------
 // push + deposit
 // ---------------------------------------------------------------------------
-size_t pd3_smem_bytes(int nx, int prec)
+// A pencil's markers are walked in chunks of at most NB markers, each inside
+// one segment; the marker fields of the next chunk are staged into shared
+// memory by bulk copies (TMA) while the current one is processed.
+template <typename T>
+struct Stage3 {
+    static constexpr int NB = P3_THREADS * Cfg3<T>::MPT;   // markers per chunk
+    static constexpr int NF = sizeof(T) == 4 ? 6 : 5;       // staged fields
+    static constexpr int AL = 16 / (int)sizeof(T);           // markers per 16 bytes
+    static constexpr int SLEN = NB + 2 * AL;                 // staged entries per field
+};
+
+template <typename T>
+static size_t pd3_bytes(int nx)
 {
-    const size_t tb = prec == AVL_FP32 ? 4 : 8;
-    const size_t nb = (size_t)P3_THREADS * (prec == AVL_FP32 ? Cfg3<float>::MPT : Cfg3<double>::MPT);
-    size_t b = tb * (32 * (size_t)nx + 7 * nb + nx);   // ring, sorted payload, E
-    b += 4 * (2 * (size_t)nx + 1) + 64;                // histogram, bin starts, padding
+    using S = Stage3<T>;
+    size_t b = 2 * (size_t)S::NF * S::SLEN * sizeof(T);      // two staging buffers
+    b += sizeof(T) * (32 * (size_t)nx + 7 * (size_t)S::NB + nx);   // ring, sorted payload, E
+    b += 4 * (2 * (size_t)nx + 1) + 4 * (NV3_MAX + 2) + 64;  // histogram, bin starts, segment row
     return (b + 15) / 16 * 16;
 }
+
+size_t pd3_smem_bytes(int nx, int prec) { return prec == AVL_FP32 ? pd3_bytes<float>(nx) : pd3_bytes<double>(nx); }
 
 template <typename T>
 struct Ring {
@@ -170,7 +185,7 @@ struct Ring {
     int nx;
     __device__ __forceinline__ T* at(int row, int q, int c, int x) const
     {
-        return r + ((size_t)(((row & 3) * 4 + q) * 2 + c)) * nx + x;
+        return r + (((row & 3) * 4 + q) * 2 + c) * nx + x;
     }
 };
 
@@ -186,15 +201,21 @@ __device__ __forceinline__ void plane_weights(T wy, T wz, T (&q)[4])
     q[3] = wy * wz;
 }
 
+// the pencil's four (v_y, v_z) planes: first grid offset of each (row 0,
+// column 0) and whether it lies on the grid
+struct Planes {
+    int base[4];
+    bool ok[4];
+};
+
 // the 16 cloud-in-cell contributions of one marker whose v_x dual row j is
-// not the segment's: into the ring (rows within one of the segment's) or
+// not its segment's: into the ring (rows within one of the segment's) or
 // straight into the global accumulator
 template <typename T>
-__device__ __forceinline__ void deposit_single(const SpDev& sp, const Ring<T>& ring, bool to_ring, T* gacc,
-                                               size_t cells, int bin, T u, int j, T w, int pjy, int pjz,
+__device__ __forceinline__ void deposit_single(const Ring<T>& ring, bool to_ring, T* gacc, int cells,
+                                               const Planes& pl, int nx, int nvx, int bin, T u, int j, T w,
                                                const T (&wq)[4], T f)
 {
-    const int nx = sp.nx, nvx = sp.nv[0], nvy = sp.nv[1], nvz = sp.nv[2];
 #pragma unroll
     for (int cx = 0; cx < 2; ++cx) {
         const int x = cx ? (bin + 1 == nx ? 0 : bin + 1) : bin;
@@ -206,15 +227,14 @@ __device__ __forceinline__ void deposit_single(const SpDev& sp, const Ring<T>& r
             const T av = ax * (cv ? w : (T)1 - w);
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
-                const int ky = pjy + (q & 1), kz = pjz + (q >> 1);
-                if (ky < 0 || ky >= nvy || kz < 0 || kz >= nvz) continue;
+                if (!pl.ok[q]) continue;
                 const T a = av * wq[q];
                 if (a == (T)0) continue;
                 if (to_ring) {
                     atomicAdd(ring.at(row, q, 0, x), a * f);
                     atomicAdd(ring.at(row, q, 1, x), a);
                 } else {
-                    const size_t o = ((size_t)((kz * nvy + ky) * nvx + row)) * nx + x;
+                    const int o = pl.base[q] + row * nx + x;
                     atomicAdd(gacc + o, a * f);
                     atomicAdd(gacc + cells + o, a);
                 }
@@ -223,48 +243,59 @@ __device__ __forceinline__ void deposit_single(const SpDev& sp, const Ring<T>& r
     }
 }
 
-// add one finished v_x row of the ring into the global accumulator (columns
-// of this thread) and clear it
-template <typename T, int CPT>
-__device__ __forceinline__ void flush_row(const SpDev& sp, const Ring<T>& ring, T* gacc, size_t cells, int row,
-                                          int pjy, int pjz)
+// exclusive scan of hist[0, nx) into start[0, nx], start[nx] = total; each
+// thread owns CPT consecutive bins and clears them for the next chunk
+template <int CPT>
+__device__ __forceinline__ void chunk_scan(int* hist, int* start, int nx, int* wsum)
 {
-    const int nx = sp.nx, nvx = sp.nv[0], nvy = sp.nv[1], nvz = sp.nv[2];
-    if (row < 0 || row >= nvx) return;
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const int i0 = t * CPT;
+    int v[CPT], loc = 0;
 #pragma unroll
-    for (int c = 0; c < CPT; ++c) {
-        const int x = threadIdx.x + c * P3_THREADS;
-        if (x >= nx) continue;
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const int ky = pjy + (q & 1), kz = pjz + (q >> 1);
-            const bool ok = ky >= 0 && ky < nvy && kz >= 0 && kz < nvz;
-            T* pn = ring.at(row, q, 0, x);
-            T* pd = ring.at(row, q, 1, x);
-            const T vn = *pn, vd = *pd;
-            *pn = (T)0;
-            *pd = (T)0;
-            if (ok && vd != (T)0) {
-                const size_t o = ((size_t)((kz * nvy + ky) * nvx + row)) * nx + x;
-                atomicAdd(gacc + o, vn);
-                atomicAdd(gacc + cells + o, vd);
-            }
-        }
+    for (int i = 0; i < CPT; ++i) {
+        v[i] = i0 + i < nx ? hist[i0 + i] : 0;
+        loc += v[i];
     }
+    int incl = loc;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    if (lane == 31) wsum[warp] = incl;
+    __syncthreads();
+    int pre = 0;
+    for (int w = 0; w < warp; ++w) pre += wsum[w];
+    int run = pre + incl - loc;
+#pragma unroll
+    for (int i = 0; i < CPT; ++i) {
+        if (i0 + i < nx) {
+            start[i0 + i] = run;
+            hist[i0 + i] = 0;
+        }
+        run += v[i];
+    }
+    if (i0 < nx && nx <= i0 + CPT) start[nx] = run;
+    __syncthreads();
 }
 
 // mode 0: deposit of the current markers of every species (refresh);
 // mode 1: push of the mobile species, then deposit of the new state
 template <typename T, int CPT>
-__global__ void __launch_bounds__(P3_THREADS, (sizeof(T) == 4 && CPT == 1) ? 3 : 1)
+__global__ void __launch_bounds__(P3_THREADS, (sizeof(T) == 4 && CPT == 1) ? 2 : 1)
     k_pd3(const StepArgs* __restrict__ A, int mode)
 {
+    using S = Stage3<T>;
     constexpr int MPT = Cfg3<T>::MPT;
-    constexpr int NB = P3_THREADS * MPT;
+    constexpr int NB = S::NB, NF = S::NF, AL = S::AL, SLEN = S::SLEN;
+    constexpr int FX = NF - 4;   // staged field of v_x (then v_y, v_z, f)
     extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ uint64_t bar[2];
     __shared__ int wsum[P3_THREADS / 32];
     __shared__ unsigned long long mov_s, far_s;
-    __shared__ int bad_s;
+    __shared__ int flag_s;
+    __shared__ int nmv_s;
+    __shared__ const void* src_s[6];
 
     const int g = blockIdx.x;
     const int s = species_of_pen(A, g);
@@ -273,62 +304,133 @@ __global__ void __launch_bounds__(P3_THREADS, (sizeof(T) == 4 && CPT == 1) ? 3 :
     if (push && !sp.mobile) return;
     Ctl* ctl = A->ctl;
     const int p = g - sp.pen_base;
-    const int nx = sp.nx, nvx = sp.nv[0];
-    const int pjy = p % (sp.nv[1] + 1) - 1, pjz = p / (sp.nv[1] + 1) - 1;
+    const int nx = sp.nx, nvx = sp.nv[0], nvy = sp.nv[1], nvz = sp.nv[2], nkey = sp.nkey;
+    const int pjy = p % (nvy + 1) - 1, pjz = p / (nvy + 1) - 1;
     const int cb = ctl->cur[s];
-    const size_t cells = (size_t)sp.nvflat * nx;
-    T* gacc = reinterpret_cast<T*>(sp.acc[ctl->asel[s]]);
-    const int* seg = sp.seg[cb] + (size_t)p * (sp.nkey + 1);
+    const int cells = sp.nvflat * nx;
+    T* const gacc = reinterpret_cast<T*>(sp.acc[ctl->asel[s]]);
+    const int* segg = sp.seg[cb] + (size_t)p * (nkey + 1);
 
-    // shared memory: ring | payload (7 arrays of NB) | E | hist | start
-    Ring<T> ring{reinterpret_cast<T*>(smem), nx};
-    T* pay = ring.r + 32 * (size_t)nx;
-    T* Es = pay + 7 * (size_t)NB;
+    // shared memory: staging | ring | payload (7 x NB) | E | hist | start | segment row
+    T* stage = reinterpret_cast<T*>(smem);
+    Ring<T> ring{stage + 2 * NF * SLEN, nx};
+    T* pay = ring.r + 32 * nx;
+    T* Es = pay + 7 * NB;
     int* hist = reinterpret_cast<int*>(Es + nx);
     int* start = hist + nx;
+    int* segs = start + nx + 1;
 
+    if (threadIdx.x == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        fence_mbar_init();
+        mov_s = 0;
+        far_s = 0;
+        flag_s = 0;
+        nmv_s = 0;
+        if constexpr (sizeof(T) == 4) {
+            src_s[0] = sp.mx[cb];
+            src_s[1] = sp.moff[cb];
+        } else {
+            src_s[0] = sp.mx[cb];
+        }
+        src_s[FX + 0] = sp.mv[cb][0];
+        src_s[FX + 1] = sp.mv[cb][1];
+        src_s[FX + 2] = sp.mv[cb][2];
+        src_s[FX + 3] = sp.mf[cb];
+    }
     for (int i = threadIdx.x; i < 32 * nx; i += P3_THREADS) ring.r[i] = (T)0;
     for (int i = threadIdx.x; i < nx; i += P3_THREADS) {
         hist[i] = 0;
         if (push) Es[i] = sizeof(T) == 4 ? (T)A->fd.E32[i] : (T)A->fd.E64[i];
     }
-    if (threadIdx.x == 0) {
-        mov_s = 0;
-        far_s = 0;
-        bad_s = 0;
-    }
+    for (int i = threadIdx.x; i <= nkey; i += P3_THREADS) segs[i] = segg[i];
     __syncthreads();
 
+    // bulk copy of the chunk [b, b + cnt) of every staged field into buffer bf
+    auto issue = [&](int bf, int b, int cnt) {
+        const int a0 = b & ~(AL - 1);
+        const int a1 = (b + cnt + AL - 1) & ~(AL - 1);
+        const unsigned bytes = (unsigned)(a1 - a0) * (unsigned)sizeof(T);
+        mbar_arrive_expect_tx(&bar[bf], bytes * NF);
+        for (int f = 0; f < NF; ++f)
+            bulk_g2s(stage + (bf * NF + f) * SLEN, reinterpret_cast<const T*>(src_s[f]) + a0, bytes, &bar[bf]);
+    };
+    // first chunk at or after key k whose segment is not empty
+    auto first_from = [&](int k, int& kb) {
+        for (; k < nkey; ++k)
+            if (segs[k] < segs[k + 1]) break;
+        kb = k < nkey ? segs[k] : 0;
+        return k;
+    };
+    if (threadIdx.x == 0) {
+        int b;
+        const int k0 = first_from(0, b);
+        if (k0 < nkey) issue(0, b, min(NB, segs[k0 + 1] - b));
+    }
+
+    // cached marker pointers (in-place write back)
+    T* const gvx = reinterpret_cast<T*>(sp.mv[cb][0]);
+    void* const gx = sp.mx[cb];
+    float* const goff = sp.moff[cb];
     VCoef<T> vc;
     vc.init(sp);
     const T qm_dt = (T)sp.qm_dt, dt_dx = (T)sp.dt_dx;
-    T* mvx = reinterpret_cast<T*>(sp.mv[cb][0]);
-    const T* mvy = reinterpret_cast<const T*>(sp.mv[cb][1]);
-    const T* mvz = reinterpret_cast<const T*>(sp.mv[cb][2]);
-    const T* mf = reinterpret_cast<const T*>(sp.mf[cb]);
+    Planes pl;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int ky = pjy + (q & 1), kz = pjz + (q >> 1);
+        pl.ok[q] = ky >= 0 && ky < nvy && kz >= 0 && kz < nvz;
+        pl.base[q] = pl.ok[q] ? (kz * nvy + ky) * nvx * nx : 0;
+    }
 
-    T R0[CPT][8], R1[CPT][8];
+    // register rows: Rm = row jseg - 1, R0 = row jseg, R1 = row jseg + 1;
+    // entry 2q: numerator, 2q + 1: denominator of plane q
+    T Rm[CPT][8], R0[CPT][8], R1[CPT][8];
 #pragma unroll
     for (int c = 0; c < CPT; ++c)
 #pragma unroll
-        for (int e = 0; e < 8; ++e) R0[c][e] = R1[c][e] = (T)0;
+        for (int e = 0; e < 8; ++e) Rm[c][e] = R0[c][e] = R1[c][e] = (T)0;
     unsigned long long nmov = 0, nfar = 0;
+    int buf = 0;
+    unsigned ph0 = 0, ph1 = 0;
 
-    for (int k = 0; k < sp.nkey; ++k) {
+    for (int k = 0; k < nkey; ++k) {
         const int jseg = k - 1;
-        const int beg = seg[k], end = seg[k + 1];
-        for (int b0 = beg; b0 < end; b0 += NB) {
-            T pu[MPT], pw[MPT], pf[MPT], pq[MPT][4];
+        const int send = segs[k + 1];
+        for (int b0 = segs[k]; b0 < send; b0 += NB) {
+            const int cnt = min(NB, send - b0);
+            // stage the next chunk into the other buffer (free since the end of
+            // the previous chunk)
+            if (threadIdx.x == 0) {
+                int nk = k, nb = b0 + NB;
+                if (nb >= send) nk = first_from(k + 1, nb);
+                if (nk < nkey) issue(buf ^ 1, nb, min(NB, segs[nk + 1] - nb));
+            }
+            const unsigned ph = buf ? ph1 : ph0;
+            if (!mbar_wait_bounded(&bar[buf], ph, WAIT_LIMIT)) flag_s = 1;
+            if (buf) ph1 ^= 1u; else ph0 ^= 1u;
+            const T* st = stage + buf * NF * SLEN;
+            const int o0 = b0 & (AL - 1);
+
+            T pu[MPT], pw[MPT], pf[MPT], py[MPT], pz[MPT];
             int pbin[MPT], prank[MPT];
 #pragma unroll
             for (int m = 0; m < MPT; ++m) {
                 prank[m] = -1;
                 pbin[m] = 0;
-                const int idx = b0 + m * P3_THREADS + threadIdx.x;
-                if (idx >= end) continue;
+                const int i = m * P3_THREADS + threadIdx.x;
+                if (i >= cnt) continue;
+                const int si = o0 + i;
+                const int idx = b0 + i;
                 Pos<T> pos;
-                pos.load(sp, cb, idx);
-                T vx = mvx[idx];
+                if constexpr (sizeof(T) == 4) {
+                    pos.c = reinterpret_cast<const int*>(st)[si];
+                    pos.o = st[SLEN + si];
+                } else {
+                    pos.xi = st[si];
+                }
+                T vx = st[(FX + 0) * SLEN + si];
                 if (push) {
                     int i0;
                     T wx;
@@ -338,16 +440,21 @@ __global__ void __launch_bounds__(P3_THREADS, (sizeof(T) == 4 && CPT == 1) ? 3 :
                     const T El = ((T)1 - wx) * Es[ia] + wx * Es[ib];
                     vx = vx + qm_dt * El;
                     pos.drift(vx * dt_dx, nx);
-                    pos.store(sp, cb, idx);
-                    mvx[idx] = vx;
+                    if constexpr (sizeof(T) == 4) {
+                        reinterpret_cast<int*>(gx)[idx] = pos.c;
+                        goff[idx] = pos.o;
+                    } else {
+                        reinterpret_cast<double*>(gx)[idx] = pos.xi;
+                    }
+                    gvx[idx] = vx;
                 }
-                const T f = mf[idx];
+                const T f = st[(FX + 3) * SLEN + si];
                 T wy, wz, w;
-                const int jy = dual3(mvy[idx], vc.a[1], vc.b[1], vc.n[1], wy);
-                const int jz = dual3(mvz[idx], vc.a[2], vc.b[2], vc.n[2], wz);
+                const int jy = dual3(st[(FX + 1) * SLEN + si], vc.a[1], vc.b[1], vc.n[1], wy);
+                const int jz = dual3(st[(FX + 2) * SLEN + si], vc.a[2], vc.b[2], vc.n[2], wz);
                 if (jy != pjy || jz != pjz) {
                     // outside the pencil only when the footprint misses the grid
-                    if (jy >= -1 && jy < vc.n[1] && jz >= -1 && jz < vc.n[2]) bad_s = 1;
+                    if (jy >= -1 && jy < nvy && jz >= -1 && jz < nvz) flag_s |= 2;
                     continue;
                 }
                 const int jx = dual3(vx, vc.a[0], vc.b[0], nvx, w);
@@ -357,52 +464,76 @@ __global__ void __launch_bounds__(P3_THREADS, (sizeof(T) == 4 && CPT == 1) ? 3 :
                 pos.cic(i0, u);
                 int bin = i0 < 0 ? i0 + nx : i0;
                 bin = min(max(bin, 0), nx - 1);
-                T wq[4];
-                plane_weights(wy, wz, wq);
                 const int d = jx - jseg;
                 if (d == 0) {
                     prank[m] = atomicAdd(&hist[bin], 1);
-                    pbin[m] = bin;
-                    pu[m] = u;
-                    pw[m] = w;
-                    pf[m] = f;
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) pq[m][q] = wq[q];
                 } else {
+                    // off its segment's row: parked at the tail of the payload
+                    // arrays (the stays fill them from the front) and deposited
+                    // by the whole block after the sort
                     ++nmov;
-                    const bool near = d == 1 || d == -1;
-                    if (!near) ++nfar;
-                    deposit_single<T>(sp, ring, near, gacc, cells, bin, u, jx, w, pjy, pjz, wq, f);
+                    if (d > 1 || d < -1) ++nfar;
+                    const int o = NB - 1 - atomicAdd(&nmv_s, 1);
+                    pay[0 * NB + o] = u;
+                    pay[1 * NB + o] = w;
+                    pay[2 * NB + o] = f;
+                    pay[3 * NB + o] = wy;
+                    pay[4 * NB + o] = wz;
+                    pay[5 * NB + o] = (T)bin;
+                    pay[6 * NB + o] = (T)jx;
                 }
+                pbin[m] = bin;
+                pu[m] = u;
+                pw[m] = w;
+                pf[m] = f;
+                py[m] = wy;
+                pz[m] = wz;
             }
             __syncthreads();
-            block_exscan(hist, start, nx, CPT, wsum);
-            for (int i = threadIdx.x; i < nx; i += P3_THREADS) hist[i] = 0;
+            const int nmv = nmv_s;
+            chunk_scan<CPT>(hist, start, nx, wsum);   // every thread has read nmv_s by its barriers
+            if (threadIdx.x == 0) nmv_s = 0;
             // stays into x-sorted order
 #pragma unroll
             for (int m = 0; m < MPT; ++m) {
                 if (prank[m] < 0) continue;
                 const int o = start[pbin[m]] + prank[m];
+                T wq[4];
+                plane_weights(py[m], pz[m], wq);
                 pay[0 * NB + o] = pu[m];
                 pay[1 * NB + o] = pw[m];
                 pay[2 * NB + o] = pf[m];
 #pragma unroll
-                for (int q = 0; q < 4; ++q) pay[(3 + q) * NB + o] = pq[m][q];
+                for (int q = 0; q < 4; ++q) pay[(3 + q) * NB + o] = wq[q];
             }
             __syncthreads();
-            // gather: column x takes weight 1 - u from dual cell x and u from x - 1
+            // markers off their segment's row: one per thread
+            for (int i = threadIdx.x; i < nmv; i += P3_THREADS) {
+                const int o = NB - 1 - i;
+                T wq[4];
+                plane_weights(pay[3 * NB + o], pay[4 * NB + o], wq);
+                const int jx = (int)pay[6 * NB + o];
+                const int d = jx - jseg;
+                deposit_single<T>(ring, d == 1 || d == -1, gacc, cells, pl, nx, nvx, (int)pay[5 * NB + o],
+                                  pay[0 * NB + o], jx, pay[1 * NB + o], wq, pay[2 * NB + o]);
+            }
+            // gather: column x takes weight u from the markers of dual cell
+            // x - 1 and 1 - u from those of dual cell x, which follow them in
+            // the sorted order (one loop; two at the periodic seam)
 #pragma unroll
             for (int c = 0; c < CPT; ++c) {
                 const int x = threadIdx.x + c * P3_THREADS;
                 if (x >= nx) continue;
                 const int xm = x == 0 ? nx - 1 : x - 1;
-#pragma unroll
-                for (int side = 0; side < 2; ++side) {
-                    const int bb = side ? xm : x;
-                    const int i1 = start[bb + 1];
-                    for (int i = start[bb]; i < i1; ++i) {
+                const int mid = start[x];
+                const int lo0 = start[xm], hi0 = x == 0 ? start[nx] : mid;
+                const int hi1 = start[x + 1];
+                for (int pass = 0; pass < (x == 0 ? 2 : 1); ++pass) {
+                    const int lo = pass ? mid : lo0, hi = (x == 0 && !pass) ? hi0 : hi1;
+                    for (int i = lo; i < hi; ++i) {
                         const T u = pay[i];
-                        const T ax = side ? u : (T)1 - u;
+                        const bool upper = x == 0 ? pass == 0 : i < mid;
+                        const T ax = upper ? u : (T)1 - u;
                         const T a1 = ax * pay[NB + i];
                         const T a0 = ax - a1;
                         const T f = pay[2 * NB + i];
@@ -419,32 +550,60 @@ __global__ void __launch_bounds__(P3_THREADS, (sizeof(T) == 4 && CPT == 1) ? 3 :
                 }
             }
             __syncthreads();
+            buf ^= 1;
         }
-        // row jseg is complete in registers: into the ring; row jseg - 1 is
-        // complete (no later segment reaches it): into the global accumulator
-        if (jseg >= 0) {
+        // row jseg - 1 is complete (no later segment reaches it): registers plus
+        // the ring's movers into the global accumulator; then rotate the rows
+        const int row = jseg - 1;
+        if (row >= 0) {
 #pragma unroll
             for (int c = 0; c < CPT; ++c) {
                 const int x = threadIdx.x + c * P3_THREADS;
                 if (x >= nx) continue;
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
-                    *ring.at(jseg, q, 0, x) += R0[c][2 * q];
-                    *ring.at(jseg, q, 1, x) += R0[c][2 * q + 1];
+                    T* rn = ring.at(row, q, 0, x);
+                    T* rd = ring.at(row, q, 1, x);
+                    const T vn = Rm[c][2 * q] + *rn, vd = Rm[c][2 * q + 1] + *rd;
+                    *rn = (T)0;
+                    *rd = (T)0;
+                    if (pl.ok[q] && vd != (T)0) {
+                        const int o = pl.base[q] + row * nx + x;
+                        atomicAdd(gacc + o, vn);
+                        atomicAdd(gacc + cells + o, vd);
+                    }
                 }
             }
         }
-        flush_row<T, CPT>(sp, ring, gacc, cells, jseg - 1, pjy, pjz);
 #pragma unroll
         for (int c = 0; c < CPT; ++c)
 #pragma unroll
             for (int e = 0; e < 8; ++e) {
+                Rm[c][e] = R0[c][e];
                 R0[c][e] = R1[c][e];
                 R1[c][e] = (T)0;
             }
         __syncthreads();
     }
-    flush_row<T, CPT>(sp, ring, gacc, cells, nvx - 1, pjy, pjz);
+    // the last row (nvx - 1) after the last segment: registers plus ring
+    {
+        const int row = nvx - 1;
+#pragma unroll
+        for (int c = 0; c < CPT; ++c) {
+            const int x = threadIdx.x + c * P3_THREADS;
+            if (x >= nx) continue;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const T vn = Rm[c][2 * q] + *ring.at(row, q, 0, x);
+                const T vd = Rm[c][2 * q + 1] + *ring.at(row, q, 1, x);
+                if (pl.ok[q] && vd != (T)0) {
+                    const int o = pl.base[q] + row * nx + x;
+                    atomicAdd(gacc + o, vn);
+                    atomicAdd(gacc + cells + o, vd);
+                }
+            }
+        }
+    }
 
     if (nmov) atomicAdd(&mov_s, nmov);
     if (nfar) atomicAdd(&far_s, nfar);
@@ -452,7 +611,8 @@ __global__ void __launch_bounds__(P3_THREADS, (sizeof(T) == 4 && CPT == 1) ? 3 :
     if (threadIdx.x == 0) {
         if (mov_s) atomicAdd(&ctl->movers[s], mov_s);
         if (far_s) atomicAdd(&ctl->far_movers[s], far_s);
-        if (bad_s) atomicOr(&ctl->err, ERR_CAPACITY);
+        if (flag_s & 2) atomicOr(&ctl->err, ERR_CAPACITY);
+        if (flag_s & 1) atomicOr(&ctl->err, ERR_TIMEOUT);
     }
 }
 
