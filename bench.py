@@ -54,7 +54,8 @@ def parse():
     p.add_argument("--steps", type=int, default=2000)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    p.add_argument("--workload", choices=["two_stream", "landau", "bump_on_tail"], default="two_stream")
+    p.add_argument("--workload", choices=["two_stream", "landau", "bump_on_tail", "two_stream_adjoint"],
+                   default="two_stream")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--nv", type=int, default=0, help="velocity cells (profiling of a smaller case)")
@@ -67,10 +68,12 @@ def workload(name, nv=0):
         return inputs.two_stream(nv=nv) if nv else inputs.two_stream()
     if name == "bump_on_tail":
         return inputs.bump_on_tail(nv=nv) if nv else inputs.bump_on_tail()
+    if name == "two_stream_adjoint":
+        return inputs.two_stream_adjoint(nv=nv) if nv else inputs.two_stream_adjoint()
     return inputs.landau(nv=nv) if nv else inputs.landau()
 
 
-SAMPLE_FRACTION = {"two_stream": 1.0 / 64, "bump_on_tail": 1.0 / 256, "landau": 1.0}
+SAMPLE_FRACTION = {"two_stream": 1.0 / 64, "bump_on_tail": 1.0 / 256, "landau": 1.0, "two_stream_adjoint": 1.0 / 16}
 
 
 def markers_of(w):
@@ -357,10 +360,118 @@ def run_ours(args):
         torch.distributed.destroy_process_group()
 
 
+def run_adjoint(args):
+    """Cost of avl_adjoint over the forward run it differentiates, and its
+    gradient against central differences of the FP64 forward run."""
+    import torch
+    from paper_1804_03901_gb300 import avl as A
+    w = workload(args.workload, args.nv)
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    nsteps, ckpt = w["steps"], w["ckpt"]
+    f0 = w["f0"][0]
+
+    def sim_of(prec, f0e):
+        w2 = dict(w)
+        w2["precision"] = prec
+        w2["f0"] = [f0e] + w["f0"][1:]
+        return build_sim(A, w2, stream.cuda_stream)
+
+    def theta(f0e):
+        return A.make_f0(f0e["beams"], f0e["modes"])
+
+    res = {}
+    for prec in ("fp32", "fp64"):
+        sim = sim_of(prec, f0)
+        sim.step(3)
+        init_markers(A, sim, w)
+        sim.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        sim.step(nsteps)
+        e1.record(stream)
+        sim.synchronize()
+        fwd_ms = e0.elapsed_time(e1)
+        sim.adjoint(0, theta(f0), nsteps, ckpt)   # warm-up (buffers)
+        t0 = time.perf_counter()
+        J, ga, gu = sim.adjoint(0, theta(f0), nsteps, ckpt)
+        adj_ms = 1e3 * (time.perf_counter() - t0)
+        res[prec] = {"J": J, "grad": np.concatenate([ga, gu]), "forward_ms": fwd_ms, "adjoint_ms": adj_ms}
+        sim.close()
+
+    # central differences of the FP64 forward run (avl_step), h = 1e-6
+    h = 1e-6
+    amps = [a for (_, a, _) in f0["modes"]]
+    drifts = [u[0] for (_, u, _) in f0["beams"]]
+
+    nfd = nsteps
+
+    def J_of(a, d):
+        f0e = {"beams": [(n, (d[b],) + tuple(u[1:]), vth) for b, (n, u, vth) in enumerate(f0["beams"])],
+               "modes": [(m, a[k], ph) for k, (m, _, ph) in enumerate(f0["modes"])]}
+        sim = sim_of("fp64", f0e)
+        sim.step(nfd)
+        E = sim.get_E()
+        sim.close()
+        return 0.5 * float(np.sum(E ** 2)) * (w["L"] / w["nx"])
+
+    def central(hh):
+        out = []
+        for k in range(len(amps)):
+            ap, am = list(amps), list(amps)
+            ap[k] += hh
+            am[k] -= hh
+            out.append((J_of(ap, drifts) - J_of(am, drifts)) / (2 * hh))
+        for b in range(len(drifts)):
+            dp, dm = list(drifts), list(drifts)
+            dp[b] += hh
+            dm[b] -= hh
+            out.append((J_of(amps, dp) - J_of(amps, dm)) / (2 * hh))
+        return np.array(out)
+
+    fd_h, fd_h2 = central(h), central(h / 2)
+    fd = (4.0 * fd_h2 - fd_h) / 3.0   # Richardson: removes the h^2 term of central differences
+    scale = float(np.max(np.abs(fd)))
+    # the same check over a short horizon in the linear phase (T = 5), where
+    # no marker crosses a cloud-in-cell kink under the perturbation
+    nfd = nsteps // 5
+    lin = {}
+    for prec in ("fp64", "fp32"):
+        sim = sim_of(prec, f0)
+        _, ga, gu = sim.adjoint(0, theta(f0), nfd, ckpt)
+        lin[prec] = np.concatenate([ga, gu])
+        sim.close()
+    fl_h, fl_h2 = central(h), central(h / 2)
+    fl = (4.0 * fl_h2 - fl_h) / 3.0
+    sl = float(np.max(np.abs(fl)))
+    linear = {"steps": nfd, "rel_diff_h_vs_richardson": float(np.max(np.abs(fl_h - fl)) / sl),
+              "fp64_adjoint_rel_err": float(np.max(np.abs(lin["fp64"] - fl)) / sl),
+              "fp32_adjoint_rel_err": float(np.max(np.abs(lin["fp32"] - fl)) / sl)}
+    r32, r64 = res["fp32"], res["fp64"]
+    line = {"metric": "adjoint_over_forward", "value": r32["adjoint_ms"] / r32["forward_ms"], "unit": "x",
+            "higher_is_better": False, "n_gpus": 1, "steps": nsteps, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": w["name"], "electrons": markers_of({"nx": w["nx"], "species": w["species"][:1],
+                                                                      "lattice": w["lattice"][:1]}),
+                       "ckpt_every": ckpt, "params": len(fd), "ions": "immobile"},
+            "fp32": {"forward_ms": r32["forward_ms"], "adjoint_ms": r32["adjoint_ms"], "J": r32["J"],
+                     "grad_rel_err_vs_fd64": float(np.max(np.abs(r32["grad"] - fd)) / scale)},
+            "fp64": {"forward_ms": r64["forward_ms"], "adjoint_ms": r64["adjoint_ms"], "J": r64["J"],
+                     "adjoint_over_forward": r64["adjoint_ms"] / r64["forward_ms"],
+                     "grad_rel_err_vs_fd64": float(np.max(np.abs(r64["grad"] - fd)) / scale)},
+            "fd": {"h": h, "kind": "central differences of the FP64 avl_step run at h and h/2, Richardson-combined",
+                   "rel_diff_h_vs_richardson": float(np.max(np.abs(fd_h - fd)) / scale),
+                   "fp64_adjoint_rel_err_vs_plain_h": float(np.max(np.abs(r64["grad"] - fd_h)) / scale),
+                   "linear_phase": linear},
+            "grad_fd64": fd.tolist()}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "two_stream_adjoint":
+        run_adjoint(args)
     else:
         run_ours(args)
 

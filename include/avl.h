@@ -206,6 +206,23 @@ avl_status avl_field_solve(int32_t nx, double L, double poisson_const, int32_t s
 avl_status avl_field_solve_noalloc(int32_t nx, double L, double poisson_const, int32_t softening,
                                    const double* rho, double* E, void* cuda_stream);
 
+/* Gradient of the field energy at the final time (spec extension; the
+ * paper has no adjoint): J = 1/2 sum_i E_i(T)^2 dx after nsteps steps that
+ * start from the markers each species got from its last avl_init_markers,
+ * with the f0 of species s replaced by theta.  Outputs (host): *J,
+ * dJ_damp[m] = dJ/d theta->amp[m] (theta->nmode values) and dJ_ddrift[b] =
+ * dJ/d theta->beam_u[b][0] (theta->nbeam values).  The discrete adjoint of
+ * the step (push, Eq. 4 reconstruction, Eq. 14 moment, Eq. 6 Poisson) runs
+ * backwards over the step history, recomputed segment by segment from
+ * checkpoints of the markers taken every ckpt_every steps; its device memory
+ * (about (ckpt_every + 1) marker states and grids, plus one marker state per
+ * checkpoint) is kept by the context for the next call.  The context's own
+ * markers, f, rho and E are left untouched.  Blocks until done.  1d1v only.
+ * Errors: AVL_EINVAL (nvdim 3, NULL pointers, nsteps < 0, ckpt_every < 1,
+ * theta counts), AVL_ESTATE (a species without lattice markers), AVL_ENOMEM. */
+avl_status avl_adjoint(avl_ctx* ctx, int32_t s, const avl_f0* theta, int32_t nsteps, int32_t ckpt_every,
+                       double* dJ_damp, double* dJ_ddrift, double* J);
+
 /* Per-kernel timing (the paper's time breakdown, Sec. 3.2): advance nsteps
  * steps exactly as avl_step does, but launched kernel by kernel with CUDA
  * events recorded on the context stream around each kernel; writes the summed

@@ -26,7 +26,7 @@ STATUS_NAMES = {0: "AVL_OK", 1: "AVL_EINVAL", 2: "AVL_ENOMEM", 3: "AVL_ECUDA",
 EXPORTED = ["avl_create", "avl_destroy", "avl_last_error", "avl_init_markers", "avl_set_markers",
             "avl_marker_count", "avl_get_markers", "avl_step", "avl_get_f", "avl_get_rho",
             "avl_get_E", "avl_get_diag", "avl_get_stats", "avl_field_solve", "avl_field_solve_noalloc",
-            "avl_profile_steps",
+            "avl_profile_steps", "avl_adjoint",
             "avl_synchronize"]
 
 
@@ -77,6 +77,7 @@ def _load():
         "avl_field_solve": (C.c_int, [C.c_int32, C.c_double, C.c_double, C.c_int32, vp, vp, vp]),
         "avl_field_solve_noalloc": (C.c_int, [C.c_int32, C.c_double, C.c_double, C.c_int32, vp, vp, vp]),
         "avl_profile_steps": (C.c_int, [vp, C.c_int32, dp, C.c_int32]),
+        "avl_adjoint": (C.c_int, [vp, C.c_int32, C.POINTER(avl_f0), C.c_int32, C.c_int32, dp, dp, dp]),
         "avl_synchronize": (C.c_int, [vp]),
     }
     for name, (res, args) in sig.items():
@@ -105,6 +106,7 @@ avl_get_stats = lib.avl_get_stats
 avl_field_solve = lib.avl_field_solve
 avl_field_solve_noalloc = lib.avl_field_solve_noalloc
 avl_profile_steps = lib.avl_profile_steps
+avl_adjoint = lib.avl_adjoint
 avl_synchronize = lib.avl_synchronize
 
 
@@ -216,6 +218,15 @@ class Simulation:
         ms = np.zeros(4)
         self._chk(avl_profile_steps(self.ctx, n, ms.ctypes.data_as(C.POINTER(C.c_double)), 4))
         return ms
+
+    def adjoint(self, s, theta, nsteps, ckpt_every):
+        """(J, dJ/d amp (nmode,), dJ/d beam x-drift (nbeam,)) of the field
+        energy after nsteps steps with the f0 of species s set to theta."""
+        ga = (C.c_double * max(1, theta.nmode))()
+        gu = (C.c_double * max(1, theta.nbeam))()
+        J = C.c_double()
+        self._chk(avl_adjoint(self.ctx, s, C.byref(theta), nsteps, ckpt_every, ga, gu, C.byref(J)))
+        return J.value, np.array(ga[:theta.nmode]), np.array(gu[:theta.nbeam])
 
     def synchronize(self):
         self._chk(avl_synchronize(self.ctx))

@@ -37,6 +37,13 @@ struct avl_ctx {
     size_t scratch_bytes = 0;
     cudaGraphExec_t gexec = nullptr;
     std::string err;
+    // creation parameters of each species' markers (for avl_adjoint)
+    bool lattice_made[MAXS] = {};
+    int lat[MAXS][4] = {};
+    unsigned long long seed_s[MAXS] = {};
+    double jitter_s[MAXS] = {};
+    avl_f0 f0_s[MAXS] = {};
+    AdjEngine* adj = nullptr;
 };
 
 static thread_local std::string g_create_err;
@@ -672,6 +679,7 @@ void avl_destroy(avl_ctx* c)
     if (!c) return;
     if (c->st) cudaStreamSynchronize(c->st);
     if (c->gexec) cudaGraphExecDestroy(c->gexec);
+    adjoint_free(c->adj);
     for (void* p : c->allocs) cudaFree(p);
     for (int s = 0; s < MAXS; ++s) free_layout(c, s);
     if (c->scratch) cudaFree(c->scratch);
@@ -710,6 +718,11 @@ avl_status avl_init_markers(avl_ctx* c, int32_t s, const int32_t lattice[4], con
     else
         AVL_CUDA(c, launch_init1(c->h, c->d_args, s, lattice, c->d_f0, seed, jitter, c->st));
     c->has_markers[s] = true;
+    c->lattice_made[s] = true;
+    for (int d = 0; d < 4; ++d) c->lat[s][d] = lattice[d];
+    c->seed_s[s] = seed;
+    c->jitter_s[s] = jitter;
+    c->f0_s[s] = *f0;
     if ((st = refresh(c))) return st;
     return read_errors(c);
 }
@@ -733,6 +746,7 @@ avl_status avl_set_markers(avl_ctx* c, int32_t s, int64_t n, const double* x, co
         dv_ = base + n;
         df_ = base + n * (1 + nvd);
     }
+    c->lattice_made[s] = false;
     if ((st = nvd == 3 ? plan_layout3(c, s, n) : plan_layout(c, s, n))) return st;
     if ((st = set_cur_zero(c, s))) return st;
     if ((st = upload_args(c))) return st;
@@ -950,6 +964,37 @@ avl_status avl_field_solve(int32_t nx, double L, double poisson_const, int32_t s
     cudaFree(tab);
     if (e || e2) return cuda_fail(nullptr, e ? e : e2, "avl_field_solve");
     return AVL_OK;
+}
+
+avl_status avl_adjoint(avl_ctx* c, int32_t s, const avl_f0* theta, int32_t nsteps, int32_t ckpt_every,
+                       double* dJ_damp, double* dJ_ddrift, double* J)
+{
+    avl_status st = check_species(c, s);
+    if (st) return st;
+    if (c->h.nvdim != 1) return fail(c, AVL_EINVAL, "avl_adjoint supports 1d1v contexts");
+    if (!theta || !dJ_damp || !dJ_ddrift || !J) return fail(c, AVL_EINVAL, "theta or an output is NULL");
+    if (nsteps < 0 || ckpt_every < 1) return fail(c, AVL_EINVAL, "nsteps must be >= 0 and ckpt_every >= 1");
+    if (theta->nbeam < 1 || theta->nbeam > 4 || theta->nmode < 0 || theta->nmode > 64)
+        return fail(c, AVL_EINVAL, "theta needs 1..4 beams and 0..64 modes");
+    for (int b = 0; b < theta->nbeam; ++b)
+        if (!(theta->beam_vth[b][0] > 0)) return fail(c, AVL_EINVAL, "beam thermal speeds must be positive");
+    AdjSpec spec{};
+    spec.theta_s = s;
+    spec.nsteps = nsteps;
+    spec.ckpt_every = ckpt_every;
+    for (int q = 0; q < c->ns; ++q) {
+        if (!c->has_markers[q] || !c->lattice_made[q])
+            return fail(c, AVL_ESTATE, "avl_adjoint needs the markers of every species from avl_init_markers");
+        spec.n[q] = c->h.sp[q].n;
+        spec.lat[q][0] = c->lat[q][0];
+        spec.lat[q][1] = c->lat[q][1];
+        spec.seed[q] = c->seed_s[q];
+        spec.jitter[q] = c->jitter_s[q];
+        spec.f0[q] = q == s ? *theta : c->f0_s[q];
+    }
+    cudaError_t e = adjoint_run(&c->adj, c->h, c->d_args, spec, c->st, dJ_damp, dJ_ddrift, J);
+    if (e) return cuda_fail(c, e, "avl_adjoint");
+    return read_errors(c);
 }
 
 avl_status avl_synchronize(avl_ctx* c)

@@ -189,6 +189,21 @@ cudaError_t launch_get3(const StepArgs& h, const StepArgs* d, int s, double* x, 
 cudaError_t launch_getf3(const StepArgs& h, int s, int asel, double* f, double* n, cudaStream_t st);
 size_t pd3_smem_bytes(int nx, int prec);
 
+// discrete adjoint of the 1d1v step (k_adjoint.cu): the species' lattice
+// parameters of their last creation, theta = the f0 of species theta_s
+struct AdjSpec {
+    int theta_s, nsteps, ckpt_every;
+    long long n[MAXS];
+    int lat[MAXS][2];
+    unsigned long long seed[MAXS];
+    double jitter[MAXS];
+    avl_f0 f0[MAXS];
+};
+struct AdjEngine;   // buffers, kept by the context between calls
+cudaError_t adjoint_run(AdjEngine** eng, const StepArgs& h, const StepArgs* d, const AdjSpec& spec,
+                        cudaStream_t st, double* dJ_amp, double* dJ_u, double* J);
+void adjoint_free(AdjEngine* e);
+
 size_t pd1_smem_bytes(const SpDev& sp, int prec);
 cudaError_t configure_vhs1(const StepArgs& h);
 cudaError_t configure_field(const StepArgs& h);

@@ -1,0 +1,664 @@
+// k_adjoint.cu -- discrete adjoint of the 1d1v time step on the GPU.
+//
+// Objective: J = 1/2 sum_i E_i(T)^2 dx after nsteps steps (the field energy
+// of Eq. 12 with the factor 1/2 and no 1/cP).  Parameters: the mode
+// amplitudes and beam x-drifts of the initial distribution f0 of one species
+// (Sec. 3.3 / Eq. 17 form); they enter only through the marker values
+// f_l = f0(x_l, v_l), so dJ/dtheta = sum_l mu_l df0_l/dtheta with
+// mu_l = dJ/df_l, the total derivative through every later reconstruction
+// (Eq. 4), moment (Eq. 14), Poisson solve (Eq. 6) and push (Sec. 2).
+//
+// The engine keeps its own markers in the fixed lattice order (marker m =
+// cell * ppc + sub, as created), so that the adjoint variables of a marker
+// stay aligned across steps.  Per step n the forward pass deposits with
+// global atomics, forms F = N / D and the charge, solves for E (the shared
+// FFT kernel) and pushes.  Checkpoints of (x, v) every K steps; the backward
+// pass recomputes each segment of K states from its checkpoint, storing
+// positions, velocities, the grids D, F and E of every state, then walks it
+// backwards:
+//   e^n   = sum_l lt_l (q/m) dt G(X^n_l),  lt = lambda_V + dt lambda_X
+//           (e^N = dx E^N at the final state)
+//   psi   = q dv P^T e^n = -q dv P e^n   (the multiplier of Eq. 6 is odd and
+//           purely imaginary)
+//   A = psi / D, B = psi F / D per cell (0 where D = 0)
+//   mu   += sum_cells A alpha;  g = sum_cells (A f - B) d alpha / d(X, V)
+//   lambda_X = lambda_X + lt (q/m) dt dE/dx(X^n) + g_X;  lambda_V = lt + g_V
+// The cloud-in-cell derivatives are the one-sided ones of the floor() rule.
+#include <math.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "avl_internal.cuh"
+#include "common.cuh"
+
+namespace avl {
+
+// device-side view of the engine's buffers
+struct AdjSp {
+    long long n;
+    int lat[2];
+    unsigned long long seed;
+    double jitter;
+    void* hx;          // [K + 1][n] positions per slot (FP32: int cell; FP64: double cells)
+    float* hoff;       // [K + 1][n] FP32 offsets
+    void* hv;          // [K + 1][n] velocities
+    void* cx;          // [C][n] checkpoints
+    float* coff;
+    void* cv;
+    void* f;           // [n] marker values
+    void* lx;          // [n] lambda_X
+    void* lv;          // [n] lambda_V
+    double* mu;        // [n] dJ / df_l
+    void* num;         // [nv][nx] deposit accumulators
+    void* den;
+    void* hF;          // [K + 1][nv][nx] F = N / D per slot
+    void* hD;          // [K + 1][nv][nx] D per slot
+};
+
+struct AdjDev {
+    int ns, theta_s, K;
+    int nact, act[MAXS];   // species stepped each time: mobile ones and theta_s
+    int nstat, stat[MAXS]; // the others (immobile): their charge is deposited once
+    AdjSp sp[MAXS];
+    double* rho;       // [nx]
+    double* rho_static;   // [nx] charge of the other (immobile) species, deposited once
+    double* e;         // [nx] adjoint deposit
+    double* tmp;       // [nx] P e
+    double* hE;        // [K + 1][nx]
+    double* grad;      // [nmode + nbeam] of the theta species
+    const avl_f0* f0;  // [ns] (theta for theta_s)
+};
+
+template <typename T>
+struct APos;
+template <>
+struct APos<float> {
+    __device__ static Pos<float> load(const AdjSp& a, int slot, long long k)
+    {
+        Pos<float> p;
+        p.c = reinterpret_cast<const int*>(a.hx)[(size_t)slot * a.n + k];
+        p.o = a.hoff[(size_t)slot * a.n + k];
+        return p;
+    }
+    __device__ static void store(const AdjSp& a, int slot, long long k, const Pos<float>& p)
+    {
+        reinterpret_cast<int*>(a.hx)[(size_t)slot * a.n + k] = p.c;
+        a.hoff[(size_t)slot * a.n + k] = p.o;
+    }
+};
+template <>
+struct APos<double> {
+    __device__ static Pos<double> load(const AdjSp& a, int slot, long long k)
+    {
+        Pos<double> p;
+        p.xi = reinterpret_cast<const double*>(a.hx)[(size_t)slot * a.n + k];
+        return p;
+    }
+    __device__ static void store(const AdjSp& a, int slot, long long k, const Pos<double>& p)
+    {
+        reinterpret_cast<double*>(a.hx)[(size_t)slot * a.n + k] = p.xi;
+    }
+};
+
+// velocity dual row j0 and weight w of row j0 + 1 (t = (v - vmin)/dv - 1/2)
+template <typename T>
+__device__ __forceinline__ int vrow(T v, const SpDev& sp, T& w)
+{
+    const double t = ((double)v - sp.vmin[0]) * sp.inv_dv[0] - 0.5;
+    if (!(t > -2.0 && t < (double)sp.nv[0] + 1.0)) {
+        w = (T)0;
+        return t > 0 ? sp.nv[0] + 1 : -2;
+    }
+    const double fl = floor(t);
+    w = (T)(t - fl);
+    return (int)fl;
+}
+
+// lattice marker m (order m = (i nv + j) ppc + a pv + b) of species s
+template <typename T>
+__global__ void k_ad_init(const StepArgs* __restrict__ A, const AdjDev* __restrict__ D, int s)
+{
+    const SpDev& sp = A->sp[s];
+    const AdjSp& a = D->sp[s];
+    const avl_f0* f0 = D->f0 + s;
+    const int px = a.lat[0], pv = a.lat[1], ppc = px * pv;
+    for (long long m = (long long)blockIdx.x * blockDim.x + threadIdx.x; m < a.n; m += (long long)gridDim.x * blockDim.x) {
+        const long long cell = m / ppc;
+        const int sub = (int)(m - cell * ppc);
+        const int i = (int)(cell / sp.nv[0]), j = (int)(cell - (long long)i * sp.nv[0]);
+        const int ia = sub / pv, ib = sub - ia * pv;
+        const double J0 = (jitter_u01(a.seed, s, m, 0) - 0.5) * a.jitter;
+        const double J1 = (jitter_u01(a.seed, s, m, 1) - 0.5) * a.jitter;
+        const double xi = (double)i + ((double)ia + 0.5 + J0) / px;
+        const double v[3] = {sp.vmin[0] + ((double)j + ((double)ib + 0.5 + J1) / pv) * sp.dv[0], 0.0, 0.0};
+        APos<T>::store(a, 0, m, pos_from_cells<T>(xi, sp.nx));
+        reinterpret_cast<T*>(a.hv)[m] = (T)v[0];
+        reinterpret_cast<T*>(a.f)[m] = (T)f0_value(f0, 1, sp.nx * sp.dx, xi * sp.dx, v);
+        reinterpret_cast<T*>(a.lx)[m] = (T)0;
+        reinterpret_cast<T*>(a.lv)[m] = (T)0;
+        a.mu[m] = 0.0;
+    }
+}
+
+// deposit of the markers of slot `slot` (numerator and denominator of Eq. 4)
+template <typename T>
+__global__ void k_ad_dep(const StepArgs* __restrict__ A, const AdjDev* __restrict__ D, int slot, int all)   // all: the static list
+{
+    const int s = all ? D->stat[blockIdx.y] : D->act[blockIdx.y];
+    const SpDev& sp = A->sp[s];
+    const AdjSp& a = D->sp[s];
+    const int nx = sp.nx, nv = sp.nv[0];
+    T* num = reinterpret_cast<T*>(a.num);
+    T* den = reinterpret_cast<T*>(a.den);
+    const T* f = reinterpret_cast<const T*>(a.f);
+    const T* vv = reinterpret_cast<const T*>(a.hv) + (size_t)slot * a.n;
+    for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < a.n; k += (long long)gridDim.x * blockDim.x) {
+        const Pos<T> p = APos<T>::load(a, slot, k);
+        int i0;
+        T wx;
+        p.cic(i0, wx);
+        int ia, ib;
+        wrap_pair(i0, nx, ia, ib);
+        T wv;
+        const int j0 = vrow(vv[k], sp, wv);
+        const T fl = f[k];
+#pragma unroll
+        for (int cv = 0; cv < 2; ++cv) {
+            const int j = j0 + cv;
+            if (j < 0 || j >= nv) continue;
+            const T av = cv ? wv : (T)1 - wv;
+            const T a0 = ((T)1 - wx) * av, a1 = wx * av;
+            atomicAdd(num + (size_t)j * nx + ia, a0 * fl);
+            atomicAdd(den + (size_t)j * nx + ia, a0);
+            atomicAdd(num + (size_t)j * nx + ib, a1 * fl);
+            atomicAdd(den + (size_t)j * nx + ib, a1);
+        }
+    }
+}
+
+// F = N / D and D into slot `slot`, accumulators cleared; charge per column
+// (Eq. 14) added into rho
+template <typename T>
+__global__ void __launch_bounds__(256) k_ad_fin(const StepArgs* __restrict__ A, const AdjDev* __restrict__ D, int slot,
+                                                int all)
+{
+    __shared__ double col[8][32];
+    const int s = all ? D->stat[blockIdx.y] : D->act[blockIdx.y];
+    const SpDev& sp = A->sp[s];
+    const AdjSp& a = D->sp[s];
+    const int nx = sp.nx, nv = sp.nv[0];
+    const int x = blockIdx.x * 32 + (threadIdx.x & 31), lr = threadIdx.x >> 5;
+    const size_t cells = (size_t)nx * nv;
+    T* num = reinterpret_cast<T*>(a.num);
+    T* den = reinterpret_cast<T*>(a.den);
+    T* F = reinterpret_cast<T*>(a.hF) + (size_t)slot * cells;
+    T* Dg = reinterpret_cast<T*>(a.hD) + (size_t)slot * cells;
+    double r = 0.0;
+    if (x < nx) {
+        for (int j = lr; j < nv; j += 8) {
+            const size_t o = (size_t)j * nx + x;
+            const T n0 = num[o], d0 = den[o];
+            const T fv = d0 > (T)0 ? n0 / d0 : (T)0;
+            F[o] = fv;
+            Dg[o] = d0;
+            num[o] = (T)0;
+            den[o] = (T)0;
+            r += (double)fv;
+        }
+    }
+    col[lr][threadIdx.x & 31] = r;
+    __syncthreads();
+    if (lr == 0 && x < nx) {
+        double t = 0.0;
+        for (int k = 0; k < 8; ++k) t += col[k][threadIdx.x];
+        atomicAdd(D->rho + x, sp.q * sp.dv[0] * t);
+    }
+}
+
+// push (Sec. 2) from slot to slot + 1 with the field of slot; immobile
+// species are copied
+template <typename T>
+__global__ void k_ad_push(const StepArgs* __restrict__ A, const AdjDev* __restrict__ D, int slot)
+{
+    const int s = D->act[blockIdx.y];
+    const SpDev& sp = A->sp[s];
+    const AdjSp& a = D->sp[s];
+    const int nx = sp.nx;
+    const double* E = D->hE + (size_t)slot * nx;
+    const T* v0 = reinterpret_cast<const T*>(a.hv) + (size_t)slot * a.n;
+    T* v1 = reinterpret_cast<T*>(a.hv) + (size_t)(slot + 1) * a.n;
+    const T qm_dt = (T)sp.qm_dt, dt_dx = (T)sp.dt_dx;
+    for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < a.n; k += (long long)gridDim.x * blockDim.x) {
+        Pos<T> p = APos<T>::load(a, slot, k);
+        T v = v0[k];
+        if (sp.mobile) {
+            int i0;
+            T w;
+            p.cic(i0, w);
+            int ia, ib;
+            wrap_pair(i0, nx, ia, ib);
+            const T El = ((T)1 - w) * (T)E[ia] + w * (T)E[ib];
+            v = v + qm_dt * El;
+            p.drift(v * dt_dx, nx);
+        }
+        APos<T>::store(a, slot + 1, k, p);
+        v1[k] = v;
+    }
+}
+
+// adjoint deposit onto the x grid: e_i += lt (q/m) dt G_i(X) over the mobile
+// markers of slot (lt = lambda_V + dt lambda_X); at the final state e = dx E
+template <typename T>
+__global__ void __launch_bounds__(256) k_ad_e(const StepArgs* __restrict__ A, const AdjDev* __restrict__ D, int slot,
+                                              int terminal)
+{
+    extern __shared__ double es[];
+    const int s = D->act[blockIdx.y];
+    const SpDev& sp = A->sp[s];
+    const AdjSp& a = D->sp[s];
+    const int nx = sp.nx;
+    if (terminal) {
+        if (blockIdx.y == 0 && blockIdx.x == 0)
+            for (int i = threadIdx.x; i < nx; i += blockDim.x) D->e[i] = sp.dx * D->hE[(size_t)slot * nx + i];
+        return;
+    }
+    if (!sp.mobile) return;
+    for (int i = threadIdx.x; i < nx; i += blockDim.x) es[i] = 0.0;
+    __syncthreads();
+    const T* lx = reinterpret_cast<const T*>(a.lx);
+    const T* lv = reinterpret_cast<const T*>(a.lv);
+    const double c0 = sp.qm_dt;
+    const double dt = sp.dt_dx * sp.dx;
+    for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < a.n; k += (long long)gridDim.x * blockDim.x) {
+        const Pos<T> p = APos<T>::load(a, slot, k);
+        int i0;
+        T w;
+        p.cic(i0, w);
+        int ia, ib;
+        wrap_pair(i0, nx, ia, ib);
+        const double c = ((double)lv[k] + dt * (double)lx[k]) * c0;
+        atomicAdd(es + ia, c * (1.0 - (double)w));
+        atomicAdd(es + ib, c * (double)w);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < nx; i += blockDim.x)
+        if (es[i] != 0.0) atomicAdd(D->e + i, es[i]);
+}
+
+// per marker: mu += sum A alpha, lambda update (see the file head); tmp = P e
+template <typename T>
+__global__ void k_ad_gather(const StepArgs* __restrict__ A, const AdjDev* __restrict__ D, int slot, int terminal)
+{
+    const int s = D->act[blockIdx.y];
+    const SpDev& sp = A->sp[s];
+    const AdjSp& a = D->sp[s];
+    const int nx = sp.nx, nv = sp.nv[0];
+    const size_t cells = (size_t)nx * nv;
+    const T* F = reinterpret_cast<const T*>(a.hF) + (size_t)slot * cells;
+    const T* Dg = reinterpret_cast<const T*>(a.hD) + (size_t)slot * cells;
+    const double* E = D->hE + (size_t)slot * nx;
+    const T* vv = reinterpret_cast<const T*>(a.hv) + (size_t)slot * a.n;
+    const T* f = reinterpret_cast<const T*>(a.f);
+    T* lx = reinterpret_cast<T*>(a.lx);
+    T* lv = reinterpret_cast<T*>(a.lv);
+    const double psi_c = -sp.q * sp.dv[0];   // psi = q dv P^T e = -q dv (P e)
+    const double idx_ = 1.0 / sp.dx, idv = sp.inv_dv[0];
+    const double dt = sp.dt_dx * sp.dx;
+    for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < a.n; k += (long long)gridDim.x * blockDim.x) {
+        const Pos<T> p = APos<T>::load(a, slot, k);
+        int i0;
+        T wxT;
+        p.cic(i0, wxT);
+        int ia, ib;
+        wrap_pair(i0, nx, ia, ib);
+        T wvT;
+        const int j0 = vrow(vv[k], sp, wvT);
+        const double wx = (double)wxT, wv = (double)wvT, fl = (double)f[k];
+        const double psa = psi_c * D->tmp[ia], psb = psi_c * D->tmp[ib];
+        double m = 0.0, gx = 0.0, gv = 0.0;
+#pragma unroll
+        for (int cv = 0; cv < 2; ++cv) {
+            const int j = j0 + cv;
+            if (j < 0 || j >= nv) continue;
+            const double av = cv ? wv : 1.0 - wv, dav = cv ? idv : -idv;
+#pragma unroll
+            for (int cx = 0; cx < 2; ++cx) {
+                const int i = cx ? ib : ia;
+                const double ax = cx ? wx : 1.0 - wx, dax = cx ? idx_ : -idx_;
+                const size_t o = (size_t)j * nx + i;
+                const double d = (double)Dg[o];
+                if (!(d > 0.0)) continue;
+                const double ps = cx ? psb : psa;
+                const double Ac = ps / d, Bc = ps * (double)F[o] / d;
+                m += Ac * ax * av;
+                const double cc = Ac * fl - Bc;
+                gx += cc * dax * av;
+                gv += cc * ax * dav;
+            }
+        }
+        a.mu[k] += m;
+        if (terminal) {
+            lx[k] = (T)gx;
+            lv[k] = (T)gv;
+        } else if (sp.mobile) {
+            const double lt = (double)lv[k] + dt * (double)lx[k];
+            const double dEdx = (E[ib] - E[ia]) * idx_;
+            lx[k] = (T)((double)lx[k] + lt * sp.qm_dt * dEdx + gx);
+            lv[k] = (T)(lt + gv);
+        }
+    }
+}
+
+// dJ/dtheta = sum_l mu_l df0_l/dtheta for the theta species: df0/d amp_m =
+// B(v) cos(k_m x + phase_m), df0/d u_b = P(x) n_b M_b(v) (v - u_b) / vth_b^2
+template <typename T>
+__global__ void __launch_bounds__(256) k_ad_theta(const StepArgs* __restrict__ A, const AdjDev* __restrict__ D)
+{
+    const int s = D->theta_s;
+    const SpDev& sp = A->sp[s];
+    const AdjSp& a = D->sp[s];
+    const avl_f0* f0 = D->f0 + s;
+    const int nm = f0->nmode, nb = f0->nbeam, nt = nm + nb;
+    __shared__ double red[64 + 4][8];
+    double acc[64 + 4];
+    for (int t = 0; t < nt; ++t) acc[t] = 0.0;
+    const int px = a.lat[0], pv = a.lat[1], ppc = px * pv;
+    const double L = sp.nx * sp.dx;
+    for (long long m = (long long)blockIdx.x * blockDim.x + threadIdx.x; m < a.n; m += (long long)gridDim.x * blockDim.x) {
+        const long long cell = m / ppc;
+        const int sub = (int)(m - cell * ppc);
+        const int i = (int)(cell / sp.nv[0]), j = (int)(cell - (long long)i * sp.nv[0]);
+        const int ia = sub / pv, ib = sub - ia * pv;
+        const double J0 = (jitter_u01(a.seed, s, m, 0) - 0.5) * a.jitter;
+        const double J1 = (jitter_u01(a.seed, s, m, 1) - 0.5) * a.jitter;
+        const double x = ((double)i + ((double)ia + 0.5 + J0) / px) * sp.dx;
+        const double v = sp.vmin[0] + ((double)j + ((double)ib + 0.5 + J1) / pv) * sp.dv[0];
+        const double mu = a.mu[m];
+        double pert = 1.0;
+        for (int q = 0; q < nm; ++q) pert += f0->amp[q] * cos(2.0 * M_PI * f0->mode[q] * x / L + f0->phase[q]);
+        double B = 0.0;
+        for (int b = 0; b < nb; ++b) {
+            const double sd = f0->beam_vth[b][0];
+            const double t = (v - f0->beam_u[b][0]) / sd;
+            const double Mb = f0->beam_n[b] * exp(-0.5 * t * t) / (sqrt(2.0 * M_PI) * sd);
+            B += Mb;
+            acc[nm + b] += mu * pert * Mb * t / sd;
+        }
+        for (int q = 0; q < nm; ++q) acc[q] += mu * B * cos(2.0 * M_PI * f0->mode[q] * x / L + f0->phase[q]);
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int t = 0; t < nt; ++t) {
+        double v = acc[t];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if (lane == 0) red[t][warp] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < nt) {
+        double v = 0.0;
+        for (int w = 0; w < 8; ++w) v += red[threadIdx.x][w];
+        atomicAdd(D->grad + threadIdx.x, v);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// host: buffers and the passes
+// ---------------------------------------------------------------------------
+struct AdjEngine {
+    int prec = -1, ns = 0, K = 0, C = 0, nx = 0;
+    long long n[MAXS] = {};
+    std::vector<void*> mem;
+    AdjDev h{};
+    AdjDev* d = nullptr;
+    avl_f0* d_f0 = nullptr;
+};
+
+static cudaError_t grab(AdjEngine* E, void** p, size_t bytes)
+{
+    cudaError_t e = cudaMalloc(p, std::max<size_t>(bytes, 16));
+    if (e == cudaSuccess) E->mem.push_back(*p);
+    return e;
+}
+
+void adjoint_free(AdjEngine* E)
+{
+    if (!E) return;
+    for (void* p : E->mem) cudaFree(p);
+    delete E;
+}
+
+static int grid_for(long long n) { return (int)std::max<long long>(1, std::min<long long>((n + 255) / 256, 152ll * 8)); }
+
+static long long nmax_active(const AdjEngine* E)
+{
+    long long nmax = 0;
+    for (int k = 0; k < E->h.nact; ++k) nmax = std::max(nmax, E->n[E->h.act[k]]);
+    return nmax;
+}
+
+// reconstruction of the stepped species at slot, rho = static + theirs, E
+template <typename T>
+static cudaError_t recon_and_field(const StepArgs& h, const StepArgs* dA, AdjEngine* E, int slot, cudaStream_t st)
+{
+    cudaError_t e = cudaMemcpyAsync(E->h.rho, E->h.rho_static, (size_t)E->nx * 8, cudaMemcpyDeviceToDevice, st);
+    if (e) return e;
+    k_ad_dep<T><<<dim3(grid_for(nmax_active(E)), E->h.nact), 256, 0, st>>>(dA, E->d, slot, 0);
+    k_ad_fin<T><<<dim3((E->nx + 31) / 32, E->h.nact), 256, 0, st>>>(dA, E->d, slot, 0);
+    if ((e = cudaGetLastError())) return e;
+    return launch_poisson(E->h.rho, E->h.hE + (size_t)slot * E->nx, E->nx, h.fd.tw, h.fd.gmul, st);
+}
+
+// charge of the species that are not stepped (immobile, not theta): once
+template <typename T>
+static cudaError_t static_charge(AdjEngine* E, const StepArgs* dA, cudaStream_t st)
+{
+    cudaError_t e = cudaMemsetAsync(E->h.rho_static, 0, (size_t)E->nx * 8, st);
+    if (e || E->h.nstat == 0) return e;
+    long long nmax = 0;
+    for (int k = 0; k < E->h.nstat; ++k) nmax = std::max(nmax, E->n[E->h.stat[k]]);
+    std::swap(E->h.rho, E->h.rho_static);   // k_ad_fin adds into D->rho
+    if ((e = cudaMemcpyAsync(E->d, &E->h, sizeof(AdjDev), cudaMemcpyHostToDevice, st))) return e;
+    k_ad_dep<T><<<dim3(grid_for(nmax), E->h.nstat), 256, 0, st>>>(dA, E->d, 0, 1);
+    k_ad_fin<T><<<dim3((E->nx + 31) / 32, E->h.nstat), 256, 0, st>>>(dA, E->d, 0, 1);
+    if ((e = cudaGetLastError())) return e;
+    std::swap(E->h.rho, E->h.rho_static);
+    return cudaMemcpyAsync(E->d, &E->h, sizeof(AdjDev), cudaMemcpyHostToDevice, st);
+}
+
+template <typename T>
+static cudaError_t push_slot(AdjEngine* E, const StepArgs* dA, int slot, cudaStream_t st)
+{
+    k_ad_push<T><<<dim3(grid_for(nmax_active(E)), E->h.nact), 256, 0, st>>>(dA, E->d, slot);
+    return cudaGetLastError();
+}
+
+template <typename T>
+static cudaError_t back_step(const StepArgs& h, const StepArgs* dA, AdjEngine* E, int slot, int terminal, cudaStream_t st)
+{
+    const long long nmax = nmax_active(E);
+    cudaError_t e = cudaMemsetAsync(E->h.e, 0, (size_t)E->nx * 8, st);
+    if (e) return e;
+    k_ad_e<T><<<dim3(grid_for(nmax), E->h.nact), 256, (size_t)E->nx * 8, st>>>(dA, E->d, slot, terminal);
+    if ((e = cudaGetLastError())) return e;
+    if ((e = launch_poisson(E->h.e, E->h.tmp, E->nx, h.fd.tw, h.fd.gmul, st))) return e;
+    k_ad_gather<T><<<dim3(grid_for(nmax), E->h.nact), 256, 0, st>>>(dA, E->d, slot, terminal);
+    return cudaGetLastError();
+}
+
+// copy the state of slot a (positions, velocities) of every species into the
+// checkpoint c (to_ckpt) or back from it into slot a
+static cudaError_t ckpt_copy(AdjEngine* E, int c, int a, bool to_ckpt, cudaStream_t st)
+{
+    const size_t pb = E->prec == AVL_FP32 ? 4 : 8;
+    for (int s = 0; s < E->ns; ++s) {
+        const AdjSp& q = E->h.sp[s];
+        const size_t n = (size_t)q.n;
+        auto cp = [&](void* ck, void* hs, size_t eb) {
+            char* cptr = static_cast<char*>(ck) + (size_t)c * n * eb;
+            char* hptr = static_cast<char*>(hs) + (size_t)a * n * eb;
+            return to_ckpt ? cudaMemcpyAsync(cptr, hptr, n * eb, cudaMemcpyDeviceToDevice, st)
+                           : cudaMemcpyAsync(hptr, cptr, n * eb, cudaMemcpyDeviceToDevice, st);
+        };
+        cudaError_t e = cp(q.cx, q.hx, pb);
+        if (!e && E->prec == AVL_FP32) e = cp(q.coff, q.hoff, 4);
+        if (!e) e = cp(q.cv, q.hv, pb);
+        if (e) return e;
+    }
+    return cudaSuccess;
+}
+
+template <typename T>
+static cudaError_t run(const StepArgs& h, const StepArgs* dA, AdjEngine* E, int nsteps, cudaStream_t st,
+                       double* grad_host, int ngrad, double* J)
+{
+    cudaError_t e;
+    const int K = E->K;
+    // initial state into slot 0
+    for (int s = 0; s < E->ns; ++s) {
+        k_ad_init<T><<<grid_for(E->n[s]), 256, 0, st>>>(dA, E->d, s);
+        if ((e = cudaGetLastError())) return e;
+    }
+    if ((e = static_charge<T>(E, dA, st))) return e;
+    if ((e = cudaMemsetAsync(E->h.grad, 0, 8 * (64 + 4), st))) return e;
+    // forward: segments of K steps; checkpoint c = state c K
+    const int nseg = std::max(1, (nsteps + K - 1) / K);
+    int last_len = nsteps;
+    for (int c = 0; c < nseg; ++c) {
+        const int len = std::min(K, nsteps - c * K);
+        if ((e = ckpt_copy(E, c, 0, true, st))) return e;
+        for (int j = 0; j < len; ++j) {
+            if ((e = recon_and_field<T>(h, dA, E, j, st))) return e;
+            if ((e = push_slot<T>(E, dA, j, st))) return e;
+        }
+        last_len = len;
+        if (c + 1 < nseg && (e = ckpt_copy(E, c + 1, len, true, st))) return e;
+        if (c + 1 < nseg && (e = ckpt_copy(E, c + 1, 0, false, st))) return e;
+    }
+    if (nsteps == 0) last_len = 0;
+    // final state: its field and J, then the backward walk of the last segment
+    if ((e = recon_and_field<T>(h, dA, E, last_len, st))) return e;
+    std::vector<double> Ef(E->nx);
+    if ((e = cudaMemcpyAsync(Ef.data(), E->h.hE + (size_t)last_len * E->nx, E->nx * 8, cudaMemcpyDeviceToHost, st)))
+        return e;
+    if ((e = back_step<T>(h, dA, E, last_len, 1, st))) return e;
+    for (int j = last_len - 1; j >= 0; --j)
+        if ((e = back_step<T>(h, dA, E, j, 0, st))) return e;
+    // earlier segments: recompute from the checkpoint, then walk back
+    for (int c = nseg - 2; c >= 0; --c) {
+        if ((e = ckpt_copy(E, c, 0, false, st))) return e;
+        for (int j = 0; j < K; ++j) {
+            if ((e = recon_and_field<T>(h, dA, E, j, st))) return e;
+            if (j + 1 < K && (e = push_slot<T>(E, dA, j, st))) return e;
+        }
+        for (int j = K - 1; j >= 0; --j)
+            if ((e = back_step<T>(h, dA, E, j, 0, st))) return e;
+    }
+    k_ad_theta<T><<<grid_for(E->n[E->h.theta_s]), 256, 0, st>>>(dA, E->d);
+    if ((e = cudaGetLastError())) return e;
+    if ((e = cudaMemcpyAsync(grad_host, E->h.grad, ngrad * 8, cudaMemcpyDeviceToHost, st))) return e;
+    if ((e = cudaStreamSynchronize(st))) return e;
+    double s2 = 0.0;
+    for (int i = 0; i < E->nx; ++i) s2 += Ef[i] * Ef[i];
+    *J = 0.5 * s2 * h.fd.dx;
+    return cudaSuccess;
+}
+
+cudaError_t adjoint_run(AdjEngine** eng, const StepArgs& h, const StepArgs* dA, const AdjSpec& spec, cudaStream_t st,
+                        double* dJ_amp, double* dJ_u, double* J)
+{
+    const int ns = h.ns, nx = h.fd.nx;
+    const int K = std::max(1, std::min(spec.ckpt_every, std::max(1, spec.nsteps)));
+    const int C = std::max(1, (spec.nsteps + K - 1) / K);
+    const size_t pb = h.prec == AVL_FP32 ? 4 : 8;
+    AdjEngine* E = *eng;
+    bool fits = E && E->prec == h.prec && E->ns == ns && E->K >= K && E->C >= C && E->nx == nx;
+    for (int s = 0; fits && s < ns; ++s) fits = E->n[s] == spec.n[s];
+    if (!fits) {
+        adjoint_free(E);
+        *eng = nullptr;
+        E = new AdjEngine();
+        E->prec = h.prec;
+        E->ns = ns;
+        E->K = K;
+        E->C = C;
+        E->nx = nx;
+        cudaError_t e = cudaSuccess;
+        auto g = [&](void** p, size_t b) {
+            if (!e) e = grab(E, p, b);
+        };
+        for (int s = 0; s < ns; ++s) {
+            AdjSp& q = E->h.sp[s];
+            const size_t n = (size_t)spec.n[s];
+            const size_t cells = (size_t)nx * h.sp[s].nv[0];
+            E->n[s] = spec.n[s];
+            q.n = spec.n[s];
+            g(&q.hx, (K + 1) * n * pb);
+            q.hoff = nullptr;
+            if (h.prec == AVL_FP32) g((void**)&q.hoff, (K + 1) * n * 4);
+            g(&q.hv, (K + 1) * n * pb);
+            g(&q.cx, C * n * pb);
+            q.coff = nullptr;
+            if (h.prec == AVL_FP32) g((void**)&q.coff, C * n * 4);
+            g(&q.cv, C * n * pb);
+            g(&q.f, n * pb);
+            g(&q.lx, n * pb);
+            g(&q.lv, n * pb);
+            g((void**)&q.mu, n * 8);
+            g(&q.num, cells * pb);
+            g(&q.den, cells * pb);
+            g(&q.hF, (K + 1) * cells * pb);
+            g(&q.hD, (K + 1) * cells * pb);
+            if (!e) e = cudaMemsetAsync(q.num, 0, cells * pb, st);
+            if (!e) e = cudaMemsetAsync(q.den, 0, cells * pb, st);
+        }
+        g((void**)&E->h.rho, nx * 8);
+        g((void**)&E->h.rho_static, nx * 8);
+        g((void**)&E->h.e, nx * 8);
+        g((void**)&E->h.tmp, nx * 8);
+        g((void**)&E->h.hE, (size_t)(K + 1) * nx * 8);
+        g((void**)&E->h.grad, 8 * (64 + 4));
+        g((void**)&E->d_f0, sizeof(avl_f0) * ns);
+        g((void**)&E->d, sizeof(AdjDev));
+        if (e) {
+            adjoint_free(E);
+            return e;
+        }
+        *eng = E;
+    }
+    E->h.ns = ns;
+    E->h.theta_s = spec.theta_s;
+    E->h.nact = 0;
+    E->h.nstat = 0;
+    for (int s = 0; s < ns; ++s) {
+        if (h.sp[s].mobile || s == spec.theta_s)
+            E->h.act[E->h.nact++] = s;
+        else
+            E->h.stat[E->h.nstat++] = s;
+    }
+    E->h.K = K;
+    E->h.f0 = E->d_f0;
+    for (int s = 0; s < ns; ++s) {
+        AdjSp& q = E->h.sp[s];
+        q.lat[0] = spec.lat[s][0];
+        q.lat[1] = spec.lat[s][1];
+        q.seed = spec.seed[s];
+        q.jitter = spec.jitter[s];
+    }
+    const int saveK = E->K;
+    E->K = K;
+    cudaError_t e = cudaMemcpyAsync(E->d_f0, spec.f0, sizeof(avl_f0) * ns, cudaMemcpyHostToDevice, st);
+    if (!e) e = cudaMemcpyAsync(E->d, &E->h, sizeof(AdjDev), cudaMemcpyHostToDevice, st);
+    if (!e) e = cudaStreamSynchronize(st);
+    double grad[64 + 4] = {};
+    const int nm = spec.f0[spec.theta_s].nmode, nb = spec.f0[spec.theta_s].nbeam;
+    if (!e)
+        e = h.prec == AVL_FP32 ? run<float>(h, dA, E, spec.nsteps, st, grad, nm + nb, J)
+                               : run<double>(h, dA, E, spec.nsteps, st, grad, nm + nb, J);
+    E->K = saveK;
+    if (e) return e;
+    for (int i = 0; i < nm; ++i) dJ_amp[i] = grad[i];
+    for (int b = 0; b < nb; ++b) dJ_u[b] = grad[nm + b];
+    return cudaSuccess;
+}
+
+}  // namespace avl

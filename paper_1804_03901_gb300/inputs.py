@@ -17,6 +17,12 @@ two_stream  Two-stream instability 1d1v, FP32: electrons 0.5 M(v-3) + 0.5
             +-10 v_th,i, unperturbed); nx = 512, L = 0.4 nx = 204.8,
             nv = 1024 on [-10, 10] v_th; 4 x 4 markers per cell (8388608 per
             species); dt = 0.05; 2000 steps.
+two_stream_adjoint  Gradient of the field energy at T = 25 of a two-stream
+            run, 1d1v: electrons 0.5 M(v-u) + 0.5 M(v+u), u = 3, with 16 mode
+            amplitudes around 1e-4 (1e-4 (1 + 0.1 N(0,1)), seeded) and
+            seeded phases; immobile ions; nx = 256, L = 102.4, nv = 512 on
+            [-10, 10]; 2 x 4 markers per cell (1048576 electrons); dt = 0.05;
+            500 steps; checkpoints every 50 steps.
 bump_on_tail  Bump-on-tail 1d3v, FP32: electrons 0.95 M3(v; 1) + 0.05
             M3(v - 4 e_x; 0.5) (isotropic Maxwellians), density perturbation
             1e-3 cos(0.3 x); immobile ions (the removed k = 0 mode);
@@ -63,6 +69,25 @@ def two_stream(nx=512, nv=1024, lattice=(4, 4, 1, 1), steps=2000, nmodes=16, amp
                dict(beams=[_maxwell(1.0, 0.0, vthi)], modes=[])],
         "lattice": [tuple(lattice), tuple(lattice)],
         "seed": BASE_SEED + 1, "jitter": 1.0, "steps": steps,
+    }
+
+
+def two_stream_adjoint(nx=256, nv=512, lattice=(2, 4, 1, 1), steps=500, ckpt=50, nmodes=16):
+    rng = np.random.default_rng(BASE_SEED + 3)
+    amps = 1e-4 * (1.0 + 0.1 * rng.standard_normal(nmodes))
+    phases = rng.uniform(0.0, 2 * math.pi, nmodes)
+    vthi = 1836.0 ** -0.5
+    return {
+        "name": f"two_stream_adjoint_1d1v_nx{nx}_nv{nv}",
+        "nvdim": 1, "nx": nx, "L": 0.4 * nx, "dt": 0.05, "precision": "fp32",
+        "species": [dict(q=-1.0, m=1.0, nv=(nv,), vmin=(-10.0,), vmax=(10.0,), mobile=True),
+                    dict(q=1.0, m=1836.0, nv=(nv,), vmin=(-10.0 * vthi,), vmax=(10.0 * vthi,),
+                         mobile=False)],
+        "f0": [dict(beams=[_maxwell(0.5, 3.0, 1.0), _maxwell(0.5, -3.0, 1.0)],
+                    modes=[(m + 1, float(amps[m]), float(phases[m])) for m in range(nmodes)]),
+               dict(beams=[_maxwell(1.0, 0.0, vthi)], modes=[])],
+        "lattice": [tuple(lattice), tuple(lattice)],
+        "seed": BASE_SEED + 3, "jitter": 1.0, "steps": steps, "ckpt": ckpt,
     }
 
 
