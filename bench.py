@@ -54,8 +54,9 @@ def parse():
     p.add_argument("--steps", type=int, default=2000)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    p.add_argument("--workload", choices=["two_stream", "landau", "bump_on_tail", "two_stream_adjoint"],
+    p.add_argument("--workload", choices=["two_stream", "landau", "bump_on_tail", "two_stream_adjoint", "ensemble"],
                    default="two_stream")
+    p.add_argument("--nrun", type=int, default=256, help="runs of the ensemble workload")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--nv", type=int, default=0, help="velocity cells (profiling of a smaller case)")
@@ -70,6 +71,8 @@ def workload(name, nv=0):
         return inputs.bump_on_tail(nv=nv) if nv else inputs.bump_on_tail()
     if name == "two_stream_adjoint":
         return inputs.two_stream_adjoint(nv=nv) if nv else inputs.two_stream_adjoint()
+    if name == "ensemble":
+        return inputs.ensemble()
     return inputs.landau(nv=nv) if nv else inputs.landau()
 
 
@@ -466,12 +469,80 @@ def run_adjoint(args):
     print(json.dumps(line), flush=True)
 
 
+def run_ensemble(args):
+    """Marker-steps/s of the batched ensemble: every run advanced by one
+    launch per kernel class per step (one CUDA graph per step), chunk size
+    chosen by the autotuner."""
+    import torch
+    from paper_1804_03901_gb300 import avl as A
+    from paper_1804_03901_gb300 import inputs
+    w = inputs.ensemble(nrun=args.nrun)
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    prec = A.AVL_FP32
+    doms = [A.make_domain(1, r["nx"], r["L"], r["dt"], 1.0, True, prec) for r in w["runs"]]
+    sps = [[A.make_species(**sp) for sp in r["species"]] for r in w["runs"]]
+    t0 = time.perf_counter()
+    b = A.Batch(doms, sps, stream=stream.cuda_stream)
+
+    def init():
+        for i, r in enumerate(w["runs"]):
+            f0 = r["f0"][0]
+            b.runs[i].init_markers(0, r["lattice"][0], A.make_f0(f0["beams"], f0["modes"]), r["seed"], w["jitter"])
+
+    init()
+    nmark = sum(b.runs[i].marker_count(0) for i in range(len(w["runs"])))
+    t_init = time.perf_counter() - t0
+    best_m = b.autotune(5)
+    init()                      # restart from t = 0 with the chosen chunk size
+    b.step(max(3, args.warmup))
+    b.synchronize()
+    init()
+    b.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks = Clocks("GPU-" + str(torch.cuda.get_device_properties(0).uuid))
+    torch.cuda.synchronize()
+    clocks.start()
+    e0.record(stream)
+    b.step(args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    b.synchronize()
+    init()
+    b.synchronize()
+    kms = b.profile_steps(args.steps)
+    hbm, peak_kind = peaks()
+    pd_ms = kms[1] / args.steps
+    algo = BYTES_PER_MARKER_ALGO[(1, "fp32")]
+    achieved = nmark * algo / (pd_ms / 1e3) / 1e9
+    names = KERNEL_NAMES[1]
+    line = {"metric": "marker_steps_per_s", "value": nmark * args.steps / (ms / 1e3), "unit": "marker-steps/s",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": w["name"], "runs": len(w["runs"]), "markers": nmark,
+                       "landau_runs": sum(r["type"] == "landau" for r in w["runs"]),
+                       "autotuned_chunk_markers": best_m, "init_s": t_init, "timed_from": "t = 0",
+                       "launches_per_step": 4, "l2": "inputs larger than L2"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                         "traffic": None, "kernel": "k_pd1 over all runs (one batched launch)",
+                         "algorithmic_bytes_per_marker": algo,
+                         "peak_kind": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)",
+                         "kernel_ms_per_step": {k: float(v / args.steps) for k, v in zip(names, kms)}},
+            "clocks": clk, "gpu_launches": 4 * args.steps}
+    print(json.dumps(line), flush=True)
+    b.close()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
     elif args.workload == "two_stream_adjoint":
         run_adjoint(args)
+    elif args.workload == "ensemble":
+        run_ensemble(args)
     else:
         run_ours(args)
 

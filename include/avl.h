@@ -223,6 +223,34 @@ avl_status avl_field_solve_noalloc(int32_t nx, double L, double poisson_const, i
 avl_status avl_adjoint(avl_ctx* ctx, int32_t s, const avl_f0* theta, int32_t nsteps, int32_t ckpt_every,
                        double* dJ_damp, double* dJ_ddrift, double* J);
 
+/* Batched ensemble (spec extension; the paper runs one simulation at a
+ * time): nrun independent 1d1v runs of any sizes, run r with domain doms[r]
+ * and the nspecies[r] species that follow in sps (runs' species listed one
+ * run after another).  All runs share one precision and the batch's stream
+ * (cuda_stream, or one the batch creates).  avl_step on the batch advances
+ * every run by one launch per kernel class (push + deposit, finalize,
+ * field) for all runs together, recorded as one CUDA graph per step; all
+ * other calls go to the runs, obtained with avl_batch_run (owned by the
+ * batch: avl_destroy on a run does nothing, avl_destroy on the batch frees
+ * every run).  avl_synchronize on the batch reports the first run's error.
+ * Errors: AVL_EINVAL (nrun outside [1, 4096], nvdim 3, mixed precision, or
+ * a run's own avl_create error, message prefixed with the run), AVL_ENOMEM. */
+avl_status avl_create_batch(int32_t nrun, const avl_domain* doms, const avl_species* sps, const int32_t* nspecies,
+                            void* cuda_stream, avl_ctx** out);
+
+/* Run r of a batch (a context for every per-run call). */
+avl_status avl_batch_run(avl_ctx* batch, int32_t r, avl_ctx** run);
+
+/* Chunk-size autotuner of the 1d1v path (a single context or a batch):
+ * snapshots every marker set, times trial_steps steps (after two untimed
+ * ones) for markers-per-chunk M in {heuristic, 1024, 2048, 4096, 8192,
+ * 16384}, keeps the fastest and restores the snapshot, so the state is that
+ * of the call (re-sorted, f, rho and E reconstructed; afterwards the markers
+ * count as caller markers for avl_adjoint).  *chunk_out = the chosen M (0:
+ * the heuristic).  Blocks until done.  Errors: AVL_EINVAL (trial_steps < 1,
+ * 1d3v), AVL_ESTATE as avl_step, AVL_ENOMEM (snapshot: 24 B per marker). */
+avl_status avl_autotune(avl_ctx* ctx, int32_t trial_steps, int32_t* chunk_out);
+
 /* Per-kernel timing (the paper's time breakdown, Sec. 3.2): advance nsteps
  * steps exactly as avl_step does, but launched kernel by kernel with CUDA
  * events recorded on the context stream around each kernel; writes the summed

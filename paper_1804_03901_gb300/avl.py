@@ -26,7 +26,7 @@ STATUS_NAMES = {0: "AVL_OK", 1: "AVL_EINVAL", 2: "AVL_ENOMEM", 3: "AVL_ECUDA",
 EXPORTED = ["avl_create", "avl_destroy", "avl_last_error", "avl_init_markers", "avl_set_markers",
             "avl_marker_count", "avl_get_markers", "avl_step", "avl_get_f", "avl_get_rho",
             "avl_get_E", "avl_get_diag", "avl_get_stats", "avl_field_solve", "avl_field_solve_noalloc",
-            "avl_profile_steps", "avl_adjoint",
+            "avl_profile_steps", "avl_adjoint", "avl_create_batch", "avl_batch_run", "avl_autotune",
             "avl_synchronize"]
 
 
@@ -78,6 +78,10 @@ def _load():
         "avl_field_solve_noalloc": (C.c_int, [C.c_int32, C.c_double, C.c_double, C.c_int32, vp, vp, vp]),
         "avl_profile_steps": (C.c_int, [vp, C.c_int32, dp, C.c_int32]),
         "avl_adjoint": (C.c_int, [vp, C.c_int32, C.POINTER(avl_f0), C.c_int32, C.c_int32, dp, dp, dp]),
+        "avl_create_batch": (C.c_int, [C.c_int32, C.POINTER(avl_domain), C.POINTER(avl_species),
+                                       C.POINTER(C.c_int32), vp, C.POINTER(vp)]),
+        "avl_batch_run": (C.c_int, [vp, C.c_int32, C.POINTER(vp)]),
+        "avl_autotune": (C.c_int, [vp, C.c_int32, C.POINTER(C.c_int32)]),
         "avl_synchronize": (C.c_int, [vp]),
     }
     for name, (res, args) in sig.items():
@@ -107,6 +111,9 @@ avl_field_solve = lib.avl_field_solve
 avl_field_solve_noalloc = lib.avl_field_solve_noalloc
 avl_profile_steps = lib.avl_profile_steps
 avl_adjoint = lib.avl_adjoint
+avl_create_batch = lib.avl_create_batch
+avl_batch_run = lib.avl_batch_run
+avl_autotune = lib.avl_autotune
 avl_synchronize = lib.avl_synchronize
 
 
@@ -258,3 +265,58 @@ class Simulation:
         d = np.zeros(4 * len(self.species), dtype=np.int64)
         self._chk(avl_get_stats(self.ctx, d.ctypes.data_as(C.POINTER(C.c_int64))))
         return d.reshape(len(self.species), 4)
+
+
+class Batch:
+    """Independent 1d1v runs advanced together (avl_create_batch).
+    runs[r] is a Simulation view of run r (owned by the batch)."""
+
+    def __init__(self, domains, species_lists, stream=None):
+        n = len(domains)
+        doms = (avl_domain * n)(*domains)
+        flat = [sp for lst in species_lists for sp in lst]
+        sps = (avl_species * len(flat))(*flat)
+        ns = (C.c_int32 * n)(*[len(lst) for lst in species_lists])
+        ctx = C.c_void_p()
+        check(avl_create_batch(n, doms, sps, ns, stream, C.byref(ctx)))
+        self.ctx = ctx
+        self.runs = []
+        for r in range(n):
+            sub = C.c_void_p()
+            check(avl_batch_run(ctx, r, C.byref(sub)), ctx)
+            v = Simulation.__new__(Simulation)
+            v.nvdim, v.nx, v.species, v.ctx = 1, domains[r].nx, list(species_lists[r]), sub
+            v._view = True
+            self.runs.append(v)
+
+    def _chk(self, st):
+        return check(st, self.ctx)
+
+    def step(self, n=1):
+        self._chk(avl_step(self.ctx, n))
+
+    def profile_steps(self, n):
+        ms = (C.c_double * 4)()
+        self._chk(avl_profile_steps(self.ctx, n, ms, 4))
+        return np.array(ms[:])
+
+    def autotune(self, trial_steps=5):
+        m = C.c_int32()
+        self._chk(avl_autotune(self.ctx, trial_steps, C.byref(m)))
+        return m.value
+
+    def synchronize(self):
+        self._chk(avl_synchronize(self.ctx))
+
+    def close(self):
+        if self.ctx:
+            for v in self.runs:
+                v.ctx = None
+            avl_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

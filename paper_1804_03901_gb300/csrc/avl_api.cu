@@ -44,6 +44,14 @@ struct avl_ctx {
     double jitter_s[MAXS] = {};
     avl_f0 f0_s[MAXS] = {};
     AdjEngine* adj = nullptr;
+    int force_M = 0;                    // chunk size chosen by avl_autotune (0: heuristic)
+    unsigned layout_version = 0;        // bumped whenever the launch shapes change
+    // a batch: independent runs advanced by one launch per kernel class
+    std::vector<avl_ctx*> runs;
+    avl_ctx* parent = nullptr;          // set on the runs of a batch
+    void* bm_mem = nullptr;             // device BatchMap + run tables
+    std::vector<unsigned> bm_versions;  // layout versions the map was built for
+    int bm_pd_blocks = 0, bm_fin_blocks = 0, bm_pd_smem = 0, bm_field_smem = 0;
 };
 
 static thread_local std::string g_create_err;
@@ -135,6 +143,7 @@ avl_status plan_layout(avl_ctx* c, int s, long long n)
     long long chunks = std::min<long long>(std::max<long long>(1, (n + 8191) / 8192), target);
     long long M = (n + chunks - 1) / chunks;
     M = (M + 63) / 64 * 64;
+    if (c->force_M > 0) M = ((long long)c->force_M + 63) / 64 * 64;
     const int m_env = env_int("AVL_CHUNK_M", 0);
     if (m_env > 0) M = (m_env + 63) / 64 * 64;
     const int nch = (int)((n + M - 1) / M);
@@ -208,6 +217,7 @@ avl_status plan_layout(avl_ctx* c, int s, long long n)
         base += c->h.sp[q].nchunk;
     }
     c->h.nchunk_total = base;
+    c->layout_version++;
     AVL_CUDA(c, configure_vhs1(c->h));
     if (c->gexec) {
         cudaGraphExecDestroy(c->gexec);
@@ -269,6 +279,7 @@ avl_status plan_layout3(avl_ctx* c, int s, long long n)
         base += c->h.sp[q].npen;
     }
     c->h.npen_total = base;
+    c->layout_version++;
     if (c->gexec) {
         cudaGraphExecDestroy(c->gexec);
         c->gexec = nullptr;
@@ -335,8 +346,11 @@ avl_status refresh(avl_ctx* c)
 // one step: push + deposit + write back (in place or re-sorted) + key counts
 // of the new state -> f, rho, diagnostics -> E, and the re-sort decision and
 // slots for the next step
+avl_status enqueue_batch_step(avl_ctx* b);
+
 avl_status enqueue_step(avl_ctx* c)
 {
+    if (!c->runs.empty()) return enqueue_batch_step(c);
     if (c->h.nvdim == 3) {
         AVL_CUDA(c, launch_pd3(c->h, c->d_args, 1, c->st));
         AVL_CUDA(c, launch_fin3(c->h, c->d_args, 0, c->st));
@@ -465,6 +479,72 @@ avl_status create_species3(avl_ctx* c, int s, const avl_species& p, int& fin_bas
         AVL_CUDA(c, cudaMemcpyAsync(pv2, v2.data(), v2.size() * 8, cudaMemcpyHostToDevice, c->st));
         AVL_CUDA(c, cudaStreamSynchronize(c->st));
     }
+    return AVL_OK;
+}
+
+// the batch's device map (run arguments, block prefixes) and kernel limits,
+// rebuilt when a run's launch shapes changed; invalidates the step graph
+avl_status ensure_batch_map(avl_ctx* b)
+{
+    const int nrun = (int)b->runs.size();
+    bool ok = b->bm_mem != nullptr && (int)b->bm_versions.size() == nrun;
+    for (int r = 0; ok && r < nrun; ++r) ok = b->bm_versions[r] == b->runs[r]->layout_version;
+    if (ok) return AVL_OK;
+    if (b->gexec) {
+        cudaGraphExecDestroy(b->gexec);
+        b->gexec = nullptr;
+    }
+    AVL_CUDA(b, cudaStreamSynchronize(b->st));
+    if (b->bm_mem) {
+        cudaFree(b->bm_mem);
+        b->bm_mem = nullptr;
+    }
+    // layout: BatchMap | args[nrun] | pd_base[nrun + 1] | fin_base[nrun + 1]
+    const size_t off_args = (sizeof(BatchMap) + 15) / 16 * 16;
+    const size_t off_pd = off_args + (size_t)nrun * sizeof(void*);
+    const size_t off_fin = off_pd + (size_t)(nrun + 1) * 4;
+    const size_t bytes = off_fin + (size_t)(nrun + 1) * 4;
+    std::vector<unsigned char> hostbuf(bytes, 0);
+    AVL_CUDA(b, cudaMalloc(&b->bm_mem, bytes));
+    unsigned char* dbase = static_cast<unsigned char*>(b->bm_mem);
+    BatchMap bm;
+    bm.nrun = nrun;
+    bm.args = reinterpret_cast<const StepArgs* const*>(dbase + off_args);
+    bm.pd_base = reinterpret_cast<const int*>(dbase + off_pd);
+    bm.fin_base = reinterpret_cast<const int*>(dbase + off_fin);
+    memcpy(hostbuf.data(), &bm, sizeof(bm));
+    const StepArgs** args = reinterpret_cast<const StepArgs**>(hostbuf.data() + off_args);
+    int* pd = reinterpret_cast<int*>(hostbuf.data() + off_pd);
+    int* fin = reinterpret_cast<int*>(hostbuf.data() + off_fin);
+    pd[0] = fin[0] = 0;
+    int pd_smem = 1024, field_smem = 0;
+    b->bm_versions.assign(nrun, 0);
+    for (int r = 0; r < nrun; ++r) {
+        const avl_ctx* c = b->runs[r];
+        args[r] = c->d_args;
+        pd[r + 1] = pd[r] + c->h.nchunk_total;
+        fin[r + 1] = fin[r] + c->h.nfin_total;
+        pd_smem = std::max(pd_smem, pd1_smem_needed(c->h));
+        field_smem = std::max(field_smem, (int)field_smem_bytes(c->h.fd.nx));
+        b->bm_versions[r] = c->layout_version;
+    }
+    AVL_CUDA(b, cudaMemcpyAsync(b->bm_mem, hostbuf.data(), bytes, cudaMemcpyHostToDevice, b->st));
+    AVL_CUDA(b, cudaStreamSynchronize(b->st));
+    b->bm_pd_blocks = pd[nrun];
+    b->bm_fin_blocks = fin[nrun];
+    b->bm_pd_smem = pd_smem;
+    b->bm_field_smem = field_smem;
+    AVL_CUDA(b, configure_batch1(b->h.prec, pd_smem, field_smem));
+    return AVL_OK;
+}
+
+// one step of every run: push + deposit, finalize, field (one launch each)
+avl_status enqueue_batch_step(avl_ctx* b)
+{
+    const BatchMap* bm = static_cast<const BatchMap*>(b->bm_mem);
+    AVL_CUDA(b, launch_pd1_batch(b->h.prec, bm, b->bm_pd_blocks, b->bm_pd_smem, 1, b->st));
+    AVL_CUDA(b, launch_fin1_batch(b->h.prec, bm, b->bm_fin_blocks, 0, b->st));
+    AVL_CUDA(b, launch_field_batch(bm, (int)b->runs.size(), b->bm_field_smem, 1, b->st));
     return AVL_OK;
 }
 
@@ -676,7 +756,15 @@ avl_status avl_create(const avl_domain* dom, const avl_species* spec, int32_t ns
 
 void avl_destroy(avl_ctx* c)
 {
-    if (!c) return;
+    if (!c || c->parent) return;   // a run belongs to its batch
+    for (avl_ctx* r : c->runs) {
+        r->parent = nullptr;
+        avl_destroy(r);
+    }
+    if (c->bm_mem) {
+        if (c->st) cudaStreamSynchronize(c->st);
+        cudaFree(c->bm_mem);
+    }
     if (c->st) cudaStreamSynchronize(c->st);
     if (c->gexec) cudaGraphExecDestroy(c->gexec);
     adjoint_free(c->adj);
@@ -808,7 +896,16 @@ avl_status avl_step(avl_ctx* c, int32_t nsteps)
     for (int s = 0; s < c->ns; ++s)
         if (c->h.sp[s].mobile && !c->has_markers[s])
             return fail(c, AVL_ESTATE, "mobile species " + std::to_string(s) + " has no markers");
+    for (size_t r = 0; r < c->runs.size(); ++r)
+        for (int s = 0; s < c->runs[r]->ns; ++s)
+            if (c->runs[r]->h.sp[s].mobile && !c->runs[r]->has_markers[s])
+                return fail(c, AVL_ESTATE, "run " + std::to_string(r) + ": mobile species " + std::to_string(s) +
+                                               " has no markers");
     if (nsteps == 0) return AVL_OK;
+    if (!c->runs.empty()) {
+        avl_status st = ensure_batch_map(c);
+        if (st) return st;
+    }
     cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
     AVL_CUDA(c, cudaStreamIsCapturing(c->st, &cap));
     if (cap != cudaStreamCaptureStatusNone || env_int("AVL_NO_GRAPH", 0)) {
@@ -910,6 +1007,12 @@ avl_status avl_profile_steps(avl_ctx* c, int32_t nsteps, double* ms, int32_t nke
     for (int s = 0; s < c->ns; ++s)
         if (c->h.sp[s].mobile && !c->has_markers[s])
             return fail(c, AVL_ESTATE, "mobile species " + std::to_string(s) + " has no markers");
+    const bool batch = !c->runs.empty();
+    if (batch) {
+        avl_status st0 = ensure_batch_map(c);
+        if (st0) return st0;
+    }
+    const BatchMap* bm = static_cast<const BatchMap*>(c->bm_mem);
     cudaEvent_t ev[5];
     for (int i = 0; i < 5; ++i) AVL_CUDA(c, cudaEventCreate(&ev[i]));
     double acc[4] = {0, 0, 0, 0};
@@ -919,11 +1022,19 @@ avl_status avl_profile_steps(avl_ctx* c, int32_t nsteps, double* ms, int32_t nke
         cudaError_t e = cudaEventRecord(ev[0], c->st);
         if (!e && d3) e = launch_sort3(c->h, c->d_args, c->st);
         if (!e) e = cudaEventRecord(ev[1], c->st);
-        if (!e) e = d3 ? launch_pd3(c->h, c->d_args, 1, c->st) : launch_pd1(c->h, c->d_args, 1, c->st);
+        if (!e)
+            e = batch ? launch_pd1_batch(c->h.prec, bm, c->bm_pd_blocks, c->bm_pd_smem, 1, c->st)
+                : d3  ? launch_pd3(c->h, c->d_args, 1, c->st)
+                      : launch_pd1(c->h, c->d_args, 1, c->st);
         if (!e) e = cudaEventRecord(ev[2], c->st);
-        if (!e) e = d3 ? launch_fin3(c->h, c->d_args, 0, c->st) : launch_fin1(c->h, c->d_args, 0, c->st);
+        if (!e)
+            e = batch ? launch_fin1_batch(c->h.prec, bm, c->bm_fin_blocks, 0, c->st)
+                : d3  ? launch_fin3(c->h, c->d_args, 0, c->st)
+                      : launch_fin1(c->h, c->d_args, 0, c->st);
         if (!e) e = cudaEventRecord(ev[3], c->st);
-        if (!e) e = launch_field(c->h, c->d_args, 1, c->st);
+        if (!e)
+            e = batch ? launch_field_batch(bm, (int)c->runs.size(), c->bm_field_smem, 1, c->st)
+                      : launch_field(c->h, c->d_args, 1, c->st);
         if (!e) e = cudaEventRecord(ev[4], c->st);
         if (!e) e = cudaEventSynchronize(ev[4]);
         for (int k = 0; k < 4 && !e; ++k) {
@@ -1001,7 +1112,141 @@ avl_status avl_synchronize(avl_ctx* c)
 {
     if (!c) return AVL_EINVAL;
     AVL_CUDA(c, cudaStreamSynchronize(c->st));
-    return read_errors(c);
+    for (size_t r = 0; r < c->runs.size(); ++r) {
+        avl_status st = read_errors(c->runs[r]);
+        if (st) return fail(c, st, "run " + std::to_string(r) + ": " + c->runs[r]->err);
+    }
+    return c->runs.empty() ? read_errors(c) : AVL_OK;
+}
+
+avl_status avl_create_batch(int32_t nrun, const avl_domain* doms, const avl_species* sps, const int32_t* nspecies,
+                            void* cuda_stream, avl_ctx** out)
+{
+    if (!out) return fail(nullptr, AVL_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (nrun < 1 || nrun > 4096) return fail(nullptr, AVL_EINVAL, "nrun must be in [1, 4096]");
+    if (!doms || !sps || !nspecies) return fail(nullptr, AVL_EINVAL, "doms, sps or nspecies is NULL");
+    for (int r = 0; r < nrun; ++r) {
+        if (doms[r].nvdim != 1) return fail(nullptr, AVL_EINVAL, "batched runs must be 1d1v");
+        if (doms[r].precision != doms[0].precision)
+            return fail(nullptr, AVL_EINVAL, "batched runs must share one precision");
+    }
+    avl_ctx* b = new avl_ctx();
+    b->dom = doms[0];
+    b->h.prec = doms[0].precision;
+    b->h.nvdim = 1;
+    cudaError_t e = cudaGetDevice(&b->device);
+    if (!e && cuda_stream) {
+        b->st = static_cast<cudaStream_t>(cuda_stream);
+    } else if (!e) {
+        e = cudaStreamCreateWithFlags(&b->st, cudaStreamNonBlocking);
+        b->own_stream = e == cudaSuccess;
+    }
+    if (e) {
+        delete b;
+        return cuda_fail(nullptr, e, "avl_create_batch");
+    }
+    int off = 0;
+    for (int r = 0; r < nrun; ++r) {
+        avl_ctx* c = nullptr;
+        avl_status st = avl_create(&doms[r], sps + off, nspecies[r], b->st, &c);
+        if (st) {
+            std::string m = "run " + std::to_string(r) + ": " + g_create_err;
+            avl_destroy(b);
+            return fail(nullptr, st, m);
+        }
+        c->parent = b;
+        b->runs.push_back(c);
+        off += nspecies[r];
+    }
+    *out = b;
+    return AVL_OK;
+}
+
+avl_status avl_batch_run(avl_ctx* b, int32_t r, avl_ctx** run)
+{
+    if (!b || !run) return AVL_EINVAL;
+    if (r < 0 || r >= (int)b->runs.size()) return fail(b, AVL_EINVAL, "run index out of range");
+    *run = b->runs[r];
+    return AVL_OK;
+}
+
+avl_status avl_autotune(avl_ctx* c, int32_t trial_steps, int32_t* chunk_out)
+{
+    if (!c) return AVL_EINVAL;
+    if (trial_steps < 1) return fail(c, AVL_EINVAL, "trial_steps must be >= 1");
+    std::vector<avl_ctx*> runs = c->runs;
+    if (runs.empty()) runs.push_back(c);
+    for (avl_ctx* r : runs)
+        if (r->h.nvdim != 1) return fail(c, AVL_EINVAL, "avl_autotune tunes 1d1v contexts");
+    // snapshot of every marker set (device), restored after each trial
+    struct Snap {
+        avl_ctx* r;
+        int s;
+        long long n;
+        double* buf;
+    };
+    std::vector<Snap> snaps;
+    auto release = [&]() {
+        for (Snap& q : snaps) cudaFree(q.buf);
+        snaps.clear();
+    };
+    for (avl_ctx* r : runs)
+        for (int s = 0; s < r->ns; ++s) {
+            if (!r->has_markers[s]) continue;
+            Snap q{r, s, r->h.sp[s].n, nullptr};
+            cudaError_t e = cudaMalloc(&q.buf, (size_t)q.n * 24);
+            if (e) {
+                release();
+                return cuda_fail(c, e, "cudaMalloc(autotune snapshot)");
+            }
+            snaps.push_back(q);
+            avl_status st = avl_get_markers(r, s, q.buf, q.buf + q.n, q.buf + 2 * q.n, 1);
+            if (st) {
+                release();
+                return fail(c, st, r->err);
+            }
+        }
+    auto restore = [&](int M) -> avl_status {
+        for (avl_ctx* r : runs) r->force_M = M;
+        for (Snap& q : snaps) {
+            avl_status st = avl_set_markers(q.r, q.s, q.n, q.buf, q.buf + q.n, q.buf + 2 * q.n, 1);
+            if (st) return fail(c, st, q.r->err);
+        }
+        return AVL_OK;
+    };
+    const int cand[] = {0, 1024, 2048, 4096, 8192, 16384};
+    int best = 0;
+    float best_ms = 0.f;
+    cudaEvent_t e0, e1;
+    AVL_CUDA(c, cudaEventCreate(&e0));
+    AVL_CUDA(c, cudaEventCreate(&e1));
+    avl_status st = AVL_OK;
+    for (int M : cand) {
+        if ((st = restore(M))) break;
+        if ((st = avl_step(c, 2))) break;   // builds the step graph
+        cudaError_t e = cudaEventRecord(e0, c->st);
+        if (!e && (st = avl_step(c, trial_steps))) break;
+        if (!e) e = cudaEventRecord(e1, c->st);
+        if (!e) e = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        if (!e) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e) {
+            st = cuda_fail(c, e, "avl_autotune");
+            break;
+        }
+        if (M == cand[0] || ms < best_ms) {
+            best = M;
+            best_ms = ms;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st == AVL_OK) st = restore(best);
+    release();
+    if (st) return st;
+    if (chunk_out) *chunk_out = best;
+    return avl_synchronize(c);
 }
 
 }  // extern "C"

@@ -149,6 +149,30 @@ struct StepArgs {
     Ctl* ctl;
 };
 
+// Several independent runs advanced by one launch per kernel class: block g
+// of a batched launch belongs to run r with base[r] <= g < base[r + 1] (its
+// local block g - base[r]); the field kernel's cluster c belongs to run c.
+struct BatchMap {
+    int nrun;
+    const StepArgs* const* args;   // [nrun] each run's arguments (device)
+    const int* pd_base;            // [nrun + 1] push + deposit blocks
+    const int* fin_base;           // [nrun + 1] finalize blocks
+};
+
+// run and local block of this block (A itself and blockIdx.x when bm is null)
+__device__ __forceinline__ const StepArgs* batch_run(const StepArgs* A, const BatchMap* bm, const int* base, int& g)
+{
+    g = (int)blockIdx.x;
+    if (!bm) return A;
+    int lo = 0, hi = bm->nrun;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (base[mid] <= g) lo = mid; else hi = mid;
+    }
+    g -= base[lo];
+    return bm->args[lo];
+}
+
 // kernel launchers (defined in the .cu files; all enqueue on `st`).
 // launch_count1: key histograms of the current markers (after creation).
 // launch_pd1 mode: 0 = refresh (every species with markers: deposit only)
@@ -158,6 +182,14 @@ cudaError_t launch_count1(const StepArgs& h, const StepArgs* d, cudaStream_t st)
 cudaError_t launch_pd1(const StepArgs& h, const StepArgs* d, int mode, cudaStream_t st);
 cudaError_t launch_fin1(const StepArgs& h, const StepArgs* d, int all_species, cudaStream_t st);
 cudaError_t launch_field(const StepArgs& h, const StepArgs* d, int count_step, cudaStream_t st);
+// batched forms (bm on the device; blocks = totals over the runs, smem = the
+// largest of the runs' needs, set beforehand by configure_batch1)
+cudaError_t launch_pd1_batch(int prec, const BatchMap* bm, int blocks, int smem, int mode, cudaStream_t st);
+cudaError_t launch_fin1_batch(int prec, const BatchMap* bm, int blocks, int all_species, cudaStream_t st);
+cudaError_t launch_field_batch(const BatchMap* bm, int nrun, int smem, int count_step, cudaStream_t st);
+cudaError_t configure_batch1(int prec, int pd_smem, int field_smem);
+size_t field_smem_bytes(int nx);
+int pd1_smem_needed(const StepArgs& h);
 // markers from the lattice generator or from caller arrays into the sorted
 // layout of buffer 0 of species s
 cudaError_t launch_init1(const StepArgs& h, const StepArgs* d, int s, const int lattice[4],
@@ -207,6 +239,7 @@ void adjoint_free(AdjEngine* e);
 size_t pd1_smem_bytes(const SpDev& sp, int prec);
 cudaError_t configure_vhs1(const StepArgs& h);
 cudaError_t configure_field(const StepArgs& h);
+cudaError_t configure_field_bytes(int bytes);
 // spectral tables of the Poisson solve (host) and the stand-alone solve
 void spectral_tables(int nx, double L, double cP, int softening, double2* tw, double* gm);
 size_t poisson_smem_bytes(int nx);

@@ -8,6 +8,20 @@
 
 namespace avl {
 
+// Raise a kernel's dynamic shared-memory limit to at least `bytes`.  The
+// limit is a property of the function for the whole process, shared by every
+// context, so it only ever grows (a smaller context created later must not
+// lower the limit another one relies on).  Host only; call outside captures.
+template <typename K>
+static cudaError_t raise_smem_limit(K* kernel, int bytes)
+{
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaFuncGetAttributes(&fa, kernel);
+    if (e) return e;
+    if (fa.maxDynamicSharedSizeBytes >= bytes) return cudaSuccess;
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+}
+
 __device__ __forceinline__ int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
 
 // periodic neighbours of a lower CIC cell i0 in [-1, nx-1]; clamped so that a

@@ -14,6 +14,7 @@
 #include <vector>
 
 #include "avl_internal.cuh"
+#include "common.cuh"
 #include "resort.cuh"
 
 namespace cg = cooperative_groups;
@@ -188,8 +189,10 @@ __device__ void resort_work(const StepArgs* __restrict__ A, int rank)
 }
 
 __global__ void __cluster_dims__(FIELD_CLUSTER, 1, 1) __launch_bounds__(FIELD_THREADS)
-    k_field(const StepArgs* __restrict__ A, int count_step)
+    k_field(const StepArgs* __restrict__ A0, int count_step, const BatchMap* __restrict__ bm)
 {
+    // one cluster per run in a batched launch
+    const StepArgs* __restrict__ A = bm ? bm->args[blockIdx.x / FIELD_CLUSTER] : A0;
     extern __shared__ __align__(16) unsigned char smem[];
     cg::cluster_group cluster = cg::this_cluster();
     const int rank = (int)cluster.block_rank();
@@ -417,7 +420,7 @@ cudaError_t launch_poisson(const double* rho, double* E, int nx, const double2* 
                            cudaStream_t st)
 {
     const size_t smem = poisson_smem_bytes(nx);
-    cudaError_t e = cudaFuncSetAttribute(k_poisson, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = raise_smem_limit(k_poisson, (int)smem);
     if (e) return e;
     const int pow2 = (nx >= 4 && (nx & (nx - 1)) == 0) ? 1 : 0;
     k_poisson<<<1, FIELD_THREADS, smem, st>>>(rho, E, nx, pow2, tw, gmul);
@@ -430,14 +433,22 @@ static size_t field_smem(const StepArgs& h)
     return ((size_t)nx * 8 + 15) / 16 * 16 + ((size_t)nx / 2 + 2) * 16;
 }
 
-cudaError_t configure_field(const StepArgs& h)
-{
-    return cudaFuncSetAttribute(k_field, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)field_smem(h));
-}
+cudaError_t configure_field_bytes(int bytes) { return raise_smem_limit(k_field, bytes); }
+
+cudaError_t configure_field(const StepArgs& h) { return configure_field_bytes((int)field_smem(h)); }
 
 cudaError_t launch_field(const StepArgs& h, const StepArgs* d, int count_step, cudaStream_t st)
 {
-    k_field<<<FIELD_CLUSTER, FIELD_THREADS, field_smem(h), st>>>(d, count_step);
+    k_field<<<FIELD_CLUSTER, FIELD_THREADS, field_smem(h), st>>>(d, count_step, nullptr);
+    return cudaGetLastError();
+}
+
+size_t field_smem_bytes(int nx) { return ((size_t)nx * 8 + 15) / 16 * 16 + ((size_t)nx / 2 + 2) * 16; }
+
+cudaError_t launch_field_batch(const BatchMap* bm, int nrun, int smem, int count_step, cudaStream_t st)
+{
+    if (nrun == 0) return cudaSuccess;
+    k_field<<<FIELD_CLUSTER * nrun, FIELD_THREADS, smem, st>>>(nullptr, count_step, bm);
     return cudaGetLastError();
 }
 

@@ -408,10 +408,12 @@ __global__ void __launch_bounds__(CNT_THREADS) k_count1(const StepArgs* __restri
 // slot of the re-sorted layout in the other buffer, and its new key is
 // counted into cnt[1 - hsel] for step n+1.
 template <typename T, bool SORTED>
-__global__ void __launch_bounds__(PD_THREADS, 2) k_pd1(const StepArgs* __restrict__ A, int mode)
+__global__ void __launch_bounds__(PD_THREADS, 2) k_pd1(const StepArgs* __restrict__ A0, int mode,
+                                                       const BatchMap* __restrict__ bm)
 {
     extern __shared__ __align__(128) unsigned char smem[];
-    const int g = blockIdx.x;
+    int g;
+    const StepArgs* __restrict__ A = batch_run(A0, bm, bm ? bm->pd_base : nullptr, g);
     const int s = species_of_chunk(A, g);
     const SpDev& sp = A->sp[s];
     if (mode == 1 && !sp.mobile) return;
@@ -750,7 +752,8 @@ struct CellSum<double> {
 constexpr int FIN_LIST = 64;   // chunks whose windows meet one finalize block's rows
 
 template <typename T>
-__global__ void __launch_bounds__(FIN_THREADS) k_fin1(const StepArgs* __restrict__ A, int all_species)
+__global__ void __launch_bounds__(FIN_THREADS) k_fin1(const StepArgs* __restrict__ A0, int all_species,
+                                                      const BatchMap* __restrict__ bm)
 {
     constexpr int RL = FIN_THREADS / FIN_XB;   // row lanes
     __shared__ double col_red[RL][FIN_XB];
@@ -758,7 +761,8 @@ __global__ void __launch_bounds__(FIN_THREADS) k_fin1(const StepArgs* __restrict
     __shared__ int clist[FIN_LIST];
     __shared__ int crow[FIN_LIST];
     __shared__ int ncl;
-    const int g = blockIdx.x;
+    int g;
+    const StepArgs* __restrict__ A = batch_run(A0, bm, bm ? bm->fin_base : nullptr, g);
     const int s = species_of_fin(A, g);
     const SpDev& sp = A->sp[s];
     if (!all_species && !sp.mobile) return;
@@ -1078,6 +1082,29 @@ __global__ void k_getf(const T* __restrict__ fg, const T* __restrict__ ng, int n
 // ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
+cudaError_t launch_pd1_batch(int prec, const BatchMap* bm, int blocks, int smem, int mode, cudaStream_t st)
+{
+    if (blocks == 0) return cudaSuccess;
+    if (prec == AVL_FP32) {
+        k_pd1<float, false><<<blocks, PD_THREADS, smem, st>>>(nullptr, mode, bm);
+        if (mode == 1) k_pd1<float, true><<<blocks, PD_THREADS, smem, st>>>(nullptr, mode, bm);
+    } else {
+        k_pd1<double, false><<<blocks, PD_THREADS, smem, st>>>(nullptr, mode, bm);
+        if (mode == 1) k_pd1<double, true><<<blocks, PD_THREADS, smem, st>>>(nullptr, mode, bm);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fin1_batch(int prec, const BatchMap* bm, int blocks, int all_species, cudaStream_t st)
+{
+    if (blocks == 0) return cudaSuccess;
+    if (prec == AVL_FP32)
+        k_fin1<float><<<blocks, FIN_THREADS, 0, st>>>(nullptr, all_species, bm);
+    else
+        k_fin1<double><<<blocks, FIN_THREADS, 0, st>>>(nullptr, all_species, bm);
+    return cudaGetLastError();
+}
+
 static int max_pd_smem(const StepArgs& h)
 {
     size_t m = 0;
@@ -1086,18 +1113,28 @@ static int max_pd_smem(const StepArgs& h)
     return (int)std::max<size_t>(m, 1024);
 }
 
+int pd1_smem_needed(const StepArgs& h) { return max_pd_smem(h); }
+
 // dynamic shared-memory limit of the deposit kernel, set whenever the chunk
 // layout changes (outside any stream capture)
-cudaError_t configure_vhs1(const StepArgs& h)
+static cudaError_t set_pd1_limit(int prec, int smem)
 {
-    const int smem = max_pd_smem(h);
     cudaError_t e;
-    if (h.prec == AVL_FP32) {
-        if ((e = cudaFuncSetAttribute(k_pd1<float, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem))) return e;
-        return cudaFuncSetAttribute(k_pd1<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (prec == AVL_FP32) {
+        if ((e = raise_smem_limit(k_pd1<float, false>, smem))) return e;
+        return raise_smem_limit(k_pd1<float, true>, smem);
     }
-    if ((e = cudaFuncSetAttribute(k_pd1<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem))) return e;
-    return cudaFuncSetAttribute(k_pd1<double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if ((e = raise_smem_limit(k_pd1<double, false>, smem))) return e;
+    return raise_smem_limit(k_pd1<double, true>, smem);
+}
+
+cudaError_t configure_vhs1(const StepArgs& h) { return set_pd1_limit(h.prec, max_pd_smem(h)); }
+
+cudaError_t configure_batch1(int prec, int pd_smem, int field_smem)
+{
+    cudaError_t e = set_pd1_limit(prec, pd_smem);
+    if (e) return e;
+    return configure_field_bytes(field_smem);
 }
 
 cudaError_t launch_count1(const StepArgs& h, const StepArgs* d, cudaStream_t st)
@@ -1115,11 +1152,11 @@ cudaError_t launch_pd1(const StepArgs& h, const StepArgs* d, int mode, cudaStrea
     if (h.nchunk_total == 0) return cudaSuccess;
     const int smem = max_pd_smem(h);
     if (h.prec == AVL_FP32) {
-        k_pd1<float, false><<<h.nchunk_total, PD_THREADS, smem, st>>>(d, mode);
-        if (mode == 1) k_pd1<float, true><<<h.nchunk_total, PD_THREADS, smem, st>>>(d, mode);
+        k_pd1<float, false><<<h.nchunk_total, PD_THREADS, smem, st>>>(d, mode, nullptr);
+        if (mode == 1) k_pd1<float, true><<<h.nchunk_total, PD_THREADS, smem, st>>>(d, mode, nullptr);
     } else {
-        k_pd1<double, false><<<h.nchunk_total, PD_THREADS, smem, st>>>(d, mode);
-        if (mode == 1) k_pd1<double, true><<<h.nchunk_total, PD_THREADS, smem, st>>>(d, mode);
+        k_pd1<double, false><<<h.nchunk_total, PD_THREADS, smem, st>>>(d, mode, nullptr);
+        if (mode == 1) k_pd1<double, true><<<h.nchunk_total, PD_THREADS, smem, st>>>(d, mode, nullptr);
     }
     return cudaGetLastError();
 }
@@ -1127,9 +1164,9 @@ cudaError_t launch_pd1(const StepArgs& h, const StepArgs* d, int mode, cudaStrea
 cudaError_t launch_fin1(const StepArgs& h, const StepArgs* d, int all_species, cudaStream_t st)
 {
     if (h.prec == AVL_FP32)
-        k_fin1<float><<<h.nfin_total, FIN_THREADS, 0, st>>>(d, all_species);
+        k_fin1<float><<<h.nfin_total, FIN_THREADS, 0, st>>>(d, all_species, nullptr);
     else
-        k_fin1<double><<<h.nfin_total, FIN_THREADS, 0, st>>>(d, all_species);
+        k_fin1<double><<<h.nfin_total, FIN_THREADS, 0, st>>>(d, all_species, nullptr);
     return cudaGetLastError();
 }
 

@@ -1006,9 +1006,9 @@ template <typename T>
 static cudaError_t set_pd3_attr(int smem)
 {
     cudaError_t e;
-    if ((e = cudaFuncSetAttribute(k_pd3<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem))) return e;
-    if ((e = cudaFuncSetAttribute(k_pd3<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem))) return e;
-    return cudaFuncSetAttribute(k_pd3<T, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if ((e = raise_smem_limit(k_pd3<T, 1>, smem))) return e;
+    if ((e = raise_smem_limit(k_pd3<T, 2>, smem))) return e;
+    return raise_smem_limit(k_pd3<T, 4>, smem);
 }
 
 cudaError_t configure_vhs3(const StepArgs& h)

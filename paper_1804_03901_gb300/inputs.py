@@ -17,6 +17,15 @@ two_stream  Two-stream instability 1d1v, FP32: electrons 0.5 M(v-3) + 0.5
             +-10 v_th,i, unperturbed); nx = 512, L = 0.4 nx = 204.8,
             nv = 1024 on [-10, 10] v_th; 4 x 4 markers per cell (8388608 per
             species); dt = 0.05; 2000 steps.
+ensemble    Batched ensemble of 256 independent 1d1v FP32 runs (run r seeded with
+            the workload seed + r): nx from {64, 128, 256, 512}, nv from
+            {128, 256, 512, 1024}, markers per cell from {4, 8, 16} (2x2, 2x4,
+            4x4), each a Landau run (Maxwellian drifting at u, v range u +- 6,
+            L = 4 pi, mode 1, dt = 0.1) or a two-stream run (beams at +-u,
+            v range +-10, L = 0.4 nx, modes 1-4 with seeded phases,
+            dt = 0.05) with probability 1/2; amplitude log-uniform in
+            [1e-4, 1e-2], drift u uniform in [0, 4]; immobile ions as the
+            removed k = 0 mode; 1000 steps.
 two_stream_adjoint  Gradient of the field energy at T = 25 of a two-stream
             run, 1d1v: electrons 0.5 M(v-u) + 0.5 M(v+u), u = 3, with 16 mode
             amplitudes around 1e-4 (1e-4 (1 + 0.1 N(0,1)), seeded) and
@@ -70,6 +79,32 @@ def two_stream(nx=512, nv=1024, lattice=(4, 4, 1, 1), steps=2000, nmodes=16, amp
         "lattice": [tuple(lattice), tuple(lattice)],
         "seed": BASE_SEED + 1, "jitter": 1.0, "steps": steps,
     }
+
+
+def ensemble(nrun=256, steps=1000):
+    rng = np.random.default_rng(BASE_SEED + 4)
+    runs = []
+    for r in range(nrun):
+        nx = int(rng.choice([64, 128, 256, 512]))
+        nv = int(rng.choice([128, 256, 512, 1024]))
+        lat = [(2, 2, 1, 1), (2, 4, 1, 1), (4, 4, 1, 1)][int(rng.integers(3))]
+        amp = float(math.exp(rng.uniform(math.log(1e-4), math.log(1e-2))))
+        u = float(rng.uniform(0.0, 4.0))
+        if rng.uniform() < 0.5:
+            run = {"type": "landau", "nx": nx, "L": 4 * math.pi, "dt": 0.1,
+                   "species": [dict(q=-1.0, m=1.0, nv=(nv,), vmin=(u - 6.0,), vmax=(u + 6.0,), mobile=True)],
+                   "f0": [dict(beams=[_maxwell(1.0, u, 1.0)], modes=[(1, amp, 0.0)])]}
+        else:
+            ph = rng.uniform(0.0, 2 * math.pi, 4)
+            run = {"type": "two_stream", "nx": nx, "L": 0.4 * nx, "dt": 0.05,
+                   "species": [dict(q=-1.0, m=1.0, nv=(nv,), vmin=(-10.0,), vmax=(10.0,), mobile=True)],
+                   "f0": [dict(beams=[_maxwell(0.5, u, 1.0), _maxwell(0.5, -u, 1.0)],
+                               modes=[(m + 1, amp, float(ph[m])) for m in range(4)])]}
+        run["lattice"] = [lat]
+        run["seed"] = BASE_SEED + 4 + r
+        runs.append(run)
+    return {"name": f"ensemble_{nrun}_runs_1d1v_fp32", "nvdim": 1, "precision": "fp32", "runs": runs,
+            "jitter": 1.0, "steps": steps}
 
 
 def two_stream_adjoint(nx=256, nv=512, lattice=(2, 4, 1, 1), steps=500, ckpt=50, nmodes=16):
