@@ -159,6 +159,21 @@ avl_status avl_get_rho(avl_ctx* ctx, double* rho, int32_t on_device);
 /* Electric field E (nx, FP64) of the current state (Eq. 6). */
 avl_status avl_get_E(avl_ctx* ctx, double* E, int32_t on_device);
 
+/* Velocity moments of species s of the current state (Sec. 3.4.2 outputs,
+ * not used by the step; formed on demand from the stored f with the
+ * midpoint rule of Eq. 14): out = (2 + nvdim) rows of nx FP64 values,
+ * row-major: rho_s = q sum f dv, j_x = q sum v_x f dv, (1d3v: j_y, j_z),
+ * M2 = q sum |v|^2 f dv (the trace of the second moment, q n <v^2>).
+ * Errors: AVL_EINVAL (species index, NULL out). */
+avl_status avl_get_moments(avl_ctx* ctx, int32_t s, double* out, int32_t on_device);
+
+/* Residual charge of the field solve of the current state (Sec. 3.4.2):
+ * drho_i = rho_i - (E_{i+1} - E_{i-1}) / (2 dx poisson_const), periodic,
+ * nx FP64 values.  Nonzero even for an exact solve, from the centred
+ * difference and the softening of Eq. 6.  Errors: AVL_EINVAL (NULL out, a
+ * batch). */
+avl_status avl_get_residual(avl_ctx* ctx, double* out, int32_t on_device);
+
 /* Diagnostics of the current state (Sec. 3.4.1, FP64, host buffer of
  * 3 + 3 * nspecies values): W_E, W_kin, W_total, then W_kin of each species,
  * N (integral of f) of each species, entropy S of each species.

@@ -214,6 +214,34 @@ def diag(nvdim, nx, L, sp: Species, f):
     return out
 
 
+def moments(nvdim, nx, L, sp: Species, f):
+    """Velocity moments of one species' reconstructed f (Sec. 3.4.2 output
+    quantities), midpoint rule over the cell-centred velocity grid like the
+    charge of Eq. 14: rows [rho_s, j_x, (j_y, j_z,) M2], each (nx,):
+      rho_s = q sum f dv,  j_d = q sum v_d f dv,  M2 = q sum |v|^2 f dv
+    (M2 = q n <v^2>, the trace of the second moment in 1d3v)."""
+    f = np.asarray(f, dtype=np.float64).reshape((nx,) + tuple(sp.nv[:nvdim]))
+    dv = [(sp.vmax[d] - sp.vmin[d]) / sp.nv[d] for d in range(nvdim)]
+    centres = [sp.vmin[d] + (np.arange(sp.nv[d]) + 0.5) * dv[d] for d in range(nvdim)]
+    grids = np.meshgrid(*centres, indexing="ij")
+    dvol = float(np.prod(dv))
+    axes = tuple(range(1, nvdim + 1))
+    out = [sp.q * dvol * f.sum(axis=axes)]
+    for d in range(nvdim):
+        out.append(sp.q * dvol * (f * grids[d]).sum(axis=axes))
+    v2 = sum(g * g for g in grids)
+    out.append(sp.q * dvol * (f * v2).sum(axis=axes))
+    return np.array(out)
+
+
+def field_residual(nx, L, cP, rho, E):
+    """Charge the field solve leaves unexplained (Sec. 3.4.2):
+    rho_i - (E_{i+1} - E_{i-1}) / (2 dx cP), centred difference, periodic."""
+    dx = L / nx
+    E = np.asarray(E, dtype=np.float64)
+    return np.asarray(rho, dtype=np.float64) - (np.roll(E, -1) - np.roll(E, 1)) / (2.0 * dx * cP)
+
+
 def field_energy(nx, L, cP, E):
     return float(lib().orc_field_energy(nx, L, cP, _dp(np.ascontiguousarray(E, dtype=np.float64))))
 

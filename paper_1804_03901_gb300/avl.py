@@ -27,6 +27,7 @@ EXPORTED = ["avl_create", "avl_destroy", "avl_last_error", "avl_init_markers", "
             "avl_marker_count", "avl_get_markers", "avl_step", "avl_get_f", "avl_get_rho",
             "avl_get_E", "avl_get_diag", "avl_get_stats", "avl_field_solve", "avl_field_solve_noalloc",
             "avl_profile_steps", "avl_adjoint", "avl_create_batch", "avl_batch_run", "avl_autotune",
+            "avl_get_moments", "avl_get_residual",
             "avl_synchronize"]
 
 
@@ -82,6 +83,8 @@ def _load():
                                        C.POINTER(C.c_int32), vp, C.POINTER(vp)]),
         "avl_batch_run": (C.c_int, [vp, C.c_int32, C.POINTER(vp)]),
         "avl_autotune": (C.c_int, [vp, C.c_int32, C.POINTER(C.c_int32)]),
+        "avl_get_moments": (C.c_int, [vp, C.c_int32, vp, C.c_int32]),
+        "avl_get_residual": (C.c_int, [vp, vp, C.c_int32]),
         "avl_synchronize": (C.c_int, [vp]),
     }
     for name, (res, args) in sig.items():
@@ -114,6 +117,8 @@ avl_adjoint = lib.avl_adjoint
 avl_create_batch = lib.avl_create_batch
 avl_batch_run = lib.avl_batch_run
 avl_autotune = lib.avl_autotune
+avl_get_moments = lib.avl_get_moments
+avl_get_residual = lib.avl_get_residual
 avl_synchronize = lib.avl_synchronize
 
 
@@ -245,6 +250,17 @@ class Simulation:
         n = np.zeros(shape) if with_n else None
         self._chk(avl_get_f(self.ctx, s, f.ctypes.data, n.ctypes.data if with_n else None, 0))
         return (f, n) if with_n else f
+
+    def get_moments(self, s):
+        """(2 + nvdim, nx): rho_s, j_x, (j_y, j_z), M2 of species s."""
+        out = np.zeros((2 + self.nvdim, self.nx))
+        self._chk(avl_get_moments(self.ctx, s, out.ctypes.data, 0))
+        return out
+
+    def get_residual(self):
+        out = np.zeros(self.nx)
+        self._chk(avl_get_residual(self.ctx, out.ctypes.data, 0))
+        return out
 
     def get_rho(self):
         r = np.zeros(self.nx)

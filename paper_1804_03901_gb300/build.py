@@ -16,7 +16,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libavl.so")
-SOURCES = ["avl_api.cu", "k_vhs1.cu", "k_vhs3.cu", "k_adjoint.cu", "k_field.cu", "field_noalloc.cu"]
+SOURCES = ["avl_api.cu", "k_vhs1.cu", "k_vhs3.cu", "k_adjoint.cu", "k_moments.cu", "k_field.cu", "field_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

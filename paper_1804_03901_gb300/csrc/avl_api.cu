@@ -972,6 +972,41 @@ avl_status avl_get_E(avl_ctx* c, double* E, int32_t on_device)
     return get_field(c, c ? c->h.fd.E64 : nullptr, E, on_device);
 }
 
+avl_status avl_get_moments(avl_ctx* c, int32_t s, double* out, int32_t on_device)
+{
+    avl_status st = check_species(c, s);
+    if (st) return st;
+    if (!out) return fail(c, AVL_EINVAL, "out is NULL");
+    const SpDev& sp = c->h.sp[s];
+    const size_t bytes = (size_t)(2 + sp.nvdim) * sp.nx * 8;
+    if (on_device) {
+        AVL_CUDA(c, launch_moments(c->h, c->d_args, s, out, c->st));
+        return AVL_OK;
+    }
+    if ((st = ensure_scratch(c, bytes))) return st;
+    AVL_CUDA(c, launch_moments(c->h, c->d_args, s, static_cast<double*>(c->scratch), c->st));
+    AVL_CUDA(c, cudaMemcpyAsync(out, c->scratch, bytes, cudaMemcpyDeviceToHost, c->st));
+    AVL_CUDA(c, cudaStreamSynchronize(c->st));
+    return AVL_OK;
+}
+
+avl_status avl_get_residual(avl_ctx* c, double* out, int32_t on_device)
+{
+    if (!c || !c->runs.empty()) return c ? fail(c, AVL_EINVAL, "a batch has no field; use a run") : AVL_EINVAL;
+    if (!out) return fail(c, AVL_EINVAL, "out is NULL");
+    const size_t bytes = (size_t)c->h.fd.nx * 8;
+    if (on_device) {
+        AVL_CUDA(c, launch_residual(c->h, c->d_args, out, c->st));
+        return AVL_OK;
+    }
+    avl_status st = ensure_scratch(c, bytes);
+    if (st) return st;
+    AVL_CUDA(c, launch_residual(c->h, c->d_args, static_cast<double*>(c->scratch), c->st));
+    AVL_CUDA(c, cudaMemcpyAsync(out, c->scratch, bytes, cudaMemcpyDeviceToHost, c->st));
+    AVL_CUDA(c, cudaStreamSynchronize(c->st));
+    return AVL_OK;
+}
+
 avl_status avl_get_diag(avl_ctx* c, double* out)
 {
     if (!c) return AVL_EINVAL;

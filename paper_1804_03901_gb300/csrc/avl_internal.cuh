@@ -221,6 +221,11 @@ cudaError_t launch_get3(const StepArgs& h, const StepArgs* d, int s, double* x, 
 cudaError_t launch_getf3(const StepArgs& h, int s, int asel, double* f, double* n, cudaStream_t st);
 size_t pd3_smem_bytes(int nx, int prec);
 
+// output moments of species s ([2 + nvdim][nx], device, FP64) and the field
+// residual ([nx]) of the current state (k_moments.cu)
+cudaError_t launch_moments(const StepArgs& h, const StepArgs* d, int s, double* out, cudaStream_t st);
+cudaError_t launch_residual(const StepArgs& h, const StepArgs* d, double* out, cudaStream_t st);
+
 // discrete adjoint of the 1d1v step (k_adjoint.cu): the species' lattice
 // parameters of their last creation, theta = the f0 of species theta_s
 struct AdjSpec {

@@ -407,13 +407,14 @@ __global__ void __launch_bounds__(CNT_THREADS) k_count1(const StepArgs* __restri
 // registers first), written back in place, or, on re-sort steps, into its
 // slot of the re-sorted layout in the other buffer, and its new key is
 // counted into cnt[1 - hsel] for step n+1.
-template <typename T, bool SORTED>
+template <typename T, bool SORTED, bool BATCH>
 __global__ void __launch_bounds__(PD_THREADS, 2) k_pd1(const StepArgs* __restrict__ A0, int mode,
                                                        const BatchMap* __restrict__ bm)
 {
     extern __shared__ __align__(128) unsigned char smem[];
-    int g;
-    const StepArgs* __restrict__ A = batch_run(A0, bm, bm ? bm->pd_base : nullptr, g);
+    int g = blockIdx.x;
+    const StepArgs* __restrict__ A = A0;
+    if constexpr (BATCH) A = batch_run(A0, bm, bm->pd_base, g);
     const int s = species_of_chunk(A, g);
     const SpDev& sp = A->sp[s];
     if (mode == 1 && !sp.mobile) return;
@@ -751,7 +752,7 @@ struct CellSum<double> {
 
 constexpr int FIN_LIST = 64;   // chunks whose windows meet one finalize block's rows
 
-template <typename T>
+template <typename T, bool BATCH>
 __global__ void __launch_bounds__(FIN_THREADS) k_fin1(const StepArgs* __restrict__ A0, int all_species,
                                                       const BatchMap* __restrict__ bm)
 {
@@ -761,8 +762,9 @@ __global__ void __launch_bounds__(FIN_THREADS) k_fin1(const StepArgs* __restrict
     __shared__ int clist[FIN_LIST];
     __shared__ int crow[FIN_LIST];
     __shared__ int ncl;
-    int g;
-    const StepArgs* __restrict__ A = batch_run(A0, bm, bm ? bm->fin_base : nullptr, g);
+    int g = blockIdx.x;
+    const StepArgs* __restrict__ A = A0;
+    if constexpr (BATCH) A = batch_run(A0, bm, bm->fin_base, g);
     const int s = species_of_fin(A, g);
     const SpDev& sp = A->sp[s];
     if (!all_species && !sp.mobile) return;
@@ -817,17 +819,31 @@ __global__ void __launch_bounds__(FIN_THREADS) k_fin1(const StepArgs* __restrict
     __syncthreads();
     const int nlist = ncl;
     const bool use_list = nlist <= FIN_LIST;
+    // the list ordered by first window row (ties by chunk), so that a column
+    // walks only the windows that cover its rows
+    __shared__ int slist[FIN_LIST], srow[FIN_LIST];
+    if (use_list) {
+        for (int t = threadIdx.x; t < nlist; t += FIN_THREADS) {
+            const int r = crow[t];
+            int rank = 0;
+            for (int q = 0; q < nlist; ++q) rank += (crow[q] < r || (crow[q] == r && q < t)) ? 1 : 0;
+            slist[rank] = clist[t];
+            srow[rank] = r;
+        }
+        __syncthreads();
+    }
 
     ColAcc<T> acc;
     if (xok) {
+        int lo = 0;   // first listed window that can still reach the rows ahead
         for (int j = j0 + lr; j < j1; j += RL) {
             CellSum<T> cs;
             if (use_list) {
-                for (int q = 0; q < nlist; ++q) {
-                    const int wr = j - shx - crow[q];
-                    if (wr >= 0 && wr < W)
-                        cs.add_partial(part + (size_t)clist[q] * planes * plane + (size_t)wr * nx + x, plane);
-                }
+                const int rel = j - shx;   // row in window coordinates
+                while (lo < nlist && srow[lo] + W <= rel) ++lo;
+                for (int q = lo; q < nlist && srow[q] <= rel; ++q)
+                    cs.add_partial(part + (size_t)slist[q] * planes * plane + (size_t)(rel - srow[q]) * nx + x,
+                                   plane);
             } else {
                 for (int cc = 0; cc < sp.nchunk; ++cc) {
                     const int wr = j - shx - sp.wrow0[cc];
@@ -1086,11 +1102,11 @@ cudaError_t launch_pd1_batch(int prec, const BatchMap* bm, int blocks, int smem,
 {
     if (blocks == 0) return cudaSuccess;
     if (prec == AVL_FP32) {
-        k_pd1<float, false><<<blocks, PD_THREADS, smem, st>>>(nullptr, mode, bm);
-        if (mode == 1) k_pd1<float, true><<<blocks, PD_THREADS, smem, st>>>(nullptr, mode, bm);
+        k_pd1<float, false, true><<<blocks, PD_THREADS, smem, st>>>(nullptr, mode, bm);
+        if (mode == 1) k_pd1<float, true, true><<<blocks, PD_THREADS, smem, st>>>(nullptr, mode, bm);
     } else {
-        k_pd1<double, false><<<blocks, PD_THREADS, smem, st>>>(nullptr, mode, bm);
-        if (mode == 1) k_pd1<double, true><<<blocks, PD_THREADS, smem, st>>>(nullptr, mode, bm);
+        k_pd1<double, false, true><<<blocks, PD_THREADS, smem, st>>>(nullptr, mode, bm);
+        if (mode == 1) k_pd1<double, true, true><<<blocks, PD_THREADS, smem, st>>>(nullptr, mode, bm);
     }
     return cudaGetLastError();
 }
@@ -1099,9 +1115,9 @@ cudaError_t launch_fin1_batch(int prec, const BatchMap* bm, int blocks, int all_
 {
     if (blocks == 0) return cudaSuccess;
     if (prec == AVL_FP32)
-        k_fin1<float><<<blocks, FIN_THREADS, 0, st>>>(nullptr, all_species, bm);
+        k_fin1<float, true><<<blocks, FIN_THREADS, 0, st>>>(nullptr, all_species, bm);
     else
-        k_fin1<double><<<blocks, FIN_THREADS, 0, st>>>(nullptr, all_species, bm);
+        k_fin1<double, true><<<blocks, FIN_THREADS, 0, st>>>(nullptr, all_species, bm);
     return cudaGetLastError();
 }
 
@@ -1117,15 +1133,19 @@ int pd1_smem_needed(const StepArgs& h) { return max_pd_smem(h); }
 
 // dynamic shared-memory limit of the deposit kernel, set whenever the chunk
 // layout changes (outside any stream capture)
-static cudaError_t set_pd1_limit(int prec, int smem)
+template <typename T>
+static cudaError_t set_pd1_limit_t(int smem)
 {
     cudaError_t e;
-    if (prec == AVL_FP32) {
-        if ((e = raise_smem_limit(k_pd1<float, false>, smem))) return e;
-        return raise_smem_limit(k_pd1<float, true>, smem);
-    }
-    if ((e = raise_smem_limit(k_pd1<double, false>, smem))) return e;
-    return raise_smem_limit(k_pd1<double, true>, smem);
+    if ((e = raise_smem_limit(k_pd1<T, false, false>, smem))) return e;
+    if ((e = raise_smem_limit(k_pd1<T, true, false>, smem))) return e;
+    if ((e = raise_smem_limit(k_pd1<T, false, true>, smem))) return e;
+    return raise_smem_limit(k_pd1<T, true, true>, smem);
+}
+
+static cudaError_t set_pd1_limit(int prec, int smem)
+{
+    return prec == AVL_FP32 ? set_pd1_limit_t<float>(smem) : set_pd1_limit_t<double>(smem);
 }
 
 cudaError_t configure_vhs1(const StepArgs& h) { return set_pd1_limit(h.prec, max_pd_smem(h)); }
@@ -1152,11 +1172,11 @@ cudaError_t launch_pd1(const StepArgs& h, const StepArgs* d, int mode, cudaStrea
     if (h.nchunk_total == 0) return cudaSuccess;
     const int smem = max_pd_smem(h);
     if (h.prec == AVL_FP32) {
-        k_pd1<float, false><<<h.nchunk_total, PD_THREADS, smem, st>>>(d, mode, nullptr);
-        if (mode == 1) k_pd1<float, true><<<h.nchunk_total, PD_THREADS, smem, st>>>(d, mode, nullptr);
+        k_pd1<float, false, false><<<h.nchunk_total, PD_THREADS, smem, st>>>(d, mode, nullptr);
+        if (mode == 1) k_pd1<float, true, false><<<h.nchunk_total, PD_THREADS, smem, st>>>(d, mode, nullptr);
     } else {
-        k_pd1<double, false><<<h.nchunk_total, PD_THREADS, smem, st>>>(d, mode, nullptr);
-        if (mode == 1) k_pd1<double, true><<<h.nchunk_total, PD_THREADS, smem, st>>>(d, mode, nullptr);
+        k_pd1<double, false, false><<<h.nchunk_total, PD_THREADS, smem, st>>>(d, mode, nullptr);
+        if (mode == 1) k_pd1<double, true, false><<<h.nchunk_total, PD_THREADS, smem, st>>>(d, mode, nullptr);
     }
     return cudaGetLastError();
 }
@@ -1164,9 +1184,9 @@ cudaError_t launch_pd1(const StepArgs& h, const StepArgs* d, int mode, cudaStrea
 cudaError_t launch_fin1(const StepArgs& h, const StepArgs* d, int all_species, cudaStream_t st)
 {
     if (h.prec == AVL_FP32)
-        k_fin1<float><<<h.nfin_total, FIN_THREADS, 0, st>>>(d, all_species, nullptr);
+        k_fin1<float, false><<<h.nfin_total, FIN_THREADS, 0, st>>>(d, all_species, nullptr);
     else
-        k_fin1<double><<<h.nfin_total, FIN_THREADS, 0, st>>>(d, all_species, nullptr);
+        k_fin1<double, false><<<h.nfin_total, FIN_THREADS, 0, st>>>(d, all_species, nullptr);
     return cudaGetLastError();
 }
 

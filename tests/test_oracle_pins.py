@@ -349,3 +349,59 @@ def test_push_gathers_with_cic_weights_linear_field():
     v = np.zeros((1, 4))
     O.push(1, nx, L, sp, x, v, 1.0, E)
     np.testing.assert_allclose(v[0], [2.0, 2.75, 3.5, 5.0], atol=1e-14)
+
+
+# --- output moments and the field residual (Sec. 3.4.2) ------------------------
+def test_moments_of_a_flat_distribution_are_exact():
+    """f = c on the velocity grid: the midpoint rule integrates v exactly and
+    v^2 with the known -h^2/24 error per cell: j = q c (b^2 - a^2)/2,
+    M2 = q c [(b^3 - a^3)/3 - (b - a) h^2 / 12]."""
+    nx, L = 5, 3.0
+    sp = O.Species(q=-1.5, m=1.0, nv=(17,), vmin=(-2.0,), vmax=(5.0,))
+    c = 0.7
+    f = np.full((nx, 17), c)
+    m = O.moments(1, nx, L, sp, f)
+    a, b = -2.0, 5.0
+    h = (b - a) / 17
+    np.testing.assert_allclose(m[0], sp.q * c * (b - a), rtol=1e-14)
+    np.testing.assert_allclose(m[1], sp.q * c * (b * b - a * a) / 2, rtol=1e-13)
+    np.testing.assert_allclose(m[2], sp.q * c * ((b ** 3 - a ** 3) / 3 - (b - a) * h * h / 12), rtol=1e-13)
+
+
+def test_moments_1d3v_separate_by_component():
+    """1d3v: f = g(vx) h(vy) k(vz) gives j_d = q (prod of the other
+    integrals) (first moment of its own factor), and M2 the sum over d."""
+    nx, L = 3, 2.0
+    sp = O.Species(q=1.0, m=1.0, nv=(6, 5, 4), vmin=(-1.0, -2.0, 0.5), vmax=(2.0, 1.0, 1.5))
+    rng = np.random.default_rng(2)
+    fac = [rng.uniform(0.1, 1.0, n) for n in sp.nv]
+    f = np.einsum("i,j,k->ijk", *fac)[None].repeat(nx, axis=0)
+    dv = [(sp.vmax[d] - sp.vmin[d]) / sp.nv[d] for d in range(3)]
+    vc = [sp.vmin[d] + (np.arange(sp.nv[d]) + 0.5) * dv[d] for d in range(3)]
+    I0 = [fac[d].sum() * dv[d] for d in range(3)]
+    I1 = [(fac[d] * vc[d]).sum() * dv[d] for d in range(3)]
+    I2 = [(fac[d] * vc[d] ** 2).sum() * dv[d] for d in range(3)]
+    m = O.moments(3, nx, L, sp, f)
+    np.testing.assert_allclose(m[0], np.prod(I0), rtol=1e-13)
+    for d in range(3):
+        others = np.prod([I0[e] for e in range(3) if e != d])
+        np.testing.assert_allclose(m[1 + d], I1[d] * others, rtol=1e-13)
+    M2 = sum(I2[d] * np.prod([I0[e] for e in range(3) if e != d]) for d in range(3))
+    np.testing.assert_allclose(m[4], M2, rtol=1e-13)
+
+
+@pytest.mark.parametrize("softening", [True, False])
+def test_field_residual_of_a_single_mode(softening):
+    """rho = cos(k x): E from Eq. 5 / Eq. 6 is c kappa/K^2 sin(k x), its
+    centred difference c (kappa/K^2)(sin(k dx)/dx) cos(k x) / c, so the
+    residual is cos(k x) (1 - kappa sin(k dx) / (dx K^2))."""
+    nx, L, cP, m = 32, 7.0, 4 * np.pi, 3
+    dx = L / nx
+    x = (np.arange(nx) + 0.0) * dx
+    k = 2 * np.pi * m / L
+    rho = np.cos(k * x)
+    E = O.poisson(nx, L, cP, softening, rho)
+    kappa = np.sin(k * dx) / dx if softening else k
+    K2 = (2 * np.sin(k * dx / 2) / dx) ** 2 if softening else k * k
+    expect = rho * (1 - kappa * np.sin(k * dx) / (dx * K2))
+    np.testing.assert_allclose(O.field_residual(nx, L, cP, rho, E), expect, atol=1e-12)
