@@ -146,15 +146,22 @@ avl_status plan_layout(avl_ctx* c, int s, long long n)
     if (c->force_M > 0) M = ((long long)c->force_M + 63) / 64 * 64;
     const int m_env = env_int("AVL_CHUNK_M", 0);
     if (m_env > 0) M = (m_env + 63) / 64 * 64;
-    const int nch = (int)((n + M - 1) / M);
     const double mpk = std::max(1.0, (double)n / sp.nvflat);
-    int span = (int)std::ceil((double)M / mpk) + 1;
-    int Wmax = span + 2 * HALO + 1;
-    Wmax = std::min(Wmax, sp.nvflat + 2 * HALO + 2);
     const int w_env = env_int("AVL_WMAX", 0);
-    if (w_env > 0) Wmax = w_env;
-    sp.M = (int)M;
-    sp.Wmax = Wmax;
+    int Wmax = 0;
+    for (;;) {
+        // window: the rows one chunk's keys span, the CIC reach and a drift halo;
+        // smaller chunks while it does not fit in shared memory
+        const int span = (int)std::ceil((double)M / mpk) + 1;
+        Wmax = std::min(span + 2 * HALO + 1, sp.nvflat + 2 * HALO + 2);
+        if (w_env > 0) Wmax = w_env;
+        sp.M = (int)M;
+        sp.Wmax = Wmax;
+        if (pd1_smem_bytes(sp, c->h.prec) <= 220 * 1024 || M <= 256 || w_env > 0 || m_env > 0 || c->force_M > 0)
+            break;
+        M = std::max<long long>(256, (M / 2 + 63) / 64 * 64);
+    }
+    const int nch = (int)((n + M - 1) / M);
     if (pd1_smem_bytes(sp, c->h.prec) > 220 * 1024)
         return fail(c, AVL_EINVAL, "window of " + std::to_string(Wmax) + " velocity rows x " + std::to_string(sp.nx) +
                                        " cells does not fit in shared memory (use fewer markers per chunk)");

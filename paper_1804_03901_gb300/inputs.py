@@ -17,6 +17,10 @@ two_stream  Two-stream instability 1d1v, FP32: electrons 0.5 M(v-3) + 0.5
             +-10 v_th,i, unperturbed); nx = 512, L = 0.4 nx = 204.8,
             nv = 1024 on [-10, 10] v_th; 4 x 4 markers per cell (8388608 per
             species); dt = 0.05; 2000 steps.
+landau_paper  The paper's own Landau run (Sec. 4.2): k = 0.4, L = 5 pi,
+            nx = 512, nv = 6600 on [-10, 10], alpha = 0.05, dt = 0.1, FP64,
+            2 x 2 markers per cell (13516800), 1000 steps (t = 100: linear
+            damping and the first trapping oscillation).
 ensemble    Batched ensemble of 256 independent 1d1v FP32 runs (run r seeded with
             the workload seed + r): nx from {64, 128, 256, 512}, nv from
             {128, 256, 512, 1024}, markers per cell from {4, 8, 16} (2x2, 2x4,
@@ -78,6 +82,17 @@ def two_stream(nx=512, nv=1024, lattice=(4, 4, 1, 1), steps=2000, nmodes=16, amp
                dict(beams=[_maxwell(1.0, 0.0, vthi)], modes=[])],
         "lattice": [tuple(lattice), tuple(lattice)],
         "seed": BASE_SEED + 1, "jitter": 1.0, "steps": steps,
+    }
+
+
+def landau_paper(nx=512, nv=6600, steps=1000, lattice=(2, 2, 1, 1)):
+    return {
+        "name": f"landau_paper_1d1v_fp64_nx{nx}_nv{nv}",
+        "nvdim": 1, "nx": nx, "L": 5 * math.pi, "dt": 0.1, "precision": "fp64",
+        "species": [dict(q=-1.0, m=1.0, nv=(nv,), vmin=(-10.0,), vmax=(10.0,), mobile=True)],
+        "f0": [dict(beams=[_maxwell(1.0, 0.0, 1.0)], modes=[(1, 0.05, 0.0)])],
+        "lattice": [tuple(lattice)],
+        "seed": BASE_SEED + 5, "jitter": 1.0, "steps": steps,
     }
 
 
