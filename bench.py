@@ -60,13 +60,19 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--nv", type=int, default=0, help="velocity cells (profiling of a smaller case)")
+    p.add_argument("--amp", type=float, default=0.0,
+                   help="two-stream perturbation amplitude instead of 1e-4 (profiling of the re-sorting, "
+                        "strongly driven state from the first step)")
     return p.parse_args()
 
 
-def workload(name, nv=0):
+def workload(name, nv=0, amp=0.0):
     from paper_1804_03901_gb300 import inputs
     if name == "two_stream":
-        return inputs.two_stream(nv=nv) if nv else inputs.two_stream()
+        kw = {"nv": nv} if nv else {}
+        if amp:
+            kw["amp"] = amp
+        return inputs.two_stream(**kw)
     if name == "bump_on_tail":
         return inputs.bump_on_tail(nv=nv) if nv else inputs.bump_on_tail()
     if name == "two_stream_adjoint":
@@ -243,7 +249,7 @@ def run_ours(args):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     from paper_1804_03901_gb300 import avl as A
 
-    w = workload(args.workload, args.nv)
+    w = workload(args.workload, args.nv, args.amp)
     # a dedicated stream: the library enqueues on it, the timing events too
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)

@@ -109,6 +109,8 @@ struct SpDev {
 
 struct FieldDev {
     int nx, pow2, softening, ndiag;
+    int resort_drift;          // 1d1v: re-sort whenever the field drifts markers a row or more
+    int resort_miss;           // 1d1v: re-sort when more than n / resort_miss markers miss their window
     double L, dx, cP;
     double* rho;               // nx
     double* E64;               // nx

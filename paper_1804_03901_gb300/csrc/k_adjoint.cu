@@ -50,10 +50,11 @@ struct AdjSp {
     void* lx;          // [n] lambda_X
     void* lv;          // [n] lambda_V
     double* mu;        // [n] dJ / df_l
-    void* num;         // [nv][nx] deposit accumulators
-    void* den;
+    void* num;         // [nv][nx][2] deposit accumulator: (numerator, denominator) pairs
+    void* den;         // unused
     void* hF;          // [K + 1][nv][nx] F = N / D per slot
     void* hD;          // [K + 1][nv][nx] D per slot
+    void* AB;          // [nv][nx][2] grid adjoint (A, B) of the state being walked back
 };
 
 struct AdjDev {
@@ -115,6 +116,18 @@ __device__ __forceinline__ int vrow(T v, const SpDev& sp, T& w)
     return (int)fl;
 }
 
+// (numerator, denominator) of one cell in one reduction: a v2 FP32
+// reduction in the FP32 path, two FP64 ones in the FP64 path
+__device__ __forceinline__ void pair_add(float* p, float n, float d)
+{
+    asm volatile("red.global.add.v2.f32 [%0], {%1, %2};" ::"l"(p), "f"(n), "f"(d) : "memory");
+}
+__device__ __forceinline__ void pair_add(double* p, double n, double d)
+{
+    atomicAdd(p, n);
+    atomicAdd(p + 1, d);
+}
+
 // lattice marker m (order m = (i nv + j) ppc + a pv + b) of species s
 template <typename T>
 __global__ void k_ad_init(const StepArgs* __restrict__ A, const AdjDev* __restrict__ D, int s)
@@ -149,8 +162,7 @@ __global__ void k_ad_dep(const StepArgs* __restrict__ A, const AdjDev* __restric
     const SpDev& sp = A->sp[s];
     const AdjSp& a = D->sp[s];
     const int nx = sp.nx, nv = sp.nv[0];
-    T* num = reinterpret_cast<T*>(a.num);
-    T* den = reinterpret_cast<T*>(a.den);
+    T* acc = reinterpret_cast<T*>(a.num);
     const T* f = reinterpret_cast<const T*>(a.f);
     const T* vv = reinterpret_cast<const T*>(a.hv) + (size_t)slot * a.n;
     for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < a.n; k += (long long)gridDim.x * blockDim.x) {
@@ -169,10 +181,8 @@ __global__ void k_ad_dep(const StepArgs* __restrict__ A, const AdjDev* __restric
             if (j < 0 || j >= nv) continue;
             const T av = cv ? wv : (T)1 - wv;
             const T a0 = ((T)1 - wx) * av, a1 = wx * av;
-            atomicAdd(num + (size_t)j * nx + ia, a0 * fl);
-            atomicAdd(den + (size_t)j * nx + ia, a0);
-            atomicAdd(num + (size_t)j * nx + ib, a1 * fl);
-            atomicAdd(den + (size_t)j * nx + ib, a1);
+            pair_add(acc + 2 * ((size_t)j * nx + ia), a0 * fl, a0);
+            pair_add(acc + 2 * ((size_t)j * nx + ib), a1 * fl, a1);
         }
     }
 }
@@ -190,20 +200,21 @@ __global__ void __launch_bounds__(256) k_ad_fin(const StepArgs* __restrict__ A, 
     const int nx = sp.nx, nv = sp.nv[0];
     const int x = blockIdx.x * 32 + (threadIdx.x & 31), lr = threadIdx.x >> 5;
     const size_t cells = (size_t)nx * nv;
-    T* num = reinterpret_cast<T*>(a.num);
-    T* den = reinterpret_cast<T*>(a.den);
+    const int rg = (nv + gridDim.z - 1) / gridDim.z;   // rows of this block's group
+    const int jb = blockIdx.z * rg, je = min(nv, jb + rg);
+    T* acc = reinterpret_cast<T*>(a.num);
     T* F = reinterpret_cast<T*>(a.hF) + (size_t)slot * cells;
     T* Dg = reinterpret_cast<T*>(a.hD) + (size_t)slot * cells;
     double r = 0.0;
     if (x < nx) {
-        for (int j = lr; j < nv; j += 8) {
+        for (int j = jb + lr; j < je; j += 8) {
             const size_t o = (size_t)j * nx + x;
-            const T n0 = num[o], d0 = den[o];
+            const T n0 = acc[2 * o], d0 = acc[2 * o + 1];
             const T fv = d0 > (T)0 ? n0 / d0 : (T)0;
             F[o] = fv;
             Dg[o] = d0;
-            num[o] = (T)0;
-            den[o] = (T)0;
+            acc[2 * o] = (T)0;
+            acc[2 * o + 1] = (T)0;
             r += (double)fv;
         }
     }
@@ -249,11 +260,25 @@ __global__ void k_ad_push(const StepArgs* __restrict__ A, const AdjDev* __restri
 
 // adjoint deposit onto the x grid: e_i += lt (q/m) dt G_i(X) over the mobile
 // markers of slot (lt = lambda_V + dt lambda_X); at the final state e = dx E
+// per-warp partial sums of the adjoint deposit: FP32 in the FP32 path (native
+// shared-memory reductions), FP64 otherwise; one copy per warp keeps the
+// contention within a warp
+template <typename T>
+struct EAcc {
+    using type = double;
+};
+template <>
+struct EAcc<float> {
+    using type = float;
+};
+
 template <typename T>
 __global__ void __launch_bounds__(256) k_ad_e(const StepArgs* __restrict__ A, const AdjDev* __restrict__ D, int slot,
-                                              int terminal)
+                                              int terminal, int copies)
 {
-    extern __shared__ double es[];
+    using S = typename EAcc<T>::type;
+    extern __shared__ __align__(16) unsigned char es_raw[];
+    S* es = reinterpret_cast<S*>(es_raw);   // [8 warps][nx]
     const int s = D->act[blockIdx.y];
     const SpDev& sp = A->sp[s];
     const AdjSp& a = D->sp[s];
@@ -264,8 +289,9 @@ __global__ void __launch_bounds__(256) k_ad_e(const StepArgs* __restrict__ A, co
         return;
     }
     if (!sp.mobile) return;
-    for (int i = threadIdx.x; i < nx; i += blockDim.x) es[i] = 0.0;
+    for (int i = threadIdx.x; i < copies * nx; i += blockDim.x) es[i] = (S)0;
     __syncthreads();
+    S* ew = copies ? es + ((threadIdx.x >> 5) % copies) * nx : nullptr;
     const T* lx = reinterpret_cast<const T*>(a.lx);
     const T* lv = reinterpret_cast<const T*>(a.lv);
     const double c0 = sp.qm_dt;
@@ -278,15 +304,46 @@ __global__ void __launch_bounds__(256) k_ad_e(const StepArgs* __restrict__ A, co
         int ia, ib;
         wrap_pair(i0, nx, ia, ib);
         const double c = ((double)lv[k] + dt * (double)lx[k]) * c0;
-        atomicAdd(es + ia, c * (1.0 - (double)w));
-        atomicAdd(es + ib, c * (double)w);
+        if (copies) {
+            atomicAdd(ew + ia, (S)(c * (1.0 - (double)w)));
+            atomicAdd(ew + ib, (S)(c * (double)w));
+        } else {   // grid too large for shared copies
+            atomicAdd(D->e + ia, c * (1.0 - (double)w));
+            atomicAdd(D->e + ib, c * (double)w);
+        }
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < nx; i += blockDim.x)
-        if (es[i] != 0.0) atomicAdd(D->e + i, es[i]);
+    for (int i = threadIdx.x; i < nx && copies; i += blockDim.x) {
+        double t = 0.0;
+        for (int q = 0; q < copies; ++q) t += (double)es[q * nx + i];
+        if (t != 0.0) atomicAdd(D->e + i, t);
+    }
 }
 
-// per marker: mu += sum A alpha, lambda update (see the file head); tmp = P e
+// grid adjoint of slot: A = psi / D, B = psi F / D (0 where D = 0) with
+// psi = q dv P^T e = -q dv (P e) = -q dv tmp
+template <typename T>
+__global__ void k_ad_grid(const StepArgs* __restrict__ A, const AdjDev* __restrict__ D, int slot)
+{
+    const int s = D->act[blockIdx.y];
+    const SpDev& sp = A->sp[s];
+    const AdjSp& a = D->sp[s];
+    const int nx = sp.nx;
+    const size_t cells = (size_t)nx * sp.nv[0];
+    const T* F = reinterpret_cast<const T*>(a.hF) + (size_t)slot * cells;
+    const T* Dg = reinterpret_cast<const T*>(a.hD) + (size_t)slot * cells;
+    T* ab = reinterpret_cast<T*>(a.AB);
+    const double psi_c = -sp.q * sp.dv[0];
+    for (size_t o = (size_t)blockIdx.x * blockDim.x + threadIdx.x; o < cells; o += (size_t)gridDim.x * blockDim.x) {
+        const double d = (double)Dg[o];
+        const double ps = psi_c * D->tmp[o % nx];
+        const bool ok = d > 0.0;
+        ab[2 * o] = ok ? (T)(ps / d) : (T)0;
+        ab[2 * o + 1] = ok ? (T)(ps * (double)F[o] / d) : (T)0;
+    }
+}
+
+// per marker: mu += sum A alpha, lambda update (see the file head)
 template <typename T>
 __global__ void k_ad_gather(const StepArgs* __restrict__ A, const AdjDev* __restrict__ D, int slot, int terminal)
 {
@@ -294,16 +351,13 @@ __global__ void k_ad_gather(const StepArgs* __restrict__ A, const AdjDev* __rest
     const SpDev& sp = A->sp[s];
     const AdjSp& a = D->sp[s];
     const int nx = sp.nx, nv = sp.nv[0];
-    const size_t cells = (size_t)nx * nv;
-    const T* F = reinterpret_cast<const T*>(a.hF) + (size_t)slot * cells;
-    const T* Dg = reinterpret_cast<const T*>(a.hD) + (size_t)slot * cells;
+    const T* ab = reinterpret_cast<const T*>(a.AB);
     const double* E = D->hE + (size_t)slot * nx;
     const T* vv = reinterpret_cast<const T*>(a.hv) + (size_t)slot * a.n;
     const T* f = reinterpret_cast<const T*>(a.f);
     T* lx = reinterpret_cast<T*>(a.lx);
     T* lv = reinterpret_cast<T*>(a.lv);
-    const double psi_c = -sp.q * sp.dv[0];   // psi = q dv P^T e = -q dv (P e)
-    const double idx_ = 1.0 / sp.dx, idv = sp.inv_dv[0];
+    const T idx_ = (T)(1.0 / sp.dx), idv = (T)sp.inv_dv[0];
     const double dt = sp.dt_dx * sp.dx;
     for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < a.n; k += (long long)gridDim.x * blockDim.x) {
         const Pos<T> p = APos<T>::load(a, slot, k);
@@ -312,40 +366,36 @@ __global__ void k_ad_gather(const StepArgs* __restrict__ A, const AdjDev* __rest
         p.cic(i0, wxT);
         int ia, ib;
         wrap_pair(i0, nx, ia, ib);
-        T wvT;
-        const int j0 = vrow(vv[k], sp, wvT);
-        const double wx = (double)wxT, wv = (double)wvT, fl = (double)f[k];
-        const double psa = psi_c * D->tmp[ia], psb = psi_c * D->tmp[ib];
-        double m = 0.0, gx = 0.0, gv = 0.0;
+        T wv;
+        const int j0 = vrow(vv[k], sp, wv);
+        const T wx = wxT, fl = f[k];
+        T m = 0, gx = 0, gv = 0;
 #pragma unroll
         for (int cv = 0; cv < 2; ++cv) {
             const int j = j0 + cv;
             if (j < 0 || j >= nv) continue;
-            const double av = cv ? wv : 1.0 - wv, dav = cv ? idv : -idv;
+            const T av = cv ? wv : (T)1 - wv, dav = cv ? idv : -idv;
 #pragma unroll
             for (int cx = 0; cx < 2; ++cx) {
                 const int i = cx ? ib : ia;
-                const double ax = cx ? wx : 1.0 - wx, dax = cx ? idx_ : -idx_;
+                const T ax = cx ? wx : (T)1 - wx, dax = cx ? idx_ : -idx_;
                 const size_t o = (size_t)j * nx + i;
-                const double d = (double)Dg[o];
-                if (!(d > 0.0)) continue;
-                const double ps = cx ? psb : psa;
-                const double Ac = ps / d, Bc = ps * (double)F[o] / d;
+                const T Ac = ab[2 * o], Bc = ab[2 * o + 1];
                 m += Ac * ax * av;
-                const double cc = Ac * fl - Bc;
+                const T cc = Ac * fl - Bc;
                 gx += cc * dax * av;
                 gv += cc * ax * dav;
             }
         }
-        a.mu[k] += m;
+        a.mu[k] += (double)m;
         if (terminal) {
             lx[k] = (T)gx;
             lv[k] = (T)gv;
         } else if (sp.mobile) {
             const double lt = (double)lv[k] + dt * (double)lx[k];
-            const double dEdx = (E[ib] - E[ia]) * idx_;
-            lx[k] = (T)((double)lx[k] + lt * sp.qm_dt * dEdx + gx);
-            lv[k] = (T)(lt + gv);
+            const double dEdx = (E[ib] - E[ia]) / sp.dx;
+            lx[k] = (T)((double)lx[k] + lt * sp.qm_dt * dEdx + (double)gx);
+            lv[k] = (T)(lt + (double)gv);
         }
     }
 }
@@ -411,6 +461,10 @@ struct AdjEngine {
     AdjDev h{};
     AdjDev* d = nullptr;
     avl_f0* d_f0 = nullptr;
+    // one full segment of K steps, forward (with pushes) and backward,
+    // recorded once and replayed for every full segment
+    cudaGraphExec_t g_fwd = nullptr, g_bwd = nullptr;
+    int g_K = 0, g_nact = -1;
 };
 
 static cudaError_t grab(AdjEngine* E, void** p, size_t bytes)
@@ -420,14 +474,29 @@ static cudaError_t grab(AdjEngine* E, void** p, size_t bytes)
     return e;
 }
 
+static void drop_graphs(AdjEngine* E)
+{
+    if (E->g_fwd) cudaGraphExecDestroy(E->g_fwd);
+    if (E->g_bwd) cudaGraphExecDestroy(E->g_bwd);
+    E->g_fwd = E->g_bwd = nullptr;
+}
+
 void adjoint_free(AdjEngine* E)
 {
     if (!E) return;
+    drop_graphs(E);
     for (void* p : E->mem) cudaFree(p);
     delete E;
 }
 
 static int grid_for(long long n) { return (int)std::max<long long>(1, std::min<long long>((n + 255) / 256, 152ll * 8)); }
+
+// row groups of the finalize so that it spreads over the SMs
+static int fin_groups(const AdjEngine* E)
+{
+    const int xb = (E->nx + 31) / 32;
+    return std::max(1, std::min(64, (2 * 152 + xb - 1) / xb));
+}
 
 static long long nmax_active(const AdjEngine* E)
 {
@@ -443,7 +512,7 @@ static cudaError_t recon_and_field(const StepArgs& h, const StepArgs* dA, AdjEng
     cudaError_t e = cudaMemcpyAsync(E->h.rho, E->h.rho_static, (size_t)E->nx * 8, cudaMemcpyDeviceToDevice, st);
     if (e) return e;
     k_ad_dep<T><<<dim3(grid_for(nmax_active(E)), E->h.nact), 256, 0, st>>>(dA, E->d, slot, 0);
-    k_ad_fin<T><<<dim3((E->nx + 31) / 32, E->h.nact), 256, 0, st>>>(dA, E->d, slot, 0);
+    k_ad_fin<T><<<dim3((E->nx + 31) / 32, E->h.nact, fin_groups(E)), 256, 0, st>>>(dA, E->d, slot, 0);
     if ((e = cudaGetLastError())) return e;
     return launch_poisson(E->h.rho, E->h.hE + (size_t)slot * E->nx, E->nx, h.fd.tw, h.fd.gmul, st);
 }
@@ -459,7 +528,7 @@ static cudaError_t static_charge(AdjEngine* E, const StepArgs* dA, cudaStream_t 
     std::swap(E->h.rho, E->h.rho_static);   // k_ad_fin adds into D->rho
     if ((e = cudaMemcpyAsync(E->d, &E->h, sizeof(AdjDev), cudaMemcpyHostToDevice, st))) return e;
     k_ad_dep<T><<<dim3(grid_for(nmax), E->h.nstat), 256, 0, st>>>(dA, E->d, 0, 1);
-    k_ad_fin<T><<<dim3((E->nx + 31) / 32, E->h.nstat), 256, 0, st>>>(dA, E->d, 0, 1);
+    k_ad_fin<T><<<dim3((E->nx + 31) / 32, E->h.nstat, fin_groups(E)), 256, 0, st>>>(dA, E->d, 0, 1);
     if ((e = cudaGetLastError())) return e;
     std::swap(E->h.rho, E->h.rho_static);
     return cudaMemcpyAsync(E->d, &E->h, sizeof(AdjDev), cudaMemcpyHostToDevice, st);
@@ -478,11 +547,76 @@ static cudaError_t back_step(const StepArgs& h, const StepArgs* dA, AdjEngine* E
     const long long nmax = nmax_active(E);
     cudaError_t e = cudaMemsetAsync(E->h.e, 0, (size_t)E->nx * 8, st);
     if (e) return e;
-    k_ad_e<T><<<dim3(grid_for(nmax), E->h.nact), 256, (size_t)E->nx * 8, st>>>(dA, E->d, slot, terminal);
+    const size_t copy_bytes = (size_t)E->nx * sizeof(typename EAcc<T>::type);
+    const int copies = (int)std::min<size_t>(8, (48 * 1024) / copy_bytes);
+    k_ad_e<T><<<dim3(grid_for(nmax), E->h.nact), 256, copies * copy_bytes, st>>>(dA, E->d, slot, terminal, copies);
     if ((e = cudaGetLastError())) return e;
     if ((e = launch_poisson(E->h.e, E->h.tmp, E->nx, h.fd.tw, h.fd.gmul, st))) return e;
+    k_ad_grid<T><<<dim3(152 * 2, E->h.nact), 256, 0, st>>>(dA, E->d, slot);
     k_ad_gather<T><<<dim3(grid_for(nmax), E->h.nact), 256, 0, st>>>(dA, E->d, slot, terminal);
     return cudaGetLastError();
+}
+
+template <typename T>
+static cudaError_t fwd_segment(const StepArgs& h, const StepArgs* dA, AdjEngine* E, int len, bool push_last,
+                               cudaStream_t st)
+{
+    cudaError_t e = cudaSuccess;
+    for (int j = 0; j < len && !e; ++j) {
+        e = recon_and_field<T>(h, dA, E, j, st);
+        if (!e && (push_last || j + 1 < len)) e = push_slot<T>(E, dA, j, st);
+    }
+    return e;
+}
+
+template <typename T>
+static cudaError_t bwd_segment(const StepArgs& h, const StepArgs* dA, AdjEngine* E, int len, cudaStream_t st)
+{
+    cudaError_t e = cudaSuccess;
+    for (int j = len - 1; j >= 0 && !e; --j) e = back_step<T>(h, dA, E, j, 0, st);
+    return e;
+}
+
+// record `body` (launches on st) as a graph and instantiate it
+template <typename F>
+static cudaError_t record(cudaStream_t st, cudaGraphExec_t* out, F body)
+{
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
+    if (e) return e;
+    cudaError_t eb = body();
+    e = cudaStreamEndCapture(st, &g);
+    if (eb || e) {
+        if (g) cudaGraphDestroy(g);
+        return eb ? eb : e;
+    }
+    e = cudaGraphInstantiate(out, g, 0);
+    cudaGraphDestroy(g);
+    return e;
+}
+
+// full segments replay the recorded graphs (kernel attributes are set by a
+// first direct launch before any recording)
+template <typename T>
+static cudaError_t full_fwd(const StepArgs& h, const StepArgs* dA, AdjEngine* E, bool push_last, cudaStream_t st)
+{
+    const int K = E->K;
+    if (!push_last) return fwd_segment<T>(h, dA, E, K, false, st);
+    if (!E->g_fwd) {
+        cudaError_t e = record(st, &E->g_fwd, [&] { return fwd_segment<T>(h, dA, E, K, true, st); });
+        if (e) return e;
+    }
+    return cudaGraphLaunch(E->g_fwd, st);
+}
+
+template <typename T>
+static cudaError_t full_bwd(const StepArgs& h, const StepArgs* dA, AdjEngine* E, cudaStream_t st)
+{
+    if (!E->g_bwd) {
+        cudaError_t e = record(st, &E->g_bwd, [&] { return bwd_segment<T>(h, dA, E, E->K, st); });
+        if (e) return e;
+    }
+    return cudaGraphLaunch(E->g_bwd, st);
 }
 
 // copy the state of slot a (positions, velocities) of every species into the
@@ -513,6 +647,11 @@ static cudaError_t run(const StepArgs& h, const StepArgs* dA, AdjEngine* E, int 
 {
     cudaError_t e;
     const int K = E->K;
+    if (E->g_K != K || E->g_nact != E->h.nact) {
+        drop_graphs(E);
+        E->g_K = K;
+        E->g_nact = E->h.nact;
+    }
     // initial state into slot 0
     for (int s = 0; s < E->ns; ++s) {
         k_ad_init<T><<<grid_for(E->n[s]), 256, 0, st>>>(dA, E->d, s);
@@ -526,9 +665,10 @@ static cudaError_t run(const StepArgs& h, const StepArgs* dA, AdjEngine* E, int 
     for (int c = 0; c < nseg; ++c) {
         const int len = std::min(K, nsteps - c * K);
         if ((e = ckpt_copy(E, c, 0, true, st))) return e;
-        for (int j = 0; j < len; ++j) {
-            if ((e = recon_and_field<T>(h, dA, E, j, st))) return e;
-            if ((e = push_slot<T>(E, dA, j, st))) return e;
+        if (len == K && c > 0) {
+            if ((e = full_fwd<T>(h, dA, E, true, st))) return e;
+        } else if ((e = fwd_segment<T>(h, dA, E, len, true, st))) {
+            return e;
         }
         last_len = len;
         if (c + 1 < nseg && (e = ckpt_copy(E, c + 1, len, true, st))) return e;
@@ -541,17 +681,12 @@ static cudaError_t run(const StepArgs& h, const StepArgs* dA, AdjEngine* E, int 
     if ((e = cudaMemcpyAsync(Ef.data(), E->h.hE + (size_t)last_len * E->nx, E->nx * 8, cudaMemcpyDeviceToHost, st)))
         return e;
     if ((e = back_step<T>(h, dA, E, last_len, 1, st))) return e;
-    for (int j = last_len - 1; j >= 0; --j)
-        if ((e = back_step<T>(h, dA, E, j, 0, st))) return e;
+    if ((e = bwd_segment<T>(h, dA, E, last_len, st))) return e;
     // earlier segments: recompute from the checkpoint, then walk back
     for (int c = nseg - 2; c >= 0; --c) {
         if ((e = ckpt_copy(E, c, 0, false, st))) return e;
-        for (int j = 0; j < K; ++j) {
-            if ((e = recon_and_field<T>(h, dA, E, j, st))) return e;
-            if (j + 1 < K && (e = push_slot<T>(E, dA, j, st))) return e;
-        }
-        for (int j = K - 1; j >= 0; --j)
-            if ((e = back_step<T>(h, dA, E, j, 0, st))) return e;
+        if ((e = full_fwd<T>(h, dA, E, true, st))) return e;
+        if ((e = full_bwd<T>(h, dA, E, st))) return e;
     }
     k_ad_theta<T><<<grid_for(E->n[E->h.theta_s]), 256, 0, st>>>(dA, E->d);
     if ((e = cudaGetLastError())) return e;
@@ -604,12 +739,12 @@ cudaError_t adjoint_run(AdjEngine** eng, const StepArgs& h, const StepArgs* dA, 
             g(&q.lx, n * pb);
             g(&q.lv, n * pb);
             g((void**)&q.mu, n * 8);
-            g(&q.num, cells * pb);
-            g(&q.den, cells * pb);
+            g(&q.num, 2 * cells * pb);
+            q.den = nullptr;
+            g(&q.AB, 2 * cells * pb);
             g(&q.hF, (K + 1) * cells * pb);
             g(&q.hD, (K + 1) * cells * pb);
-            if (!e) e = cudaMemsetAsync(q.num, 0, cells * pb, st);
-            if (!e) e = cudaMemsetAsync(q.den, 0, cells * pb, st);
+            if (!e) e = cudaMemsetAsync(q.num, 0, 2 * cells * pb, st);
         }
         g((void**)&E->h.rho, nx * 8);
         g((void**)&E->h.rho_static, nx * 8);

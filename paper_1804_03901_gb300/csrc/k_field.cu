@@ -168,7 +168,8 @@ __device__ void resort_work(const StepArgs* __restrict__ A, int rank)
             // CTA 0 is rewriting now); at a row or more, re-sort every step
             const int ssel = ctl->shsel[s];
             const int drift = max(abs(ctl->shift_min[s][ssel]), abs(ctl->shift_max[s][ssel]));
-            const bool resort = drift >= 1 || miss * 2000ull > (unsigned long long)sp.n;
+            const bool resort = (A->fd.resort_drift && drift >= 1) ||
+                                miss * (unsigned long long)A->fd.resort_miss > (unsigned long long)sp.n;
             if (threadIdx.x == 0) {
                 Ctl* cw = A->ctl;
                 cw->uncovered[s] = miss;
