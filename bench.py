@@ -57,6 +57,7 @@ def parse():
     p.add_argument("--workload", choices=["two_stream", "landau", "bump_on_tail", "two_stream_adjoint", "ensemble"],
                    default="two_stream")
     p.add_argument("--nrun", type=int, default=256, help="runs of the ensemble workload")
+    p.add_argument("--no-autotune", action="store_true", help="ensemble: keep the chunk-size heuristic")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--nv", type=int, default=0, help="velocity cells (profiling of a smaller case)")
@@ -499,7 +500,7 @@ def run_ensemble(args):
     init()
     nmark = sum(b.runs[i].marker_count(0) for i in range(len(w["runs"])))
     t_init = time.perf_counter() - t0
-    best_m = b.autotune(5)
+    best_m = 0 if args.no_autotune else b.autotune(5)
     init()                      # restart from t = 0 with the chosen chunk size
     b.step(max(3, args.warmup))
     b.synchronize()
