@@ -82,6 +82,8 @@ def lib():
         L.orc_poisson.argtypes = [C.c_int32, C.c_double, C.c_double, C.c_int32, dp, dp]
         L.orc_push.restype = None
         L.orc_push.argtypes = [gp, C.c_int64, dp, dp, C.c_double, C.c_double, dp]
+        L.orc_push_boris.restype = None
+        L.orc_push_boris.argtypes = [gp, C.c_int64, dp, dp, C.c_double, C.c_double, dp, dp]
         L.orc_diag.restype = None
         L.orc_diag.argtypes = [gp, C.c_double, dp, dp]
         L.orc_field_energy.restype = C.c_double
@@ -207,6 +209,16 @@ def push(nvdim, nx, L, sp: Species, x, v, dt, E):
                    _dp(np.ascontiguousarray(E, dtype=np.float64)))
 
 
+def push_boris(nx, L, sp: Species, x, v, dt, E, B):
+    """1d3v Boris push with background field B (3,), in place on x (n,) and
+    v (3, n)."""
+    g = make_grid(3, nx, L, sp)
+    assert x.dtype == np.float64 and v.dtype == np.float64 and v.flags.c_contiguous
+    Bv = np.ascontiguousarray(B, dtype=np.float64)
+    lib().orc_push_boris(C.byref(g), x.size, _dp(x), _dp(v), sp.q / sp.m, dt,
+                         _dp(np.ascontiguousarray(E, dtype=np.float64)), _dp(Bv))
+
+
 def diag(nvdim, nx, L, sp: Species, f):
     g = make_grid(nvdim, nx, L, sp)
     out = np.zeros(3)
@@ -261,6 +273,7 @@ class OracleSim:
         self.rho_s = [np.zeros(nx) for _ in self.species]
         self.rho = np.zeros(nx)
         self.E = np.zeros(nx)
+        self.B = np.zeros(3)     # background magnetic field (1d3v)
         self.nstep = 0
 
     def init_markers(self, s, lattice, f0: F0, seed, jitter=1.0):
@@ -300,7 +313,10 @@ class OracleSim:
         for _ in range(n):
             for s, sp in enumerate(self.species):
                 if sp.mobile and self.x[s] is not None:
-                    push(self.nvdim, self.nx, self.L, sp, self.x[s], self.v[s], self.dt, self.E)
+                    if self.nvdim == 3 and np.any(self.B != 0):
+                        push_boris(self.nx, self.L, sp, self.x[s], self.v[s], self.dt, self.E, self.B)
+                    else:
+                        push(self.nvdim, self.nx, self.L, sp, self.x[s], self.v[s], self.dt, self.E)
             for s, sp in enumerate(self.species):
                 if sp.mobile:
                     self._reconstruct(s)

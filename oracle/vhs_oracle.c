@@ -310,6 +310,45 @@ void orc_push(const orc_grid* g, int64_t n, double* x, double* v, double qm, dou
     }
 }
 
+/* Boris push (Boris 1970; Birdsall & Langdon Sec. 4-4): with a = (q/m) dt/2,
+ * v- = v + a E x_hat; t = a B; s = 2 t / (1 + |t|^2);
+ * v' = v- + v- x t;  v+ = v- + v' x s;  v_new = v+ + a E x_hat;
+ * x_new = x + v_new,x dt (periodic).  E is gathered with the cloud-in-cell
+ * weights of the reconstruction, as in orc_push.  v is component-major
+ * (v[d * n + l]). */
+void orc_push_boris(const orc_grid* g, int64_t n, double* x, double* v, double qm, double dt,
+                    const double* E, const double B[3])
+{
+    const double dx = g->L / g->nx;
+    const double a = 0.5 * qm * dt;
+    const double t[3] = {a * B[0], a * B[1], a * B[2]};
+    const double t2 = t[0] * t[0] + t[1] * t[1] + t[2] * t[2];
+    const double sf = 2.0 / (1.0 + t2);
+    const double s[3] = {sf * t[0], sf * t[1], sf * t[2]};
+    for (int64_t l = 0; l < n; ++l) {
+        int64_t i0;
+        double w;
+        cic1(x[l] / dx, &i0, &w);
+        int64_t ia = ((i0 % g->nx) + g->nx) % g->nx;
+        int64_t ib = (((i0 + 1) % g->nx) + g->nx) % g->nx;
+        double El = (1.0 - w) * E[ia] + w * E[ib];
+        double vm[3] = {v[l] + a * El, v[n + l], v[2 * n + l]};
+        double vp[3] = {vm[0] + (vm[1] * t[2] - vm[2] * t[1]), vm[1] + (vm[2] * t[0] - vm[0] * t[2]),
+                        vm[2] + (vm[0] * t[1] - vm[1] * t[0])};
+        double vq[3] = {vm[0] + (vp[1] * s[2] - vp[2] * s[1]), vm[1] + (vp[2] * s[0] - vp[0] * s[2]),
+                        vm[2] + (vp[0] * s[1] - vp[1] * s[0])};
+        double vx = vq[0] + a * El;
+        double xn = x[l] + vx * dt;
+        xn = fmod(xn, g->L);
+        if (xn < 0.0) xn += g->L;
+        if (xn >= g->L) xn -= g->L;
+        v[l] = vx;
+        v[n + l] = vq[1];
+        v[2 * n + l] = vq[2];
+        x[l] = xn;
+    }
+}
+
 /* Diagnostics of one species on its reconstructed grid (Sec. 3.4.1):
  * out[0] = N = sum f dx dv                       (number of particles)
  * out[1] = W_kin = m/2 sum |v_j|^2 f dx dv        (kinetic energy, cell centres)

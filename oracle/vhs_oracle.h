@@ -75,6 +75,14 @@ void orc_poisson(int32_t nx, double L, double cP, int32_t softening,
 void orc_push(const orc_grid* g, int64_t n, double* x, double* v, double qm, double dt,
               const double* E);
 
+/* Boris push with a static background magnetic field B[3] (1d3v; Sec. 3.2:
+ * the full Boris push for background magnetic fields): half kick by E along
+ * x, rotation about B by the Boris angle 2 atan(|q/m B dt/2|), half kick,
+ * then x += v_x dt wrapped into [0, L).  The force is q (E + v x B) in the
+ * normalised units of the library (B carries the factor 1/c of CGS). */
+void orc_push_boris(const orc_grid* g, int64_t n, double* x, double* v, double qm, double dt,
+                    const double* E, const double B[3]);
+
 void orc_diag(const orc_grid* g, double m, const double* f, double out[3]);
 double orc_field_energy(int32_t nx, double L, double cP, const double* E);
 

@@ -405,3 +405,67 @@ def test_field_residual_of_a_single_mode(softening):
     K2 = (2 * np.sin(k * dx / 2) / dx) ** 2 if softening else k * k
     expect = rho * (1 - kappa * np.sin(k * dx) / (dx * K2))
     np.testing.assert_allclose(O.field_residual(nx, L, cP, rho, E), expect, atol=1e-12)
+
+
+# --- Boris push with a background magnetic field (1d3v) -----------------------
+def _rodrigues(v, axis, ang):
+    k = axis / np.linalg.norm(axis)
+    return v * np.cos(ang) + np.cross(k, v) * np.sin(ang) + k * np.dot(k, v) * (1 - np.cos(ang))
+
+
+def _boris_sp():
+    return O.Species(q=-1.3, m=0.7, nv=(4, 4, 4), vmin=(-5.0,) * 3, vmax=(5.0,) * 3)
+
+
+def test_boris_pure_gyration_closed_form():
+    """E = 0: each step rotates v about B by the Boris angle 2 atan(|t|),
+    t = (q/m)(dt/2) B, in the sense of dv/dt = (q/m) v x B (about -sign(q/m) B);
+    after n steps v = R(n angle) v0, |v| and v . B unchanged."""
+    sp = _boris_sp()
+    nx, L, dt = 8, 3.0, 0.37
+    B = np.array([0.4, -1.1, 0.7])
+    qm = sp.q / sp.m
+    t = 0.5 * qm * dt * B
+    ang = 2 * np.arctan(np.linalg.norm(t))
+    v0 = np.array([[0.3], [1.2], [-0.8]])
+    x = np.array([1.0])
+    v = v0.copy()
+    E = np.zeros(nx)
+    for n in range(1, 41):
+        O.push_boris(nx, L, sp, x, v, dt, E, B)
+        expect = _rodrigues(v0[:, 0], -np.sign(qm) * B, n * ang)
+        np.testing.assert_allclose(v[:, 0], expect, rtol=0, atol=1e-13)
+    # free streaming along x with the rotating v_x
+    assert 0 <= x[0] < L
+
+
+def test_boris_exb_drift_is_a_fixed_point():
+    """Uniform E along x perpendicular to B: the drift velocity E x B / B^2
+    (force q (E + v x B) = 0) is left unchanged by every Boris step."""
+    sp = _boris_sp()
+    nx, L, dt = 8, 3.0, 0.2
+    E0 = 0.35
+    B = np.array([0.0, 0.6, -0.9])
+    vd = np.cross(np.array([E0, 0.0, 0.0]), B) / np.dot(B, B)
+    v = vd.reshape(3, 1).copy()
+    x = np.array([0.5])
+    E = np.full(nx, E0)
+    for _ in range(50):
+        O.push_boris(nx, L, sp, x, v, dt, E, B)
+        np.testing.assert_allclose(v[:, 0], vd, rtol=0, atol=1e-13)
+
+
+def test_boris_without_field_is_the_kick_push():
+    """B = 0: the Boris push is the kick-drift push of Sec. 2 (two half kicks)."""
+    sp = _boris_sp()
+    nx, L, dt = 16, 5.0, 0.1
+    rng = np.random.default_rng(4)
+    n = 50
+    x = rng.uniform(0, L, n)
+    v = rng.uniform(-3, 3, (3, n))
+    E = rng.normal(size=nx)
+    x2, v2 = x.copy(), v.copy()
+    O.push_boris(nx, L, sp, x, v, dt, E, np.zeros(3))
+    O.push(3, nx, L, sp, x2, v2, dt, E)
+    np.testing.assert_allclose(v, v2, rtol=0, atol=1e-14)
+    np.testing.assert_allclose(x, x2, rtol=0, atol=1e-12)
