@@ -61,12 +61,13 @@ typedef struct avl_ctx avl_ctx;
  *   and value in FP32, deposit sums compensated in FP32 (1d1v; 1d3v sums
  *   plain FP32); the Poisson solve, the charge-neutral k = 0 handling and
  *   the diagnostics stay FP64.
- * nvdim = 3 (Sec. 2 with three velocity dimensions, no magnetic field: the
- *   field accelerates v_x only) needs nx <= 1024 (FP32) or nx <= 512 (FP64),
- *   nv[0] in [2, 1024], nv[1], nv[2] in [2, 4096] and fewer than 2^31 grid
- *   cells; all species of a context share nvdim. */
+ * nvdim = 3 (Sec. 2 with three velocity dimensions: the field accelerates
+ *   v_x, an optional static background magnetic field, avl_set_bfield, turns
+ *   v) needs nx <= 1024 (FP32) or nx <= 512 (FP64), nv[0] in [2, 1024],
+ *   nv[1], nv[2] in [2, 4096] and fewer than 2^31 grid cells; all species of
+ *   a context share nvdim. */
 typedef struct {
-    int32_t nvdim;          /* 1 (1d1v) or 3 (1d3v, no magnetic field) */
+    int32_t nvdim;          /* 1 (1d1v) or 3 (1d3v) */
     int32_t nx;             /* cells in x, >= 4 */
     double L;               /* domain length */
     double dt;              /* time step */
@@ -147,6 +148,20 @@ avl_status avl_get_markers(avl_ctx* ctx, int32_t s, double* x, double* v, double
  * diagnostics of the new state.  Enqueued asynchronously (a CUDA graph per
  * step).  Errors: AVL_ESTATE if a mobile species has no markers. */
 avl_status avl_step(avl_ctx* ctx, int32_t nsteps);
+
+/* Static background magnetic field B = (B_x, B_y, B_z) of a 1d3v context
+ * (Sec. 3.2: the full Boris push of the 1d3v version; Sec. 3.3: the time step
+ * should resolve a gyration with at least 2 pi steps).  From the next step on,
+ * every mobile species is pushed by the Boris scheme: half kick by E_x at the
+ * marker's position, rotation of v about B by the angle 2 atan(|t|),
+ * t = (q/m)(dt/2) B, half kick, x += v_x dt; the force is q (E + v x B) in
+ * the library's units (CGS users pass B / c).  B = (0, 0, 0) returns to the
+ * field-free push.  A magnetized step pushes, re-sorts every marker by its
+ * (v_y, v_z, v_x) dual rows into the other buffer and then deposits, so it
+ * costs about three times a field-free step.  The stored state (markers, f,
+ * rho, E) is not changed by the call.  Errors: AVL_EINVAL (nvdim 1, B NULL or
+ * not finite). */
+avl_status avl_set_bfield(avl_ctx* ctx, const double* B);
 
 /* Reconstructed f of species s and, if n_opt is not NULL, the denominator of
  * Eq. 4 (sum of weights, the paper's "n" output, Sec. 3.4.3); FP64,
@@ -270,7 +285,9 @@ avl_status avl_autotune(avl_ctx* ctx, int32_t trial_steps, int32_t* chunk_out);
  * steps exactly as avl_step does, but launched kernel by kernel with CUDA
  * events recorded on the context stream around each kernel; writes the summed
  * milliseconds of each kernel class into ms[0..3] = {1d1v: key count + slot
- * scan, 1d3v: pencil re-sort; push + deposit (+ re-sorted write in 1d1v);
+ * scan, 1d3v: pencil re-sort (with a magnetic field: Boris push + global
+ * re-sort); push + deposit (+ re-sorted write in 1d1v; deposit only in a
+ * magnetized 1d3v step);
  * finalize (f, moment, diagnostics); field (Poisson)}.  Blocks until done.
  * Errors: AVL_EINVAL (nkernels < 4 or ms NULL), AVL_ESTATE as avl_step. */
 avl_status avl_profile_steps(avl_ctx* ctx, int32_t nsteps, double* ms, int32_t nkernels);

@@ -27,7 +27,7 @@ EXPORTED = ["avl_create", "avl_destroy", "avl_last_error", "avl_init_markers", "
             "avl_marker_count", "avl_get_markers", "avl_step", "avl_get_f", "avl_get_rho",
             "avl_get_E", "avl_get_diag", "avl_get_stats", "avl_field_solve", "avl_field_solve_noalloc",
             "avl_profile_steps", "avl_adjoint", "avl_create_batch", "avl_batch_run", "avl_autotune",
-            "avl_get_moments", "avl_get_residual",
+            "avl_get_moments", "avl_get_residual", "avl_set_bfield",
             "avl_synchronize"]
 
 
@@ -85,6 +85,7 @@ def _load():
         "avl_autotune": (C.c_int, [vp, C.c_int32, C.POINTER(C.c_int32)]),
         "avl_get_moments": (C.c_int, [vp, C.c_int32, vp, C.c_int32]),
         "avl_get_residual": (C.c_int, [vp, vp, C.c_int32]),
+        "avl_set_bfield": (C.c_int, [vp, vp]),
         "avl_synchronize": (C.c_int, [vp]),
     }
     for name, (res, args) in sig.items():
@@ -119,6 +120,7 @@ avl_batch_run = lib.avl_batch_run
 avl_autotune = lib.avl_autotune
 avl_get_moments = lib.avl_get_moments
 avl_get_residual = lib.avl_get_residual
+avl_set_bfield = lib.avl_set_bfield
 avl_synchronize = lib.avl_synchronize
 
 
@@ -256,6 +258,12 @@ class Simulation:
         out = np.zeros((2 + self.nvdim, self.nx))
         self._chk(avl_get_moments(self.ctx, s, out.ctypes.data, 0))
         return out
+
+    def set_bfield(self, B):
+        """Static background magnetic field (B_x, B_y, B_z) of a 1d3v run: the
+        following steps use the Boris push."""
+        b = np.ascontiguousarray(B, dtype=np.float64).reshape(3)
+        self._chk(avl_set_bfield(self.ctx, b.ctypes.data))
 
     def get_residual(self):
         out = np.zeros(self.nx)

@@ -271,12 +271,13 @@ avl_status plan_layout3(avl_ctx* c, int s, long long n)
         sp.seg[b] = (int*)sg;
     }
     void* kc = nullptr;
-    if (!e) e = grab(&kc, ((size_t)npen * nkey + 1) * 4, true);
+    if (!e) e = grab(&kc, (2 * (size_t)npen * nkey + 1) * 4, true);
     if (e) {
         free_layout(c, s);
         return cuda_fail(c, e, "cudaMalloc(markers)");
     }
     sp.kcount = (int*)kc;
+    sp.kcur = (int*)kc + (size_t)npen * nkey;
     sp.npen = npen;
     sp.nkey = nkey;
     sp.n = n;
@@ -355,9 +356,29 @@ avl_status refresh(avl_ctx* c)
 // slots for the next step
 avl_status enqueue_batch_step(avl_ctx* b);
 
+// 1d3v with a magnetic field: Boris push of every mobile species, then the
+// global (pencil, key) re-sort into the other buffer
+cudaError_t launch_magnetized_push(avl_ctx* c)
+{
+    cudaError_t e = cudaSuccess;
+    for (int s = 0; s < c->ns && !e; ++s) {
+        if (!c->h.sp[s].mobile) continue;
+        e = launch_bpush3(c->h, c->d_args, s, c->st);
+        if (!e) e = launch_rsort3(c->h, c->d_args, s, c->st);
+    }
+    return e;
+}
+
 avl_status enqueue_step(avl_ctx* c)
 {
     if (!c->runs.empty()) return enqueue_batch_step(c);
+    if (c->h.nvdim == 3 && c->h.fd.magnetized) {
+        AVL_CUDA(c, launch_magnetized_push(c));
+        AVL_CUDA(c, launch_pd3(c->h, c->d_args, 2, c->st));
+        AVL_CUDA(c, launch_fin3(c->h, c->d_args, 0, c->st));
+        AVL_CUDA(c, launch_field(c->h, c->d_args, 1, c->st));
+        return AVL_OK;
+    }
     if (c->h.nvdim == 3) {
         AVL_CUDA(c, launch_pd3(c->h, c->d_args, 1, c->st));
         AVL_CUDA(c, launch_fin3(c->h, c->d_args, 0, c->st));
@@ -930,6 +951,24 @@ avl_status avl_step(avl_ctx* c, int32_t nsteps)
     return AVL_OK;
 }
 
+avl_status avl_set_bfield(avl_ctx* c, const double* B)
+{
+    if (!c) return AVL_EINVAL;
+    if (c->h.nvdim != 3) return fail(c, AVL_EINVAL, "a magnetic field needs nvdim = 3");
+    if (!B) return fail(c, AVL_EINVAL, "B is NULL");
+    for (int d = 0; d < 3; ++d)
+        if (!isfinite(B[d])) return fail(c, AVL_EINVAL, "B must be finite");
+    AVL_CUDA(c, cudaStreamSynchronize(c->st));
+    FieldDev& fd = c->h.fd;
+    for (int d = 0; d < 3; ++d) fd.B[d] = B[d];
+    fd.magnetized = (B[0] != 0.0 || B[1] != 0.0 || B[2] != 0.0) ? 1 : 0;
+    if (c->gexec) {
+        cudaGraphExecDestroy(c->gexec);
+        c->gexec = nullptr;
+    }
+    return upload_args(c);
+}
+
 avl_status avl_get_f(avl_ctx* c, int32_t s, double* f, double* n_opt, int32_t on_device)
 {
     avl_status st = check_species(c, s);
@@ -1062,13 +1101,13 @@ avl_status avl_profile_steps(avl_ctx* c, int32_t nsteps, double* ms, int32_t nke
     double acc[4] = {0, 0, 0, 0};
     avl_status st = AVL_OK;
     for (int i = 0; i < nsteps && st == AVL_OK; ++i) {
-        const bool d3 = c->h.nvdim == 3;
+        const bool d3 = c->h.nvdim == 3, mag = d3 && c->h.fd.magnetized;
         cudaError_t e = cudaEventRecord(ev[0], c->st);
-        if (!e && d3) e = launch_sort3(c->h, c->d_args, c->st);
+        if (!e && d3) e = mag ? launch_magnetized_push(c) : launch_sort3(c->h, c->d_args, c->st);
         if (!e) e = cudaEventRecord(ev[1], c->st);
         if (!e)
             e = batch ? launch_pd1_batch(c->h.prec, bm, c->bm_pd_blocks, c->bm_pd_smem, 1, c->st)
-                : d3  ? launch_pd3(c->h, c->d_args, 1, c->st)
+                : d3  ? launch_pd3(c->h, c->d_args, mag ? 2 : 1, c->st)
                       : launch_pd1(c->h, c->d_args, 1, c->st);
         if (!e) e = cudaEventRecord(ev[2], c->st);
         if (!e)

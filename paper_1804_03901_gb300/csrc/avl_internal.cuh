@@ -17,13 +17,15 @@
 //   Window partial sums of chunk c: [nchunk][planes][Wmax][nx] covering the
 //   velocity rows [wrow0[c], wrow0[c] + Wmax).
 //
-// HBM layout of one species (1d3v, no magnetic field: v_y, v_z never change):
+// HBM layout of one species (1d3v):
 //   markers as above plus v_y, v_z (FP32: cell, off, vx, vy, vz, f = 24 B);
 //   velocities are absolute.  Sorted by pencil p = (jz + 1)(nvy + 1) + jy + 1
 //   (jy, jz: dual rows of v_y, v_z, clamped to [-1, nv - 1]) and inside a
 //   pencil by key k = jx + 1 (dual row of v_x, clamped likewise): seg[b][p][k]
 //   is the first marker of key k of pencil p in buffer b, seg[b][p][nkey] the
-//   end of the pencil.  A pencil's range is the same in both buffers.
+//   end of the pencil.  Without a magnetic field v_y and v_z never change, so
+//   a pencil's range is the same in both buffers; with one, every step re-sorts
+//   the whole species by (pencil, key) into the other buffer.
 //   Grids are stored [vz][vy][vx][x] (x fastest); acc[a] holds the numerator
 //   and then the denominator of Eq. 4 for the deposit into accumulator a.
 #pragma once
@@ -104,7 +106,8 @@ struct SpDev {
     int* seg[2];               // [npen][nkey + 1] first marker of every key, per buffer
     void* acc[2];              // [2][nvflat][nx] numerator, denominator of the deposit
     void* v2row;               // [nvflat] |v|^2 at the centre of every velocity cell
-    int* kcount;               // [npen * nkey + 1] creation scratch (counts, then cursors)
+    int* kcount;               // [npen * nkey] bucket counts (zero between operations)
+    int* kcur;                 // [npen * nkey] slot cursors of a creation or global re-sort
 };
 
 struct FieldDev {
@@ -118,6 +121,8 @@ struct FieldDev {
     const double2* tw;         // exp(-2 pi i k / nx), k < nx
     const double* gmul;        // cP kappa / K^2 for m <= nx/2 (0 at m = 0 and Nyquist)
     double* diag;              // 3 + 3 ns
+    double B[3];               // 1d3v: static background magnetic field (Boris push)
+    int magnetized;            // B != 0 (1d3v): push, global re-sort, deposit
 };
 
 struct Ctl {
@@ -204,12 +209,18 @@ cudaError_t launch_get1(const StepArgs& h, const StepArgs* d, int s, double* x, 
                         double* f, cudaStream_t st);
 cudaError_t launch_getf(const StepArgs& h, int s, double* f, double* n, cudaStream_t st);
 
-// 1d3v (k_vhs3.cu).  launch_pd3 mode as launch_pd1; launch_sort3 re-sorts the
-// pencils of the species the field kernel marked (a no-op otherwise)
+// 1d3v (k_vhs3.cu).  launch_pd3 mode as launch_pd1, and 2 = deposit only,
+// mobile species (after a magnetized push and re-sort); launch_sort3 re-sorts
+// the pencils of the species the field kernel marked (a no-op otherwise).
+// launch_bpush3: Boris push of species s in place, counting the new buckets;
+// launch_rsort3: the counted markers of species s re-sorted by (pencil, key)
+// into the other buffer, which becomes current.
 cudaError_t configure_vhs3(const StepArgs& h);
 cudaError_t launch_pd3(const StepArgs& h, const StepArgs* d, int mode, cudaStream_t st);
 cudaError_t launch_fin3(const StepArgs& h, const StepArgs* d, int all_species, cudaStream_t st);
 cudaError_t launch_sort3(const StepArgs& h, const StepArgs* d, cudaStream_t st);
+cudaError_t launch_bpush3(const StepArgs& h, const StepArgs* d, int s, cudaStream_t st);
+cudaError_t launch_rsort3(const StepArgs& h, const StepArgs* d, int s, cudaStream_t st);
 cudaError_t launch_init3(const StepArgs& h, const StepArgs* d, int s, const int lattice[4],
                          const avl_f0* f0_dev, unsigned long long seed, double jitter,
                          cudaStream_t st);

@@ -1,11 +1,11 @@
 // k_vhs3.cu -- 1d3v kernels of the Vlasov-Hybrid time step (Fig. 2; Sec. 2
-// with three velocity dimensions and no magnetic field, so that the field
-// changes v_x only and v_y, v_z ride along unchanged).
+// with three velocity dimensions).
 //
-// Layout: markers sorted by pencil (the dual rows of v_y and v_z, fixed for
-// the life of a marker) and inside a pencil by key (dual row of v_x + 1).
-// One CTA owns one pencil and walks its keys in order; per segment (the
-// markers stored under one key):
+// Without a magnetic field the field changes v_x only and v_y, v_z ride
+// along unchanged.  Layout: markers sorted by pencil (the dual rows of v_y and
+// v_z, fixed for the life of a marker) and inside a pencil by key (dual row
+// of v_x + 1).  One CTA owns one pencil and walks its keys in order; per
+// segment (the markers stored under one key):
 //   push    gather E (cloud-in-cell, Sec. 2), v_x += (q/m) E dt, x += v_x dt,
 //           written back in place
 //   sort    the markers whose new key is still the segment's key ("stays")
@@ -21,6 +21,13 @@
 // counts decide the next re-sort (k_sort3, per pencil, into the other
 // buffer).  k_fin3 forms f = num / den, the moment (Eq. 14) and the
 // diagnostics (Sec. 3.4.1) and clears the other accumulator.
+//
+// With a static background magnetic field (Sec. 3.2: the Boris push of the
+// 1d3v version) every velocity component turns, so a marker's pencil changes
+// from step to step.  The step is then: Boris push in place with the count of
+// every marker's new (pencil, key) bucket (k_bpush3), a global counting sort
+// into the other buffer (k_src3_scan, k_rs3_scatter), and the pencil deposit
+// above without a push (k_pd3 mode 2), in which no marker is off its segment.
 #include <math.h>
 
 #include <algorithm>
@@ -280,7 +287,8 @@ __device__ __forceinline__ void chunk_scan(int* hist, int* start, int nx, int* w
 }
 
 // mode 0: deposit of the current markers of every species (refresh);
-// mode 1: push of the mobile species, then deposit of the new state
+// mode 1: push of the mobile species, then deposit of the new state;
+// mode 2: deposit of the mobile species (pushed and re-sorted before)
 template <typename T, int CPT>
 __global__ void __launch_bounds__(P3_THREADS, (sizeof(T) == 4 && CPT == 1) ? 2 : 1)
     k_pd3(const StepArgs* __restrict__ A, int mode)
@@ -301,7 +309,7 @@ __global__ void __launch_bounds__(P3_THREADS, (sizeof(T) == 4 && CPT == 1) ? 2 :
     const int s = species_of_pen(A, g);
     const SpDev& sp = A->sp[s];
     const bool push = mode == 1;
-    if (push && !sp.mobile) return;
+    if (mode != 0 && !sp.mobile) return;
     Ctl* ctl = A->ctl;
     const int p = g - sp.pen_base;
     const int nx = sp.nx, nvx = sp.nv[0], nvy = sp.nv[1], nvz = sp.nv[2], nkey = sp.nkey;
@@ -866,16 +874,25 @@ __global__ void __launch_bounds__(256) k_src3_count(const StepArgs* __restrict__
     if (nbad && bad) atomicAdd(bad, (unsigned long long)nbad);
 }
 
-// exclusive scan of the bucket counts (one block) -> cursors and seg[0]
-__global__ void __launch_bounds__(1024) k_src3_scan(const StepArgs* __restrict__ A, int s)
+// exclusive scan of the bucket counts (one block) -> slot cursors kcur and
+// the segment table of the target buffer; the counts are cleared for the
+// next use.  Creation (resort = 0) fills buffer 0; a global re-sort
+// (resort = 1) fills the other buffer and makes it current, so that the
+// scatter reads buffer 1 - cur and writes buffer cur.
+__global__ void __launch_bounds__(1024) k_src3_scan(const StepArgs* __restrict__ A, int s, int resort)
 {
     __shared__ int warp_sums[32];
-    __shared__ int carry;
+    __shared__ int carry, dst_s;
     const SpDev& sp = A->sp[s];
     const int nb = sp.npen * sp.nkey;
     int* c = sp.kcount;
-    if (threadIdx.x == 0) carry = 0;
+    int* cur = sp.kcur;
+    if (threadIdx.x == 0) {
+        carry = 0;
+        dst_s = resort ? 1 - A->ctl->cur[s] : 0;
+    }
     __syncthreads();
+    const int dst = dst_s;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     for (int b0 = 0; b0 < nb; b0 += blockDim.x) {
         const int i = b0 + threadIdx.x;
@@ -897,17 +914,26 @@ __global__ void __launch_bounds__(1024) k_src3_scan(const StepArgs* __restrict__
         }
         __syncthreads();
         const int incl = x + (warp > 0 ? warp_sums[warp - 1] : 0) + carry;
-        if (i < nb) c[i] = incl - v;
+        if (i < nb) {
+            cur[i] = incl - v;
+            c[i] = 0;
+        }
         __syncthreads();
         if (threadIdx.x == blockDim.x - 1) carry = incl;
         __syncthreads();
     }
     const int total = carry;
     const int nk = sp.nkey;
+    int* sg = sp.seg[dst];
     for (int i = threadIdx.x; i < sp.npen * (nk + 1); i += blockDim.x) {
         const int p = i / (nk + 1), k = i % (nk + 1);
         const int b = p * nk + k;   // k == nk: first bucket of the next pencil
-        sp.seg[0][i] = b < nb ? c[b] : total;
+        sg[i] = b < nb ? cur[b] : total;
+    }
+    if (resort && threadIdx.x == 0) {
+        if ((long long)total != sp.n) atomicOr(&A->ctl->err, ERR_CAPACITY);
+        A->ctl->cur[s] = dst;
+        A->ctl->nsort[s] += 1;
     }
 }
 
@@ -930,7 +956,7 @@ __global__ void __launch_bounds__(256) k_src3_scatter(const StepArgs* __restrict
             for (int d = 0; d < 3; ++d) v[d] = (T)mk.v[d];
             b = bucket3<T>(sp, vc, v);
         }
-        const int slot = warp_slot(sp.kcount, b, ok);
+        const int slot = warp_slot(sp.kcur, b, ok);
         if (!ok) continue;
         if (slot < 0 || (long long)slot >= sp.n) {
             over = true;
@@ -940,6 +966,122 @@ __global__ void __launch_bounds__(256) k_src3_scatter(const StepArgs* __restrict
         pos.store(sp, 0, slot);
         for (int d = 0; d < 3; ++d) reinterpret_cast<T*>(sp.mv[0][d])[slot] = v[d];
         reinterpret_cast<T*>(sp.mf[0])[slot] = (T)mk.f;
+    }
+    if (over) atomicOr(&A->ctl->err, ERR_CAPACITY);
+}
+
+// ---------------------------------------------------------------------------
+// static background magnetic field: Boris push and global re-sort
+// ---------------------------------------------------------------------------
+// Boris coefficients of a species (storage precision): a = (q/m) dt / 2,
+// t = a B (tangent of half the rotation angle along B), s = 2 t / (1 + |t|^2)
+template <typename T>
+struct BorisCoef {
+    T a, t[3], s[3];
+    __device__ __forceinline__ void init(const SpDev& sp, const double (&B)[3])
+    {
+        const double a2 = 0.5 * sp.qm_dt;
+        double tt[3], t2 = 0.0;
+        for (int d = 0; d < 3; ++d) {
+            tt[d] = a2 * B[d];
+            t2 += tt[d] * tt[d];
+        }
+        const double f = 2.0 / (1.0 + t2);
+        a = (T)a2;
+        for (int d = 0; d < 3; ++d) {
+            t[d] = (T)tt[d];
+            s[d] = (T)(f * tt[d]);
+        }
+    }
+};
+
+// Boris push of every marker of species s in buffer cur, written back in
+// place: half kick by E_x at the old position, rotation v- -> v+ about B,
+// half kick, x += v_x dt.  The (pencil, key) bucket of the new velocities,
+// computed from the stored values exactly as the scatter recomputes it, is
+// counted into kcount (one atomic per distinct bucket of a warp).
+template <typename T>
+__global__ void __launch_bounds__(256) k_bpush3(const StepArgs* __restrict__ A, int s)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    T* Es = reinterpret_cast<T*>(smem);
+    const SpDev& sp = A->sp[s];
+    const int cb = A->ctl->cur[s];
+    const int nx = sp.nx;
+    for (int i = threadIdx.x; i < nx; i += blockDim.x)
+        Es[i] = sizeof(T) == 4 ? (T)A->fd.E32[i] : (T)A->fd.E64[i];
+    __syncthreads();
+    BorisCoef<T> bc;
+    bc.init(sp, A->fd.B);
+    VCoef<T> vc;
+    vc.init(sp);
+    const T dt_dx = (T)sp.dt_dx;
+    T* const g0 = reinterpret_cast<T*>(sp.mv[cb][0]);
+    T* const g1 = reinterpret_cast<T*>(sp.mv[cb][1]);
+    T* const g2 = reinterpret_cast<T*>(sp.mv[cb][2]);
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    const long long n_pad = (sp.n + 31) / 32 * 32;
+    for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < n_pad; k += stride) {
+        const bool ok = k < sp.n;
+        int b = 0;
+        if (ok) {
+            Pos<T> pos;
+            pos.load(sp, cb, (int)k);
+            int i0, ia, ib;
+            T wx;
+            pos.cic(i0, wx);
+            wrap_pair(i0, nx, ia, ib);
+            const T aE = bc.a * (((T)1 - wx) * Es[ia] + wx * Es[ib]);
+            const T m0 = g0[k] + aE, m1 = g1[k], m2 = g2[k];
+            const T p0 = m0 + (m1 * bc.t[2] - m2 * bc.t[1]);
+            const T p1 = m1 + (m2 * bc.t[0] - m0 * bc.t[2]);
+            const T p2 = m2 + (m0 * bc.t[1] - m1 * bc.t[0]);
+            const T v[3] = {m0 + (p1 * bc.s[2] - p2 * bc.s[1]) + aE, m1 + (p2 * bc.s[0] - p0 * bc.s[2]),
+                            m2 + (p0 * bc.s[1] - p1 * bc.s[0])};
+            pos.drift(v[0] * dt_dx, nx);
+            pos.store(sp, cb, (int)k);
+            g0[k] = v[0];
+            g1[k] = v[1];
+            g2[k] = v[2];
+            b = bucket3<T>(sp, vc, v);
+        }
+        const int kk = ok ? b : -1;
+        const unsigned grp = __match_any_sync(0xffffffffu, kk);
+        if (ok && (threadIdx.x & 31) == __ffs(grp) - 1) atomicAdd(&sp.kcount[b], __popc(grp));
+    }
+}
+
+// the markers of species s from buffer 1 - cur into their (pencil, key)
+// buckets of buffer cur (k_src3_scan has placed the cursors and flipped cur)
+template <typename T>
+__global__ void __launch_bounds__(256) k_rs3_scatter(const StepArgs* __restrict__ A, int s)
+{
+    const SpDev& sp = A->sp[s];
+    const int dst = A->ctl->cur[s], src = 1 - dst;
+    VCoef<T> vc;
+    vc.init(sp);
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    const long long n_pad = (sp.n + 31) / 32 * 32;
+    bool over = false;
+    for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < n_pad; k += stride) {
+        const bool ok = k < sp.n;
+        T v[3] = {(T)0, (T)0, (T)0};
+        int b = 0;
+        if (ok) {
+            for (int d = 0; d < 3; ++d) v[d] = reinterpret_cast<const T*>(sp.mv[src][d])[k];
+            b = bucket3<T>(sp, vc, v);
+        }
+        const int slot = warp_slot(sp.kcur, b, ok);
+        if (!ok) continue;
+        if (slot < 0 || (long long)slot >= sp.n) {
+            over = true;
+            continue;
+        }
+        Pos<T> pos;
+        pos.load(sp, src, (int)k);
+        pos.store(sp, dst, slot);
+        for (int d = 0; d < 3; ++d) reinterpret_cast<T*>(sp.mv[dst][d])[slot] = v[d];
+        reinterpret_cast<T*>(sp.mf[dst])[slot] = reinterpret_cast<const T*>(sp.mf[src])[k];
     }
     if (over) atomicOr(&A->ctl->err, ERR_CAPACITY);
 }
@@ -1057,7 +1199,7 @@ cudaError_t launch_sort3(const StepArgs& h, const StepArgs* d, cudaStream_t st)
     return cudaGetLastError();
 }
 
-// source -> layout in buffer 0 (kcount must be zero; the caller clears it)
+// source -> layout in buffer 0 (kcount is zero before and after)
 template <typename Src>
 static cudaError_t source_to_layout3(const StepArgs& h, const StepArgs* d, int s, Src src, unsigned long long* bad,
                                      cudaStream_t st)
@@ -1066,11 +1208,11 @@ static cudaError_t source_to_layout3(const StepArgs& h, const StepArgs* d, int s
     const int blocks = (int)std::max<long long>(1, std::min<long long>((n + 255) / 256, 152ll * 16));
     if (h.prec == AVL_FP32) {
         k_src3_count<float, Src><<<blocks, 256, 0, st>>>(d, s, src, bad);
-        k_src3_scan<<<1, 1024, 0, st>>>(d, s);
+        k_src3_scan<<<1, 1024, 0, st>>>(d, s, 0);
         k_src3_scatter<float, Src><<<blocks, 256, 0, st>>>(d, s, src);
     } else {
         k_src3_count<double, Src><<<blocks, 256, 0, st>>>(d, s, src, bad);
-        k_src3_scan<<<1, 1024, 0, st>>>(d, s);
+        k_src3_scan<<<1, 1024, 0, st>>>(d, s, 0);
         k_src3_scatter<double, Src><<<blocks, 256, 0, st>>>(d, s, src);
     }
     return cudaGetLastError();
@@ -1088,6 +1230,36 @@ cudaError_t launch_set3(const StepArgs& h, const StepArgs* d, int s, long long n
 {
     const ArraySrc3 src{x, v, f, n};
     return source_to_layout3(h, d, s, src, bad, st);
+}
+
+static int marker_blocks(long long n)
+{
+    return (int)std::max<long long>(1, std::min<long long>((n + 255) / 256, 152ll * 16));
+}
+
+cudaError_t launch_bpush3(const StepArgs& h, const StepArgs* d, int s, cudaStream_t st)
+{
+    const long long n = h.sp[s].n;
+    if (n == 0) return cudaSuccess;
+    const int blocks = marker_blocks(n);
+    if (h.prec == AVL_FP32)
+        k_bpush3<float><<<blocks, 256, (size_t)h.sp[s].nx * 4, st>>>(d, s);
+    else
+        k_bpush3<double><<<blocks, 256, (size_t)h.sp[s].nx * 8, st>>>(d, s);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rsort3(const StepArgs& h, const StepArgs* d, int s, cudaStream_t st)
+{
+    const long long n = h.sp[s].n;
+    if (n == 0) return cudaSuccess;
+    const int blocks = marker_blocks(n);
+    k_src3_scan<<<1, 1024, 0, st>>>(d, s, 1);
+    if (h.prec == AVL_FP32)
+        k_rs3_scatter<float><<<blocks, 256, 0, st>>>(d, s);
+    else
+        k_rs3_scatter<double><<<blocks, 256, 0, st>>>(d, s);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_get3(const StepArgs& h, const StepArgs* d, int s, double* x, double* v, double* f, cudaStream_t st)
