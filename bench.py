@@ -36,16 +36,22 @@ sys.path.insert(0, ROOT)
 # per velocity dimension: kernel classes of avl_profile_steps, launches per
 # step, algorithmic bytes per marker of the push + deposit kernel (read x,
 # v, f and write x, v_x) and the bytes of the stored layout it moves
+# ("3B": 1d3v with a magnetic field, whose push + deposit kernel deposits only)
 KERNEL_NAMES = {1: ["k_count1", "k_pd1", "k_fin1", "k_field"],
-                3: ["k_sort3", "k_pd3", "k_fin3", "k_field"]}
-LAUNCHES_PER_STEP = {1: 4,   # k_pd1 (in place and re-sorting instances), k_fin1, k_field
-                     3: 4}   # k_pd3, k_fin3, k_field, k_sort3
+                3: ["k_sort3", "k_pd3", "k_fin3", "k_field"],
+                "3B": ["k_bpush3 + k_src3_scan + k_rs3_scatter", "k_pd3", "k_fin3", "k_field"]}
+LAUNCHES_PER_STEP = {1: 4,     # k_pd1 (in place and re-sorting instances), k_fin1, k_field
+                     3: 4,     # k_pd3, k_fin3, k_field, k_sort3
+                     "3B": 6}  # k_bpush3, k_src3_scan, k_rs3_scatter (one mobile species), k_pd3, k_fin3, k_field
 BYTES_PER_MARKER_ALGO = {(1, "fp32"): 20.0, (1, "fp64"): 40.0,    # 1d1v: read x, v, f; write x, v
-                         (3, "fp32"): 28.0, (3, "fp64"): 56.0}    # 1d3v: read x, vx, vy, vz, f; write x, vx
+                         (3, "fp32"): 28.0, (3, "fp64"): 56.0,    # 1d3v: read x, vx, vy, vz, f; write x, vx
+                         ("3B", "fp32"): 24.0, ("3B", "fp64"): 40.0}   # deposit only: read x, v, f
 BYTES_PER_MARKER_LAYOUT = {(1, "fp32"): 32.0, (1, "fp64"): 48.0,  # read and re-sorted write of all fields
-                           (3, "fp32"): 36.0, (3, "fp64"): 64.0}  # read all fields, write cell, off, vx in place
+                           (3, "fp32"): 36.0, (3, "fp64"): 64.0,  # read all fields, write cell, off, vx in place
+                           ("3B", "fp32"): 24.0, ("3B", "fp64"): 40.0}
 KERNEL_DESC = {1: "k_pd1 (gather + push + VHS deposit + re-sorted write)",
-               3: "k_pd3 (gather + push + x-sorted VHS deposit per pencil, in place)"}
+               3: "k_pd3 (gather + push + x-sorted VHS deposit per pencil, in place)",
+               "3B": "k_pd3 mode 2 (x-sorted VHS deposit per pencil of the Boris-pushed, re-sorted markers)"}
 
 
 def parse():
@@ -54,7 +60,8 @@ def parse():
     p.add_argument("--steps", type=int, default=2000)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    p.add_argument("--workload", choices=["two_stream", "landau", "bump_on_tail", "two_stream_adjoint", "ensemble"],
+    p.add_argument("--workload", choices=["two_stream", "landau", "bump_on_tail", "bernstein", "two_stream_adjoint",
+                                          "ensemble"],
                    default="two_stream")
     p.add_argument("--nrun", type=int, default=256, help="runs of the ensemble workload")
     p.add_argument("--no-autotune", action="store_true", help="ensemble: keep the chunk-size heuristic")
@@ -76,6 +83,8 @@ def workload(name, nv=0, amp=0.0):
         return inputs.two_stream(**kw)
     if name == "bump_on_tail":
         return inputs.bump_on_tail(nv=nv) if nv else inputs.bump_on_tail()
+    if name == "bernstein":
+        return inputs.bernstein(nv=nv) if nv else inputs.bernstein()
     if name == "two_stream_adjoint":
         return inputs.two_stream_adjoint(nv=nv) if nv else inputs.two_stream_adjoint()
     if name == "ensemble":
@@ -83,7 +92,8 @@ def workload(name, nv=0, amp=0.0):
     return inputs.landau(nv=nv) if nv else inputs.landau()
 
 
-SAMPLE_FRACTION = {"two_stream": 1.0 / 64, "bump_on_tail": 1.0 / 256, "landau": 1.0, "two_stream_adjoint": 1.0 / 16}
+SAMPLE_FRACTION = {"two_stream": 1.0 / 64, "bump_on_tail": 1.0 / 256, "bernstein": 1.0 / 256, "landau": 1.0,
+                   "two_stream_adjoint": 1.0 / 16}
 
 
 def markers_of(w):
@@ -185,6 +195,8 @@ def build_sim(A, w, stream, seed_offset=0):
     dom = A.make_domain(w["nvdim"], w["nx"], w["L"], w["dt"], 1.0, True, prec)
     sim = A.Simulation(dom, [A.make_species(**sp) for sp in w["species"]], stream=stream)
     init_markers(A, sim, w, seed_offset)
+    if "B" in w:
+        sim.set_bfield(w["B"])
     return sim
 
 
@@ -199,6 +211,8 @@ def cpu_oracle_rate(w, budget_s=12.0, sample_fraction=1.0, steps=None, seed=0):
     from oracle import oracle as O
     species = [O.Species(**sp) for sp in w["species"]]
     sim = O.OracleSim(w["nvdim"], w["nx"], w["L"], w["dt"], species)
+    if "B" in w:
+        sim.B = np.asarray(w["B"], dtype=np.float64)
     rng = np.random.default_rng(seed)
     for s, (f0, lat) in enumerate(zip(w["f0"], w["lattice"])):
         sim.init_markers(s, lat, O.F0(f0["beams"], f0["modes"]), w["seed"], w["jitter"])
@@ -301,13 +315,14 @@ def run_ours(args):
     pd_ms = kms[1] / args.steps
     prec = w["precision"]
     nvd = w["nvdim"]
-    algo, lay = BYTES_PER_MARKER_ALGO[(nvd, prec)], BYTES_PER_MARKER_LAYOUT[(nvd, prec)]
+    kind = "3B" if nvd == 3 and any(w.get("B", (0.0, 0.0, 0.0))) else nvd
+    algo, lay = BYTES_PER_MARKER_ALGO[(kind, prec)], BYTES_PER_MARKER_LAYOUT[(kind, prec)]
     achieved = nmark * algo / (pd_ms / 1e3) / 1e9
     traffic_pm = recorded_traffic(w["name"], prec, nvd)
-    names = KERNEL_NAMES[nvd]
+    names = KERNEL_NAMES[kind]
     roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
                 "traffic": traffic_pm * nmark if traffic_pm else None,
-                "kernel": KERNEL_DESC[nvd],
+                "kernel": KERNEL_DESC[kind],
                 "algorithmic_bytes_per_marker": algo,
                 "layout_bytes_per_marker": lay,
                 "frac_layout_bytes": nmark * lay / (pd_ms / 1e3) / 1e9 / hbm,
@@ -358,9 +373,10 @@ def run_ours(args):
                            "steps_in_run": w["steps"], "timed_from": "t = 0",
                            "l2": {"two_stream": "inputs larger than L2 (markers 16 B each, 268 MB per step read)",
                                   "bump_on_tail": "inputs larger than L2 (markers 24 B each, 3.2 GB per step read)",
+                                  "bernstein": "inputs larger than L2 (markers 24 B each, 3.2 GB per step read)",
                                   "landau": "small workload (fits in L2)"}[args.workload],
                            "parallelism": "single GPU" if world == 1 else f"{world} independent replicas"},
-                "roofline": roofline, "clocks": clk, "gpu_launches": LAUNCHES_PER_STEP[nvd] * args.steps,
+                "roofline": roofline, "clocks": clk, "gpu_launches": LAUNCHES_PER_STEP[kind] * args.steps,
                 ("out_of_window_runs_last_step" if nvd == 1 else "movers_last_step"): [int(x) for x in stats[:, 0]],
                 "resort_steps": [int(x) for x in stats[:, 1]], "e2e": e2e,
                 "cpu_baseline": cpu}

@@ -1,0 +1,90 @@
+"""Parity at the full sizes of the benchmarked workloads, in the launch
+configuration the benchmark times (lattice markers, steps replayed as the
+library's CUDA graph), against the FP64 oracle.
+
+After a few steps the oracle takes the GPU's marker state and rebuilds every
+grid from it (Eq. 4 reconstruction, Eq. 14 moment, Eq. 6 field), and then
+both advance one step from that identical state.  The whole grids are
+compared (relative L2, FP32 tolerance 1e-5 as in the small cases): the
+denominator n of Eq. 4 checks every marker's position and velocity, f its
+value, rho and E the moment and the solve.
+
+The net charge of Eq. 14 is a difference of nearly equal species charges in
+these quasi-neutral runs (two-stream: |rho| ~ 4e-5 of either species'), so
+rounding at the FP32 level of f shows in rho amplified by that ratio.  rho's
+error is therefore measured against the species charge scale
+||sum_s |rho_s|||, and E against the FP64 solve (Eq. 6) of the GPU's own rho.
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_1804_03901_gb300 import inputs
+
+from test_gpu_parity3 import TOL, rel, sync_oracle_to_gpu
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def A():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_1804_03901_gb300 import build
+    build.build()
+    from paper_1804_03901_gb300 import avl
+    return avl
+
+
+def compare_grids(sim, orc, tol, what):
+    for s in range(len(orc.species)):
+        f, n = sim.get_f(s, with_n=True)
+        assert f.shape == orc.f[s].shape
+        assert rel(f, orc.f[s]) < tol, (what, "f", s, rel(f, orc.f[s]))
+        assert rel(n, orc.den[s]) < tol, (what, "n", s, rel(n, orc.den[s]))
+    rho, E = sim.get_rho(), sim.get_E()
+    scale = np.linalg.norm(sum(np.abs(r) for r in orc.rho_s))
+    err = np.linalg.norm(rho - orc.rho) / scale
+    assert err < tol, (what, "rho against the species charge scale", err)
+    E_of_rho = O.poisson(orc.nx, orc.L, orc.cP, orc.softening, rho)
+    assert rel(E, E_of_rho) < 1e-10, (what, "E against the FP64 solve of rho", rel(E, E_of_rho))
+
+
+def build_pair(A, w):
+    prec = A.AVL_FP32 if w["precision"] == "fp32" else A.AVL_FP64
+    dom = A.make_domain(w["nvdim"], w["nx"], w["L"], w["dt"], 1.0, True, prec)
+    sim = A.Simulation(dom, [A.make_species(**sp) for sp in w["species"]])
+    for s, (f0, lat) in enumerate(zip(w["f0"], w["lattice"])):
+        sim.init_markers(s, lat, A.make_f0(f0["beams"], f0["modes"]), w["seed"], w["jitter"])
+    orc = O.OracleSim(w["nvdim"], w["nx"], w["L"], w["dt"], [O.Species(**sp) for sp in w["species"]])
+    if "B" in w:
+        sim.set_bfield(w["B"])
+        orc.B = np.asarray(w["B"], dtype=np.float64)
+    return sim, orc
+
+
+@pytest.mark.parametrize("name,steps", [("two_stream", 20), ("two_stream_driven", 20), ("bump_on_tail", 4),
+                                        ("bernstein", 4)])
+def test_full_size_parity(A, name, steps):
+    """two_stream: 2 x 8388608 markers on 512 x 1024 cells (FP32 1d1v);
+    two_stream_driven: the same with 5e-2 perturbations, so that the markers
+    leave their deposit windows and the layout re-sorts; bump_on_tail and
+    bernstein: 134217728 markers on 256 x 64^3 cells (FP32 1d3v, the latter
+    with the Boris push and the global re-sort of every step)."""
+    w = {"two_stream": inputs.two_stream, "two_stream_driven": lambda: inputs.two_stream(amp=5e-2),
+         "bump_on_tail": inputs.bump_on_tail, "bernstein": inputs.bernstein}[name]()
+    sim, orc = build_pair(A, w)
+    sim.step(steps)
+    sync_oracle_to_gpu(sim, orc)
+    tol = TOL[1 if w["precision"] == "fp32" else 0]
+    compare_grids(sim, orc, tol, f"{name} after {steps} steps")
+    sim.step(1)
+    orc.step(1)
+    compare_grids(sim, orc, tol, f"{name} step {steps + 1}")
+    st = sim.get_stats()
+    if name == "two_stream_driven":
+        assert st[0, 1] >= 1, st     # the layout re-sorted at full size
+    if name == "bernstein":
+        assert st[0, 1] == steps + 1, st
+    sim.close()
