@@ -58,9 +58,9 @@ typedef struct avl_ctx avl_ctx;
 /* Simulation domain (Sec. 3.1, Sec. 3.3 numerical parameters).
  * precision AVL_FP64: markers, deposit and grid in FP64.
  * precision AVL_FP32: marker position = int32 cell + FP32 offset, velocity
- *   and value in FP32, deposit sums compensated in FP32 (1d1v; 1d3v sums
- *   plain FP32); the Poisson solve, the charge-neutral k = 0 handling and
- *   the diagnostics stay FP64.
+ *   and value in FP32, deposit sums in FP32 (1d1v: plain within a chunk,
+ *   compensated over chunks; 1d3v: plain); the Poisson solve, the
+ *   charge-neutral k = 0 handling and the diagnostics stay FP64.
  * nvdim = 3 (Sec. 2 with three velocity dimensions: the field accelerates
  *   v_x, an optional static background magnetic field, avl_set_bfield, turns
  *   v) needs nx <= 1024 (FP32) or nx <= 512 (FP64), nv[0] in [2, 1024],

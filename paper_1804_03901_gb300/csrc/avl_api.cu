@@ -205,7 +205,7 @@ avl_status plan_layout(avl_ctx* c, int s, long long n)
     if (!e) e = grab(&po, (size_t)nch * HIST_S * 4, true);
     if (!e) e = grab(&pk, (size_t)nch * 4, true);
     if (!e) e = grab(&pw, (size_t)nch * 4, true);
-    if (!e) e = grab(&sp.partial, (size_t)nch * 16 * Wmax * sp.nx, true);
+    if (!e) e = grab(&sp.partial, (size_t)nch * window_bytes(sp, c->h.prec), true);
     if (e) {
         free_layout(c, s);
         return cuda_fail(c, e, "cudaMalloc(markers)");

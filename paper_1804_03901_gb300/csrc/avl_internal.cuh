@@ -255,6 +255,7 @@ cudaError_t adjoint_run(AdjEngine** eng, const StepArgs& h, const StepArgs* d, c
 void adjoint_free(AdjEngine* e);
 
 size_t pd1_smem_bytes(const SpDev& sp, int prec);
+size_t window_bytes(const SpDev& sp, int prec);
 cudaError_t configure_vhs1(const StepArgs& h);
 cudaError_t configure_field(const StepArgs& h);
 cudaError_t configure_field_bytes(int bytes);

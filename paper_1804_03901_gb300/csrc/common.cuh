@@ -153,9 +153,9 @@ __device__ __forceinline__ void two_sum_add(float& hi, float& lo, float x)
 }
 
 
-// FP32 path: float-float arithmetic (an unevaluated sum hi + lo) so that the
-// cell values and the column sums keep the accuracy of the compensated
-// deposit without per-cell FP64 work.
+// FP32 path: float-float arithmetic (an unevaluated sum hi + lo) for the sum
+// of the chunks' window partials, the cell values and the column sums,
+// without per-cell FP64 work.
 struct ff {
     float hi, lo;
 };

@@ -132,26 +132,16 @@ __device__ __forceinline__ void store8(double* p, const double (&o)[8])
     for (int q = 0; q < 4; ++q) reinterpret_cast<double2*>(p)[q] = make_double2(o[2 * q], o[2 * q + 1]);
 }
 
-// rounding error of old + x exactly; that error and the caller's own low part
-// accumulate in the lo plane
-__device__ __forceinline__ void smem_comp_add(float* hi, float* lo, float x, float xlo)
-{
-    const float old = atomicAdd(hi, x);
-    const float s = __fadd_rn(old, x);
-    const float bp = __fsub_rn(s, old);
-    const float err = __fadd_rn(__fsub_rn(old, __fsub_rn(s, bp)), __fsub_rn(x, bp));
-    const float l = __fadd_rn(err, xlo);
-    if (l != 0.0f) atomicAdd(lo, l);
-}
-
 // numerator and denominator contributions of a run of markers that share the
 // same four cells (lower corner i0, j0)
 template <typename T>
 struct Run;
 
-// FP32: a run holds at most MPT markers, summed plainly in registers (its
-// rounding error is relative to the small run sum); the run sums are then
-// accumulated in shared memory with compensation
+// FP32: a run holds at most MPT markers, summed plainly in registers; the run
+// sums are added into the window with plain FP32 shared-memory reductions.
+// A window cell receives the runs of one chunk only (about 16 markers per
+// phase cell times 4 corners), so its rounding error stays near 1e-7 of the
+// cell value; the sum over chunks in the finalize is compensated.
 template <>
 struct Run<float> {
     int i0, j0;
@@ -171,13 +161,13 @@ struct Run<float> {
             dh[k] = __fadd_rn(dh[k], a[k]);
         }
     }
-    // window planes: num_hi, num_lo, den_hi, den_lo
+    // window planes: num, den
     __device__ __forceinline__ void to_window(float* win, int plane, const int (&cell)[4]) const
     {
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-            smem_comp_add(win + cell[k], win + plane + cell[k], nh[k], 0.f);
-            smem_comp_add(win + 2 * plane + cell[k], win + 3 * plane + cell[k], dh[k], 0.f);
+            atomicAdd(win + cell[k], nh[k]);
+            atomicAdd(win + plane + cell[k], dh[k]);
         }
     }
     __device__ __forceinline__ double num(int k) const { return (double)nh[k]; }
@@ -258,11 +248,17 @@ __device__ __forceinline__ bool flush_run(const Run<T>& r, T* win, int plane, in
     return true;
 }
 
+// one chunk's deposit window: numerator and denominator planes of Wmax rows
+size_t window_bytes(const SpDev& sp, int prec)
+{
+    return (size_t)2 * (prec == AVL_FP32 ? 4 : 8) * sp.Wmax * sp.nx;
+}
+
 size_t pd1_smem_bytes(const SpDev& sp, int prec)
 {
     size_t eb = (size_t)sp.nx * (prec == AVL_FP32 ? 4 : 8);
     eb = (eb + 15) & ~size_t(15);
-    return eb + 32 + (size_t)2 * HIST_S * 4 + (size_t)4 * sp.nx + (size_t)16 * sp.Wmax * sp.nx;
+    return eb + 32 + (size_t)2 * HIST_S * 4 + (size_t)4 * sp.nx + window_bytes(sp, prec);
 }
 
 // ---------------------------------------------------------------------------
@@ -442,7 +438,7 @@ __global__ void __launch_bounds__(PD_THREADS, 2) k_pd1(const StepArgs* __restric
     int* shs = hcur + HIST_S;                              // per-column row shift (nx)
     unsigned char* winb = smem + eb + 32 + 2 * HIST_S * 4 + ((4 * nx + 15) & ~15);
     const int plane = W * nx;
-    const size_t win_bytes = (size_t)16 * plane;
+    const size_t win_bytes = (size_t)2 * sizeof(T) * plane;
 
     const T* Eg = (sizeof(T) == 4) ? reinterpret_cast<const T*>(A->fd.E32) : reinterpret_cast<const T*>(A->fd.E64);
     const bool use_bulk = push && ((nx * sizeof(T)) % 16 == 0);
@@ -701,9 +697,7 @@ struct CellSum<float> {
     __device__ __forceinline__ void add_partial(const float* p, int plane)
     {
         ff_add(num, p[0]);
-        num.lo = __fadd_rn(num.lo, p[plane]);
-        ff_add(den, p[2 * plane]);
-        den.lo = __fadd_rn(den.lo, p[3 * plane]);
+        ff_add(den, p[plane]);
     }
     __device__ __forceinline__ void add_ovf(double n, double d)
     {
@@ -750,7 +744,7 @@ struct CellSum<double> {
     }
 };
 
-constexpr int FIN_LIST = 64;   // chunks whose windows meet one finalize block's rows
+constexpr int FIN_LIST = 256;  // chunks whose windows meet one finalize block's rows
 
 template <typename T, bool BATCH>
 __global__ void __launch_bounds__(FIN_THREADS) k_fin1(const StepArgs* __restrict__ A0, int all_species,
@@ -783,7 +777,7 @@ __global__ void __launch_bounds__(FIN_THREADS) k_fin1(const StepArgs* __restrict
     T* fg = reinterpret_cast<T*>(sp.fgrid);
     T* ng = reinterpret_cast<T*>(sp.ngrid);
     const T* part = reinterpret_cast<const T*>(sp.partial);
-    constexpr int planes = sizeof(T) == 4 ? 4 : 2;
+    constexpr int planes = 2;
 
     // chunks whose deposit windows meet rows [j0, j1), in chunk order (the
     // windows are stored shifted by shift[x] per column; all_species marks a
