@@ -741,7 +741,7 @@ avl_status avl_create(const avl_domain* dom, const avl_species* spec, int32_t ns
         const size_t nvk = (size_t)sp.nvflat;
         void *pf, *pn, *po, *pr, *pd, *p1, *p2, *p3, *p4, *p5, *p6;
         if ((e = dalloc(c, &pf, cells * pb, true)) || (e = dalloc(c, &pn, cells * pb, true)) ||
-            (e = dalloc(c, &po, 2 * cells * 8, true)) || (e = dalloc(c, &pr, (size_t)sp.nrq * nx * 8, true)) ||
+            (e = dalloc(c, &po, 2 * cells * 8 + nvk * 8, true)) || (e = dalloc(c, &pr, (size_t)sp.nrq * nx * 8, true)) ||
             (e = dalloc(c, &pd, (size_t)sp.nfin * 4 * 8, true)) || (e = dalloc(c, &p1, nvk * 4, true)) ||
             (e = dalloc(c, &p2, nvk * 4, true)) || (e = dalloc(c, &p3, (nvk + 1) * 4, true)) ||
             (e = dalloc(c, &p4, nvk * 4, true)) || (e = dalloc(c, &p5, (size_t)nx * 4, true)) ||
@@ -752,6 +752,7 @@ avl_status avl_create(const avl_domain* dom, const avl_species* spec, int32_t ns
         sp.fgrid = pf;
         sp.ngrid = pn;
         sp.ovf = (double*)po;
+        sp.ovf_tag = reinterpret_cast<int*>(sp.ovf + 2 * cells);
         sp.rho_part = (double*)pr;
         sp.dpart = (double*)pd;
         sp.far_cnt[0] = (int*)p1;

@@ -95,6 +95,7 @@ struct SpDev {
     void* ngrid;
     void* partial;             // [nchunk][planes][Wmax][nx]
     double* ovf;               // [2][nvflat][nx] FP64 overflow num/den
+    int* ovf_tag;              // [nvflat] step tag (step + 1) of the last overflow into each row
     double* rho_part;          // [nrq][nx] charge of this species per row group
     double* dpart;             // [nfin][4] : N, Wkin, S, -
     // finalize blocks: FIN_XB x-columns times a group of rq velocity rows

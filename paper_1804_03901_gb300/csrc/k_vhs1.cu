@@ -206,10 +206,12 @@ struct Run<double> {
     __device__ __forceinline__ double den(int k) const { return dh[k]; }
 };
 
-// the rare out-of-window path: FP64 global atomics into the overflow grids
+// the rare out-of-window path: FP64 global atomics into the overflow grids;
+// each row written is tagged with the step (tag), so that the finalize reads
+// and clears only the rows of this step's overflow
 __device__ __forceinline__ void flush_overflow(int ia, int ib, int j0, int nx, int nv, double n0, double n1, double n2,
                                             double n3, double d0, double d1, double d2, double d3,
-                                            double* ovf_num, double* ovf_den)
+                                            double* ovf_num, double* ovf_den, int* ovf_tag, int tag)
 {
     if (j0 >= 0 && j0 < nv) {
         const size_t o = (size_t)j0 * nx;
@@ -217,6 +219,7 @@ __device__ __forceinline__ void flush_overflow(int ia, int ib, int j0, int nx, i
         atomicAdd(ovf_den + o + ia, d0);
         atomicAdd(ovf_num + o + ib, n1);
         atomicAdd(ovf_den + o + ib, d1);
+        ovf_tag[j0] = tag;
     }
     if (j0 + 1 >= 0 && j0 + 1 < nv) {
         const size_t o = (size_t)(j0 + 1) * nx;
@@ -224,6 +227,7 @@ __device__ __forceinline__ void flush_overflow(int ia, int ib, int j0, int nx, i
         atomicAdd(ovf_den + o + ia, d2);
         atomicAdd(ovf_num + o + ib, n3);
         atomicAdd(ovf_den + o + ib, d3);
+        ovf_tag[j0 + 1] = tag;
     }
 }
 
@@ -232,7 +236,7 @@ __device__ __forceinline__ void flush_overflow(int ia, int ib, int j0, int nx, i
 // Returns true for the overflow path.
 template <typename T>
 __device__ __forceinline__ bool flush_run(const Run<T>& r, T* win, int plane, int row0, int W, int nx, int nv,
-                                          const int* sh, double* ovf_num, double* ovf_den)
+                                          const int* sh, double* ovf_num, double* ovf_den, int* ovf_tag, int tag)
 {
     if (r.j0 + 1 < 0 || r.j0 >= nv) return false;   // footprint entirely off the velocity grid
     int ia, ib;
@@ -244,7 +248,7 @@ __device__ __forceinline__ bool flush_run(const Run<T>& r, T* win, int plane, in
         return false;
     }
     flush_overflow(ia, ib, r.j0, nx, nv, r.num(0), r.num(1), r.num(2), r.num(3), r.den(0), r.den(1), r.den(2),
-                   r.den(3), ovf_num, ovf_den);
+                   r.den(3), ovf_num, ovf_den, ovf_tag, tag);
     return true;
 }
 
@@ -496,6 +500,8 @@ __global__ void __launch_bounds__(PD_THREADS, 2) k_pd1(const StepArgs* __restric
     const T dvk = (T)sp.dv[0];
     double* ovf_num = sp.ovf;
     double* ovf_den = sp.ovf + (size_t)nv * nx;
+    int* ovf_tag = sp.ovf_tag;
+    const int tag = (int)ctl->step + 1;
     T* dvp = reinterpret_cast<T*>(sp.mv[cb][0]);
     const T* fp = reinterpret_cast<const T*>(sp.mf[cb]);
     const int nb = sorted_write ? 1 - cb : cb;
@@ -569,7 +575,10 @@ __global__ void __launch_bounds__(PD_THREADS, 2) k_pd1(const StepArgs* __restric
                 const int j0 = kb + (int)ft;
                 const T wv = t - ft;
                 if (!have || i0 != run.i0 || j0 != run.j0) {
-                    if (have) n_over += flush_run<T>(run, win, plane, row0, W, nx, nv, shs, ovf_num, ovf_den) ? 1u : 0u;
+                    if (have)
+                        n_over += flush_run<T>(run, win, plane, row0, W, nx, nv, shs, ovf_num, ovf_den, ovf_tag, tag)
+                                      ? 1u
+                                      : 0u;
                     run.reset(i0, j0);
                     have = true;
                 }
@@ -577,7 +586,8 @@ __global__ void __launch_bounds__(PD_THREADS, 2) k_pd1(const StepArgs* __restric
                 run.add(a, fl);
             }
         }
-        if (have) n_over += flush_run<T>(run, win, plane, row0, W, nx, nv, shs, ovf_num, ovf_den) ? 1u : 0u;
+        if (have)
+            n_over += flush_run<T>(run, win, plane, row0, W, nx, nv, shs, ovf_num, ovf_den, ovf_tag, tag) ? 1u : 0u;
         if (!push) continue;
         if (!sorted_write) {
             // in place: the positions and velocities go back where they came
@@ -774,6 +784,8 @@ __global__ void __launch_bounds__(FIN_THREADS) k_fin1(const StepArgs* __restrict
     const bool any_ovf = ctl->ovf_count[s] != 0;
     double* ovf_num = sp.ovf;
     double* ovf_den = sp.ovf + (size_t)nv * nx;
+    const int* ovf_tag = sp.ovf_tag;
+    const int tag = (int)ctl->step + 1;
     T* fg = reinterpret_cast<T*>(sp.fgrid);
     T* ng = reinterpret_cast<T*>(sp.ngrid);
     const T* part = reinterpret_cast<const T*>(sp.partial);
@@ -845,7 +857,7 @@ __global__ void __launch_bounds__(FIN_THREADS) k_fin1(const StepArgs* __restrict
                         cs.add_partial(part + (size_t)cc * planes * plane + (size_t)wr * nx + x, plane);
                 }
             }
-            if (any_ovf) {
+            if (any_ovf && ovf_tag[j] == tag) {
                 const size_t o = (size_t)j * nx + x;
                 cs.add_ovf(ovf_num[o], ovf_den[o]);
                 ovf_num[o] = 0.0;
