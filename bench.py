@@ -37,19 +37,19 @@ sys.path.insert(0, ROOT)
 # step, algorithmic bytes per marker of the push + deposit kernel (read x,
 # v, f and write x, v_x) and the bytes of the stored layout it moves
 # ("3B": 1d3v with a magnetic field, whose push + deposit kernel deposits only)
-KERNEL_NAMES = {1: ["k_count1", "k_pd1", "k_fin1", "k_field"],
+KERNEL_NAMES = {1: ["k_rs1", "k_pd1", "k_fin1", "k_field"],
                 3: ["k_sort3", "k_pd3", "k_fin3", "k_field"],
                 "3B": ["k_bpush3 + k_src3_scan + k_rs3_scatter", "k_pd3", "k_fin3", "k_field"]}
-LAUNCHES_PER_STEP = {1: 4,     # k_pd1 (in place and re-sorting instances), k_fin1, k_field
+LAUNCHES_PER_STEP = {1: 4,     # k_rs1 (re-sort scatter, exits at once on other steps), k_pd1, k_fin1, k_field
                      3: 4,     # k_pd3, k_fin3, k_field, k_sort3
                      "3B": 6}  # k_bpush3, k_src3_scan, k_rs3_scatter (one mobile species), k_pd3, k_fin3, k_field
 BYTES_PER_MARKER_ALGO = {(1, "fp32"): 20.0, (1, "fp64"): 40.0,    # 1d1v: read x, v, f; write x, v
                          (3, "fp32"): 28.0, (3, "fp64"): 56.0,    # 1d3v: read x, vx, vy, vz, f; write x, vx
                          ("3B", "fp32"): 24.0, ("3B", "fp64"): 40.0}   # deposit only: read x, v, f
-BYTES_PER_MARKER_LAYOUT = {(1, "fp32"): 32.0, (1, "fp64"): 48.0,  # read and re-sorted write of all fields
+BYTES_PER_MARKER_LAYOUT = {(1, "fp32"): 28.0, (1, "fp64"): 40.0,  # read all fields, write cell, off, dv in place
                            (3, "fp32"): 36.0, (3, "fp64"): 64.0,  # read all fields, write cell, off, vx in place
                            ("3B", "fp32"): 24.0, ("3B", "fp64"): 40.0}
-KERNEL_DESC = {1: "k_pd1 (gather + push + VHS deposit + re-sorted write)",
+KERNEL_DESC = {1: "k_pd1 (gather + push + VHS deposit, written back in place)",
                3: "k_pd3 (gather + push + x-sorted VHS deposit per pencil, in place)",
                "3B": "k_pd3 mode 2 (x-sorted VHS deposit per pencil of the Boris-pushed, re-sorted markers)"}
 

@@ -304,9 +304,6 @@ avl_status set_cur_zero(avl_ctx* c, int s)
     AVL_CUDA(c, cudaMemcpyAsync(&c->d_ctl->hsel[s], &zero, sizeof(int), cudaMemcpyHostToDevice, c->st));
     AVL_CUDA(c, cudaMemcpyAsync(&c->d_ctl->sort_now[s], &zero, sizeof(int), cudaMemcpyHostToDevice, c->st));
     AVL_CUDA(c, cudaMemcpyAsync(&c->d_ctl->sort_next[s], &zero, sizeof(int), cudaMemcpyHostToDevice, c->st));
-    // the fresh layout is sorted by the keys of the current state
-    const int one = 1;
-    AVL_CUDA(c, cudaMemcpyAsync(&c->d_ctl->prev_sorted[s], &one, sizeof(int), cudaMemcpyHostToDevice, c->st));
     const SpDev& sp = c->h.sp[s];
     if (sp.nvdim == 1) {
         AVL_CUDA(c, cudaMemsetAsync(sp.far_cnt[0], 0, (size_t)sp.nvflat * 4, c->st));
@@ -386,6 +383,7 @@ avl_status enqueue_step(avl_ctx* c)
         AVL_CUDA(c, launch_sort3(c->h, c->d_args, c->st));
         return AVL_OK;
     }
+    AVL_CUDA(c, launch_rs1(c->h, c->d_args, c->st));
     AVL_CUDA(c, launch_pd1(c->h, c->d_args, 1, c->st));
     AVL_CUDA(c, launch_fin1(c->h, c->d_args, 0, c->st));
     AVL_CUDA(c, launch_field(c->h, c->d_args, 1, c->st));
@@ -566,10 +564,12 @@ avl_status ensure_batch_map(avl_ctx* b)
     return AVL_OK;
 }
 
-// one step of every run: push + deposit, finalize, field (one launch each)
+// one step of every run: re-sort (where marked), push + deposit, finalize,
+// field (one launch each)
 avl_status enqueue_batch_step(avl_ctx* b)
 {
     const BatchMap* bm = static_cast<const BatchMap*>(b->bm_mem);
+    AVL_CUDA(b, launch_rs1_batch(b->h.prec, bm, b->bm_pd_blocks, b->st));
     AVL_CUDA(b, launch_pd1_batch(b->h.prec, bm, b->bm_pd_blocks, b->bm_pd_smem, 1, b->st));
     AVL_CUDA(b, launch_fin1_batch(b->h.prec, bm, b->bm_fin_blocks, 0, b->st));
     AVL_CUDA(b, launch_field_batch(bm, (int)b->runs.size(), b->bm_field_smem, 1, b->st));
@@ -1104,7 +1104,10 @@ avl_status avl_profile_steps(avl_ctx* c, int32_t nsteps, double* ms, int32_t nke
     for (int i = 0; i < nsteps && st == AVL_OK; ++i) {
         const bool d3 = c->h.nvdim == 3, mag = d3 && c->h.fd.magnetized;
         cudaError_t e = cudaEventRecord(ev[0], c->st);
-        if (!e && d3) e = mag ? launch_magnetized_push(c) : launch_sort3(c->h, c->d_args, c->st);
+        if (!e)
+            e = batch ? launch_rs1_batch(c->h.prec, bm, c->bm_pd_blocks, c->st)
+                : d3  ? (mag ? launch_magnetized_push(c) : launch_sort3(c->h, c->d_args, c->st))
+                      : launch_rs1(c->h, c->d_args, c->st);
         if (!e) e = cudaEventRecord(ev[1], c->st);
         if (!e)
             e = batch ? launch_pd1_batch(c->h.prec, bm, c->bm_pd_blocks, c->bm_pd_smem, 1, c->st)

@@ -2,8 +2,9 @@
 // host layer of the GB300 Vlasov-Hybrid library.
 //
 // HBM layout of one species (1d1v):
-//   markers, double-buffered (every step writes the re-sorted markers into
-//   the other buffer), structure of arrays:
+//   markers, double-buffered (a re-sorting step writes the markers sorted
+//   by their keys into the other buffer before the push), structure of
+//   arrays:
 //     FP32: cell int32[n], off f32[n] (position in cells = cell + off, off in
 //           [0,1)), dv f32[n], f f32[n]                      16 B per marker
 //     FP64: xi f64[n] (position in cells), dv f64[n], f f64[n]   24 B
@@ -128,7 +129,7 @@ struct FieldDev {
 
 struct Ctl {
     int cur[MAXS];             // buffer holding the current markers
-    int sort_now[MAXS];        // this step writes the markers re-sorted
+    int sort_now[MAXS];        // this step re-sorts the markers before the push
     int sort_next[MAXS];       // decided by the field kernel for the next step
     int hsel[MAXS];            // which cnt / far_cnt buffer holds the current counts
     unsigned long long ovf_count[MAXS];
@@ -137,8 +138,6 @@ struct Ctl {
     unsigned long long uncovered[MAXS];   // markers outside their chunk's best window (decision input)
     int shift_min[MAXS][2], shift_max[MAXS][2];   // range of each shift table
     int shsel[MAXS];           // which shift table belongs to this step's field
-    int prev_sorted[MAXS];     // the current layout was re-sorted by the previous step
-                               // (sorted by the keys of the previous state)
     long long step;
     int err;
     // 1d3v
@@ -183,15 +182,19 @@ __device__ __forceinline__ const StepArgs* batch_run(const StepArgs* A, const Ba
 
 // kernel launchers (defined in the .cu files; all enqueue on `st`).
 // launch_count1: key histograms of the current markers (after creation).
+// launch_rs1: markers of the species the field kernel marked into the layout
+//             sorted by their current keys (other buffer; a no-op otherwise).
 // launch_pd1 mode: 0 = refresh (every species with markers: deposit only)
 //                  1 = step (mobile species: push, deposit, write back in
-//                      place or re-sorted, key histograms of the new state)
+//                      place, key histograms of the new state)
 cudaError_t launch_count1(const StepArgs& h, const StepArgs* d, cudaStream_t st);
+cudaError_t launch_rs1(const StepArgs& h, const StepArgs* d, cudaStream_t st);
 cudaError_t launch_pd1(const StepArgs& h, const StepArgs* d, int mode, cudaStream_t st);
 cudaError_t launch_fin1(const StepArgs& h, const StepArgs* d, int all_species, cudaStream_t st);
 cudaError_t launch_field(const StepArgs& h, const StepArgs* d, int count_step, cudaStream_t st);
 // batched forms (bm on the device; blocks = totals over the runs, smem = the
 // largest of the runs' needs, set beforehand by configure_batch1)
+cudaError_t launch_rs1_batch(int prec, const BatchMap* bm, int blocks, cudaStream_t st);
 cudaError_t launch_pd1_batch(int prec, const BatchMap* bm, int blocks, int smem, int mode, cudaStream_t st);
 cudaError_t launch_fin1_batch(int prec, const BatchMap* bm, int blocks, int all_species, cudaStream_t st);
 cudaError_t launch_field_batch(const BatchMap* bm, int nrun, int smem, int count_step, cudaStream_t st);

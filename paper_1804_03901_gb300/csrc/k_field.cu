@@ -134,10 +134,12 @@ __device__ void poisson_spectral(double* rho_s, double2* work, double* Eout, int
 }
 
 // After a step: CTA 1 of the field cluster decides, per mobile species,
-// whether the next step writes its markers re-sorted (when the best deposit
-// windows of the chunks, placed from the key counts of the new state, would
-// miss more than a small fraction of the markers) and if so prepares the
-// slots; CTAs 2.. clear the key counts consumed by this step for reuse.
+// whether the next step re-sorts its markers before the push (when the field
+// drifts markers a row or more, or the best deposit windows of the chunks,
+// placed from the key counts of the new state, would miss more than a small
+// fraction of the markers) and if so prepares the slots and the key
+// histograms of the re-sorted chunks; CTAs 2.. clear the key counts consumed
+// by this step for reuse.
 __device__ void resort_work(const StepArgs* __restrict__ A, int rank)
 {
     const Ctl* ctl = A->ctl;
@@ -175,7 +177,12 @@ __device__ void resort_work(const StepArgs* __restrict__ A, int rank)
                 cw->uncovered[s] = miss;
                 cw->sort_next[s] = resort ? 1 : 0;
             }
-            if (resort) scan_layout(sp, kref, cnt, far, true, sp.KB[1 - cur_after]);
+            if (resort) {
+                scan_layout(sp, kref, cnt, far, true, sp.KB[1 - cur_after]);
+                // the next step deposits from the re-sorted layout: its window
+                // placement takes the key histograms of the re-sorted chunks
+                sorted_chunk_hist(sp, sp.KB[1 - cur_after], sp.cnt[1 - hs]);
+            }
             __syncthreads();
         } else {
             // clear cnt[hs] and far_cnt[hs] for the next step's counting
@@ -369,7 +376,6 @@ __global__ void __cluster_dims__(FIELD_CLUSTER, 1, 1) __launch_bounds__(FIELD_TH
                 ctl->cur[s] = 1 - ctl->cur[s];
                 ctl->nsort[s] += 1;
             }
-            ctl->prev_sorted[s] = ctl->sort_now[s];
             ctl->sort_now[s] = ctl->sort_next[s];
             ctl->hsel[s] = 1 - ctl->hsel[s];
             ctl->shsel[s] = 1 - ctl->shsel[s];

@@ -1,18 +1,19 @@
 // k_vhs1.cu -- 1d1v kernels of the Vlasov-Hybrid time step (Fig. 2).
 //
 // One step of one species runs as
-//   k_count1   keys of the current markers per chunk; the last CTA scans the
-//              counts into the slots of the re-sorted layout and places the
-//              deposit window of every chunk
+//   k_rs1      only on steps the field kernel marked for re-sorting: every
+//              marker into its slot of the layout sorted by its current key,
+//              in the other buffer
 //   k_pd1      per chunk: gather E + push (Sec. 2), VHS deposit of the
 //              numerator and denominator of Eq. 4 into a shared-memory window
 //              (runs of markers with the same cloud-in-cell footprint are
-//              summed in registers first), and the write of every pushed
-//              marker into its slot of the re-sorted layout
+//              summed in registers first), the pushed markers written back in
+//              place and their new keys counted
 //   k_fin1     f = num / den (Eq. 4), velocity moment (Eq. 14), per-block
 //              diagnostics (Sec. 3.4.1)
-// Marker creation (lattice weighted to f0, Sec. 2 / Sec. 3.1) and caller
-// markers go through the same count / scan / scatter with another source.
+// k_count1 counts the keys of freshly created markers.  Marker creation
+// (lattice weighted to f0, Sec. 2 / Sec. 3.1) and caller markers go through
+// a count / scan / scatter of their own.
 #include <math.h>
 
 #include <algorithm>
@@ -346,21 +347,6 @@ __device__ __forceinline__ void hist_add(int* hist, int* far_cnt, int code, bool
     }
 }
 
-// warp-aggregated global histogram by (target chunk, key code) for markers
-// written re-sorted: gcode = chunk * HIST_S + code, or -(key + 1) for far keys
-__device__ __forceinline__ void ghist_add(int* cnt, int* far_cnt, int gcode, bool valid)
-{
-    const int key = valid ? gcode : INT_MIN;
-    const unsigned mask = __match_any_sync(0xffffffffu, key);
-    const int lane = threadIdx.x & 31;
-    if (valid && lane == __ffs(mask) - 1) {
-        if (gcode >= 0)
-            atomicAdd(cnt + gcode, __popc(mask));
-        else
-            atomicAdd(far_cnt + (-gcode - 1), __popc(mask));
-    }
-}
-
 // ---------------------------------------------------------------------------
 // key histograms of the current markers (after marker creation; one CTA per chunk)
 // ---------------------------------------------------------------------------
@@ -399,15 +385,118 @@ __global__ void __launch_bounds__(CNT_THREADS) k_count1(const StepArgs* __restri
 }
 
 // ---------------------------------------------------------------------------
-// push + deposit + write back (one CTA per chunk)
+// re-sort (one CTA per chunk): markers into the layout sorted by their keys
 // ---------------------------------------------------------------------------
-// Step n of a chunk: the deposit window is placed from the histogram of the
-// chunk's current keys (cnt[hsel], written by step n-1); every marker is
-// pushed, deposited (runs of markers with the same footprint summed in
-// registers first), written back in place, or, on re-sort steps, into its
-// slot of the re-sorted layout in the other buffer, and its new key is
-// counted into cnt[1 - hsel] for step n+1.
-template <typename T, bool SORTED, bool BATCH>
+// On a step the field kernel marked for re-sorting, every marker of the chunk
+// goes, before the push, to its slot of the layout sorted by its current key
+// (slots prepared by the field kernel from the key counts of the current
+// state) in the other buffer, with its velocity re-referenced to the target
+// chunk.  The push + deposit kernel then works in place on that buffer.
+constexpr int RS_ROUNDS = 4;       // 32-marker rounds per warp and tile of the re-sort
+constexpr int RS_KB_SMEM = 4096;   // reference keys of the target chunks staged in shared memory
+
+template <typename T, bool BATCH>
+__global__ void __launch_bounds__(PD_THREADS) k_rs1(const StepArgs* __restrict__ A0, const BatchMap* __restrict__ bm)
+{
+    __shared__ int scnt[HIST_S], offs_s[HIST_S];
+    __shared__ int kbn_s[RS_KB_SMEM];
+    __shared__ int nbad_s;
+    int g = blockIdx.x;
+    const StepArgs* __restrict__ A = A0;
+    if constexpr (BATCH) A = batch_run(A0, bm, bm->pd_base, g);
+    const int s = species_of_chunk(A, g);
+    const SpDev& sp = A->sp[s];
+    Ctl* ctl = A->ctl;
+    if (!sp.mobile || !ctl->sort_now[s]) return;
+    const int c = g - sp.chunk_base;
+    const int cb = ctl->cur[s], nb = 1 - cb;
+    const int n_all = (int)sp.n;
+    const int nv = sp.nvflat;
+    const int beg = c * sp.M, end = min((c + 1) * sp.M, n_all);
+    const int kb = sp.KB[cb][c];
+    const int kbase = kb - HIST_R;
+    const int* kb_new_g = sp.KB[nb];
+    const bool kb_in_smem = sp.nchunk <= RS_KB_SMEM;
+    for (int i = threadIdx.x; i < HIST_S; i += PD_THREADS) {
+        scnt[i] = 0;
+        offs_s[i] = sp.offs[(size_t)c * HIST_S + i];
+    }
+    if (kb_in_smem)
+        for (int i = threadIdx.x; i < sp.nchunk; i += PD_THREADS) kbn_s[i] = kb_new_g[i];
+    if (threadIdx.x == 0) nbad_s = 0;
+    __syncthreads();
+    const int* kb_new = kb_in_smem ? kbn_s : kb_new_g;
+    const T inv_dv = (T)sp.inv_dv[0];
+    const T dvk = (T)sp.dv[0];
+    const T* dvp = reinterpret_cast<const T*>(sp.mv[cb][0]);
+    const T* fp = reinterpret_cast<const T*>(sp.mf[cb]);
+    T* dvp_out = reinterpret_cast<T*>(sp.mv[nb][0]);
+    T* fp_out = reinterpret_cast<T*>(sp.mf[nb]);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const unsigned lt = (1u << lane) - 1u;
+    int n_bad = 0;
+    // a tile: every warp takes RS_ROUNDS x 32 consecutive markers, lane l the
+    // l-th of each round, so that a round's slots (warp-aggregated per key,
+    // in storage order) and its stores are contiguous
+    constexpr int TILE = PD_THREADS * RS_ROUNDS;
+    for (int tb = beg; tb < end; tb += TILE) {
+        const int w0 = tb + warp * 32 * RS_ROUNDS;
+        T dv[RS_ROUNDS], f[RS_ROUNDS];
+        Pos<T> pos[RS_ROUNDS];
+#pragma unroll
+        for (int r = 0; r < RS_ROUNDS; ++r) {
+            const int i = w0 + r * 32 + lane;
+            if (i < end) {
+                dv[r] = dvp[i];
+                f[r] = fp[i];
+                pos[r].load(sp, cb, i);
+            } else {
+                dv[r] = (T)0;
+                f[r] = (T)0;
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < RS_ROUNDS; ++r) {
+            const int i = w0 + r * 32 + lane;
+            const bool ok = i < end;
+            const int code = ok ? rel_code(key_rel(dv[r], kb, inv_dv, nv), kbase) : -1;
+            const unsigned grp = __match_any_sync(0xffffffffu, code);
+            const int leader = __ffs(grp) - 1;
+            int base = 0;
+            if (ok && lane == leader) {
+                const int cnt = __popc(grp);
+                base = code < HIST_S ? offs_s[code] + atomicAdd(&scnt[code], cnt)
+                                     : atomicAdd(sp.far_cur + (code - HIST_S), cnt);
+            }
+            base = __shfl_sync(0xffffffffu, base, leader);
+            if (!ok) continue;
+            const int d = base + __popc(grp & lt);
+            if ((unsigned)d >= (unsigned)n_all) {
+                ++n_bad;
+                continue;
+            }
+            const int kb2 = kb_new[chunk_of(d, sp.div_m, sp.div_l)];
+            pos[r].store(sp, nb, d);
+            dvp_out[d] = dv[r] + (T)(kb - kb2) * dvk;
+            fp_out[d] = f[r];
+        }
+    }
+    if (n_bad) atomicAdd(&nbad_s, n_bad);
+    __syncthreads();
+    if (threadIdx.x == 0 && nbad_s) atomicOr(&ctl->err, ERR_CAPACITY);
+}
+
+// ---------------------------------------------------------------------------
+// push + deposit + write back in place (one CTA per chunk)
+// ---------------------------------------------------------------------------
+// The deposit window is placed from the histogram of the chunk's current
+// keys (cnt[hsel]: counted by the previous step, or, after a re-sort, the
+// key ranges of the re-sorted chunks) and follows this step's drift column
+// by column; every marker is pushed, deposited (runs of markers with the
+// same footprint summed in registers first) and written back in place, and
+// its new key is counted into cnt[1 - hsel] for the next step.  On a re-sort
+// step the markers are read from the buffer k_rs1 has just written.
+template <typename T, bool BATCH>
 __global__ void __launch_bounds__(PD_THREADS, 2) k_pd1(const StepArgs* __restrict__ A0, int mode,
                                                        const BatchMap* __restrict__ bm)
 {
@@ -420,14 +509,10 @@ __global__ void __launch_bounds__(PD_THREADS, 2) k_pd1(const StepArgs* __restric
     if (mode == 1 && !sp.mobile) return;
     Ctl* ctl = A->ctl;
     const bool push = mode == 1;
-    // one instantiation per write mode; the other one's CTAs leave at once
-    if (push && (ctl->sort_now[s] != 0) != SORTED) return;
-    if (!push && SORTED) return;
-    const bool sorted_write = SORTED;
     const int hs = ctl->hsel[s];
     const int c = g - sp.chunk_base;
     const int nx = sp.nx, nv = sp.nvflat, W = sp.Wmax;
-    const int cb = ctl->cur[s];
+    const int cb = (push && ctl->sort_now[s]) ? 1 - ctl->cur[s] : ctl->cur[s];
     const int n_all = (int)sp.n;
     const int beg = c * sp.M, end = min((c + 1) * sp.M, n_all);
     const int kb = sp.KB[cb][c];
@@ -436,8 +521,8 @@ __global__ void __launch_bounds__(PD_THREADS, 2) k_pd1(const StepArgs* __restric
     const size_t eb = ((size_t)nx * sizeof(T) + 15) & ~size_t(15);
     T* Es = reinterpret_cast<T*>(smem);
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem + eb);
-    int* misc = reinterpret_cast<int*>(smem + eb + 16);   // [0] overflow runs, [1] bad slots, [2] row0
-    int* scnt = reinterpret_cast<int*>(smem + eb + 32);   // slot counters (re-sort) / next-step histogram
+    int* misc = reinterpret_cast<int*>(smem + eb + 16);   // [0] overflow runs, [2] row0
+    int* scnt = reinterpret_cast<int*>(smem + eb + 32);   // next-step histogram
     int* hcur = scnt + HIST_S;                             // current-key histogram (window placement)
     int* shs = hcur + HIST_S;                              // per-column row shift (nx)
     unsigned char* winb = smem + eb + 32 + 2 * HIST_S * 4 + ((4 * nx + 15) & ~15);
@@ -448,7 +533,6 @@ __global__ void __launch_bounds__(PD_THREADS, 2) k_pd1(const StepArgs* __restric
     const bool use_bulk = push && ((nx * sizeof(T)) % 16 == 0);
     if (threadIdx.x == 0) {
         misc[0] = 0;
-        misc[1] = 0;
         if (use_bulk) {
             mbar_init(bar, 1);
             fence_mbar_init();
@@ -458,18 +542,13 @@ __global__ void __launch_bounds__(PD_THREADS, 2) k_pd1(const StepArgs* __restric
         scnt[i] = 0;
         hcur[i] = sp.cnt[hs][(size_t)c * HIST_S + i];
     }
-    // window coordinate of a deposit at row j, column x: j - shs[x].  After a
-    // re-sorting step the layout is ordered by the keys of the previous state,
-    // so the window follows the chunk's key range and removes the drift of
-    // both steps; otherwise it is placed from the histogram of current keys
-    // and removes this step's drift.
-    const bool two_step = push && ctl->prev_sorted[s];
+    // window coordinate of a deposit at row j, column x: j - shs[x], which
+    // removes this step's drift
     const int ssel = ctl->shsel[s];
-    for (int i = threadIdx.x; i < nx; i += PD_THREADS)
-        shs[i] = push ? sp.shift[ssel][i] + (two_step ? sp.shift[1 - ssel][i] : 0) : 0;
+    for (int i = threadIdx.x; i < nx; i += PD_THREADS) shs[i] = push ? sp.shift[ssel][i] : 0;
     __syncthreads();
     if (threadIdx.x == 0) {
-        const int r0 = two_step ? kb - HALO : best_window(hcur, kbase, W, nullptr);
+        const int r0 = best_window(hcur, kbase, W, nullptr);
         misc[2] = r0;
         sp.wrow0[c] = r0;
         if (use_bulk) {
@@ -497,21 +576,14 @@ __global__ void __launch_bounds__(PD_THREADS, 2) k_pd1(const StepArgs* __restric
     const T qm_dt = (T)sp.qm_dt;
     const T dt_dx = (T)sp.dt_dx;
     const T vref_dtdx = (T)((sp.vmin[0] + (double)kb * sp.dv[0]) * sp.dt_dx);
-    const T dvk = (T)sp.dv[0];
     double* ovf_num = sp.ovf;
     double* ovf_den = sp.ovf + (size_t)nv * nx;
     int* ovf_tag = sp.ovf_tag;
     const int tag = (int)ctl->step + 1;
     T* dvp = reinterpret_cast<T*>(sp.mv[cb][0]);
     const T* fp = reinterpret_cast<const T*>(sp.mf[cb]);
-    const int nb = sorted_write ? 1 - cb : cb;
-    T* dvp_out = reinterpret_cast<T*>(sp.mv[nb][0]);
-    T* fp_out = reinterpret_cast<T*>(sp.mf[nb]);
-    const int* offs = sp.offs + (size_t)c * HIST_S;
-    const int* kb_new = sp.KB[1 - cb];
-    int* cnt_next = sp.cnt[1 - hs];
     int* far_next = sp.far_cnt[1 - hs];
-    unsigned n_over = 0, n_bad = 0;
+    unsigned n_over = 0;
 
     for (int base = beg; base < end; base += PD_THREADS * MPT) {
         const int g0 = base + threadIdx.x * MPT;
@@ -537,15 +609,6 @@ __global__ void __launch_bounds__(PD_THREADS, 2) k_pd1(const StepArgs* __restric
 #pragma unroll
                 for (int m = 0; m < MPT; ++m) pos8[m].xi = x8[m];
             }
-        }
-        // slots in the re-sorted layout, keyed by the current state
-        int dst[MPT];
-        if (sorted_write) {
-            int code[MPT];
-#pragma unroll
-            for (int m = 0; m < MPT; ++m)
-                code[m] = (g0 + m < end) ? rel_code(key_rel(dv8[m], kb, inv_dv, nv), kbase) : -1;
-            assign_slots(code, scnt, offs, sp.far_cur, dst);
         }
         Run<T> run;
         run.reset(0x7fffffff, 0);
@@ -589,100 +652,38 @@ __global__ void __launch_bounds__(PD_THREADS, 2) k_pd1(const StepArgs* __restric
         if (have)
             n_over += flush_run<T>(run, win, plane, row0, W, nx, nv, shs, ovf_num, ovf_den, ovf_tag, tag) ? 1u : 0u;
         if (!push) continue;
-        if (!sorted_write) {
-            // in place: the positions and velocities go back where they came
-            // from; the new keys are counted for this chunk
-            if (any) {
-                storeg(dvp_out + g0, dv8);
-                if constexpr (sizeof(T) == 4) {
-                    int c8[MPT];
-                    float o8[MPT];
-#pragma unroll
-                    for (int m = 0; m < MPT; ++m) {
-                        c8[m] = pos8[m].c;
-                        o8[m] = pos8[m].o;
-                    }
-                    storeg(reinterpret_cast<int*>(sp.mx[nb]) + g0, c8);
-                    storeg(sp.moff[nb] + g0, o8);
-                } else {
-                    double x8[MPT];
-#pragma unroll
-                    for (int m = 0; m < MPT; ++m) x8[m] = pos8[m].xi;
-                    storeg(reinterpret_cast<double*>(sp.mx[nb]) + g0, x8);
-                }
-            }
-#pragma unroll
-            for (int m = 0; m < MPT; ++m) {
-                const bool ok = g0 + m < end;
-                const int code = ok ? rel_code(key_rel(dv8[m], kb, inv_dv, nv), kbase) : 0;
-                hist_add(scnt, far_next, code, ok);
-            }
-        } else {
-            // re-sorted: every marker goes to its slot with the velocity
-            // re-referenced to the target chunk; the new key is counted for
-            // the target chunk from exactly the stored values
-            T dvo[MPT];
-            int gcode[MPT];
-#pragma unroll
-            for (int m = 0; m < MPT; ++m) {
-                const int d = dst[m];
-                const bool ok = (g0 + m < end) && ((unsigned)d < (unsigned)n_all);
-                const int c2 = ok ? chunk_of(d, sp.div_m, sp.div_l) : c;
-                const int kb2 = kb_new[c2];
-                dvo[m] = dv8[m] + (T)(kb - kb2) * dvk;
-                const int key = key_rel(dvo[m], kb2, inv_dv, nv);
-                const int r2 = key - (kb2 - HIST_R);
-                gcode[m] = (r2 >= 0 && r2 < HIST_S) ? c2 * HIST_S + r2 : -(key + 1);
-            }
-            bool vec = any && (g0 + MPT <= end) && (dst[0] % MPT == 0) && ((unsigned)dst[0] + MPT <= (unsigned)n_all);
-#pragma unroll
-            for (int m = 1; m < MPT; ++m) vec = vec && (dst[m] == dst[0] + m);
-            if (vec) {
-                const int d0 = dst[0];
-                storeg(dvp_out + d0, dvo);
-                storeg(fp_out + d0, f8);
-                if constexpr (sizeof(T) == 4) {
-                    int c8[MPT];
-                    float o8[MPT];
-#pragma unroll
-                    for (int m = 0; m < MPT; ++m) {
-                        c8[m] = pos8[m].c;
-                        o8[m] = pos8[m].o;
-                    }
-                    storeg(reinterpret_cast<int*>(sp.mx[nb]) + d0, c8);
-                    storeg(sp.moff[nb] + d0, o8);
-                } else {
-                    double x8[MPT];
-#pragma unroll
-                    for (int m = 0; m < MPT; ++m) x8[m] = pos8[m].xi;
-                    storeg(reinterpret_cast<double*>(sp.mx[nb]) + d0, x8);
-                }
-            } else if (any) {
+        // in place: the positions and velocities go back where they came
+        // from; the new keys are counted for this chunk
+        if (any) {
+            storeg(dvp + g0, dv8);
+            if constexpr (sizeof(T) == 4) {
+                int c8[MPT];
+                float o8[MPT];
 #pragma unroll
                 for (int m = 0; m < MPT; ++m) {
-                    if (g0 + m >= end) continue;
-                    const int d = dst[m];
-                    if ((unsigned)d < (unsigned)n_all) {
-                        pos8[m].store(sp, nb, d);
-                        dvp_out[d] = dvo[m];
-                        fp_out[d] = f8[m];
-                    } else {
-                        ++n_bad;
-                    }
+                    c8[m] = pos8[m].c;
+                    o8[m] = pos8[m].o;
                 }
-            }
+                storeg(reinterpret_cast<int*>(sp.mx[cb]) + g0, c8);
+                storeg(sp.moff[cb] + g0, o8);
+            } else {
+                double x8[MPT];
 #pragma unroll
-            for (int m = 0; m < MPT; ++m) {
-                const bool ok = (g0 + m < end) && ((unsigned)dst[m] < (unsigned)n_all);
-                ghist_add(cnt_next, far_next, gcode[m], ok);
+                for (int m = 0; m < MPT; ++m) x8[m] = pos8[m].xi;
+                storeg(reinterpret_cast<double*>(sp.mx[cb]) + g0, x8);
             }
+        }
+#pragma unroll
+        for (int m = 0; m < MPT; ++m) {
+            const bool ok = g0 + m < end;
+            const int code = ok ? rel_code(key_rel(dv8[m], kb, inv_dv, nv), kbase) : 0;
+            hist_add(scnt, far_next, code, ok);
         }
     }
     if (n_over) atomicAdd(&misc[0], (int)n_over);
-    if (n_bad) atomicAdd(&misc[1], (int)n_bad);
     __syncthreads();
-    if (push && !sorted_write)
-        for (int i = threadIdx.x; i < HIST_S; i += PD_THREADS) cnt_next[(size_t)c * HIST_S + i] = scnt[i];
+    if (push)
+        for (int i = threadIdx.x; i < HIST_S; i += PD_THREADS) sp.cnt[1 - hs][(size_t)c * HIST_S + i] = scnt[i];
     // flush the window to this chunk's partial sums with one bulk copy
     if (threadIdx.x == 0) {
         fence_proxy_async_smem();
@@ -690,7 +691,6 @@ __global__ void __launch_bounds__(PD_THREADS, 2) k_pd1(const StepArgs* __restric
         bulk_s2g(dstp, winb, (unsigned)win_bytes);
         bulk_commit();
         if (misc[0]) atomicAdd(&ctl->ovf_count[s], (unsigned long long)misc[0]);
-        if (misc[1]) atomicOr(&ctl->err, ERR_CAPACITY);
         bulk_wait_all();
     }
 }
@@ -795,11 +795,10 @@ __global__ void __launch_bounds__(FIN_THREADS) k_fin1(const StepArgs* __restrict
     // windows are stored shifted by shift[x] per column; all_species marks a
     // refresh, whose deposit used no shift)
     const bool shifted = !all_species && sp.mobile;
-    const bool two_step = shifted && ctl->prev_sorted[s];
     const int ssel = ctl->shsel[s];
-    const int smin = shifted ? ctl->shift_min[s][ssel] + (two_step ? ctl->shift_min[s][1 - ssel] : 0) : 0;
-    const int smax = shifted ? ctl->shift_max[s][ssel] + (two_step ? ctl->shift_max[s][1 - ssel] : 0) : 0;
-    const int shx = (shifted && xok) ? sp.shift[ssel][x] + (two_step ? sp.shift[1 - ssel][x] : 0) : 0;
+    const int smin = shifted ? ctl->shift_min[s][ssel] : 0;
+    const int smax = shifted ? ctl->shift_max[s][ssel] : 0;
+    const int shx = (shifted && xok) ? sp.shift[ssel][x] : 0;
     if (threadIdx.x == 0) ncl = 0;
     __syncthreads();
     if (threadIdx.x < 32) {
@@ -1108,12 +1107,20 @@ cudaError_t launch_pd1_batch(int prec, const BatchMap* bm, int blocks, int smem,
 {
     if (blocks == 0) return cudaSuccess;
     if (prec == AVL_FP32) {
-        k_pd1<float, false, true><<<blocks, PD_THREADS, smem, st>>>(nullptr, mode, bm);
-        if (mode == 1) k_pd1<float, true, true><<<blocks, PD_THREADS, smem, st>>>(nullptr, mode, bm);
+        k_pd1<float, true><<<blocks, PD_THREADS, smem, st>>>(nullptr, mode, bm);
     } else {
-        k_pd1<double, false, true><<<blocks, PD_THREADS, smem, st>>>(nullptr, mode, bm);
-        if (mode == 1) k_pd1<double, true, true><<<blocks, PD_THREADS, smem, st>>>(nullptr, mode, bm);
+        k_pd1<double, true><<<blocks, PD_THREADS, smem, st>>>(nullptr, mode, bm);
     }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rs1_batch(int prec, const BatchMap* bm, int blocks, cudaStream_t st)
+{
+    if (blocks == 0) return cudaSuccess;
+    if (prec == AVL_FP32)
+        k_rs1<float, true><<<blocks, PD_THREADS, 0, st>>>(nullptr, bm);
+    else
+        k_rs1<double, true><<<blocks, PD_THREADS, 0, st>>>(nullptr, bm);
     return cudaGetLastError();
 }
 
@@ -1143,10 +1150,8 @@ template <typename T>
 static cudaError_t set_pd1_limit_t(int smem)
 {
     cudaError_t e;
-    if ((e = raise_smem_limit(k_pd1<T, false, false>, smem))) return e;
-    if ((e = raise_smem_limit(k_pd1<T, true, false>, smem))) return e;
-    if ((e = raise_smem_limit(k_pd1<T, false, true>, smem))) return e;
-    return raise_smem_limit(k_pd1<T, true, true>, smem);
+    if ((e = raise_smem_limit(k_pd1<T, false>, smem))) return e;
+    return raise_smem_limit(k_pd1<T, true>, smem);
 }
 
 static cudaError_t set_pd1_limit(int prec, int smem)
@@ -1178,12 +1183,20 @@ cudaError_t launch_pd1(const StepArgs& h, const StepArgs* d, int mode, cudaStrea
     if (h.nchunk_total == 0) return cudaSuccess;
     const int smem = max_pd_smem(h);
     if (h.prec == AVL_FP32) {
-        k_pd1<float, false, false><<<h.nchunk_total, PD_THREADS, smem, st>>>(d, mode, nullptr);
-        if (mode == 1) k_pd1<float, true, false><<<h.nchunk_total, PD_THREADS, smem, st>>>(d, mode, nullptr);
+        k_pd1<float, false><<<h.nchunk_total, PD_THREADS, smem, st>>>(d, mode, nullptr);
     } else {
-        k_pd1<double, false, false><<<h.nchunk_total, PD_THREADS, smem, st>>>(d, mode, nullptr);
-        if (mode == 1) k_pd1<double, true, false><<<h.nchunk_total, PD_THREADS, smem, st>>>(d, mode, nullptr);
+        k_pd1<double, false><<<h.nchunk_total, PD_THREADS, smem, st>>>(d, mode, nullptr);
     }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rs1(const StepArgs& h, const StepArgs* d, cudaStream_t st)
+{
+    if (h.nchunk_total == 0) return cudaSuccess;
+    if (h.prec == AVL_FP32)
+        k_rs1<float, false><<<h.nchunk_total, PD_THREADS, 0, st>>>(d, nullptr);
+    else
+        k_rs1<double, false><<<h.nchunk_total, PD_THREADS, 0, st>>>(d, nullptr);
     return cudaGetLastError();
 }
 

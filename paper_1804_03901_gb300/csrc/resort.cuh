@@ -152,4 +152,26 @@ static __device__ void scan_layout(const SpDev& sp, const int* __restrict__ kref
     __syncthreads();
 }
 
+// Key histograms of the chunks of a layout sorted by key, from the first
+// slot of every key (base_new, written by scan_layout): cnt_out[c][r] = the
+// slots of chunk c ([c M, (c + 1) M)) that hold key kb_new[c] - HIST_R + r.
+// Called by a whole block after scan_layout.
+static __device__ void sorted_chunk_hist(const SpDev& sp, const int* __restrict__ kb_new, int* __restrict__ cnt_out)
+{
+    const int nv = sp.nvflat;
+    const long long total = (long long)sp.nchunk * HIST_S;
+    for (long long i = threadIdx.x; i < total; i += blockDim.x) {
+        const int c = (int)(i / HIST_S), r = (int)(i % HIST_S);
+        const int k = kb_new[c] - HIST_R + r;
+        int n = 0;
+        if (k >= 0 && k < nv) {
+            const long long lo = max((long long)sp.base_new[k], (long long)c * sp.M);
+            const long long hi = min((long long)sp.base_new[k + 1], min((long long)(c + 1) * sp.M, sp.n));
+            n = hi > lo ? (int)(hi - lo) : 0;
+        }
+        cnt_out[i] = n;
+    }
+    __syncthreads();
+}
+
 }  // namespace avl
