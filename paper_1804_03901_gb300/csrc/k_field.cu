@@ -133,66 +133,134 @@ __device__ void poisson_spectral(double* rho_s, double2* work, double* Eout, int
     }
 }
 
-// After a step: CTA 1 of the field cluster decides, per mobile species,
-// whether the next step re-sorts its markers before the push (when the field
-// drifts markers a row or more, or the best deposit windows of the chunks,
-// placed from the key counts of the new state, would miss more than a small
-// fraction of the markers) and if so prepares the slots and the key
-// histograms of the re-sorted chunks; CTAs 2.. clear the key counts consumed
-// by this step for reuse.
+// Markers a chunk's best deposit window holds: the largest sum of wk
+// consecutive bins of its HIST_S-bin key histogram (the window best_window
+// places).  Called by a whole warp; one coalesced load and a warp scan.
+__device__ int best_cover_warp(const int* __restrict__ hist, int wk)
+{
+    static_assert(HIST_S == 64, "two bins per lane");
+    const int lane = threadIdx.x & 31;
+    const int2 h = reinterpret_cast<const int2*>(hist)[lane];
+    int S = h.x + h.y;   // inclusive prefix of the bin pairs over the lanes
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, S, o);
+        if (lane >= o) S += y;
+    }
+    // P(i) = sum of bins [0, i): P(2 l + 2) = S(l), P(2 l + 1) = S(l) - h.y(l)
+    auto P = [&](int i) {
+        const int src = max(i - 1, 0) >> 1;
+        const int Ss = __shfl_sync(0xffffffffu, S, src);
+        const int hy = __shfl_sync(0xffffffffu, h.y, src);
+        return i == 0 ? 0 : ((i & 1) ? Ss - hy : Ss);
+    };
+    int best = 0;
+    for (int q = 0; q < 2; ++q) {
+        const int r = 2 * lane + q;
+        const int a = P(r), b = P(min(r + wk, HIST_S));
+        if (r + wk <= HIST_S) best = max(best, b - a);
+    }
+    return __reduce_max_sync(0xffffffffu, best);
+}
+
+constexpr int FIELD_DECIDE = FIELD_CLUSTER - 2;   // CTAs 1 .. FIELD_DECIDE decide the re-sorts
+constexpr int FIELD_DIAG = FIELD_CLUSTER - 1;     // the last CTA sums the diagnostics
+
+// After a step: CTA 1 + (s mod FIELD_DECIDE) of the field cluster decides,
+// for mobile species s, whether the next step re-sorts its markers before
+// the push (when the field drifts markers a row or more, or the best deposit
+// windows of the chunks, placed from the key counts of the new state, would
+// miss more than a small fraction of the markers) and if so prepares the
+// slots and the key histograms of the re-sorted chunks; then CTAs 1.. clear
+// the key counts consumed by this step for reuse.
 __device__ void resort_work(const StepArgs* __restrict__ A, int rank)
 {
     const Ctl* ctl = A->ctl;
-    for (int s = 0; s < A->ns; ++s) {
+    __shared__ unsigned long long miss;
+    for (int s = rank - 1; rank <= FIELD_DECIDE && s < A->ns; s += FIELD_DECIDE) {
         const SpDev& sp = A->sp[s];
         const int hs = ctl->hsel[s];
         if (!sp.mobile || sp.nchunk == 0) continue;
-        if (rank == 1) {
-            const int cur_after = ctl->sort_now[s] ? 1 - ctl->cur[s] : ctl->cur[s];
-            const int* kref = sp.KB[cur_after];
-            const int* cnt = sp.cnt[1 - hs];
-            const int* far = sp.far_cnt[1 - hs];
-            // markers outside the best window of their chunk
-            __shared__ unsigned long long miss;
-            if (threadIdx.x == 0) miss = 0;
-            __syncthreads();
-            unsigned long long my = 0;
-            for (int c = threadIdx.x; c < sp.nchunk; c += blockDim.x) {
-                int covered = 0;
-                best_window(cnt + (size_t)c * HIST_S, kref[c] - HIST_R, sp.Wmax, &covered);
-                const int beg = c * sp.M;
-                const int end = (int)min((long long)(c + 1) * sp.M, sp.n);
-                my += (unsigned long long)((end - beg) - covered);
-            }
-            atomicAdd(&miss, my);
-            __syncthreads();
-            // rows this step's field drifts markers (its table is not the one
-            // CTA 0 is rewriting now); at a row or more, re-sort every step
-            const int ssel = ctl->shsel[s];
-            const int drift = max(abs(ctl->shift_min[s][ssel]), abs(ctl->shift_max[s][ssel]));
-            const bool resort = (A->fd.resort_drift && drift >= 1) ||
-                                miss * (unsigned long long)A->fd.resort_miss > (unsigned long long)sp.n;
-            if (threadIdx.x == 0) {
-                Ctl* cw = A->ctl;
-                cw->uncovered[s] = miss;
-                cw->sort_next[s] = resort ? 1 : 0;
-            }
-            if (resort) {
-                scan_layout(sp, kref, cnt, far, true, sp.KB[1 - cur_after]);
-                // the next step deposits from the re-sorted layout: its window
-                // placement takes the key histograms of the re-sorted chunks
-                sorted_chunk_hist(sp, sp.KB[1 - cur_after], sp.cnt[1 - hs]);
-            }
-            __syncthreads();
-        } else {
-            // clear cnt[hs] and far_cnt[hs] for the next step's counting
-            const int nclr = FIELD_CLUSTER - 2;
-            const int r = rank - 2;
-            const size_t ncnt = (size_t)sp.nchunk * HIST_S;
-            for (size_t i = (size_t)r * blockDim.x + threadIdx.x; i < ncnt; i += (size_t)nclr * blockDim.x)
-                sp.cnt[hs][i] = 0;
-            for (int i = r * blockDim.x + threadIdx.x; i < sp.nvflat; i += nclr * blockDim.x) sp.far_cnt[hs][i] = 0;
+        const int cur_after = ctl->sort_now[s] ? 1 - ctl->cur[s] : ctl->cur[s];
+        const int* kref = sp.KB[cur_after];
+        const int* cnt = sp.cnt[1 - hs];
+        const int* far = sp.far_cnt[1 - hs];
+        // markers outside the best window of their chunk (a warp per chunk)
+        if (threadIdx.x == 0) miss = 0;
+        __syncthreads();
+        const int wk = max(1, min(HIST_S, sp.Wmax - 2 * HALO - 1));
+        unsigned long long my = 0;
+        for (int c = threadIdx.x >> 5; c < sp.nchunk; c += FIELD_THREADS / 32) {
+            const int covered = best_cover_warp(cnt + (size_t)c * HIST_S, wk);
+            const int beg = c * sp.M;
+            const int end = (int)min((long long)(c + 1) * sp.M, sp.n);
+            if ((threadIdx.x & 31) == 0) my += (unsigned long long)((end - beg) - covered);
         }
+        if (my) atomicAdd(&miss, my);
+        __syncthreads();
+        // rows this step's field drifts markers (its table is not the one
+        // CTA 0 is rewriting now); at a row or more, re-sort every step
+        const int ssel = ctl->shsel[s];
+        const int drift = max(abs(ctl->shift_min[s][ssel]), abs(ctl->shift_max[s][ssel]));
+        const bool resort = (A->fd.resort_drift && drift >= 1) ||
+                            miss * (unsigned long long)A->fd.resort_miss > (unsigned long long)sp.n;
+        if (threadIdx.x == 0) {
+            Ctl* cw = A->ctl;
+            cw->uncovered[s] = miss;
+            cw->sort_next[s] = resort ? 1 : 0;
+        }
+        if (resort) {
+            scan_layout(sp, kref, cnt, far, true, sp.KB[1 - cur_after]);
+            // the next step deposits from the re-sorted layout: its window
+            // placement takes the key histograms of the re-sorted chunks
+            sorted_chunk_hist(sp, sp.KB[1 - cur_after], sp.cnt[1 - hs]);
+        }
+        __syncthreads();
+    }
+    // clear cnt[hs] and far_cnt[hs] of every species for the next step's counting
+    const int nclr = FIELD_CLUSTER - 1;
+    const int r = rank - 1;
+    for (int s = 0; s < A->ns; ++s) {
+        const SpDev& sp = A->sp[s];
+        if (!sp.mobile || sp.nchunk == 0) continue;
+        const int hs = ctl->hsel[s];
+        const size_t ncnt = (size_t)sp.nchunk * HIST_S;
+        for (size_t i = (size_t)r * blockDim.x + threadIdx.x; i < ncnt; i += (size_t)nclr * blockDim.x)
+            sp.cnt[hs][i] = 0;
+        for (int i = r * blockDim.x + threadIdx.x; i < sp.nvflat; i += nclr * blockDim.x) sp.far_cnt[hs][i] = 0;
+    }
+}
+
+// per-species sums of the finalize blocks' diagnostics (N, W_kin, S; fixed
+// order per thread, then over the warps) into out[3 s + q] (CTA 0's shared
+// memory); called by the whole block of CTA FIELD_DIAG
+__device__ void diag_sums(const StepArgs* __restrict__ A, double* out)
+{
+    __shared__ double dsum[3 * MAXS][FIELD_THREADS / 32];
+    const int ns = A->ns;
+    for (int s = 0; s < ns; ++s) {
+        const SpDev& sp = A->sp[s];
+        double N = 0.0, Wk = 0.0, S = 0.0;
+        for (int k = threadIdx.x; k < sp.nfin; k += FIELD_THREADS) {
+            N += sp.dpart[(size_t)k * 4 + 0];
+            Wk += sp.dpart[(size_t)k * 4 + 1];
+            S += sp.dpart[(size_t)k * 4 + 2];
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            N += __shfl_down_sync(0xffffffffu, N, o);
+            Wk += __shfl_down_sync(0xffffffffu, Wk, o);
+            S += __shfl_down_sync(0xffffffffu, S, o);
+        }
+        if ((threadIdx.x & 31) == 0) {
+            dsum[3 * s + 0][threadIdx.x >> 5] = N;
+            dsum[3 * s + 1][threadIdx.x >> 5] = Wk;
+            dsum[3 * s + 2][threadIdx.x >> 5] = S;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < 3 * ns) {
+        double v = 0.0;
+        for (int w = 0; w < FIELD_THREADS / 32; ++w) v += dsum[threadIdx.x][w];
+        out[threadIdx.x] = v;
     }
 }
 
@@ -209,6 +277,7 @@ __global__ void __cluster_dims__(FIELD_CLUSTER, 1, 1) __launch_bounds__(FIELD_TH
     double* rho_s = reinterpret_cast<double*>(smem);                 // nx
     double2* work = reinterpret_cast<double2*>(smem + ((size_t)nx * 8 + 15) / 16 * 16);   // nx/2 + 1
     __shared__ double red[FIELD_THREADS / 32];
+    __shared__ double dfin[3 * MAXS];   // per-species diagnostics sums (written by CTA FIELD_DIAG)
 
     // --- rho slice: sum over species and row blocks (fixed order) --------
     double* rho0 = cluster.map_shared_rank(rho_s, 0);
@@ -224,6 +293,7 @@ __global__ void __cluster_dims__(FIELD_CLUSTER, 1, 1) __launch_bounds__(FIELD_TH
     }
     cluster.sync();
     if (rank != 0) {
+        if (rank == FIELD_DIAG) diag_sums(A, cluster.map_shared_rank(dfin, 0));
         if (count_step) resort_work(A, rank);
         cluster.sync();
         return;
@@ -289,42 +359,25 @@ __global__ void __cluster_dims__(FIELD_CLUSTER, 1, 1) __launch_bounds__(FIELD_TH
             }
         }
     }
-    // per-species sums of the finalize blocks' diagnostics (fixed order per thread)
-    __shared__ double dsum[3 * MAXS][FIELD_THREADS / 32];
-    const int ns = A->ns;
-    for (int s = 0; s < ns; ++s) {
-        const SpDev& sp = A->sp[s];
-        double N = 0.0, Wk = 0.0, S = 0.0;
-        for (int k = threadIdx.x; k < sp.nfin; k += FIELD_THREADS) {
-            N += sp.dpart[(size_t)k * 4 + 0];
-            Wk += sp.dpart[(size_t)k * 4 + 1];
-            S += sp.dpart[(size_t)k * 4 + 2];
-        }
-        for (int o = 16; o > 0; o >>= 1) {
-            N += __shfl_down_sync(0xffffffffu, N, o);
-            Wk += __shfl_down_sync(0xffffffffu, Wk, o);
-            S += __shfl_down_sync(0xffffffffu, S, o);
-        }
-        if ((threadIdx.x & 31) == 0) {
-            dsum[3 * s + 0][threadIdx.x >> 5] = N;
-            dsum[3 * s + 1][threadIdx.x >> 5] = Wk;
-            dsum[3 * s + 2][threadIdx.x >> 5] = S;
-        }
-    }
     __syncthreads();
+    __shared__ double WE_s;
     if (threadIdx.x == 0) {
         double s2 = 0.0;
         for (int w = 0; w < FIELD_THREADS / 32; ++w) s2 += red[w];
-        const double WE = s2 * fd.dx / (2.0 * fd.cP);
+        WE_s = s2 * fd.dx / (2.0 * fd.cP);
+    }
+    // wait for the diagnostics sums, the re-sort decisions and the clearing by
+    // the other CTAs, then write the diagnostics row and make this step's
+    // markers and key counts current
+    cluster.sync();
+    if (threadIdx.x == 0) {
+        Ctl* ctl = A->ctl;
+        const int ns = A->ns;
+        const double WE = WE_s;
         double wk_tot = 0.0;
         bool bad = !isfinite(WE);
         for (int s = 0; s < ns; ++s) {
-            double N = 0.0, Wk = 0.0, S = 0.0;
-            for (int w = 0; w < FIELD_THREADS / 32; ++w) {
-                N += dsum[3 * s + 0][w];
-                Wk += dsum[3 * s + 1][w];
-                S += dsum[3 * s + 2][w];
-            }
+            const double N = dfin[3 * s + 0], Wk = dfin[3 * s + 1], S = dfin[3 * s + 2];
             fd.diag[3 + s] = Wk;
             fd.diag[3 + ns + s] = N;
             fd.diag[3 + 2 * ns + s] = S;
@@ -334,18 +387,11 @@ __global__ void __cluster_dims__(FIELD_CLUSTER, 1, 1) __launch_bounds__(FIELD_TH
         fd.diag[0] = WE;
         fd.diag[1] = wk_tot;
         fd.diag[2] = WE + wk_tot;
-        Ctl* ctl = A->ctl;
         if (bad) ctl->err |= ERR_NUMERIC;
         for (int s = 0; s < ns; ++s) {
             ctl->ovf_last[s] = ctl->ovf_count[s];
             ctl->ovf_count[s] = 0;
         }
-    }
-    // wait for the re-sort decision of CTA 1 and the clearing by the others,
-    // then make this step's markers and key counts current
-    cluster.sync();
-    if (threadIdx.x == 0) {
-        Ctl* ctl = A->ctl;
         for (int s = 0; s < ns; ++s) {
             const SpDev& sp = A->sp[s];
             if (sp.nvdim == 3) {
