@@ -59,6 +59,10 @@ def compare_grids(sim, orc, tol, what=""):
     rho, E = sim.get_rho(), sim.get_E()
     assert rel(rho, orc.rho) < tol, (what, "rho", rel(rho, orc.rho))
     assert rel(E, orc.E) < tol, (what, "E", rel(E, orc.E))
+    # diagnostics (Sec. 3.4.1): W_E, W_kin, W_total, per species W_kin, N, S
+    d, do = sim.get_diag(), orc.diag()
+    err = np.abs(d - do) / np.maximum(np.abs(do), 1e-300)
+    assert np.all(err < tol), (what, "diag", err)
 
 
 def compare_markers(sim, orc, tol_x, tol_v, L):
