@@ -24,6 +24,8 @@
 //   mu   += sum_cells A alpha;  g = sum_cells (A f - B) d alpha / d(X, V)
 //   lambda_X = lambda_X + lt (q/m) dt dE/dx(X^n) + g_X;  lambda_V = lt + g_V
 // The cloud-in-cell derivatives are the one-sided ones of the floor() rule.
+// Per-marker and per-cell arithmetic runs in the storage precision (FP64 is a
+// small fraction of the FP32 rate on this GPU); mu, the charge and E stay FP64.
 #include <math.h>
 
 #include <algorithm>
@@ -102,17 +104,24 @@ struct APos<double> {
     }
 };
 
-// velocity dual row j0 and weight w of row j0 + 1 (t = (v - vmin)/dv - 1/2)
+// velocity dual row j0 and weight w of row j0 + 1 (t = (v - vmin)/dv - 1/2),
+// in the storage precision with one explicit fused multiply-add, so that
+// the deposit and the gather find the same row and weight
 template <typename T>
 __device__ __forceinline__ int vrow(T v, const SpDev& sp, T& w)
 {
-    const double t = ((double)v - sp.vmin[0]) * sp.inv_dv[0] - 0.5;
-    if (!(t > -2.0 && t < (double)sp.nv[0] + 1.0)) {
+    const T a = (T)sp.inv_dv[0], b = (T)(-sp.vmin[0] * sp.inv_dv[0] - 0.5);
+    T t;
+    if constexpr (sizeof(T) == 4)
+        t = __fmaf_rn(v, a, b);
+    else
+        t = __fma_rn(v, a, b);
+    if (!(t > (T)-2 && t < (T)(sp.nv[0] + 1))) {
         w = (T)0;
-        return t > 0 ? sp.nv[0] + 1 : -2;
+        return t > (T)0 ? sp.nv[0] + 1 : -2;
     }
-    const double fl = floor(t);
-    w = (T)(t - fl);
+    const T fl = floor(t);
+    w = t - fl;
     return (int)fl;
 }
 
@@ -294,8 +303,8 @@ __global__ void __launch_bounds__(256) k_ad_e(const StepArgs* __restrict__ A, co
     S* ew = copies ? es + ((threadIdx.x >> 5) % copies) * nx : nullptr;
     const T* lx = reinterpret_cast<const T*>(a.lx);
     const T* lv = reinterpret_cast<const T*>(a.lv);
-    const double c0 = sp.qm_dt;
-    const double dt = sp.dt_dx * sp.dx;
+    const T c0 = (T)sp.qm_dt;
+    const T dt = (T)(sp.dt_dx * sp.dx);
     for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < a.n; k += (long long)gridDim.x * blockDim.x) {
         const Pos<T> p = APos<T>::load(a, slot, k);
         int i0;
@@ -303,13 +312,13 @@ __global__ void __launch_bounds__(256) k_ad_e(const StepArgs* __restrict__ A, co
         p.cic(i0, w);
         int ia, ib;
         wrap_pair(i0, nx, ia, ib);
-        const double c = ((double)lv[k] + dt * (double)lx[k]) * c0;
+        const T c = (lv[k] + dt * lx[k]) * c0;
         if (copies) {
-            atomicAdd(ew + ia, (S)(c * (1.0 - (double)w)));
-            atomicAdd(ew + ib, (S)(c * (double)w));
+            atomicAdd(ew + ia, (S)(c * ((T)1 - w)));
+            atomicAdd(ew + ib, (S)(c * w));
         } else {   // grid too large for shared copies
-            atomicAdd(D->e + ia, c * (1.0 - (double)w));
-            atomicAdd(D->e + ib, c * (double)w);
+            atomicAdd(D->e + ia, (double)(c * ((T)1 - w)));
+            atomicAdd(D->e + ib, (double)(c * w));
         }
     }
     __syncthreads();
@@ -335,11 +344,11 @@ __global__ void k_ad_grid(const StepArgs* __restrict__ A, const AdjDev* __restri
     T* ab = reinterpret_cast<T*>(a.AB);
     const double psi_c = -sp.q * sp.dv[0];
     for (size_t o = (size_t)blockIdx.x * blockDim.x + threadIdx.x; o < cells; o += (size_t)gridDim.x * blockDim.x) {
-        const double d = (double)Dg[o];
-        const double ps = psi_c * D->tmp[o % nx];
-        const bool ok = d > 0.0;
-        ab[2 * o] = ok ? (T)(ps / d) : (T)0;
-        ab[2 * o + 1] = ok ? (T)(ps * (double)F[o] / d) : (T)0;
+        const T d = Dg[o];
+        const T ps = (T)(psi_c * D->tmp[o % nx]);
+        const T A_ = d > (T)0 ? ps / d : (T)0;
+        ab[2 * o] = A_;
+        ab[2 * o + 1] = A_ * F[o];
     }
 }
 
@@ -358,7 +367,8 @@ __global__ void k_ad_gather(const StepArgs* __restrict__ A, const AdjDev* __rest
     T* lx = reinterpret_cast<T*>(a.lx);
     T* lv = reinterpret_cast<T*>(a.lv);
     const T idx_ = (T)(1.0 / sp.dx), idv = (T)sp.inv_dv[0];
-    const double dt = sp.dt_dx * sp.dx;
+    const T dt = (T)(sp.dt_dx * sp.dx);
+    const T qm_dt = (T)sp.qm_dt;
     for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < a.n; k += (long long)gridDim.x * blockDim.x) {
         const Pos<T> p = APos<T>::load(a, slot, k);
         int i0;
@@ -389,13 +399,14 @@ __global__ void k_ad_gather(const StepArgs* __restrict__ A, const AdjDev* __rest
         }
         a.mu[k] += (double)m;
         if (terminal) {
-            lx[k] = (T)gx;
-            lv[k] = (T)gv;
+            lx[k] = gx;
+            lv[k] = gv;
         } else if (sp.mobile) {
-            const double lt = (double)lv[k] + dt * (double)lx[k];
-            const double dEdx = (E[ib] - E[ia]) / sp.dx;
-            lx[k] = (T)((double)lx[k] + lt * sp.qm_dt * dEdx + (double)gx);
-            lv[k] = (T)(lt + (double)gv);
+            const T lxk = lx[k];
+            const T lt = lv[k] + dt * lxk;
+            const T dEdx = (T)(E[ib] - E[ia]) * idx_;
+            lx[k] = lxk + lt * (qm_dt * dEdx) + gx;
+            lv[k] = lt + gv;
         }
     }
 }
