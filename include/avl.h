@@ -284,10 +284,9 @@ avl_status avl_autotune(avl_ctx* ctx, int32_t trial_steps, int32_t* chunk_out);
 /* Per-kernel timing (the paper's time breakdown, Sec. 3.2): advance nsteps
  * steps exactly as avl_step does, but launched kernel by kernel with CUDA
  * events recorded on the context stream around each kernel; writes the summed
- * milliseconds of each kernel class into ms[0..3] = {1d1v: key count + slot
- * scan, 1d3v: pencil re-sort (with a magnetic field: Boris push + global
- * re-sort); push + deposit (+ re-sorted write in 1d1v; deposit only in a
- * magnetized 1d3v step);
+ * milliseconds of each kernel class into ms[0..3] = {1d1v: re-sort scatter,
+ * 1d3v: pencil re-sort (with a magnetic field: Boris push + global
+ * re-sort); push + deposit (deposit only in a magnetized 1d3v step);
  * finalize (f, moment, diagnostics); field (Poisson)}.  Blocks until done.
  * Errors: AVL_EINVAL (nkernels < 4 or ms NULL), AVL_ESTATE as avl_step. */
 avl_status avl_profile_steps(avl_ctx* ctx, int32_t nsteps, double* ms, int32_t nkernels);

@@ -215,38 +215,32 @@ struct Planes {
     bool ok[4];
 };
 
-// the 16 cloud-in-cell contributions of one marker whose v_x dual row j is
-// not its segment's: into the ring (rows within one of the segment's) or
-// straight into the global accumulator
+// A marker whose v_x dual row j is not its segment's deposits its 16
+// cloud-in-cell contributions apart from the gather: into the ring (rows
+// within one of the segment's) or straight into the global accumulator.
+// This is one of them: corner bits x (bit 0), v_x row (bit 1), (v_y, v_z)
+// plane (bits 2-3).
 template <typename T>
-__device__ __forceinline__ void deposit_single(const Ring<T>& ring, bool to_ring, T* gacc, int cells,
-                                               const Planes& pl, int nx, int nvx, int bin, T u, int j, T w,
-                                               const T (&wq)[4], T f)
+__device__ __forceinline__ void deposit_corner(const Ring<T>& ring, bool to_ring, T* gacc, int cells, const Planes& pl,
+                                               int nx, int nvx, int bin, T u, int j, T w, T wy, T wz, T f, int corner)
 {
-#pragma unroll
-    for (int cx = 0; cx < 2; ++cx) {
-        const int x = cx ? (bin + 1 == nx ? 0 : bin + 1) : bin;
-        const T ax = cx ? u : (T)1 - u;
-#pragma unroll
-        for (int cv = 0; cv < 2; ++cv) {
-            const int row = j + cv;
-            if (row < 0 || row >= nvx) continue;
-            const T av = ax * (cv ? w : (T)1 - w);
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                if (!pl.ok[q]) continue;
-                const T a = av * wq[q];
-                if (a == (T)0) continue;
-                if (to_ring) {
-                    atomicAdd(ring.at(row, q, 0, x), a * f);
-                    atomicAdd(ring.at(row, q, 1, x), a);
-                } else {
-                    const int o = pl.base[q] + row * nx + x;
-                    atomicAdd(gacc + o, a * f);
-                    atomicAdd(gacc + cells + o, a);
-                }
-            }
-        }
+    const int cx = corner & 1, cv = (corner >> 1) & 1, q = corner >> 2;
+    const bool okq = q == 0 ? pl.ok[0] : q == 1 ? pl.ok[1] : q == 2 ? pl.ok[2] : pl.ok[3];
+    const int row = j + cv;
+    if (!okq || row < 0 || row >= nvx) return;
+    const int x = cx ? (bin + 1 == nx ? 0 : bin + 1) : bin;
+    const T ax = cx ? u : (T)1 - u;
+    const T ay = (q & 1) ? wy : (T)1 - wy, az = (q & 2) ? wz : (T)1 - wz;
+    const T a = ax * (cv ? w : (T)1 - w) * (ay * az);
+    if (a == (T)0) return;
+    if (to_ring) {
+        atomicAdd(ring.at(row, q, 0, x), a * f);
+        atomicAdd(ring.at(row, q, 1, x), a);
+    } else {
+        const int base = q == 0 ? pl.base[0] : q == 1 ? pl.base[1] : q == 2 ? pl.base[2] : pl.base[3];
+        const int o = base + row * nx + x;
+        atomicAdd(gacc + o, a * f);
+        atomicAdd(gacc + cells + o, a);
     }
 }
 
@@ -515,15 +509,16 @@ __global__ void __launch_bounds__(P3_THREADS, (sizeof(T) == 4 && CPT == 1) ? 2 :
                 for (int q = 0; q < 4; ++q) pay[(3 + q) * NB + o] = wq[q];
             }
             __syncthreads();
-            // markers off their segment's row: one per thread
-            for (int i = threadIdx.x; i < nmv; i += P3_THREADS) {
-                const int o = NB - 1 - i;
-                T wq[4];
-                plane_weights(pay[3 * NB + o], pay[4 * NB + o], wq);
+            // markers off their segment's row: one thread per (marker, corner),
+            // so that a chunk's few movers do not hold one warp behind the
+            // others at the chunk's barrier
+            for (int t = threadIdx.x; t < nmv * 16; t += P3_THREADS) {
+                const int o = NB - 1 - (t >> 4);
                 const int jx = (int)pay[6 * NB + o];
                 const int d = jx - jseg;
-                deposit_single<T>(ring, d == 1 || d == -1, gacc, cells, pl, nx, nvx, (int)pay[5 * NB + o],
-                                  pay[0 * NB + o], jx, pay[1 * NB + o], wq, pay[2 * NB + o]);
+                deposit_corner<T>(ring, d == 1 || d == -1, gacc, cells, pl, nx, nvx, (int)pay[5 * NB + o],
+                                  pay[0 * NB + o], jx, pay[1 * NB + o], pay[3 * NB + o], pay[4 * NB + o],
+                                  pay[2 * NB + o], t & 15);
             }
             // gather: column x takes weight u from the markers of dual cell
             // x - 1 and 1 - u from those of dual cell x, which follow them in
