@@ -39,10 +39,10 @@ sys.path.insert(0, ROOT)
 # ("3B": 1d3v with a magnetic field, whose push + deposit kernel deposits only)
 KERNEL_NAMES = {1: ["k_rs1", "k_pd1", "k_fin1", "k_field"],
                 3: ["k_sort3", "k_pd3", "k_fin3", "k_field"],
-                "3B": ["k_bpush3 + k_src3_scan + k_rs3_scatter", "k_pd3", "k_fin3", "k_field"]}
+                "3B": ["k_bpush3 + k_src3_tsum + k_src3_scan + k_rs3_scatter + k_src3_flip", "k_pd3", "k_fin3", "k_field"]}
 LAUNCHES_PER_STEP = {1: 4,     # k_rs1 (re-sort scatter, exits at once on other steps), k_pd1, k_fin1, k_field
                      3: 4,     # k_pd3, k_fin3, k_field, k_sort3
-                     "3B": 6}  # k_bpush3, k_src3_scan, k_rs3_scatter (one mobile species), k_pd3, k_fin3, k_field
+                     "3B": 8}  # k_bpush3, k_src3_tsum, k_src3_scan, k_rs3_scatter, k_src3_flip (one mobile species), k_pd3, k_fin3, k_field
 BYTES_PER_MARKER_ALGO = {(1, "fp32"): 20.0, (1, "fp64"): 40.0,    # 1d1v: read x, v, f; write x, v
                          (3, "fp32"): 28.0, (3, "fp64"): 56.0,    # 1d3v: read x, vx, vy, vz, f; write x, vx
                          ("3B", "fp32"): 24.0, ("3B", "fp64"): 40.0}   # deposit only: read x, v, f

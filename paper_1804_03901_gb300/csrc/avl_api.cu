@@ -271,13 +271,15 @@ avl_status plan_layout3(avl_ctx* c, int s, long long n)
         sp.seg[b] = (int*)sg;
     }
     void* kc = nullptr;
-    if (!e) e = grab(&kc, (2 * (size_t)npen * nkey + 1) * 4, true);
+    const size_t ntile = ((size_t)npen * nkey + 1023) / 1024;
+    if (!e) e = grab(&kc, (2 * (size_t)npen * nkey + ntile + 1) * 4, true);
     if (e) {
         free_layout(c, s);
         return cuda_fail(c, e, "cudaMalloc(markers)");
     }
     sp.kcount = (int*)kc;
     sp.kcur = (int*)kc + (size_t)npen * nkey;
+    sp.ktile = (int*)kc + 2 * (size_t)npen * nkey;
     sp.npen = npen;
     sp.nkey = nkey;
     sp.n = n;

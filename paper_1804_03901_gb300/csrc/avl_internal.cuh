@@ -110,6 +110,7 @@ struct SpDev {
     void* v2row;               // [nvflat] |v|^2 at the centre of every velocity cell
     int* kcount;               // [npen * nkey] bucket counts (zero between operations)
     int* kcur;                 // [npen * nkey] slot cursors of a creation or global re-sort
+    int* ktile;                // [ceil(npen * nkey / 1024)] bucket counts per scan tile
 };
 
 struct FieldDev {

@@ -26,8 +26,9 @@
 // 1d3v version) every velocity component turns, so a marker's pencil changes
 // from step to step.  The step is then: Boris push in place with the count of
 // every marker's new (pencil, key) bucket (k_bpush3), a global counting sort
-// into the other buffer (k_src3_scan, k_rs3_scatter), and the pencil deposit
-// above without a push (k_pd3 mode 2), in which no marker is off its segment.
+// into the other buffer (k_src3_tsum, k_src3_scan, k_rs3_scatter,
+// k_src3_flip), and the pencil deposit above without a push (k_pd3 mode 2),
+// in which no marker is off its segment.
 #include <math.h>
 
 #include <algorithm>
@@ -869,65 +870,83 @@ __global__ void __launch_bounds__(256) k_src3_count(const StepArgs* __restrict__
     if (nbad && bad) atomicAdd(bad, (unsigned long long)nbad);
 }
 
-// exclusive scan of the bucket counts (one block) -> slot cursors kcur and
-// the segment table of the target buffer; the counts are cleared for the
-// next use.  Creation (resort = 0) fills buffer 0; a global re-sort
-// (resort = 1) fills the other buffer and makes it current, so that the
-// scatter reads buffer 1 - cur and writes buffer cur.
-__global__ void __launch_bounds__(1024) k_src3_scan(const StepArgs* __restrict__ A, int s, int resort)
+// Exclusive scan of the bucket counts over tiles of SCAN_TILE buckets (one
+// block each): k_src3_tsum sums every tile, k_src3_scan adds the totals of
+// the tiles before its own and scans the tile into the slot cursors kcur and
+// the segment table of the target buffer, clearing the counts for the next
+// use.  Creation (resort = 0) fills buffer 0; a global re-sort (resort = 1)
+// fills buffer 1 - cur, and k_src3_flip makes it current after the scatter.
+constexpr int SCAN_TILE = 1024;
+
+__device__ __forceinline__ int block_sum_1024(int v, int* ws)
 {
-    __shared__ int warp_sums[32];
-    __shared__ int carry, dst_s;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    v = __reduce_add_sync(0xffffffffu, v);
+    if (lane == 0) ws[warp] = v;
+    __syncthreads();
+    int t = lane < (int)(blockDim.x >> 5) ? ws[lane] : 0;
+    t = __reduce_add_sync(0xffffffffu, t);
+    __syncthreads();
+    return t;
+}
+
+__global__ void __launch_bounds__(SCAN_TILE) k_src3_tsum(const StepArgs* __restrict__ A, int s)
+{
+    __shared__ int ws[32];
     const SpDev& sp = A->sp[s];
     const int nb = sp.npen * sp.nkey;
-    int* c = sp.kcount;
-    int* cur = sp.kcur;
-    if (threadIdx.x == 0) {
-        carry = 0;
-        dst_s = resort ? 1 - A->ctl->cur[s] : 0;
+    const int i = blockIdx.x * SCAN_TILE + threadIdx.x;
+    const int t = block_sum_1024(i < nb ? sp.kcount[i] : 0, ws);
+    if (threadIdx.x == 0) sp.ktile[blockIdx.x] = t;
+}
+
+__global__ void __launch_bounds__(SCAN_TILE) k_src3_scan(const StepArgs* __restrict__ A, int s, int resort)
+{
+    __shared__ int ws[32];
+    const SpDev& sp = A->sp[s];
+    const int nb = sp.npen * sp.nkey, nk = sp.nkey;
+    const int dst = resort ? 1 - A->ctl->cur[s] : 0;
+    int o = 0;
+    for (int t = threadIdx.x; t < (int)blockIdx.x; t += SCAN_TILE) o += sp.ktile[t];
+    const int off = block_sum_1024(o, ws);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int i = blockIdx.x * SCAN_TILE + threadIdx.x;
+    const int v = i < nb ? sp.kcount[i] : 0;
+    int x = v;
+    for (int d = 1; d < 32; d <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, d);
+        if (lane >= d) x += y;
+    }
+    if (lane == 31) ws[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        int w = ws[lane];
+        for (int d = 1; d < 32; d <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, w, d);
+            if (lane >= d) w += y;
+        }
+        ws[lane] = w;
     }
     __syncthreads();
-    const int dst = dst_s;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int b0 = 0; b0 < nb; b0 += blockDim.x) {
-        const int i = b0 + threadIdx.x;
-        const int v = i < nb ? c[i] : 0;
-        int x = v;
-        for (int o = 1; o < 32; o <<= 1) {
-            const int y = __shfl_up_sync(0xffffffffu, x, o);
-            if (lane >= o) x += y;
-        }
-        if (lane == 31) warp_sums[warp] = x;
-        __syncthreads();
-        if (warp == 0) {
-            int w = lane < nw ? warp_sums[lane] : 0;
-            for (int o = 1; o < 32; o <<= 1) {
-                const int y = __shfl_up_sync(0xffffffffu, w, o);
-                if (lane >= o) w += y;
-            }
-            warp_sums[lane] = w;
-        }
-        __syncthreads();
-        const int incl = x + (warp > 0 ? warp_sums[warp - 1] : 0) + carry;
-        if (i < nb) {
-            cur[i] = incl - v;
-            c[i] = 0;
-        }
-        __syncthreads();
-        if (threadIdx.x == blockDim.x - 1) carry = incl;
-        __syncthreads();
-    }
-    const int total = carry;
-    const int nk = sp.nkey;
+    if (i >= nb) return;
+    const int excl = off + x - v + (warp > 0 ? ws[warp - 1] : 0);
+    sp.kcur[i] = excl;
+    sp.kcount[i] = 0;
     int* sg = sp.seg[dst];
-    for (int i = threadIdx.x; i < sp.npen * (nk + 1); i += blockDim.x) {
-        const int p = i / (nk + 1), k = i % (nk + 1);
-        const int b = p * nk + k;   // k == nk: first bucket of the next pencil
-        sg[i] = b < nb ? cur[b] : total;
+    const int p = i / nk, k = i - p * nk;
+    sg[p * (nk + 1) + k] = excl;
+    if (k == 0 && p > 0) sg[(p - 1) * (nk + 1) + nk] = excl;   // end of the previous pencil
+    if (i == nb - 1) {
+        sg[p * (nk + 1) + nk] = excl + v;
+        if (resort && (long long)(excl + v) != sp.n) atomicOr(&A->ctl->err, ERR_CAPACITY);
     }
-    if (resort && threadIdx.x == 0) {
-        if ((long long)total != sp.n) atomicOr(&A->ctl->err, ERR_CAPACITY);
-        A->ctl->cur[s] = dst;
+}
+
+// after a global re-sort: the buffer written becomes current
+__global__ void k_src3_flip(const StepArgs* __restrict__ A, int s)
+{
+    if (threadIdx.x == 0) {
+        A->ctl->cur[s] = 1 - A->ctl->cur[s];
         A->ctl->nsort[s] += 1;
     }
 }
@@ -1046,37 +1065,62 @@ __global__ void __launch_bounds__(256) k_bpush3(const StepArgs* __restrict__ A, 
     }
 }
 
-// the markers of species s from buffer 1 - cur into their (pencil, key)
-// buckets of buffer cur (k_src3_scan has placed the cursors and flipped cur)
+// the markers of species s from buffer cur into their (pencil, key) buckets
+// of buffer 1 - cur (k_src3_scan has placed the cursors).  A warp takes
+// RS3_ROUNDS x 32 consecutive markers: all loads first, then one slot per
+// round (a match on the bucket and one atomic per distinct bucket, all
+// rounds' atomics in flight together), then the stores.
+constexpr int RS3_ROUNDS = 4;
+
 template <typename T>
 __global__ void __launch_bounds__(256) k_rs3_scatter(const StepArgs* __restrict__ A, int s)
 {
     const SpDev& sp = A->sp[s];
-    const int dst = A->ctl->cur[s], src = 1 - dst;
+    const int src = A->ctl->cur[s], dst = 1 - src;
     VCoef<T> vc;
     vc.init(sp);
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    const long long n_pad = (sp.n + 31) / 32 * 32;
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u;
+    const long long wid = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+    const long long n = sp.n;
+    const T* f_src = reinterpret_cast<const T*>(sp.mf[src]);
     bool over = false;
-    for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < n_pad; k += stride) {
-        const bool ok = k < sp.n;
-        T v[3] = {(T)0, (T)0, (T)0};
-        int b = 0;
-        if (ok) {
-            for (int d = 0; d < 3; ++d) v[d] = reinterpret_cast<const T*>(sp.mv[src][d])[k];
-            b = bucket3<T>(sp, vc, v);
+    for (long long w0 = wid * 32 * RS3_ROUNDS; w0 < n; w0 += nw * 32 * RS3_ROUNDS) {
+        T v[RS3_ROUNDS][3], fv[RS3_ROUNDS];
+        Pos<T> pos[RS3_ROUNDS];
+        int b[RS3_ROUNDS];
+#pragma unroll
+        for (int r = 0; r < RS3_ROUNDS; ++r) {
+            const long long k = w0 + r * 32 + lane;
+            b[r] = -1;
+            if (k < n) {
+                for (int d = 0; d < 3; ++d) v[r][d] = reinterpret_cast<const T*>(sp.mv[src][d])[k];
+                fv[r] = f_src[k];
+                pos[r].load(sp, src, (int)k);
+                b[r] = bucket3<T>(sp, vc, v[r]);
+            }
         }
-        const int slot = warp_slot(sp.kcur, b, ok);
-        if (!ok) continue;
-        if (slot < 0 || (long long)slot >= sp.n) {
-            over = true;
-            continue;
+        unsigned grp[RS3_ROUNDS];
+        int base[RS3_ROUNDS];
+#pragma unroll
+        for (int r = 0; r < RS3_ROUNDS; ++r) {
+            grp[r] = __match_any_sync(0xffffffffu, b[r]);
+            base[r] = 0;
+            if (b[r] >= 0 && lane == __ffs(grp[r]) - 1) base[r] = atomicAdd(&sp.kcur[b[r]], __popc(grp[r]));
         }
-        Pos<T> pos;
-        pos.load(sp, src, (int)k);
-        pos.store(sp, dst, slot);
-        for (int d = 0; d < 3; ++d) reinterpret_cast<T*>(sp.mv[dst][d])[slot] = v[d];
-        reinterpret_cast<T*>(sp.mf[dst])[slot] = reinterpret_cast<const T*>(sp.mf[src])[k];
+#pragma unroll
+        for (int r = 0; r < RS3_ROUNDS; ++r) {
+            const int slot = __shfl_sync(0xffffffffu, base[r], __ffs(grp[r]) - 1) + __popc(grp[r] & lt);
+            if (b[r] < 0) continue;
+            if (slot < 0 || (long long)slot >= n) {
+                over = true;
+                continue;
+            }
+            pos[r].store(sp, dst, slot);
+            for (int d = 0; d < 3; ++d) reinterpret_cast<T*>(sp.mv[dst][d])[slot] = v[r][d];
+            reinterpret_cast<T*>(sp.mf[dst])[slot] = fv[r];
+        }
     }
     if (over) atomicOr(&A->ctl->err, ERR_CAPACITY);
 }
@@ -1194,6 +1238,16 @@ cudaError_t launch_sort3(const StepArgs& h, const StepArgs* d, cudaStream_t st)
     return cudaGetLastError();
 }
 
+// bucket counts -> cursors and segment table (creation: buffer 0; re-sort:
+// buffer 1 - cur)
+static void scan3(const StepArgs& h, const StepArgs* d, int s, int resort, cudaStream_t st)
+{
+    const int nb = h.sp[s].npen * h.sp[s].nkey;
+    const int tiles = (nb + SCAN_TILE - 1) / SCAN_TILE;
+    k_src3_tsum<<<tiles, SCAN_TILE, 0, st>>>(d, s);
+    k_src3_scan<<<tiles, SCAN_TILE, 0, st>>>(d, s, resort);
+}
+
 // source -> layout in buffer 0 (kcount is zero before and after)
 template <typename Src>
 static cudaError_t source_to_layout3(const StepArgs& h, const StepArgs* d, int s, Src src, unsigned long long* bad,
@@ -1203,11 +1257,11 @@ static cudaError_t source_to_layout3(const StepArgs& h, const StepArgs* d, int s
     const int blocks = (int)std::max<long long>(1, std::min<long long>((n + 255) / 256, 152ll * 16));
     if (h.prec == AVL_FP32) {
         k_src3_count<float, Src><<<blocks, 256, 0, st>>>(d, s, src, bad);
-        k_src3_scan<<<1, 1024, 0, st>>>(d, s, 0);
+        scan3(h, d, s, 0, st);
         k_src3_scatter<float, Src><<<blocks, 256, 0, st>>>(d, s, src);
     } else {
         k_src3_count<double, Src><<<blocks, 256, 0, st>>>(d, s, src, bad);
-        k_src3_scan<<<1, 1024, 0, st>>>(d, s, 0);
+        scan3(h, d, s, 0, st);
         k_src3_scatter<double, Src><<<blocks, 256, 0, st>>>(d, s, src);
     }
     return cudaGetLastError();
@@ -1249,11 +1303,12 @@ cudaError_t launch_rsort3(const StepArgs& h, const StepArgs* d, int s, cudaStrea
     const long long n = h.sp[s].n;
     if (n == 0) return cudaSuccess;
     const int blocks = marker_blocks(n);
-    k_src3_scan<<<1, 1024, 0, st>>>(d, s, 1);
+    scan3(h, d, s, 1, st);
     if (h.prec == AVL_FP32)
         k_rs3_scatter<float><<<blocks, 256, 0, st>>>(d, s);
     else
         k_rs3_scatter<double><<<blocks, 256, 0, st>>>(d, s);
+    k_src3_flip<<<1, 32, 0, st>>>(d, s);
     return cudaGetLastError();
 }
 
