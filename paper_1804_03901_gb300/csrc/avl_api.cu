@@ -599,7 +599,8 @@ avl_status avl_create(const avl_domain* dom, const avl_species* spec, int32_t ns
     if (dom->nvdim != 1 && dom->nvdim != 3) return fail(nullptr, AVL_EINVAL, "nvdim must be 1 or 3");
     if (dom->nx < 4 || dom->nx > (1 << 20)) return fail(nullptr, AVL_EINVAL, "nx must be in [4, 2^20]");
     if (dom->nvdim == 3 && (dom->precision == AVL_FP32 || dom->precision == AVL_FP64) &&
-        pd3_smem_bytes(dom->nx, dom->precision) > 220 * 1024)
+        (dom->nx > (dom->precision == AVL_FP32 ? 1024 : 512) ||
+         pd3_smem_bytes(dom->nx, NV3_MAX + 1, dom->precision) > 220 * 1024))
         return fail(nullptr, AVL_EINVAL, "1d3v needs nx <= 1024 (FP32) or nx <= 512 (FP64)");
     if (!(dom->L > 0) || !(dom->dt > 0) || !(dom->poisson_const > 0) || !isfinite(dom->L) ||
         !isfinite(dom->dt) || !isfinite(dom->poisson_const))

@@ -237,7 +237,7 @@ cudaError_t launch_get3(const StepArgs& h, const StepArgs* d, int s, double* x, 
 // f (and n) of the current deposit in the caller's [x][vx][vy][vz] order;
 // asel = accumulator selector after the last deposit
 cudaError_t launch_getf3(const StepArgs& h, int s, int asel, double* f, double* n, cudaStream_t st);
-size_t pd3_smem_bytes(int nx, int prec);
+size_t pd3_smem_bytes(int nx, int nkey, int prec);
 
 // output moments of species s ([2 + nvdim][nx], device, FP64) and the field
 // residual ([nx]) of the current state (k_moments.cu)

@@ -16,9 +16,9 @@
 //           pencil's four (v_y, v_z) cells -- no atomics
 //   flush   a finished v_x row is added into the global accumulators; each
 //           cell receives the sums of the four pencils that reach it
-// Markers whose key moved one row since the last re-sort deposit through a
-// four-row shared-memory ring, farther ones through global atomics; their
-// counts decide the next re-sort (k_sort3, per pencil, into the other
+// Markers whose key moved since the last re-sort deposit their 16
+// contributions through global reductions, one thread per contribution;
+// their counts decide the next re-sort (k_sort3, per pencil, into the other
 // buffer).  k_fin3 forms f = num / den, the moment (Eq. 14) and the
 // diagnostics (Sec. 3.4.1) and clears the other accumulator.
 //
@@ -43,7 +43,7 @@ template <typename T>
 struct Cfg3;
 template <>
 struct Cfg3<float> {
-    static constexpr int MPT = 3;   // markers per thread and chunk
+    static constexpr int MPT = 2;   // markers per thread and chunk
 };
 template <>
 struct Cfg3<double> {
@@ -176,26 +176,27 @@ struct Stage3 {
 };
 
 template <typename T>
-static size_t pd3_bytes(int nx)
+static size_t pd3_bytes(int nx, int nkey)
 {
     using S = Stage3<T>;
     size_t b = 2 * (size_t)S::NF * S::SLEN * sizeof(T);      // two staging buffers
-    b += sizeof(T) * (32 * (size_t)nx + 7 * (size_t)S::NB + nx);   // ring, sorted payload, E
-    b += 4 * (2 * (size_t)nx + 1) + 4 * (NV3_MAX + 2) + 64;  // histogram, bin starts, segment row
+    b += sizeof(T) * (7 * (size_t)S::NB + nx);                 // sorted payload, E
+    b += 4 * (2 * (size_t)nx + 1) + 4 * ((size_t)nkey + 2) + 64;   // histogram, bin starts, segment row
     return (b + 15) / 16 * 16;
 }
 
-size_t pd3_smem_bytes(int nx, int prec) { return prec == AVL_FP32 ? pd3_bytes<float>(nx) : pd3_bytes<double>(nx); }
+size_t pd3_smem_bytes(int nx, int nkey, int prec)
+{
+    return prec == AVL_FP32 ? pd3_bytes<float>(nx, nkey) : pd3_bytes<double>(nx, nkey);
+}
 
-template <typename T>
-struct Ring {
-    T* r;   // [4 rows][4 planes][2: num, den][nx]
-    int nx;
-    __device__ __forceinline__ T* at(int row, int q, int c, int x) const
-    {
-        return r + (((row & 3) * 4 + q) * 2 + c) * nx + x;
-    }
-};
+// largest key count (nv[0] + 1) over the species of a context
+static int nkey_max(const StepArgs& h)
+{
+    int m = 2;
+    for (int s = 0; s < h.ns; ++s) m = std::max(m, h.sp[s].nv[0] + 1);
+    return m;
+}
 
 // weights of the pencil's four (v_y, v_z) cells: (jy, jz), (jy+1, jz),
 // (jy, jz+1), (jy+1, jz+1)
@@ -217,13 +218,12 @@ struct Planes {
 };
 
 // A marker whose v_x dual row j is not its segment's deposits its 16
-// cloud-in-cell contributions apart from the gather: into the ring (rows
-// within one of the segment's) or straight into the global accumulator.
-// This is one of them: corner bits x (bit 0), v_x row (bit 1), (v_y, v_z)
-// plane (bits 2-3).
+// cloud-in-cell contributions apart from the gather, straight into the
+// global accumulator.  This is one of them: corner bits x (bit 0), v_x row
+// (bit 1), (v_y, v_z) plane (bits 2-3).
 template <typename T>
-__device__ __forceinline__ void deposit_corner(const Ring<T>& ring, bool to_ring, T* gacc, int cells, const Planes& pl,
-                                               int nx, int nvx, int bin, T u, int j, T w, T wy, T wz, T f, int corner)
+__device__ __forceinline__ void deposit_corner(T* gacc, int cells, const Planes& pl, int nx, int nvx, int bin, T u,
+                                               int j, T w, T wy, T wz, T f, int corner)
 {
     const int cx = corner & 1, cv = (corner >> 1) & 1, q = corner >> 2;
     const bool okq = q == 0 ? pl.ok[0] : q == 1 ? pl.ok[1] : q == 2 ? pl.ok[2] : pl.ok[3];
@@ -234,15 +234,10 @@ __device__ __forceinline__ void deposit_corner(const Ring<T>& ring, bool to_ring
     const T ay = (q & 1) ? wy : (T)1 - wy, az = (q & 2) ? wz : (T)1 - wz;
     const T a = ax * (cv ? w : (T)1 - w) * (ay * az);
     if (a == (T)0) return;
-    if (to_ring) {
-        atomicAdd(ring.at(row, q, 0, x), a * f);
-        atomicAdd(ring.at(row, q, 1, x), a);
-    } else {
-        const int base = q == 0 ? pl.base[0] : q == 1 ? pl.base[1] : q == 2 ? pl.base[2] : pl.base[3];
-        const int o = base + row * nx + x;
-        atomicAdd(gacc + o, a * f);
-        atomicAdd(gacc + cells + o, a);
-    }
+    const int base = q == 0 ? pl.base[0] : q == 1 ? pl.base[1] : q == 2 ? pl.base[2] : pl.base[3];
+    const int o = base + row * nx + x;
+    atomicAdd(gacc + o, a * f);
+    atomicAdd(gacc + cells + o, a);
 }
 
 // exclusive scan of hist[0, nx) into start[0, nx], start[nx] = total; each
@@ -285,7 +280,7 @@ __device__ __forceinline__ void chunk_scan(int* hist, int* start, int nx, int* w
 // mode 1: push of the mobile species, then deposit of the new state;
 // mode 2: deposit of the mobile species (pushed and re-sorted before)
 template <typename T, int CPT>
-__global__ void __launch_bounds__(P3_THREADS, (sizeof(T) == 4 && CPT == 1) ? 2 : 1)
+__global__ void __launch_bounds__(P3_THREADS, sizeof(T) == 4 ? (CPT == 1 ? 4 : (CPT == 2 ? 2 : 1)) : (CPT == 1 ? 2 : 1))
     k_pd3(const StepArgs* __restrict__ A, int mode)
 {
     using S = Stage3<T>;
@@ -314,10 +309,9 @@ __global__ void __launch_bounds__(P3_THREADS, (sizeof(T) == 4 && CPT == 1) ? 2 :
     T* const gacc = reinterpret_cast<T*>(sp.acc[ctl->asel[s]]);
     const int* segg = sp.seg[cb] + (size_t)p * (nkey + 1);
 
-    // shared memory: staging | ring | payload (7 x NB) | E | hist | start | segment row
+    // shared memory: staging | payload (7 x NB) | E | hist | start | segment row
     T* stage = reinterpret_cast<T*>(smem);
-    Ring<T> ring{stage + 2 * NF * SLEN, nx};
-    T* pay = ring.r + 32 * nx;
+    T* pay = stage + 2 * NF * SLEN;
     T* Es = pay + 7 * NB;
     int* hist = reinterpret_cast<int*>(Es + nx);
     int* start = hist + nx;
@@ -342,7 +336,6 @@ __global__ void __launch_bounds__(P3_THREADS, (sizeof(T) == 4 && CPT == 1) ? 2 :
         src_s[FX + 2] = sp.mv[cb][2];
         src_s[FX + 3] = sp.mf[cb];
     }
-    for (int i = threadIdx.x; i < 32 * nx; i += P3_THREADS) ring.r[i] = (T)0;
     for (int i = threadIdx.x; i < nx; i += P3_THREADS) {
         hist[i] = 0;
         if (push) Es[i] = sizeof(T) == 4 ? (T)A->fd.E32[i] : (T)A->fd.E64[i];
@@ -517,7 +510,7 @@ __global__ void __launch_bounds__(P3_THREADS, (sizeof(T) == 4 && CPT == 1) ? 2 :
                 const int o = NB - 1 - (t >> 4);
                 const int jx = (int)pay[6 * NB + o];
                 const int d = jx - jseg;
-                deposit_corner<T>(ring, d == 1 || d == -1, gacc, cells, pl, nx, nvx, (int)pay[5 * NB + o],
+                deposit_corner<T>(gacc, cells, pl, nx, nvx, (int)pay[5 * NB + o],
                                   pay[0 * NB + o], jx, pay[1 * NB + o], pay[3 * NB + o], pay[4 * NB + o],
                                   pay[2 * NB + o], t & 15);
             }
@@ -556,8 +549,8 @@ __global__ void __launch_bounds__(P3_THREADS, (sizeof(T) == 4 && CPT == 1) ? 2 :
             __syncthreads();
             buf ^= 1;
         }
-        // row jseg - 1 is complete (no later segment reaches it): registers plus
-        // the ring's movers into the global accumulator; then rotate the rows
+        // row jseg - 1 is complete (no later segment reaches it): registers into
+        // the global accumulator; then rotate the rows
         const int row = jseg - 1;
         if (row >= 0) {
 #pragma unroll
@@ -566,11 +559,7 @@ __global__ void __launch_bounds__(P3_THREADS, (sizeof(T) == 4 && CPT == 1) ? 2 :
                 if (x >= nx) continue;
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
-                    T* rn = ring.at(row, q, 0, x);
-                    T* rd = ring.at(row, q, 1, x);
-                    const T vn = Rm[c][2 * q] + *rn, vd = Rm[c][2 * q + 1] + *rd;
-                    *rn = (T)0;
-                    *rd = (T)0;
+                    const T vn = Rm[c][2 * q], vd = Rm[c][2 * q + 1];
                     if (pl.ok[q] && vd != (T)0) {
                         const int o = pl.base[q] + row * nx + x;
                         atomicAdd(gacc + o, vn);
@@ -589,7 +578,7 @@ __global__ void __launch_bounds__(P3_THREADS, (sizeof(T) == 4 && CPT == 1) ? 2 :
             }
         __syncthreads();
     }
-    // the last row (nvx - 1) after the last segment: registers plus ring
+    // the last row (nvx - 1) after the last segment
     {
         const int row = nvx - 1;
 #pragma unroll
@@ -598,8 +587,8 @@ __global__ void __launch_bounds__(P3_THREADS, (sizeof(T) == 4 && CPT == 1) ? 2 :
             if (x >= nx) continue;
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
-                const T vn = Rm[c][2 * q] + *ring.at(row, q, 0, x);
-                const T vd = Rm[c][2 * q + 1] + *ring.at(row, q, 1, x);
+                const T vn = Rm[c][2 * q];
+                const T vd = Rm[c][2 * q + 1];
                 if (pl.ok[q] && vd != (T)0) {
                     const int o = pl.base[q] + row * nx + x;
                     atomicAdd(gacc + o, vn);
@@ -1194,14 +1183,14 @@ static cudaError_t set_pd3_attr(int smem)
 
 cudaError_t configure_vhs3(const StepArgs& h)
 {
-    const int smem = (int)pd3_smem_bytes(h.fd.nx, h.prec);
+    const int smem = (int)pd3_smem_bytes(h.fd.nx, nkey_max(h), h.prec);
     return h.prec == AVL_FP32 ? set_pd3_attr<float>(smem) : set_pd3_attr<double>(smem);
 }
 
 template <typename T>
 static void pd3_go(const StepArgs& h, const StepArgs* d, int mode, cudaStream_t st)
 {
-    const int smem = (int)pd3_smem_bytes(h.fd.nx, h.prec);
+    const int smem = (int)pd3_smem_bytes(h.fd.nx, nkey_max(h), h.prec);
     switch (cpt_of(h.fd.nx)) {
         case 1: k_pd3<T, 1><<<h.npen_total, P3_THREADS, smem, st>>>(d, mode); break;
         case 2: k_pd3<T, 2><<<h.npen_total, P3_THREADS, smem, st>>>(d, mode); break;
