@@ -150,15 +150,21 @@ avl_status plan_layout(avl_ctx* c, int s, long long n)
     const int w_env = env_int("AVL_WMAX", 0);
     int Wmax = 0;
     for (;;) {
-        // window: the rows one chunk's keys span, the CIC reach and a drift halo;
-        // smaller chunks while it does not fit in shared memory
+        // window: the rows one chunk's keys span, the CIC reach, a drift halo and
+        // WIN_SPARE rows for the spread of a chunk's keys between re-sorts (left
+        // out first when the window does not fit in shared memory); smaller
+        // chunks while it still does not fit
         const int span = (int)std::ceil((double)M / mpk) + 1;
-        Wmax = std::min(span + 2 * HALO + 1, sp.nvflat + 2 * HALO + 2);
-        if (w_env > 0) Wmax = w_env;
-        sp.M = (int)M;
-        sp.Wmax = Wmax;
-        if (pd1_smem_bytes(sp, c->h.prec) <= 220 * 1024 || M <= 256 || w_env > 0 || m_env > 0 || c->force_M > 0)
-            break;
+        bool fits = false;
+        for (int spare = WIN_SPARE;; spare = 0) {
+            Wmax = std::min(span + 2 * HALO + 1 + spare, sp.nvflat + 2 * HALO + 2);
+            if (w_env > 0) Wmax = w_env;
+            sp.M = (int)M;
+            sp.Wmax = Wmax;
+            fits = pd1_smem_bytes(sp, c->h.prec) <= 220 * 1024;
+            if (fits || spare == 0) break;
+        }
+        if (fits || M <= 256 || w_env > 0 || m_env > 0 || c->force_M > 0) break;
         M = std::max<long long>(256, (M / 2 + 63) / 64 * 64);
     }
     const int nch = (int)((n + M - 1) / M);
@@ -670,7 +676,7 @@ avl_status avl_create(const avl_domain* dom, const avl_species* spec, int32_t ns
     fd.softening = dom->softening;
     fd.ndiag = 3 + 3 * nspecies;
     fd.resort_drift = env_int("AVL_RESORT_DRIFT", 1) != 0 ? 1 : 0;
-    fd.resort_miss = std::max(1, env_int("AVL_RESORT_MISS", 2000));
+    fd.resort_miss = std::max(1, env_int("AVL_RESORT_MISS", 100));
     fd.L = dom->L;
     fd.dx = dx;
     fd.cP = dom->poisson_const;

@@ -44,6 +44,7 @@ constexpr int CNT_THREADS = 512;    // key-count block
 constexpr int HIST_S = 64;          // keys per chunk histogram
 constexpr int HIST_R = 16;          // of which below the chunk's reference key
 constexpr int HALO = 2;             // window rows beyond the chunk's keys (one step of drift)
+constexpr int WIN_SPARE = 4;        // further window rows for the key spread between re-sorts
 constexpr int FIN_THREADS = 256;    // finalize block
 constexpr int FIN_XB = 16;          // x columns per finalize block
 constexpr int FIELD_THREADS = 512;  // Poisson cluster block
@@ -117,6 +118,7 @@ struct FieldDev {
     int nx, pow2, softening, ndiag;
     int resort_drift;          // 1d1v: re-sort whenever the field drifts markers a row or more
     int resort_miss;           // 1d1v: re-sort when more than n / resort_miss markers miss their window
+                               // (default 100: the overflow path takes up to 1 % cheaper than a re-sort)
     double L, dx, cP;
     double* rho;               // nx
     double* E64;               // nx
