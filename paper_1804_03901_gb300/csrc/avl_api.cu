@@ -1255,6 +1255,34 @@ avl_status avl_create_batch(int32_t nrun, const avl_domain* doms, const avl_spec
         b->runs.push_back(c);
         off += nspecies[r];
     }
+    // finalize row groups for the whole launch: each run's were sized as if it
+    // filled the GPU alone; about 64 blocks per SM over all runs instead (row
+    // groups only grow, so the runs' charge and diagnostics partials still fit)
+    if (env_int("AVL_RQ", 0) <= 0) {
+        double cells = 0.0;
+        for (avl_ctx* c : b->runs)
+            for (int s = 0; s < c->ns; ++s) cells += (double)c->h.sp[s].nx * c->h.sp[s].nvflat;
+        const double per_block = cells / (64.0 * b->runs[0]->num_sms);
+        const int rq_batch = std::max(8, (int)std::ceil(per_block / FIN_XB));
+        for (avl_ctx* c : b->runs) {
+            int fin_base = 0;
+            for (int s = 0; s < c->ns; ++s) {
+                SpDev& sp = c->h.sp[s];
+                sp.rq = std::min(std::max(sp.rq, rq_batch), sp.nvflat);
+                sp.nrq = (sp.nvflat + sp.rq - 1) / sp.rq;
+                sp.nfin = sp.nxb * sp.nrq;
+                sp.fin_base = fin_base;
+                fin_base += sp.nfin;
+            }
+            c->h.nfin_total = fin_base;
+            avl_status st = upload_args(c);
+            if (st) {
+                std::string m = c->err;
+                avl_destroy(b);
+                return fail(nullptr, st, m);
+            }
+        }
+    }
     *out = b;
     return AVL_OK;
 }
