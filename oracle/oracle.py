@@ -84,6 +84,10 @@ def lib():
         L.orc_push.argtypes = [gp, C.c_int64, dp, dp, C.c_double, C.c_double, dp]
         L.orc_push_boris.restype = None
         L.orc_push_boris.argtypes = [gp, C.c_int64, dp, dp, C.c_double, C.c_double, dp, dp]
+        L.orc_refine_markers.restype = C.c_int64
+        L.orc_refine_markers.argtypes = [gp, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(_F0), C.c_int32,
+                                         C.c_uint64, C.c_double, C.c_double, C.c_double, C.c_int32, dp, dp, dp,
+                                         dp, dp, dp]
         L.orc_diag.restype = None
         L.orc_diag.argtypes = [gp, C.c_double, dp, dp]
         L.orc_field_energy.restype = C.c_double
@@ -217,6 +221,28 @@ def push_boris(nx, L, sp: Species, x, v, dt, E, B):
     Bv = np.ascontiguousarray(B, dtype=np.float64)
     lib().orc_push_boris(C.byref(g), x.size, _dp(x), _dp(v), sp.q / sp.m, dt,
                          _dp(np.ascontiguousarray(E, dtype=np.float64)), _dp(Bv))
+
+
+def refine_markers(nx, L, sp: Species, box, lattice, f0: F0, species_index, seed, jitter, dt, Ehist,
+                   feet=False):
+    """1d1v marker refinement by tracing back (orc_refine_markers): new markers
+    on a jittered lattice[0] x lattice[1] sub-lattice of every cell of the box
+    [box[0], box[1]) x [box[2], box[3]) at the current time, traced back through
+    the fields Ehist (nhist, nx) of the states since the initial one, with
+    f = f0 at the foot.  Returns x, v (1, n), f and, with feet=True, x0, v0."""
+    g = make_grid(1, nx, L, sp)
+    n = (box[1] - box[0]) * (box[3] - box[2]) * lattice[0] * lattice[1]
+    Eh = np.ascontiguousarray(Ehist, dtype=np.float64).reshape(-1, nx)
+    x, v, fl = np.zeros(n), np.zeros(n), np.zeros(n)
+    x0, v0 = np.zeros(n), np.zeros(n)
+    b = (C.c_int32 * 4)(*[int(q) for q in box])
+    lat = (C.c_int32 * 2)(*[int(q) for q in lattice])
+    c = f0.to_c()
+    got = lib().orc_refine_markers(C.byref(g), b, lat, C.byref(c), species_index, seed, jitter, sp.q / sp.m, dt,
+                                   Eh.shape[0], _dp(Eh), _dp(x), _dp(v), _dp(fl), _dp(x0), _dp(v0))
+    assert got == n
+    out = (x, v.reshape(1, n), fl)
+    return out + (x0, v0) if feet else out
 
 
 def diag(nvdim, nx, L, sp: Species, f):

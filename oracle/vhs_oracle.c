@@ -32,6 +32,9 @@
  *   orc_push                E == 0: free streaming x + v t mod L; constant E:
  *                           the discrete parabola of kick-drift leapfrog.
  *   orc_diag, field energy  closed forms for a Maxwellian and a single mode.
+ *   orc_refine_markers      free streaming f0(x - v t, v); the closed form of
+ *                           the inverse step under a uniform field; the feet
+ *                           pushed forward by orc_push return the markers.
  *   whole step              linear Landau damping rate and frequency against the
  *                           root of the plasma dispersion function; two-stream
  *                           growth rate; conservation of N and total energy.
@@ -347,6 +350,50 @@ void orc_push_boris(const orc_grid* g, int64_t n, double* x, double* v, double q
         v[2 * n + l] = vq[2];
         x[l] = xn;
     }
+}
+
+/* Marker refinement by tracing back (Sec. 2), see the header. */
+int64_t orc_refine_markers(const orc_grid* g, const int32_t box[4], const int32_t lattice[2], const orc_f0* p,
+                           int32_t species, uint64_t seed, double jitter, double qm, double dt, int32_t nhist,
+                           const double* Ehist, double* x, double* v, double* fl, double* x0, double* v0)
+{
+    const double dx = g->L / g->nx;
+    const double dv = (g->vmax[0] - g->vmin[0]) / g->nv[0];
+    const int64_t ppc = (int64_t)lattice[0] * lattice[1];
+    const int64_t nrow = box[3] - box[2];
+    int64_t m = 0;
+    for (int64_t i = box[0]; i < box[1]; ++i)
+    for (int64_t j = box[2]; j < box[3]; ++j)
+    for (int64_t a = 0; a < lattice[0]; ++a)
+    for (int64_t b = 0; b < lattice[1]; ++b) {
+        m = ((i - box[0]) * nrow + (j - box[2])) * ppc + a * lattice[1] + b;
+        double jx = (orc_jitter_uniform(seed, species, m, 0) - 0.5) * jitter;
+        double jv = (orc_jitter_uniform(seed, species, m, 1) - 0.5) * jitter;
+        double xm = ((double)i + ((double)a + 0.5 + jx) / lattice[0]) * dx;
+        double vm = g->vmin[0] + ((double)j + ((double)b + 0.5 + jv) / lattice[1]) * dv;
+        x[m] = xm;
+        v[m] = vm;
+        /* back along the characteristic: undo the drift, then the kick of
+         * state n, whose field is gathered at the earlier position */
+        for (int32_t n = nhist - 1; n >= 0; --n) {
+            double xn = xm - vm * dt;
+            xn = fmod(xn, g->L);
+            if (xn < 0.0) xn += g->L;
+            if (xn >= g->L) xn -= g->L;
+            xm = xn;
+            int64_t i0; double w;
+            cic1(xm / dx, &i0, &w);
+            int64_t ia = ((i0 % g->nx) + g->nx) % g->nx;
+            int64_t ib = (((i0 + 1) % g->nx) + g->nx) % g->nx;
+            const double* E = Ehist + (int64_t)n * g->nx;
+            double El = (1.0 - w) * E[ia] + w * E[ib];
+            vm = vm - qm * El * dt;
+        }
+        if (x0) x0[m] = xm;
+        if (v0) v0[m] = vm;
+        fl[m] = orc_f0_eval(p, 1, g->L, xm, &vm);
+    }
+    return (box[1] - box[0]) * nrow * ppc;
 }
 
 /* Diagnostics of one species on its reconstructed grid (Sec. 3.4.1):

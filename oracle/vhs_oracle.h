@@ -83,6 +83,22 @@ void orc_push(const orc_grid* g, int64_t n, double* x, double* v, double qm, dou
 void orc_push_boris(const orc_grid* g, int64_t n, double* x, double* v, double qm, double dt,
                     const double* E, const double B[3]);
 
+/* Marker refinement by tracing back to the initial state (Sec. 2: markers of
+ * different weight; a phase-space patch that needs more resolution later is
+ * traced back to the initial state and given more markers there).  1d1v.
+ * New markers sit on a jittered px x pv sub-lattice of every cell of the box
+ * [box[0], box[1]) x [box[2], box[3]) (x cells x velocity rows) at the
+ * current time, with the jitter recipe of orc_init_markers (stream species,
+ * marker m = ((i - box[0]) * (box[3] - box[2]) + (j - box[2])) * ppc + sub).
+ * Each is traced back nhist steps by the inverse of the kick-drift step,
+ *   x_n = x_{n+1} - v_{n+1} dt (periodic),  v_n = v_{n+1} - (q/m) dt E^n(x_n),
+ * with E^n = Ehist[n * nx ...] the field of state n (n = nhist - 1 .. 0), and
+ * takes f_l = f0 at the foot.  Writes x, v, fl at the current time and, if not
+ * NULL, the feet x0, v0; returns the number of markers. */
+int64_t orc_refine_markers(const orc_grid* g, const int32_t box[4], const int32_t lattice[2], const orc_f0* p,
+                           int32_t species, uint64_t seed, double jitter, double qm, double dt, int32_t nhist,
+                           const double* Ehist, double* x, double* v, double* fl, double* x0, double* v0);
+
 void orc_diag(const orc_grid* g, double m, const double* f, double out[3]);
 double orc_field_energy(int32_t nx, double L, double cP, const double* E);
 
