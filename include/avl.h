@@ -149,6 +149,38 @@ avl_status avl_get_markers(avl_ctx* ctx, int32_t s, double* x, double* v, double
  * step).  Errors: AVL_ESTATE if a mobile species has no markers. */
 avl_status avl_step(avl_ctx* ctx, int32_t nsteps);
 
+/* Field history for marker refinement (not used by the step itself): from
+ * this call on, the electric field of every state (E after each step, or
+ * after a re-creation of markers) is kept in a device buffer of
+ * (max_steps + 1) x nx FP64 values that the call allocates (the previous one
+ * is freed); slot 0 takes the current E.  Call it before avl_init_markers of
+ * the species to be refined.  Errors: AVL_EINVAL (max_steps outside
+ * [1, 2^24], a batch), AVL_ENOMEM. */
+avl_status avl_record_history(avl_ctx* ctx, int32_t max_steps);
+
+/* Marker refinement by tracing back to the initial state (Sec. 2: markers of
+ * very different weight can share a cell; a phase-space patch that needs more
+ * resolution later is traced back to the initial state and given more
+ * markers there), 1d1v.  Adds lattice[0] x lattice[1] markers in every cell
+ * of the box [box[0], box[1]) x [box[2], box[3]) (x cells x velocity rows) of
+ * species s at the current time, on the jittered sub-lattice of
+ * avl_init_markers (seed and jitter as there; use a seed other than the
+ * creation's).  Each new marker is traced back to the species' creation by
+ * the inverse of the kick-drift step, x_n = x_{n+1} - v_{n+1} dt (periodic),
+ * v_n = v_{n+1} - (q/m) dt E^n(x_n), through the recorded fields, and takes
+ * f = f0 (the creation's f0) at the foot; f is constant along
+ * characteristics, and the reconstruction of Eq. 4 weighs denser markers by
+ * their overlap only.  The species is then re-laid out and f, rho and E are
+ * recomputed for the enlarged marker set (as avl_set_markers does).  The
+ * adjoint is no longer available for the species (its markers are not the
+ * creation lattice).  *added_opt (if not NULL) receives the number added.
+ * Errors: AVL_EINVAL (nvdim 3, box outside the grid, lattice < 1 or more than
+ * 4096 points, jitter outside [0, 1], 2^31 markers), AVL_ESTATE (markers not
+ * from avl_init_markers, or no history covering every step since their
+ * creation). */
+avl_status avl_refine_markers(avl_ctx* ctx, int32_t s, const int32_t* box, const int32_t* lattice, uint64_t seed,
+                              double jitter, int64_t* added_opt);
+
 /* Static background magnetic field B = (B_x, B_y, B_z) of a 1d3v context
  * (Sec. 3.2: the full Boris push of the 1d3v version; Sec. 3.3: the time step
  * should resolve a gyration with at least 2 pi steps).  From the next step on,

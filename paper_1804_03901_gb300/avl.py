@@ -27,7 +27,7 @@ EXPORTED = ["avl_create", "avl_destroy", "avl_last_error", "avl_init_markers", "
             "avl_marker_count", "avl_get_markers", "avl_step", "avl_get_f", "avl_get_rho",
             "avl_get_E", "avl_get_diag", "avl_get_stats", "avl_field_solve", "avl_field_solve_noalloc",
             "avl_profile_steps", "avl_adjoint", "avl_create_batch", "avl_batch_run", "avl_autotune",
-            "avl_get_moments", "avl_get_residual", "avl_set_bfield",
+            "avl_get_moments", "avl_get_residual", "avl_set_bfield", "avl_record_history", "avl_refine_markers",
             "avl_synchronize"]
 
 
@@ -86,6 +86,8 @@ def _load():
         "avl_get_moments": (C.c_int, [vp, C.c_int32, vp, C.c_int32]),
         "avl_get_residual": (C.c_int, [vp, vp, C.c_int32]),
         "avl_set_bfield": (C.c_int, [vp, vp]),
+        "avl_record_history": (C.c_int, [vp, C.c_int32]),
+        "avl_refine_markers": (C.c_int, [vp, C.c_int32, vp, vp, C.c_uint64, C.c_double, vp]),
         "avl_synchronize": (C.c_int, [vp]),
     }
     for name, (res, args) in sig.items():
@@ -121,6 +123,8 @@ avl_autotune = lib.avl_autotune
 avl_get_moments = lib.avl_get_moments
 avl_get_residual = lib.avl_get_residual
 avl_set_bfield = lib.avl_set_bfield
+avl_record_history = lib.avl_record_history
+avl_refine_markers = lib.avl_refine_markers
 avl_synchronize = lib.avl_synchronize
 
 
@@ -258,6 +262,20 @@ class Simulation:
         out = np.zeros((2 + self.nvdim, self.nx))
         self._chk(avl_get_moments(self.ctx, s, out.ctypes.data, 0))
         return out
+
+    def record_history(self, max_steps):
+        """Keep E of every state from now on (for refine_markers)."""
+        self._chk(avl_record_history(self.ctx, int(max_steps)))
+
+    def refine_markers(self, s, box, lattice, seed, jitter=1.0):
+        """Add markers to the box [x0, x1) x [v0, v1) of cells of species s,
+        traced back to the creation for their values; returns the count."""
+        b = np.ascontiguousarray(box, dtype=np.int32).reshape(4)
+        lat = np.ascontiguousarray(lattice, dtype=np.int32).reshape(2)
+        added = C.c_int64(0)
+        self._chk(avl_refine_markers(self.ctx, int(s), b.ctypes.data, lat.ctypes.data, int(seed), float(jitter),
+                                     C.byref(added)))
+        return int(added.value)
 
     def set_bfield(self, B):
         """Static background magnetic field (B_x, B_y, B_z) of a 1d3v run: the

@@ -44,6 +44,11 @@ struct avl_ctx {
     double jitter_s[MAXS] = {};
     avl_f0 f0_s[MAXS] = {};
     AdjEngine* adj = nullptr;
+    // marker refinement: species whose markers carry f0 of their creation, the
+    // step of that creation, and the field history buffer
+    bool refinable[MAXS] = {};
+    long long init_step[MAXS] = {};
+    void* hist_mem = nullptr;
     int force_M = 0;                    // chunk size chosen by avl_autotune (0: heuristic)
     unsigned layout_version = 0;        // bumped whenever the launch shapes change
     // a batch: independent runs advanced by one launch per kernel class
@@ -811,6 +816,7 @@ void avl_destroy(avl_ctx* c)
     for (void* p : c->allocs) cudaFree(p);
     for (int s = 0; s < MAXS; ++s) free_layout(c, s);
     if (c->scratch) cudaFree(c->scratch);
+    if (c->hist_mem) cudaFree(c->hist_mem);
     if (c->own_stream && c->st) cudaStreamDestroy(c->st);
     delete c;
 }
@@ -847,6 +853,13 @@ avl_status avl_init_markers(avl_ctx* c, int32_t s, const int32_t lattice[4], con
         AVL_CUDA(c, launch_init1(c->h, c->d_args, s, lattice, c->d_f0, seed, jitter, c->st));
     c->has_markers[s] = true;
     c->lattice_made[s] = true;
+    c->refinable[s] = true;
+    {
+        long long step = 0;
+        AVL_CUDA(c, cudaMemcpyAsync(&step, &c->d_ctl->step, 8, cudaMemcpyDeviceToHost, c->st));
+        AVL_CUDA(c, cudaStreamSynchronize(c->st));
+        c->init_step[s] = step;
+    }
     for (int d = 0; d < 4; ++d) c->lat[s][d] = lattice[d];
     c->seed_s[s] = seed;
     c->jitter_s[s] = jitter;
@@ -875,6 +888,7 @@ avl_status avl_set_markers(avl_ctx* c, int32_t s, int64_t n, const double* x, co
         df_ = base + n * (1 + nvd);
     }
     c->lattice_made[s] = false;
+    c->refinable[s] = false;
     if ((st = nvd == 3 ? plan_layout3(c, s, n) : plan_layout(c, s, n))) return st;
     if ((st = set_cur_zero(c, s))) return st;
     if ((st = upload_args(c))) return st;
@@ -958,6 +972,82 @@ avl_status avl_step(avl_ctx* c, int32_t nsteps)
     avl_status st = build_graph(c);
     if (st) return st;
     for (int i = 0; i < nsteps; ++i) AVL_CUDA(c, cudaGraphLaunch(c->gexec, c->st));
+    return AVL_OK;
+}
+
+avl_status avl_record_history(avl_ctx* c, int32_t max_steps)
+{
+    if (!c) return AVL_EINVAL;
+    if (!c->runs.empty()) return fail(c, AVL_EINVAL, "record the history on the runs of a batch, not the batch");
+    if (max_steps < 1 || max_steps > (1 << 24)) return fail(c, AVL_EINVAL, "max_steps must be in [1, 2^24]");
+    const int nx = c->h.fd.nx;
+    AVL_CUDA(c, cudaStreamSynchronize(c->st));
+    if (c->hist_mem) {
+        cudaFree(c->hist_mem);
+        c->hist_mem = nullptr;
+        c->h.fd.hist = nullptr;
+    }
+    const size_t bytes = ((size_t)max_steps + 1) * nx * 8;
+    cudaError_t e = cudaMalloc(&c->hist_mem, bytes);
+    if (e) {
+        c->hist_mem = nullptr;
+        upload_args(c);
+        return cuda_fail(c, e, "cudaMalloc(field history)");
+    }
+    long long step = 0;
+    AVL_CUDA(c, cudaMemcpyAsync(&step, &c->d_ctl->step, 8, cudaMemcpyDeviceToHost, c->st));
+    AVL_CUDA(c, cudaMemcpyAsync(c->hist_mem, c->h.fd.E64, (size_t)nx * 8, cudaMemcpyDeviceToDevice, c->st));
+    AVL_CUDA(c, cudaStreamSynchronize(c->st));
+    c->h.fd.hist = static_cast<double*>(c->hist_mem);
+    c->h.fd.hist_cap = max_steps + 1;
+    c->h.fd.hist_origin = step;
+    return upload_args(c);
+}
+
+avl_status avl_refine_markers(avl_ctx* c, int32_t s, const int32_t* box, const int32_t* lattice, uint64_t seed,
+                              double jitter, int64_t* added)
+{
+    avl_status st = check_species(c, s);
+    if (st) return st;
+    if (added) *added = 0;
+    if (!box || !lattice) return fail(c, AVL_EINVAL, "box or lattice is NULL");
+    if (c->h.nvdim != 1) return fail(c, AVL_EINVAL, "marker refinement is 1d1v");
+    const SpDev& sp = c->h.sp[s];
+    if (!(box[0] >= 0 && box[0] < box[1] && box[1] <= sp.nx && box[2] >= 0 && box[2] < box[3] &&
+          box[3] <= sp.nvflat))
+        return fail(c, AVL_EINVAL, "box must satisfy 0 <= x0 < x1 <= nx and 0 <= v0 < v1 <= nv");
+    if (lattice[0] < 1 || lattice[1] < 1 || (long long)lattice[0] * lattice[1] > 4096)
+        return fail(c, AVL_EINVAL, "lattice must be {px, pv} >= 1 with at most 4096 points");
+    if (!(jitter >= 0.0 && jitter <= 1.0)) return fail(c, AVL_EINVAL, "jitter must be in [0, 1]");
+    if (!c->refinable[s])
+        return fail(c, AVL_ESTATE, "species markers were not created by avl_init_markers (no initial f0 to trace to)");
+    const FieldDev& fd = c->h.fd;
+    if (!fd.hist) return fail(c, AVL_ESTATE, "no field history: call avl_record_history before avl_init_markers");
+    long long step = 0;
+    AVL_CUDA(c, cudaMemcpyAsync(&step, &c->d_ctl->step, 8, cudaMemcpyDeviceToHost, c->st));
+    AVL_CUDA(c, cudaStreamSynchronize(c->st));
+    const long long first = c->init_step[s] - fd.hist_origin, nhist = step - c->init_step[s];
+    if (first < 0 || first + nhist > fd.hist_cap)
+        return fail(c, AVL_ESTATE, "the field history does not cover every step since the species' markers were created");
+    const long long count = (long long)(box[1] - box[0]) * (box[3] - box[2]) * lattice[0] * lattice[1];
+    const long long n_old = sp.n, n_new = n_old + count;
+    if (n_new >= (1ll << 31) - 1024) return fail(c, AVL_EINVAL, "too many markers for one species (2^31)");
+    if ((st = ensure_scratch(c, (size_t)n_new * 24))) return st;
+    double* x = static_cast<double*>(c->scratch);
+    double* v = x + n_new;
+    double* f = v + n_new;
+    AVL_CUDA(c, launch_get1(c->h, c->d_args, s, x, v, f, c->st));
+    AVL_CUDA(c, cudaMemcpyAsync(c->d_f0, &c->f0_s[s], sizeof(avl_f0), cudaMemcpyHostToDevice, c->st));
+    const int b[4] = {box[0], box[1], box[2], box[3]}, lat[2] = {lattice[0], lattice[1]};
+    AVL_CUDA(c, launch_refine1(c->h, s, b, lat, c->d_f0, seed, jitter, c->dom.dt, (int)nhist,
+                               fd.hist + first * fd.nx, count, x + n_old, v + n_old, f + n_old, c->st));
+    // the whole set into a fresh layout (re-sorted, reconstructed, field solved)
+    // (avl_set_markers clears the creation lattice: the adjoint needs its order)
+    const long long init_step = c->init_step[s];
+    if ((st = avl_set_markers(c, s, n_new, x, v, f, 1))) return st;
+    c->refinable[s] = true;
+    c->init_step[s] = init_step;
+    if (added) *added = count;
     return AVL_OK;
 }
 

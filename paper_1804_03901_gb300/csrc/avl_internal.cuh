@@ -126,6 +126,10 @@ struct FieldDev {
     const double2* tw;         // exp(-2 pi i k / nx), k < nx
     const double* gmul;        // cP kappa / K^2 for m <= nx/2 (0 at m = 0 and Nyquist)
     double* diag;              // 3 + 3 ns
+    double* hist;              // field history for marker refinement: [hist_cap][nx] FP64, or null;
+                               // slot k holds E of the state after step hist_origin + k
+    int hist_cap;
+    long long hist_origin;
     double B[3];               // 1d3v: static background magnetic field (Boris push)
     int magnetized;            // B != 0 (1d3v): push, global re-sort, deposit
 };
@@ -215,6 +219,12 @@ cudaError_t launch_set1(const StepArgs& h, const StepArgs* d, int s, long long n
 cudaError_t launch_get1(const StepArgs& h, const StepArgs* d, int s, double* x, double* v,
                         double* f, cudaStream_t st);
 cudaError_t launch_getf(const StepArgs& h, int s, double* f, double* n, cudaStream_t st);
+// marker refinement (1d1v): count new markers on a jittered lattice of the box
+// of cells at the current time, traced back nhist steps through Ehist (E of
+// the species' initial state first) to f = f0 at the foot; FP64 outputs
+cudaError_t launch_refine1(const StepArgs& h, int s, const int box[4], const int lattice[2], const avl_f0* f0_dev,
+                           unsigned long long seed, double jitter, double dt, int nhist, const double* Ehist,
+                           long long count, double* x, double* v, double* f, cudaStream_t st);
 
 // 1d3v (k_vhs3.cu).  launch_pd3 mode as launch_pd1, and 2 = deposit only,
 // mobile species (after a magnetized push and re-sort); launch_sort3 re-sorts

@@ -311,6 +311,12 @@ __global__ void __cluster_dims__(FIELD_CLUSTER, 1, 1) __launch_bounds__(FIELD_TH
         fd.E32[x] = (float)e;
         we += e * e;
     }
+    // field history (marker refinement): E of the state this kernel finishes
+    if (fd.hist) {
+        const long long slot = (count_step ? A->ctl->step + 1 : A->ctl->step) - fd.hist_origin;
+        if (slot >= 0 && slot < fd.hist_cap)
+            for (int x = threadIdx.x; x < nx; x += FIELD_THREADS) fd.hist[slot * nx + x] = Eout[x];
+    }
     for (int o = 16; o > 0; o >>= 1) we += __shfl_down_sync(0xffffffffu, we, o);
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = we;
     __syncthreads();

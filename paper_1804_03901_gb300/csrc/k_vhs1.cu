@@ -696,6 +696,89 @@ __global__ void __launch_bounds__(PD_THREADS, 2) k_pd1(const StepArgs* __restric
 }
 
 // ---------------------------------------------------------------------------
+// marker refinement: new markers traced back to the initial state (Sec. 2)
+// ---------------------------------------------------------------------------
+struct RefineArgs {
+    int nx, nv, s, box[4], lat[2];
+    double dx, L, vmin, dv, qm, dt, jitter;
+    unsigned long long seed;
+    int nhist;
+    const double* Eh;    // [nhist][nx], E of the species' initial state first
+    const avl_f0* f0;
+    long long count;
+};
+
+// marker m of the box lattice (m = ((i - box0) rows + (j - box2)) ppc + a pv + b),
+// jittered like the creation lattice, at the current time; then back along
+// its characteristic by the inverse kick-drift step, x_n = x_{n+1} - v dt and
+// v_n = v_{n+1} - (q/m) dt E^n(x_n), in FP64 without fused operations (the
+// same sequence of roundings as a plain evaluation); f = f0 at the foot
+__global__ void __launch_bounds__(256) k_refine1(RefineArgs R, double* __restrict__ xo, double* __restrict__ vo,
+                                                 double* __restrict__ fo)
+{
+    const int ppc = R.lat[0] * R.lat[1];
+    const int nrow = R.box[3] - R.box[2];
+    for (long long m = (long long)blockIdx.x * blockDim.x + threadIdx.x; m < R.count;
+         m += (long long)gridDim.x * blockDim.x) {
+        const long long cell = m / ppc;
+        const int sub = (int)(m - cell * ppc);
+        const int i = R.box[0] + (int)(cell / nrow), j = R.box[2] + (int)(cell % nrow);
+        const int a = sub / R.lat[1], b = sub - (sub / R.lat[1]) * R.lat[1];
+        const double J0 = (jitter_u01(R.seed, R.s, m, 0) - 0.5) * R.jitter;
+        const double J1 = (jitter_u01(R.seed, R.s, m, 1) - 0.5) * R.jitter;
+        double x = ((double)i + ((double)a + 0.5 + J0) / R.lat[0]) * R.dx;
+        double v = R.vmin + ((double)j + ((double)b + 0.5 + J1) / R.lat[1]) * R.dv;
+        xo[m] = x;
+        vo[m] = v;
+        for (int n = R.nhist - 1; n >= 0; --n) {
+            double xn = fmod(__dsub_rn(x, __dmul_rn(v, R.dt)), R.L);
+            if (xn < 0.0) xn += R.L;
+            if (xn >= R.L) xn -= R.L;
+            x = xn;
+            const double u = __dsub_rn(__ddiv_rn(x, R.dx), 0.5);
+            const double fl = floor(u);
+            const double w = __dsub_rn(u, fl);
+            int ia, ib;
+            wrap_pair((int)fl, R.nx, ia, ib);
+            const double* E = R.Eh + (size_t)n * R.nx;
+            const double El = __dadd_rn(__dmul_rn(__dsub_rn(1.0, w), E[ia]), __dmul_rn(w, E[ib]));
+            v = __dsub_rn(v, __dmul_rn(__dmul_rn(R.qm, El), R.dt));
+        }
+        fo[m] = f0_value(R.f0, 1, R.L, x, &v);
+    }
+}
+
+cudaError_t launch_refine1(const StepArgs& h, int s, const int box[4], const int lattice[2], const avl_f0* f0_dev,
+                           unsigned long long seed, double jitter, double dt, int nhist, const double* Ehist,
+                           long long count, double* x, double* v, double* f, cudaStream_t st)
+{
+    if (count == 0) return cudaSuccess;
+    const SpDev& sp = h.sp[s];
+    RefineArgs R;
+    R.nx = sp.nx;
+    R.nv = sp.nvflat;
+    R.s = s;
+    for (int k = 0; k < 4; ++k) R.box[k] = box[k];
+    R.lat[0] = lattice[0];
+    R.lat[1] = lattice[1];
+    R.dx = sp.dx;
+    R.L = sp.dx * sp.nx;
+    R.vmin = sp.vmin[0];
+    R.dv = sp.dv[0];
+    R.qm = sp.qm;
+    R.dt = dt;
+    R.jitter = jitter;
+    R.seed = seed;
+    R.nhist = nhist;
+    R.Eh = Ehist;
+    R.f0 = f0_dev;
+    R.count = count;
+    const int blocks = (int)std::max<long long>(1, std::min<long long>((count + 255) / 256, 152ll * 8));
+    k_refine1<<<blocks, 256, 0, st>>>(R, x, v, f);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
 // finalize: f = num / den (Eq. 4), charge per row group (Eq. 14), diagnostics
 // ---------------------------------------------------------------------------
 template <typename T>
