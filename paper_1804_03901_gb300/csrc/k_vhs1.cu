@@ -787,10 +787,11 @@ struct CellSum;
 template <>
 struct CellSum<float> {
     ff num{0.f, 0.f}, den{0.f, 0.f};
-    __device__ __forceinline__ void add_partial(const float* p, int plane)
+    __device__ __forceinline__ void add_partial(const float* p, int plane) { add_pair(p[0], p[plane]); }
+    __device__ __forceinline__ void add_pair(float n, float d)
     {
-        ff_add(num, p[0]);
-        ff_add(den, p[plane]);
+        ff_add(num, n);
+        ff_add(den, d);
     }
     __device__ __forceinline__ void add_ovf(double n, double d)
     {
@@ -819,10 +820,11 @@ struct CellSum<float> {
 template <>
 struct CellSum<double> {
     double num = 0.0, den = 0.0;
-    __device__ __forceinline__ void add_partial(const double* p, int plane)
+    __device__ __forceinline__ void add_partial(const double* p, int plane) { add_pair(p[0], p[plane]); }
+    __device__ __forceinline__ void add_pair(double n, double d)
     {
-        num += p[0];
-        den += p[plane];
+        num += n;
+        den += d;
     }
     __device__ __forceinline__ void add_ovf(double n, double d)
     {
@@ -840,7 +842,7 @@ struct CellSum<double> {
 constexpr int FIN_LIST = 256;  // chunks whose windows meet one finalize block's rows
 
 template <typename T, bool BATCH>
-__global__ void __launch_bounds__(FIN_THREADS) k_fin1(const StepArgs* __restrict__ A0, int all_species,
+__global__ void __launch_bounds__(FIN_THREADS, 4) k_fin1(const StepArgs* __restrict__ A0, int all_species,
                                                       const BatchMap* __restrict__ bm)
 {
     constexpr int RL = FIN_THREADS / FIN_XB;   // row lanes
@@ -884,73 +886,110 @@ __global__ void __launch_bounds__(FIN_THREADS) k_fin1(const StepArgs* __restrict
     const int shx = (shifted && xok) ? sp.shift[ssel][x] : 0;
     if (threadIdx.x == 0) ncl = 0;
     __syncthreads();
-    if (threadIdx.x < 32) {
-        for (int c0 = 0; c0 < sp.nchunk; c0 += 32) {
-            const int cc = c0 + threadIdx.x;
-            int r0 = 0;
-            bool hit = false;
-            if (cc < sp.nchunk) {
-                r0 = sp.wrow0[cc];
-                hit = r0 + smin < j1 && r0 + W + smax > j0;
-            }
-            const unsigned m = __ballot_sync(0xffffffffu, hit);
-            const int pos = ncl + __popc(m & ((1u << threadIdx.x) - 1u));
-            if (hit && pos < FIN_LIST) {
+    for (int cc = threadIdx.x; cc < sp.nchunk; cc += FIN_THREADS) {
+        const int r0 = sp.wrow0[cc];
+        if (r0 + smin < j1 && r0 + W + smax > j0) {
+            const int pos = atomicAdd(&ncl, 1);
+            if (pos < FIN_LIST) {
                 clist[pos] = cc;
                 crow[pos] = r0;
             }
-            __syncwarp();
-            if (threadIdx.x == 0) ncl += __popc(m);
-            __syncwarp();
         }
     }
     __syncthreads();
     const int nlist = ncl;
     const bool use_list = nlist <= FIN_LIST;
-    // the list ordered by first window row (ties by chunk), so that a column
-    // walks only the windows that cover its rows
+    // the list ordered by first window row, ties by chunk (so that the sums
+    // over windows keep one order whatever order the list was filled in); a
+    // column walks only the windows that cover its rows
     __shared__ int slist[FIN_LIST], srow[FIN_LIST];
     if (use_list) {
         for (int t = threadIdx.x; t < nlist; t += FIN_THREADS) {
-            const int r = crow[t];
+            const int r = crow[t], c = clist[t];
             int rank = 0;
-            for (int q = 0; q < nlist; ++q) rank += (crow[q] < r || (crow[q] == r && q < t)) ? 1 : 0;
-            slist[rank] = clist[t];
+            for (int q = 0; q < nlist; ++q) rank += (crow[q] < r || (crow[q] == r && clist[q] < c)) ? 1 : 0;
+            slist[rank] = c;
             srow[rank] = r;
         }
         __syncthreads();
     }
 
     ColAcc<T> acc;
-    if (xok) {
+    // overflow rows, f = num / den, f and n stored, charge and diagnostics
+    auto finish = [&](int j, CellSum<T>& cs) {
+        if (any_ovf && ovf_tag[j] == tag) {
+            const size_t o = (size_t)j * nx + x;
+            cs.add_ovf(ovf_num[o], ovf_den[o]);
+            ovf_num[o] = 0.0;
+            ovf_den[o] = 0.0;
+        }
+        T fh, fl, dsum;
+        cs.value(fh, fl, dsum);
+        fg[(size_t)j * nx + x] = fh + fl;
+        ng[(size_t)j * nx + x] = dsum;
+        const T vj = (T)(sp.vmin[0] + (j + 0.5) * sp.dv[0]);
+        acc.add(fh, fl, vj * vj);
+    };
+    if (xok && use_list) {
+        // two rows at a time, the partials of their first WSLOT windows loaded
+        // together (the loads of a row no longer wait for the previous row);
+        // windows are added in list order, as one row at a time would
+        constexpr int WSLOT = 3;
+        const T* pcol = part + x;
+        const size_t wstride = (size_t)planes * plane;
         int lo = 0;   // first listed window that can still reach the rows ahead
-        for (int j = j0 + lr; j < j1; j += RL) {
-            CellSum<T> cs;
-            if (use_list) {
-                const int rel = j - shx;   // row in window coordinates
-                while (lo < nlist && srow[lo] + W <= rel) ++lo;
-                for (int q = lo; q < nlist && srow[q] <= rel; ++q)
-                    cs.add_partial(part + (size_t)slist[q] * planes * plane + (size_t)(rel - srow[q]) * nx + x,
-                                   plane);
-            } else {
-                for (int cc = 0; cc < sp.nchunk; ++cc) {
-                    const int wr = j - shx - sp.wrow0[cc];
-                    if (wr >= 0 && wr < W)
-                        cs.add_partial(part + (size_t)cc * planes * plane + (size_t)wr * nx + x, plane);
+        for (int j = j0 + lr; j < j1; j += 2 * RL) {
+            const int jb = j + RL;
+            const bool two = jb < j1;
+            const int ra = j - shx, rb = jb - shx;   // rows in window coordinates
+            while (lo < nlist && srow[lo] + W <= ra) ++lo;
+            int lob = lo;
+            while (lob < nlist && srow[lob] + W <= rb) ++lob;
+            T na[WSLOT], da[WSLOT], nb[WSLOT], db[WSLOT];
+            bool oa[WSLOT], ob[WSLOT];
+#pragma unroll
+            for (int k = 0; k < WSLOT; ++k) {
+                const int qa = lo + k, qb = lob + k;
+                oa[k] = qa < nlist && srow[qa] <= ra;
+                ob[k] = two && qb < nlist && srow[qb] <= rb;
+                na[k] = da[k] = nb[k] = db[k] = (T)0;
+                if (oa[k]) {
+                    const T* pp = pcol + (size_t)slist[qa] * wstride + (size_t)(ra - srow[qa]) * nx;
+                    na[k] = pp[0];
+                    da[k] = pp[plane];
+                }
+                if (ob[k]) {
+                    const T* pp = pcol + (size_t)slist[qb] * wstride + (size_t)(rb - srow[qb]) * nx;
+                    nb[k] = pp[0];
+                    db[k] = pp[plane];
                 }
             }
-            if (any_ovf && ovf_tag[j] == tag) {
-                const size_t o = (size_t)j * nx + x;
-                cs.add_ovf(ovf_num[o], ovf_den[o]);
-                ovf_num[o] = 0.0;
-                ovf_den[o] = 0.0;
+            CellSum<T> ca, cb;
+#pragma unroll
+            for (int k = 0; k < WSLOT; ++k)
+                if (oa[k]) ca.add_pair(na[k], da[k]);
+            for (int q = lo + WSLOT; q < nlist && srow[q] <= ra; ++q)
+                ca.add_partial(pcol + (size_t)slist[q] * wstride + (size_t)(ra - srow[q]) * nx, plane);
+            finish(j, ca);
+            if (two) {
+#pragma unroll
+                for (int k = 0; k < WSLOT; ++k)
+                    if (ob[k]) cb.add_pair(nb[k], db[k]);
+                for (int q = lob + WSLOT; q < nlist && srow[q] <= rb; ++q)
+                    cb.add_partial(pcol + (size_t)slist[q] * wstride + (size_t)(rb - srow[q]) * nx, plane);
+                finish(jb, cb);
             }
-            T fh, fl, dsum;
-            cs.value(fh, fl, dsum);
-            fg[(size_t)j * nx + x] = fh + fl;
-            ng[(size_t)j * nx + x] = dsum;
-            const T vj = (T)(sp.vmin[0] + (j + 0.5) * sp.dv[0]);
-            acc.add(fh, fl, vj * vj);
+            lo = lob;
+        }
+    } else if (xok) {
+        // more windows meet these rows than the list holds: scan every chunk
+        for (int j = j0 + lr; j < j1; j += RL) {
+            CellSum<T> cs;
+            for (int cc = 0; cc < sp.nchunk; ++cc) {
+                const int wr = j - shx - sp.wrow0[cc];
+                if (wr >= 0 && wr < W) cs.add_partial(part + (size_t)cc * planes * plane + (size_t)wr * nx + x, plane);
+            }
+            finish(j, cs);
         }
     }
     // charge of this species per column, summed over the row lanes in order
