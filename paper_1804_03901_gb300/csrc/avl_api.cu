@@ -473,7 +473,7 @@ avl_status create_species3(avl_ctx* c, int s, const avl_species& p, int& fin_bas
     sp.npen = 0;
     sp.n = 0;
     sp.nxb = (nx + FIN3_X - 1) / FIN3_X;
-    const int nrq0 = std::max(1, (4 * c->num_sms + c->ns * sp.nxb - 1) / (c->ns * sp.nxb));
+    const int nrq0 = std::max(1, (16 * c->num_sms + c->ns * sp.nxb - 1) / (c->ns * sp.nxb));
     int rq = std::max(1, (sp.nvflat + nrq0 - 1) / nrq0);
     const int rq_env = env_int("AVL_RQ", 0);
     if (rq_env > 0) rq = std::min(rq_env, sp.nvflat);

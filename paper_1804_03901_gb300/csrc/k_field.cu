@@ -280,16 +280,31 @@ __global__ void __cluster_dims__(FIELD_CLUSTER, 1, 1) __launch_bounds__(FIELD_TH
     __shared__ double dfin[3 * MAXS];   // per-species diagnostics sums (written by CTA FIELD_DIAG)
 
     // --- rho slice: sum over species and row blocks (fixed order) --------
+    // tpx threads per column (a power of two up to 32) take every tpx-th
+    // partial row and are summed by a fixed shuffle tree
     double* rho0 = cluster.map_shared_rank(rho_s, 0);
     const int per = (nx + FIELD_CLUSTER - 1) / FIELD_CLUSTER;
     const int xlo = rank * per, xhi = min(nx, xlo + per);
-    for (int x = xlo + threadIdx.x; x < xhi; x += FIELD_THREADS) {
-        double r = 0.0;
-        for (int s = 0; s < A->ns; ++s) {
-            const SpDev& sp = A->sp[s];
-            for (int k = 0; k < sp.nrq; ++k) r += sp.rho_part[(size_t)k * nx + x];
+    {
+        int tpx = 1;
+        while (tpx < 32 && tpx * 2 * max(per, 1) <= FIELD_THREADS) tpx *= 2;
+        const int part = threadIdx.x & (tpx - 1);
+        const int cols = FIELD_THREADS / tpx;
+        int nrows = 0;
+        for (int s = 0; s < A->ns; ++s) nrows += A->sp[s].nrq;
+        for (int x0 = xlo; x0 < xhi; x0 += cols) {
+            const int x = x0 + threadIdx.x / tpx;
+            double r = 0.0;
+            if (x < xhi) {
+                int s = 0, base = 0;
+                for (int k = part; k < nrows; k += tpx) {
+                    while (k - base >= A->sp[s].nrq) base += A->sp[s++].nrq;
+                    r += A->sp[s].rho_part[(size_t)(k - base) * nx + x];
+                }
+            }
+            for (int o = tpx >> 1; o > 0; o >>= 1) r += __shfl_down_sync(0xffffffffu, r, o, tpx);
+            if (part == 0 && x < xhi) rho0[x] = r;
         }
-        rho0[x] = r;
     }
     cluster.sync();
     if (rank != 0) {

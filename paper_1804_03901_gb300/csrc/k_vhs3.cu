@@ -637,15 +637,33 @@ __global__ void __launch_bounds__(FIN3_X * FIN3_R) k_fin3(const StepArgs* __rest
     T* fg = reinterpret_cast<T*>(sp.fgrid);
     const T* v2 = reinterpret_cast<const T*>(sp.v2row);
     ColAcc<T> acc;
+    auto cell = [&](int j, T nn, T dd, T v2j) {
+        const size_t o = (size_t)j * nx + x;
+        const T f = dd > (T)0 ? nn / dd : (T)0;
+        fg[o] = f;
+        clr[o] = (T)0;
+        clr[cells + o] = (T)0;
+        acc.add(f, (T)0, v2j);
+    };
     if (xok) {
-        for (int j = j0 + lr; j < j1; j += FIN3_R) {
+        // four rows per iteration, their loads issued together; the cells
+        // are still taken in row order
+        int j = j0 + lr;
+        for (; j + 3 * FIN3_R < j1; j += 4 * FIN3_R) {
+            T nn[4], dd[4], vv[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const size_t o = (size_t)(j + k * FIN3_R) * nx + x;
+                nn[k] = num[o];
+                dd[k] = den[o];
+                vv[k] = v2[j + k * FIN3_R];
+            }
+#pragma unroll
+            for (int k = 0; k < 4; ++k) cell(j + k * FIN3_R, nn[k], dd[k], vv[k]);
+        }
+        for (; j < j1; j += FIN3_R) {
             const size_t o = (size_t)j * nx + x;
-            const T nn = num[o], dd = den[o];
-            const T f = dd > (T)0 ? nn / dd : (T)0;
-            fg[o] = f;
-            clr[o] = (T)0;
-            clr[cells + o] = (T)0;
-            acc.add(f, (T)0, v2[j]);
+            cell(j, num[o], den[o], v2[j]);
         }
     }
     const double dvol = sp.dv[0] * sp.dv[1] * sp.dv[2];
