@@ -133,6 +133,15 @@ __device__ __forceinline__ void store8(double* p, const double (&o)[8])
     for (int q = 0; q < 4; ++q) reinterpret_cast<double2*>(p)[q] = make_double2(o[2 * q], o[2 * q + 1]);
 }
 
+// periodic neighbours of a lower cloud-in-cell cell i0, which is in
+// [-1, nx - 1] for every stored position (cell in [0, nx), offset in
+// [0, 1)); any other value still maps into the grid
+__device__ __forceinline__ void wrap_pair_in(int i0, int nx, int& ia, int& ib)
+{
+    ia = (unsigned)i0 < (unsigned)nx ? i0 : nx - 1;
+    ib = (unsigned)(i0 + 1) < (unsigned)nx ? i0 + 1 : 0;
+}
+
 // numerator and denominator contributions of a run of markers that share the
 // same four cells (lower corner i0, j0)
 template <typename T>
@@ -241,7 +250,7 @@ __device__ __forceinline__ bool flush_run(const Run<T>& r, T* win, int plane, in
 {
     if (r.j0 + 1 < 0 || r.j0 >= nv) return false;   // footprint entirely off the velocity grid
     int ia, ib;
-    wrap_pair(r.i0, nx, ia, ib);
+    wrap_pair_in(r.i0, nx, ia, ib);
     const int wa = r.j0 - sh[ia] - row0, wb = r.j0 - sh[ib] - row0;
     if (wa >= 0 && wa + 1 < W && wb >= 0 && wb + 1 < W) {
         const int cell[4] = {wa * nx + ia, wb * nx + ib, (wa + 1) * nx + ia, (wb + 1) * nx + ib};
@@ -615,7 +624,9 @@ __global__ void __launch_bounds__(PD_THREADS, 2) k_pd1(const StepArgs* __restric
         bool have = false;
 #pragma unroll
         for (int m = 0; m < MPT; ++m) {
-            if (g0 + m < end) {
+            const bool okm = g0 + m < end;
+            int code = 0;
+            if (okm) {
                 Pos<T>& pos = pos8[m];
                 T dv = dv8[m];
                 const T fl = f8[m];
@@ -623,7 +634,7 @@ __global__ void __launch_bounds__(PD_THREADS, 2) k_pd1(const StepArgs* __restric
                     int i0, ia, ib;
                     T w;
                     pos.cic(i0, w);
-                    wrap_pair(i0, nx, ia, ib);
+                    wrap_pair_in(i0, nx, ia, ib);
                     const T El = ((T)1 - w) * Es[ia] + w * Es[ib];
                     dv += qm_dt * El;
                     pos.drift(vref_dtdx + dv * dt_dx, nx);
@@ -633,9 +644,16 @@ __global__ void __launch_bounds__(PD_THREADS, 2) k_pd1(const StepArgs* __restric
                 int i0;
                 T wx;
                 pos.cic(i0, wx);
-                const T t = dv * inv_dv - (T)0.5;
+                // the fused multiply-add of key_rel, so that the footprint row
+                // is the key every other kernel computes from the stored value
+                T t;
+                if constexpr (sizeof(T) == 4)
+                    t = __fmaf_rn(dv, inv_dv, -0.5f);
+                else
+                    t = __fma_rn(dv, inv_dv, -0.5);
                 const T ft = floor(t);
                 const int j0 = kb + (int)ft;
+                code = rel_code(clampi(j0, 0, nv - 1), kbase);
                 const T wv = t - ft;
                 if (!have || i0 != run.i0 || j0 != run.j0) {
                     if (have)
@@ -648,12 +666,13 @@ __global__ void __launch_bounds__(PD_THREADS, 2) k_pd1(const StepArgs* __restric
                 const T a[4] = {((T)1 - wx) * ((T)1 - wv), wx * ((T)1 - wv), ((T)1 - wx) * wv, wx * wv};
                 run.add(a, fl);
             }
+            // the new key counted for this chunk (next step's window)
+            if (push) hist_add(scnt, far_next, code, okm);
         }
         if (have)
             n_over += flush_run<T>(run, win, plane, row0, W, nx, nv, shs, ovf_num, ovf_den, ovf_tag, tag) ? 1u : 0u;
         if (!push) continue;
-        // in place: the positions and velocities go back where they came
-        // from; the new keys are counted for this chunk
+        // in place: the positions and velocities go back where they came from
         if (any) {
             storeg(dvp + g0, dv8);
             if constexpr (sizeof(T) == 4) {
@@ -672,12 +691,6 @@ __global__ void __launch_bounds__(PD_THREADS, 2) k_pd1(const StepArgs* __restric
                 for (int m = 0; m < MPT; ++m) x8[m] = pos8[m].xi;
                 storeg(reinterpret_cast<double*>(sp.mx[cb]) + g0, x8);
             }
-        }
-#pragma unroll
-        for (int m = 0; m < MPT; ++m) {
-            const bool ok = g0 + m < end;
-            const int code = ok ? rel_code(key_rel(dv8[m], kb, inv_dv, nv), kbase) : 0;
-            hist_add(scnt, far_next, code, ok);
         }
     }
     if (n_over) atomicAdd(&misc[0], (int)n_over);
