@@ -145,7 +145,9 @@ avl_status plan_layout(avl_ctx* c, int s, long long n)
     sp.n = 0;
     const int per_sm = std::max(1, env_int("AVL_CHUNKS_PER_SM", 2));
     const long long target = std::max(1, per_sm * c->num_sms / c->ns);
-    long long chunks = std::min<long long>(std::max<long long>(1, (n + 8191) / 8192), target);
+    // small runs: chunks of at least 512 markers spread over the SMs (FP64 in
+    // particular gains from the extra SMs); large runs: the target count
+    long long chunks = std::min<long long>(std::max<long long>(1, (n + 511) / 512), target);
     long long M = (n + chunks - 1) / chunks;
     M = (M + 63) / 64 * 64;
     if (c->force_M > 0) M = ((long long)c->force_M + 63) / 64 * 64;
