@@ -697,6 +697,19 @@ avl_status avl_create(const avl_domain* dom, const avl_species* spec, int32_t ns
         cuda_fail(c, e, "cudaMalloc(field)");
         return bail(AVL_ENOMEM);
     }
+    fd.green = nullptr;
+    if (nx <= GREEN_MAX) {
+        std::vector<double> G(nx);
+        green_table(nx, gm.data(), G.data());
+        void* p_g = nullptr;
+        if ((e = dalloc(c, &p_g, nx * 8, false)) ||
+            (e = cudaMemcpyAsync(p_g, G.data(), nx * 8, cudaMemcpyHostToDevice, c->st)) ||
+            (e = cudaStreamSynchronize(c->st))) {
+            cuda_fail(c, e, "Green's function table");
+            return bail(AVL_ECUDA);
+        }
+        fd.green = (const double*)p_g;
+    }
     fd.rho = (double*)p_rho;
     fd.E64 = (double*)p_E64;
     fd.E32 = (float*)p_E32;

@@ -54,6 +54,7 @@ constexpr int P3_THREADS = 256;     // 1d3v pencil block (one thread per x colum
 constexpr int FIN3_X = 32;          // 1d3v finalize: x columns per block
 constexpr int FIN3_R = 8;           //                row lanes per block
 constexpr int NV3_MAX = 1024;       // 1d3v: largest nv[0] (key histogram of a pencil in shared memory)
+constexpr int GREEN_MAX = 1024;     // largest nx solved by the circulant product (adjoint engine)
 
 // device-side error bits (Ctl::err)
 enum : int { ERR_TIMEOUT = 1, ERR_NUMERIC = 2, ERR_CAPACITY = 4 };
@@ -125,6 +126,7 @@ struct FieldDev {
     float* E32;                // nx
     const double2* tw;         // exp(-2 pi i k / nx), k < nx
     const double* gmul;        // cP kappa / K^2 for m <= nx/2 (0 at m = 0 and Nyquist)
+    const double* green;       // nx <= GREEN_MAX: G of E = G (circulant) rho, else null
     double* diag;              // 3 + 3 ns
     double* hist;              // field history for marker refinement: [hist_cap][nx] FP64, or null;
                                // slot k holds E of the state after step hist_origin + k
@@ -279,6 +281,8 @@ cudaError_t configure_field_bytes(int bytes);
 // spectral tables of the Poisson solve (host) and the stand-alone solve
 void spectral_tables(int nx, double L, double cP, int softening, double2* tw, double* gm);
 size_t poisson_smem_bytes(int nx);
+void green_table(int nx, const double* gm, double* G);
+cudaError_t launch_poisson_dense(const double* rho, double* E, int nx, const double* G, cudaStream_t st);
 cudaError_t launch_poisson(const double* rho, double* E, int nx, const double2* tw, const double* gmul,
                            cudaStream_t st);
 

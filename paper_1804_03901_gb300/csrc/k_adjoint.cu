@@ -516,6 +516,15 @@ static long long nmax_active(const AdjEngine* E)
     return nmax;
 }
 
+// the Poisson solve of Eq. 6 (P rho; the backward pass applies it to e):
+// the circulant product with the Green's function on many blocks where the
+// context has the table, else the single-block FFT
+static cudaError_t solve(const StepArgs& h, const double* in, double* out, int nx, cudaStream_t st)
+{
+    if (h.fd.green) return launch_poisson_dense(in, out, nx, h.fd.green, st);
+    return launch_poisson(in, out, nx, h.fd.tw, h.fd.gmul, st);
+}
+
 // reconstruction of the stepped species at slot, rho = static + theirs, E
 template <typename T>
 static cudaError_t recon_and_field(const StepArgs& h, const StepArgs* dA, AdjEngine* E, int slot, cudaStream_t st)
@@ -525,7 +534,7 @@ static cudaError_t recon_and_field(const StepArgs& h, const StepArgs* dA, AdjEng
     k_ad_dep<T><<<dim3(grid_for(nmax_active(E)), E->h.nact), 256, 0, st>>>(dA, E->d, slot, 0);
     k_ad_fin<T><<<dim3((E->nx + 31) / 32, E->h.nact, fin_groups(E)), 256, 0, st>>>(dA, E->d, slot, 0);
     if ((e = cudaGetLastError())) return e;
-    return launch_poisson(E->h.rho, E->h.hE + (size_t)slot * E->nx, E->nx, h.fd.tw, h.fd.gmul, st);
+    return solve(h, E->h.rho, E->h.hE + (size_t)slot * E->nx, E->nx, st);
 }
 
 // charge of the species that are not stepped (immobile, not theta): once
@@ -562,7 +571,7 @@ static cudaError_t back_step(const StepArgs& h, const StepArgs* dA, AdjEngine* E
     const int copies = (int)std::min<size_t>(8, (48 * 1024) / copy_bytes);
     k_ad_e<T><<<dim3(grid_for(nmax), E->h.nact), 256, copies * copy_bytes, st>>>(dA, E->d, slot, terminal, copies);
     if ((e = cudaGetLastError())) return e;
-    if ((e = launch_poisson(E->h.e, E->h.tmp, E->nx, h.fd.tw, h.fd.gmul, st))) return e;
+    if ((e = solve(h, E->h.e, E->h.tmp, E->nx, st))) return e;
     k_ad_grid<T><<<dim3(152 * 2, E->h.nact), 256, 0, st>>>(dA, E->d, slot);
     k_ad_gather<T><<<dim3(grid_for(nmax), E->h.nact), 256, 0, st>>>(dA, E->d, slot, terminal);
     return cudaGetLastError();

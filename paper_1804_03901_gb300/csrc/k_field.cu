@@ -11,6 +11,7 @@
 #include <cooperative_groups.h>
 #include <math.h>
 
+#include <algorithm>
 #include <vector>
 
 #include "avl_internal.cuh"
@@ -488,6 +489,55 @@ void spectral_tables(int nx, double L, double cP, int softening, double2* tw, do
         }
         gm[m] = cP * kappa / K2;
     }
+}
+
+// Green's function of the spectral solve (Eq. 6): E_i = sum_j G[(i - j) mod nx]
+// rho_j with G_n = (2 / nx) sum_m gm[m] sin(2 pi m n / nx) over the modes that
+// carry a field (the multiplier -i gm[m] is odd in m, so the pairs (m, -m)
+// give a sine; k = 0 and the Nyquist mode drop out).  Angles from exact
+// integer indices (m n mod nx).
+void green_table(int nx, const double* gm, double* G)
+{
+    std::vector<double> sn(nx);
+    for (int k = 0; k < nx; ++k) sn[k] = sin(2.0 * M_PI * (double)k / (double)nx);
+    for (int n = 0; n < nx; ++n) {
+        double acc = 0.0;
+        for (int m = 1; m <= nx / 2; ++m) acc += gm[m] * sn[(int)(((long long)m * n) % nx)];
+        G[n] = 2.0 * acc / (double)nx;
+    }
+}
+
+// The same solve as the circulant product with G, spread over many blocks
+// (one warp per output, lanes over j, a fixed shuffle tree): FP64 work is
+// spread over the SMs instead of one CTA's FFT.  rho, E, G: nx FP64 values.
+__global__ void __launch_bounds__(256) k_poisson_dense(const double* __restrict__ rho, double* __restrict__ E, int nx,
+                                                       const double* __restrict__ G)
+{
+    extern __shared__ __align__(16) unsigned char smem_d[];
+    double* r = reinterpret_cast<double*>(smem_d);
+    double* g = r + nx;
+    for (int i = threadIdx.x; i < nx; i += blockDim.x) {
+        r[i] = rho[i];
+        g[i] = G[i];
+    }
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int i = blockIdx.x * nw + warp; i < nx; i += gridDim.x * nw) {
+        double acc = 0.0;
+        for (int j = lane; j < nx; j += 32) {
+            const int d = i - j;
+            acc = fma(g[d < 0 ? d + nx : d], r[j], acc);
+        }
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+        if (lane == 0) E[i] = acc;
+    }
+}
+
+cudaError_t launch_poisson_dense(const double* rho, double* E, int nx, const double* G, cudaStream_t st)
+{
+    const int blocks = std::max(1, std::min((nx + 7) / 8, 148));
+    k_poisson_dense<<<blocks, 256, (size_t)nx * 16, st>>>(rho, E, nx, G);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_poisson(const double* rho, double* E, int nx, const double2* tw, const double* gmul,
