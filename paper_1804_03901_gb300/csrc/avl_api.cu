@@ -566,7 +566,7 @@ avl_status ensure_batch_map(avl_ctx* b)
         pd[r + 1] = pd[r] + c->h.nchunk_total;
         fin[r + 1] = fin[r] + c->h.nfin_total;
         pd_smem = std::max(pd_smem, pd1_smem_needed(c->h));
-        field_smem = std::max(field_smem, (int)field_smem_bytes(c->h.fd.nx));
+        field_smem = std::max(field_smem, (int)field_smem_bytes(c->h));
         b->bm_versions[r] = c->layout_version;
     }
     AVL_CUDA(b, cudaMemcpyAsync(b->bm_mem, hostbuf.data(), bytes, cudaMemcpyHostToDevice, b->st));
@@ -687,6 +687,7 @@ avl_status avl_create(const avl_domain* dom, const avl_species* spec, int32_t ns
     fd.L = dom->L;
     fd.dx = dx;
     fd.cP = dom->poisson_const;
+    fd.we_scale = dx / (2.0 * dom->poisson_const);
     std::vector<double2> tw(nx);
     std::vector<double> gm(nx / 2 + 1, 0.0);
     spectral_tables(nx, dom->L, dom->poisson_const, dom->softening, tw.data(), gm.data());

@@ -121,6 +121,7 @@ struct FieldDev {
     int resort_miss;           // 1d1v: re-sort when more than n / resort_miss markers miss their window
                                // (default 100: the overflow path takes up to 1 % cheaper than a re-sort)
     double L, dx, cP;
+    double we_scale;           // dx / (2 cP): field energy per sum of E^2 over the cells
     double* rho;               // nx
     double* E64;               // nx
     float* E32;                // nx
@@ -208,7 +209,7 @@ cudaError_t launch_pd1_batch(int prec, const BatchMap* bm, int blocks, int smem,
 cudaError_t launch_fin1_batch(int prec, const BatchMap* bm, int blocks, int all_species, cudaStream_t st);
 cudaError_t launch_field_batch(const BatchMap* bm, int nrun, int smem, int count_step, cudaStream_t st);
 cudaError_t configure_batch1(int prec, int pd_smem, int field_smem);
-size_t field_smem_bytes(int nx);
+size_t field_smem_bytes(const StepArgs& h);
 int pd1_smem_needed(const StepArgs& h);
 // markers from the lattice generator or from caller arrays into the sorted
 // layout of buffer 0 of species s

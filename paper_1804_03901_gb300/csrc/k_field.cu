@@ -30,14 +30,37 @@ __device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_doub
 __device__ __forceinline__ double2 csub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
 __device__ __forceinline__ double2 conj2(double2 a) { return make_double2(a.x, -a.y); }
 
-// in-place radix-2 decimation-in-time FFT of length M (power of two) on
-// shared memory, input already in bit-reversed order; tw[k] = exp(-2 pi i k/N)
-// with N = 2 M; inverse uses the conjugate twiddles (no scaling).
-__device__ void fft_pow2(double2* a, int M, int N, const double2* __restrict__ tw, bool inverse)
+// in-place radix-2 decimation-in-time FFT of length M (a power of two) on
+// shared memory, input already in bit-reversed order; tw[k] = exp(-2 pi i
+// k / N) for k = 0 .. M with N = 2 M, staged in shared memory; the inverse
+// uses the conjugate twiddles (no scaling).  One butterfly per thread and
+// stage: an FP64 warp instruction occupies its SM sub-partition for the same
+// time whatever the number of active lanes, so the butterflies are packed
+// into full warps.  The first two stages, whose twiddles are 1 and -i (+i
+// for the inverse), take no multiplies.
+__device__ void fft_pow2(double2* a, int M, const double2* tw, bool inverse)
 {
-    for (int len = 2; len <= M; len <<= 1) {
+    // stage 1: (2 t, 2 t + 1), w = 1
+    for (int t = threadIdx.x; t < M / 2; t += blockDim.x) {
+        const double2 u = a[2 * t], v = a[2 * t + 1];
+        a[2 * t] = cadd(u, v);
+        a[2 * t + 1] = csub(u, v);
+    }
+    __syncthreads();
+    if (M >= 4) {
+        // stage 2: (4 g + k, 4 g + k + 2), w = 1 for k = 0 and -i (+i) for k = 1
+        for (int t = threadIdx.x; t < M / 2; t += blockDim.x) {
+            const int i1 = 4 * (t >> 1) + (t & 1), i2 = i1 + 2;
+            const double2 u = a[i1], x = a[i2];
+            const double2 v = (t & 1) ? (inverse ? make_double2(-x.y, x.x) : make_double2(x.y, -x.x)) : x;
+            a[i1] = cadd(u, v);
+            a[i2] = csub(u, v);
+        }
+        __syncthreads();
+    }
+    for (int len = 8; len <= M; len <<= 1) {
         const int half = len >> 1;
-        const int step = N / len;
+        const int step = 2 * M / len;
         for (int t = threadIdx.x; t < M / 2; t += blockDim.x) {
             const int grp = t / half, k = t - grp * half;
             const int i1 = grp * len + k, i2 = i1 + half;
@@ -54,64 +77,99 @@ __device__ void fft_pow2(double2* a, int M, int N, const double2* __restrict__ t
 
 __device__ __forceinline__ int bitrev(int x, int bits) { return (int)(__brev((unsigned)x) >> (32 - bits)); }
 
+// Shared memory of the solve: rho / E (nx doubles), the spectrum (nx/2 + 2
+// complex) and, for power-of-two nx, the staged tables: twiddles (nx/2 + 1
+// complex) and multipliers (nx/2 + 1 doubles).
+__host__ __device__ inline size_t poisson_rho_bytes(int nx) { return ((size_t)nx * 8 + 15) / 16 * 16; }
+__host__ __device__ inline size_t poisson_work_bytes(int nx) { return ((size_t)nx / 2 + 2) * 16; }
+__host__ __device__ inline bool poisson_pow2(int nx) { return nx >= 4 && (nx & (nx - 1)) == 0; }
+__host__ __device__ inline size_t poisson_smem_bytes_dev(int nx)
+{
+    return poisson_rho_bytes(nx) + poisson_work_bytes(nx) + (poisson_pow2(nx) ? ((size_t)nx / 2 + 1) * 24 : 0);
+}
+
+// 1 / (4 M) for M = nx/2 = 2^bits: the halvings of the even/odd split and
+// the 1/M of the inverse transform, an exact power of two set from its
+// exponent (no FP64 division)
+__device__ __forceinline__ double poisson_scale(int bits)
+{
+    return __longlong_as_double((long long)(1023 - bits - 2) << 52);
+}
+
+__device__ __forceinline__ int log2_pow2(int M)
+{
+    int bits = 0;
+    while ((1 << bits) < M) ++bits;
+    return bits;
+}
+
+// Tables of the power-of-two solve into shared memory: twiddles
+// exp(-2 pi i k / nx) and multipliers gmul[k] / (4 M), k = 0 .. nx/2.  Whole
+// block; the caller synchronises before poisson_spectral.
+__device__ void stage_tables(double2* tw_s, double* gm_s, const double2* __restrict__ tw,
+                             const double* __restrict__ gmul, int nx)
+{
+    const double c = poisson_scale(log2_pow2(nx / 2));
+    for (int k = threadIdx.x; k <= nx / 2; k += blockDim.x) {
+        tw_s[k] = tw[k];
+        gm_s[k] = gmul[k] * c;
+    }
+}
+
 // Spectral Poisson solve (Eq. 5 / Eq. 6a-c) by the whole block: rho_s holds
-// rho in shared memory (nx doubles, overwritten), work is shared scratch of
-// nx/2 + 2 complex values; tw[k] = exp(-2 pi i k / nx), gmul[m] = cP kappa_m /
-// K2_m (zero at m = 0 and at the Nyquist mode).  Writes E (nx) to Eout.
-__device__ void poisson_spectral(double* rho_s, double2* work, double* Eout, int nx, int pow2,
-                                 const double2* __restrict__ tw, const double* __restrict__ gmul)
+// rho in shared memory (nx doubles) and holds E on return; work is shared
+// scratch of nx/2 + 2 complex values; tw_s, gm_s the staged tables
+// (power-of-two nx); tw[k] = exp(-2 pi i k / nx) and gmul[m] = cP kappa_m /
+// K2_m (zero at m = 0 and at the Nyquist mode) in global memory.
+//
+// Power-of-two nx: rho packed as z_n = rho_2n + i rho_2n+1 goes through one
+// complex FFT of length M = nx/2; the modes m and M - m are unpacked
+// together (X = rho-hat, Eq. 6a), multiplied by -i g (Eq. 6b-c) and packed
+// back for the inverse transform, whose output pairs are E_2n, E_2n+1.  The
+// halvings of the even/odd split and the 1/M of the inverse, all powers of
+// two, are folded into g.
+__device__ void poisson_spectral(double* rho_s, double2* work, const double2* tw_s, const double* gm_s, int nx,
+                                 int pow2, const double2* __restrict__ tw, const double* __restrict__ gmul)
 {
     if (pow2) {
         const int M = nx / 2;
-        int bits = 0;
-        while ((1 << bits) < M) ++bits;
-        for (int n = threadIdx.x; n < M; n += FIELD_THREADS)
+        const int bits = log2_pow2(M);
+        for (int n = threadIdx.x; n < M; n += blockDim.x)
             work[bitrev(n, bits)] = make_double2(rho_s[2 * n], rho_s[2 * n + 1]);
         __syncthreads();
-        fft_pow2(work, M, nx, tw, false);
-        // unpack X_m = Ev_m + W^m Od_m and form Ehat_m = -i g_m X_m  (m = 0..M)
-        // then pack Y_m = Ev'_m + i Od'_m of the field for the inverse.
-        double2* Y = reinterpret_cast<double2*>(rho_s);   // reuse: needs M * 16 = nx * 8 bytes
-        // compute Ehat into registers per m, then pair (m, M - m)
-        for (int m = threadIdx.x; m < M; m += FIELD_THREADS) {
-            // X_m and X_{M-m}
-            const double2 Zm = work[m];
-            const double2 Zc = conj2(work[(M - m) % M]);
-            const double2 ev = make_double2(0.5 * (Zm.x + Zc.x), 0.5 * (Zm.y + Zc.y));
-            const double2 dd = make_double2(0.5 * (Zm.x - Zc.x), 0.5 * (Zm.y - Zc.y));   // = i Od
-            const double2 od = make_double2(dd.y, -dd.x);                                 // Od = -i dd
-            const double2 Xm = cadd(ev, cmul(tw[m], od));
-            // partner index p = M - m (for m = 0 the partner is the Nyquist mode M)
-            const int mp = M - m;
-            const double2 Zp = work[mp % M];
-            const double2 Zpc = conj2(work[m]);   // Z_{M - mp} = Z_m
-            const double2 evp = make_double2(0.5 * (Zp.x + Zpc.x), 0.5 * (Zp.y + Zpc.y));
-            const double2 ddp = make_double2(0.5 * (Zp.x - Zpc.x), 0.5 * (Zp.y - Zpc.y));
-            const double2 odp = make_double2(ddp.y, -ddp.x);
-            double2 twp = (mp < nx) ? tw[mp] : make_double2(1.0, 0.0);
-            const double2 Xp = cadd(evp, cmul(twp, odp));
-            // Ehat = -i g X  ->  (g X.y, -g X.x)
-            const double gm = gmul[m], gp = gmul[mp];
+        fft_pow2(work, M, tw_s, false);
+        double2* Y = reinterpret_cast<double2*>(rho_s);   // M complex values over the nx doubles
+        // thread t takes the modes m = t and M - t; thread 0 takes m = M/2,
+        // its own partner, and Y_0 = 0 (g vanishes at m = 0 and at the
+        // Nyquist mode M), so that M/2 threads fill whole warps
+        if (threadIdx.x == 0) Y[0] = make_double2(0.0, 0.0);
+        for (int t = threadIdx.x; t < M / 2; t += blockDim.x) {
+            const int m = t == 0 ? M / 2 : t;
+            const int p = M - m;
+            const double2 A = work[m];
+            const double2 B = conj2(work[p]);
+            const double2 S = cadd(A, B), D = csub(A, B);
+            // W^p = -conj(W^m), so with V = W^m (-i D):
+            // 2 X_m = S + V,  2 X_p = conj(S) + W^p (i conj D) = conj(S - V)
+            const double2 twm = tw_s[m];
+            const double2 V = cmul(twm, make_double2(D.y, -D.x));
+            const double2 Xm = cadd(S, V), Xp = conj2(csub(S, V));
+            // E-hat = -i g X, with the scale folded into g
+            const double gm = gm_s[m], gp = gm_s[p];
             const double2 Em = make_double2(gm * Xm.y, -gm * Xm.x);
             const double2 Ep = make_double2(gp * Xp.y, -gp * Xp.x);
-            // inverse pack: Ev'_m = (E_m + conj(E_{M-m}))/2, Od'_m = (E_m - conj(E_{M-m}))/2 * exp(+2 pi i m/N)
-            const double2 Epc = conj2(Ep);
-            const double2 ev2 = make_double2(0.5 * (Em.x + Epc.x), 0.5 * (Em.y + Epc.y));
-            const double2 od2 = cmul(make_double2(0.5 * (Em.x - Epc.x), 0.5 * (Em.y - Epc.y)), conj2(tw[m]));
-            Y[bitrev(m, bits)] = make_double2(ev2.x - od2.y, ev2.y + od2.x);   // ev2 + i od2
+            // Y_m = F + i O with F = E_m + conj E_p, O = (E_m - conj E_p) conj(W^m);
+            // for the partner F' = conj(F) and O' = conj(O)
+            const double2 F = cadd(Em, conj2(Ep)), O = cmul(csub(Em, conj2(Ep)), conj2(twm));
+            Y[bitrev(m, bits)] = make_double2(F.x - O.y, F.y + O.x);
+            if (p != m) Y[bitrev(p, bits)] = make_double2(F.x + O.y, -F.y + O.x);
         }
         __syncthreads();
-        fft_pow2(Y, M, nx, tw, true);
-        const double inv = 1.0 / (double)M;
-        for (int n = threadIdx.x; n < M; n += FIELD_THREADS) {
-            const double2 y = Y[n];
-            Eout[2 * n] = y.x * inv;
-            Eout[2 * n + 1] = y.y * inv;
-        }
+        fft_pow2(Y, M, tw_s, true);
     } else {
         // direct DFT: Ehat_m for m = 1 .. (nx-1)/2, then E_i = (2/N) sum Re(Ehat_m e^{+i})
         const int mmax = (nx - 1) / 2;
-        for (int m = 1 + threadIdx.x; m <= mmax; m += FIELD_THREADS) {
+        for (int m = 1 + threadIdx.x; m <= mmax; m += blockDim.x) {
             double rr = 0.0, ri = 0.0;
             for (int i = 0; i < nx; ++i) {
                 const double2 w = tw[(int)(((long long)m * i) % nx)];
@@ -122,26 +180,27 @@ __device__ void poisson_spectral(double* rho_s, double2* work, double* Eout, int
             work[m] = make_double2(g * ri, -g * rr);   // -i g (rr + i ri)
         }
         __syncthreads();
-        for (int i = threadIdx.x; i < nx; i += FIELD_THREADS) {
+        for (int i = threadIdx.x; i < nx; i += blockDim.x) {
             double acc = 0.0;
             for (int m = 1; m <= mmax; ++m) {
                 const double2 w = tw[(int)(((long long)m * i) % nx)];
                 // Re(E_m * conj(w))
                 acc += work[m].x * w.x + work[m].y * w.y;
             }
-            Eout[i] = 2.0 * acc / (double)nx;
+            rho_s[i] = 2.0 * acc / (double)nx;
         }
+        __syncthreads();
     }
 }
 
 // Markers a chunk's best deposit window holds: the largest sum of wk
 // consecutive bins of its HIST_S-bin key histogram (the window best_window
-// places).  Called by a whole warp; one coalesced load and a warp scan.
-__device__ int best_cover_warp(const int* __restrict__ hist, int wk)
+// places).  Called by a whole warp with lane l holding bins 2 l and 2 l + 1
+// (one coalesced load); a warp scan.
+__device__ __forceinline__ int best_cover_warp(int2 h, int wk)
 {
     static_assert(HIST_S == 64, "two bins per lane");
     const int lane = threadIdx.x & 31;
-    const int2 h = reinterpret_cast<const int2*>(hist)[lane];
     int S = h.x + h.y;   // inclusive prefix of the bin pairs over the lanes
     for (int o = 1; o < 32; o <<= 1) {
         const int y = __shfl_up_sync(0xffffffffu, S, o);
@@ -173,8 +232,16 @@ constexpr int FIELD_DIAG = FIELD_CLUSTER - 1;     // the last CTA sums the diagn
 // miss more than a small fraction of the markers) and if so prepares the
 // slots and the key histograms of the re-sorted chunks; then CTAs 1.. clear
 // the key counts consumed by this step for reuse.
-__device__ void resort_work(const StepArgs* __restrict__ A, int rank)
+__device__ __forceinline__ unsigned dynamic_smem_bytes()
 {
+    unsigned r;
+    asm("mov.u32 %0, %%dynamic_smem_size;" : "=r"(r));
+    return r;
+}
+
+__device__ void resort_work(const StepArgs* __restrict__ A, int rank, int* dyn)
+{
+    const size_t dyn_bytes = dynamic_smem_bytes();
     const Ctl* ctl = A->ctl;
     __shared__ unsigned long long miss;
     for (int s = rank - 1; rank <= FIELD_DECIDE && s < A->ns; s += FIELD_DECIDE) {
@@ -185,16 +252,33 @@ __device__ void resort_work(const StepArgs* __restrict__ A, int rank)
         const int* kref = sp.KB[cur_after];
         const int* cnt = sp.cnt[1 - hs];
         const int* far = sp.far_cnt[1 - hs];
+        // the scan of the re-sort in this CTA's dynamic shared memory (unused
+        // by the CTAs other than 0) when the key range fits
+        int* base_s = ((size_t)sp.nvflat + 1) * 4 <= dyn_bytes ? dyn : nullptr;
         // markers outside the best window of their chunk (a warp per chunk)
         if (threadIdx.x == 0) miss = 0;
         __syncthreads();
         const int wk = max(1, min(HIST_S, sp.Wmax - 2 * HALO - 1));
         unsigned long long my = 0;
-        for (int c = threadIdx.x >> 5; c < sp.nchunk; c += FIELD_THREADS / 32) {
-            const int covered = best_cover_warp(cnt + (size_t)c * HIST_S, wk);
-            const int beg = c * sp.M;
-            const int end = (int)min((long long)(c + 1) * sp.M, sp.n);
-            if ((threadIdx.x & 31) == 0) my += (unsigned long long)((end - beg) - covered);
+        // two chunks per warp and pass, the next pass's histograms loaded ahead
+        const int nw = FIELD_THREADS / 32, lane = threadIdx.x & 31;
+        const int2* cnt2 = reinterpret_cast<const int2*>(cnt);
+        auto load = [&](int c) { return c < sp.nchunk ? cnt2[(size_t)c * (HIST_S / 2) + lane] : make_int2(0, 0); };
+        int c = threadIdx.x >> 5;
+        int2 ha = load(c), hb = load(c + nw);
+        for (; c < sp.nchunk; c += 2 * nw) {
+            const int2 a = ha, b = hb;
+            ha = load(c + 2 * nw);
+            hb = load(c + 3 * nw);
+            const int cov_a = best_cover_warp(a, wk), cov_b = best_cover_warp(b, wk);
+            if (lane == 0) {
+                const long long beg = (long long)c * sp.M;
+                my += (unsigned long long)(min(beg + sp.M, sp.n) - beg - cov_a);
+                if (c + nw < sp.nchunk) {
+                    const long long beg_b = (long long)(c + nw) * sp.M;
+                    my += (unsigned long long)(min(beg_b + sp.M, sp.n) - beg_b - cov_b);
+                }
+            }
         }
         if (my) atomicAdd(&miss, my);
         __syncthreads();
@@ -210,10 +294,10 @@ __device__ void resort_work(const StepArgs* __restrict__ A, int rank)
             cw->sort_next[s] = resort ? 1 : 0;
         }
         if (resort) {
-            scan_layout(sp, kref, cnt, far, true, sp.KB[1 - cur_after]);
+            scan_layout(sp, kref, cnt, far, true, sp.KB[1 - cur_after], base_s);
             // the next step deposits from the re-sorted layout: its window
             // placement takes the key histograms of the re-sorted chunks
-            sorted_chunk_hist(sp, sp.KB[1 - cur_after], sp.cnt[1 - hs]);
+            sorted_chunk_hist(sp, sp.KB[1 - cur_after], sp.cnt[1 - hs], base_s ? base_s : sp.base_new);
         }
         __syncthreads();
     }
@@ -275,10 +359,17 @@ __global__ void __cluster_dims__(FIELD_CLUSTER, 1, 1) __launch_bounds__(FIELD_TH
     const int rank = (int)cluster.block_rank();
     const FieldDev& fd = A->fd;
     const int nx = fd.nx;
-    double* rho_s = reinterpret_cast<double*>(smem);                 // nx
-    double2* work = reinterpret_cast<double2*>(smem + ((size_t)nx * 8 + 15) / 16 * 16);   // nx/2 + 1
+    double* rho_s = reinterpret_cast<double*>(smem);                                  // nx
+    double2* work = reinterpret_cast<double2*>(smem + poisson_rho_bytes(nx));          // nx/2 + 2
+    double2* tw_s = reinterpret_cast<double2*>(smem + poisson_rho_bytes(nx) + poisson_work_bytes(nx));
+    double* gm_s = reinterpret_cast<double*>(tw_s + nx / 2 + 1);
     __shared__ double red[FIELD_THREADS / 32];
     __shared__ double dfin[3 * MAXS];   // per-species diagnostics sums (written by CTA FIELD_DIAG)
+    __shared__ float shf_s[MAXS];       // per species: rows per unit field and step (shift table)
+    __shared__ int tgt_s[MAXS];         // per species: shift table this kernel writes
+
+    // CTA 0 stages the tables of the solve while the cluster sums rho
+    if (rank == 0 && fd.pow2) stage_tables(tw_s, gm_s, fd.tw, fd.gmul, nx);
 
     // --- rho slice: sum over species and row blocks (fixed order) --------
     // tpx threads per column (a power of two up to 32) take every tpx-th
@@ -310,31 +401,55 @@ __global__ void __cluster_dims__(FIELD_CLUSTER, 1, 1) __launch_bounds__(FIELD_TH
     cluster.sync();
     if (rank != 0) {
         if (rank == FIELD_DIAG) diag_sums(A, cluster.map_shared_rank(dfin, 0));
-        if (count_step) resort_work(A, rank);
+        if (count_step) resort_work(A, rank, reinterpret_cast<int*>(smem));
         cluster.sync();
         return;
     }
 
     // --- CTA 0: Poisson --------------------------------------------------
     for (int x = threadIdx.x; x < nx; x += FIELD_THREADS) fd.rho[x] = rho_s[x];
-    double* Eout = fd.E64;
-    poisson_spectral(rho_s, work, Eout, nx, fd.pow2, fd.tw, fd.gmul);
-    __syncthreads();
-    // --- E in FP32, field energy, diagnostics row --------------------------
-    double we = 0.0;
-    for (int x = threadIdx.x; x < nx; x += FIELD_THREADS) {
-        const double e = Eout[x];
-        fd.E32[x] = (float)e;
-        we += e * e;
+    // per-species constants of the shift tables: loads issued before the
+    // solve, their values used after it
+    double qm_dt = 0.0, inv_dv = 0.0;
+    int mobile = 0, shsel = 0;
+    if (threadIdx.x < A->ns) {
+        const SpDev& sp = A->sp[threadIdx.x];
+        mobile = sp.mobile;
+        qm_dt = sp.qm_dt;
+        inv_dv = sp.inv_dv[0];
+        shsel = A->ctl->shsel[threadIdx.x];
     }
+    poisson_spectral(rho_s, work, tw_s, gm_s, nx, fd.pow2, fd.tw, fd.gmul);
+    if (threadIdx.x < A->ns) {
+        shf_s[threadIdx.x] = mobile ? (float)(qm_dt * inv_dv) : 0.f;
+        tgt_s[threadIdx.x] = count_step ? 1 - shsel : shsel;
+    }
+    const double* E_s = rho_s;   // E, FP64, in shared memory
+    // --- E in FP64 and FP32, field energy, diagnostics row -----------------
+    float* E32_s = reinterpret_cast<float*>(work);   // the spectrum is no longer needed
+    for (int x = threadIdx.x; x < nx; x += FIELD_THREADS) {
+        const double e = E_s[x];
+        const float e32 = (float)e;
+        fd.E64[x] = e;
+        fd.E32[x] = e32;
+        E32_s[x] = e32;
+    }
+    // field energy sum by four full warps, one per SM sub-partition (FP64
+    // instructions cost the same for any number of active lanes)
+    constexpr int WE_THREADS = 128;
+    double we = 0.0;
+    if (threadIdx.x < WE_THREADS)
+        for (int x = threadIdx.x; x < nx; x += WE_THREADS) we = fma(E_s[x], E_s[x], we);
     // field history (marker refinement): E of the state this kernel finishes
     if (fd.hist) {
         const long long slot = (count_step ? A->ctl->step + 1 : A->ctl->step) - fd.hist_origin;
         if (slot >= 0 && slot < fd.hist_cap)
-            for (int x = threadIdx.x; x < nx; x += FIELD_THREADS) fd.hist[slot * nx + x] = Eout[x];
+            for (int x = threadIdx.x; x < nx; x += FIELD_THREADS) fd.hist[slot * nx + x] = E_s[x];
     }
-    for (int o = 16; o > 0; o >>= 1) we += __shfl_down_sync(0xffffffffu, we, o);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = we;
+    if (threadIdx.x < WE_THREADS) {
+        for (int o = 16; o > 0; o >>= 1) we += __shfl_down_sync(0xffffffffu, we, o);
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = we;
+    }
     __syncthreads();
     // velocity rows the new field moves a marker in one step, per column
     // (used by the next step's deposit windows and finalize).  After a step
@@ -350,13 +465,14 @@ __global__ void __cluster_dims__(FIELD_CLUSTER, 1, 1) __launch_bounds__(FIELD_TH
         __syncthreads();
         for (int s = 0; s < A->ns; ++s) {
             const SpDev& sp = A->sp[s];
-            const double f = sp.mobile ? sp.qm_dt * sp.inv_dv[0] : 0.0;
-            const int tgt = count_step ? 1 - cw->shsel[s] : cw->shsel[s];
+            // FP32: the table only places the deposit windows
+            const float f = shf_s[s];
+            const int tgt = tgt_s[s];
             int lmin = 0x7fffffff, lmax = -0x7fffffff;
             for (int x = threadIdx.x; x < nx; x += FIELD_THREADS) {
-                double d = f * Eout[x];
-                d = d > 1.0e6 ? 1.0e6 : (d < -1.0e6 ? -1.0e6 : d);
-                const int sh = isfinite(d) ? (int)rint(d) : 0;
+                float d = f * E32_s[x];
+                d = d > 1.0e6f ? 1.0e6f : (d < -1.0e6f ? -1.0e6f : d);
+                const int sh = isfinite(d) ? __float2int_rn(d) : 0;
                 sp.shift[tgt][x] = sh;
                 if (!count_step) sp.shift[1 - tgt][x] = 0;
                 lmin = min(lmin, sh);
@@ -372,7 +488,7 @@ __global__ void __cluster_dims__(FIELD_CLUSTER, 1, 1) __launch_bounds__(FIELD_TH
         __syncthreads();
         if (threadIdx.x < A->ns) {
             const int q = threadIdx.x;
-            const int tgt = count_step ? 1 - cw->shsel[q] : cw->shsel[q];
+            const int tgt = tgt_s[q];
             cw->shift_min[q][tgt] = smin_s[q];
             cw->shift_max[q][tgt] = smax_s[q];
             if (!count_step) {
@@ -385,50 +501,70 @@ __global__ void __cluster_dims__(FIELD_CLUSTER, 1, 1) __launch_bounds__(FIELD_TH
     __shared__ double WE_s;
     if (threadIdx.x == 0) {
         double s2 = 0.0;
-        for (int w = 0; w < FIELD_THREADS / 32; ++w) s2 += red[w];
-        WE_s = s2 * fd.dx / (2.0 * fd.cP);
+        for (int w = 0; w < WE_THREADS / 32; ++w) s2 += red[w];
+        WE_s = s2 * fd.we_scale;
     }
     // wait for the diagnostics sums, the re-sort decisions and the clearing by
     // the other CTAs, then write the diagnostics row and make this step's
     // markers and key counts current
+    // warp 0, lane s: species s's control values that no other CTA of this
+    // kernel writes, loaded before the barrier
+    Ctl* ctl = A->ctl;
+    const int ns = A->ns;
+    const int s = threadIdx.x;
+    const bool lane_sp = threadIdx.x < 32 && s < ns;
+    unsigned long long ovf = 0, mv = 0, fm = 0;
+    int sp_dim = 0, sp_mobile = 0, sp_nchunk = 0, sort_now = 0;
+    long long sp_n = 0;
+    if (lane_sp) {
+        const SpDev& sp = A->sp[s];
+        sp_dim = sp.nvdim;
+        sp_mobile = sp.mobile;
+        sp_nchunk = sp.nchunk;
+        sp_n = sp.n;
+        ovf = ctl->ovf_count[s];
+        mv = ctl->movers[s];
+        fm = ctl->far_movers[s];
+        sort_now = ctl->sort_now[s];
+    }
     cluster.sync();
-    if (threadIdx.x == 0) {
-        Ctl* ctl = A->ctl;
-        const int ns = A->ns;
+    if (threadIdx.x < 32) {
         const double WE = WE_s;
-        double wk_tot = 0.0;
-        bool bad = !isfinite(WE);
-        for (int s = 0; s < ns; ++s) {
-            const double N = dfin[3 * s + 0], Wk = dfin[3 * s + 1], S = dfin[3 * s + 2];
+        double N = 0.0, Wk = 0.0, S = 0.0;
+        if (s < ns) {
+            N = dfin[3 * s + 0];
+            Wk = dfin[3 * s + 1];
+            S = dfin[3 * s + 2];
             fd.diag[3 + s] = Wk;
             fd.diag[3 + ns + s] = N;
             fd.diag[3 + 2 * ns + s] = S;
-            wk_tot += Wk;
-            bad = bad || !isfinite(N) || !isfinite(Wk) || !isfinite(S);
         }
-        fd.diag[0] = WE;
-        fd.diag[1] = wk_tot;
-        fd.diag[2] = WE + wk_tot;
-        if (bad) ctl->err |= ERR_NUMERIC;
-        for (int s = 0; s < ns; ++s) {
-            ctl->ovf_last[s] = ctl->ovf_count[s];
+        const bool bad = __any_sync(0xffffffffu, s < ns && (!isfinite(N) || !isfinite(Wk) || !isfinite(S))) ||
+                         !isfinite(WE);
+        if (s == 0) {
+            double wk_tot = 0.0;   // species order
+            for (int q = 0; q < ns; ++q) wk_tot += dfin[3 * q + 1];
+            fd.diag[0] = WE;
+            fd.diag[1] = wk_tot;
+            fd.diag[2] = WE + wk_tot;
+            if (bad) ctl->err |= ERR_NUMERIC;
+            if (count_step) ctl->step += 1;
+        }
+        if (s < ns) {
+            ctl->ovf_last[s] = ovf;
             ctl->ovf_count[s] = 0;
-        }
-        for (int s = 0; s < ns; ++s) {
-            const SpDev& sp = A->sp[s];
-            if (sp.nvdim == 3) {
+            if (sp_dim == 3) {
                 // 1d3v: the deposit just finalized becomes current, the other
                 // accumulator (cleared by the finalize) takes the next one.
                 // Re-sort when more than 1/64 of the markers sit off their
                 // segment's row, or 1/4096 two or more rows off.
-                const bool deposited = count_step ? sp.mobile != 0 : true;
+                const bool deposited = count_step ? sp_mobile != 0 : true;
                 if (deposited) ctl->asel[s] ^= 1;
-                const unsigned long long mv = ctl->movers[s], fm = ctl->far_movers[s];
                 ctl->movers[s] = 0;
                 ctl->far_movers[s] = 0;
-                if (count_step && sp.mobile) {
+                if (count_step && sp_mobile) {
                     ctl->movers_last[s] = mv;
-                    const unsigned long long n = (unsigned long long)sp.n;
+                    const unsigned long long n = (unsigned long long)sp_n;
                     const int so = (n > 0 && (mv * 64ull > n || fm * 4096ull > n)) ? 1 : 0;
                     ctl->sort_now[s] = so;
                     if (so) {
@@ -436,19 +572,16 @@ __global__ void __cluster_dims__(FIELD_CLUSTER, 1, 1) __launch_bounds__(FIELD_TH
                         ctl->nsort[s] += 1;
                     }
                 }
-                continue;
+            } else if (count_step && sp_mobile && sp_nchunk > 0) {
+                if (sort_now) {
+                    ctl->cur[s] = 1 - ctl->cur[s];
+                    ctl->nsort[s] += 1;
+                }
+                ctl->sort_now[s] = ctl->sort_next[s];
+                ctl->hsel[s] = 1 - ctl->hsel[s];
+                ctl->shsel[s] = 1 - ctl->shsel[s];
             }
-            if (!count_step) continue;
-            if (!sp.mobile || sp.nchunk == 0) continue;
-            if (ctl->sort_now[s]) {
-                ctl->cur[s] = 1 - ctl->cur[s];
-                ctl->nsort[s] += 1;
-            }
-            ctl->sort_now[s] = ctl->sort_next[s];
-            ctl->hsel[s] = 1 - ctl->hsel[s];
-            ctl->shsel[s] = 1 - ctl->shsel[s];
         }
-        if (count_step) ctl->step += 1;
     }
 }
 
@@ -459,13 +592,17 @@ __global__ void __launch_bounds__(FIELD_THREADS)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     double* rho_s = reinterpret_cast<double*>(smem);
-    double2* work = reinterpret_cast<double2*>(smem + ((size_t)nx * 8 + 15) / 16 * 16);
+    double2* work = reinterpret_cast<double2*>(smem + poisson_rho_bytes(nx));
+    double2* tw_s = reinterpret_cast<double2*>(smem + poisson_rho_bytes(nx) + poisson_work_bytes(nx));
+    double* gm_s = reinterpret_cast<double*>(tw_s + nx / 2 + 1);
+    if (pow2) stage_tables(tw_s, gm_s, tw, gmul, nx);
     for (int x = threadIdx.x; x < nx; x += FIELD_THREADS) rho_s[x] = rho[x];
     __syncthreads();
-    poisson_spectral(rho_s, work, E, nx, pow2, tw, gmul);
+    poisson_spectral(rho_s, work, tw_s, gm_s, nx, pow2, tw, gmul);
+    for (int x = threadIdx.x; x < nx; x += FIELD_THREADS) E[x] = rho_s[x];
 }
 
-size_t poisson_smem_bytes(int nx) { return ((size_t)nx * 8 + 15) / 16 * 16 + ((size_t)nx / 2 + 2) * 16; }
+size_t poisson_smem_bytes(int nx) { return poisson_smem_bytes_dev(nx); }
 
 void spectral_tables(int nx, double L, double cP, int softening, double2* tw, double* gm)
 {
@@ -546,28 +683,24 @@ cudaError_t launch_poisson(const double* rho, double* E, int nx, const double2* 
     const size_t smem = poisson_smem_bytes(nx);
     cudaError_t e = raise_smem_limit(k_poisson, (int)smem);
     if (e) return e;
-    const int pow2 = (nx >= 4 && (nx & (nx - 1)) == 0) ? 1 : 0;
+    const int pow2 = poisson_pow2(nx) ? 1 : 0;
     k_poisson<<<1, FIELD_THREADS, smem, st>>>(rho, E, nx, pow2, tw, gmul);
     return cudaGetLastError();
 }
 
-static size_t field_smem(const StepArgs& h)
-{
-    const int nx = h.fd.nx;
-    return ((size_t)nx * 8 + 15) / 16 * 16 + ((size_t)nx / 2 + 2) * 16;
-}
+// dynamic shared memory of the field kernel: the solve's (CTA 0)
+size_t field_smem_bytes(const StepArgs& h) { return poisson_smem_bytes(h.fd.nx); }
 
 cudaError_t configure_field_bytes(int bytes) { return raise_smem_limit(k_field, bytes); }
 
-cudaError_t configure_field(const StepArgs& h) { return configure_field_bytes((int)field_smem(h)); }
+cudaError_t configure_field(const StepArgs& h) { return configure_field_bytes((int)field_smem_bytes(h)); }
 
 cudaError_t launch_field(const StepArgs& h, const StepArgs* d, int count_step, cudaStream_t st)
 {
-    k_field<<<FIELD_CLUSTER, FIELD_THREADS, field_smem(h), st>>>(d, count_step, nullptr);
+    k_field<<<FIELD_CLUSTER, FIELD_THREADS, field_smem_bytes(h), st>>>(d, count_step, nullptr);
     return cudaGetLastError();
 }
 
-size_t field_smem_bytes(int nx) { return ((size_t)nx * 8 + 15) / 16 * 16 + ((size_t)nx / 2 + 2) * 16; }
 
 cudaError_t launch_field_batch(const BatchMap* bm, int nrun, int smem, int count_step, cudaStream_t st)
 {

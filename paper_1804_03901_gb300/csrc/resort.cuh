@@ -65,9 +65,11 @@ __device__ __forceinline__ void chunk_range(const int* kref, int nch, int k, boo
 // markers of that key; chunks in order), far_cur[k] (first slot of the far
 // markers of key k) and, if kb_new is given, the reference key of every
 // chunk of the new layout (the key of its first slot).  kref is staged in
-// shared memory when it fits.  Called by a whole block.
+// shared memory when it fits; base_s, if given, is block shared memory of
+// nvflat + 1 ints where the scan runs (and keeps base_new for the caller).
+// Called by a whole block.
 static __device__ void scan_layout(const SpDev& sp, const int* __restrict__ kref_g, const int* __restrict__ cnt,
-                            const int* __restrict__ far_cnt, bool sorted, int* kb_new)
+                            const int* __restrict__ far_cnt, bool sorted, int* kb_new, int* base_s = nullptr)
 {
     const int nv = sp.nvflat, nch = sp.nchunk;
     __shared__ int warp_sums[32];
@@ -78,17 +80,19 @@ static __device__ void scan_layout(const SpDev& sp, const int* __restrict__ kref
         for (int c = threadIdx.x; c < nch; c += blockDim.x) kref_s[c] = kref_g[c];
         kref = kref_s;
     }
+    int* base = base_s ? base_s : sp.base_new;
     __syncthreads();
     // (a) totals per key
     for (int k = threadIdx.x; k < nv; k += blockDim.x) {
         int tot = far_cnt[k];
         int c0, c1;
         chunk_range(kref, nch, k, sorted, c0, c1);
+#pragma unroll 4
         for (int c = c0; c < c1; ++c) {
             const int r = k - (kref[c] - HIST_R);
             if (r >= 0 && r < HIST_S) tot += cnt[(size_t)c * HIST_S + r];
         }
-        sp.base_new[k] = tot;
+        base[k] = tot;
     }
     __syncthreads();
     // (b) exclusive scan over keys
@@ -97,7 +101,7 @@ static __device__ void scan_layout(const SpDev& sp, const int* __restrict__ kref
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     for (int b0 = 0; b0 < nv; b0 += blockDim.x) {
         const int i = b0 + threadIdx.x;
-        const int v = i < nv ? sp.base_new[i] : 0;
+        const int v = i < nv ? base[i] : 0;
         int x = v;
         for (int o = 1; o < 32; o <<= 1) {
             const int y = __shfl_up_sync(0xffffffffu, x, o);
@@ -115,18 +119,21 @@ static __device__ void scan_layout(const SpDev& sp, const int* __restrict__ kref
         }
         __syncthreads();
         const int incl = x + (warp > 0 ? warp_sums[warp - 1] : 0) + carry;
-        if (i < nv) sp.base_new[i] = incl - v;
+        if (i < nv) base[i] = incl - v;
         __syncthreads();
         if (threadIdx.x == blockDim.x - 1) carry = incl;
         __syncthreads();
     }
-    if (threadIdx.x == 0) sp.base_new[nv] = carry;
+    if (threadIdx.x == 0) base[nv] = carry;
     __syncthreads();
+    if (base_s)
+        for (int k = threadIdx.x; k <= nv; k += blockDim.x) sp.base_new[k] = base_s[k];
     // (c) first slot of every (chunk, key), then of the far markers of each key
     for (int k = threadIdx.x; k < nv; k += blockDim.x) {
-        int run = sp.base_new[k];
+        int run = base[k];
         int c0, c1;
         chunk_range(kref, nch, k, sorted, c0, c1);
+#pragma unroll 4
         for (int c = c0; c < c1; ++c) {
             const int r = k - (kref[c] - HIST_R);
             if (r >= 0 && r < HIST_S) {
@@ -144,7 +151,7 @@ static __device__ void scan_layout(const SpDev& sp, const int* __restrict__ kref
             int lo = 0, hi = nv;   // largest k with base_new[k] <= p
             while (hi - lo > 1) {
                 const int mid = (lo + hi) >> 1;
-                if (sp.base_new[mid] <= p) lo = mid; else hi = mid;
+                if (base[mid] <= p) lo = mid; else hi = mid;
             }
             kb_new[c] = lo;
         }
@@ -153,10 +160,12 @@ static __device__ void scan_layout(const SpDev& sp, const int* __restrict__ kref
 }
 
 // Key histograms of the chunks of a layout sorted by key, from the first
-// slot of every key (base_new, written by scan_layout): cnt_out[c][r] = the
-// slots of chunk c ([c M, (c + 1) M)) that hold key kb_new[c] - HIST_R + r.
-// Called by a whole block after scan_layout.
-static __device__ void sorted_chunk_hist(const SpDev& sp, const int* __restrict__ kb_new, int* __restrict__ cnt_out)
+// slot of every key (base: base_new as scan_layout left it, in global or
+// shared memory): cnt_out[c][r] = the slots of chunk c ([c M, (c + 1) M))
+// that hold key kb_new[c] - HIST_R + r.  Called by a whole block after
+// scan_layout.
+static __device__ void sorted_chunk_hist(const SpDev& sp, const int* __restrict__ kb_new, int* __restrict__ cnt_out,
+                                         const int* base)
 {
     const int nv = sp.nvflat;
     const long long total = (long long)sp.nchunk * HIST_S;
@@ -165,8 +174,8 @@ static __device__ void sorted_chunk_hist(const SpDev& sp, const int* __restrict_
         const int k = kb_new[c] - HIST_R + r;
         int n = 0;
         if (k >= 0 && k < nv) {
-            const long long lo = max((long long)sp.base_new[k], (long long)c * sp.M);
-            const long long hi = min((long long)sp.base_new[k + 1], min((long long)(c + 1) * sp.M, sp.n));
+            const long long lo = max((long long)base[k], (long long)c * sp.M);
+            const long long hi = min((long long)base[k + 1], min((long long)(c + 1) * sp.M, sp.n));
             n = hi > lo ? (int)(hi - lo) : 0;
         }
         cnt_out[i] = n;
