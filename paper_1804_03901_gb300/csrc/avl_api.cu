@@ -682,8 +682,8 @@ avl_status avl_create(const avl_domain* dom, const avl_species* spec, int32_t ns
     fd.pow2 = (nx >= 4 && (nx & (nx - 1)) == 0) ? 1 : 0;
     fd.softening = dom->softening;
     fd.ndiag = 3 + 3 * nspecies;
-    fd.resort_drift = env_int("AVL_RESORT_DRIFT", 1) != 0 ? 1 : 0;
-    fd.resort_miss = std::max(1, env_int("AVL_RESORT_MISS", 100));
+    fd.resort_drift = env_int("AVL_RESORT_DRIFT", 0) != 0 ? 1 : 0;
+    fd.resort_miss = std::max(1, env_int("AVL_RESORT_MISS", 30));
     fd.L = dom->L;
     fd.dx = dx;
     fd.cP = dom->poisson_const;

@@ -117,9 +117,10 @@ struct SpDev {
 
 struct FieldDev {
     int nx, pow2, softening, ndiag;
-    int resort_drift;          // 1d1v: re-sort whenever the field drifts markers a row or more
+    int resort_drift;          // 1d1v: re-sort whenever the field drifts markers a row or more (default
+                               // off: the per-column shift tables already move the windows with the drift)
     int resort_miss;           // 1d1v: re-sort when more than n / resort_miss markers miss their window
-                               // (default 100: the overflow path takes up to 1 % cheaper than a re-sort)
+                               // (default 30: the overflow path takes up to ~3 % cheaper than a re-sort)
     double L, dx, cP;
     double we_scale;           // dx / (2 cP): field energy per sum of E^2 over the cells
     double* rho;               // nx
