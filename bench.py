@@ -49,6 +49,15 @@ BYTES_PER_MARKER_ALGO = {(1, "fp32"): 20.0, (1, "fp64"): 40.0,    # 1d1v: read x
 BYTES_PER_MARKER_LAYOUT = {(1, "fp32"): 28.0, (1, "fp64"): 40.0,  # read all fields, write cell, off, dv in place
                            (3, "fp32"): 36.0, (3, "fp64"): 64.0,  # read all fields, write cell, off, vx in place
                            ("3B", "fp32"): 24.0, ("3B", "fp64"): 40.0}
+# FP64 floating-point operations per marker of the 1d1v push + deposit (an FMA
+# counts 2): field gather (1 - w) E_a + w E_b 4, its CIC weight 2, kick 2,
+# drift 2, new CIC weights in x 2 and v 3, the four corner weights 6, the
+# numerator and denominator sums 12
+FP64_FLOPS_PER_MARKER = {1: 33.0}
+# FP64 FMA lanes per clock per SM on the GB300 (a warp's FP64 instruction
+# holds its SM sub-partition 64 clocks; four sub-partitions): an in-bounds
+# microbenchmark of dependent and independent FMA chains
+FP64_FMA_PER_SM_CLK = 2.0
 KERNEL_DESC = {1: "k_pd1 (gather + push + VHS deposit, written back in place)",
                3: "k_pd3 (gather + push + x-sorted VHS deposit per pencil, in place)",
                "3B": "k_pd3 mode 2 (x-sorted VHS deposit per pencil of the Boris-pushed, re-sorted markers)"}
@@ -329,31 +338,49 @@ def run_ours(args):
                 "peak_kind": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else peak_kind,
                 "kernel_ms_per_step": {k: float(v / args.steps) for k, v in zip(names, kms)},
                 "kernel_share": {k: float(v / kms.sum()) for k, v in zip(names, kms)}}
+    if prec == "fp64" and kind in FP64_FLOPS_PER_MARKER:
+        # the FP64 form: the same kernel against the FP64 pipe
+        props = torch.cuda.get_device_properties(torch.cuda.current_device())
+        mhz = clk.get("sm_max_mhz") or clk.get("sm_mhz") or 2070.0
+        fpeak = FP64_FMA_PER_SM_CLK * 2.0 * props.multi_processor_count * mhz * 1e6 / 1e12
+        fach = nmark * FP64_FLOPS_PER_MARKER[kind] / (pd_ms / 1e3) / 1e12
+        roofline["fp64_pipe"] = {"achieved": fach, "peak": fpeak, "unit": "TFLOP/s", "frac": fach / fpeak,
+                                 "flops_per_marker": FP64_FLOPS_PER_MARKER[kind],
+                                 "peak_kind": "2 FP64 FMA lanes per clock per SM (microbenchmark) x SMs x max SM clock"}
 
     # end to end through the C ABI with host buffers
     e2e = None
     if not args.no_e2e:
+        # the initial state of the same run (from t = 0, as the device-timed steps)
+        init_markers(A, sim, w, rank)
+        sim.synchronize()
         hx, hv, hf = [], [], []
         for s in range(len(w["species"])):
             x, v, f = sim.get_markers(s)
             hx.append(torch.from_numpy(x).pin_memory())
             hv.append(torch.from_numpy(np.ascontiguousarray(v[:nvd])).pin_memory())
             hf.append(torch.from_numpy(f).pin_memory())
-        diag = torch.zeros(3 + 3 * len(w["species"]), dtype=torch.float64).pin_memory()
+        nd = 3 + 3 * len(w["species"])
+        diag = torch.zeros((args.steps, nd), dtype=torch.float64).pin_memory()
         h2d = sum(t.numel() * 8 for t in hx + hv + hf)
         barrier()
         t0 = time.perf_counter()
         for s in range(len(w["species"])):
             sim.set_markers(s, hx[s], hv[s], hf[s])
-        for _ in range(args.steps):
+        for k in range(args.steps):
             sim.step(1)
-            A.check(A.avl_get_diag(sim.ctx, A.C.cast(diag.data_ptr(), A.C.POINTER(A.C.c_double))), sim.ctx)
+            sim.get_diag_async(diag[k].data_ptr())
+        sim.synchronize()
+        rows = diag.numpy()
+        if not np.all(np.isfinite(rows)):
+            raise RuntimeError("non-finite diagnostics in the end-to-end run")
         barrier()
         el = time.perf_counter() - t0
         e2e = {"value": nmark * world * args.steps / el, "unit": "marker-steps/s",
-               "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": diag.numel() * 8,
+               "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": nd * 8,
                "note": "timed: avl_set_markers of the initial state from pinned host memory, then K x "
-                       "(avl_step + avl_get_diag to pinned host)"}
+                       "(avl_step + avl_get_diag_async of that step's diagnostics row into pinned host "
+                       "memory), avl_synchronize and the host's check of every row"}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:

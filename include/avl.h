@@ -228,6 +228,15 @@ avl_status avl_get_residual(avl_ctx* ctx, double* out, int32_t on_device);
  * Returns AVL_ENUMERIC if any value is NaN or Inf. */
 avl_status avl_get_diag(avl_ctx* ctx, double* out);
 
+/* The same diagnostics row, copied to the host buffer out (3 + 3 * nspecies
+ * FP64 values; page-locked host memory keeps the copy asynchronous) in
+ * stream order behind the steps enqueued so far, without waiting: out holds
+ * the row of the current state once the context's stream has drained
+ * (avl_synchronize).  The caller keeps out valid until then and checks the
+ * values itself (avl_synchronize reports AVL_ENUMERIC for a non-finite
+ * field energy or species sum).  Errors: AVL_EINVAL (NULL out), AVL_ECUDA. */
+avl_status avl_get_diag_async(avl_ctx* ctx, double* out);
+
 /* Counters (host buffer of 4 int64 per species): [0] 1d1v: runs of markers
  * that deposited through the out-of-window path in the last step; 1d3v:
  * markers whose v_x dual row had left their segment's in the last step;

@@ -25,7 +25,7 @@ STATUS_NAMES = {0: "AVL_OK", 1: "AVL_EINVAL", 2: "AVL_ENOMEM", 3: "AVL_ECUDA",
 
 EXPORTED = ["avl_create", "avl_destroy", "avl_last_error", "avl_init_markers", "avl_set_markers",
             "avl_marker_count", "avl_get_markers", "avl_step", "avl_get_f", "avl_get_rho",
-            "avl_get_E", "avl_get_diag", "avl_get_stats", "avl_field_solve", "avl_field_solve_noalloc",
+            "avl_get_E", "avl_get_diag", "avl_get_diag_async", "avl_get_stats", "avl_field_solve", "avl_field_solve_noalloc",
             "avl_profile_steps", "avl_adjoint", "avl_create_batch", "avl_batch_run", "avl_autotune",
             "avl_get_moments", "avl_get_residual", "avl_set_bfield", "avl_record_history", "avl_refine_markers",
             "avl_synchronize"]
@@ -74,6 +74,7 @@ def _load():
         "avl_get_rho": (C.c_int, [vp, vp, C.c_int32]),
         "avl_get_E": (C.c_int, [vp, vp, C.c_int32]),
         "avl_get_diag": (C.c_int, [vp, dp]),
+        "avl_get_diag_async": (C.c_int, [vp, vp]),
         "avl_get_stats": (C.c_int, [vp, i64p]),
         "avl_field_solve": (C.c_int, [C.c_int32, C.c_double, C.c_double, C.c_int32, vp, vp, vp]),
         "avl_field_solve_noalloc": (C.c_int, [C.c_int32, C.c_double, C.c_double, C.c_int32, vp, vp, vp]),
@@ -112,6 +113,7 @@ avl_get_f = lib.avl_get_f
 avl_get_rho = lib.avl_get_rho
 avl_get_E = lib.avl_get_E
 avl_get_diag = lib.avl_get_diag
+avl_get_diag_async = lib.avl_get_diag_async
 avl_get_stats = lib.avl_get_stats
 avl_field_solve = lib.avl_field_solve
 avl_field_solve_noalloc = lib.avl_field_solve_noalloc
@@ -302,6 +304,11 @@ class Simulation:
         d = np.zeros(3 + 3 * len(self.species))
         self._chk(avl_get_diag(self.ctx, d.ctypes.data_as(C.POINTER(C.c_double))))
         return d
+
+    def get_diag_async(self, out_ptr):
+        """Enqueue the copy of the current diagnostics row to the host address
+        out_ptr (page-locked, 3 + 3 nspecies doubles); valid after synchronize()."""
+        self._chk(avl_get_diag_async(self.ctx, out_ptr))
 
     def get_stats(self):
         d = np.zeros(4 * len(self.species), dtype=np.int64)

@@ -1183,6 +1183,14 @@ avl_status avl_get_diag(avl_ctx* c, double* out)
     return AVL_OK;
 }
 
+avl_status avl_get_diag_async(avl_ctx* c, double* out)
+{
+    if (!c) return AVL_EINVAL;
+    if (!out) return fail(c, AVL_EINVAL, "out is NULL");
+    AVL_CUDA(c, cudaMemcpyAsync(out, c->h.fd.diag, c->h.fd.ndiag * 8, cudaMemcpyDeviceToHost, c->st));
+    return AVL_OK;
+}
+
 avl_status avl_get_stats(avl_ctx* c, int64_t* out)
 {
     if (!c) return AVL_EINVAL;

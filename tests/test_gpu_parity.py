@@ -260,3 +260,32 @@ def test_errors_are_reported(A):
         sim.init_markers(0, (0, 1, 1, 1), A.make_f0([(1.0, (0.0,), (1.0,))]), 1, 1.0)
     assert e.value.status == AVL_EINVAL
     sim.synchronize()
+
+
+@pytest.mark.parametrize("prec", [0, 1], ids=["fp64", "fp32"])
+def test_diag_async_rows_match_blocking_reads(A, prec):
+    """avl_get_diag_async enqueues the diagnostics row behind the steps: a
+    row per step into page-locked memory, read after avl_synchronize, equals
+    the blocking avl_get_diag of the same state and the oracle's row."""
+    import torch
+    nx, nv, L, dt = 32, 40, 6.0, 0.1
+    species = [dict(q=-1.0, m=1.0, nv=(nv,), vmin=(-5.0,), vmax=(5.0,))]
+    sim, orc = make_pair(A, nx, L, dt, species, prec)
+    sim.init_markers(0, (2, 2, 1, 1), A.make_f0([(1.0, (0.0,), (1.0,))], [(1, 0.05, 0.0)]), 5, 1.0)
+    nd = 3 + 3 * len(species)
+    rows = torch.zeros((5, nd), dtype=torch.float64).pin_memory()
+    ref = []
+    for k in range(5):
+        sim.step(1)
+        sim.get_diag_async(rows[k].data_ptr())
+        ref.append(sim.get_diag())
+    sim.step(1)
+    sim.get_diag_async(rows[4].data_ptr())   # overwritten in stream order
+    sim.synchronize()
+    got = rows.numpy()
+    assert np.array_equal(got[:4], np.array(ref[:4]))
+    last = sim.get_diag()
+    assert np.array_equal(got[4], last)
+    sync_oracle_to_gpu(sim, orc)
+    err = np.abs(last - orc.diag()) / np.maximum(np.abs(orc.diag()), 1e-300)
+    assert np.all(err < TOL[prec]), err
