@@ -78,14 +78,17 @@ __device__ void fft_pow2(double2* a, int M, const double2* tw, bool inverse)
 __device__ __forceinline__ int bitrev(int x, int bits) { return (int)(__brev((unsigned)x) >> (32 - bits)); }
 
 // Shared memory of the solve: rho / E (nx doubles), the spectrum (nx/2 + 2
-// complex) and, for power-of-two nx, the staged tables: twiddles (nx/2 + 1
-// complex) and multipliers (nx/2 + 1 doubles).
+// complex) and, for power-of-two nx up to POISSON_STAGE_MAX, the staged
+// tables: twiddles (nx/2 + 1 complex) and multipliers (nx/2 + 1 doubles);
+// larger grids read the tables from global memory.
+constexpr int POISSON_STAGE_MAX = 4096;
 __host__ __device__ inline size_t poisson_rho_bytes(int nx) { return ((size_t)nx * 8 + 15) / 16 * 16; }
 __host__ __device__ inline size_t poisson_work_bytes(int nx) { return ((size_t)nx / 2 + 2) * 16; }
 __host__ __device__ inline bool poisson_pow2(int nx) { return nx >= 4 && (nx & (nx - 1)) == 0; }
+__host__ __device__ inline bool poisson_stage(int nx) { return poisson_pow2(nx) && nx <= POISSON_STAGE_MAX; }
 __host__ __device__ inline size_t poisson_smem_bytes_dev(int nx)
 {
-    return poisson_rho_bytes(nx) + poisson_work_bytes(nx) + (poisson_pow2(nx) ? ((size_t)nx / 2 + 1) * 24 : 0);
+    return poisson_rho_bytes(nx) + poisson_work_bytes(nx) + (poisson_stage(nx) ? ((size_t)nx / 2 + 1) * 24 : 0);
 }
 
 // 1 / (4 M) for M = nx/2 = 2^bits: the halvings of the even/odd split and
@@ -118,7 +121,9 @@ __device__ void stage_tables(double2* tw_s, double* gm_s, const double2* __restr
 
 // Spectral Poisson solve (Eq. 5 / Eq. 6a-c) by the whole block: rho_s holds
 // rho in shared memory (nx doubles) and holds E on return; work is shared
-// scratch of nx/2 + 2 complex values; tw_s, gm_s the staged tables
+// scratch of nx/2 + 2 complex values; tw_s the twiddles for the power-of-two
+// path (staged in shared memory or the global table), gm_s the staged
+// multipliers (already scaled; null: gmul scaled here)
 // (power-of-two nx); tw[k] = exp(-2 pi i k / nx) and gmul[m] = cP kappa_m /
 // K2_m (zero at m = 0 and at the Nyquist mode) in global memory.
 //
@@ -155,7 +160,8 @@ __device__ void poisson_spectral(double* rho_s, double2* work, const double2* tw
             const double2 V = cmul(twm, make_double2(D.y, -D.x));
             const double2 Xm = cadd(S, V), Xp = conj2(csub(S, V));
             // E-hat = -i g X, with the scale folded into g
-            const double gm = gm_s[m], gp = gm_s[p];
+            const double c = gm_s ? 1.0 : poisson_scale(bits);
+            const double gm = gm_s ? gm_s[m] : gmul[m] * c, gp = gm_s ? gm_s[p] : gmul[p] * c;
             const double2 Em = make_double2(gm * Xm.y, -gm * Xm.x);
             const double2 Ep = make_double2(gp * Xp.y, -gp * Xp.x);
             // Y_m = F + i O with F = E_m + conj E_p, O = (E_m - conj E_p) conj(W^m);
@@ -369,7 +375,8 @@ __global__ void __cluster_dims__(FIELD_CLUSTER, 1, 1) __launch_bounds__(FIELD_TH
     __shared__ int tgt_s[MAXS];         // per species: shift table this kernel writes
 
     // CTA 0 stages the tables of the solve while the cluster sums rho
-    if (rank == 0 && fd.pow2) stage_tables(tw_s, gm_s, fd.tw, fd.gmul, nx);
+    const bool staged = poisson_stage(nx);
+    if (rank == 0 && staged) stage_tables(tw_s, gm_s, fd.tw, fd.gmul, nx);
 
     // --- rho slice: sum over species and row blocks (fixed order) --------
     // tpx threads per column (a power of two up to 32) take every tpx-th
@@ -419,7 +426,7 @@ __global__ void __cluster_dims__(FIELD_CLUSTER, 1, 1) __launch_bounds__(FIELD_TH
         inv_dv = sp.inv_dv[0];
         shsel = A->ctl->shsel[threadIdx.x];
     }
-    poisson_spectral(rho_s, work, tw_s, gm_s, nx, fd.pow2, fd.tw, fd.gmul);
+    poisson_spectral(rho_s, work, staged ? tw_s : fd.tw, staged ? gm_s : nullptr, nx, fd.pow2, fd.tw, fd.gmul);
     if (threadIdx.x < A->ns) {
         shf_s[threadIdx.x] = mobile ? (float)(qm_dt * inv_dv) : 0.f;
         tgt_s[threadIdx.x] = count_step ? 1 - shsel : shsel;
@@ -595,10 +602,11 @@ __global__ void __launch_bounds__(FIELD_THREADS)
     double2* work = reinterpret_cast<double2*>(smem + poisson_rho_bytes(nx));
     double2* tw_s = reinterpret_cast<double2*>(smem + poisson_rho_bytes(nx) + poisson_work_bytes(nx));
     double* gm_s = reinterpret_cast<double*>(tw_s + nx / 2 + 1);
-    if (pow2) stage_tables(tw_s, gm_s, tw, gmul, nx);
+    const bool staged = poisson_stage(nx);
+    if (staged) stage_tables(tw_s, gm_s, tw, gmul, nx);
     for (int x = threadIdx.x; x < nx; x += FIELD_THREADS) rho_s[x] = rho[x];
     __syncthreads();
-    poisson_spectral(rho_s, work, tw_s, gm_s, nx, pow2, tw, gmul);
+    poisson_spectral(rho_s, work, staged ? tw_s : tw, staged ? gm_s : nullptr, nx, pow2, tw, gmul);
     for (int x = threadIdx.x; x < nx; x += FIELD_THREADS) E[x] = rho_s[x];
 }
 

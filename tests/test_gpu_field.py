@@ -20,7 +20,7 @@ def A():
     return avl
 
 
-@pytest.mark.parametrize("nx", [4, 15, 64, 512, 4096, 6000])
+@pytest.mark.parametrize("nx", [4, 15, 64, 512, 4096, 6000, 8192])
 @pytest.mark.parametrize("soft,cP", [(1, 1.0), (0, 4 * np.pi)])
 def test_field_solve_matches_oracle(A, nx, soft, cP):
     import torch
