@@ -7,7 +7,9 @@
 // CTA 0 then runs an FP64 real FFT of length nx (a complex radix-2 FFT of
 // length nx/2 with the even/odd split), multiplies by -i cP kappa / K^2,
 // transforms back, and writes E in FP64 and FP32.  A direct DFT serves grid
-// sizes that are not a power of two.
+// sizes that are not a power of two.  Beside the solve, CTAs 1 .. decide the
+// next step's 1d1v re-sorts and prepare their slots, and the last CTA sums
+// the diagnostics.
 #include <cooperative_groups.h>
 #include <math.h>
 
@@ -32,8 +34,9 @@ __device__ __forceinline__ double2 conj2(double2 a) { return make_double2(a.x, -
 
 // in-place radix-2 decimation-in-time FFT of length M (a power of two) on
 // shared memory, input already in bit-reversed order; tw[k] = exp(-2 pi i
-// k / N) for k = 0 .. M with N = 2 M, staged in shared memory; the inverse
-// uses the conjugate twiddles (no scaling).  One butterfly per thread and
+// k / N) for k = 0 .. M with N = 2 M (the copy staged in shared memory, or
+// the global table for large grids); the inverse uses the conjugate
+// twiddles (no scaling).  One butterfly per thread and
 // stage: an FP64 warp instruction occupies its SM sub-partition for the same
 // time whatever the number of active lanes, so the butterflies are packed
 // into full warps.  The first two stages, whose twiddles are 1 and -i (+i
