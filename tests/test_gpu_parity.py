@@ -289,3 +289,25 @@ def test_diag_async_rows_match_blocking_reads(A, prec):
     sync_oracle_to_gpu(sim, orc)
     err = np.abs(last - orc.diag()) / np.maximum(np.abs(orc.diag()), 1e-300)
     assert np.all(err < TOL[prec]), err
+
+
+def test_conservation_drift_fp32_within_oracle_drift(A):
+    """The Landau workload (32768 markers, 200 steps) in the FP32 path,
+    free running beside the FP64 oracle: the drifts of N (integral of f)
+    and of the total energy over the run stay within 1.5 times the oracle's
+    own drift (the ratio reconstruction does not conserve N exactly, Sec.
+    3.4.1), with an FP32 rounding floor of 1e-6."""
+    w = inputs.landau()
+    sim, orc = make_pair(A, w["nx"], w["L"], w["dt"], w["species"], 1)
+    f0 = w["f0"][0]
+    sim.init_markers(0, w["lattice"][0], A.make_f0(f0["beams"], f0["modes"]), w["seed"], w["jitter"])
+    orc.init_markers(0, w["lattice"][0], O.F0(f0["beams"], f0["modes"]), w["seed"], w["jitter"])
+    orc.refresh()
+    g0, o0 = sim.get_diag(), orc.diag()
+    sim.step(w["steps"])
+    orc.step(w["steps"])
+    g1, o1 = sim.get_diag(), orc.diag()
+    for q, what in ((4, "N"), (2, "W_total")):
+        dg = abs(g1[q] - g0[q]) / abs(g0[q])
+        do = abs(o1[q] - o0[q]) / abs(o0[q])
+        assert dg <= 1.5 * do + 1e-6, (what, dg, do)
