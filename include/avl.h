@@ -225,7 +225,8 @@ avl_status avl_get_residual(avl_ctx* ctx, double* out, int32_t on_device);
  * 3 + 3 * nspecies values): W_E, W_kin, W_total, then W_kin of each species,
  * N (integral of f) of each species, entropy S of each species.
  * W_E = 1/(2 poisson_const) sum E^2 dx (Eq. 12); W_kin = m/2 sum v^2 f dx dv.
- * Returns AVL_ENUMERIC if any value is NaN or Inf. */
+ * Returns AVL_ENUMERIC if any value is NaN or Inf, AVL_EINVAL for a NULL out
+ * or a batch (its runs hold the rows). */
 avl_status avl_get_diag(avl_ctx* ctx, double* out);
 
 /* The same diagnostics row, copied to the host buffer out (3 + 3 * nspecies
@@ -234,7 +235,8 @@ avl_status avl_get_diag(avl_ctx* ctx, double* out);
  * the row of the current state once the context's stream has drained
  * (avl_synchronize).  The caller keeps out valid until then and checks the
  * values itself (avl_synchronize reports AVL_ENUMERIC for a non-finite
- * field energy or species sum).  Errors: AVL_EINVAL (NULL out), AVL_ECUDA. */
+ * field energy or species sum).  Errors: AVL_EINVAL (NULL out, a batch),
+ * AVL_ECUDA. */
 avl_status avl_get_diag_async(avl_ctx* ctx, double* out);
 
 /* Counters (host buffer of 4 int64 per species): [0] 1d1v: runs of markers

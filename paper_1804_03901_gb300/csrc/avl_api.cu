@@ -1174,6 +1174,7 @@ avl_status avl_get_residual(avl_ctx* c, double* out, int32_t on_device)
 avl_status avl_get_diag(avl_ctx* c, double* out)
 {
     if (!c) return AVL_EINVAL;
+    if (!c->runs.empty()) return fail(c, AVL_EINVAL, "a batch has no diagnostics row; use a run");
     if (!out) return fail(c, AVL_EINVAL, "out is NULL");
     const int nd = c->h.fd.ndiag;
     AVL_CUDA(c, cudaMemcpyAsync(out, c->h.fd.diag, nd * 8, cudaMemcpyDeviceToHost, c->st));
@@ -1186,6 +1187,7 @@ avl_status avl_get_diag(avl_ctx* c, double* out)
 avl_status avl_get_diag_async(avl_ctx* c, double* out)
 {
     if (!c) return AVL_EINVAL;
+    if (!c->runs.empty()) return fail(c, AVL_EINVAL, "a batch has no diagnostics row; use a run");
     if (!out) return fail(c, AVL_EINVAL, "out is NULL");
     AVL_CUDA(c, cudaMemcpyAsync(out, c->h.fd.diag, c->h.fd.ndiag * 8, cudaMemcpyDeviceToHost, c->st));
     return AVL_OK;

@@ -132,4 +132,10 @@ def test_batch_errors(A):
     with pytest.raises(A.AvlError):   # run 1 has no markers
         b.runs[0].init_markers(0, (2, 2, 1, 1), A.make_f0([(1.0, (0.0,), (1.0,))]), 1)
         b.step(1)
+    # the diagnostics rows belong to the runs, not to the batch
+    import numpy as np
+    row = np.zeros(6)
+    ptr = row.ctypes.data_as(A.C.POINTER(A.C.c_double))
+    assert A.avl_get_diag(b.ctx, ptr) == A.AVL_EINVAL
+    assert A.avl_get_diag_async(b.ctx, row.ctypes.data) == A.AVL_EINVAL
     b.close()
