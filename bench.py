@@ -119,6 +119,24 @@ def dist_env():
     return rank, world, local
 
 
+def max_over_ranks(x, world, device="cuda"):
+    """The job's time from each rank's: the largest (all-reduce MAX over the
+    process group; the value itself for one rank)."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(markers_per_rank, world, steps, seconds):
+    """Whole-job marker-steps/s of `world` independent replicas, each moving
+    markers_per_rank markers for `steps` steps, in the job's time."""
+    return markers_per_rank * world * steps / seconds
+
+
 def peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -310,11 +328,8 @@ def run_ours(args):
     ms = e0.elapsed_time(e1)
     sim.synchronize()
     stats = sim.get_stats()
-    if world > 1:
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
-    value = nmark * world * args.steps / (ms / 1e3)
+    ms = max_over_ranks(ms, world)
+    value = job_rate(nmark, world, args.steps, ms / 1e3)
 
     # per-kernel CUDA-event timing over the same K steps from t = 0
     init_markers(A, sim, w, rank)
@@ -375,8 +390,8 @@ def run_ours(args):
         if not np.all(np.isfinite(rows)):
             raise RuntimeError("non-finite diagnostics in the end-to-end run")
         barrier()
-        el = time.perf_counter() - t0
-        e2e = {"value": nmark * world * args.steps / el, "unit": "marker-steps/s",
+        el = max_over_ranks(time.perf_counter() - t0, world)
+        e2e = {"value": job_rate(nmark, world, args.steps, el), "unit": "marker-steps/s",
                "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": nd * 8,
                "note": "timed: avl_set_markers of the initial state from pinned host memory, then K x "
                        "(avl_step + avl_get_diag_async of that step's diagnostics row into pinned host "
