@@ -110,7 +110,8 @@ typedef struct {
 avl_status avl_create(const avl_domain* dom, const avl_species* sp, int32_t nspecies,
                       void* cuda_stream, avl_ctx** out);
 
-/* Release all device memory of the context (after draining its stream). */
+/* Release all device memory of the context (after draining its stream).
+ * NULL is ignored; a run of a batch is released with its batch. */
 void avl_destroy(avl_ctx* ctx);
 
 /* Message for the last failing call on ctx ("" if none).  ctx may be NULL,
@@ -136,10 +137,12 @@ avl_status avl_init_markers(avl_ctx* ctx, int32_t s, const int32_t lattice[4],
 avl_status avl_set_markers(avl_ctx* ctx, int32_t s, int64_t n, const double* x,
                            const double* v, const double* f, int32_t on_device);
 
-/* Number of markers of species s. */
+/* Number of markers of species s.  Errors: AVL_EINVAL (species index out of
+ * range, NULL n). */
 avl_status avl_marker_count(avl_ctx* ctx, int32_t s, int64_t* n);
 
-/* Copy the markers of species s out as FP64 (layout above, library order). */
+/* Copy the markers of species s out as FP64 (layout above, library order).
+ * Errors: AVL_EINVAL (species index out of range), AVL_ESTATE (no markers). */
 avl_status avl_get_markers(avl_ctx* ctx, int32_t s, double* x, double* v, double* f,
                            int32_t on_device);
 
@@ -197,13 +200,16 @@ avl_status avl_set_bfield(avl_ctx* ctx, const double* B);
 
 /* Reconstructed f of species s and, if n_opt is not NULL, the denominator of
  * Eq. 4 (sum of weights, the paper's "n" output, Sec. 3.4.3); FP64,
- * [x][v...] row-major. */
+ * [x][v...] row-major.  Errors: AVL_EINVAL (species index out of range,
+ * NULL f), AVL_ENOMEM (host reads stage through a scratch buffer). */
 avl_status avl_get_f(avl_ctx* ctx, int32_t s, double* f, double* n_opt, int32_t on_device);
 
-/* Net charge density rho (nx, FP64) of the current state (Eq. 14). */
+/* Net charge density rho (nx, FP64) of the current state (Eq. 14).
+ * Errors: AVL_EINVAL (NULL rho, a batch: its runs hold the fields). */
 avl_status avl_get_rho(avl_ctx* ctx, double* rho, int32_t on_device);
 
-/* Electric field E (nx, FP64) of the current state (Eq. 6). */
+/* Electric field E (nx, FP64) of the current state (Eq. 6).
+ * Errors: AVL_EINVAL (NULL E, a batch). */
 avl_status avl_get_E(avl_ctx* ctx, double* E, int32_t on_device);
 
 /* Velocity moments of species s of the current state (Sec. 3.4.2 outputs,
@@ -244,7 +250,7 @@ avl_status avl_get_diag_async(avl_ctx* ctx, double* out);
  * markers whose v_x dual row had left their segment's in the last step;
  * [1] steps that re-sorted this species so far; [2] 1d1v: markers outside
  * their chunk's best window at the last decision, 1d3v: 0; [3] steps so
- * far. */
+ * far.  Errors: AVL_EINVAL (NULL out). */
 avl_status avl_get_stats(avl_ctx* ctx, int64_t* out);
 
 /* Stand-alone spectral Poisson solve (Sec. 3.1, Eq. 5 / Eq. 6a-c): E from
@@ -311,7 +317,8 @@ avl_status avl_adjoint(avl_ctx* ctx, int32_t s, const avl_f0* theta, int32_t nst
 avl_status avl_create_batch(int32_t nrun, const avl_domain* doms, const avl_species* sps, const int32_t* nspecies,
                             void* cuda_stream, avl_ctx** out);
 
-/* Run r of a batch (a context for every per-run call). */
+/* Run r of a batch (a context for every per-run call).  Errors: AVL_EINVAL
+ * (NULL batch or run, r out of range). */
 avl_status avl_batch_run(avl_ctx* batch, int32_t r, avl_ctx** run);
 
 /* Chunk-size autotuner of the 1d1v path (a single context or a batch):

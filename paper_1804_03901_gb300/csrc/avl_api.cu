@@ -1118,6 +1118,7 @@ avl_status avl_get_f(avl_ctx* c, int32_t s, double* f, double* n_opt, int32_t on
 static avl_status get_field(avl_ctx* c, const double* src, double* dst, int on_device)
 {
     if (!c) return AVL_EINVAL;
+    if (!c->runs.empty()) return fail(c, AVL_EINVAL, "a batch has no field; use a run");
     if (!dst) return fail(c, AVL_EINVAL, "output is NULL");
     const size_t bytes = (size_t)c->h.fd.nx * 8;
     AVL_CUDA(c, cudaMemcpyAsync(dst, src, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
