@@ -58,9 +58,10 @@ typedef struct avl_ctx avl_ctx;
 /* Simulation domain (Sec. 3.1, Sec. 3.3 numerical parameters).
  * precision AVL_FP64: markers, deposit and grid in FP64.
  * precision AVL_FP32: marker position = int32 cell + FP32 offset, velocity
- *   and value in FP32, deposit sums in FP32 (1d1v: plain within a chunk,
- *   compensated over chunks; 1d3v: plain); the Poisson solve, the
- *   charge-neutral k = 0 handling and the diagnostics stay FP64.
+ *   and value in FP32, deposit sums in FP32 (1d1v: the numerator as
+ *   deviations from the previous reconstruction within a chunk, float-float
+ *   over chunks, f = num / den in float-float; 1d3v: plain); the Poisson
+ *   solve, the charge-neutral k = 0 handling and the diagnostics stay FP64.
  * nvdim = 3 (Sec. 2 with three velocity dimensions: the field accelerates
  *   v_x, an optional static background magnetic field, avl_set_bfield, turns
  *   v) needs nx <= 1024 (FP32) or nx <= 512 (FP64), nv[0] in [2, 1024],
@@ -270,18 +271,24 @@ avl_status avl_field_solve(int32_t nx, double L, double poisson_const, int32_t s
  * solve: their GPU memory is fully reserved by another allocator (a caching
  * allocator, a fixed budget), or they run a time-critical loop that must not
  * pay for cudaMalloc/cudaFree, which synchronise the device.  The transform
- * tables live in one file-scope device array of 328 KiB, sized for
- * nx <= 16384, that every GPU loading the library holds until the process
- * exits; the call allocates nothing (no cudaMalloc, cudaFree or allocating
- * library routine).  Same arguments and result as avl_field_solve, but the
- * work is only enqueued on cuda_stream (the call does not wait for it).
- * The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress, with that device current); make that first call
- * before any stream capture.  Every call on a device shares the array and
- * rewrites all of it before reading it, so no state carries over between
- * calls; calls that overlap on the GPU (other streams, other host threads)
- * race on it.  Errors (message via avl_last_error(NULL)): AVL_EINVAL for nx
- * outside [4, 16384] and the argument errors of avl_field_solve; AVL_ECUDA. */
+ * tables live in one file-scope device array of 250 KiB, sized for the
+ * largest grid one block's shared memory can solve (nx <= 12798; power-of-two
+ * grids up to 8192).  The call itself allocates nothing (no cudaMalloc,
+ * cudaFree or allocating library routine).  The CUDA runtime loads the
+ * library's device code lazily: the array (and the solve's kernels) are
+ * placed on a device by the first call there, which looks up the array's
+ * device address (cudaGetSymbolAddress, with that device current).  Make
+ * that first call on each device before reserving the rest of its memory
+ * and before any stream capture; every later call finds them in place (the
+ * address is looked up again on every call, which allocates nothing once
+ * the code is loaded), and they stay until the process exits.  Same
+ * arguments and result as avl_field_solve, but the work is only enqueued on
+ * cuda_stream (the call does not wait for it).  Every call on a device
+ * shares the array and rewrites the part it uses before reading it, so no
+ * state carries over between calls; calls that overlap on the GPU (other
+ * streams, other host threads) race on it.  Errors (message via
+ * avl_last_error(NULL)): AVL_EINVAL for nx outside [4, 12798] and the
+ * argument errors of avl_field_solve; AVL_ECUDA. */
 avl_status avl_field_solve_noalloc(int32_t nx, double L, double poisson_const, int32_t softening,
                                    const double* rho, double* E, void* cuda_stream);
 
@@ -342,8 +349,22 @@ avl_status avl_autotune(avl_ctx* ctx, int32_t trial_steps, int32_t* chunk_out);
 avl_status avl_profile_steps(avl_ctx* ctx, int32_t nsteps, double* ms, int32_t nkernels);
 
 /* Block the host until the context's stream has drained; reports device-side
- * error flags (AVL_ETIMEOUT, AVL_ENUMERIC). */
+ * error flags (AVL_ETIMEOUT, AVL_ENUMERIC) raised by the work enqueued so far
+ * and clears them, so that each flag is reported once.  On a batch: the
+ * first run's error. */
 avl_status avl_synchronize(avl_ctx* ctx);
+
+/* Failure detection (spec extension; the paper has no counterpart):
+ * the deposit kernels stage marker fields and E with bulk copies (TMA) and
+ * wait for them on an mbarrier at most `polls` polls (default 2^22, about a
+ * second); a wait that gives up sets the AVL_ETIMEOUT flag, drains the copy
+ * with the default limit (so no copy is left in flight) and the step goes
+ * on.  polls = 0 makes every such wait give up at once, which forces the
+ * failure path without any fault (a test of the host's error handling: the
+ * step's results stay valid, the next avl_synchronize returns AVL_ETIMEOUT);
+ * polls < 0 restores the default.  On a batch: every run.  Errors:
+ * AVL_EINVAL (NULL ctx), AVL_ECUDA. */
+avl_status avl_set_wait_limit(avl_ctx* ctx, int64_t polls);
 
 #ifdef __cplusplus
 }

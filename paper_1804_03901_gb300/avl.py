@@ -28,7 +28,7 @@ EXPORTED = ["avl_create", "avl_destroy", "avl_last_error", "avl_init_markers", "
             "avl_get_E", "avl_get_diag", "avl_get_diag_async", "avl_get_stats", "avl_field_solve", "avl_field_solve_noalloc",
             "avl_profile_steps", "avl_adjoint", "avl_create_batch", "avl_batch_run", "avl_autotune",
             "avl_get_moments", "avl_get_residual", "avl_set_bfield", "avl_record_history", "avl_refine_markers",
-            "avl_synchronize"]
+            "avl_synchronize", "avl_set_wait_limit"]
 
 
 class avl_domain(C.Structure):
@@ -90,6 +90,7 @@ def _load():
         "avl_record_history": (C.c_int, [vp, C.c_int32]),
         "avl_refine_markers": (C.c_int, [vp, C.c_int32, vp, vp, C.c_uint64, C.c_double, vp]),
         "avl_synchronize": (C.c_int, [vp]),
+        "avl_set_wait_limit": (C.c_int, [vp, C.c_int64]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -128,6 +129,7 @@ avl_set_bfield = lib.avl_set_bfield
 avl_record_history = lib.avl_record_history
 avl_refine_markers = lib.avl_refine_markers
 avl_synchronize = lib.avl_synchronize
+avl_set_wait_limit = lib.avl_set_wait_limit
 
 
 def check(status, ctx=None):
@@ -250,6 +252,11 @@ class Simulation:
 
     def synchronize(self):
         self._chk(avl_synchronize(self.ctx))
+
+    def set_wait_limit(self, polls):
+        """Polls of the first bounded wait of the deposit kernels (0: give up
+        at once and flag AVL_ETIMEOUT; negative: the default)."""
+        self._chk(avl_set_wait_limit(self.ctx, int(polls)))
 
     def get_f(self, s, with_n=False):
         sp = self.species[s]

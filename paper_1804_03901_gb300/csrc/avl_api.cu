@@ -357,8 +357,14 @@ avl_status refresh(avl_ctx* c)
     avl_status st = clear_far_counts(c);
     if (st) return st;
     AVL_CUDA(c, launch_count1(c->h, c->d_args, c->st));
-    AVL_CUDA(c, launch_pd1(c->h, c->d_args, 0, c->st));
-    AVL_CUDA(c, launch_fin1(c->h, c->d_args, 1, c->st));
+    // FP32 deposits sum deviations from the stored f (exact for any stored
+    // values); a second pass takes the first pass's f as that reference, so
+    // that a fresh marker set is reconstructed as precisely as a step
+    const int passes = c->h.prec == AVL_FP32 ? 2 : 1;
+    for (int p = 0; p < passes; ++p) {
+        AVL_CUDA(c, launch_pd1(c->h, c->d_args, 0, c->st));
+        AVL_CUDA(c, launch_fin1(c->h, c->d_args, 1, c->st));
+    }
     AVL_CUDA(c, launch_field(c->h, c->d_args, 0, c->st));
     return AVL_OK;
 }
@@ -433,11 +439,17 @@ avl_status check_species(avl_ctx* c, int s)
     return AVL_OK;
 }
 
+// the device-side error flags of the work enqueued so far; flags are cleared
+// once they are reported
 avl_status read_errors(avl_ctx* c)
 {
     int err = 0;
     AVL_CUDA(c, cudaMemcpyAsync(&err, &c->d_ctl->err, sizeof(int), cudaMemcpyDeviceToHost, c->st));
     AVL_CUDA(c, cudaStreamSynchronize(c->st));
+    if (err) {
+        AVL_CUDA(c, cudaMemsetAsync(&c->d_ctl->err, 0, sizeof(int), c->st));
+        AVL_CUDA(c, cudaStreamSynchronize(c->st));
+    }
     if (err & ERR_TIMEOUT) return fail(c, AVL_ETIMEOUT, "a bounded device-side wait gave up");
     if (err & ERR_NUMERIC) return fail(c, AVL_ENUMERIC, "NaN or Inf in the field or diagnostics");
     if (err & ERR_CAPACITY) return fail(c, AVL_ECUDA, "internal check of the marker layout failed");
@@ -806,6 +818,14 @@ avl_status avl_create(const avl_domain* dom, const avl_species* spec, int32_t ns
     c->d_f0 = (avl_f0*)pf0;
     c->d_bad = (unsigned long long*)pbad;
     h.ctl = c->d_ctl;
+    {
+        const long long wl = WAIT_LIMIT;
+        if ((e = cudaMemcpyAsync(&c->d_ctl->wait_limit, &wl, sizeof(wl), cudaMemcpyHostToDevice, c->st)) ||
+            (e = cudaStreamSynchronize(c->st))) {
+            cuda_fail(c, e, "avl_create (control block)");
+            return bail(AVL_ECUDA);
+        }
+    }
     if ((e = configure_vhs1(h)) || (e = configure_vhs3(h)) || (e = configure_field(h))) {
         cuda_fail(c, e, "cudaFuncSetAttribute (shared memory)");
         return bail(AVL_ECUDA);
@@ -1401,6 +1421,18 @@ avl_status avl_create_batch(int32_t nrun, const avl_domain* doms, const avl_spec
         }
     }
     *out = b;
+    return AVL_OK;
+}
+
+avl_status avl_set_wait_limit(avl_ctx* c, int64_t polls)
+{
+    if (!c) return AVL_EINVAL;
+    const long long wl = polls < 0 ? WAIT_LIMIT : (long long)polls;
+    std::vector<avl_ctx*> targets = c->runs.empty() ? std::vector<avl_ctx*>{c} : c->runs;
+    for (avl_ctx* t : targets) {
+        AVL_CUDA(c, cudaMemcpyAsync(&t->d_ctl->wait_limit, &wl, sizeof(wl), cudaMemcpyHostToDevice, c->st));
+        AVL_CUDA(c, cudaStreamSynchronize(c->st));
+    }
     return AVL_OK;
 }
 

@@ -49,12 +49,20 @@ constexpr int FIN_THREADS = 256;    // finalize block
 constexpr int FIN_XB = 16;          // x columns per finalize block
 constexpr int FIELD_THREADS = 512;  // Poisson cluster block
 constexpr int FIELD_CLUSTER = 8;    // CTAs in the Poisson cluster
-constexpr long long WAIT_LIMIT = 1ll << 22;   // bounded mbarrier polls
+constexpr long long WAIT_LIMIT = 1ll << 22;   // bounded mbarrier polls: the default limit of a first wait
+                                              // (Ctl::wait_limit) and the limit of the drain that follows
+                                              // a first wait that gave up
 constexpr int P3_THREADS = 256;     // 1d3v pencil block (one thread per x column and CPT3 columns)
 constexpr int FIN3_X = 32;          // 1d3v finalize: x columns per block
 constexpr int FIN3_R = 8;           //                row lanes per block
 constexpr int NV3_MAX = 1024;       // 1d3v: largest nv[0] (key histogram of a pencil in shared memory)
 constexpr int GREEN_MAX = 1024;     // largest nx solved by the circulant product (adjoint engine)
+
+// elements of one deposit-window plane (numerator, denominator or reference)
+// of a 1d1v chunk: Wmax rows x nx columns, padded to a multiple of 4 so that
+// every plane (FP32 or FP64) starts and ends on a 16-byte boundary, as the
+// bulk copies of the window need
+__host__ __device__ inline int win_plane(int W, int nx) { return (W * nx + 3) & ~3; }
 
 // device-side error bits (Ctl::err)
 enum : int { ERR_TIMEOUT = 1, ERR_NUMERIC = 2, ERR_CAPACITY = 4 };
@@ -151,6 +159,7 @@ struct Ctl {
     int shsel[MAXS];           // which shift table belongs to this step's field
     long long step;
     int err;
+    long long wait_limit;      // polls of the first bounded wait on a bulk copy (avl_set_wait_limit)
     // 1d3v
     int asel[MAXS];                        // accumulator the next deposit writes into
     unsigned long long movers[MAXS];       // markers whose key left their segment (this pass)

@@ -6,19 +6,22 @@
 // another allocator (a framework's caching allocator, a fixed memory budget),
 // or a time-critical loop that must not pay for cudaMalloc / cudaFree, which
 // synchronise the device.  For them the transform tables (the only scratch
-// the solve needs) live in one file-scope device array that every GPU
-// loading this library keeps until the process exits.
+// the solve needs) live in one file-scope device array.  The CUDA runtime
+// places it on a GPU together with this file's kernels when the first call
+// there loads the module (lazy loading), and it stays until the process
+// exits; callers make that first call before they reserve the rest of the
+// GPU's memory and before any stream capture.
 #include <cuda_runtime.h>
 #include <math.h>
-
-#include <mutex>
 
 #include "avl_internal.cuh"
 
 namespace avl {
 
-// largest grid the fixed scratch serves
-constexpr int NOALLOC_MAX_NX = 16384;
+// largest grid the fixed scratch serves: the largest nx whose solve fits one
+// block's 200 KiB of shared memory (16 nx + 32 bytes without staged tables);
+// power-of-two grids stop at 8192 below it
+constexpr int NOALLOC_MAX_NX = 12798;
 // twiddles exp(-2 pi i k / nx) (nx complex) followed by cP kappa / K^2 (nx/2 + 1)
 constexpr size_t NOALLOC_TW_BYTES = (size_t)NOALLOC_MAX_NX * sizeof(double2);
 constexpr size_t NOALLOC_BYTES = NOALLOC_TW_BYTES + ((size_t)NOALLOC_MAX_NX / 2 + 1) * sizeof(double);
@@ -55,26 +58,17 @@ __global__ void k_noalloc_tables(int nx, double L, double cP, int softening)
 }
 
 namespace {
-constexpr int MAX_DEVICES = 64;
-std::mutex g_setup_mutex;
-void* g_scratch_addr[MAX_DEVICES] = {};
-
-// once per device, with that device current: the device address of the
-// array (its name in host code is only a host-side stand-in)
+// the device address of the array on the current device (its name in host
+// code is only a host-side stand-in).  Looked up on every call: after the
+// first call has loaded the module on a device the lookup allocates nothing,
+// and a context reset that reloads the module at another address is
+// followed.
 cudaError_t scratch_address(void** out)
 {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_field_scratch);
     if (e) return e;
-    if (dev < 0 || dev >= MAX_DEVICES) return cudaErrorInvalidDevice;
-    std::lock_guard<std::mutex> lock(g_setup_mutex);
-    if (!g_scratch_addr[dev]) {
-        void* p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_field_scratch);
-        if (e) return e;
-        g_scratch_addr[dev] = p;
-    }
-    *out = g_scratch_addr[dev];
+    *out = p;
     return cudaSuccess;
 }
 }  // namespace
@@ -88,7 +82,9 @@ extern "C" avl_status avl_field_solve_noalloc(int32_t nx, double L, double poiss
 {
     using namespace avl;
     if (nx < 4 || nx > NOALLOC_MAX_NX)
-        return avl_noalloc_fail(AVL_EINVAL, "nx must be in [4, 16384] for the allocation-free field solve");
+        return avl_noalloc_fail(AVL_EINVAL,
+                                "nx must be in [4, 12798] for the allocation-free field solve (the largest grid "
+                                "one block's shared memory solves)");
     if (!(L > 0) || !(poisson_const > 0) || !isfinite(L) || !isfinite(poisson_const))
         return avl_noalloc_fail(AVL_EINVAL, "L and poisson_const must be positive and finite");
     if (softening != 0 && softening != 1) return avl_noalloc_fail(AVL_EINVAL, "softening must be 0 or 1");

@@ -147,40 +147,55 @@ __device__ __forceinline__ void wrap_pair_in(int i0, int nx, int& ia, int& ib)
 template <typename T>
 struct Run;
 
-// FP32: a run holds at most MPT markers, summed plainly in registers; the run
-// sums are added into the window with plain FP32 shared-memory reductions.
-// A window cell receives the runs of one chunk only (about 16 markers per
-// phase cell times 4 corners), so its rounding error stays near 1e-7 of the
-// cell value; the sum over chunks in the finalize is compensated.
+// FP32: a run holds at most MPT markers, summed in registers; the run sums
+// are added into the window with plain FP32 shared-memory reductions.  The
+// window's numerator plane holds deviations from a reference value per
+// cell, sum alpha (f_l - f_ref), with f_ref the cell's f of the previous
+// reconstruction (staged in shared memory beside the window); the finalize
+// forms f = f_ref + sum alpha (f_l - f_ref) / sum alpha, which is Eq. 4 for
+// any f_ref.  A run sums alpha (f_l - r) about the value r of its first
+// marker and shifts the sum to each cell's reference when it is flushed,
+// fma(r - f_ref, sum alpha, sum alpha (f_l - r)), so that every rounding of
+// the numerator (products, register sums, window sums) scales with the
+// spread of the marker values in the cell and the change of f since the
+// previous reconstruction (a few per cent of f for a smooth f) instead of
+// with f itself; the rounding of the denominator enters f only through
+// (f - f_ref) as well.  Runs outside the window carry absolute values into
+// the FP64 overflow grids.
 template <>
 struct Run<float> {
     int i0, j0;
+    float r;
     float nh[4], dh[4];
     __device__ __forceinline__ void reset(int i, int j)
     {
         i0 = i;
         j0 = j;
+        r = 0.f;
 #pragma unroll
         for (int k = 0; k < 4; ++k) nh[k] = dh[k] = 0.f;
     }
-    __device__ __forceinline__ void add(const float (&a)[4], float f)
+    __device__ __forceinline__ void add(const float (&a)[4], float f, bool first)
     {
+        if (first) r = f;
+        const float d = __fsub_rn(f, r);
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-            nh[k] = __fadd_rn(nh[k], __fmul_rn(a[k], f));
+            nh[k] = __fmaf_rn(a[k], d, nh[k]);
             dh[k] = __fadd_rn(dh[k], a[k]);
         }
     }
-    // window planes: num, den
-    __device__ __forceinline__ void to_window(float* win, int plane, const int (&cell)[4]) const
+    // window planes: num (deviations from fref), den
+    __device__ __forceinline__ void to_window(float* win, int plane, const int (&cell)[4], const float* fref) const
     {
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-            atomicAdd(win + cell[k], nh[k]);
+            atomicAdd(win + cell[k], __fmaf_rn(__fsub_rn(r, fref[cell[k]]), dh[k], nh[k]));
             atomicAdd(win + plane + cell[k], dh[k]);
         }
     }
-    __device__ __forceinline__ double num(int k) const { return (double)nh[k]; }
+    // absolute sums (overflow path, FP64)
+    __device__ __forceinline__ double num(int k) const { return (double)nh[k] + (double)r * (double)dh[k]; }
     __device__ __forceinline__ double den(int k) const { return (double)dh[k]; }
 };
 
@@ -195,7 +210,7 @@ struct Run<double> {
 #pragma unroll
         for (int k = 0; k < 4; ++k) nh[k] = dh[k] = 0.0;
     }
-    __device__ __forceinline__ void add(const double (&a)[4], double f)
+    __device__ __forceinline__ void add(const double (&a)[4], double f, bool)
     {
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
@@ -204,7 +219,7 @@ struct Run<double> {
         }
     }
     // window planes: num, den
-    __device__ __forceinline__ void to_window(double* win, int plane, const int (&cell)[4]) const
+    __device__ __forceinline__ void to_window(double* win, int plane, const int (&cell)[4], const double*) const
     {
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
@@ -246,7 +261,8 @@ __device__ __forceinline__ void flush_overflow(int ia, int ib, int j0, int nx, i
 // Returns true for the overflow path.
 template <typename T>
 __device__ __forceinline__ bool flush_run(const Run<T>& r, T* win, int plane, int row0, int W, int nx, int nv,
-                                          const int* sh, double* ovf_num, double* ovf_den, int* ovf_tag, int tag)
+                                          const int* sh, const T* fref, double* ovf_num, double* ovf_den,
+                                          int* ovf_tag, int tag)
 {
     if (r.j0 + 1 < 0 || r.j0 >= nv) return false;   // footprint entirely off the velocity grid
     int ia, ib;
@@ -254,7 +270,7 @@ __device__ __forceinline__ bool flush_run(const Run<T>& r, T* win, int plane, in
     const int wa = r.j0 - sh[ia] - row0, wb = r.j0 - sh[ib] - row0;
     if (wa >= 0 && wa + 1 < W && wb >= 0 && wb + 1 < W) {
         const int cell[4] = {wa * nx + ia, wb * nx + ib, (wa + 1) * nx + ia, (wb + 1) * nx + ib};
-        r.to_window(win, plane, cell);
+        r.to_window(win, plane, cell, fref);
         return false;
     }
     flush_overflow(ia, ib, r.j0, nx, nv, r.num(0), r.num(1), r.num(2), r.num(3), r.den(0), r.den(1), r.den(2),
@@ -265,14 +281,21 @@ __device__ __forceinline__ bool flush_run(const Run<T>& r, T* win, int plane, in
 // one chunk's deposit window: numerator and denominator planes of Wmax rows
 size_t window_bytes(const SpDev& sp, int prec)
 {
-    return (size_t)2 * (prec == AVL_FP32 ? 4 : 8) * sp.Wmax * sp.nx;
+    return (size_t)2 * (prec == AVL_FP32 ? 4 : 8) * win_plane(sp.Wmax, sp.nx);
+}
+
+// the FP32 reference plane (f of the previous reconstruction over the window)
+static size_t fref_bytes(const SpDev& sp, int prec)
+{
+    return prec == AVL_FP32 ? (size_t)4 * win_plane(sp.Wmax, sp.nx) : 0;
 }
 
 size_t pd1_smem_bytes(const SpDev& sp, int prec)
 {
     size_t eb = (size_t)sp.nx * (prec == AVL_FP32 ? 4 : 8);
     eb = (eb + 15) & ~size_t(15);
-    return eb + 32 + (size_t)2 * HIST_S * 4 + (size_t)4 * sp.nx + window_bytes(sp, prec);
+    return eb + 32 + (size_t)2 * HIST_S * 4 + (((size_t)4 * sp.nx + 15) & ~size_t(15)) + window_bytes(sp, prec) +
+           fref_bytes(sp, prec);
 }
 
 // ---------------------------------------------------------------------------
@@ -535,7 +558,7 @@ __global__ void __launch_bounds__(PD_THREADS, 2) k_pd1(const StepArgs* __restric
     int* hcur = scnt + HIST_S;                             // current-key histogram (window placement)
     int* shs = hcur + HIST_S;                              // per-column row shift (nx)
     unsigned char* winb = smem + eb + 32 + 2 * HIST_S * 4 + ((4 * nx + 15) & ~15);
-    const int plane = W * nx;
+    const int plane = win_plane(W, nx);
     const size_t win_bytes = (size_t)2 * sizeof(T) * plane;
 
     const T* Eg = (sizeof(T) == 4) ? reinterpret_cast<const T*>(A->fd.E32) : reinterpret_cast<const T*>(A->fd.E64);
@@ -572,15 +595,37 @@ __global__ void __launch_bounds__(PD_THREADS, 2) k_pd1(const StepArgs* __restric
     }
     if (push && !use_bulk)
         for (int i = threadIdx.x; i < nx; i += PD_THREADS) Es[i] = Eg[i];
-    if (use_bulk && !mbar_wait_bounded(bar, 0, WAIT_LIMIT)) {
+    // a first wait that gives up flags the timeout; the copy is drained and
+    // the step goes on (every thread reaches the barrier below)
+    if (use_bulk && !mbar_wait_or_drain(bar, 0, ctl->wait_limit, WAIT_LIMIT))
         if (threadIdx.x == 0) atomicOr(&ctl->err, ERR_TIMEOUT);
-        mbar_wait_bounded(bar, 0, WAIT_LIMIT);
-        return;
-    }
     __syncthreads();
     const int row0 = misc[2];
 
     T* win = reinterpret_cast<T*>(winb);
+    // FP32: the reference plane, f of the previous reconstruction at every
+    // window cell (grid row wr + row0 + shs[x] of column x; 0 off the grid)
+    T* fref = win + 2 * plane;
+    if constexpr (sizeof(T) == 4) {
+        // eight rows' loads in flight per thread before their stores
+        constexpr int RB = 8;
+        const float* fprev = reinterpret_cast<const float*>(sp.fgrid);
+        for (int x = threadIdx.x; x < nx; x += PD_THREADS) {
+            const int j0x = row0 + shs[x];
+            for (int wr0 = 0; wr0 < W; wr0 += RB) {
+                float v[RB];
+#pragma unroll
+                for (int k = 0; k < RB; ++k) {
+                    const int j = j0x + wr0 + k;
+                    v[k] = (wr0 + k < W && (unsigned)j < (unsigned)nv) ? fprev[(size_t)j * nx + x] : 0.f;
+                }
+#pragma unroll
+                for (int k = 0; k < RB; ++k)
+                    if (wr0 + k < W) fref[(wr0 + k) * nx + x] = v[k];
+            }
+        }
+        __syncthreads();
+    }
     const T inv_dv = (T)sp.inv_dv[0];
     const T qm_dt = (T)sp.qm_dt;
     const T dt_dx = (T)sp.dt_dx;
@@ -655,22 +700,25 @@ __global__ void __launch_bounds__(PD_THREADS, 2) k_pd1(const StepArgs* __restric
                 const int j0 = kb + (int)ft;
                 code = rel_code(clampi(j0, 0, nv - 1), kbase);
                 const T wv = t - ft;
-                if (!have || i0 != run.i0 || j0 != run.j0) {
+                const bool first = !have || i0 != run.i0 || j0 != run.j0;
+                if (first) {
                     if (have)
-                        n_over += flush_run<T>(run, win, plane, row0, W, nx, nv, shs, ovf_num, ovf_den, ovf_tag, tag)
+                        n_over += flush_run<T>(run, win, plane, row0, W, nx, nv, shs, fref, ovf_num, ovf_den, ovf_tag,
+                                               tag)
                                       ? 1u
                                       : 0u;
                     run.reset(i0, j0);
                     have = true;
                 }
                 const T a[4] = {((T)1 - wx) * ((T)1 - wv), wx * ((T)1 - wv), ((T)1 - wx) * wv, wx * wv};
-                run.add(a, fl);
+                run.add(a, fl, first);
             }
             // the new key counted for this chunk (next step's window)
             if (push) hist_add(scnt, far_next, code, okm);
         }
         if (have)
-            n_over += flush_run<T>(run, win, plane, row0, W, nx, nv, shs, ovf_num, ovf_den, ovf_tag, tag) ? 1u : 0u;
+            n_over += flush_run<T>(run, win, plane, row0, W, nx, nv, shs, fref, ovf_num, ovf_den, ovf_tag, tag) ? 1u
+                                                                                                                : 0u;
         if (!push) continue;
         // in place: the positions and velocities go back where they came from
         if (any) {
@@ -797,6 +845,10 @@ cudaError_t launch_refine1(const StepArgs& h, int s, const int box[4], const int
 template <typename T>
 struct CellSum;
 
+// FP32: the window partials hold sum alpha (f_l - f_ref) and sum alpha
+// (see Run<float>); they are summed over the chunks in float-float, the FP64
+// overflow sums (absolute values) join as num - f_ref den, and
+// f = f_ref + num / den is formed in float-float.
 template <>
 struct CellSum<float> {
     ff num{0.f, 0.f}, den{0.f, 0.f};
@@ -806,23 +858,27 @@ struct CellSum<float> {
         ff_add(num, n);
         ff_add(den, d);
     }
-    __device__ __forceinline__ void add_ovf(double n, double d)
+    __device__ __forceinline__ void add_ovf(double n, double d, float fr)
     {
-        ff_add(num, (float)n);
-        num.lo = __fadd_rn(num.lo, (float)(n - (double)(float)n));
+        const double nd = n - (double)fr * d;
+        ff_add(num, (float)nd);
+        num.lo = __fadd_rn(num.lo, (float)(nd - (double)(float)nd));
         ff_add(den, (float)d);
         den.lo = __fadd_rn(den.lo, (float)(d - (double)(float)d));
     }
-    // f = num / den as float-float (q, r / den); den = 0 gives f = 0
-    __device__ __forceinline__ void value(float& fh, float& fl, float& dsum) const
+    // f = f_ref + num / den as float-float (fh, fl); den = 0 gives f = 0
+    __device__ __forceinline__ void value(float fr, float& fh, float& fl, float& dsum) const
     {
         dsum = __fadd_rn(den.hi, den.lo);
         if (den.hi > 0.f) {
             const float q = __fdiv_rn(num.hi, den.hi);
             float r = fmaf(-q, den.hi, num.hi);
             r = __fadd_rn(r, __fsub_rn(num.lo, __fmul_rn(q, den.lo)));
-            fh = q;
-            fl = __fdiv_rn(r, den.hi);
+            const float ql = __fdiv_rn(r, den.hi);
+            float h = fr, l = 0.f;
+            two_sum_add(h, l, q);
+            fh = h;
+            fl = __fadd_rn(l, ql);
         } else {
             fh = 0.f;
             fl = 0.f;
@@ -839,12 +895,12 @@ struct CellSum<double> {
         num += n;
         den += d;
     }
-    __device__ __forceinline__ void add_ovf(double n, double d)
+    __device__ __forceinline__ void add_ovf(double n, double d, double)
     {
         num += n;
         den += d;
     }
-    __device__ __forceinline__ void value(double& fh, double& fl, double& dsum) const
+    __device__ __forceinline__ void value(double, double& fh, double& fl, double& dsum) const
     {
         dsum = den;
         fh = den > 0.0 ? num / den : 0.0;
@@ -878,7 +934,7 @@ __global__ void __launch_bounds__(FIN_THREADS, 4) k_fin1(const StepArgs* __restr
     const int x = xb * FIN_XB + col;
     const bool xok = x < nx;
     const int j0 = rqi * sp.rq, j1 = min(nv, j0 + sp.rq);
-    const int plane = W * nx;
+    const int plane = win_plane(W, nx);
     const bool any_ovf = ctl->ovf_count[s] != 0;
     double* ovf_num = sp.ovf;
     double* ovf_den = sp.ovf + (size_t)nv * nx;
@@ -929,15 +985,18 @@ __global__ void __launch_bounds__(FIN_THREADS, 4) k_fin1(const StepArgs* __restr
 
     ColAcc<T> acc;
     // overflow rows, f = num / den, f and n stored, charge and diagnostics
+    // (FP32: f_ref = the cell's f of the previous reconstruction, read before
+    // it is overwritten; the deposit kernel staged the same value)
     auto finish = [&](int j, CellSum<T>& cs) {
+        const T fr = sizeof(T) == 4 ? fg[(size_t)j * nx + x] : (T)0;
         if (any_ovf && ovf_tag[j] == tag) {
             const size_t o = (size_t)j * nx + x;
-            cs.add_ovf(ovf_num[o], ovf_den[o]);
+            cs.add_ovf(ovf_num[o], ovf_den[o], fr);
             ovf_num[o] = 0.0;
             ovf_den[o] = 0.0;
         }
         T fh, fl, dsum;
-        cs.value(fh, fl, dsum);
+        cs.value(fr, fh, fl, dsum);
         fg[(size_t)j * nx + x] = fh + fl;
         ng[(size_t)j * nx + x] = dsum;
         const T vj = (T)(sp.vmin[0] + (j + 0.5) * sp.dv[0]);

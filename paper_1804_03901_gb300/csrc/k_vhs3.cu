@@ -301,6 +301,7 @@ __global__ void __launch_bounds__(P3_THREADS, sizeof(T) == 4 ? (CPT == 1 ? 4 : (
     const bool push = mode == 1;
     if (mode != 0 && !sp.mobile) return;
     Ctl* ctl = A->ctl;
+    const long long wait_first = ctl->wait_limit;
     const int p = g - sp.pen_base;
     const int nx = sp.nx, nvx = sp.nv[0], nvy = sp.nv[1], nvz = sp.nv[2], nkey = sp.nkey;
     const int pjy = p % (nvy + 1) - 1, pjz = p / (nvy + 1) - 1;
@@ -404,7 +405,7 @@ __global__ void __launch_bounds__(P3_THREADS, sizeof(T) == 4 ? (CPT == 1 ? 4 : (
                 if (nk < nkey) issue(buf ^ 1, nb, min(NB, segs[nk + 1] - nb));
             }
             const unsigned ph = buf ? ph1 : ph0;
-            if (!mbar_wait_bounded(&bar[buf], ph, WAIT_LIMIT)) flag_s = 1;
+            if (!mbar_wait_or_drain(&bar[buf], ph, wait_first, WAIT_LIMIT)) flag_s = 1;
             if (buf) ph1 ^= 1u; else ph0 ^= 1u;
             const T* st = stage + buf * NF * SLEN;
             const int o0 = b0 & (AL - 1);

@@ -51,6 +51,19 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity
     return false;
 }
 
+// Wait for a phase of an mbarrier that counts a bulk copy: at most
+// `first_limit` polls, then, if the phase has not completed, report the
+// timeout (returns false) after draining the copy with up to `drain_limit`
+// polls, so that the block does not go on, or exit, with the copy still in
+// flight into its shared memory.
+__device__ __forceinline__ bool mbar_wait_or_drain(uint64_t* bar, unsigned parity, long long first_limit,
+                                                   long long drain_limit)
+{
+    if (mbar_wait_bounded(bar, parity, first_limit)) return true;
+    mbar_wait_bounded(bar, parity, drain_limit);
+    return false;
+}
+
 // Bulk copy global -> shared, completion counted on `bar` (bytes % 16 == 0,
 // both addresses 16-byte aligned).
 __device__ __forceinline__ void bulk_g2s(void* dst_smem, const void* src, unsigned bytes,

@@ -5,15 +5,15 @@ library's CUDA graph), against the FP64 oracle.
 After a few steps the oracle takes the GPU's marker state and rebuilds every
 grid from it (Eq. 4 reconstruction, Eq. 14 moment, Eq. 6 field), and then
 both advance one step from that identical state.  The whole grids are
-compared (relative L2, FP32 tolerance 1e-5 as in the small cases): the
-denominator n of Eq. 4 checks every marker's position and velocity, f its
-value, rho and E the moment and the solve.
+compared by plain relative L2 (FP32 tolerance 1e-5 as in the small cases):
+the denominator n of Eq. 4 checks every marker's position and velocity, f
+its value, rho and E the moment and the solve.
 
 The net charge of Eq. 14 is a difference of nearly equal species charges in
-these quasi-neutral runs (two-stream: |rho| ~ 4e-5 of either species'), so
-rounding at the FP32 level of f shows in rho amplified by that ratio.  rho's
-error is therefore measured against the species charge scale
-||sum_s |rho_s|||, and E against the FP64 solve (Eq. 6) of the GPU's own rho.
+the quasi-neutral two-stream runs (|rho| ~ 1e-4 of either species'), so the
+FP32 path must reconstruct each species' charge to about 1e-10: the deposit
+sums deviations from the previous reconstruction (see k_vhs1.cu), which
+this test holds to the plain tolerance.
 """
 import numpy as np
 import pytest
@@ -44,9 +44,11 @@ def compare_grids(sim, orc, tol, what):
         assert rel(f, orc.f[s]) < tol, (what, "f", s, rel(f, orc.f[s]))
         assert rel(n, orc.den[s]) < tol, (what, "n", s, rel(n, orc.den[s]))
     rho, E = sim.get_rho(), sim.get_E()
-    scale = np.linalg.norm(sum(np.abs(r) for r in orc.rho_s))
-    err = np.linalg.norm(rho - orc.rho) / scale
-    assert err < tol, (what, "rho against the species charge scale", err)
+    errs = {"rho": rel(rho, orc.rho), "E": rel(E, orc.E)}
+    print(what, {k: f"{v:.2e}" for k, v in errs.items()})
+    assert errs["rho"] < tol, (what, "rho", errs["rho"])
+    assert errs["E"] < tol, (what, "E", errs["E"])
+    # the solve itself: E against the FP64 solve (Eq. 6) of the GPU's own rho
     E_of_rho = O.poisson(orc.nx, orc.L, orc.cP, orc.softening, rho)
     assert rel(E, E_of_rho) < 1e-10, (what, "E against the FP64 solve of rho", rel(E, E_of_rho))
 
