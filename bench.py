@@ -1,19 +1,25 @@
 #!/usr/bin/env python3
 """Throughput of the Vlasov-Hybrid time step on GB300 (marker-steps/s).
 
-Default workload: the two-stream instability 1d1v in the FP32 production
-form (nx = 512, nv = 1024, 4 x 4 markers per cell, electrons + mobile ions,
-16.8 M markers, dt = 0.05), timed over K full steps (K = 2000 is the whole
-run, linear growth and nonlinear saturation) starting from t = 0.  One step
-is the whole hot path: gather + push, VHS reconstruction, moment, FP64
-Poisson, diagnostics and the re-sort check.
+Default workload: bump-on-tail 1d3v, the largest single-GPU configuration
+(nx = 256, nv = 64^3 over [-8, 8]^3, 2 markers per cell: 134 217 728
+markers, dt = 0.05, a 500-step run).  The line's value is the FP64 form
+(the paper's precision); the FP32 production form of the same workload is
+reported beside it under "fp32".  Each form is timed over K full steps from
+the middle of the run (the state after half the run's steps, reached by
+untimed steps), so that the timed steps see the re-sorting, grown state of
+the run rather than its first steps.  One step is the whole hot path:
+gather + push, VHS reconstruction, moment, FP64 Poisson, diagnostics and the
+re-sort check.  The adjoint / forward cost of the two-stream adjoint
+workload (500 steps) is reported as "adjoint_over_forward".
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload NAME] [--precision auto|fp64|fp32|both]
 
 Prints one JSON line.  --impl reference times the FP64 CPU oracle on the
-host cores instead (a bounded sample of the same workload per step).
-Under torchrun each rank runs an independent replica (weak scaling, no
-collective on the data path).
+host cores instead (an x-slab of the same workload per step).  Under
+torchrun each rank runs an independent replica (weak scaling, no collective
+on the data path).
 """
 from __future__ import annotations
 
@@ -66,16 +72,21 @@ KERNEL_DESC = {1: "k_pd1 (gather + push + VHS deposit, written back in place)",
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=2000)
+    p.add_argument("--steps", type=int, default=20)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--workload", choices=["two_stream", "landau", "bump_on_tail", "bernstein", "two_stream_adjoint",
-                                          "ensemble"],
-                   default="two_stream")
+                                          "ensemble", "landau_paper"],
+                   default="bump_on_tail")
+    p.add_argument("--precision", choices=["auto", "fp64", "fp32", "both"], default="auto",
+                   help="auto: both forms for bump_on_tail (FP64 first), else the workload's own")
+    p.add_argument("--start-step", type=int, default=-1,
+                   help="untimed steps before the warm-up (-1: half the run, 0: time from t = 0)")
     p.add_argument("--nrun", type=int, default=256, help="runs of the ensemble workload")
     p.add_argument("--no-autotune", action="store_true", help="ensemble: keep the chunk-size heuristic")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--no-adjoint", action="store_true", help="leave out the adjoint / forward cost")
     p.add_argument("--nv", type=int, default=0, help="velocity cells (profiling of a smaller case)")
     p.add_argument("--amp", type=float, default=0.0,
                    help="two-stream perturbation amplitude instead of 1e-4 (profiling of the re-sorting, "
@@ -98,11 +109,59 @@ def workload(name, nv=0, amp=0.0):
         return inputs.two_stream_adjoint(nv=nv) if nv else inputs.two_stream_adjoint()
     if name == "ensemble":
         return inputs.ensemble()
+    if name == "landau_paper":
+        return inputs.landau_paper(nv=nv) if nv else inputs.landau_paper()
     return inputs.landau(nv=nv) if nv else inputs.landau()
 
 
-SAMPLE_FRACTION = {"two_stream": 1.0 / 64, "bump_on_tail": 1.0 / 256, "bernstein": 1.0 / 256, "landau": 1.0,
-                   "two_stream_adjoint": 1.0 / 16}
+def with_precision(w, prec):
+    """The workload in precision prec, named for it."""
+    w2 = dict(w)
+    w2["precision"] = prec
+    w2["name"] = w["name"].replace("_fp32_", f"_{prec}_").replace("_fp64_", f"_{prec}_")
+    if f"_{prec}_" not in w2["name"]:
+        w2["name"] = w2["name"] + f"_{prec}"
+    return w2
+
+
+def precisions(args, w):
+    if args.precision == "auto":
+        return ["fp64", "fp32"] if args.workload == "bump_on_tail" else [w["precision"]]
+    if args.precision == "both":
+        return ["fp64", "fp32"]
+    return [args.precision]
+
+
+# x-slab of the workload that the CPU oracle times per step: nx / SLAB cells
+# (same cell width, markers per cell and velocity grid, so that the markers
+# and the grid cells shrink together and the rate per marker is the full
+# workload's); the reference arm takes a thinner slab to stay within minutes
+SLAB = {"two_stream": 8, "bump_on_tail": 16, "bernstein": 16, "landau": 1, "landau_paper": 8,
+        "two_stream_adjoint": 4}
+REF_SLAB = {"two_stream": 16, "bump_on_tail": 32, "bernstein": 32, "landau": 1, "landau_paper": 16,
+            "two_stream_adjoint": 8}
+
+
+def host_cpu():
+    """Host CPU model and core count (recorded beside every CPU rate)."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    if model is None:
+        try:
+            for line in open("/proc/cpuinfo"):
+                if line.lower().startswith(("model name", "cpu part")):
+                    model = line.split(":", 1)[1].strip()
+                    break
+        except OSError:
+            model = "unknown"
+    return model or "unknown", os.cpu_count() or 1
 
 
 def markers_of(w):
@@ -232,21 +291,27 @@ def init_markers(A, sim, w, seed_offset=0):
         sim.init_markers(s, lat, A.make_f0(f0["beams"], f0["modes"]), w["seed"] + seed_offset, w["jitter"])
 
 
-def cpu_oracle_rate(w, budget_s=12.0, sample_fraction=1.0, steps=None, seed=0):
-    """Marker-steps/s of the FP64 oracle (single thread) on the workload, or on
-    a random marker subsample of it."""
+def slab_of(w, slab):
+    """The workload restricted to nx / slab cells of the same width."""
+    if slab <= 1:
+        return w
+    w2 = dict(w)
+    w2["nx"] = max(4, w["nx"] // slab)
+    w2["L"] = w["L"] * w2["nx"] / w["nx"]
+    return w2
+
+
+def cpu_oracle_rate(w, budget_s=12.0, slab=1, steps=None):
+    """Marker-steps/s of the FP64 oracle (single thread) on an x-slab of the
+    workload: (rate, markers, steps done, seconds)."""
     from oracle import oracle as O
-    species = [O.Species(**sp) for sp in w["species"]]
-    sim = O.OracleSim(w["nvdim"], w["nx"], w["L"], w["dt"], species)
-    if "B" in w:
-        sim.B = np.asarray(w["B"], dtype=np.float64)
-    rng = np.random.default_rng(seed)
-    for s, (f0, lat) in enumerate(zip(w["f0"], w["lattice"])):
-        sim.init_markers(s, lat, O.F0(f0["beams"], f0["modes"]), w["seed"], w["jitter"])
-        if sample_fraction < 1.0:
-            n = sim.x[s].size
-            keep = rng.choice(n, max(1, int(n * sample_fraction)), replace=False)
-            sim.set_markers(s, sim.x[s][keep], sim.v[s][:, keep], sim.fl[s][keep])
+    ws = slab_of(w, slab)
+    species = [O.Species(**sp) for sp in ws["species"]]
+    sim = O.OracleSim(ws["nvdim"], ws["nx"], ws["L"], ws["dt"], species)
+    if "B" in ws:
+        sim.B = np.asarray(ws["B"], dtype=np.float64)
+    for s, (f0, lat) in enumerate(zip(ws["f0"], ws["lattice"])):
+        sim.init_markers(s, lat, O.F0(f0["beams"], f0["modes"]), ws["seed"], ws["jitter"])
     sim.refresh()
     nmark = sum(x.size for x in sim.x)
     done, t0 = 0, time.perf_counter()
@@ -261,50 +326,85 @@ def cpu_oracle_rate(w, budget_s=12.0, sample_fraction=1.0, steps=None, seed=0):
     return nmark * done / el, nmark, done, el
 
 
+def cpu_baseline_entry(w, slab, budget_s=12.0):
+    """The oracle's rate on the host cores of this run, with the host CPU and
+    the per-core rate times the core count (an ideal-scaling figure: the
+    oracle itself runs on one thread)."""
+    rate, nm, done, el = cpu_oracle_rate(w, budget_s=budget_s, slab=slab)
+    model, cores = host_cpu()
+    return {"value": rate, "unit": "marker-steps/s", "cores": 1, "kind": "oracle",
+            "sample": f"{done} full steps of an x-slab of the {w['name']} workload (1/{slab} of the x cells: "
+                      f"nx = {slab_of(w, slab)['nx']}, same cell width, markers per cell and velocity grid; "
+                      f"{nm} markers), FP64 oracle, 1 thread, {el:.1f} s",
+            "host_cpu": model, "host_cores": cores,
+            "ideal_scaling_all_cores": {"value": rate * cores, "unit": "marker-steps/s",
+                                        "note": f"per-core rate x {cores} cores (not measured: the oracle "
+                                                f"runs on one thread)"}}
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return
     w = workload(args.workload, args.nv)
-    frac = SAMPLE_FRACTION[args.workload]
-    cpu_oracle_rate(w, sample_fraction=frac, steps=max(1, args.warmup))   # warm-up (page-in)
-    rate, nmark, done, el = cpu_oracle_rate(w, sample_fraction=frac, steps=args.steps)
-    sample = (f"FP64 oracle, 1 thread, {done} steps of the {w['name']} workload with a random "
-              f"{frac:.4g} marker subsample ({nmark} markers) on the full grids")
+    prec = precisions(args, w)[0]
+    w = with_precision(w, prec)
+    slab = REF_SLAB.get(args.workload, 1)
+    cpu_oracle_rate(w, slab=slab, steps=max(1, args.warmup))   # warm-up (page-in)
+    rate, nmark, done, el = cpu_oracle_rate(w, slab=slab, steps=args.steps)
+    model, cores = host_cpu()
+    sample = (f"FP64 oracle, 1 thread, {done} full steps of an x-slab of the {w['name']} workload "
+              f"(1/{slab} of the x cells, nx = {slab_of(w, slab)['nx']}, {nmark} markers)")
     line = {"impl": "reference", "metric": "marker_steps_per_s", "value": rate, "unit": "marker-steps/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * el / done, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": w["name"], "sample": sample},
             "cpu_baseline": {"value": rate, "unit": "marker-steps/s", "cores": 1, "kind": "oracle",
-                             "sample": sample},
+                             "sample": sample, "host_cpu": model, "host_cores": cores},
             "e2e": {"value": rate, "unit": "marker-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
-def run_ours(args):
-    import torch
-    rank, world, local = dist_env()
-    torch.cuda.set_device(local)
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    from paper_1804_03901_gb300 import avl as A
+# FP64 floating-point operations per marker of the 1d3v push + deposit k_pd3
+# (an FMA counts 2; see fp64_flops_3d)
+def fp64_flops_3d():
+    push = 2 + 4 + 2 + 2          # CIC weight of x, field gather, kick, drift
+    weights = 3 * 3 + 2 + 6       # dual rows and weights of v_x, v_y, v_z; new x weight; four (v_y, v_z) weights
+    gather = 2 * (5 + 16 * 2)     # per column of the marker (two): ax, a1, a0, a0 f, a1 f; 16 FMAs into the rows
+    return float(push + weights + gather)
 
-    w = workload(args.workload, args.nv, args.amp)
-    # a dedicated stream: the library enqueues on it, the timing events too
-    stream = torch.cuda.Stream()
-    torch.cuda.set_stream(stream)
+
+FP64_FLOPS_PER_MARKER[3] = fp64_flops_3d()
+
+
+def measure(A, w, args, rank, world, local, stream):
+    """Device-timed, profiled and end-to-end rates of one precision form of
+    the workload, timed from the state after args.start_step (or half the
+    run) untimed steps and W warm-up steps."""
+    import torch
+    prec = w["precision"]
     sim = build_sim(A, w, stream.cuda_stream, seed_offset=rank)
     nmark = markers_of(w)
-    for s in range(len(w["species"])):
+    ns = len(w["species"])
+    nvd = w["nvdim"]
+    for s in range(ns):
         assert sim.marker_count(s) > 0
-
-    # warm-up, then restart the run from t = 0
+    start = w["steps"] // 2 if args.start_step < 0 else args.start_step
+    if start:
+        sim.step(start)
     sim.step(max(3, args.warmup))
     sim.synchronize()
-    init_markers(A, sim, w, rank)
-    sim.synchronize()
+    # the state the timed steps start from, kept on the host for the
+    # end-to-end leg and the per-kernel profile
+    hx, hv, hf = [], [], []
+    if not args.no_e2e:
+        for s in range(ns):
+            x, v, f = sim.get_markers(s)
+            hx.append(torch.from_numpy(x).pin_memory())
+            hv.append(torch.from_numpy(np.ascontiguousarray(v[:nvd])).pin_memory())
+            hf.append(torch.from_numpy(f).pin_memory())
+            del x, v, f
 
     def barrier():
         torch.cuda.synchronize()
@@ -331,56 +431,15 @@ def run_ours(args):
     ms = max_over_ranks(ms, world)
     value = job_rate(nmark, world, args.steps, ms / 1e3)
 
-    # per-kernel CUDA-event timing over the same K steps from t = 0
-    init_markers(A, sim, w, rank)
-    sim.synchronize()
-    kms = sim.profile_steps(args.steps)
-    hbm, peak_kind = peaks()
-    pd_ms = kms[1] / args.steps
-    prec = w["precision"]
-    nvd = w["nvdim"]
-    kind = "3B" if nvd == 3 and any(w.get("B", (0.0, 0.0, 0.0))) else nvd
-    algo, lay = BYTES_PER_MARKER_ALGO[(kind, prec)], BYTES_PER_MARKER_LAYOUT[(kind, prec)]
-    achieved = nmark * algo / (pd_ms / 1e3) / 1e9
-    traffic_pm = recorded_traffic(w["name"], prec, nvd)
-    names = KERNEL_NAMES[kind]
-    roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-                "traffic": traffic_pm * nmark if traffic_pm else None,
-                "kernel": KERNEL_DESC[kind],
-                "algorithmic_bytes_per_marker": algo,
-                "layout_bytes_per_marker": lay,
-                "frac_layout_bytes": nmark * lay / (pd_ms / 1e3) / 1e9 / hbm,
-                "peak_kind": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else peak_kind,
-                "kernel_ms_per_step": {k: float(v / args.steps) for k, v in zip(names, kms)},
-                "kernel_share": {k: float(v / kms.sum()) for k, v in zip(names, kms)}}
-    if prec == "fp64" and kind in FP64_FLOPS_PER_MARKER:
-        # the FP64 form: the same kernel against the FP64 pipe
-        props = torch.cuda.get_device_properties(torch.cuda.current_device())
-        mhz = clk.get("sm_max_mhz") or clk.get("sm_mhz") or 2070.0
-        fpeak = FP64_FMA_PER_SM_CLK * 2.0 * props.multi_processor_count * mhz * 1e6 / 1e12
-        fach = nmark * FP64_FLOPS_PER_MARKER[kind] / (pd_ms / 1e3) / 1e12
-        roofline["fp64_pipe"] = {"achieved": fach, "peak": fpeak, "unit": "TFLOP/s", "frac": fach / fpeak,
-                                 "flops_per_marker": FP64_FLOPS_PER_MARKER[kind],
-                                 "peak_kind": "2 FP64 FMA lanes per clock per SM (microbenchmark) x SMs x max SM clock"}
-
-    # end to end through the C ABI with host buffers
+    # end to end through the C ABI with host buffers, from the same state
     e2e = None
     if not args.no_e2e:
-        # the initial state of the same run (from t = 0, as the device-timed steps)
-        init_markers(A, sim, w, rank)
-        sim.synchronize()
-        hx, hv, hf = [], [], []
-        for s in range(len(w["species"])):
-            x, v, f = sim.get_markers(s)
-            hx.append(torch.from_numpy(x).pin_memory())
-            hv.append(torch.from_numpy(np.ascontiguousarray(v[:nvd])).pin_memory())
-            hf.append(torch.from_numpy(f).pin_memory())
-        nd = 3 + 3 * len(w["species"])
+        nd = 3 + 3 * ns
         diag = torch.zeros((args.steps, nd), dtype=torch.float64).pin_memory()
         h2d = sum(t.numel() * 8 for t in hx + hv + hf)
         barrier()
         t0 = time.perf_counter()
-        for s in range(len(w["species"])):
+        for s in range(ns):
             sim.set_markers(s, hx[s], hv[s], hf[s])
         for k in range(args.steps):
             sim.step(1)
@@ -393,37 +452,146 @@ def run_ours(args):
         el = max_over_ranks(time.perf_counter() - t0, world)
         e2e = {"value": job_rate(nmark, world, args.steps, el), "unit": "marker-steps/s",
                "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": nd * 8,
-               "note": "timed: avl_set_markers of the initial state from pinned host memory, then K x "
-                       "(avl_step + avl_get_diag_async of that step's diagnostics row into pinned host "
-                       "memory), avl_synchronize and the host's check of every row"}
+               "note": "timed: avl_set_markers of the start state (FP64 x, v, f of every marker) from pinned "
+                       "host memory, then K x (avl_step + avl_get_diag_async of that step's diagnostics row "
+                       "into pinned host memory), avl_synchronize and the host's check of every row; the "
+                       "start state's upload is counted once and spread over the K steps"}
+
+    # per-kernel CUDA-event timing over K steps from the same state
+    if not args.no_e2e:
+        for s in range(ns):
+            sim.set_markers(s, hx[s], hv[s], hf[s])
+    sim.synchronize()
+    kms = sim.profile_steps(args.steps)
+    hbm, peak_kind = peaks()
+    pd_ms = kms[1] / args.steps
+    kind = "3B" if nvd == 3 and any(w.get("B", (0.0, 0.0, 0.0))) else nvd
+    algo, lay = BYTES_PER_MARKER_ALGO[(kind, prec)], BYTES_PER_MARKER_LAYOUT[(kind, prec)]
+    achieved = nmark * algo / (pd_ms / 1e3) / 1e9
+    traffic_pm = recorded_traffic(w["name"], prec, nvd)
+    names = KERNEL_NAMES[kind]
+    hbm_entry = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                 "traffic": traffic_pm * nmark if traffic_pm else None,
+                 "kernel": KERNEL_DESC[kind],
+                 "algorithmic_bytes_per_marker": algo,
+                 "layout_bytes_per_marker": lay,
+                 "frac_layout_bytes": nmark * lay / (pd_ms / 1e3) / 1e9 / hbm,
+                 "peak_kind": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else peak_kind,
+                 "kernel_ms_per_step": {k: float(v / args.steps) for k, v in zip(names, kms)},
+                 "kernel_share": {k: float(v / kms.sum()) for k, v in zip(names, kms)}}
+    roofline = hbm_entry
+    if prec == "fp64" and kind in FP64_FLOPS_PER_MARKER:
+        # the FP64 form is bound by the FP64 pipe (a small fraction of the
+        # FP32 rate on this GPU): the same kernel against it
+        props = torch.cuda.get_device_properties(torch.cuda.current_device())
+        mhz = clk.get("sm_max_mhz") or clk.get("sm_mhz") or 2070.0
+        fpeak = FP64_FMA_PER_SM_CLK * 2.0 * props.multi_processor_count * mhz * 1e6 / 1e12
+        fach = nmark * FP64_FLOPS_PER_MARKER[kind] / (pd_ms / 1e3) / 1e12
+        roofline = {"bound": "alu", "achieved": fach, "peak": fpeak, "unit": "TFLOP/s", "frac": fach / fpeak,
+                    "traffic": hbm_entry["traffic"], "kernel": KERNEL_DESC[kind],
+                    "flops_per_marker": FP64_FLOPS_PER_MARKER[kind],
+                    "peak_kind": "FP64 pipe: 2 FMA lanes per clock per SM (in-bounds microbenchmark) x 2 FLOP x "
+                                 "SMs x the sampled maximum SM clock",
+                    "kernel_ms_per_step": hbm_entry["kernel_ms_per_step"],
+                    "kernel_share": hbm_entry["kernel_share"],
+                    "hbm": {k: hbm_entry[k] for k in ("achieved", "peak", "unit", "frac", "algorithmic_bytes_per_marker",
+                                                      "peak_kind")}}
+    sim.close()
+    return {"value": value, "ms_per_step": ms / args.steps, "dtype": "f32" if prec == "fp32" else "f64",
+            "workload": w["name"], "markers": nmark, "start_step": start, "roofline": roofline, "clocks": clk,
+            "e2e": e2e, "kind": kind, "stats": stats}
+
+
+def adjoint_cost(A, stream, nv=0):
+    """Wall time of avl_adjoint over the forward run it differentiates
+    (two-stream adjoint workload, 500 steps, checkpoints every 50), FP32 and
+    FP64."""
+    import torch
+    w = workload("two_stream_adjoint", nv)
+    out = {"workload": w["name"], "steps": w["steps"], "ckpt_every": w["ckpt"]}
+    f0 = w["f0"][0]
+    for prec in ("fp32", "fp64"):
+        w2 = dict(w)
+        w2["precision"] = prec
+        sim = build_sim(A, w2, stream.cuda_stream)
+        sim.step(3)
+        init_markers(A, sim, w2)
+        sim.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        sim.step(w["steps"])
+        e1.record(stream)
+        sim.synchronize()
+        fwd = e0.elapsed_time(e1)
+        theta = A.make_f0(f0["beams"], f0["modes"])
+        sim.adjoint(0, theta, w["steps"], w["ckpt"])   # warm-up (buffers)
+        t0 = time.perf_counter()
+        sim.adjoint(0, theta, w["steps"], w["ckpt"])
+        adj = 1e3 * (time.perf_counter() - t0)
+        sim.close()
+        out[prec] = {"value": adj / fwd, "forward_ms": fwd, "adjoint_ms": adj}
+    out["value"] = out["fp32"]["value"]
+    out["unit"] = "x (adjoint wall time / forward wall time, FP32; FP64 beside)"
+    return out
+
+
+def run_ours(args):
+    import torch
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_1804_03901_gb300 import avl as A
+
+    base = workload(args.workload, args.nv, args.amp)
+    # a dedicated stream: the library enqueues on it, the timing events too
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    forms = [measure(A, with_precision(base, p), args, rank, world, local, stream) for p in precisions(args, base)]
+    main_form = forms[0]
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        frac = 1.0 if args.workload == "two_stream" else SAMPLE_FRACTION[args.workload]
-        rate, nm, done, el = cpu_oracle_rate(w, budget_s=12.0, sample_fraction=frac)
-        what = "full steps" if frac == 1.0 else f"steps of a random {frac:.4g} marker subsample (full grids)"
-        cpu = {"value": rate, "unit": "marker-steps/s", "cores": 1, "kind": "oracle",
-               "sample": f"{done} {what} of the {w['name']} workload ({nm} markers), FP64, 1 thread, "
-                         f"{el:.1f} s"}
+        cpu = cpu_baseline_entry(with_precision(base, "fp64"), SLAB.get(args.workload, 1))
+    adj = None
+    if rank == 0 and world == 1 and not args.no_adjoint:
+        adj = adjoint_cost(A, stream)
 
+    l2 = {"two_stream": "inputs larger than L2 (markers 16 B each, 268 MB per step read)",
+          "bump_on_tail": "inputs larger than L2 (markers 24 B (FP32) / 40 B (FP64) each, 3.2 / 5.4 GB per step)",
+          "bernstein": "inputs larger than L2 (markers 24 B each, 3.2 GB per step read)",
+          "landau_paper": "inputs larger than L2 (markers 24 B each, 324 MB per step read)",
+          "landau": "small workload (fits in L2)"}[args.workload]
     if rank == 0:
-        line = {"metric": "marker_steps_per_s", "value": value, "unit": "marker-steps/s", "n_gpus": world,
-                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+        f = main_form
+        kind, nvd = f["kind"], base["nvdim"]
+        line = {"metric": "marker_steps_per_s", "value": f["value"], "unit": "marker-steps/s", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": f["ms_per_step"],
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-                "dtype": "f32" if prec == "fp32" else "f64", "data": "synthetic",
-                "config": {"workload": w["name"], "markers": nmark, "species": len(w["species"]),
-                           "steps_in_run": w["steps"], "timed_from": "t = 0",
-                           "l2": {"two_stream": "inputs larger than L2 (markers 16 B each, 268 MB per step read)",
-                                  "bump_on_tail": "inputs larger than L2 (markers 24 B each, 3.2 GB per step read)",
-                                  "bernstein": "inputs larger than L2 (markers 24 B each, 3.2 GB per step read)",
-                                  "landau": "small workload (fits in L2)"}[args.workload],
-                           "parallelism": "single GPU" if world == 1 else f"{world} independent replicas"},
-                "roofline": roofline, "clocks": clk, "gpu_launches": LAUNCHES_PER_STEP[kind] * args.steps,
-                ("out_of_window_runs_last_step" if nvd == 1 else "movers_last_step"): [int(x) for x in stats[:, 0]],
-                "resort_steps": [int(x) for x in stats[:, 1]], "e2e": e2e,
-                "cpu_baseline": cpu}
+                "dtype": f["dtype"], "data": "synthetic",
+                "config": {"workload": f["workload"], "markers": f["markers"], "species": len(base["species"]),
+                           "steps_in_run": base["steps"],
+                           "timed_from": (f"step {f['start_step']} of the {base['steps']}-step run (state reached "
+                                          f"by untimed steps), then {max(3, args.warmup)} warm-up steps"
+                                          if f["start_step"] else "t = 0"),
+                           "l2": l2, "parallelism": "single GPU" if world == 1 else f"{world} independent replicas"},
+                "roofline": f["roofline"], "clocks": f["clocks"],
+                "gpu_launches": LAUNCHES_PER_STEP[kind] * args.steps,
+                ("out_of_window_runs_last_step" if nvd == 1 else "movers_last_step"): [int(x) for x in
+                                                                                      f["stats"][:, 0]],
+                "resort_steps": [int(x) for x in f["stats"][:, 1]], "e2e": f["e2e"], "cpu_baseline": cpu}
+        for g in forms[1:]:
+            line[g["dtype"].replace("f", "fp")] = {
+                "value": g["value"], "unit": "marker-steps/s", "ms_per_step": g["ms_per_step"], "dtype": g["dtype"],
+                "workload": g["workload"], "roofline": g["roofline"], "clocks": g["clocks"], "e2e": g["e2e"],
+                "cpu_baseline": cpu, "gpu_launches": LAUNCHES_PER_STEP[g["kind"]] * args.steps,
+                "resort_steps": [int(x) for x in g["stats"][:, 1]],
+                "note": "the same workload in the FP32 production form, timed the same way; cpu_baseline is the "
+                        "FP64 oracle (it has no FP32 form)"}
+        if adj is not None:
+            line["adjoint_over_forward"] = adj
         print(json.dumps(line), flush=True)
-    sim.close()
     if world > 1:
         torch.distributed.destroy_process_group()
 
