@@ -807,11 +807,17 @@ avl_status avl_create(const avl_domain* dom, const avl_species* spec, int32_t ns
     h.nchunk_total = 0;
     h.nfin_total = fin_base;
 
-    void *pa, *pc, *pf0, *pbad;
+    void *pa, *pc, *pf0, *pbad, *plog;
     if ((e = dalloc(c, &pa, sizeof(StepArgs), false)) || (e = dalloc(c, &pc, sizeof(Ctl), true)) ||
-        (e = dalloc(c, &pf0, sizeof(avl_f0), false)) || (e = dalloc(c, &pbad, 8, true))) {
+        (e = dalloc(c, &pf0, sizeof(avl_f0), false)) || (e = dalloc(c, &pbad, 8, true)) ||
+        (e = dalloc(c, &plog, 128 * sizeof(double2), false))) {
         cuda_fail(c, e, "cudaMalloc(control)");
         return bail(AVL_ENOMEM);
+    }
+    h.fd.logtab = (const double2*)plog;
+    if ((e = init_log_table((double2*)plog, c->st))) {
+        cuda_fail(c, e, "avl_create (logarithm table)");
+        return bail(AVL_ECUDA);
     }
     c->d_args = (StepArgs*)pa;
     c->d_ctl = (Ctl*)pc;

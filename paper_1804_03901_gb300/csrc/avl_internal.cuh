@@ -138,6 +138,7 @@ struct FieldDev {
     const double* gmul;        // cP kappa / K^2 for m <= nx/2 (0 at m = 0 and Nyquist)
     const double* green;       // nx <= GREEN_MAX: G of E = G (circulant) rho, else null
     double* diag;              // 3 + 3 ns
+    const double2* logtab;     // [128] (log c_j, 1 / c_j) of the FP64 entropy logarithm (log_tab)
     double* hist;              // field history for marker refinement: [hist_cap][nx] FP64, or null;
                                // slot k holds E of the state after step hist_origin + k
     int hist_cap;
@@ -296,5 +297,7 @@ void green_table(int nx, const double* gm, double* G);
 cudaError_t launch_poisson_dense(const double* rho, double* E, int nx, const double* G, cudaStream_t st);
 cudaError_t launch_poisson(const double* rho, double* E, int nx, const double2* tw, const double* gmul,
                            cudaStream_t st);
+// table of the FP64 entropy logarithm: tab[j] = (log c_j, 1 / c_j), c_j = 1 + (j + 1/2) / 128
+cudaError_t init_log_table(double2* tab, cudaStream_t st);
 
 }  // namespace avl

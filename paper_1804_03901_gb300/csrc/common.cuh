@@ -162,6 +162,32 @@ struct ff {
 
 __device__ __forceinline__ void ff_add(ff& a, float x) { two_sum_add(a.hi, a.lo, x); }
 
+// Natural logarithm of a positive FP64 value by table-driven argument
+// reduction (P. T. P. Tang, "Table-driven implementation of the logarithm
+// function in IEEE floating-point arithmetic", ACM TOMS 16, 1990): with
+// f = 2^e m, m in [1, 2), and c_j = 1 + (j + 1/2) / 128 the centre of the
+// 1/128 interval that holds m, log f = e ln 2 + log c_j + log1p(r), where
+// r = m / c_j - 1 (|r| < 2^-8) and log1p(r) is its Taylor series to r^6
+// (the next term is below 2e-18).  tab[j] = (log c_j, 1 / c_j), filled once
+// per context (init_log_table).  About ten FP64 operations instead of the
+// library logarithm's longer sequence; subnormal f take the library path.
+__device__ __forceinline__ double log_tab(double f, const double2* __restrict__ tab)
+{
+    if (f < 2.2250738585072014e-308) return log(f);
+    const long long b = __double_as_longlong(f);
+    const int e = (int)(b >> 52) - 1023;
+    const int j = (int)((b >> 45) & 127);
+    const double m = __longlong_as_double((b & 0x000FFFFFFFFFFFFFll) | 0x3FF0000000000000ll);
+    const double2 t = __ldg(tab + j);
+    const double r = fma(m, t.y, -1.0);
+    double q = fma(r, -1.0 / 6.0, 0.2);
+    q = fma(r, q, -0.25);
+    q = fma(r, q, 1.0 / 3.0);
+    q = fma(r, q, -0.5);
+    const double lp = fma(r * r, q, r);
+    return fma((double)e, 0.69314718055994530942, t.x + lp);
+}
+
 template <typename T>
 struct ColAcc;
 
@@ -183,11 +209,12 @@ struct ColAcc<float> {
 template <>
 struct ColAcc<double> {
     double rho = 0.0, w = 0.0, ent = 0.0;
+    const double2* logtab = nullptr;
     __device__ __forceinline__ void add(double fh, double, double v2)
     {
         rho += fh;
         w += v2 * fh;
-        if (fh > 0.0) ent += fh * log(fh);
+        if (fh > 0.0) ent += fh * log_tab(fh, logtab);
     }
     __device__ __forceinline__ double r() const { return rho; }
     __device__ __forceinline__ double wk() const { return w; }

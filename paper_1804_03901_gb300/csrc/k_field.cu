@@ -720,4 +720,19 @@ cudaError_t launch_field_batch(const BatchMap* bm, int nrun, int smem, int count
     return cudaGetLastError();
 }
 
+__global__ void k_log_table(double2* tab)
+{
+    const int j = threadIdx.x;
+    if (j < 128) {
+        const double c = 1.0 + ((double)j + 0.5) / 128.0;
+        tab[j] = make_double2(log(c), 1.0 / c);
+    }
+}
+
+cudaError_t init_log_table(double2* tab, cudaStream_t st)
+{
+    k_log_table<<<1, 128, 0, st>>>(tab);
+    return cudaGetLastError();
+}
+
 }  // namespace avl

@@ -984,6 +984,7 @@ __global__ void __launch_bounds__(FIN_THREADS, 4) k_fin1(const StepArgs* __restr
     }
 
     ColAcc<T> acc;
+    if constexpr (sizeof(T) == 8) acc.logtab = A->fd.logtab;
     // overflow rows, f = num / den, f and n stored, charge and diagnostics
     // (FP32: f_ref = the cell's f of the previous reconstruction, read before
     // it is overwritten; the deposit kernel staged the same value)

@@ -80,16 +80,19 @@ __device__ __forceinline__ int dual3(float v, float a, float b, int n, float& w)
     w = t - fl;
     return (int)fl;
 }
+// FP64: floor by one saturating conversion to int (NaN gives 0), the range
+// test in integers, so that the FP64 pipe (the kernel's limit) sees three
+// operations instead of six
 __device__ __forceinline__ int dual3(double v, double a, double b, int n, double& w)
 {
     const double t = __fma_rn(v, a, b);
-    if (!(t > -2.0 && t < (double)n)) {
+    const int fl = __double2int_rd(t);
+    if (fl < -2 || fl >= n) {
         w = 0.0;
-        return t > 0.0 ? n : -2;
+        return fl < 0 ? -2 : n;
     }
-    const double fl = floor(t);
-    w = t - fl;
-    return (int)fl;
+    w = t - (double)fl;
+    return fl;
 }
 
 // coefficients of dual3 for dimension d of a species, in storage precision
@@ -175,13 +178,28 @@ struct Stage3 {
     static constexpr int SLEN = NB + 2 * AL;                 // staged entries per field
 };
 
+// FP64 gather (see k_pd3): count buckets of the columns' pair counts; the
+// gather's column blocks are laid out for eight warps
+constexpr int GBK = 64;
+static_assert(P3_THREADS == 256, "k_pd3's FP64 gather pairs the eight warps of a block by sub-partition");
+
+// FP64: the two row planes of the column accumulators, the column order and
+// the count buckets, after the integer arrays (16-byte aligned)
 template <typename T>
-static size_t pd3_bytes(int nx, int nkey)
+static size_t pd3_acc_offset(int nx, int nkey)
 {
     using S = Stage3<T>;
     size_t b = 2 * (size_t)S::NF * S::SLEN * sizeof(T);      // two staging buffers
     b += sizeof(T) * (7 * (size_t)S::NB + nx);                 // sorted payload, E
     b += 4 * (2 * (size_t)nx + 1) + 4 * ((size_t)nkey + 2) + 64;   // histogram, bin starts, segment row
+    return (b + 15) / 16 * 16;
+}
+
+template <typename T>
+static size_t pd3_bytes(int nx, int nkey)
+{
+    size_t b = pd3_acc_offset<T>(nx, nkey);
+    if (sizeof(T) == 8) b += 2 * 8 * (size_t)nx * sizeof(T) + 4 * (size_t)nx + 8 * (size_t)GBK + 16;
     return (b + 15) / 16 * 16;
 }
 
@@ -317,6 +335,14 @@ __global__ void __launch_bounds__(P3_THREADS, sizeof(T) == 4 ? (CPT == 1 ? 4 : (
     int* hist = reinterpret_cast<int*>(Es + nx);
     int* start = hist + nx;
     int* segs = start + nx + 1;
+    // FP64: column accumulators of rows jseg, jseg + 1 in two planes of 8 x nx
+    // (entry e of column x: plane[e * nx + x]), the columns in order of their
+    // pair counts, the count buckets and their first positions
+    const size_t acc_off = (((size_t)(reinterpret_cast<unsigned char*>(segs + nkey + 2) - smem)) + 15) / 16 * 16;
+    T* RA = reinterpret_cast<T*>(smem + acc_off);
+    int* ordc = reinterpret_cast<int*>(RA + 2 * 8 * nx);
+    int* gbk = ordc + nx;
+    int* gbase = gbk + GBK;
 
     if (threadIdx.x == 0) {
         mbar_init(&bar[0], 1);
@@ -342,6 +368,10 @@ __global__ void __launch_bounds__(P3_THREADS, sizeof(T) == 4 ? (CPT == 1 ? 4 : (
         if (push) Es[i] = sizeof(T) == 4 ? (T)A->fd.E32[i] : (T)A->fd.E64[i];
     }
     for (int i = threadIdx.x; i <= nkey; i += P3_THREADS) segs[i] = segg[i];
+    if constexpr (sizeof(T) == 8) {
+        for (int i = threadIdx.x; i < 2 * 8 * nx; i += P3_THREADS) RA[i] = 0.0;
+        for (int i = threadIdx.x; i < GBK; i += P3_THREADS) gbk[i] = 0;
+    }
     __syncthreads();
 
     // bulk copy of the chunk [b, b + cnt) of every staged field into buffer bf
@@ -391,6 +421,7 @@ __global__ void __launch_bounds__(P3_THREADS, sizeof(T) == 4 ? (CPT == 1 ? 4 : (
     unsigned long long nmov = 0, nfar = 0;
     int buf = 0;
     unsigned ph0 = 0, ph1 = 0;
+    int rp = 0;   // FP64: plane of row jseg (the other holds row jseg + 1)
 
     for (int k = 0; k < nkey; ++k) {
         const int jseg = k - 1;
@@ -503,7 +534,39 @@ __global__ void __launch_bounds__(P3_THREADS, sizeof(T) == 4 ? (CPT == 1 ? 4 : (
 #pragma unroll
                 for (int q = 0; q < 4; ++q) pay[(3 + q) * NB + o] = wq[q];
             }
+            // FP64: pairs (marker, column) of each column = the markers of its
+            // two dual cells; the columns are counting-sorted by that count
+            // so that a warp's lanes loop over nearly equal counts (an FP64
+            // warp instruction costs its sub-partition the same whatever the
+            // number of active lanes)
+            int gb[CPT], grank[CPT];
+            if constexpr (sizeof(T) == 8) {
+#pragma unroll
+                for (int c = 0; c < CPT; ++c) {
+                    const int x = threadIdx.x + c * P3_THREADS;
+                    gb[c] = -1;
+                    if (x >= nx) continue;
+                    const int xm = x == 0 ? nx - 1 : x - 1;
+                    const int cnt = (start[xm + 1] - start[xm]) + (start[x + 1] - start[x]);
+                    gb[c] = min(cnt, GBK - 1);
+                    grank[c] = atomicAdd(&gbk[gb[c]], 1);
+                }
+            }
             __syncthreads();
+            if constexpr (sizeof(T) == 8) {
+                if (threadIdx.x < 32) {   // exclusive scan of the buckets (two per lane)
+                    const int lane = threadIdx.x;
+                    const int a0 = gbk[2 * lane], a1 = gbk[2 * lane + 1];
+                    int incl = a0 + a1;
+#pragma unroll
+                    for (int o = 1; o < 32; o <<= 1) {
+                        const int y = __shfl_up_sync(0xffffffffu, incl, o);
+                        if (lane >= o) incl += y;
+                    }
+                    gbase[2 * lane] = incl - a0 - a1;
+                    gbase[2 * lane + 1] = incl - a1;
+                }
+            }
             // markers off their segment's row: one thread per (marker, corner),
             // so that a chunk's few movers do not hold one warp behind the
             // others at the chunk's barrier
@@ -518,6 +581,63 @@ __global__ void __launch_bounds__(P3_THREADS, sizeof(T) == 4 ? (CPT == 1 ? 4 : (
             // gather: column x takes weight u from the markers of dual cell
             // x - 1 and 1 - u from those of dual cell x, which follow them in
             // the sorted order (one loop; two at the periodic seam)
+            if constexpr (sizeof(T) == 8) {
+                __syncthreads();
+#pragma unroll
+                for (int c = 0; c < CPT; ++c)
+                    if (gb[c] >= 0) ordc[gbase[gb[c]] + grank[c]] = threadIdx.x + c * P3_THREADS;
+                __syncthreads();
+                for (int i = threadIdx.x; i < GBK; i += P3_THREADS) gbk[i] = 0;
+                T* P0 = RA + (size_t)rp * 8 * nx;
+                T* P1 = RA + (size_t)(rp ^ 1) * 8 * nx;
+                // the two warps of an SM sub-partition (warps w and w + 4) take
+                // a light and a heavy block of 32 sorted columns, so that the
+                // sub-partitions' FP64 work is alike
+                const int wp = threadIdx.x >> 5;
+                const int gslot = ((wp < 4 ? wp : 11 - wp) << 5) | (threadIdx.x & 31);
+#pragma unroll
+                for (int c = 0; c < CPT; ++c) {
+                    const int idx = gslot + c * P3_THREADS;
+                    if (idx >= nx) continue;
+                    const int x = ordc[idx];
+                    const int xm = x == 0 ? nx - 1 : x - 1;
+                    const int mid = start[x];
+                    const int lo0 = start[xm], hi0 = x == 0 ? start[nx] : mid;
+                    const int hi1 = start[x + 1];
+                    if (lo0 == hi0 && mid == hi1) continue;   // no pairs (x == 0: lo0 <= hi0 = start[nx])
+                    T A0[8], A1[8];
+#pragma unroll
+                    for (int e = 0; e < 8; ++e) {
+                        A0[e] = P0[e * nx + x];
+                        A1[e] = P1[e * nx + x];
+                    }
+                    for (int pass = 0; pass < (x == 0 ? 2 : 1); ++pass) {
+                        const int lo = pass ? mid : lo0, hi = (x == 0 && !pass) ? hi0 : hi1;
+                        for (int i = lo; i < hi; ++i) {
+                            const T u = pay[i];
+                            const bool upper = x == 0 ? pass == 0 : i < mid;
+                            const T ax = upper ? u : (T)1 - u;
+                            const T a1 = ax * pay[NB + i];
+                            const T a0 = ax - a1;
+                            const T f = pay[2 * NB + i];
+                            const T f0 = a0 * f, f1 = a1 * f;
+#pragma unroll
+                            for (int q = 0; q < 4; ++q) {
+                                const T wqv = pay[(3 + q) * NB + i];
+                                A0[2 * q] += f0 * wqv;
+                                A0[2 * q + 1] += a0 * wqv;
+                                A1[2 * q] += f1 * wqv;
+                                A1[2 * q + 1] += a1 * wqv;
+                            }
+                        }
+                    }
+#pragma unroll
+                    for (int e = 0; e < 8; ++e) {
+                        P0[e * nx + x] = A0[e];
+                        P1[e * nx + x] = A1[e];
+                    }
+                }
+            } else
 #pragma unroll
             for (int c = 0; c < CPT; ++c) {
                 const int x = threadIdx.x + c * P3_THREADS;
@@ -550,6 +670,31 @@ __global__ void __launch_bounds__(P3_THREADS, sizeof(T) == 4 ? (CPT == 1 ? 4 : (
             __syncthreads();
             buf ^= 1;
         }
+        if constexpr (sizeof(T) == 8) {
+            // row jseg is complete (the next segment reaches rows jseg + 1 and
+            // jseg + 2): its plane into the global accumulator and cleared,
+            // then the planes swap
+            T* P0 = RA + (size_t)rp * 8 * nx;
+#pragma unroll
+            for (int c = 0; c < CPT; ++c) {
+                const int x = threadIdx.x + c * P3_THREADS;
+                if (x >= nx) continue;
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const T vn = P0[(2 * q) * nx + x], vd = P0[(2 * q + 1) * nx + x];
+                    if (jseg >= 0 && jseg < nvx && pl.ok[q] && vd != (T)0) {
+                        const int o = pl.base[q] + jseg * nx + x;
+                        atomicAdd(gacc + o, vn);
+                        atomicAdd(gacc + cells + o, vd);
+                    }
+                    P0[(2 * q) * nx + x] = (T)0;
+                    P0[(2 * q + 1) * nx + x] = (T)0;
+                }
+            }
+            rp ^= 1;
+            __syncthreads();
+            continue;
+        }
         // row jseg - 1 is complete (no later segment reaches it): registers into
         // the global accumulator; then rotate the rows
         const int row = jseg - 1;
@@ -580,7 +725,7 @@ __global__ void __launch_bounds__(P3_THREADS, sizeof(T) == 4 ? (CPT == 1 ? 4 : (
         __syncthreads();
     }
     // the last row (nvx - 1) after the last segment
-    {
+    if constexpr (sizeof(T) == 4) {
         const int row = nvx - 1;
 #pragma unroll
         for (int c = 0; c < CPT; ++c) {
@@ -638,6 +783,7 @@ __global__ void __launch_bounds__(FIN3_X * FIN3_R) k_fin3(const StepArgs* __rest
     T* fg = reinterpret_cast<T*>(sp.fgrid);
     const T* v2 = reinterpret_cast<const T*>(sp.v2row);
     ColAcc<T> acc;
+    if constexpr (sizeof(T) == 8) acc.logtab = A->fd.logtab;
     auto cell = [&](int j, T nn, T dd, T v2j) {
         const size_t o = (size_t)j * nx + x;
         const T f = dd > (T)0 ? nn / dd : (T)0;

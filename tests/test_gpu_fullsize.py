@@ -66,16 +66,24 @@ def build_pair(A, w):
     return sim, orc
 
 
+def _fp64(w):
+    w["precision"] = "fp64"
+    return w
+
+
 @pytest.mark.parametrize("name,steps", [("two_stream", 20), ("two_stream_driven", 20), ("bump_on_tail", 4),
-                                        ("bernstein", 4)])
+                                        ("bump_on_tail_fp64", 4), ("bernstein", 4)])
 def test_full_size_parity(A, name, steps):
     """two_stream: 2 x 8388608 markers on 512 x 1024 cells (FP32 1d1v);
     two_stream_driven: the same with 5e-2 perturbations, so that the markers
     leave their deposit windows and the layout re-sorts; bump_on_tail and
     bernstein: 134217728 markers on 256 x 64^3 cells (FP32 1d3v, the latter
-    with the Boris push and the global re-sort of every step)."""
+    with the Boris push and the global re-sort of every step);
+    bump_on_tail_fp64: the benchmark's FP64 form of bump_on_tail (tolerance
+    1e-10)."""
     w = {"two_stream": inputs.two_stream, "two_stream_driven": lambda: inputs.two_stream(amp=5e-2),
-         "bump_on_tail": inputs.bump_on_tail, "bernstein": inputs.bernstein}[name]()
+         "bump_on_tail": inputs.bump_on_tail, "bump_on_tail_fp64": lambda: _fp64(inputs.bump_on_tail()),
+         "bernstein": inputs.bernstein}[name]()
     sim, orc = build_pair(A, w)
     sim.step(steps)
     sync_oracle_to_gpu(sim, orc)
