@@ -98,3 +98,21 @@ def test_full_size_parity(A, name, steps):
     if name == "bernstein":
         assert st[0, 1] == steps + 1, st
     sim.close()
+
+
+def test_paper_landau_run_parity_at_production_size(A):
+    """The paper's own Landau run (Sec. 4.2: k = 0.4, L = 5 pi, nx = 512,
+    nv = 6600 on [-10, 10], alpha = 0.05, dt = 0.1, FP64, 2 x 2 markers per
+    cell: 13516800 markers), whose deposit window does not fit in shared
+    memory at the default chunk size, so the layout planner halves the
+    chunks.  After 10 steps the oracle rebuilds every grid from the GPU's
+    markers; then both take one step; f, n, rho and E agree within 1e-10."""
+    w = inputs.landau_paper()
+    sim, orc = build_pair(A, w)
+    sim.step(10)
+    sync_oracle_to_gpu(sim, orc)
+    compare_grids(sim, orc, 1e-10, "landau_paper after 10 steps")
+    sim.step(1)
+    orc.step(1)
+    compare_grids(sim, orc, 1e-10, "landau_paper step 11")
+    sim.close()
