@@ -279,6 +279,8 @@ avl_status plan_layout3(avl_ctx* c, int s, long long n)
         }
         for (int d = 0; d < 3 && !e; ++d) e = grab(&sp.mv[b][d], pb * nn, true);
         if (!e) e = grab(&sp.mf[b], pb * nn, true);
+        sp.mwq[b] = nullptr;
+        if (!e && c->h.prec == AVL_FP64) e = grab(&sp.mwq[b], 4 * pb * nn, true);
         void* sg = nullptr;
         if (!e) e = grab(&sg, (size_t)npen * (nkey + 1) * 4, true);
         sp.seg[b] = (int*)sg;

@@ -87,6 +87,8 @@ struct SpDev {
     float* moff[2];            // FP32 only
     void* mv[2][3];            // velocity components (vx chunk-relative)
     void* mf[2];
+    void* mwq[2];              // FP64 1d3v: [n][4] weights of the marker's four (v_y, v_z) cells (the
+                               // pencil's planes; 0 when the footprint misses the grid), per buffer
     int* KB[2];                // [nchunk] reference key of each chunk, per buffer
     // re-sort tables; cnt / far_cnt are double-buffered: [hsel] holds the key
     // counts of the current state, [1 - hsel] collects those of the next

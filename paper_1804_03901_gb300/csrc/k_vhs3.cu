@@ -173,7 +173,11 @@ __device__ void block_exscan(const int* in, int* out, int n, int items, int* wsu
 template <typename T>
 struct Stage3 {
     static constexpr int NB = P3_THREADS * Cfg3<T>::MPT;   // markers per chunk
-    static constexpr int NF = sizeof(T) == 4 ? 6 : 5;       // staged fields
+    // staged fields: FP32 cell, offset, v_x, v_y, v_z, f; FP64 x, v_x, f (the
+    // weights of the (v_y, v_z) cells are stored beside the marker)
+    static constexpr int NF = sizeof(T) == 4 ? 6 : 3;
+    static constexpr int FVX = sizeof(T) == 4 ? 2 : 1;       // staged field of v_x
+    static constexpr int FF = NF - 1;                         // staged field of f
     static constexpr int AL = 16 / (int)sizeof(T);           // markers per 16 bytes
     static constexpr int SLEN = NB + 2 * AL;                 // staged entries per field
 };
@@ -228,6 +232,30 @@ __device__ __forceinline__ void plane_weights(T wy, T wz, T (&q)[4])
     q[3] = wy * wz;
 }
 
+// FP64: the weights of a marker's four (v_y, v_z) cells, stored beside the
+// marker (they change only when a magnetic field turns v): the plane weights
+// of its dual cells, or 0 when its footprint misses the grid in v_y or v_z
+// (such a marker sits in a clamped pencil and deposits nothing)
+template <typename T>
+__device__ __forceinline__ void marker_planes(const VCoef<T>& vc, T vy, T vz, T (&wq)[4])
+{
+    T wy, wz;
+    const int jy = dual3(vy, vc.a[1], vc.b[1], vc.n[1], wy);
+    const int jz = dual3(vz, vc.a[2], vc.b[2], vc.n[2], wz);
+    if (jy < -1 || jy >= vc.n[1] || jz < -1 || jz >= vc.n[2]) {
+        wq[0] = wq[1] = wq[2] = wq[3] = (T)0;
+        return;
+    }
+    plane_weights(wy, wz, wq);
+}
+
+__device__ __forceinline__ void store_planes(void* mwq, long long k, const double (&wq)[4])
+{
+    double2* p = reinterpret_cast<double2*>(mwq) + 2 * k;
+    p[0] = make_double2(wq[0], wq[1]);
+    p[1] = make_double2(wq[2], wq[3]);
+}
+
 // the pencil's four (v_y, v_z) planes: first grid offset of each (row 0,
 // column 0) and whether it lies on the grid
 struct Planes {
@@ -240,8 +268,8 @@ struct Planes {
 // global accumulator.  This is one of them: corner bits x (bit 0), v_x row
 // (bit 1), (v_y, v_z) plane (bits 2-3).
 template <typename T>
-__device__ __forceinline__ void deposit_corner(T* gacc, int cells, const Planes& pl, int nx, int nvx, int bin, T u,
-                                               int j, T w, T wy, T wz, T f, int corner)
+__device__ __forceinline__ void deposit_corner_q(T* gacc, int cells, const Planes& pl, int nx, int nvx, int bin, T u,
+                                                 int j, T w, T wqv, T f, int corner)
 {
     const int cx = corner & 1, cv = (corner >> 1) & 1, q = corner >> 2;
     const bool okq = q == 0 ? pl.ok[0] : q == 1 ? pl.ok[1] : q == 2 ? pl.ok[2] : pl.ok[3];
@@ -249,13 +277,22 @@ __device__ __forceinline__ void deposit_corner(T* gacc, int cells, const Planes&
     if (!okq || row < 0 || row >= nvx) return;
     const int x = cx ? (bin + 1 == nx ? 0 : bin + 1) : bin;
     const T ax = cx ? u : (T)1 - u;
-    const T ay = (q & 1) ? wy : (T)1 - wy, az = (q & 2) ? wz : (T)1 - wz;
-    const T a = ax * (cv ? w : (T)1 - w) * (ay * az);
+    const T a = ax * (cv ? w : (T)1 - w) * wqv;
     if (a == (T)0) return;
     const int base = q == 0 ? pl.base[0] : q == 1 ? pl.base[1] : q == 2 ? pl.base[2] : pl.base[3];
     const int o = base + row * nx + x;
     atomicAdd(gacc + o, a * f);
     atomicAdd(gacc + cells + o, a);
+}
+
+// FP32: the plane weight from the marker's (v_y, v_z) cell weights
+template <typename T>
+__device__ __forceinline__ void deposit_corner(T* gacc, int cells, const Planes& pl, int nx, int nvx, int bin, T u,
+                                               int j, T w, T wy, T wz, T f, int corner)
+{
+    const int q = corner >> 2;
+    const T ay = (q & 1) ? wy : (T)1 - wy, az = (q & 2) ? wz : (T)1 - wz;
+    deposit_corner_q<T>(gacc, cells, pl, nx, nvx, bin, u, j, w, ay * az, f, corner);
 }
 
 // exclusive scan of hist[0, nx) into start[0, nx], start[nx] = total; each
@@ -304,7 +341,7 @@ __global__ void __launch_bounds__(P3_THREADS, sizeof(T) == 4 ? (CPT == 1 ? 4 : (
     using S = Stage3<T>;
     constexpr int MPT = Cfg3<T>::MPT;
     constexpr int NB = S::NB, NF = S::NF, AL = S::AL, SLEN = S::SLEN;
-    constexpr int FX = NF - 4;   // staged field of v_x (then v_y, v_z, f)
+    constexpr int FVX = S::FVX, FF = S::FF;   // staged fields of v_x and f (FP32: v_y, v_z between)
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ uint64_t bar[2];
     __shared__ int wsum[P3_THREADS / 32];
@@ -358,10 +395,12 @@ __global__ void __launch_bounds__(P3_THREADS, sizeof(T) == 4 ? (CPT == 1 ? 4 : (
         } else {
             src_s[0] = sp.mx[cb];
         }
-        src_s[FX + 0] = sp.mv[cb][0];
-        src_s[FX + 1] = sp.mv[cb][1];
-        src_s[FX + 2] = sp.mv[cb][2];
-        src_s[FX + 3] = sp.mf[cb];
+        src_s[FVX] = sp.mv[cb][0];
+        if constexpr (sizeof(T) == 4) {
+            src_s[FVX + 1] = sp.mv[cb][1];
+            src_s[FVX + 2] = sp.mv[cb][2];
+        }
+        src_s[FF] = sp.mf[cb];
     }
     for (int i = threadIdx.x; i < nx; i += P3_THREADS) {
         hist[i] = 0;
@@ -435,6 +474,21 @@ __global__ void __launch_bounds__(P3_THREADS, sizeof(T) == 4 ? (CPT == 1 ? 4 : (
                 if (nb >= send) nk = first_from(k + 1, nb);
                 if (nk < nkey) issue(buf ^ 1, nb, min(NB, segs[nk + 1] - nb));
             }
+            // FP64: the stored (v_y, v_z) cell weights of this chunk's markers,
+            // loaded while its staged fields are in flight
+            double2 qlo[MPT], qhi[MPT];
+            if constexpr (sizeof(T) == 8) {
+                const double2* wqg = reinterpret_cast<const double2*>(sp.mwq[cb]);
+#pragma unroll
+                for (int m = 0; m < MPT; ++m) {
+                    const int i = m * P3_THREADS + threadIdx.x;
+                    qlo[m] = qhi[m] = make_double2(0.0, 0.0);
+                    if (i < cnt) {
+                        qlo[m] = wqg[2 * (long long)(b0 + i)];
+                        qhi[m] = wqg[2 * (long long)(b0 + i) + 1];
+                    }
+                }
+            }
             const unsigned ph = buf ? ph1 : ph0;
             if (!mbar_wait_or_drain(&bar[buf], ph, wait_first, WAIT_LIMIT)) flag_s = 1;
             if (buf) ph1 ^= 1u; else ph0 ^= 1u;
@@ -458,7 +512,7 @@ __global__ void __launch_bounds__(P3_THREADS, sizeof(T) == 4 ? (CPT == 1 ? 4 : (
                 } else {
                     pos.xi = st[si];
                 }
-                T vx = st[(FX + 0) * SLEN + si];
+                T vx = st[FVX * SLEN + si];
                 if (push) {
                     int i0;
                     T wx;
@@ -476,14 +530,16 @@ __global__ void __launch_bounds__(P3_THREADS, sizeof(T) == 4 ? (CPT == 1 ? 4 : (
                     }
                     gvx[idx] = vx;
                 }
-                const T f = st[(FX + 3) * SLEN + si];
-                T wy, wz, w;
-                const int jy = dual3(st[(FX + 1) * SLEN + si], vc.a[1], vc.b[1], vc.n[1], wy);
-                const int jz = dual3(st[(FX + 2) * SLEN + si], vc.a[2], vc.b[2], vc.n[2], wz);
-                if (jy != pjy || jz != pjz) {
-                    // outside the pencil only when the footprint misses the grid
-                    if (jy >= -1 && jy < nvy && jz >= -1 && jz < nvz) flag_s |= 2;
-                    continue;
+                const T f = st[FF * SLEN + si];
+                T wy = (T)0, wz = (T)0, w;
+                if constexpr (sizeof(T) == 4) {
+                    const int jy = dual3(st[(FVX + 1) * SLEN + si], vc.a[1], vc.b[1], vc.n[1], wy);
+                    const int jz = dual3(st[(FVX + 2) * SLEN + si], vc.a[2], vc.b[2], vc.n[2], wz);
+                    if (jy != pjy || jz != pjz) {
+                        // outside the pencil only when the footprint misses the grid
+                        if (jy >= -1 && jy < nvy && jz >= -1 && jz < nvz) flag_s |= 2;
+                        continue;
+                    }
                 }
                 const int jx = dual3(vx, vc.a[0], vc.b[0], nvx, w);
                 if (jx < -1 || jx >= nvx) continue;
@@ -505,8 +561,12 @@ __global__ void __launch_bounds__(P3_THREADS, sizeof(T) == 4 ? (CPT == 1 ? 4 : (
                     pay[0 * NB + o] = u;
                     pay[1 * NB + o] = w;
                     pay[2 * NB + o] = f;
-                    pay[3 * NB + o] = wy;
-                    pay[4 * NB + o] = wz;
+                    if constexpr (sizeof(T) == 4) {
+                        pay[3 * NB + o] = wy;
+                        pay[4 * NB + o] = wz;
+                    } else {
+                        pay[3 * NB + o] = (T)idx;   // FP64: its stored cell weights are read by index
+                    }
                     pay[5 * NB + o] = (T)bin;
                     pay[6 * NB + o] = (T)jx;
                 }
@@ -527,7 +587,14 @@ __global__ void __launch_bounds__(P3_THREADS, sizeof(T) == 4 ? (CPT == 1 ? 4 : (
                 if (prank[m] < 0) continue;
                 const int o = start[pbin[m]] + prank[m];
                 T wq[4];
-                plane_weights(py[m], pz[m], wq);
+                if constexpr (sizeof(T) == 4) {
+                    plane_weights(py[m], pz[m], wq);
+                } else {
+                    wq[0] = qlo[m].x;
+                    wq[1] = qlo[m].y;
+                    wq[2] = qhi[m].x;
+                    wq[3] = qhi[m].y;
+                }
                 pay[0 * NB + o] = pu[m];
                 pay[1 * NB + o] = pw[m];
                 pay[2 * NB + o] = pf[m];
@@ -573,10 +640,15 @@ __global__ void __launch_bounds__(P3_THREADS, sizeof(T) == 4 ? (CPT == 1 ? 4 : (
             for (int t = threadIdx.x; t < nmv * 16; t += P3_THREADS) {
                 const int o = NB - 1 - (t >> 4);
                 const int jx = (int)pay[6 * NB + o];
-                const int d = jx - jseg;
-                deposit_corner<T>(gacc, cells, pl, nx, nvx, (int)pay[5 * NB + o],
-                                  pay[0 * NB + o], jx, pay[1 * NB + o], pay[3 * NB + o], pay[4 * NB + o],
-                                  pay[2 * NB + o], t & 15);
+                if constexpr (sizeof(T) == 4) {
+                    deposit_corner<T>(gacc, cells, pl, nx, nvx, (int)pay[5 * NB + o], pay[0 * NB + o], jx,
+                                      pay[1 * NB + o], pay[3 * NB + o], pay[4 * NB + o], pay[2 * NB + o], t & 15);
+                } else {
+                    const long long mi = (long long)pay[3 * NB + o];
+                    const T wqv = reinterpret_cast<const double*>(sp.mwq[cb])[4 * mi + ((t & 15) >> 2)];
+                    deposit_corner_q<T>(gacc, cells, pl, nx, nvx, (int)pay[5 * NB + o], pay[0 * NB + o], jx,
+                                        pay[1 * NB + o], wqv, pay[2 * NB + o], t & 15);
+                }
             }
             // gather: column x takes weight u from the markers of dual cell
             // x - 1 and 1 - u from those of dual cell x, which follow them in
@@ -908,6 +980,12 @@ __global__ void __launch_bounds__(P3_THREADS) k_sort3(const StepArgs* __restrict
             reinterpret_cast<T*>(sp.mv[dst][1])[slot] = reinterpret_cast<const T*>(sp.mv[src][1])[k];
             reinterpret_cast<T*>(sp.mv[dst][2])[slot] = reinterpret_cast<const T*>(sp.mv[src][2])[k];
             reinterpret_cast<T*>(sp.mf[dst])[slot] = reinterpret_cast<const T*>(sp.mf[src])[k];
+            if constexpr (sizeof(T) == 8) {
+                const double2* ps = reinterpret_cast<const double2*>(sp.mwq[src]) + 2 * (long long)k;
+                double2* pd = reinterpret_cast<double2*>(sp.mwq[dst]) + 2 * (long long)slot;
+                pd[0] = ps[0];
+                pd[1] = ps[1];
+            }
         }
     }
 }
@@ -1134,6 +1212,11 @@ __global__ void __launch_bounds__(256) k_src3_scatter(const StepArgs* __restrict
         pos.store(sp, 0, slot);
         for (int d = 0; d < 3; ++d) reinterpret_cast<T*>(sp.mv[0][d])[slot] = v[d];
         reinterpret_cast<T*>(sp.mf[0])[slot] = (T)mk.f;
+        if constexpr (sizeof(T) == 8) {
+            double wq[4];
+            marker_planes<double>(vc, v[1], v[2], wq);
+            store_planes(sp.mwq[0], slot, wq);
+        }
     }
     if (over) atomicOr(&A->ctl->err, ERR_CAPACITY);
 }
@@ -1274,6 +1357,11 @@ __global__ void __launch_bounds__(256) k_rs3_scatter(const StepArgs* __restrict_
             pos[r].store(sp, dst, slot);
             for (int d = 0; d < 3; ++d) reinterpret_cast<T*>(sp.mv[dst][d])[slot] = v[r][d];
             reinterpret_cast<T*>(sp.mf[dst])[slot] = fv[r];
+            if constexpr (sizeof(T) == 8) {
+                double wq[4];
+                marker_planes<double>(vc, v[r][1], v[r][2], wq);
+                store_planes(sp.mwq[dst], slot, wq);
+            }
         }
     }
     if (over) atomicOr(&A->ctl->err, ERR_CAPACITY);
