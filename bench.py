@@ -367,10 +367,11 @@ def run_reference(args):
 
 
 # FP64 floating-point operations per marker of the 1d3v push + deposit k_pd3
-# (an FMA counts 2; see fp64_flops_3d)
+# (an FMA counts 2; the weights of the marker's (v_y, v_z) cells are stored
+# beside it and not recomputed per step)
 def fp64_flops_3d():
     push = 2 + 4 + 2 + 2          # CIC weight of x, field gather, kick, drift
-    weights = 3 * 3 + 2 + 6       # dual rows and weights of v_x, v_y, v_z; new x weight; four (v_y, v_z) weights
+    weights = 2 + 3               # new CIC weight of x; dual row and weight of v_x
     gather = 2 * (5 + 16 * 2)     # per column of the marker (two): ax, a1, a0, a0 f, a1 f; 16 FMAs into the rows
     return float(push + weights + gather)
 

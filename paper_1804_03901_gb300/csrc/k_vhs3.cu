@@ -178,6 +178,10 @@ struct Stage3 {
     static constexpr int NF = sizeof(T) == 4 ? 6 : 3;
     static constexpr int FVX = sizeof(T) == 4 ? 2 : 1;       // staged field of v_x
     static constexpr int FF = NF - 1;                         // staged field of f
+    // the balanced gather (column accumulators in shared-memory row planes,
+    // columns sorted by their pair counts): the FP64 form, whose instructions
+    // cost an SM sub-partition the same whatever their active lanes
+    static constexpr bool BAL = sizeof(T) == 8;
     static constexpr int AL = 16 / (int)sizeof(T);           // markers per 16 bytes
     static constexpr int SLEN = NB + 2 * AL;                 // staged entries per field
 };
@@ -203,7 +207,7 @@ template <typename T>
 static size_t pd3_bytes(int nx, int nkey)
 {
     size_t b = pd3_acc_offset<T>(nx, nkey);
-    if (sizeof(T) == 8) b += 2 * 8 * (size_t)nx * sizeof(T) + 4 * (size_t)nx + 8 * (size_t)GBK + 16;
+    if (Stage3<T>::BAL) b += 2 * 8 * (size_t)nx * sizeof(T) + 4 * (size_t)nx + 8 * (size_t)GBK + 16;
     return (b + 15) / 16 * 16;
 }
 
@@ -407,7 +411,7 @@ __global__ void __launch_bounds__(P3_THREADS, sizeof(T) == 4 ? (CPT == 1 ? 4 : (
         if (push) Es[i] = sizeof(T) == 4 ? (T)A->fd.E32[i] : (T)A->fd.E64[i];
     }
     for (int i = threadIdx.x; i <= nkey; i += P3_THREADS) segs[i] = segg[i];
-    if constexpr (sizeof(T) == 8) {
+    if constexpr (S::BAL) {
         for (int i = threadIdx.x; i < 2 * 8 * nx; i += P3_THREADS) RA[i] = 0.0;
         for (int i = threadIdx.x; i < GBK; i += P3_THREADS) gbk[i] = 0;
     }
@@ -607,7 +611,7 @@ __global__ void __launch_bounds__(P3_THREADS, sizeof(T) == 4 ? (CPT == 1 ? 4 : (
             // warp instruction costs its sub-partition the same whatever the
             // number of active lanes)
             int gb[CPT], grank[CPT];
-            if constexpr (sizeof(T) == 8) {
+            if constexpr (S::BAL) {
 #pragma unroll
                 for (int c = 0; c < CPT; ++c) {
                     const int x = threadIdx.x + c * P3_THREADS;
@@ -620,7 +624,7 @@ __global__ void __launch_bounds__(P3_THREADS, sizeof(T) == 4 ? (CPT == 1 ? 4 : (
                 }
             }
             __syncthreads();
-            if constexpr (sizeof(T) == 8) {
+            if constexpr (S::BAL) {
                 if (threadIdx.x < 32) {   // exclusive scan of the buckets (two per lane)
                     const int lane = threadIdx.x;
                     const int a0 = gbk[2 * lane], a1 = gbk[2 * lane + 1];
@@ -653,7 +657,7 @@ __global__ void __launch_bounds__(P3_THREADS, sizeof(T) == 4 ? (CPT == 1 ? 4 : (
             // gather: column x takes weight u from the markers of dual cell
             // x - 1 and 1 - u from those of dual cell x, which follow them in
             // the sorted order (one loop; two at the periodic seam)
-            if constexpr (sizeof(T) == 8) {
+            if constexpr (S::BAL) {
                 __syncthreads();
 #pragma unroll
                 for (int c = 0; c < CPT; ++c)
@@ -742,7 +746,7 @@ __global__ void __launch_bounds__(P3_THREADS, sizeof(T) == 4 ? (CPT == 1 ? 4 : (
             __syncthreads();
             buf ^= 1;
         }
-        if constexpr (sizeof(T) == 8) {
+        if constexpr (S::BAL) {
             // row jseg is complete (the next segment reaches rows jseg + 1 and
             // jseg + 2): its plane into the global accumulator and cleared,
             // then the planes swap
@@ -797,7 +801,7 @@ __global__ void __launch_bounds__(P3_THREADS, sizeof(T) == 4 ? (CPT == 1 ? 4 : (
         __syncthreads();
     }
     // the last row (nvx - 1) after the last segment
-    if constexpr (sizeof(T) == 4) {
+    if constexpr (!S::BAL) {
         const int row = nvx - 1;
 #pragma unroll
         for (int c = 0; c < CPT; ++c) {
