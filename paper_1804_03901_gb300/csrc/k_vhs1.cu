@@ -528,10 +528,11 @@ __global__ void __launch_bounds__(PD_THREADS) k_rs1(const StepArgs* __restrict__
 // same footprint summed in registers first) and written back in place, and
 // its new key is counted into cnt[1 - hsel] for the next step.  On a re-sort
 // step the markers are read from the buffer k_rs1 has just written.
-template <typename T, bool BATCH>
-__global__ void __launch_bounds__(PD_THREADS, 2) k_pd1(const StepArgs* __restrict__ A0, int mode,
+template <typename T, bool BATCH, bool PUSH>
+__global__ void __launch_bounds__(PD_THREADS, 2) k_pd1(const StepArgs* __restrict__ A0,
                                                        const BatchMap* __restrict__ bm)
 {
+    constexpr int mode = PUSH ? 1 : 0;
     extern __shared__ __align__(128) unsigned char smem[];
     int g = blockIdx.x;
     const StepArgs* __restrict__ A = A0;
@@ -667,9 +668,8 @@ __global__ void __launch_bounds__(PD_THREADS, 2) k_pd1(const StepArgs* __restric
         Run<T> run;
         run.reset(0x7fffffff, 0);
         bool have = false;
-#pragma unroll
-        for (int m = 0; m < MPT; ++m) {
-            const bool okm = g0 + m < end;
+        // one marker of the thread's group: push, footprint, run, key count
+        auto one = [&](int m, bool okm) __attribute__((always_inline)) {
             int code = 0;
             if (okm) {
                 Pos<T>& pos = pos8[m];
@@ -715,7 +715,9 @@ __global__ void __launch_bounds__(PD_THREADS, 2) k_pd1(const StepArgs* __restric
             }
             // the new key counted for this chunk (next step's window)
             if (push) hist_add(scnt, far_next, code, okm);
-        }
+        };
+#pragma unroll
+        for (int m = 0; m < MPT; ++m) one(m, g0 + m < end);
         if (have)
             n_over += flush_run<T>(run, win, plane, row0, W, nx, nv, shs, fref, ovf_num, ovf_den, ovf_tag, tag) ? 1u
                                                                                                                 : 0u;
@@ -1302,9 +1304,15 @@ cudaError_t launch_pd1_batch(int prec, const BatchMap* bm, int blocks, int smem,
 {
     if (blocks == 0) return cudaSuccess;
     if (prec == AVL_FP32) {
-        k_pd1<float, true><<<blocks, PD_THREADS, smem, st>>>(nullptr, mode, bm);
+        if (mode == 1)
+            k_pd1<float, true, true><<<blocks, PD_THREADS, smem, st>>>(nullptr, bm);
+        else
+            k_pd1<float, true, false><<<blocks, PD_THREADS, smem, st>>>(nullptr, bm);
     } else {
-        k_pd1<double, true><<<blocks, PD_THREADS, smem, st>>>(nullptr, mode, bm);
+        if (mode == 1)
+            k_pd1<double, true, true><<<blocks, PD_THREADS, smem, st>>>(nullptr, bm);
+        else
+            k_pd1<double, true, false><<<blocks, PD_THREADS, smem, st>>>(nullptr, bm);
     }
     return cudaGetLastError();
 }
@@ -1345,8 +1353,10 @@ template <typename T>
 static cudaError_t set_pd1_limit_t(int smem)
 {
     cudaError_t e;
-    if ((e = raise_smem_limit(k_pd1<T, false>, smem))) return e;
-    return raise_smem_limit(k_pd1<T, true>, smem);
+    if ((e = raise_smem_limit(k_pd1<T, false, false>, smem))) return e;
+    if ((e = raise_smem_limit(k_pd1<T, false, true>, smem))) return e;
+    if ((e = raise_smem_limit(k_pd1<T, true, false>, smem))) return e;
+    return raise_smem_limit(k_pd1<T, true, true>, smem);
 }
 
 static cudaError_t set_pd1_limit(int prec, int smem)
@@ -1378,9 +1388,15 @@ cudaError_t launch_pd1(const StepArgs& h, const StepArgs* d, int mode, cudaStrea
     if (h.nchunk_total == 0) return cudaSuccess;
     const int smem = max_pd_smem(h);
     if (h.prec == AVL_FP32) {
-        k_pd1<float, false><<<h.nchunk_total, PD_THREADS, smem, st>>>(d, mode, nullptr);
+        if (mode == 1)
+            k_pd1<float, false, true><<<h.nchunk_total, PD_THREADS, smem, st>>>(d, nullptr);
+        else
+            k_pd1<float, false, false><<<h.nchunk_total, PD_THREADS, smem, st>>>(d, nullptr);
     } else {
-        k_pd1<double, false><<<h.nchunk_total, PD_THREADS, smem, st>>>(d, mode, nullptr);
+        if (mode == 1)
+            k_pd1<double, false, true><<<h.nchunk_total, PD_THREADS, smem, st>>>(d, nullptr);
+        else
+            k_pd1<double, false, false><<<h.nchunk_total, PD_THREADS, smem, st>>>(d, nullptr);
     }
     return cudaGetLastError();
 }
