@@ -81,12 +81,15 @@ SPECIES2 = lambda nv: [dict(q=-1.0, m=1.0, nv=(nv,), vmin=(-3.0,), vmax=(3.0,)),
 
 @pytest.mark.parametrize("prec", [0, 1], ids=["fp64", "fp32"])
 @pytest.mark.parametrize("nx,nv,n,chunk", [(64, 96, 20011, 1024), (48, 40, 5003, 640), (64, 96, 20011, 0),
-                                            (4, 2, 7, 0), (32, 64, 30000, 64)])
+                                            (4, 2, 7, 0), (32, 64, 30000, 64), (15, 24, 3001, 0),
+                                            (13, 30, 5003, 256)])
 def test_step_parity_random_markers(A, monkeypatch, prec, nx, nv, n, chunk):
     """Random marker states (some beyond the velocity grid, values over 12
     decades), many chunks and a ragged last chunk, power-of-two (FFT) and
-    other (DFT) grids; one set + refresh and three steps (each re-sorting the
-    markers), each compared from identical states."""
+    other (DFT) grids, odd nx (deposit windows of an odd number of cells,
+    padded to 16-byte bulk copies; E staged without the bulk copy); one set +
+    refresh and three steps (each re-sorting the markers), each compared from
+    identical states."""
     if chunk:
         monkeypatch.setenv("AVL_CHUNK_M", str(chunk))
     L, dt = 7.3, 0.07
