@@ -190,3 +190,58 @@ def test_adjoint_matches_oracle_at_config4_size(A, prec):
     tolJ, tolg = (1e-10, 1e-8) if prec == 0 else (2e-3, 2e-3)
     assert errJ < tolJ
     assert errg < tolg
+
+
+def test_adjoint_matches_finite_differences_at_config4_size(A):
+    """The two-stream adjoint workload at full size (1048576 electrons,
+    nx = 256, nv = 512, 16 mode amplitudes and 2 beam drifts): the FP64
+    adjoint against central differences of the library's FP64 forward run
+    at h = 1e-10, over 100 steps (linear phase) and the full 500 steps
+    (T = 25, checkpoints every 50).  The differences carry an O(h) error of
+    their own from markers crossing cloud-in-cell kinks (it sets the 1e-5
+    disagreement at h = 1e-6) and a roundoff error O(eps J / h) that takes
+    over below h = 1e-10.  Measured: 1.6e-7 (100 steps) and 1.0e-6
+    (500 steps) relative to the largest component."""
+    from paper_1804_03901_gb300 import inputs
+    w = inputs.two_stream_adjoint()
+    f0 = w["f0"][0]
+
+    def sim_of(f0e):
+        dom = A.make_domain(1, w["nx"], w["L"], w["dt"], 1.0, True, A.AVL_FP64)
+        sim = A.Simulation(dom, [A.make_species(**sp) for sp in w["species"]])
+        for s, (ff, lat) in enumerate(zip([f0e] + w["f0"][1:], w["lattice"])):
+            sim.init_markers(s, lat, A.make_f0(ff["beams"], ff["modes"]), w["seed"], w["jitter"])
+        return sim
+
+    amps = [a for (_, a, _) in f0["modes"]]
+    drifts = [u[0] for (_, u, _) in f0["beams"]]
+
+    def J_of(a, d, n):
+        f0e = {"beams": [(nb, (d[b],) + tuple(u[1:]), vth) for b, (nb, u, vth) in enumerate(f0["beams"])],
+               "modes": [(m, a[k], ph) for k, (m, _, ph) in enumerate(f0["modes"])]}
+        sim = sim_of(f0e)
+        sim.step(n)
+        E = sim.get_E()
+        sim.close()
+        return 0.5 * float(np.sum(E ** 2)) * (w["L"] / w["nx"])
+
+    h = 1e-10
+    for n, tol in ((100, 1e-6), (500, 1.5e-6)):
+        sim = sim_of(f0)
+        _, ga, gu = sim.adjoint(0, A.make_f0(f0["beams"], f0["modes"]), n, 50)
+        sim.close()
+        g = np.concatenate([ga, gu])
+        fd = []
+        for k in range(len(amps)):
+            ap, am = list(amps), list(amps)
+            ap[k] += h
+            am[k] -= h
+            fd.append((J_of(ap, drifts, n) - J_of(am, drifts, n)) / (2 * h))
+        for b in range(len(drifts)):
+            dp, dm = list(drifts), list(drifts)
+            dp[b] += h
+            dm[b] -= h
+            fd.append((J_of(amps, dp, n) - J_of(amps, dm, n)) / (2 * h))
+        err = float(np.max(np.abs(np.array(fd) - g)) / np.max(np.abs(g)))
+        print(f"config-4 size adjoint vs central differences (h = 1e-10), {n} steps: {err:.2e}")
+        assert err < tol, (n, err)
