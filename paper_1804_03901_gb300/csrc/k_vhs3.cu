@@ -13,7 +13,12 @@
 //   gather  one thread per x column adds the 16 cloud-in-cell weights (Eq. 4
 //           numerator alpha f and denominator alpha) of the markers of its
 //           two dual cells into registers: rows j, j+1 of v_x times the
-//           pencil's four (v_y, v_z) cells -- no atomics
+//           pencil's four (v_y, v_z) cells -- no atomics.  FP64: the columns
+//           are counting-sorted by their marker counts first and their sums
+//           kept in shared-memory row planes, so that a warp's lanes loop
+//           over nearly equal counts (an FP64 warp instruction costs its SM
+//           sub-partition the same whatever its active lanes); the weights
+//           of a marker's (v_y, v_z) cells are stored beside it
 //   flush   a finished v_x row is added into the global accumulators; each
 //           cell receives the sums of the four pencils that reach it
 // Markers whose key moved since the last re-sort deposit their 16
@@ -376,9 +381,10 @@ __global__ void __launch_bounds__(P3_THREADS, sizeof(T) == 4 ? (CPT == 1 ? 4 : (
     int* hist = reinterpret_cast<int*>(Es + nx);
     int* start = hist + nx;
     int* segs = start + nx + 1;
-    // FP64: column accumulators of rows jseg, jseg + 1 in two planes of 8 x nx
-    // (entry e of column x: plane[e * nx + x]), the columns in order of their
-    // pair counts, the count buckets and their first positions
+    // balanced gather (FP64): column accumulators of rows jseg, jseg + 1 in
+    // two planes of 8 x nx (entry e of column x: plane[e * nx + x]), the
+    // columns in order of their pair counts, the count buckets and their
+    // first positions
     const size_t acc_off = (((size_t)(reinterpret_cast<unsigned char*>(segs + nkey + 2) - smem)) + 15) / 16 * 16;
     T* RA = reinterpret_cast<T*>(smem + acc_off);
     int* ordc = reinterpret_cast<int*>(RA + 2 * 8 * nx);
@@ -536,6 +542,8 @@ __global__ void __launch_bounds__(P3_THREADS, sizeof(T) == 4 ? (CPT == 1 ? 4 : (
                 }
                 const T f = st[FF * SLEN + si];
                 T wy = (T)0, wz = (T)0, w;
+                // FP32: the (v_y, v_z) dual cells, checked against the pencil;
+                // FP64: the stored cell weights (0 for a footprint off the grid)
                 if constexpr (sizeof(T) == 4) {
                     const int jy = dual3(st[(FVX + 1) * SLEN + si], vc.a[1], vc.b[1], vc.n[1], wy);
                     const int jz = dual3(st[(FVX + 2) * SLEN + si], vc.a[2], vc.b[2], vc.n[2], wz);
