@@ -62,6 +62,10 @@ typedef struct avl_ctx avl_ctx;
  *   deviations from the previous reconstruction within a chunk, float-float
  *   over chunks, f = num / den in float-float; 1d3v: plain); the Poisson
  *   solve, the charge-neutral k = 0 handling and the diagnostics stay FP64.
+ * nvdim = 1: one chunk's deposit window (at least 7 velocity rows x nx
+ *   cells, 12 B per cell in FP32, 16 B in FP64) must fit one CTA's shared
+ *   memory, which bounds nx near 2400 (FP32) / 1800 (FP64); beyond it
+ *   avl_init_markers and avl_set_markers return AVL_EINVAL.
  * nvdim = 3 (Sec. 2 with three velocity dimensions: the field accelerates
  *   v_x, an optional static background magnetic field, avl_set_bfield, turns
  *   v) needs nx <= 1024 (FP32) or nx <= 512 (FP64), nv[0] in [2, 1024],

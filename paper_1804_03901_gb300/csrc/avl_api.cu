@@ -834,7 +834,9 @@ avl_status avl_create(const avl_domain* dom, const avl_species* spec, int32_t ns
             return bail(AVL_ECUDA);
         }
     }
-    if ((e = configure_vhs1(h)) || (e = configure_vhs3(h)) || (e = configure_field(h))) {
+    // only the deposit kernels of the context's velocity dimension (the other
+    // dimension's shared memory at this nx may exceed what a CTA can hold)
+    if ((e = dom->nvdim == 1 ? configure_vhs1(h) : configure_vhs3(h)) || (e = configure_field(h))) {
         cuda_fail(c, e, "cudaFuncSetAttribute (shared memory)");
         return bail(AVL_ECUDA);
     }

@@ -314,3 +314,29 @@ def test_conservation_drift_fp32_within_oracle_drift(A):
         dg = abs(g1[q] - g0[q]) / abs(g0[q])
         do = abs(o1[q] - o0[q]) / abs(o0[q])
         assert dg <= 1.5 * do + 1e-6, (what, dg, do)
+
+
+def test_largest_deposit_window(A):
+    """A wide x grid (nx = 2048): the FP32 deposit window of 8 velocity rows
+    (numerator, denominator and the reference plane: 196 KB) still fits one
+    CTA's shared memory and the step matches the oracle; the FP64 window
+    (8 bytes per plane cell) does not, and creating the markers reports
+    AVL_EINVAL instead of launching."""
+    nx, L, dt = 2048, 7.3, 0.07
+    species = SPECIES2(64)
+    sim, orc = make_pair(A, nx, L, dt, species, A.AVL_FP32)
+    for s, sp in enumerate(species):
+        x, v, f = inputs.random_markers(31 + s, 20011, L, sp["vmin"][0], sp["vmax"][0])
+        sim.set_markers(s, x, v, f)
+    for k in range(2):
+        sync_oracle_to_gpu(sim, orc)
+        sim.step(1)
+        orc.step(1)
+        compare_grids(sim, orc, TOL[1], f"nx 2048 step {k}")
+    sim.close()
+    sim, _ = make_pair(A, nx, L, dt, species, A.AVL_FP64)
+    x, v, f = inputs.random_markers(31, 20011, L, species[0]["vmin"][0], species[0]["vmax"][0])
+    with pytest.raises(A.AvlError) as e:
+        sim.set_markers(0, x, v, f)
+    assert e.value.status == A.AVL_EINVAL and "shared memory" in str(e.value)
+    sim.close()

@@ -173,3 +173,26 @@ def test_errors3(A):
     sim.init_markers(0, (1, 1, 1, 1), f0, 1)
     sim.step(2)
     sim.synchronize()
+
+
+@pytest.mark.parametrize("prec,nx", [(1, 1024), (0, 512)], ids=["fp32-nx1024", "fp64-nx512"])
+def test_step_parity_at_the_largest_nx3(A, prec, nx):
+    """The largest x grids of the 1d3v path (FP32 1024: four columns per
+    thread; FP64 512: two, with the FP64 gather's shared-memory row planes at
+    their largest); one larger is rejected when the context is created."""
+    L, dt = 7.3, 0.07
+    species = species2((5, 3, 3))
+    sim, orc = make_pair(A, nx, L, dt, species, prec)
+    for s, sp in enumerate(species):
+        x, v, f = inputs.random_markers3(7 * nx + s, 20011, L, sp["vmin"], sp["vmax"])
+        sim.set_markers(s, x, v, f)
+    for k in range(2):
+        sync_oracle_to_gpu(sim, orc)
+        sim.step(1)
+        orc.step(1)
+        compare_grids(sim, orc, TOL[prec], f"nx {nx} step {k}")
+    sim.close()
+    dom = A.make_domain(3, nx + 1, L, dt, 1.0, True, prec)
+    with pytest.raises(A.AvlError) as e:
+        A.Simulation(dom, [A.make_species(**species[0])])
+    assert e.value.status == A.AVL_EINVAL
