@@ -107,7 +107,11 @@ struct Pos<double> {
     {
         double x = xi + disp;
         const double n = static_cast<double>(nx);
-        if (x < 0.0 || x >= n) {
+        // x < 0 or x >= n from the bit patterns (a negative x or -0 has the
+        // sign bit set; for x >= +0 the order of doubles is the integer
+        // order of their bits), so that the FP64 pipe is left to arithmetic
+        const long long bx = __double_as_longlong(x);
+        if (bx < 0 || bx >= __double_as_longlong(n)) {
             x = fmod(x, n);
             if (x < 0.0) x += n;
             if (x >= n) x -= n;

@@ -14,11 +14,12 @@
 //           numerator alpha f and denominator alpha) of the markers of its
 //           two dual cells into registers: rows j, j+1 of v_x times the
 //           pencil's four (v_y, v_z) cells -- no atomics.  FP64: the columns
-//           are counting-sorted by their marker counts first and their sums
-//           kept in shared-memory row planes, so that a warp's lanes loop
-//           over nearly equal counts (an FP64 warp instruction costs its SM
-//           sub-partition the same whatever its active lanes); the weights
-//           of a marker's (v_y, v_z) cells are stored beside it
+//           are counting-sorted by their pair counts, their sums kept in
+//           shared-memory row planes, and each of 128 lanes walks a light
+//           and a heavy column in one loop, so that a warp's lanes do nearly
+//           equal work (an FP64 warp instruction costs its SM sub-partition
+//           the same whatever its active lanes); the weights of a marker's
+//           (v_y, v_z) cells are stored beside it
 //   flush   a finished v_x row is added into the global accumulators; each
 //           cell receives the sums of the four pencils that reach it
 // Markers whose key moved since the last re-sort deposit their 16
@@ -194,7 +195,8 @@ struct Stage3 {
 // FP64 gather (see k_pd3): count buckets of the columns' pair counts; the
 // gather's column blocks are laid out for eight warps
 constexpr int GBK = 64;
-static_assert(P3_THREADS == 256, "k_pd3's FP64 gather pairs the eight warps of a block by sub-partition");
+constexpr int GL = 128;   // gather lanes: one warp per SM sub-partition
+static_assert(P3_THREADS >= GL && GL % 32 == 0, "k_pd3's FP64 gather needs GL threads");
 
 // FP64: the two row planes of the column accumulators, the column order and
 // the count buckets, after the integer arrays (16-byte aligned)
@@ -344,7 +346,7 @@ __device__ __forceinline__ void chunk_scan(int* hist, int* start, int nx, int* w
 // mode 1: push of the mobile species, then deposit of the new state;
 // mode 2: deposit of the mobile species (pushed and re-sorted before)
 template <typename T, int CPT>
-__global__ void __launch_bounds__(P3_THREADS, sizeof(T) == 4 ? (CPT == 1 ? 4 : (CPT == 2 ? 2 : 1)) : (CPT == 1 ? 2 : 1))
+__global__ void __launch_bounds__(P3_THREADS, sizeof(T) == 4 ? (CPT == 1 ? 3 : (CPT == 2 ? 2 : 1)) : (CPT == 1 ? 2 : 1))
     k_pd3(const StepArgs* __restrict__ A, int mode)
 {
     using S = Stage3<T>;
@@ -674,51 +676,69 @@ __global__ void __launch_bounds__(P3_THREADS, sizeof(T) == 4 ? (CPT == 1 ? 4 : (
                 for (int i = threadIdx.x; i < GBK; i += P3_THREADS) gbk[i] = 0;
                 T* P0 = RA + (size_t)rp * 8 * nx;
                 T* P1 = RA + (size_t)(rp ^ 1) * 8 * nx;
-                // the two warps of an SM sub-partition (warps w and w + 4) take
-                // a light and a heavy block of 32 sorted columns, so that the
-                // sub-partitions' FP64 work is alike
-                const int wp = threadIdx.x >> 5;
-                const int gslot = ((wp < 4 ? wp : 11 - wp) << 5) | (threadIdx.x & 31);
-#pragma unroll
-                for (int c = 0; c < CPT; ++c) {
-                    const int idx = gslot + c * P3_THREADS;
-                    if (idx >= nx) continue;
-                    const int x = ordc[idx];
-                    const int xm = x == 0 ? nx - 1 : x - 1;
-                    const int mid = start[x];
-                    const int lo0 = start[xm], hi0 = x == 0 ? start[nx] : mid;
-                    const int hi1 = start[x + 1];
-                    if (lo0 == hi0 && mid == hi1) continue;   // no pairs (x == 0: lo0 <= hi0 = start[nx])
+                // gather lanes: the first GL threads (one warp per SM
+                // sub-partition) each take the sorted columns l and 2K - 1 - l
+                // (then 2K + l, 4K - 1 - l, ...), a light and a heavy one, and
+                // walk their pairs in one loop, so that the lanes of a warp do
+                // nearly equal work; a lane's accumulators go back to the row
+                // planes when its column changes.  Each column is summed in
+                // pair order (dual cell x - 1, then dual cell x).
+                const int K = min(GL, (nx + 1) >> 1);
+                const int l = threadIdx.x;
+                if (l < K) {
+                    int r = 0, x = -1, lo = 0, nup = 0, blo = 0, n = 0, kr = 0;
                     T A0[8], A1[8];
+                    for (;;) {
+                        if (kr == n) {
+                            if (x >= 0) {
 #pragma unroll
-                    for (int e = 0; e < 8; ++e) {
-                        A0[e] = P0[e * nx + x];
-                        A1[e] = P1[e * nx + x];
-                    }
-                    for (int pass = 0; pass < (x == 0 ? 2 : 1); ++pass) {
-                        const int lo = pass ? mid : lo0, hi = (x == 0 && !pass) ? hi0 : hi1;
-                        for (int i = lo; i < hi; ++i) {
-                            const T u = pay[i];
-                            const bool upper = x == 0 ? pass == 0 : i < mid;
-                            const T ax = upper ? u : (T)1 - u;
-                            const T a1 = ax * pay[NB + i];
-                            const T a0 = ax - a1;
-                            const T f = pay[2 * NB + i];
-                            const T f0 = a0 * f, f1 = a1 * f;
+                                for (int e = 0; e < 8; ++e) {
+                                    P0[e * nx + x] = A0[e];
+                                    P1[e * nx + x] = A1[e];
+                                }
+                            }
+                            x = -1;
+                            while (r * K < nx) {
+                                const int pos = r * K + ((r & 1) ? K - 1 - l : l);
+                                ++r;
+                                if (pos >= nx) continue;
+                                const int cx = ordc[pos];
+                                const int cxm = cx == 0 ? nx - 1 : cx - 1;
+                                const int a0 = start[cxm], a1 = start[cxm + 1];
+                                const int b0 = start[cx], b1 = start[cx + 1];
+                                if (a1 - a0 + b1 - b0 == 0) continue;
+                                x = cx;
+                                lo = a0;
+                                nup = a1 - a0;
+                                blo = b0;
+                                n = nup + b1 - b0;
+                                kr = 0;
+                                break;
+                            }
+                            if (x < 0) break;
 #pragma unroll
-                            for (int q = 0; q < 4; ++q) {
-                                const T wqv = pay[(3 + q) * NB + i];
-                                A0[2 * q] += f0 * wqv;
-                                A0[2 * q + 1] += a0 * wqv;
-                                A1[2 * q] += f1 * wqv;
-                                A1[2 * q + 1] += a1 * wqv;
+                            for (int e = 0; e < 8; ++e) {
+                                A0[e] = P0[e * nx + x];
+                                A1[e] = P1[e * nx + x];
                             }
                         }
-                    }
+                        const bool upper = kr < nup;
+                        const int i = upper ? lo + kr : blo + (kr - nup);
+                        ++kr;
+                        const T u = pay[i];
+                        const T ax = upper ? u : (T)1 - u;
+                        const T a1 = ax * pay[NB + i];
+                        const T a0 = ax - a1;
+                        const T f = pay[2 * NB + i];
+                        const T f0 = a0 * f, f1 = a1 * f;
 #pragma unroll
-                    for (int e = 0; e < 8; ++e) {
-                        P0[e * nx + x] = A0[e];
-                        P1[e * nx + x] = A1[e];
+                        for (int q = 0; q < 4; ++q) {
+                            const T wqv = pay[(3 + q) * NB + i];
+                            A0[2 * q] += f0 * wqv;
+                            A0[2 * q + 1] += a0 * wqv;
+                            A1[2 * q] += f1 * wqv;
+                            A1[2 * q + 1] += a1 * wqv;
+                        }
                     }
                 }
             } else
@@ -766,7 +786,7 @@ __global__ void __launch_bounds__(P3_THREADS, sizeof(T) == 4 ? (CPT == 1 ? 4 : (
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
                     const T vn = P0[(2 * q) * nx + x], vd = P0[(2 * q + 1) * nx + x];
-                    if (jseg >= 0 && jseg < nvx && pl.ok[q] && vd != (T)0) {
+                    if (jseg >= 0 && jseg < nvx && pl.ok[q] && __double_as_longlong(vd) != 0) {
                         const int o = pl.base[q] + jseg * nx + x;
                         atomicAdd(gacc + o, vn);
                         atomicAdd(gacc + cells + o, vd);
