@@ -812,7 +812,7 @@ avl_status avl_create(const avl_domain* dom, const avl_species* spec, int32_t ns
     void *pa, *pc, *pf0, *pbad, *plog;
     if ((e = dalloc(c, &pa, sizeof(StepArgs), false)) || (e = dalloc(c, &pc, sizeof(Ctl), true)) ||
         (e = dalloc(c, &pf0, sizeof(avl_f0), false)) || (e = dalloc(c, &pbad, 8, true)) ||
-        (e = dalloc(c, &plog, 128 * sizeof(double2), false))) {
+        (e = dalloc(c, &plog, LOG_TAB_N * sizeof(double2), false))) {
         cuda_fail(c, e, "cudaMalloc(control)");
         return bail(AVL_ENOMEM);
     }

@@ -49,6 +49,10 @@ constexpr int FIN_THREADS = 256;    // finalize block
 constexpr int FIN_XB = 16;          // x columns per finalize block
 constexpr int FIELD_THREADS = 512;  // Poisson cluster block
 constexpr int FIELD_CLUSTER = 8;    // CTAs in the Poisson cluster
+// table of the FP64 entropy logarithm (log_tab): one entry per 1/2048 of the
+// mantissa interval [1, 2)
+constexpr int LOG_TAB_BITS = 11;
+constexpr int LOG_TAB_N = 1 << LOG_TAB_BITS;
 constexpr long long WAIT_LIMIT = 1ll << 22;   // bounded mbarrier polls: the default limit of a first wait
                                               // (Ctl::wait_limit) and the limit of the drain that follows
                                               // a first wait that gave up
@@ -140,7 +144,7 @@ struct FieldDev {
     const double* gmul;        // cP kappa / K^2 for m <= nx/2 (0 at m = 0 and Nyquist)
     const double* green;       // nx <= GREEN_MAX: G of E = G (circulant) rho, else null
     double* diag;              // 3 + 3 ns
-    const double2* logtab;     // [128] (log c_j, 1 / c_j) of the FP64 entropy logarithm (log_tab)
+    const double2* logtab;     // [LOG_TAB_N] (log c_j, 1 / c_j) of the FP64 entropy logarithm (log_tab)
     double* hist;              // field history for marker refinement: [hist_cap][nx] FP64, or null;
                                // slot k holds E of the state after step hist_origin + k
     int hist_cap;

@@ -169,27 +169,43 @@ __device__ __forceinline__ void ff_add(ff& a, float x) { two_sum_add(a.hi, a.lo,
 // Natural logarithm of a positive FP64 value by table-driven argument
 // reduction (P. T. P. Tang, "Table-driven implementation of the logarithm
 // function in IEEE floating-point arithmetic", ACM TOMS 16, 1990): with
-// f = 2^e m, m in [1, 2), and c_j = 1 + (j + 1/2) / 128 the centre of the
-// 1/128 interval that holds m, log f = e ln 2 + log c_j + log1p(r), where
-// r = m / c_j - 1 (|r| < 2^-8) and log1p(r) is its Taylor series to r^6
-// (the next term is below 2e-18).  tab[j] = (log c_j, 1 / c_j), filled once
-// per context (init_log_table).  About ten FP64 operations instead of the
-// library logarithm's longer sequence; subnormal f take the library path.
+// f = 2^e m, m in [1, 2), and c_j = 1 + (j + 1/2) / 2048 the centre of the
+// 1/2048 interval that holds m, log f = e ln 2 + log c_j + log1p(r), where
+// r = m / c_j - 1 (|r| < 2^-12) and log1p(r) is its Taylor series to r^4
+// (the next term is below 2e-19).  tab[j] = (log c_j, 1 / c_j), filled once
+// per context (init_log_table).  Seven FP64 operations besides the exponent's
+// conversion; subnormal f (found from the bits) take the library path.
 __device__ __forceinline__ double log_tab(double f, const double2* __restrict__ tab)
 {
-    if (f < 2.2250738585072014e-308) return log(f);
     const long long b = __double_as_longlong(f);
+    if (b < 0x0010000000000000ll) return log(f);
     const int e = (int)(b >> 52) - 1023;
-    const int j = (int)((b >> 45) & 127);
+    const int j = (int)((b >> (52 - LOG_TAB_BITS)) & (LOG_TAB_N - 1));
     const double m = __longlong_as_double((b & 0x000FFFFFFFFFFFFFll) | 0x3FF0000000000000ll);
     const double2 t = __ldg(tab + j);
     const double r = fma(m, t.y, -1.0);
-    double q = fma(r, -1.0 / 6.0, 0.2);
-    q = fma(r, q, -0.25);
-    q = fma(r, q, 1.0 / 3.0);
+    double q = fma(r, -0.25, 1.0 / 3.0);
     q = fma(r, q, -0.5);
     const double lp = fma(r * r, q, r);
     return fma((double)e, 0.69314718055994530942, t.x + lp);
+}
+
+// n / d for a normal d > 0 by two Newton-Raphson steps on the reciprocal
+// (r <- r + r (1 - d r), each step squaring the relative error) from the
+// PTX approximate reciprocal, then one correction of the quotient
+// (q <- q + r (n - d q)), as in P. Markstein, "Computation of elementary
+// functions on the IBM RISC System/6000 processor", IBM J. Res. Dev. 34,
+// 1990; other d take the division operator.
+__device__ __forceinline__ double div_nr(double n, double d)
+{
+    const long long b = __double_as_longlong(d);
+    if (b < 0x0030000000000000ll || b >= 0x7FC0000000000000ll) return n / d;   // d < 2^-1020, d >= 2^1021
+    double r;
+    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(d));
+    r = fma(r, fma(-d, r, 1.0), r);
+    r = fma(r, fma(-d, r, 1.0), r);
+    const double q = n * r;
+    return fma(r, fma(-d, q, n), q);
 }
 
 template <typename T>
@@ -218,7 +234,7 @@ struct ColAcc<double> {
     {
         rho += fh;
         w += v2 * fh;
-        if (fh > 0.0) ent += fh * log_tab(fh, logtab);
+        if (__double_as_longlong(fh) > 0) ent += fh * log_tab(fh, logtab);   // fh > 0 (fh is not a NaN)
     }
     __device__ __forceinline__ double r() const { return rho; }
     __device__ __forceinline__ double wk() const { return w; }

@@ -722,16 +722,16 @@ cudaError_t launch_field_batch(const BatchMap* bm, int nrun, int smem, int count
 
 __global__ void k_log_table(double2* tab)
 {
-    const int j = threadIdx.x;
-    if (j < 128) {
-        const double c = 1.0 + ((double)j + 0.5) / 128.0;
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < LOG_TAB_N) {
+        const double c = 1.0 + ((double)j + 0.5) / (double)LOG_TAB_N;
         tab[j] = make_double2(log(c), 1.0 / c);
     }
 }
 
 cudaError_t init_log_table(double2* tab, cudaStream_t st)
 {
-    k_log_table<<<1, 128, 0, st>>>(tab);
+    k_log_table<<<(LOG_TAB_N + 255) / 256, 256, 0, st>>>(tab);
     return cudaGetLastError();
 }
 

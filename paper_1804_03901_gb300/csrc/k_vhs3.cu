@@ -890,7 +890,11 @@ __global__ void __launch_bounds__(FIN3_X * FIN3_R) k_fin3(const StepArgs* __rest
     if constexpr (sizeof(T) == 8) acc.logtab = A->fd.logtab;
     auto cell = [&](int j, T nn, T dd, T v2j) {
         const size_t o = (size_t)j * nx + x;
-        const T f = dd > (T)0 ? nn / dd : (T)0;
+        T f;
+        if constexpr (sizeof(T) == 8)
+            f = __double_as_longlong(dd) > 0 ? div_nr(nn, dd) : 0.0;   // dd >= 0 is a sum of weights
+        else
+            f = dd > (T)0 ? nn / dd : (T)0;
         fg[o] = f;
         clr[o] = (T)0;
         clr[cells + o] = (T)0;

@@ -55,7 +55,8 @@ def pair_1d3v(A, prec):
     return sim, orc, P3
 
 
-@pytest.mark.parametrize("nvdim,prec", [(1, 1), (1, 0), (3, 1)], ids=["1d1v-fp32", "1d1v-fp64", "1d3v-fp32"])
+@pytest.mark.parametrize("nvdim,prec", [(1, 1), (1, 0), (3, 1), (3, 0)],
+                         ids=["1d1v-fp32", "1d1v-fp64", "1d3v-fp32", "1d3v-fp64"])
 def test_bounded_wait_timeout_is_reported_and_the_context_recovers(A, nvdim, prec):
     sim, orc, P = (pair_1d1v if nvdim == 1 else pair_1d3v)(A, prec)
     tol = P.TOL[prec]
