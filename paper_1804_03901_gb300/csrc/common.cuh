@@ -103,9 +103,12 @@ struct Pos<double> {
         i0 = static_cast<int>(fl);
         w = u - fl;
     }
-    __device__ __forceinline__ void drift(double disp, int nx)
+    __device__ __forceinline__ void drift(double disp, int nx) { wrap(xi + disp, nx); }
+    // the same drift with the displacement v c fused into the addition
+    __device__ __forceinline__ void drift_fma(double v, double c, int nx) { wrap(fma(v, c, xi), nx); }
+    // x into [0, nx) (periodic)
+    __device__ __forceinline__ void wrap(double x, int nx)
     {
-        double x = xi + disp;
         const double n = static_cast<double>(nx);
         // x < 0 or x >= n from the bit patterns (a negative x or -0 has the
         // sign bit set; for x >= +0 the order of doubles is the integer
