@@ -344,9 +344,13 @@ __device__ __forceinline__ void chunk_scan(int* hist, int* start, int nx, int* w
 
 // mode 0: deposit of the current markers of every species (refresh);
 // mode 1: push of the mobile species, then deposit of the new state;
-// mode 2: deposit of the mobile species (pushed and re-sorted before)
-template <typename T, int CPT>
-__global__ void __launch_bounds__(P3_THREADS, sizeof(T) == 4 ? (CPT == 1 ? 3 : (CPT == 2 ? 2 : 1)) : (CPT == 1 ? 2 : 1))
+// mode 2: deposit of the mobile species (pushed and re-sorted before).
+// PUSH (mode 1) is a template parameter so that the deposit-only instances
+// keep their own register budget (FP32, one column per thread: three CTAs
+// per SM with the push, four without).
+template <typename T, int CPT, bool PUSH>
+__global__ void __launch_bounds__(P3_THREADS, sizeof(T) == 4 ? (CPT == 1 ? (PUSH ? 3 : 4) : (CPT == 2 ? 2 : 1))
+                                                             : (CPT == 1 ? 2 : 1))
     k_pd3(const StepArgs* __restrict__ A, int mode)
 {
     using S = Stage3<T>;
@@ -364,7 +368,7 @@ __global__ void __launch_bounds__(P3_THREADS, sizeof(T) == 4 ? (CPT == 1 ? 3 : (
     const int g = blockIdx.x;
     const int s = species_of_pen(A, g);
     const SpDev& sp = A->sp[s];
-    const bool push = mode == 1;
+    constexpr bool push = PUSH;   // mode == 1
     if (mode != 0 && !sp.mobile) return;
     Ctl* ctl = A->ctl;
     const long long wait_first = ctl->wait_limit;
@@ -1474,9 +1478,12 @@ template <typename T>
 static cudaError_t set_pd3_attr(int smem)
 {
     cudaError_t e;
-    if ((e = raise_smem_limit(k_pd3<T, 1>, smem))) return e;
-    if ((e = raise_smem_limit(k_pd3<T, 2>, smem))) return e;
-    return raise_smem_limit(k_pd3<T, 4>, smem);
+    if ((e = raise_smem_limit(k_pd3<T, 1, false>, smem))) return e;
+    if ((e = raise_smem_limit(k_pd3<T, 2, false>, smem))) return e;
+    if ((e = raise_smem_limit(k_pd3<T, 4, false>, smem))) return e;
+    if ((e = raise_smem_limit(k_pd3<T, 1, true>, smem))) return e;
+    if ((e = raise_smem_limit(k_pd3<T, 2, true>, smem))) return e;
+    return raise_smem_limit(k_pd3<T, 4, true>, smem);
 }
 
 cudaError_t configure_vhs3(const StepArgs& h)
@@ -1490,9 +1497,18 @@ static void pd3_go(const StepArgs& h, const StepArgs* d, int mode, cudaStream_t 
 {
     const int smem = (int)pd3_smem_bytes(h.fd.nx, nkey_max(h), h.prec);
     switch (cpt_of(h.fd.nx)) {
-        case 1: k_pd3<T, 1><<<h.npen_total, P3_THREADS, smem, st>>>(d, mode); break;
-        case 2: k_pd3<T, 2><<<h.npen_total, P3_THREADS, smem, st>>>(d, mode); break;
-        default: k_pd3<T, 4><<<h.npen_total, P3_THREADS, smem, st>>>(d, mode); break;
+        case 1:
+            if (mode == 1) k_pd3<T, 1, true><<<h.npen_total, P3_THREADS, smem, st>>>(d, mode);
+            else k_pd3<T, 1, false><<<h.npen_total, P3_THREADS, smem, st>>>(d, mode);
+            break;
+        case 2:
+            if (mode == 1) k_pd3<T, 2, true><<<h.npen_total, P3_THREADS, smem, st>>>(d, mode);
+            else k_pd3<T, 2, false><<<h.npen_total, P3_THREADS, smem, st>>>(d, mode);
+            break;
+        default:
+            if (mode == 1) k_pd3<T, 4, true><<<h.npen_total, P3_THREADS, smem, st>>>(d, mode);
+            else k_pd3<T, 4, false><<<h.npen_total, P3_THREADS, smem, st>>>(d, mode);
+            break;
     }
 }
 
