@@ -45,6 +45,81 @@
 
 namespace avl {
 
+// FP64 1d3v position: a 64-bit fixed-point count of 2^-52 cells, x = X 2^-52
+// cells with 0 <= X < nx 2^52 <= 2^61 (FP64 1d3v has nx <= 512).  It
+// resolves 2^-52 cells everywhere (a double of the same x resolves 2^-52 x),
+// and the cloud-in-cell reads the weight straight from the bits: the 52 low
+// bits of X - 2^51 are the mantissa of 1 + w, so that w and the lower cell
+// cost one FP64 operation instead of four (the form is limited by the FP64
+// pipe).  The drift converts the displacement once (a multiply and a
+// conversion).
+struct PosX {
+    long long X;
+    static constexpr double ONE = 4503599627370496.0;   // 2^52: one cell
+    __device__ __forceinline__ void load(const SpDev& sp, int cb, int k)
+    {
+        X = reinterpret_cast<const long long*>(sp.mx[cb])[k];
+    }
+    __device__ __forceinline__ void store(const SpDev& sp, int cb, int k) const
+    {
+        reinterpret_cast<long long*>(sp.mx[cb])[k] = X;
+    }
+    // cloud-in-cell: lower cell i0 (may be -1) and weight w of cell i0 + 1
+    __device__ __forceinline__ void cic(int& i0, double& w) const
+    {
+        const long long U = X - (1ll << 51);   // x - 1/2
+        i0 = (int)(U >> 52);                   // floor (arithmetic shift)
+        w = __longlong_as_double(0x3FF0000000000000ll | (U & 0x000FFFFFFFFFFFFFll)) - 1.0;
+    }
+    // x into [0, nx) (periodic); Y computed modulo 2^64 so that no
+    // displacement overflows
+    __device__ __forceinline__ void wrap(long long Y, int nx)
+    {
+        const long long N = (long long)nx << 52;
+        if ((unsigned long long)Y >= (unsigned long long)N) {
+            Y %= N;
+            if (Y < 0) Y += N;
+        }
+        X = Y;
+    }
+    // displacement of `scaled` 2^-52 cells (a double, rounded to the nearest
+    // count; the conversion saturates and maps NaN to 0)
+    __device__ __forceinline__ void drift_scaled(double scaled, int nx)
+    {
+        wrap((long long)((unsigned long long)X + (unsigned long long)__double2ll_rn(scaled)), nx);
+    }
+    __device__ __forceinline__ void drift(double disp, int nx) { drift_scaled(disp * ONE, nx); }
+    __device__ __forceinline__ double cells() const { return (double)X * (1.0 / ONE); }
+    __device__ __forceinline__ static PosX from_cells(double xi, int nx)
+    {
+        PosX p;
+        p.X = 0;
+        p.drift(xi, nx);
+        return p;
+    }
+};
+
+template <typename T>
+struct Pos3Sel {
+    using type = Pos<T>;
+};
+template <>
+struct Pos3Sel<double> {
+    using type = PosX;
+};
+// position type of the 1d3v kernels: FP32 int cell + FP32 offset, FP64 PosX
+template <typename T>
+using Pos3 = typename Pos3Sel<T>::type;
+
+template <typename T>
+__device__ __forceinline__ Pos3<T> pos3_from_cells(double xi, int nx)
+{
+    if constexpr (sizeof(T) == 8)
+        return PosX::from_cells(xi, nx);
+    else
+        return pos_from_cells<T>(xi, nx);
+}
+
 template <typename T>
 struct Cfg3;
 template <>
@@ -458,6 +533,7 @@ __global__ void __launch_bounds__(P3_THREADS, sizeof(T) == 4 ? (CPT == 1 ? (PUSH
     VCoef<T> vc;
     vc.init(sp);
     const T qm_dt = (T)sp.qm_dt, dt_dx = (T)sp.dt_dx;
+    const double dt_dx52 = sp.dt_dx * PosX::ONE;   // FP64: dt / dx in 2^-52 cells
     Planes pl;
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
@@ -521,12 +597,12 @@ __global__ void __launch_bounds__(P3_THREADS, sizeof(T) == 4 ? (CPT == 1 ? (PUSH
                 if (i >= cnt) continue;
                 const int si = o0 + i;
                 const int idx = b0 + i;
-                Pos<T> pos;
+                Pos3<T> pos;
                 if constexpr (sizeof(T) == 4) {
                     pos.c = reinterpret_cast<const int*>(st)[si];
                     pos.o = st[SLEN + si];
                 } else {
-                    pos.xi = st[si];
+                    pos.X = reinterpret_cast<const long long*>(st)[si];
                 }
                 T vx = st[FVX * SLEN + si];
                 if (push) {
@@ -537,11 +613,11 @@ __global__ void __launch_bounds__(P3_THREADS, sizeof(T) == 4 ? (CPT == 1 ? (PUSH
                     wrap_pair(i0, nx, ia, ib);
                     if constexpr (sizeof(T) == 8) {
                         // FP64 (the FP64 pipe limits this form): E_a + w (E_b - E_a)
-                        // and x + v (dt / dx) as fused operations, one FP64
-                        // operation each fewer than the plain forms
+                        // fused, one FP64 operation fewer than the plain form;
+                        // the displacement in 2^-52 cells (dt_dx52 = dt / dx 2^52)
                         const T Ea = Es[ia];
                         vx = fma(qm_dt, fma(wx, Es[ib] - Ea, Ea), vx);
-                        pos.drift_fma(vx, dt_dx, nx);
+                        pos.drift_scaled(vx * dt_dx52, nx);
                     } else {
                         const T El = ((T)1 - wx) * Es[ia] + wx * Es[ib];
                         vx = vx + qm_dt * El;
@@ -551,7 +627,7 @@ __global__ void __launch_bounds__(P3_THREADS, sizeof(T) == 4 ? (CPT == 1 ? (PUSH
                         reinterpret_cast<int*>(gx)[idx] = pos.c;
                         goff[idx] = pos.o;
                     } else {
-                        reinterpret_cast<double*>(gx)[idx] = pos.xi;
+                        reinterpret_cast<long long*>(gx)[idx] = pos.X;
                     }
                     gvx[idx] = vx;
                 }
@@ -1022,7 +1098,7 @@ __global__ void __launch_bounds__(P3_THREADS) k_sort3(const StepArgs* __restrict
         }
         const int slot = beg + warp_slot(cnt, key, ok);
         if (ok && slot >= beg && slot < end) {
-            Pos<T> pos;
+            Pos3<T> pos;
             pos.load(sp, src, k);
             pos.store(sp, dst, slot);
             reinterpret_cast<T*>(sp.mv[dst][0])[slot] = vx;
@@ -1257,7 +1333,7 @@ __global__ void __launch_bounds__(256) k_src3_scatter(const StepArgs* __restrict
             over = true;
             continue;
         }
-        const Pos<T> pos = pos_from_cells<T>(mk.xi, sp.nx);
+        const Pos3<T> pos = pos3_from_cells<T>(mk.xi, sp.nx);
         pos.store(sp, 0, slot);
         for (int d = 0; d < 3; ++d) reinterpret_cast<T*>(sp.mv[0][d])[slot] = v[d];
         reinterpret_cast<T*>(sp.mf[0])[slot] = (T)mk.f;
@@ -1325,7 +1401,7 @@ __global__ void __launch_bounds__(256) k_bpush3(const StepArgs* __restrict__ A, 
         const bool ok = k < sp.n;
         int b = 0;
         if (ok) {
-            Pos<T> pos;
+            Pos3<T> pos;
             pos.load(sp, cb, (int)k);
             int i0, ia, ib;
             T wx;
@@ -1374,7 +1450,7 @@ __global__ void __launch_bounds__(256) k_rs3_scatter(const StepArgs* __restrict_
     bool over = false;
     for (long long w0 = wid * 32 * RS3_ROUNDS; w0 < n; w0 += nw * 32 * RS3_ROUNDS) {
         T v[RS3_ROUNDS][3], fv[RS3_ROUNDS];
-        Pos<T> pos[RS3_ROUNDS];
+        Pos3<T> pos[RS3_ROUNDS];
         int b[RS3_ROUNDS];
 #pragma unroll
         for (int r = 0; r < RS3_ROUNDS; ++r) {
@@ -1424,7 +1500,7 @@ __global__ void k_get3(const StepArgs* __restrict__ A, int s, double* __restrict
     const int cb = A->ctl->cur[s];
     const long long n = sp.n;
     for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
-        Pos<T> pos;
+        Pos3<T> pos;
         pos.load(sp, cb, (int)k);
         if (x) x[k] = pos.cells() * sp.dx;
         if (v)
