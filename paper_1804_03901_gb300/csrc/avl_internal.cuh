@@ -87,7 +87,7 @@ struct SpDev {
     unsigned div_m;            // magic multiplier and shift for slot / M
     int div_l;
     // markers
-    void* mx[2];               // FP32: int cell; FP64: double xi
+    void* mx[2];               // FP32: int cell; FP64: 1d1v double xi, 1d3v int64 X (2^-52 cells)
     float* moff[2];            // FP32 only
     void* mv[2][3];            // velocity components (vx chunk-relative)
     void* mf[2];

@@ -161,22 +161,33 @@ __device__ __forceinline__ int dual3(float v, float a, float b, int n, float& w)
     w = t - fl;
     return (int)fl;
 }
-// FP64: floor by one saturating conversion to int (NaN gives 0), the range
-// test in integers, so that the FP64 pipe (the kernel's limit) sees three
-// operations instead of six
-__device__ __forceinline__ int dual3(double v, double a, double b, int n, double& w)
+// FP64: a and b come scaled by 2^52 (dual_coef), so that t 2^52 rounds to a
+// 64-bit count of 2^-52 rows in one saturating conversion (NaN gives 0);
+// the row is its high bits and the weight its low 52 bits, read as the
+// mantissa of 1 + w: the FP64 pipe (the kernel's limit) sees three
+// operations, the range test is in integers
+__device__ __forceinline__ int dual3(double v, double a52, double b52, int n, double& w)
 {
-    const double t = __fma_rn(v, a, b);
-    const int fl = __double2int_rd(t);
+    const long long t = __double2ll_rn(__fma_rn(v, a52, b52));
+    const int fl = (int)(t >> 52);
     if (fl < -2 || fl >= n) {
         w = 0.0;
         return fl < 0 ? -2 : n;
     }
-    w = t - (double)fl;
+    w = __longlong_as_double(0x3FF0000000000000ll | (t & 0x000FFFFFFFFFFFFFll)) - 1.0;
     return fl;
 }
 
-// coefficients of dual3 for dimension d of a species, in storage precision
+// coefficients a, b of dual3 for dimension d of a species, in storage
+// precision (FP64: times 2^52)
+template <typename T>
+__device__ __forceinline__ void dual_coef(const SpDev& sp, int d, T& a, T& b)
+{
+    const double s = sizeof(T) == 8 ? 4503599627370496.0 : 1.0;
+    a = (T)(sp.inv_dv[d] * s);
+    b = (T)((-sp.vmin[d] * sp.inv_dv[d] - 0.5) * s);
+}
+
 template <typename T>
 struct VCoef {
     T a[3], b[3];
@@ -184,8 +195,7 @@ struct VCoef {
     __device__ __forceinline__ void init(const SpDev& sp)
     {
         for (int d = 0; d < 3; ++d) {
-            a[d] = (T)sp.inv_dv[d];
-            b[d] = (T)(-sp.vmin[d] * sp.inv_dv[d] - 0.5);
+            dual_coef<T>(sp, d, a[d], b[d]);
             n[d] = sp.nv[d];
         }
     }
@@ -1066,7 +1076,8 @@ __global__ void __launch_bounds__(P3_THREADS) k_sort3(const StepArgs* __restrict
     const int* sg = sp.seg[src] + (size_t)p * (nk + 1);
     int* dg = sp.seg[dst] + (size_t)p * (nk + 1);
     const int beg = sg[0], end = sg[nk];
-    const T ax = (T)sp.inv_dv[0], bx = (T)(-sp.vmin[0] * sp.inv_dv[0] - 0.5);
+    T ax, bx;
+    dual_coef<T>(sp, 0, ax, bx);
     const T* vxs = reinterpret_cast<const T*>(sp.mv[src][0]);
     for (int i = threadIdx.x; i < nk + 1; i += P3_THREADS) cnt[i] = 0;
     __syncthreads();
