@@ -193,19 +193,19 @@ __device__ __forceinline__ double log_tab(double f, const double2* __restrict__ 
     return fma((double)e, 0.69314718055994530942, t.x + lp);
 }
 
-// n / d for a normal d > 0 by two Newton-Raphson steps on the reciprocal
-// (r <- r + r (1 - d r), each step squaring the relative error) from the
-// PTX approximate reciprocal, then one correction of the quotient
-// (q <- q + r (n - d q)), as in P. Markstein, "Computation of elementary
+// n / d for a normal d > 0 by one Newton-Raphson step on the reciprocal
+// (r <- r + r (1 - d r), which squares its relative error) from the PTX
+// approximate reciprocal (within about 2^-20), then one correction of the
+// quotient (q <- q + r (n - d q)), which squares the error of q = n r again
+// and leaves the rounding (P. Markstein, "Computation of elementary
 // functions on the IBM RISC System/6000 processor", IBM J. Res. Dev. 34,
-// 1990; other d take the division operator.
+// 1990); other d take the division operator.
 __device__ __forceinline__ double div_nr(double n, double d)
 {
     const long long b = __double_as_longlong(d);
     if (b < 0x0030000000000000ll || b >= 0x7FC0000000000000ll) return n / d;   // d < 2^-1020, d >= 2^1021
     double r;
     asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(d));
-    r = fma(r, fma(-d, r, 1.0), r);
     r = fma(r, fma(-d, r, 1.0), r);
     const double q = n * r;
     return fma(r, fma(-d, q, n), q);

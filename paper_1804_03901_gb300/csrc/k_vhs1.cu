@@ -905,7 +905,7 @@ struct CellSum<double> {
     __device__ __forceinline__ void value(double, double& fh, double& fl, double& dsum) const
     {
         dsum = den;
-        fh = den > 0.0 ? num / den : 0.0;
+        fh = __double_as_longlong(den) > 0 ? div_nr(num, den) : 0.0;   // den >= 0 is a sum of weights
         fl = 0.0;
     }
 };
