@@ -280,6 +280,11 @@ struct Stage3 {
 // FP64 gather (see k_pd3): count buckets of the columns' pair counts; the
 // gather's column blocks are laid out for eight warps
 constexpr int GBK = 64;
+// the short remainder (fewer markers) of a segment just over NB markers
+// skips the x sort and the gather: its markers deposit by global reductions
+// like the markers off their row, which saves the phases of the sort (scan,
+// scatter, column order) and their barriers for a handful of markers
+constexpr int P3_TAIL = 96;
 constexpr int GL = 128;   // gather lanes: one warp per SM sub-partition
 static_assert(P3_THREADS >= GL && GL % 32 == 0, "k_pd3's FP64 gather needs GL threads");
 
@@ -569,6 +574,7 @@ __global__ void __launch_bounds__(P3_THREADS, sizeof(T) == 4 ? (CPT == 1 ? (PUSH
         const int send = segs[k + 1];
         for (int b0 = segs[k]; b0 < send; b0 += NB) {
             const int cnt = min(NB, send - b0);
+            const bool tail = b0 > segs[k] && cnt < P3_TAIL;   // the remainder of a segment over NB
             // stage the next chunk into the other buffer (free since the end of
             // the previous chunk)
             if (threadIdx.x == 0) {
@@ -662,14 +668,16 @@ __global__ void __launch_bounds__(P3_THREADS, sizeof(T) == 4 ? (CPT == 1 ? (PUSH
                 int bin = i0 < 0 ? i0 + nx : i0;
                 bin = min(max(bin, 0), nx - 1);
                 const int d = jx - jseg;
-                if (d == 0) {
+                if (d == 0 && !tail) {
                     prank[m] = atomicAdd(&hist[bin], 1);
                 } else {
-                    // off its segment's row: parked at the tail of the payload
-                    // arrays (the stays fill them from the front) and deposited
-                    // by the whole block after the sort
-                    ++nmov;
-                    if (d > 1 || d < -1) ++nfar;
+                    // off its segment's row (or in a short chunk): parked at the
+                    // tail of the payload arrays (the stays fill them from the
+                    // front) and deposited by the whole block after the sort
+                    if (d != 0) {
+                        ++nmov;
+                        if (d > 1 || d < -1) ++nfar;
+                    }
                     const int o = NB - 1 - atomicAdd(&nmv_s, 1);
                     pay[0 * NB + o] = u;
                     pay[1 * NB + o] = w;
@@ -692,6 +700,33 @@ __global__ void __launch_bounds__(P3_THREADS, sizeof(T) == 4 ? (CPT == 1 ? (PUSH
             }
             __syncthreads();
             const int nmv = nmv_s;
+            // the parked markers: one thread per (marker, corner) into the global
+            // accumulator, so that a chunk's few movers do not hold one warp
+            // behind the others at the chunk's barrier
+            auto deposit_parked = [&]() {
+                for (int t = threadIdx.x; t < nmv * 16; t += P3_THREADS) {
+                    const int o = NB - 1 - (t >> 4);
+                    const int jx = (int)pay[6 * NB + o];
+                    if constexpr (sizeof(T) == 4) {
+                        deposit_corner<T>(gacc, cells, pl, nx, nvx, (int)pay[5 * NB + o], pay[0 * NB + o], jx,
+                                          pay[1 * NB + o], pay[3 * NB + o], pay[4 * NB + o], pay[2 * NB + o],
+                                          t & 15);
+                    } else {
+                        const long long mi = (long long)pay[3 * NB + o];
+                        const T wqv = reinterpret_cast<const double*>(sp.mwq[cb])[4 * mi + ((t & 15) >> 2)];
+                        deposit_corner_q<T>(gacc, cells, pl, nx, nvx, (int)pay[5 * NB + o], pay[0 * NB + o], jx,
+                                            pay[1 * NB + o], wqv, pay[2 * NB + o], t & 15);
+                    }
+                }
+            };
+            if (tail) {
+                __syncthreads();   // every thread has read nmv_s
+                if (threadIdx.x == 0) nmv_s = 0;
+                deposit_parked();
+                __syncthreads();
+                buf ^= 1;
+                continue;
+            }
             chunk_scan<CPT>(hist, start, nx, wsum);   // every thread has read nmv_s by its barriers
             if (threadIdx.x == 0) nmv_s = 0;
             // stays into x-sorted order
@@ -747,22 +782,7 @@ __global__ void __launch_bounds__(P3_THREADS, sizeof(T) == 4 ? (CPT == 1 ? (PUSH
                     gbase[2 * lane + 1] = incl - a1;
                 }
             }
-            // markers off their segment's row: one thread per (marker, corner),
-            // so that a chunk's few movers do not hold one warp behind the
-            // others at the chunk's barrier
-            for (int t = threadIdx.x; t < nmv * 16; t += P3_THREADS) {
-                const int o = NB - 1 - (t >> 4);
-                const int jx = (int)pay[6 * NB + o];
-                if constexpr (sizeof(T) == 4) {
-                    deposit_corner<T>(gacc, cells, pl, nx, nvx, (int)pay[5 * NB + o], pay[0 * NB + o], jx,
-                                      pay[1 * NB + o], pay[3 * NB + o], pay[4 * NB + o], pay[2 * NB + o], t & 15);
-                } else {
-                    const long long mi = (long long)pay[3 * NB + o];
-                    const T wqv = reinterpret_cast<const double*>(sp.mwq[cb])[4 * mi + ((t & 15) >> 2)];
-                    deposit_corner_q<T>(gacc, cells, pl, nx, nvx, (int)pay[5 * NB + o], pay[0 * NB + o], jx,
-                                        pay[1 * NB + o], wqv, pay[2 * NB + o], t & 15);
-                }
-            }
+            deposit_parked();
             // gather: column x takes weight u from the markers of dual cell
             // x - 1 and 1 - u from those of dual cell x, which follow them in
             // the sorted order (one loop; two at the periodic seam)
