@@ -296,8 +296,8 @@ avl_status avl_field_solve(int32_t nx, double L, double poisson_const, int32_t s
 avl_status avl_field_solve_noalloc(int32_t nx, double L, double poisson_const, int32_t softening,
                                    const double* rho, double* E, void* cuda_stream);
 
-/* Gradient of the field energy at the final time (spec extension; the
- * paper has no adjoint): J = 1/2 sum_i E_i(T)^2 dx after nsteps steps that
+/* Gradient of the field energy at the final time (an extension beyond the
+ * paper, which has no adjoint): J = 1/2 sum_i E_i(T)^2 dx after nsteps steps that
  * start from the markers each species got from its last avl_init_markers,
  * with the f0 of species s replaced by theta.  Outputs (host): *J,
  * dJ_damp[m] = dJ/d theta->amp[m] (theta->nmode values) and dJ_ddrift[b] =
@@ -313,8 +313,8 @@ avl_status avl_field_solve_noalloc(int32_t nx, double L, double poisson_const, i
 avl_status avl_adjoint(avl_ctx* ctx, int32_t s, const avl_f0* theta, int32_t nsteps, int32_t ckpt_every,
                        double* dJ_damp, double* dJ_ddrift, double* J);
 
-/* Batched ensemble (spec extension; the paper runs one simulation at a
- * time): nrun independent 1d1v runs of any sizes, run r with domain doms[r]
+/* Batched ensemble (an extension beyond the paper, which runs one simulation
+ * at a time): nrun independent 1d1v runs of any sizes, run r with domain doms[r]
  * and the nspecies[r] species that follow in sps (runs' species listed one
  * run after another).  All runs share one precision and the batch's stream
  * (cuda_stream, or one the batch creates).  avl_step on the batch advances
@@ -358,7 +358,7 @@ avl_status avl_profile_steps(avl_ctx* ctx, int32_t nsteps, double* ms, int32_t n
  * first run's error. */
 avl_status avl_synchronize(avl_ctx* ctx);
 
-/* Failure detection (spec extension; the paper has no counterpart):
+/* Failure detection (an extension beyond the paper, which has no counterpart):
  * the deposit kernels stage marker fields and E with bulk copies (TMA) and
  * wait for them on an mbarrier at most `polls` polls (default 2^22, about a
  * second); a wait that gives up sets the AVL_ETIMEOUT flag, drains the copy
