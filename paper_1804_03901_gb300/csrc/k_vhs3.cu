@@ -280,10 +280,12 @@ struct Stage3 {
 // FP64 gather (see k_pd3): count buckets of the columns' pair counts; the
 // gather's column blocks are laid out for eight warps
 constexpr int GBK = 64;
-// the short remainder (fewer markers) of a segment just over NB markers
-// skips the x sort and the gather: its markers deposit by global reductions
-// like the markers off their row, which saves the phases of the sort (scan,
-// scatter, column order) and their barriers for a handful of markers
+// FP64: the short remainder (fewer markers) of a segment just over NB
+// markers skips the x sort and the gather: its markers deposit by global
+// reductions like the markers off their row, which saves the phases of the
+// sort (scan, scatter, column order) and their barriers for a handful of
+// markers (in FP32 the gather of a few markers costs less than their global
+// reductions)
 constexpr int P3_TAIL = 96;
 constexpr int GL = 128;   // gather lanes: one warp per SM sub-partition
 static_assert(P3_THREADS >= GL && GL % 32 == 0, "k_pd3's FP64 gather needs GL threads");
@@ -574,7 +576,7 @@ __global__ void __launch_bounds__(P3_THREADS, sizeof(T) == 4 ? (CPT == 1 ? (PUSH
         const int send = segs[k + 1];
         for (int b0 = segs[k]; b0 < send; b0 += NB) {
             const int cnt = min(NB, send - b0);
-            const bool tail = b0 > segs[k] && cnt < P3_TAIL;   // the remainder of a segment over NB
+            const bool tail = S::BAL && b0 > segs[k] && cnt < P3_TAIL;   // FP64: the remainder of a segment over NB
             // stage the next chunk into the other buffer (free since the end of
             // the previous chunk)
             if (threadIdx.x == 0) {
