@@ -537,10 +537,40 @@ def adjoint_cost(A, stream, nv=0):
     return out
 
 
+def host_near_gpu(dev):
+    """Bind this process to the CPUs next to GPU `dev` (the local_cpulist of
+    its PCI device, within the CPUs the process may use), so that the pinned
+    host buffers of the end-to-end leg are placed in the memory the GPU
+    reaches fastest.  Returns the CPU list, or None where the system gives
+    none."""
+    import torch
+    p = torch.cuda.get_device_properties(dev)
+    try:
+        path = "/sys/bus/pci/devices/%04x:%02x:%02x.0/local_cpulist" % (
+            p.pci_domain_id, p.pci_bus_id, p.pci_device_id)
+        with open(path) as fh:
+            spec = fh.read().strip()
+    except (AttributeError, OSError):
+        return None
+    cpus = set()
+    for part in spec.split(","):
+        if "-" in part:
+            a, b = part.split("-")
+            cpus.update(range(int(a), int(b) + 1))
+        elif part:
+            cpus.add(int(part))
+    cpus &= os.sched_getaffinity(0)
+    if not cpus:
+        return None
+    os.sched_setaffinity(0, cpus)
+    return ",".join(str(c) for c in sorted(cpus))
+
+
 def run_ours(args):
     import torch
     rank, world, local = dist_env()
     torch.cuda.set_device(local)
+    host_cpus = host_near_gpu(local)
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
@@ -580,7 +610,8 @@ def run_ours(args):
                            "timed_from": (f"step {f['start_step']} of the {base['steps']}-step run (state reached "
                                           f"by untimed steps), then {max(3, args.warmup)} warm-up steps"
                                           if f["start_step"] else "t = 0"),
-                           "l2": l2, "parallelism": "single GPU" if world == 1 else f"{world} independent replicas"},
+                           "l2": l2, "parallelism": "single GPU" if world == 1 else f"{world} independent replicas",
+                           "host_cpus": host_cpus or "not bound (no local CPU list)"},
                 "roofline": f["roofline"], "clocks": f["clocks"],
                 "gpu_launches": LAUNCHES_PER_STEP[kind] * args.steps,
                 ("out_of_window_runs_last_step" if nvd == 1 else "movers_last_step"): [int(x) for x in
