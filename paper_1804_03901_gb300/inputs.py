@@ -196,6 +196,27 @@ def random_markers(seed, n, L, vmin, vmax, v_overhang=0.05, fmin=1e-12, fmax=1.0
     return x, v, f
 
 
+def boundary_markers3(seed, n, nx, L, nv, vmin, vmax):
+    """1d3v markers on the places where a cloud-in-cell weight is 0 or 1:
+    x at 0, at the cell edges and centres and one rounding below L; each
+    velocity component at the dual-row boundaries (cell centres), at vmin,
+    at vmax, one rounding below vmax and a quarter cell below vmin.  f over
+    three decades, distinct for every marker."""
+    rng = np.random.default_rng(seed)
+    dx = L / nx
+    nv, vmin, vmax = np.asarray(nv), np.asarray(vmin, float), np.asarray(vmax, float)
+    dv = (vmax - vmin) / nv
+    xs = np.concatenate([[0.0, np.nextafter(L, 0.0)], dx * np.arange(nx), dx * (np.arange(nx) + 0.5)])
+    x = xs[rng.integers(0, xs.size, n)]
+    v = np.empty((3, n))
+    for d in range(3):
+        rows = np.concatenate([vmin[d] + dv[d] * (np.arange(-1, nv[d] + 1) + 0.5),
+                               [vmin[d], vmax[d], np.nextafter(vmax[d], -np.inf), vmin[d] - 0.25 * dv[d]]])
+        v[d] = rows[rng.integers(0, rows.size, n)]
+    f = np.exp(rng.uniform(-3.0 * math.log(10.0), 0.0, n)) * (1.0 + 1e-9 * np.arange(n))
+    return x, v, f
+
+
 def random_markers3(seed, n, L, vmin, vmax, v_overhang=0.05, fmin=1e-12, fmax=1.0):
     """1d3v version of random_markers: v has shape (3, n), each component
     uniform over its range widened by v_overhang on both sides."""

@@ -196,3 +196,35 @@ def test_step_parity_at_the_largest_nx3(A, prec, nx):
     with pytest.raises(A.AvlError) as e:
         A.Simulation(dom, [A.make_species(**species[0])])
     assert e.value.status == A.AVL_EINVAL
+
+
+@pytest.mark.parametrize("prec", [0, 1], ids=["fp64", "fp32"])
+def test_boundary_positions_and_rows3(A, prec):
+    """Markers placed where the cloud-in-cell and the dual velocity rows
+    decide a cell: x at 0, at cell edges and centres, one rounding below L;
+    velocity components at dual-row boundaries (weight 0 or 1), on the grid's
+    first and last rows and just outside it (the FP64 deposit keeps positions
+    and rows as fixed-point counts, so these are the cases where its
+    rounding could pick another cell).  They sit among random markers that
+    give every reached cell a weight well above rounding: a weight that is 0
+    in exact arithmetic may come out as 0 or as 2^-52 on either side, and a
+    cell reached by such weights alone takes f = num / den = the marker's f
+    or 0 (Eq. 4), which no tolerance separates.  Set + refresh and two
+    steps, compared with the oracle from identical states."""
+    nx, L, dt = 16, 7.3, 0.07
+    species = species2((8, 6, 5))
+    sim, orc = make_pair(A, nx, L, dt, species, prec)
+    dx = L / nx
+    for s, sp in enumerate(species):
+        xb, vb, fb = inputs.boundary_markers3(77 + s, 1500, nx, L, sp["nv"], sp["vmin"], sp["vmax"])
+        xr, vr, fr = inputs.random_markers3(177 + s, 30000, L, sp["vmin"], sp["vmax"], fmin=1e-3)
+        sim.set_markers(s, np.concatenate([xb, xr]), np.concatenate([vb, vr], axis=1), np.concatenate([fb, fr]))
+    sync_oracle_to_gpu(sim, orc)
+    compare_grids(sim, orc, TOL[prec], "set")
+    for k in range(2):
+        sync_oracle_to_gpu(sim, orc)
+        sim.step(1)
+        orc.step(1)
+        compare_grids(sim, orc, TOL[prec], f"step {k}")
+        compare_markers(sim, orc, 1e-12 * L if prec == 0 else 2e-6 * dx, 1e-12 if prec == 0 else 1e-5, L)
+    sim.synchronize()
