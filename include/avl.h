@@ -65,7 +65,9 @@ typedef struct avl_ctx avl_ctx;
  * nvdim = 1: one chunk's deposit window (at least 7 velocity rows x nx
  *   cells, 12 B per cell in FP32, 16 B in FP64) must fit one CTA's shared
  *   memory, which bounds nx near 2400 (FP32) / 1800 (FP64); beyond it
- *   avl_init_markers and avl_set_markers return AVL_EINVAL.
+ *   avl_init_markers and avl_set_markers return AVL_EINVAL.  FP64 marker
+ *   positions are kept as 64-bit fixed-point counts of 2^-52 cells (in
+ *   both dimensions), which also needs nx < 2048.
  * nvdim = 3 (Sec. 2 with three velocity dimensions: the field accelerates
  *   v_x, an optional static background magnetic field, avl_set_bfield, turns
  *   v) needs nx <= 1024 (FP32) or nx <= 512 (FP64), nv[0] in [2, 1024],

@@ -139,6 +139,9 @@ void free_layout(avl_ctx* c, int s)
 avl_status plan_layout(avl_ctx* c, int s, long long n)
 {
     SpDev& sp = c->h.sp[s];
+    // FP64 positions are fixed-point counts of 2^-52 cells (PosX): nx 2^52 < 2^63
+    if (c->h.prec == AVL_FP64 && sp.nx >= 2048)
+        return fail(c, AVL_EINVAL, "FP64 1d1v markers need nx < 2048");
     AVL_CUDA(c, cudaStreamSynchronize(c->st));
     free_layout(c, s);
     sp.nchunk = 0;

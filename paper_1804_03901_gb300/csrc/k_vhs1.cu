@@ -84,6 +84,11 @@ __device__ __forceinline__ void loadg(const double* p, double (&o)[4])
     const double2 a = reinterpret_cast<const double2*>(p)[0], b = reinterpret_cast<const double2*>(p)[1];
     o[0] = a.x; o[1] = a.y; o[2] = b.x; o[3] = b.y;
 }
+__device__ __forceinline__ void loadg(const long long* p, long long (&o)[4])
+{
+    const longlong2 a = reinterpret_cast<const longlong2*>(p)[0], b = reinterpret_cast<const longlong2*>(p)[1];
+    o[0] = a.x; o[1] = a.y; o[2] = b.x; o[3] = b.y;
+}
 __device__ __forceinline__ void storeg(float* p, const float (&o)[4])
 {
     *reinterpret_cast<float4*>(p) = make_float4(o[0], o[1], o[2], o[3]);
@@ -96,6 +101,11 @@ __device__ __forceinline__ void storeg(double* p, const double (&o)[4])
 {
     reinterpret_cast<double2*>(p)[0] = make_double2(o[0], o[1]);
     reinterpret_cast<double2*>(p)[1] = make_double2(o[2], o[3]);
+}
+__device__ __forceinline__ void storeg(long long* p, const long long (&o)[4])
+{
+    reinterpret_cast<longlong2*>(p)[0] = make_longlong2(o[0], o[1]);
+    reinterpret_cast<longlong2*>(p)[1] = make_longlong2(o[2], o[3]);
 }
 // eight consecutive values (count kernel)
 __device__ __forceinline__ void load8(const float* p, float (&o)[8])
@@ -474,7 +484,7 @@ __global__ void __launch_bounds__(PD_THREADS) k_rs1(const StepArgs* __restrict__
     for (int tb = beg; tb < end; tb += TILE) {
         const int w0 = tb + warp * 32 * RS_ROUNDS;
         T dv[RS_ROUNDS], f[RS_ROUNDS];
-        Pos<T> pos[RS_ROUNDS];
+        PosM<T> pos[RS_ROUNDS];
 #pragma unroll
         for (int r = 0; r < RS_ROUNDS; ++r) {
             const int i = w0 + r * 32 + lane;
@@ -631,6 +641,8 @@ __global__ void __launch_bounds__(PD_THREADS, 2) k_pd1(const StepArgs* __restric
     const T qm_dt = (T)sp.qm_dt;
     const T dt_dx = (T)sp.dt_dx;
     const T vref_dtdx = (T)((sp.vmin[0] + (double)kb * sp.dv[0]) * sp.dt_dx);
+    // FP64: the displacement in 2^-52 cells (fixed-point positions, PosX)
+    const double dt_dx52 = sp.dt_dx * PosX::ONE, vref_dtdx52 = (double)vref_dtdx * PosX::ONE;
     double* ovf_num = sp.ovf;
     double* ovf_den = sp.ovf + (size_t)nv * nx;
     int* ovf_tag = sp.ovf_tag;
@@ -644,7 +656,7 @@ __global__ void __launch_bounds__(PD_THREADS, 2) k_pd1(const StepArgs* __restric
         const int g0 = base + threadIdx.x * MPT;
         const bool any = g0 < end;
         T dv8[MPT], f8[MPT];
-        Pos<T> pos8[MPT];
+        PosM<T> pos8[MPT];
         if (any) {
             loadg(dvp + g0, dv8);
             loadg(fp + g0, f8);
@@ -659,10 +671,10 @@ __global__ void __launch_bounds__(PD_THREADS, 2) k_pd1(const StepArgs* __restric
                     pos8[m].o = o8[m];
                 }
             } else {
-                double x8[MPT];
-                loadg(reinterpret_cast<const double*>(sp.mx[cb]) + g0, x8);
+                long long x8[MPT];
+                loadg(reinterpret_cast<const long long*>(sp.mx[cb]) + g0, x8);
 #pragma unroll
-                for (int m = 0; m < MPT; ++m) pos8[m].xi = x8[m];
+                for (int m = 0; m < MPT; ++m) pos8[m].X = x8[m];
             }
         }
         Run<T> run;
@@ -672,7 +684,7 @@ __global__ void __launch_bounds__(PD_THREADS, 2) k_pd1(const StepArgs* __restric
         auto one = [&](int m, bool okm) __attribute__((always_inline)) {
             int code = 0;
             if (okm) {
-                Pos<T>& pos = pos8[m];
+                PosM<T>& pos = pos8[m];
                 T dv = dv8[m];
                 const T fl = f8[m];
                 if (push) {
@@ -682,7 +694,10 @@ __global__ void __launch_bounds__(PD_THREADS, 2) k_pd1(const StepArgs* __restric
                     wrap_pair_in(i0, nx, ia, ib);
                     const T El = ((T)1 - w) * Es[ia] + w * Es[ib];
                     dv += qm_dt * El;
-                    pos.drift(vref_dtdx + dv * dt_dx, nx);
+                    if constexpr (sizeof(T) == 8)
+                        pos.drift_scaled(__fma_rn(dv, dt_dx52, vref_dtdx52), nx);   // in 2^-52 cells
+                    else
+                        pos.drift(vref_dtdx + dv * dt_dx, nx);
                     dv8[m] = dv;
                 }
                 // cloud-in-cell footprint of the new state (Eq. 4 weights)
@@ -736,10 +751,10 @@ __global__ void __launch_bounds__(PD_THREADS, 2) k_pd1(const StepArgs* __restric
                 storeg(reinterpret_cast<int*>(sp.mx[cb]) + g0, c8);
                 storeg(sp.moff[cb] + g0, o8);
             } else {
-                double x8[MPT];
+                long long x8[MPT];
 #pragma unroll
-                for (int m = 0; m < MPT; ++m) x8[m] = pos8[m].xi;
-                storeg(reinterpret_cast<double*>(sp.mx[cb]) + g0, x8);
+                for (int m = 0; m < MPT; ++m) x8[m] = pos8[m].X;
+                storeg(reinterpret_cast<long long*>(sp.mx[cb]) + g0, x8);
             }
         }
     }
@@ -1240,7 +1255,7 @@ __global__ void __launch_bounds__(PD_THREADS) k_src_scatter(const StepArgs* __re
                 const int d = dst[m];
                 if ((unsigned)d < (unsigned)n_all) {
                     const int c2 = chunk_of(d, sp.div_m, sp.div_l);
-                    const Pos<T> p = pos_from_cells<T>(mk.xi, sp.nx);
+                    const PosM<T> p = posm_from_cells<T>(mk.xi, sp.nx);
                     p.store(sp, 0, d);
                     const double vref = sp.vmin[0] + (double)sp.KB[0][c2] * sp.dv[0];
                     reinterpret_cast<T*>(sp.mv[0][0])[d] = (T)(mk.v - vref);
@@ -1265,7 +1280,7 @@ __global__ void k_get1(const StepArgs* __restrict__ A, int s, double* __restrict
     const int beg = c * sp.M, end = (int)min((long long)(c + 1) * sp.M, sp.n);
     const double vref = sp.vmin[0] + (double)sp.KB[cb][c] * sp.dv[0];
     for (int k = beg + threadIdx.x; k < end; k += blockDim.x) {
-        Pos<T> pos;
+        PosM<T> pos;
         pos.load(sp, cb, k);
         if (x) x[k] = pos.cells() * sp.dx;
         if (v) v[k] = vref + (double)reinterpret_cast<const T*>(sp.mv[cb][0])[k];

@@ -45,79 +45,15 @@
 
 namespace avl {
 
-// FP64 1d3v position: a 64-bit fixed-point count of 2^-52 cells, x = X 2^-52
-// cells with 0 <= X < nx 2^52 <= 2^61 (FP64 1d3v has nx <= 512).  It
-// resolves 2^-52 cells everywhere (a double of the same x resolves 2^-52 x),
-// and the cloud-in-cell reads the weight straight from the bits: the 52 low
-// bits of X - 2^51 are the mantissa of 1 + w, so that w and the lower cell
-// cost one FP64 operation instead of four (the form is limited by the FP64
-// pipe).  The drift converts the displacement once (a multiply and a
-// conversion).
-struct PosX {
-    long long X;
-    static constexpr double ONE = 4503599627370496.0;   // 2^52: one cell
-    __device__ __forceinline__ void load(const SpDev& sp, int cb, int k)
-    {
-        X = reinterpret_cast<const long long*>(sp.mx[cb])[k];
-    }
-    __device__ __forceinline__ void store(const SpDev& sp, int cb, int k) const
-    {
-        reinterpret_cast<long long*>(sp.mx[cb])[k] = X;
-    }
-    // cloud-in-cell: lower cell i0 (may be -1) and weight w of cell i0 + 1
-    __device__ __forceinline__ void cic(int& i0, double& w) const
-    {
-        const long long U = X - (1ll << 51);   // x - 1/2
-        i0 = (int)(U >> 52);                   // floor (arithmetic shift)
-        w = __longlong_as_double(0x3FF0000000000000ll | (U & 0x000FFFFFFFFFFFFFll)) - 1.0;
-    }
-    // x into [0, nx) (periodic); Y computed modulo 2^64 so that no
-    // displacement overflows
-    __device__ __forceinline__ void wrap(long long Y, int nx)
-    {
-        const long long N = (long long)nx << 52;
-        if ((unsigned long long)Y >= (unsigned long long)N) {
-            Y %= N;
-            if (Y < 0) Y += N;
-        }
-        X = Y;
-    }
-    // displacement of `scaled` 2^-52 cells (a double, rounded to the nearest
-    // count; the conversion saturates and maps NaN to 0)
-    __device__ __forceinline__ void drift_scaled(double scaled, int nx)
-    {
-        wrap((long long)((unsigned long long)X + (unsigned long long)__double2ll_rn(scaled)), nx);
-    }
-    __device__ __forceinline__ void drift(double disp, int nx) { drift_scaled(disp * ONE, nx); }
-    __device__ __forceinline__ double cells() const { return (double)X * (1.0 / ONE); }
-    __device__ __forceinline__ static PosX from_cells(double xi, int nx)
-    {
-        PosX p;
-        p.X = 0;
-        p.drift(xi, nx);
-        return p;
-    }
-};
-
+// position type of the 1d3v kernels (common.cuh): FP32 int cell + FP32
+// offset, FP64 PosX
 template <typename T>
-struct Pos3Sel {
-    using type = Pos<T>;
-};
-template <>
-struct Pos3Sel<double> {
-    using type = PosX;
-};
-// position type of the 1d3v kernels: FP32 int cell + FP32 offset, FP64 PosX
-template <typename T>
-using Pos3 = typename Pos3Sel<T>::type;
+using Pos3 = PosM<T>;
 
 template <typename T>
 __device__ __forceinline__ Pos3<T> pos3_from_cells(double xi, int nx)
 {
-    if constexpr (sizeof(T) == 8)
-        return PosX::from_cells(xi, nx);
-    else
-        return pos_from_cells<T>(xi, nx);
+    return posm_from_cells<T>(xi, nx);
 }
 
 template <typename T>

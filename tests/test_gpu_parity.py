@@ -319,9 +319,11 @@ def test_conservation_drift_fp32_within_oracle_drift(A):
 def test_largest_deposit_window(A):
     """A wide x grid (nx = 2048): the FP32 deposit window of 8 velocity rows
     (numerator, denominator and the reference plane: 196 KB) still fits one
-    CTA's shared memory and the step matches the oracle; the FP64 window
-    (8 bytes per plane cell) does not, and creating the markers reports
-    AVL_EINVAL instead of launching."""
+    CTA's shared memory and the step matches the oracle.  In FP64 creating
+    the markers reports AVL_EINVAL instead of launching: at nx = 2048 for
+    the fixed-point positions (nx 2^52 must stay below 2^63), at nx = 2040
+    because the window (8 bytes per plane cell, 7 rows at least) does not
+    fit."""
     nx, L, dt = 2048, 7.3, 0.07
     species = SPECIES2(64)
     sim, orc = make_pair(A, nx, L, dt, species, A.AVL_FP32)
@@ -334,9 +336,10 @@ def test_largest_deposit_window(A):
         orc.step(1)
         compare_grids(sim, orc, TOL[1], f"nx 2048 step {k}")
     sim.close()
-    sim, _ = make_pair(A, nx, L, dt, species, A.AVL_FP64)
-    x, v, f = inputs.random_markers(31, 20011, L, species[0]["vmin"][0], species[0]["vmax"][0])
-    with pytest.raises(A.AvlError) as e:
-        sim.set_markers(0, x, v, f)
-    assert e.value.status == A.AVL_EINVAL and "shared memory" in str(e.value)
-    sim.close()
+    for nxd, why in ((2048, "nx < 2048"), (2040, "shared memory")):
+        sim, _ = make_pair(A, nxd, L, dt, species, A.AVL_FP64)
+        x, v, f = inputs.random_markers(31, 20011, L, species[0]["vmin"][0], species[0]["vmax"][0])
+        with pytest.raises(A.AvlError) as e:
+            sim.set_markers(0, x, v, f)
+        assert e.value.status == A.AVL_EINVAL and why in str(e.value), (nxd, str(e.value))
+        sim.close()
