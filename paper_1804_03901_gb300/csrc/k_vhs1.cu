@@ -538,8 +538,10 @@ __global__ void __launch_bounds__(PD_THREADS) k_rs1(const StepArgs* __restrict__
 // same footprint summed in registers first) and written back in place, and
 // its new key is counted into cnt[1 - hsel] for the next step.  On a re-sort
 // step the markers are read from the buffer k_rs1 has just written.
+// FP64: one CTA per SM with the registers the push and deposit need (at two
+// CTAs, 64 registers, it spills).
 template <typename T, bool BATCH, bool PUSH>
-__global__ void __launch_bounds__(PD_THREADS, 2) k_pd1(const StepArgs* __restrict__ A0,
+__global__ void __launch_bounds__(PD_THREADS, sizeof(T) == 8 ? 1 : 2) k_pd1(const StepArgs* __restrict__ A0,
                                                        const BatchMap* __restrict__ bm)
 {
     constexpr int mode = PUSH ? 1 : 0;
