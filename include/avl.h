@@ -311,7 +311,9 @@ avl_status avl_field_solve_noalloc(int32_t nx, double L, double poisson_const, i
  * checkpoint) is kept by the context for the next call.  The context's own
  * markers, f, rho and E are left untouched.  Blocks until done.  1d1v only.
  * Errors: AVL_EINVAL (nvdim 3, NULL pointers, nsteps < 0, ckpt_every < 1,
- * theta counts), AVL_ESTATE (a species without lattice markers), AVL_ENOMEM. */
+ * theta counts, FP64 with nx >= 2048: its positions are fixed-point counts
+ * of 2^-52 cells), AVL_ESTATE (a species without lattice markers),
+ * AVL_ENOMEM. */
 avl_status avl_adjoint(avl_ctx* ctx, int32_t s, const avl_f0* theta, int32_t nsteps, int32_t ckpt_every,
                        double* dJ_damp, double* dJ_ddrift, double* J);
 

@@ -1329,6 +1329,8 @@ avl_status avl_adjoint(avl_ctx* c, int32_t s, const avl_f0* theta, int32_t nstep
     avl_status st = check_species(c, s);
     if (st) return st;
     if (c->h.nvdim != 1) return fail(c, AVL_EINVAL, "avl_adjoint supports 1d1v contexts");
+    if (c->h.prec == AVL_FP64 && c->h.fd.nx >= 2048)   // fixed-point positions (PosX)
+        return fail(c, AVL_EINVAL, "the FP64 adjoint needs nx < 2048");
     if (!theta || !dJ_damp || !dJ_ddrift || !J) return fail(c, AVL_EINVAL, "theta or an output is NULL");
     if (nsteps < 0 || ckpt_every < 1) return fail(c, AVL_EINVAL, "nsteps must be >= 0 and ckpt_every >= 1");
     if (theta->nbeam < 1 || theta->nbeam > 4 || theta->nmode < 0 || theta->nmode > 64)

@@ -42,7 +42,7 @@ struct AdjSp {
     int lat[2];
     unsigned long long seed;
     double jitter;
-    void* hx;          // [K + 1][n] positions per slot (FP32: int cell; FP64: double cells)
+    void* hx;          // [K + 1][n] positions per slot (FP32: int cell; FP64: int64 2^-52 cells, PosX)
     float* hoff;       // [K + 1][n] FP32 offsets
     void* hv;          // [K + 1][n] velocities
     void* cx;          // [C][n] checkpoints
@@ -92,15 +92,15 @@ struct APos<float> {
 };
 template <>
 struct APos<double> {
-    __device__ static Pos<double> load(const AdjSp& a, int slot, long long k)
+    __device__ static PosX load(const AdjSp& a, int slot, long long k)
     {
-        Pos<double> p;
-        p.xi = reinterpret_cast<const double*>(a.hx)[(size_t)slot * a.n + k];
+        PosX p;
+        p.X = reinterpret_cast<const long long*>(a.hx)[(size_t)slot * a.n + k];
         return p;
     }
-    __device__ static void store(const AdjSp& a, int slot, long long k, const Pos<double>& p)
+    __device__ static void store(const AdjSp& a, int slot, long long k, const PosX& p)
     {
-        reinterpret_cast<double*>(a.hx)[(size_t)slot * a.n + k] = p.xi;
+        reinterpret_cast<long long*>(a.hx)[(size_t)slot * a.n + k] = p.X;
     }
 };
 
@@ -154,7 +154,7 @@ __global__ void k_ad_init(const StepArgs* __restrict__ A, const AdjDev* __restri
         const double J1 = (jitter_u01(a.seed, s, m, 1) - 0.5) * a.jitter;
         const double xi = (double)i + ((double)ia + 0.5 + J0) / px;
         const double v[3] = {sp.vmin[0] + ((double)j + ((double)ib + 0.5 + J1) / pv) * sp.dv[0], 0.0, 0.0};
-        APos<T>::store(a, 0, m, pos_from_cells<T>(xi, sp.nx));
+        APos<T>::store(a, 0, m, posm_from_cells<T>(xi, sp.nx));
         reinterpret_cast<T*>(a.hv)[m] = (T)v[0];
         reinterpret_cast<T*>(a.f)[m] = (T)f0_value(f0, 1, sp.nx * sp.dx, xi * sp.dx, v);
         reinterpret_cast<T*>(a.lx)[m] = (T)0;
@@ -175,7 +175,7 @@ __global__ void k_ad_dep(const StepArgs* __restrict__ A, const AdjDev* __restric
     const T* f = reinterpret_cast<const T*>(a.f);
     const T* vv = reinterpret_cast<const T*>(a.hv) + (size_t)slot * a.n;
     for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < a.n; k += (long long)gridDim.x * blockDim.x) {
-        const Pos<T> p = APos<T>::load(a, slot, k);
+        const PosM<T> p = APos<T>::load(a, slot, k);
         int i0;
         T wx;
         p.cic(i0, wx);
@@ -250,7 +250,7 @@ __global__ void k_ad_push(const StepArgs* __restrict__ A, const AdjDev* __restri
     T* v1 = reinterpret_cast<T*>(a.hv) + (size_t)(slot + 1) * a.n;
     const T qm_dt = (T)sp.qm_dt, dt_dx = (T)sp.dt_dx;
     for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < a.n; k += (long long)gridDim.x * blockDim.x) {
-        Pos<T> p = APos<T>::load(a, slot, k);
+        PosM<T> p = APos<T>::load(a, slot, k);
         T v = v0[k];
         if (sp.mobile) {
             int i0;
@@ -306,7 +306,7 @@ __global__ void __launch_bounds__(256) k_ad_e(const StepArgs* __restrict__ A, co
     const T c0 = (T)sp.qm_dt;
     const T dt = (T)(sp.dt_dx * sp.dx);
     for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < a.n; k += (long long)gridDim.x * blockDim.x) {
-        const Pos<T> p = APos<T>::load(a, slot, k);
+        const PosM<T> p = APos<T>::load(a, slot, k);
         int i0;
         T w;
         p.cic(i0, w);
@@ -370,7 +370,7 @@ __global__ void k_ad_gather(const StepArgs* __restrict__ A, const AdjDev* __rest
     const T dt = (T)(sp.dt_dx * sp.dx);
     const T qm_dt = (T)sp.qm_dt;
     for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < a.n; k += (long long)gridDim.x * blockDim.x) {
-        const Pos<T> p = APos<T>::load(a, slot, k);
+        const PosM<T> p = APos<T>::load(a, slot, k);
         int i0;
         T wxT;
         p.cic(i0, wxT);
