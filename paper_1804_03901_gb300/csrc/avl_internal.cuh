@@ -7,7 +7,8 @@
 //   arrays:
 //     FP32: cell int32[n], off f32[n] (position in cells = cell + off, off in
 //           [0,1)), dv f32[n], f f32[n]                      16 B per marker
-//     FP64: xi f64[n] (position in cells), dv f64[n], f f64[n]   24 B
+//     FP64: X int64[n] (position: a count of 2^-52 cells), dv f64[n],
+//           f f64[n]                                         24 B
 //   Markers are sorted by their key, the lower velocity row of their
 //   cloud-in-cell footprint (the "dual row", clamped to [0, nv)).  The marker
 //   array is cut into chunks of M markers (chunk c = [c M, (c+1) M)); one CTA
@@ -87,7 +88,7 @@ struct SpDev {
     unsigned div_m;            // magic multiplier and shift for slot / M
     int div_l;
     // markers
-    void* mx[2];               // FP32: int cell; FP64: 1d1v double xi, 1d3v int64 X (2^-52 cells)
+    void* mx[2];               // FP32: int cell; FP64: int64 X (2^-52 cells)
     float* moff[2];            // FP32 only
     void* mv[2][3];            // velocity components (vx chunk-relative)
     void* mf[2];

@@ -84,55 +84,14 @@ struct Pos<float> {
     __device__ __forceinline__ double cells() const { return (double)c + (double)o; }
 };
 
-// FP64: position in cells, xi in [0, nx)
-template <>
-struct Pos<double> {
-    double xi;
-    __device__ __forceinline__ void load(const SpDev& sp, int cb, int k)
-    {
-        xi = reinterpret_cast<const double*>(sp.mx[cb])[k];
-    }
-    __device__ __forceinline__ void store(const SpDev& sp, int cb, int k) const
-    {
-        reinterpret_cast<double*>(sp.mx[cb])[k] = xi;
-    }
-    __device__ __forceinline__ void cic(int& i0, double& w) const
-    {
-        const double u = xi - 0.5;
-        const double fl = floor(u);
-        i0 = static_cast<int>(fl);
-        w = u - fl;
-    }
-    __device__ __forceinline__ void drift(double disp, int nx) { wrap(xi + disp, nx); }
-    // the same drift with the displacement v c fused into the addition
-    __device__ __forceinline__ void drift_fma(double v, double c, int nx) { wrap(fma(v, c, xi), nx); }
-    // x into [0, nx) (periodic)
-    __device__ __forceinline__ void wrap(double x, int nx)
-    {
-        const double n = static_cast<double>(nx);
-        // x < 0 or x >= n from the bit patterns (a negative x or -0 has the
-        // sign bit set; for x >= +0 the order of doubles is the integer
-        // order of their bits), so that the FP64 pipe is left to arithmetic
-        const long long bx = __double_as_longlong(x);
-        if (bx < 0 || bx >= __double_as_longlong(n)) {
-            x = fmod(x, n);
-            if (x < 0.0) x += n;
-            if (x >= n) x -= n;
-        }
-        xi = x;
-    }
-    __device__ __forceinline__ double cells() const { return xi; }
-};
-
-// FP64 marker position of the step kernels: a 64-bit fixed-point count of
-// 2^-52 cells, x = X 2^-52 cells with 0 <= X < nx 2^52 < 2^63 (FP64 grids
-// have nx < 2048).  It resolves 2^-52 cells everywhere (a double of the
-// same x resolves 2^-52 x),
-// and the cloud-in-cell reads the weight straight from the bits: the 52 low
-// bits of X - 2^51 are the mantissa of 1 + w, so that w and the lower cell
-// cost one FP64 operation instead of four (the form is limited by the FP64
-// pipe).  The drift converts the displacement once (a multiply and a
-// conversion).
+// FP64 marker position (step kernels and adjoint engine): a 64-bit
+// fixed-point count of 2^-52 cells, x = X 2^-52 cells with
+// 0 <= X < nx 2^52 < 2^63 (FP64 grids have nx < 2048).  It resolves 2^-52
+// cells everywhere (a double of the same x resolves 2^-52 x), and the
+// cloud-in-cell reads the weight straight from the bits: the 52 low bits of
+// X - 2^51 are the mantissa of 1 + w, so that w and the lower cell cost one
+// FP64 operation instead of four (the form is limited by the FP64 pipe).
+// The drift converts the displacement once (a multiply and a conversion).
 struct PosX {
     long long X;
     static constexpr double ONE = 4503599627370496.0;   // 2^52: one cell
@@ -180,24 +139,27 @@ struct PosX {
 };
 
 template <typename T>
-struct PosSel {
-    using type = Pos<T>;
+struct PosSel;
+template <>
+struct PosSel<float> {
+    using type = Pos<float>;
 };
 template <>
 struct PosSel<double> {
     using type = PosX;
 };
-// marker position type of the step kernels: FP32 int cell + FP32 offset,
-// FP64 PosX (the adjoint keeps plain Pos<double> in its own arrays)
+// marker position type: FP32 int cell + FP32 offset, FP64 PosX
 template <typename T>
 using PosM = typename PosSel<T>::type;
 
 // position from a value in cells (FP64) given by a caller or the generator
 template <typename T>
-__device__ __forceinline__ Pos<T> pos_from_cells(double xi, int nx)
+__device__ __forceinline__ PosM<T> posm_from_cells(double xi, int nx)
 {
-    Pos<T> p;
-    if constexpr (sizeof(T) == 4) {
+    if constexpr (sizeof(T) == 8) {
+        return PosX::from_cells(xi, nx);
+    } else {
+        Pos<float> p;
         const double c = floor(xi);
         int ci = (int)c;
         const double o = xi - c;
@@ -209,19 +171,8 @@ __device__ __forceinline__ Pos<T> pos_from_cells(double xi, int nx)
             p.o = 0.0f;
             p.c = (p.c + 1) % nx;
         }
-    } else {
-        p.xi = xi < nx ? xi : xi - nx;
+        return p;
     }
-    return p;
-}
-
-template <typename T>
-__device__ __forceinline__ PosM<T> posm_from_cells(double xi, int nx)
-{
-    if constexpr (sizeof(T) == 8)
-        return PosX::from_cells(xi, nx);
-    else
-        return pos_from_cells<T>(xi, nx);
 }
 
 // ---------------------------------------------------------------------------
